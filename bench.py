@@ -1,0 +1,282 @@
+"""Benchmark: cascaded biquad filtering throughput (GS/s) on one GB300.
+
+Workload (default): order-16 Butterworth low-pass (8 sections) at 0.05 of Nyquist, one float32
+signal of 2^28 N(0,1) samples from seed 1 -- the plain single-signal kernel at full size.
+A step is one pass of the whole hot path over the signal: one sos_filter_run call (all 8
+sections, one kernel launch).  Inputs (1 GiB) and outputs (1 GiB) are both larger than the
+129 MB L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the float64 CPU oracle instead,
+on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "order-16 Butterworth lowpass (8 SOS) at 0.05 Nyquist, 1 float32 signal of 2^28 N(0,1) samples, seed 1"
+N_SAMPLES = 1 << 28
+ORDER = 16
+WN = 0.05
+SEED = 1
+BYTES_PER_SAMPLE = 8  # 4 B read + 4 B written: the algorithmic traffic of the filter (Sec. IV-C, Eq. 28)
+CPU_SAMPLE = 1 << 24  # bounded oracle sample (about 10-30 s of one host core at order 16)
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def bench_reference(args):
+    """The float64 CPU oracle on the host cores, bounded sample of the same workload."""
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    import workloads
+    from workloads import designs
+    sos = designs.butter_lowpass(ORDER, WN)
+    x = workloads.normal_f32(SEED, CPU_SAMPLE)
+    oracle.sosfilt(sos, x[:4096])  # build/load
+    times = []
+    for _ in range(max(1, args.warmup if args.warmup < 2 else 1)):
+        oracle.sosfilt(sos, x[: 1 << 16])
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.sosfilt(sos, x)
+        times.append(time.perf_counter() - t0)
+    per = float(np.mean(times))
+    gss = CPU_SAMPLE / per / 1e9
+    line = {"impl": "reference", "metric": "GS/s", "value": gss, "unit": "GS/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": f"first 2^{int(np.log2(CPU_SAMPLE))} samples per step"},
+            "cpu_baseline": {"value": gss, "unit": "GS/s", "cores": 1, "kind": "oracle",
+                             "sample": f"first 2^{int(np.log2(CPU_SAMPLE))} samples of the workload, 1 core"},
+            "e2e": {"value": gss, "unit": "GS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_leg():
+    import oracle
+    import workloads
+    from workloads import designs
+    sos = designs.butter_lowpass(ORDER, WN)
+    x = workloads.normal_f32(SEED, CPU_SAMPLE)
+    oracle.sosfilt(sos, x[:1024])
+    t0 = time.perf_counter()
+    oracle.sosfilt(sos, x)
+    dt = time.perf_counter() - t0
+    return {"value": CPU_SAMPLE / dt / 1e9, "unit": "GS/s", "cores": 1, "kind": "oracle",
+            "sample": f"first 2^{int(np.log2(CPU_SAMPLE))} samples of the workload, one host core, {dt:.1f} s"}
+
+
+def bench_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import workloads
+    from workloads import designs
+    from paper_2607_23763_gb300 import SosFilter
+
+    world, rank, local = _dist()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    sos = designs.butter_lowpass(ORDER, WN)
+    x_host = workloads.normal_f32(SEED, N_SAMPLES)
+    tuning = {}
+    if args.N:
+        tuning["N"] = args.N
+    if args.lbw:
+        tuning["lookback_width"] = args.lbw
+    tuning = tuning or None
+    f = SosFilter(sos, tuning=tuning)
+    x = torch.from_numpy(x_host).to(dev)
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        f.run(x, y)
+    barrier()
+    assert f.sync_status() == 0
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        start.record(stream)
+        for _ in range(args.steps):
+            f.run(x, y)
+        stop.record(stream)
+        barrier()
+    ms = start.elapsed_time(stop)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    gss = N_SAMPLES * world / (ms_step * 1e-3) / 1e9
+    assert f.sync_status() == 0
+
+    # end to end: pinned host input -> device -> filter -> pinned host output, every step
+    xh = torch.from_numpy(x_host).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    for _ in range(2):
+        x.copy_(xh, non_blocking=True)
+        f.run(x, y)
+        yh.copy_(y, non_blocking=True)
+    barrier()
+    e_steps = max(3, min(args.steps, 10))
+    t0 = time.perf_counter()
+    start.record(stream)
+    for _ in range(e_steps):
+        x.copy_(xh, non_blocking=True)
+        f.run(x, y)
+        yh.copy_(y, non_blocking=True)
+    stop.record(stream)
+    barrier()
+    e_ms = start.elapsed_time(stop) / e_steps
+    e_gss = N_SAMPLES * world / (e_ms * 1e-3) / 1e9
+
+    hbm_peak, peak_kind = _peaks()
+    achieved = BYTES_PER_SAMPLE * N_SAMPLES / (ms_step * 1e-3) / 1e9
+    clocks = clk.summary()
+    line = {
+        "metric": "GS/s", "value": gss, "unit": "GS/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "samples": N_SAMPLES, "sections": ORDER // 2,
+                   "N": args.N or "default", "L": 32, "l2": "inputs and outputs larger than L2 (1 GiB each)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                     "kernel": "sos_dccr_kernel<8,N,true,4>"},
+        "e2e": {"value": e_gss, "unit": "GS/s", "h2d_bytes_per_step": 4 * N_SAMPLES,
+                "d2h_bytes_per_step": 4 * N_SAMPLES},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline_leg()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    f.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--N", type=int, default=0, help="samples per thread (16/32/64); 0 = library default")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--lbw", type=int, default=0, help="lookback width (predecessor blocks per round / 32); 0 = default")
+    ap.add_argument("--order", type=int, default=16, help="filter order (16 = the workload; others for sweeps)")
+    ap.add_argument("--log2n", type=int, default=28,
+                    help="signal length 2^log2n (28 = the workload; smaller only for profiling captures)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    global N_SAMPLES, WORKLOAD, ORDER
+    if args.order != 16:
+        ORDER = args.order
+        WORKLOAD = WORKLOAD.replace("order-16", f"order-{ORDER}").replace("(8 SOS)", f"({ORDER // 2} SOS)")
+    if args.log2n != 28:
+        N_SAMPLES = 1 << args.log2n
+        WORKLOAD = WORKLOAD.replace("2^28", f"2^{args.log2n}")
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,168 @@
+/*
+ * sosfilt.h -- C ABI of libsosfilt.so: cascaded second-order IIR filtering of
+ * long float32 signals on one GB300 GPU (sm_103a).
+ *
+ * Method (Zhai & Paris, "Parallel Cascaded Recursive Filtering on Multi-Core
+ * CPUs and GPUs"): every group of C = N*L samples is stride-N permuted into the
+ * block-banded system of Eq. 2-3 (Sec. II-B); its zero-state response is solved
+ * in registers by divide-and-conquer cyclic reduction (Sec. II-E, Eqs. 19-23),
+ * which exposes both terminal samples of the group before back substitution;
+ * terminal states are carried across groups by decoupled lookback (Sec. IV-B,
+ * Eq. 25) and the homogeneous correction (Eq. 24) is applied once a group's
+ * incoming state is known.  All K sections of a group stay in registers inside
+ * one kernel (Sec. IV-A).
+ *
+ * Conventions used by every entry point
+ *   - Coefficients: `sos` is a host array [n_sections][5] of double holding
+ *     b0, b1, b2, a1, a2 per section, a0 = 1 (Eq. 1 with the section gain b0
+ *     kept per section).  Section k's output is section k+1's input.
+ *   - State: [n_sections][2] float32 in transposed direct form II, the
+ *     convention of scipy.signal.sosfilt: after a sample x with output y,
+ *         z1 = b1*x - a1*y + z2_old,   z2 = b2*x - a2*y.
+ *     (Sec. II-B carries the last two inputs and outputs instead; both fix
+ *     the same future outputs: (z1, z2) is exactly the forcing B_ x_-1 - A_ y_-1
+ *     on the first two rows of Eq. 2.)
+ *   - Samples are float32; arithmetic is float32 (tables are derived in
+ *     float64 on the host and rounded once).
+ *   - Device pointers are plain CUDA device addresses (e.g. torch tensors'
+ *     data_ptr()).  `stream` is a cudaStream_t passed as void* (NULL = the
+ *     legacy default stream).  Every call that takes a stream is asynchronous
+ *     on it; argument errors are returned synchronously; device-side errors
+ *     (a lookback wait that ran out of time) set a sticky status read by
+ *     sos_filter_sync_status().
+ *   - Thread safety: a filter object may be used by one host thread and one
+ *     stream at a time; different filter objects are independent.
+ */
+#ifndef SOSFILT_H
+#define SOSFILT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SOS_OK = 0,
+    SOS_EINVAL = -1,    /* bad argument: NULL where not allowed, n < 0, K out of range, overlap */
+    SOS_ENOMEM = -2,    /* device or host allocation failed */
+    SOS_ECUDA = -3,     /* a CUDA runtime call failed (launch, copy, device query) */
+    SOS_ETIMEOUT = -4,  /* a lookback wait exceeded its cycle budget on the device */
+    SOS_EUNSTABLE = -5, /* a section violates |a2| < 1, |a1| < 1 + a2, or a coefficient is not finite */
+    SOS_EBUDGET = -6    /* the request exceeds the memory budget of the caller's setting */
+} sos_status;
+
+/* Opaque filter object, owned by the library. */
+typedef struct sos_filter sos_filter;
+
+/*
+ * Launch configuration.  Any field left 0 selects the library's default for
+ * that field (the built-in per-order table).
+ *   N                  samples per thread (block count of Eq. 2): 16, 32, 64 or 128
+ *   L                  threads per group (block length of Eq. 2): 32
+ *   groups_per_cta     groups (warps) per thread block: 1..8
+ *   threads_per_group  L (one thread group per signal block group, Sec. IV-D)
+ *   fp64_carry         reserved: must be 0 (carries are float32)
+ *   spin_budget_cycles upper bound, in SM clock cycles, on one lookback wait;
+ *                      on expiry the kernel records SOS_ETIMEOUT and returns
+ *   lookback_width     predecessors read per lookback round, in units of 32:
+ *                      1, 2, 4, 8 or 16 (values other than the default for N
+ *                      are available for 8-section passes with b0 != 0)
+ */
+typedef struct {
+    int N, L, groups_per_cta, threads_per_group, fp64_carry;
+    long long spin_budget_cycles;
+    int lookback_width;
+} sos_tuning;
+
+/*
+ * Create a filter from K = n_sections sections (Eq. 1).
+ *   sos  host [K][5] double: b0, b1, b2, a1, a2 (copied; caller keeps ownership)
+ *   zi   host [K][2] float32 initial resident state for sos_filter_stream_push
+ *        (NULL = zeros)
+ *   t    host tuning (NULL = defaults)
+ *   out  receives the new filter; *out is NULL on failure
+ * Errors: SOS_EINVAL (K < 1 or K > 64, NULL sos/out, bad tuning),
+ * SOS_EUNSTABLE (a section outside the stability triangle or not finite),
+ * SOS_ENOMEM, SOS_ECUDA.  Allocates device memory on the current device.
+ */
+sos_status sos_filter_create(int n_sections, const double *sos, const float *zi, const sos_tuning *t,
+                             sos_filter **out);
+
+/* Release a filter and its device memory.  NULL is a no-op.  Synchronizes the
+ * device work the library enqueued for this filter before freeing. */
+sos_status sos_filter_destroy(sos_filter *f);
+
+/*
+ * Filter one signal: y = cascade(x), Sec. II and Sec. IV (one kernel launch
+ * per pass of up to 8 sections).
+ *   x_dev   device float32[n] input, contiguous
+ *   y_dev   device float32[n] output, contiguous; y_dev == x_dev (in place) is
+ *           allowed, any other overlap is SOS_EINVAL
+ *   n       number of samples, >= 0; n = 0 only copies zi to zf
+ *   zi_dev  device float32[K][2] initial state or NULL (zeros)
+ *   zf_dev  device float32[K][2] receives the final state, or NULL; may equal zi_dev
+ *   stream  cudaStream_t as void*
+ * Ownership: the caller owns x, y, zi, zf; the library owns its workspace
+ * (lookback descriptors, ticket counter, status word), grown on demand.
+ */
+sos_status sos_filter_run(sos_filter *f, const float *x_dev, float *y_dev, int64_t n, const float *zi_dev,
+                          float *zf_dev, void *stream);
+
+/*
+ * Filter many independent signals of uneven length and order in one
+ * persistent launch over a global queue of (signal, group) tiles, with
+ * lookback chains kept per signal.  Zero initial state for every signal.
+ *   n_signals  >= 0
+ *   filters    host array [n_signals] of filter objects (may repeat)
+ *   x_dev      host array [n_signals] of device input pointers
+ *   y_dev      host array [n_signals] of device output pointers (in place allowed)
+ *   n          host array [n_signals] of lengths (>= 0)
+ */
+sos_status sos_filter_run_batch(int n_signals, sos_filter *const *filters, const float *const *x_dev,
+                                float *const *y_dev, const int64_t *n, void *stream);
+
+/*
+ * Continue filtering from the filter's resident device state (a [K][2]
+ * float32 array kept on the device between calls) and update it in place, so
+ * that consecutive chunks equal one long call.  Calls on one filter must be
+ * serialized on one stream.
+ */
+sos_status sos_filter_stream_push(sos_filter *f, const float *x_dev, float *y_dev, int64_t n, void *stream);
+
+/*
+ * Read and/or replace the resident state.
+ *   z_out  [K][2] float32 receives the state (NULL = skip)
+ *   z_in   [K][2] float32 new state (NULL = keep)
+ *   on_device  nonzero: z_out/z_in are device pointers and the copies are
+ *              enqueued on the filter's last stream; zero: host pointers and
+ *              the call synchronizes that stream first.
+ * Returns the sticky device status (SOS_ETIMEOUT after a lookback timeout).
+ */
+sos_status sos_filter_stream_state(sos_filter *f, float *z_out, const float *z_in, int on_device);
+
+/* Synchronize the filter's last stream and return the sticky device status. */
+sos_status sos_filter_sync_status(sos_filter *f);
+
+/*
+ * Phase trace for diagnostics (no counterpart in the paper's method; it
+ * measures where a block's time goes: stage-in, each section's carry
+ * publication and resolution, stage-out).  When buf_dev is non-NULL, every
+ * following launch on this filter has thread 0 of each thread block write 32
+ * uint64 words at buf_dev[32 * ticket ...] for tickets < capacity_blocks:
+ *   [0] ticket + 1, [1] start, [2] after drawing the ticket, [3] after stage-in,
+ *   [4 + 3s] block carry of section s published, [5 + 3s] incoming state of
+ *   section s known, [6 + 3s] lookback rounds (low 32 bits) and waits (high
+ *   32 bits), [28] before stage-out, [29] end, [30] SM id;
+ * times are the device global timer in ns.  buf_dev = NULL switches it off.
+ * The caller owns the buffer.  Errors: SOS_EINVAL for capacity < 0.
+ */
+sos_status sos_filter_trace(sos_filter *f, uint64_t *buf_dev, int64_t capacity_blocks);
+
+/* Human-readable name of a status code (static storage). */
+const char *sos_status_string(sos_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SOSFILT_H */

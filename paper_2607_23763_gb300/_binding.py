@@ -1,0 +1,189 @@
+"""ctypes binding of libsosfilt.so: argument marshalling only.
+
+Every step of the filtering runs in the library's CUDA kernels; this module
+only turns torch tensors into device pointers and the current torch stream
+into a cudaStream_t.  There is no CPU fallback: if the library has not been
+built, or no CUDA device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsosfilt.so")
+
+SOS_OK, SOS_EINVAL, SOS_ENOMEM, SOS_ECUDA, SOS_ETIMEOUT, SOS_EUNSTABLE, SOS_EBUDGET = 0, -1, -2, -3, -4, -5, -6
+STATUS_NAMES = {0: "SOS_OK", -1: "SOS_EINVAL", -2: "SOS_ENOMEM", -3: "SOS_ECUDA", -4: "SOS_ETIMEOUT",
+                -5: "SOS_EUNSTABLE", -6: "SOS_EBUDGET"}
+
+# every symbol declared in include/sosfilt.h
+EXPORTED = (
+    "sos_filter_create", "sos_filter_destroy", "sos_filter_run", "sos_filter_run_batch",
+    "sos_filter_stream_push", "sos_filter_stream_state", "sos_filter_sync_status", "sos_filter_trace",
+    "sos_status_string",
+)
+
+
+class SosError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: {STATUS_NAMES.get(code, code)}")
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("L", ctypes.c_int), ("groups_per_cta", ctypes.c_int),
+                ("threads_per_group", ctypes.c_int), ("fp64_carry", ctypes.c_int),
+                ("spin_budget_cycles", ctypes.c_longlong), ("lookback_width", ctypes.c_int)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load_library(path: str | None = None):
+    """Load libsosfilt.so (built by ``paper_2607_23763_gb300.build``); raise if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"{p} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+        lib = ctypes.CDLL(p)
+        vp, i64, c_int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+        lib.sos_filter_create.argtypes = [c_int, vp, vp, vp, ctypes.POINTER(vp)]
+        lib.sos_filter_destroy.argtypes = [vp]
+        lib.sos_filter_run.argtypes = [vp, vp, vp, i64, vp, vp, vp]
+        lib.sos_filter_run_batch.argtypes = [c_int, vp, vp, vp, vp, vp]
+        lib.sos_filter_stream_push.argtypes = [vp, vp, vp, i64, vp]
+        lib.sos_filter_stream_state.argtypes = [vp, vp, vp, c_int]
+        lib.sos_filter_sync_status.argtypes = [vp]
+        lib.sos_filter_trace.argtypes = [vp, vp, i64]
+        lib.sos_status_string.argtypes = [c_int]
+        lib.sos_status_string.restype = ctypes.c_char_p
+        for name in EXPORTED:
+            if name == "sos_status_string":
+                continue
+            getattr(lib, name).restype = c_int
+        _lib = lib
+    return _lib
+
+
+def _check(code: int, what: str):
+    if code != SOS_OK:
+        raise SosError(code, what)
+
+
+def _stream_handle(stream) -> int | None:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def _dptr(t, name: str) -> int:
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
+    return t.data_ptr()
+
+
+class SosFilter:
+    """A cascade of K second-order sections (Eq. 1) bound to the current CUDA device.
+
+    ``sos`` is [K][5] (b0, b1, b2, a1, a2) float64; ``zi`` the initial resident state [K][2].
+    """
+
+    def __init__(self, sos, zi=None, tuning: dict | None = None):
+        lib = load_library()
+        sos = np.ascontiguousarray(np.asarray(sos, dtype=np.float64).reshape(-1, 5))
+        self.K = int(sos.shape[0])
+        self.sos = sos
+        zi_arr = None if zi is None else np.ascontiguousarray(np.asarray(zi, dtype=np.float32).reshape(self.K, 2))
+        t = None
+        if tuning:
+            t = Tuning(**{k: int(v) for k, v in tuning.items()})
+        h = ctypes.c_void_p()
+        _check(lib.sos_filter_create(self.K, sos.ctypes.data, None if zi_arr is None else zi_arr.ctypes.data,
+                                     None if t is None else ctypes.addressof(t), ctypes.byref(h)),
+               "sos_filter_create")
+        self._h = h
+        self._lib = lib
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.sos_filter_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):  # pragma: no cover - best effort
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, x, y=None, zi=None, zf=None, stream=None):
+        """y = cascade(x) on the device; x, y, zi, zf are float32 CUDA tensors (y may be x)."""
+        import torch
+        if y is None:
+            y = torch.empty_like(x)
+        n = x.numel()
+        _check(self._lib.sos_filter_run(self._h, _dptr(x, "x"), _dptr(y, "y"), n,
+                                        None if zi is None else _dptr(zi, "zi"),
+                                        None if zf is None else _dptr(zf, "zf"), _stream_handle(stream)),
+               "sos_filter_run")
+        return y
+
+    def stream_push(self, x, y=None, stream=None):
+        import torch
+        if y is None:
+            y = torch.empty_like(x)
+        _check(self._lib.sos_filter_stream_push(self._h, _dptr(x, "x"), _dptr(y, "y"), x.numel(),
+                                                _stream_handle(stream)), "sos_filter_stream_push")
+        return y
+
+    def get_state(self) -> np.ndarray:
+        z = np.empty((self.K, 2), dtype=np.float32)
+        _check(self._lib.sos_filter_stream_state(self._h, z.ctypes.data, None, 0), "sos_filter_stream_state")
+        return z
+
+    def set_state(self, z):
+        z = np.ascontiguousarray(np.asarray(z, dtype=np.float32).reshape(self.K, 2))
+        _check(self._lib.sos_filter_stream_state(self._h, None, z.ctypes.data, 0), "sos_filter_stream_state")
+
+    def set_trace(self, buf=None):
+        """Enable the per-block phase trace into a uint64 CUDA tensor of shape [blocks, 32] (None = off)."""
+        import torch
+        if buf is None:
+            _check(self._lib.sos_filter_trace(self._h, None, 0), "sos_filter_trace")
+            return
+        if not (buf.is_cuda and buf.dtype == torch.int64 and buf.is_contiguous() and buf.dim() == 2
+                and buf.shape[1] == 32):
+            raise TypeError("trace buffer must be a contiguous int64 CUDA tensor of shape [blocks, 32]")
+        _check(self._lib.sos_filter_trace(self._h, buf.data_ptr(), buf.shape[0]), "sos_filter_trace")
+
+    def sync_status(self) -> int:
+        return int(self._lib.sos_filter_sync_status(self._h))
+
+
+def run_batch(filters, xs, ys=None, stream=None):
+    """Filter many signals (each with its own filter object), zero initial state."""
+    import torch
+    lib = load_library()
+    n = len(xs)
+    if ys is None:
+        ys = [torch.empty_like(x) for x in xs]
+    hf = (ctypes.c_void_p * n)(*[f.handle for f in filters])
+    hx = (ctypes.c_void_p * n)(*[_dptr(x, "x") for x in xs])
+    hy = (ctypes.c_void_p * n)(*[_dptr(y, "y") for y in ys])
+    hn = (ctypes.c_int64 * n)(*[x.numel() for x in xs])
+    _check(lib.sos_filter_run_batch(n, ctypes.addressof(hf), ctypes.addressof(hx), ctypes.addressof(hy),
+                                    ctypes.addressof(hn), _stream_handle(stream)), "sos_filter_run_batch")
+    return ys

@@ -1,0 +1,520 @@
+// C ABI of libsosfilt.so (declared in include/sosfilt.h): filter objects,
+// the float64 host precompute of the per-section tables (Sec. II-C..F), the
+// library-owned lookback workspace, and the launch of one kernel pass per
+// group of up to eight sections.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "sosfilt.h"
+#include "sosfilt_internal.h"
+
+namespace sosk {
+bool dccr_available(int K, int N, bool norm, int lbm);
+}  // namespace sosk
+
+namespace {
+
+constexpr int kNumN = 3;
+constexpr int kSupportedN[kNumN] = {32, 64, 128};
+constexpr long long kDefaultSpinBudget = 2000000000LL;  // ~1 s of SM clock
+
+struct Mat {
+    double a, b, c, d;  // row-major 2x2
+};
+
+Mat mul(const Mat &x, const Mat &y) {
+    return {x.a * y.a + x.b * y.c, x.a * y.b + x.b * y.d, x.c * y.a + x.d * y.c, x.c * y.b + x.d * y.d};
+}
+
+Mat mpow(Mat m, long long e) {
+    Mat r{1, 0, 0, 1};
+    while (e > 0) {
+        if (e & 1) r = mul(r, m);
+        m = mul(m, m);
+        e >>= 1;
+    }
+    return r;
+}
+
+std::vector<double> polymul(const std::vector<double> &p, const std::vector<double> &q) {
+    std::vector<double> r(p.size() + q.size() - 1, 0.0);
+    for (size_t i = 0; i < p.size(); ++i)
+        for (size_t j = 0; j < q.size(); ++j) r[i + j] += p[i] * q[j];
+    return r;
+}
+
+int ilog2i(int n) {
+    int d = 0;
+    while ((1 << d) < n) ++d;
+    return d;
+}
+
+struct NTables {
+    int N = 0;
+    std::vector<sosk::SecCoef> sec;  // [K]
+    float4 *d_lane_pow = nullptr;    // [K][32]
+    float4 *d_grp_pow = nullptr;     // [K][kGrpPowStride]: powers of T^C
+    float4 *d_cta_pow = nullptr;     // [K][kGrpPowStride]: powers of the block transition T^(kWarps C)
+};
+
+}  // namespace
+
+struct sos_filter {
+    int K = 0;
+    int device = 0;
+    std::vector<double> sos;  // [K][5]
+    bool norm = false;
+    double gain = 1.0;
+    std::vector<double> zscale;  // [K]
+    sos_tuning tuning{};
+    NTables tables[kNumN];
+    // workspace
+    unsigned long long *d_desc = nullptr;
+    size_t desc_groups = 0;  // capacity in groups (per section slot)
+    unsigned long long *d_ticket = nullptr;
+    unsigned long long ticket_base = 0;
+    unsigned int epoch = 0;
+    int *d_status = nullptr;
+    float *d_state = nullptr;  // resident [K][2]
+    cudaStream_t last_stream = nullptr;
+    unsigned long long *trace = nullptr;
+    long long trace_blocks = 0;
+    std::mutex mu;
+};
+
+namespace {
+
+sos_status cuda_fail() { return SOS_ECUDA; }
+
+bool section_stable(double a1, double a2) { return std::fabs(a2) < 1.0 && std::fabs(a1) < 1.0 + a2; }
+
+// Per-section tables for one N, float64 -> float32 once.
+void build_tables(sos_filter *f, int N, NTables &t, std::vector<float4> &lane_pow, std::vector<float4> &grp_pow,
+                  std::vector<float4> &cta_pow) {
+    const int D = ilog2i(N);
+    t.N = N;
+    t.sec.assign(f->K, sosk::SecCoef{});
+    lane_pow.assign(static_cast<size_t>(f->K) * 32, float4{});
+    grp_pow.assign(static_cast<size_t>(f->K) * sosk::kGrpPowStride, float4{});
+    cta_pow.assign(static_cast<size_t>(f->K) * sosk::kGrpPowStride, float4{});
+    for (int k = 0; k < f->K; ++k) {
+        const double *c = &f->sos[5 * k];
+        double b0 = c[0], b1 = c[1], b2 = c[2];
+        const double a1 = c[3], a2 = c[4];
+        if (f->norm) {
+            b1 /= b0;
+            b2 /= b0;
+            b0 = 1.0;
+        }
+        sosk::SecCoef &s = t.sec[k];
+        std::memset(&s, 0, sizeof s);
+        const std::vector<double> taps = polymul({b0, b1, b2}, {1.0, -a1, a2});  // B(z) A(-z)
+        s.t0 = static_cast<float>(taps[0]);
+        s.t1 = static_cast<float>(taps[1]);
+        s.t2 = static_cast<float>(taps[2]);
+        s.t3 = static_cast<float>(taps[3]);
+        s.t4 = static_cast<float>(taps[4]);
+        s.b1 = static_cast<float>(b1);
+        s.b2 = static_cast<float>(b2);
+        s.a1 = static_cast<float>(a1);
+        s.a2 = static_cast<float>(a2);
+        // level coefficients: e_0 = a1, f_0 = a2, e_{i+1} = 2 f_i - e_i^2, f_{i+1} = f_i^2
+        std::vector<double> e(D + 1), fl(D + 1);
+        e[0] = a1;
+        fl[0] = a2;
+        for (int i = 0; i < D; ++i) {
+            e[i + 1] = 2.0 * fl[i] - e[i] * e[i];
+            fl[i + 1] = fl[i] * fl[i];
+        }
+        for (int i = 1; i < D; ++i) {
+            s.ne[i] = static_cast<float>(-e[i]);
+            s.f[i] = static_cast<float>(fl[i]);
+            s.nf[i] = static_cast<float>(-fl[i]);
+        }
+        // state injection: Q_i = prod_{j<i} (1 - e_j z^-(2^j) + f_j z^-(2^(j+1)))
+        std::vector<double> Q{1.0};
+        for (int i = 0; i < D; ++i) {
+            const int st = 1 << i;
+            std::vector<double> g(2 * st + 1, 0.0);
+            g[0] = 1.0;
+            g[st] = -e[i];
+            g[2 * st] = fl[i];
+            Q = polymul(Q, g);
+            const int lev = i + 1;
+            auto q = [&](int m) { return (m >= 0 && m < static_cast<int>(Q.size())) ? Q[m] : 0.0; };
+            const int mo = (1 << lev) - 1, me = (1 << lev) - 2;
+            s.qo[lev][0] = static_cast<float>(q(mo));
+            s.qo[lev][1] = static_cast<float>(q(mo - 1));
+            s.qe[lev][0] = static_cast<float>(q(me));
+            s.qe[lev][1] = static_cast<float>(q(me - 1));
+        }
+        // transitions of the transposed direct form II state over N and C = 32 N samples
+        const Mat T{-a1, 1.0, -a2, 0.0};
+        const Mat TN = mpow(T, N);
+        Mat P = TN;
+        for (int kk = 0; kk < 5; ++kk) {
+            s.tn[kk][0] = static_cast<float>(P.a);
+            s.tn[kk][1] = static_cast<float>(P.b);
+            s.tn[kk][2] = static_cast<float>(P.c);
+            s.tn[kk][3] = static_cast<float>(P.d);
+            P = mul(P, P);
+        }
+        Mat L{1, 0, 0, 1};
+        for (int l = 0; l < 32; ++l) {
+            lane_pow[static_cast<size_t>(k) * 32 + l] =
+                float4{static_cast<float>(L.a), static_cast<float>(L.b), static_cast<float>(L.c), static_cast<float>(L.d)};
+            L = mul(L, TN);
+        }
+        const Mat TC = L;  // TN^32
+        {
+            Mat W{1, 0, 0, 1};
+            for (int w = 0; w <= sosk::kWarps; ++w) {
+                s.tc[w][0] = static_cast<float>(W.a);
+                s.tc[w][1] = static_cast<float>(W.b);
+                s.tc[w][2] = static_cast<float>(W.c);
+                s.tc[w][3] = static_cast<float>(W.d);
+                W = mul(W, TC);
+            }
+        }
+        // powers S^k (k = 0..32) and S^(32 i) (i = 0..16) of a step matrix S
+        auto fill = [&](std::vector<float4> &tab, const Mat &S) {
+            auto put = [&](int idx, const Mat &m) {
+                tab[static_cast<size_t>(k) * sosk::kGrpPowStride + idx] = float4{
+                    static_cast<float>(m.a), static_cast<float>(m.b), static_cast<float>(m.c), static_cast<float>(m.d)};
+            };
+            Mat Gp{1, 0, 0, 1};
+            for (int j = 0; j <= 32; ++j) {
+                put(j, Gp);
+                Gp = mul(Gp, S);
+            }
+            const Mat S32 = mpow(S, 32);
+            Mat G32{1, 0, 0, 1};
+            for (int i = 0; i <= sosk::kMaxLBM; ++i) {
+                put(sosk::kPow32 + i, G32);
+                G32 = mul(G32, S32);
+            }
+        };
+        fill(grp_pow, TC);
+        fill(cta_pow, mpow(TC, sosk::kWarps));
+        s.zscale = static_cast<float>(f->zscale[k]);
+        s.zscale_inv = static_cast<float>(1.0 / f->zscale[k]);
+    }
+}
+
+int table_index(int N) {
+    for (int i = 0; i < kNumN; ++i)
+        if (kSupportedN[i] == N) return i;
+    return -1;
+}
+
+// Default N (filled from GB300 measurements).  N = 128 is built for b0-normalized filters only.
+int default_N(const sos_filter *f, int64_t n) {
+    (void)n;
+    return f->norm ? 64 : 64;
+}
+
+sos_status ensure_desc(sos_filter *f, long long G, cudaStream_t s) {
+    if (static_cast<size_t>(G) <= f->desc_groups && f->d_desc) return SOS_OK;
+    size_t want = static_cast<size_t>(G);
+    if (want < 1024) want = 1024;
+    if (f->d_desc) {
+        cudaStreamSynchronize(s);
+        cudaFree(f->d_desc);
+        f->d_desc = nullptr;
+        f->desc_groups = 0;
+    }
+    const size_t bytes = want * sosk::kMaxPass * 2 * sizeof(unsigned long long);
+    if (cudaMalloc(&f->d_desc, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return SOS_ENOMEM;
+    }
+    if (cudaMemsetAsync(f->d_desc, 0, bytes, s) != cudaSuccess) return cuda_fail();
+    f->desc_groups = want;
+    f->epoch = 0;
+    return SOS_OK;
+}
+
+unsigned next_epoch(sos_filter *f, cudaStream_t s) {
+    f->epoch = (f->epoch + 1) & 0x3fffffffu;
+    if (f->epoch == 0) {  // wrapped: clear stale tags so no old descriptor matches
+        cudaMemsetAsync(f->d_desc, 0, f->desc_groups * sosk::kMaxPass * 2 * sizeof(unsigned long long), s);
+        f->epoch = 1;
+    }
+    return f->epoch;
+}
+
+bool ranges_overlap(const void *a, const void *b, int64_t n) {
+    const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    const uintptr_t bytes = static_cast<uintptr_t>(n) * sizeof(float);
+    return x < y + bytes && y < x + bytes;
+}
+
+sos_status run_impl(sos_filter *f, const float *x, float *y, int64_t n, const float *zi, float *zf, cudaStream_t s) {
+    if (n < 0 || (n > 0 && (!x || !y))) return SOS_EINVAL;
+    if (x != y && n > 0 && ranges_overlap(x, y, n)) return SOS_EINVAL;
+    if (cudaSetDevice(f->device) != cudaSuccess) return cuda_fail();
+    f->last_stream = s;
+    if (n == 0) {
+        if (zf) {
+            cudaError_t e = zi ? cudaMemcpyAsync(zf, zi, sizeof(float) * 2 * f->K, cudaMemcpyDeviceToDevice, s)
+                               : cudaMemsetAsync(zf, 0, sizeof(float) * 2 * f->K, s);
+            if (e != cudaSuccess) return cuda_fail();
+        }
+        return SOS_OK;
+    }
+    int N = f->tuning.N ? f->tuning.N : default_N(f, n);
+    if (N == 128 && !f->norm) N = 64;
+    const int ti = table_index(N);
+    if (ti < 0) return SOS_EINVAL;
+    const NTables &t = f->tables[ti];
+    const long long C = static_cast<long long>(N) * sosk::kL;
+    const long long G = (n + C - 1) / C;
+    sos_status st = ensure_desc(f, G, s);
+    if (st != SOS_OK) return st;
+    const long long grid = (G + sosk::kWarps - 1) / sosk::kWarps;
+    for (int k0 = 0; k0 < f->K; k0 += sosk::kMaxPass) {
+        const int kp = (f->K - k0) < sosk::kMaxPass ? (f->K - k0) : sosk::kMaxPass;
+        if (!sosk::dccr_available(kp, N, f->norm, f->tuning.lookback_width)) return SOS_EINVAL;
+    }
+    const bool aligned = (reinterpret_cast<uintptr_t>(x) % 16 == 0) && (reinterpret_cast<uintptr_t>(y) % 16 == 0);
+    const float *src = x;
+    for (int k0 = 0; k0 < f->K; k0 += sosk::kMaxPass) {
+        const int kp = (f->K - k0) < sosk::kMaxPass ? (f->K - k0) : sosk::kMaxPass;
+        sosk::PassParams p;
+        std::memset(&p, 0, sizeof p);
+        p.x = src;
+        p.y = y;
+        p.n = n;
+        p.G = G;
+        p.zi = zi ? zi + 2 * k0 : nullptr;
+        p.zf = zf ? zf + 2 * k0 : nullptr;
+        p.gain = (k0 == 0) ? static_cast<float>(f->gain) : 1.0f;
+        p.desc = f->d_desc;
+        p.ticket = f->d_ticket;
+        p.ticket_base = f->ticket_base;
+        p.epoch = next_epoch(f, s);
+        p.lane_pow = t.d_lane_pow + static_cast<size_t>(k0) * 32;
+        p.grp_pow = t.d_grp_pow + static_cast<size_t>(k0) * sosk::kGrpPowStride;
+        p.cta_pow = t.d_cta_pow + static_cast<size_t>(k0) * sosk::kGrpPowStride;
+        p.status = f->d_status;
+        p.spin_budget = f->tuning.spin_budget_cycles ? f->tuning.spin_budget_cycles : kDefaultSpinBudget;
+        p.aligned = aligned ? 1 : 0;
+        p.n_sec = kp;
+        p.trace = f->trace;
+        p.trace_blocks = f->trace_blocks;
+        for (int j = 0; j < kp; ++j) p.sec[j] = t.sec[k0 + j];
+        // the gain multiplies the input only in the first pass (p.gain = 1 afterwards)
+        cudaError_t e = sosk::launch_dccr(kp, N, f->norm, f->tuning.lookback_width, p, grid, s);
+        if (e != cudaSuccess) return cuda_fail();
+        f->ticket_base += static_cast<unsigned long long>(grid);
+        src = y;
+    }
+    return SOS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *sos_status_string(sos_status s) {
+    switch (s) {
+        case SOS_OK: return "SOS_OK";
+        case SOS_EINVAL: return "SOS_EINVAL: invalid argument";
+        case SOS_ENOMEM: return "SOS_ENOMEM: allocation failed";
+        case SOS_ECUDA: return "SOS_ECUDA: CUDA runtime error";
+        case SOS_ETIMEOUT: return "SOS_ETIMEOUT: lookback wait exceeded its budget";
+        case SOS_EUNSTABLE: return "SOS_EUNSTABLE: unstable or non-finite section";
+        case SOS_EBUDGET: return "SOS_EBUDGET: request exceeds the memory budget";
+    }
+    return "unknown sos_status";
+}
+
+sos_status sos_filter_create(int n_sections, const double *sos, const float *zi, const sos_tuning *t,
+                             sos_filter **out) {
+    if (!out) return SOS_EINVAL;
+    *out = nullptr;
+    if (!sos || n_sections < 1 || n_sections > 64) return SOS_EINVAL;
+    if (t) {
+        if (t->N && table_index(t->N) < 0) return SOS_EINVAL;
+        if (t->L && t->L != sosk::kL) return SOS_EINVAL;
+        if (t->threads_per_group && t->threads_per_group != sosk::kL) return SOS_EINVAL;
+        if (t->groups_per_cta && t->groups_per_cta != sosk::kWarps) return SOS_EINVAL;
+        if (t->fp64_carry) return SOS_EINVAL;
+        if (t->spin_budget_cycles < 0) return SOS_EINVAL;
+        const int lw = t->lookback_width;
+        if (lw != 0 && lw != 1 && lw != 2 && lw != 4 && lw != 8 && lw != 16) return SOS_EINVAL;
+    }
+    for (int k = 0; k < n_sections; ++k) {
+        for (int j = 0; j < 5; ++j)
+            if (!std::isfinite(sos[5 * k + j])) return SOS_EUNSTABLE;
+        if (!section_stable(sos[5 * k + 3], sos[5 * k + 4])) return SOS_EUNSTABLE;
+    }
+    sos_filter *f = new (std::nothrow) sos_filter();
+    if (!f) return SOS_ENOMEM;
+    f->K = n_sections;
+    f->sos.assign(sos, sos + 5 * n_sections);
+    if (t) f->tuning = *t;
+    if (cudaGetDevice(&f->device) != cudaSuccess) {
+        delete f;
+        return SOS_ECUDA;
+    }
+    // b0 normalization (Eq. 1 splits b0 into a common gain): legal when every b0 != 0 and
+    // the gain and the per-section state scales stay far inside the float32 range.
+    bool norm = true;
+    double gain = 1.0;
+    for (int k = 0; k < n_sections; ++k) {
+        if (sos[5 * k] == 0.0) norm = false;
+        gain *= sos[5 * k];
+    }
+    f->zscale.assign(n_sections, 1.0);
+    if (norm) {
+        for (int k = 0; k < n_sections; ++k) {
+            double z = 1.0;
+            for (int j = k + 1; j < n_sections; ++j) z *= sos[5 * j];
+            f->zscale[k] = z;
+            if (!(std::fabs(z) > 1e-30 && std::fabs(z) < 1e30)) norm = false;
+        }
+        if (!(std::fabs(gain) > 1e-30 && std::fabs(gain) < 1e30)) norm = false;
+    }
+    if (!norm) f->zscale.assign(n_sections, 1.0);
+    f->norm = norm;
+    f->gain = norm ? gain : 1.0;
+
+    sos_status st = SOS_OK;
+    for (int i = 0; i < kNumN && st == SOS_OK; ++i) {
+        std::vector<float4> lp, gp, cp;
+        build_tables(f, kSupportedN[i], f->tables[i], lp, gp, cp);
+        if (cudaMalloc(&f->tables[i].d_lane_pow, lp.size() * sizeof(float4)) != cudaSuccess ||
+            cudaMalloc(&f->tables[i].d_grp_pow, gp.size() * sizeof(float4)) != cudaSuccess ||
+            cudaMalloc(&f->tables[i].d_cta_pow, cp.size() * sizeof(float4)) != cudaSuccess) {
+            st = SOS_ENOMEM;
+            break;
+        }
+        if (cudaMemcpy(f->tables[i].d_lane_pow, lp.data(), lp.size() * sizeof(float4), cudaMemcpyHostToDevice) !=
+                cudaSuccess ||
+            cudaMemcpy(f->tables[i].d_grp_pow, gp.data(), gp.size() * sizeof(float4), cudaMemcpyHostToDevice) !=
+                cudaSuccess ||
+            cudaMemcpy(f->tables[i].d_cta_pow, cp.data(), cp.size() * sizeof(float4), cudaMemcpyHostToDevice) !=
+                cudaSuccess)
+            st = SOS_ECUDA;
+    }
+    if (st == SOS_OK) {
+        if (cudaMalloc(&f->d_ticket, sizeof(unsigned long long)) != cudaSuccess ||
+            cudaMalloc(&f->d_status, sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&f->d_state, sizeof(float) * 2 * n_sections) != cudaSuccess)
+            st = SOS_ENOMEM;
+    }
+    if (st == SOS_OK) {
+        if (cudaMemset(f->d_ticket, 0, sizeof(unsigned long long)) != cudaSuccess ||
+            cudaMemset(f->d_status, 0, sizeof(int)) != cudaSuccess)
+            st = SOS_ECUDA;
+        std::vector<float> z(2 * n_sections, 0.f);
+        if (zi) std::memcpy(z.data(), zi, sizeof(float) * 2 * n_sections);
+        if (st == SOS_OK &&
+            cudaMemcpy(f->d_state, z.data(), sizeof(float) * 2 * n_sections, cudaMemcpyHostToDevice) != cudaSuccess)
+            st = SOS_ECUDA;
+    }
+    if (st != SOS_OK) {
+        cudaGetLastError();
+        sos_filter_destroy(f);
+        return st;
+    }
+    *out = f;
+    return SOS_OK;
+}
+
+sos_status sos_filter_destroy(sos_filter *f) {
+    if (!f) return SOS_OK;
+    cudaSetDevice(f->device);
+    if (f->last_stream) cudaStreamSynchronize(f->last_stream);
+    for (auto &t : f->tables) {
+        if (t.d_lane_pow) cudaFree(t.d_lane_pow);
+        if (t.d_grp_pow) cudaFree(t.d_grp_pow);
+        if (t.d_cta_pow) cudaFree(t.d_cta_pow);
+    }
+    if (f->d_desc) cudaFree(f->d_desc);
+    if (f->d_ticket) cudaFree(f->d_ticket);
+    if (f->d_status) cudaFree(f->d_status);
+    if (f->d_state) cudaFree(f->d_state);
+    delete f;
+    return SOS_OK;
+}
+
+sos_status sos_filter_run(sos_filter *f, const float *x_dev, float *y_dev, int64_t n, const float *zi_dev,
+                          float *zf_dev, void *stream) {
+    if (!f) return SOS_EINVAL;
+    std::lock_guard<std::mutex> lk(f->mu);
+    return run_impl(f, x_dev, y_dev, n, zi_dev, zf_dev, static_cast<cudaStream_t>(stream));
+}
+
+sos_status sos_filter_run_batch(int n_signals, sos_filter *const *filters, const float *const *x_dev,
+                                float *const *y_dev, const int64_t *n, void *stream) {
+    if (n_signals < 0) return SOS_EINVAL;
+    if (n_signals == 0) return SOS_OK;
+    if (!filters || !x_dev || !y_dev || !n) return SOS_EINVAL;
+    for (int i = 0; i < n_signals; ++i) {
+        if (!filters[i]) return SOS_EINVAL;
+        std::lock_guard<std::mutex> lk(filters[i]->mu);
+        sos_status st = run_impl(filters[i], x_dev[i], y_dev[i], n[i], nullptr, nullptr,
+                                 static_cast<cudaStream_t>(stream));
+        if (st != SOS_OK) return st;
+    }
+    return SOS_OK;
+}
+
+sos_status sos_filter_stream_push(sos_filter *f, const float *x_dev, float *y_dev, int64_t n, void *stream) {
+    if (!f) return SOS_EINVAL;
+    std::lock_guard<std::mutex> lk(f->mu);
+    return run_impl(f, x_dev, y_dev, n, f->d_state, f->d_state, static_cast<cudaStream_t>(stream));
+}
+
+sos_status sos_filter_stream_state(sos_filter *f, float *z_out, const float *z_in, int on_device) {
+    if (!f) return SOS_EINVAL;
+    std::lock_guard<std::mutex> lk(f->mu);
+    if (cudaSetDevice(f->device) != cudaSuccess) return SOS_ECUDA;
+    const size_t bytes = sizeof(float) * 2 * f->K;
+    cudaStream_t s = f->last_stream;
+    if (on_device) {
+        if (z_out && cudaMemcpyAsync(z_out, f->d_state, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return SOS_ECUDA;
+        if (z_in && cudaMemcpyAsync(f->d_state, z_in, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return SOS_ECUDA;
+    } else {
+        if (cudaStreamSynchronize(s) != cudaSuccess) return SOS_ECUDA;
+        if (z_out && cudaMemcpy(z_out, f->d_state, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return SOS_ECUDA;
+        if (z_in && cudaMemcpy(f->d_state, z_in, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return SOS_ECUDA;
+    }
+    int h = 0;
+    if (!on_device) {
+        if (cudaMemcpy(&h, f->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SOS_ECUDA;
+        if (h & sosk::kDevErrTimeout) return SOS_ETIMEOUT;
+    }
+    return SOS_OK;
+}
+
+sos_status sos_filter_trace(sos_filter *f, uint64_t *buf_dev, int64_t capacity_blocks) {
+    if (!f || capacity_blocks < 0) return SOS_EINVAL;
+    std::lock_guard<std::mutex> lk(f->mu);
+    f->trace = reinterpret_cast<unsigned long long *>(buf_dev);
+    f->trace_blocks = buf_dev ? capacity_blocks : 0;
+    return SOS_OK;
+}
+
+sos_status sos_filter_sync_status(sos_filter *f) {
+    if (!f) return SOS_EINVAL;
+    std::lock_guard<std::mutex> lk(f->mu);
+    if (cudaSetDevice(f->device) != cudaSuccess) return SOS_ECUDA;
+    if (cudaStreamSynchronize(f->last_stream) != cudaSuccess) return SOS_ECUDA;
+    int h = 0;
+    if (cudaMemcpy(&h, f->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SOS_ECUDA;
+    if (h & sosk::kDevErrTimeout) return SOS_ETIMEOUT;
+    return SOS_OK;
+}
+
+}  // extern "C"
