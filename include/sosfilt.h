@@ -55,24 +55,38 @@ typedef enum {
 /* Opaque filter object, owned by the library. */
 typedef struct sos_filter sos_filter;
 
+/* Carry schemes (see sos_tuning.carry). */
+enum {
+    SOS_CARRY_DEFAULT = 0, /* SOS_CARRY_CASCADE */
+    SOS_CARRY_CASCADE = 1, /* one carry per tile for the whole cascade state (2K words): a
+                              zero-state pass through all sections, one decoupled lookback
+                              (Sec. IV-B, Eq. 25 on the cascade state), then the homogeneous
+                              correction of Eq. 24 applied once to the output */
+    SOS_CARRY_SECTION = 2  /* one decoupled lookback per section, as in Sec. IV-B */
+};
+
 /*
  * Launch configuration.  Any field left 0 selects the library's default for
  * that field (the built-in per-order table).
- *   N                  samples per thread (block count of Eq. 2): 16, 32, 64 or 128
+ *   N                  samples per thread (block count of Eq. 2): 32 or 64 for
+ *                      the cascade carry; 32, 64 or 128 for per-section carries
  *   L                  threads per group (block length of Eq. 2): 32
- *   groups_per_cta     groups (warps) per thread block: 1..8
+ *   groups_per_cta     reserved, must be 0 (the library picks the groups per thread
+ *                      block from N and the carry scheme)
  *   threads_per_group  L (one thread group per signal block group, Sec. IV-D)
  *   fp64_carry         reserved: must be 0 (carries are float32)
  *   spin_budget_cycles upper bound, in SM clock cycles, on one lookback wait;
  *                      on expiry the kernel records SOS_ETIMEOUT and returns
- *   lookback_width     predecessors read per lookback round, in units of 32:
- *                      1, 2, 4, 8 or 16 (values other than the default for N
- *                      are available for 8-section passes with b0 != 0)
+ *   lookback_width     per-section carries only: predecessors read per lookback
+ *                      round, in units of 32: 1, 2, 4, 8 or 16 (values other than
+ *                      the default for N exist for 8-section passes with b0 != 0)
+ *   carry              SOS_CARRY_DEFAULT, SOS_CARRY_CASCADE or SOS_CARRY_SECTION
  */
 typedef struct {
     int N, L, groups_per_cta, threads_per_group, fp64_carry;
     long long spin_budget_cycles;
     int lookback_width;
+    int carry;
 } sos_tuning;
 
 /*

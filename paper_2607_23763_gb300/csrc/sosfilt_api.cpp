@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -16,6 +17,15 @@
 
 namespace sosk {
 bool dccr_available(int K, int N, bool norm, int lbm);
+int cascade_blocks_per_sm_32(int K, bool norm);
+int cascade_blocks_per_sm_64(int K, bool norm);
+size_t cascade_smem_32(int K);
+size_t cascade_smem_64(int K);
+int cascade_blocks_per_sm(int K, int N, bool norm) {
+    return N == 32 ? cascade_blocks_per_sm_32(K, norm) : N == 64 ? cascade_blocks_per_sm_64(K, norm) : 0;
+}
+int cascade_warps(int N) { return N == 32 ? 8 : 4; }
+size_t cascade_smem(int K, int N) { return N == 32 ? cascade_smem_32(K) : N == 64 ? cascade_smem_64(K) : 0; }
 }  // namespace sosk
 
 namespace {
@@ -63,6 +73,58 @@ struct NTables {
     float4 *d_cta_pow = nullptr;     // [K][kGrpPowStride]: powers of the block transition T^(kWarps C)
 };
 
+// Dense float64 matrices acting on the cascade state (2K words, section-major, (z1, z2) each).
+struct DMat {
+    int n = 0;
+    std::vector<double> a;
+    explicit DMat(int n_ = 0) : n(n_), a(static_cast<size_t>(n_) * n_, 0.0) {}
+    double &at(int i, int j) { return a[static_cast<size_t>(i) * n + j]; }
+    double at(int i, int j) const { return a[static_cast<size_t>(i) * n + j]; }
+};
+
+DMat deye(int n) {
+    DMat r(n);
+    for (int i = 0; i < n; ++i) r.at(i, i) = 1.0;
+    return r;
+}
+
+DMat dmul(const DMat &x, const DMat &y) {
+    DMat r(x.n);
+    for (int i = 0; i < x.n; ++i)
+        for (int k = 0; k < x.n; ++k) {
+            const double v = x.at(i, k);
+            if (v == 0.0) continue;
+            for (int j = 0; j < x.n; ++j) r.at(i, j) += v * y.at(k, j);
+        }
+    return r;
+}
+
+DMat dpow(DMat m, long long e) {
+    DMat r = deye(m.n);
+    while (e > 0) {
+        if (e & 1) r = dmul(r, m);
+        m = dmul(m, m);
+        e >>= 1;
+    }
+    return r;
+}
+
+// One pass (<= 8 sections) of the cascade-carry kernel for one N.
+struct CasPass {
+    int k0 = 0, kp = 0;
+    std::vector<double> coef;  // [kp][5] b0, b1, b2, a1, a2 as the kernel applies them
+    DMat M1;                   // one-sample zero-input transition of the pass's cascade state
+    std::vector<float> H;      // [2 kp][N] zero-input output basis
+    float *d_tab = nullptr;    // device table block (CasDims<kp>::TAB floats)
+    long long tail_p = -1;     // position for which A_tail is cached
+    std::vector<float> A_tail; // packed transition over tail_p + 1 samples
+};
+
+struct CasTables {
+    int N = 0;
+    std::vector<CasPass> passes;
+};
+
 }  // namespace
 
 struct sos_filter {
@@ -74,6 +136,7 @@ struct sos_filter {
     std::vector<double> zscale;  // [K]
     sos_tuning tuning{};
     NTables tables[kNumN];
+    CasTables cas[2];  // N = 32, 64
     // workspace
     unsigned long long *d_desc = nullptr;
     size_t desc_groups = 0;  // capacity in groups (per section slot)
@@ -207,6 +270,117 @@ void build_tables(sos_filter *f, int N, NTables &t, std::vector<float4> &lane_po
     }
 }
 
+// Zero-input step of a cascade with coefficients c[kp][5] (as applied in the kernel's domain).
+double cascade_step(const std::vector<double> &c, int kp, std::vector<double> &z, double x) {
+    double v = x;
+    for (int s = 0; s < kp; ++s) {
+        const double *q = &c[5 * s];
+        const double y = q[0] * v + z[2 * s];
+        const double z1 = q[1] * v - q[3] * y + z[2 * s + 1];
+        const double z2 = q[2] * v - q[4] * y;
+        z[2 * s] = z1;
+        z[2 * s + 1] = z2;
+        v = y;
+    }
+    return v;
+}
+
+// Packed lower block-triangular storage: block (s, t), s >= t, at 4 (s(s+1)/2 + t), row-major 2x2.
+void pack_into(const DMat &m, int kp, float *dst) {
+    for (int s = 0; s < kp; ++s)
+        for (int t = 0; t <= s; ++t) {
+            float *b = dst + 4 * (s * (s + 1) / 2 + t);
+            b[0] = static_cast<float>(m.at(2 * s, 2 * t));
+            b[1] = static_cast<float>(m.at(2 * s, 2 * t + 1));
+            b[2] = static_cast<float>(m.at(2 * s + 1, 2 * t));
+            b[3] = static_cast<float>(m.at(2 * s + 1, 2 * t + 1));
+        }
+}
+
+int packed_floats(int kp) { return 2 * kp * (kp + 1); }
+int lane_stride(int kp) {
+    const int nf = packed_floats(kp);
+    return ((nf / 4) & 1) ? nf : nf + 4;
+}
+int table_floats(int kp) {
+    return 32 * lane_stride(kp) + (1 + 5 + sosk::kMaxWin) * packed_floats(kp) + 2 * (2 * kp) * (2 * kp);
+}
+
+void dense_colmajor_into(const DMat &m, float *dst) {
+    for (int j = 0; j < m.n; ++j)
+        for (int i = 0; i < m.n; ++i) dst[static_cast<size_t>(j) * m.n + i] = static_cast<float>(m.at(i, j));
+}
+
+// Transitions and output basis of every pass for one N, in float64, uploaded once.
+sos_status build_cascade(sos_filter *f, int N, CasTables &ct) {
+    ct.N = N;
+    ct.passes.clear();
+    const int W = sosk::cascade_warps(N);
+    for (int k0 = 0; k0 < f->K; k0 += sosk::kMaxPass) {
+        CasPass ps;
+        ps.k0 = k0;
+        ps.kp = (f->K - k0) < sosk::kMaxPass ? (f->K - k0) : sosk::kMaxPass;
+        const int kp = ps.kp, S = 2 * kp;
+        ps.coef.resize(5 * kp);
+        for (int j = 0; j < kp; ++j) {
+            const double *c = &f->sos[5 * (k0 + j)];
+            double b0 = c[0], b1 = c[1], b2 = c[2];
+            if (f->norm) {
+                b1 /= b0;
+                b2 /= b0;
+                b0 = 1.0;
+            }
+            ps.coef[5 * j + 0] = b0;
+            ps.coef[5 * j + 1] = b1;
+            ps.coef[5 * j + 2] = b2;
+            ps.coef[5 * j + 3] = c[3];
+            ps.coef[5 * j + 4] = c[4];
+        }
+        ps.M1 = DMat(S);
+        ps.H.assign(static_cast<size_t>(S) * N, 0.f);
+        for (int j = 0; j < S; ++j) {
+            std::vector<double> z(S, 0.0);
+            z[j] = 1.0;
+            cascade_step(ps.coef, kp, z, 0.0);
+            for (int i = 0; i < S; ++i) ps.M1.at(i, j) = z[i];
+            std::vector<double> h(S, 0.0);
+            h[j] = 1.0;
+            for (int m = 0; m < N; ++m) ps.H[static_cast<size_t>(j) * N + m] = static_cast<float>(cascade_step(ps.coef, kp, h, 0.0));
+        }
+        const DMat MN = dpow(ps.M1, N);
+        const DMat AC = dpow(MN, 32);
+        const DMat AT = dpow(AC, W);
+        const int nf = packed_floats(kp), ms = lane_stride(kp);
+        std::vector<float> tab(table_floats(kp), 0.f);
+        DMat L = deye(S);
+        for (int l = 0; l < 32; ++l) {
+            pack_into(L, kp, &tab[static_cast<size_t>(l) * ms]);
+            L = dmul(L, MN);
+        }
+        float *p_ac = &tab[32 * static_cast<size_t>(ms)];
+        pack_into(AC, kp, p_ac);
+        DMat P2 = AT;
+        for (int k = 0; k < 5; ++k) {
+            pack_into(P2, kp, p_ac + nf * (1 + k));
+            P2 = dmul(P2, P2);
+        }
+        const DMat AT32 = dpow(AT, 32);
+        DMat Pw = deye(S);
+        for (int w = 0; w < sosk::kMaxWin; ++w) {
+            pack_into(Pw, kp, p_ac + nf * (6 + w));
+            Pw = dmul(Pw, AT32);
+        }
+        float *p_dense = p_ac + nf * (6 + sosk::kMaxWin);
+        dense_colmajor_into(AC, p_dense);
+        dense_colmajor_into(AT, p_dense + S * S);
+        if (cudaMalloc(&ps.d_tab, tab.size() * sizeof(float)) != cudaSuccess) return SOS_ENOMEM;
+        if (cudaMemcpy(ps.d_tab, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+            return SOS_ECUDA;
+        ct.passes.push_back(std::move(ps));
+    }
+    return SOS_OK;
+}
+
 int table_index(int N) {
     for (int i = 0; i < kNumN; ++i)
         if (kSupportedN[i] == N) return i;
@@ -255,19 +429,9 @@ bool ranges_overlap(const void *a, const void *b, int64_t n) {
     return x < y + bytes && y < x + bytes;
 }
 
-sos_status run_impl(sos_filter *f, const float *x, float *y, int64_t n, const float *zi, float *zf, cudaStream_t s) {
-    if (n < 0 || (n > 0 && (!x || !y))) return SOS_EINVAL;
-    if (x != y && n > 0 && ranges_overlap(x, y, n)) return SOS_EINVAL;
-    if (cudaSetDevice(f->device) != cudaSuccess) return cuda_fail();
-    f->last_stream = s;
-    if (n == 0) {
-        if (zf) {
-            cudaError_t e = zi ? cudaMemcpyAsync(zf, zi, sizeof(float) * 2 * f->K, cudaMemcpyDeviceToDevice, s)
-                               : cudaMemsetAsync(zf, 0, sizeof(float) * 2 * f->K, s);
-            if (e != cudaSuccess) return cuda_fail();
-        }
-        return SOS_OK;
-    }
+// Per-section carries: one decoupled lookback per section and thread block (sosfilt_dccr.cuh).
+sos_status run_sections(sos_filter *f, const float *x, float *y, int64_t n, const float *zi, float *zf,
+                        cudaStream_t s) {
     int N = f->tuning.N ? f->tuning.N : default_N(f, n);
     if (N == 128 && !f->norm) N = 64;
     const int ti = table_index(N);
@@ -318,6 +482,123 @@ sos_status run_impl(sos_filter *f, const float *x, float *y, int64_t n, const fl
     return SOS_OK;
 }
 
+int sm_count(int device) {
+    static int cached[64] = {0};
+    if (device >= 0 && device < 64 && cached[device]) return cached[device];
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || n <= 0) n = 1;
+    if (device >= 0 && device < 64) cached[device] = n;
+    return n;
+}
+
+template <int K, int N>
+sos_status launch_cascade_pass(sos_filter *f, CasPass &ps, const sosk::SecCoef *sec, const float *x, float *y,
+                               long long n, long long G, long long n_tiles, long long grid, const float *zi,
+                               float *zf, bool first, bool aligned, cudaStream_t s) {
+    static_assert(K >= 1 && K <= sosk::kMaxPass, "pass size");
+    auto p = std::make_unique<sosk::CasParams<K, N>>();
+    std::memset(p.get(), 0, sizeof(*p));
+    p->x = x;
+    p->y = y;
+    p->n = n;
+    p->G = G;
+    p->n_tiles = n_tiles;
+    p->zi = zi;
+    p->zf = zf;
+    p->gain = first ? static_cast<float>(f->gain) : 1.0f;
+    p->desc = f->d_desc;
+    p->ticket = f->d_ticket;
+    p->ticket_base = f->ticket_base;
+    p->epoch = next_epoch(f, s);
+    p->status = f->d_status;
+    p->spin_budget = f->tuning.spin_budget_cycles ? f->tuning.spin_budget_cycles : kDefaultSpinBudget;
+    p->aligned = aligned ? 1 : 0;
+    p->tab = ps.d_tab;
+    p->trace = f->trace;
+    p->trace_tiles = f->trace_blocks;
+    for (int j = 0; j < K; ++j) p->sec[j] = sec[j];
+    for (int j = 0; j < 2 * K; ++j)
+        for (int m = 0; m < N; ++m) p->H[j][m] = ps.H[static_cast<size_t>(j) * N + m];
+    if (zf) {
+        const long long C = 32LL * N;
+        const long long tp = n - 1 - (G - 1) * C;  // last real sample inside the last group
+        if (ps.tail_p != tp) {
+            ps.A_tail.assign(packed_floats(K), 0.f);
+            pack_into(dpow(ps.M1, tp + 1), K, ps.A_tail.data());
+            ps.tail_p = tp;
+        }
+        std::memcpy(p->A_tail, ps.A_tail.data(), sizeof(float) * packed_floats(K));
+    }
+    cudaError_t e = sosk::launch_cascade<K, N>(f->norm, *p, grid, s);
+    if (e != cudaSuccess) return SOS_ECUDA;
+    f->ticket_base += static_cast<unsigned long long>(n_tiles + grid);
+    return SOS_OK;
+}
+
+template <int N>
+sos_status launch_cascade_any(int K, sos_filter *f, CasPass &ps, const sosk::SecCoef *sec, const float *x, float *y,
+                              long long n, long long G, long long n_tiles, long long grid, const float *zi, float *zf,
+                              bool first, bool aligned, cudaStream_t s) {
+    switch (K) {
+#define SOSK_CASE(k) \
+    case k: return launch_cascade_pass<k, N>(f, ps, sec, x, y, n, G, n_tiles, grid, zi, zf, first, aligned, s);
+        SOSK_CASE(1) SOSK_CASE(2) SOSK_CASE(3) SOSK_CASE(4) SOSK_CASE(5) SOSK_CASE(6) SOSK_CASE(7) SOSK_CASE(8)
+#undef SOSK_CASE
+        default: return SOS_EINVAL;
+    }
+}
+
+// One carry per tile for the whole cascade (sosfilt_cascade.cuh), persistent grid.
+sos_status run_cascade(sos_filter *f, const float *x, float *y, int64_t n, const float *zi, float *zf,
+                       cudaStream_t s) {
+    int N = f->tuning.N ? f->tuning.N : 32;
+    if (N != 32 && N != 64) return SOS_EINVAL;
+    const int ci = (N == 32) ? 0 : 1;
+    const int ti = table_index(N);
+    const long long C = 32LL * N;
+    const long long W = sosk::cascade_warps(N);
+    const long long G = (n + C - 1) / C;
+    const long long n_tiles = (G + W - 1) / W;
+    sos_status st = ensure_desc(f, G, s);
+    if (st != SOS_OK) return st;
+    const bool aligned = (reinterpret_cast<uintptr_t>(x) % 16 == 0) && (reinterpret_cast<uintptr_t>(y) % 16 == 0);
+    const float *src = x;
+    for (auto &ps : f->cas[ci].passes) {
+        const int bps = sosk::cascade_blocks_per_sm(ps.kp, N, f->norm);
+        if (bps <= 0) return SOS_ECUDA;
+        long long grid = static_cast<long long>(bps) * sm_count(f->device);
+        if (grid > n_tiles) grid = n_tiles;
+        if (N == 32)
+            st = launch_cascade_any<32>(ps.kp, f, ps, &f->tables[ti].sec[ps.k0], src, y, n, G, n_tiles, grid,
+                                        zi ? zi + 2 * ps.k0 : nullptr, zf ? zf + 2 * ps.k0 : nullptr, ps.k0 == 0,
+                                        aligned, s);
+        else
+            st = launch_cascade_any<64>(ps.kp, f, ps, &f->tables[ti].sec[ps.k0], src, y, n, G, n_tiles, grid,
+                                        zi ? zi + 2 * ps.k0 : nullptr, zf ? zf + 2 * ps.k0 : nullptr, ps.k0 == 0,
+                                        aligned, s);
+        if (st != SOS_OK) return st;
+        src = y;
+    }
+    return SOS_OK;
+}
+
+sos_status run_impl(sos_filter *f, const float *x, float *y, int64_t n, const float *zi, float *zf, cudaStream_t s) {
+    if (n < 0 || (n > 0 && (!x || !y))) return SOS_EINVAL;
+    if (x != y && n > 0 && ranges_overlap(x, y, n)) return SOS_EINVAL;
+    if (cudaSetDevice(f->device) != cudaSuccess) return cuda_fail();
+    f->last_stream = s;
+    if (n == 0) {
+        if (zf) {
+            cudaError_t e = zi ? cudaMemcpyAsync(zf, zi, sizeof(float) * 2 * f->K, cudaMemcpyDeviceToDevice, s)
+                               : cudaMemsetAsync(zf, 0, sizeof(float) * 2 * f->K, s);
+            if (e != cudaSuccess) return cuda_fail();
+        }
+        return SOS_OK;
+    }
+    if (f->tuning.carry == SOS_CARRY_SECTION) return run_sections(f, x, y, n, zi, zf, s);
+    return run_cascade(f, x, y, n, zi, zf, s);
+}
+
 }  // namespace
 
 extern "C" {
@@ -341,12 +622,16 @@ sos_status sos_filter_create(int n_sections, const double *sos, const float *zi,
     *out = nullptr;
     if (!sos || n_sections < 1 || n_sections > 64) return SOS_EINVAL;
     if (t) {
-        if (t->N && table_index(t->N) < 0) return SOS_EINVAL;
+        if (t->N && t->N != 32 && t->N != 64 && t->N != 128) return SOS_EINVAL;
         if (t->L && t->L != sosk::kL) return SOS_EINVAL;
         if (t->threads_per_group && t->threads_per_group != sosk::kL) return SOS_EINVAL;
-        if (t->groups_per_cta && t->groups_per_cta != sosk::kWarps) return SOS_EINVAL;
+        if (t->groups_per_cta) return SOS_EINVAL;  // chosen by the library from N and the carry scheme
         if (t->fp64_carry) return SOS_EINVAL;
         if (t->spin_budget_cycles < 0) return SOS_EINVAL;
+        if (t->carry != SOS_CARRY_DEFAULT && t->carry != SOS_CARRY_CASCADE && t->carry != SOS_CARRY_SECTION)
+            return SOS_EINVAL;
+        if ((t->carry == SOS_CARRY_DEFAULT || t->carry == SOS_CARRY_CASCADE) && t->N && t->N != 32 && t->N != 64)
+            return SOS_EINVAL;
         const int lw = t->lookback_width;
         if (lw != 0 && lw != 1 && lw != 2 && lw != 4 && lw != 8 && lw != 16) return SOS_EINVAL;
     }
@@ -404,6 +689,7 @@ sos_status sos_filter_create(int n_sections, const double *sos, const float *zi,
                 cudaSuccess)
             st = SOS_ECUDA;
     }
+    for (int i = 0; i < 2 && st == SOS_OK; ++i) st = build_cascade(f, i == 0 ? 32 : 64, f->cas[i]);
     if (st == SOS_OK) {
         if (cudaMalloc(&f->d_ticket, sizeof(unsigned long long)) != cudaSuccess ||
             cudaMalloc(&f->d_status, sizeof(int)) != cudaSuccess ||
@@ -438,6 +724,9 @@ sos_status sos_filter_destroy(sos_filter *f) {
         if (t.d_grp_pow) cudaFree(t.d_grp_pow);
         if (t.d_cta_pow) cudaFree(t.d_cta_pow);
     }
+    for (auto &ct : f->cas)
+        for (auto &ps : ct.passes)
+            if (ps.d_tab) cudaFree(ps.d_tab);
     if (f->d_desc) cudaFree(f->d_desc);
     if (f->d_ticket) cudaFree(f->d_ticket);
     if (f->d_status) cudaFree(f->d_status);

@@ -21,41 +21,9 @@
 // The reduction and back substitution are lane-local: the only cross-lane
 // traffic per section is the 5-round scan and the lookback.
 #pragma once
-#include <cuda_runtime.h>
-
-#include "sosfilt_internal.h"
+#include "sosfilt_dccr_core.cuh"
 
 namespace sosk {
-
-__host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
-
-__device__ __forceinline__ unsigned long long pack_word(unsigned tag, float v) {
-    return (static_cast<unsigned long long>(tag) << 32) | __float_as_uint(v);
-}
-
-__device__ __forceinline__ void st_relaxed_v2(unsigned long long *p, unsigned long long a,
-                                              unsigned long long b) {
-    asm volatile("st.relaxed.gpu.global.v2.b64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
-}
-
-__device__ __forceinline__ void ld_relaxed_v2(const unsigned long long *p, unsigned long long &a,
-                                              unsigned long long &b) {
-    asm volatile("ld.relaxed.gpu.global.v2.b64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
-}
-
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-    return t;
-}
-
-template <int N>
-__device__ __forceinline__ float pick(const float (&r)[N], int m) {
-    float v = 0.f;
-#pragma unroll
-    for (int j = 0; j < N; ++j) v = (j == m) ? r[j] : v;
-    return v;
-}
 
 // Warp-parallel decoupled lookback for one section of group g (g >= 1), Sec. IV-B.
 // One round reads the descriptors of 32*M predecessors with independent loads (one memory
@@ -158,66 +126,6 @@ __device__ __forceinline__ float2 lookback_resolve(const PassParams &p, const un
     }
     return acc;
 }
-
-template <int N, bool NORM>
-struct Section {
-    static constexpr int D = ilog2(N);
-
-    // Steps 1-2: zero-state reduction of the lane, in place.  After it, register m
-    // holds v_i[m] for the level i at which row m is eliminated (levels 1..D).
-    static __device__ __forceinline__ void reduce(float (&r)[N], const SecCoef &c) {
-        // first level, both parities (divide and conquer), taps of B(z) A(-z)
-#pragma unroll
-        for (int m = N - 1; m >= 0; --m) {
-            float v = NORM ? r[m] : c.t0 * r[m];
-            if (m >= 1) v = fmaf(c.t1, r[m - 1], v);
-            if (m >= 2) v = fmaf(c.t2, r[m - 2], v);
-            if (m >= 3) v = fmaf(c.t3, r[m - 3], v);
-            if (m >= 4) v = fmaf(c.t4, r[m - 4], v);
-            r[m] = v;
-        }
-        // levels 1 -> D on each chain (descending m keeps v_i[m - 2^(i+1)] unmodified)
-#pragma unroll
-        for (int i = 1; i < D; ++i) {
-            const int s = 1 << i;
-#pragma unroll
-            for (int par = 1; par >= 0; --par) {
-                const int first = par ? 2 * s - 1 : 2 * s - 2;
-#pragma unroll
-                for (int m = N - 2 + par; m >= first; m -= 2 * s) {
-                    float v = fmaf(c.ne[i], r[m - s], r[m]);
-                    if (m - 2 * s >= 0) v = fmaf(c.f[i], r[m - 2 * s], v);
-                    r[m] = v;
-                }
-            }
-        }
-    }
-
-    // Step 5: back substitution with the lane's incoming state z (scaled domain).
-    static __device__ __forceinline__ void back_substitute(float (&r)[N], const SecCoef &c, float z1, float z2) {
-        r[N - 1] = fmaf(c.qo[D][0], z1, fmaf(c.qo[D][1], z2, r[N - 1]));
-        r[N - 2] = fmaf(c.qe[D][0], z1, fmaf(c.qe[D][1], z2, r[N - 2]));
-#pragma unroll
-        for (int i = D - 1; i >= 1; --i) {
-            const int s = 1 << i;
-#pragma unroll
-            for (int par = 1; par >= 0; --par) {
-                const int first = par ? s - 1 : s - 2;
-#pragma unroll
-                for (int m = first; m < N; m += 2 * s) {
-                    float v = r[m];
-                    if (m == first) {
-                        v = par ? fmaf(c.qo[i][0], z1, fmaf(c.qo[i][1], z2, v))
-                                : fmaf(c.qe[i][0], z1, fmaf(c.qe[i][1], z2, v));
-                    }
-                    if (m - s >= 0) v = fmaf(c.ne[i], r[m - s], v);
-                    if (m - 2 * s >= 0) v = fmaf(c.nf[i], r[m - 2 * s], v);
-                    r[m] = v;
-                }
-            }
-        }
-    }
-};
 
 // One thread block = WARPS consecutive groups.  Per section the groups' zero-state carries are
 // combined in shared memory into the block's carry, and one leader warp runs the decoupled

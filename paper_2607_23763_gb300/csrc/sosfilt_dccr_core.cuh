@@ -1,0 +1,168 @@
+// Device building blocks shared by the kernels: memory-ordering and async-copy
+// primitives, and the register-resident divide-and-conquer cyclic reduction of one
+// section over one group (Sec. II-E, Eqs. 14-23).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "sosfilt_internal.h"
+
+namespace sosk {
+
+
+__host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
+
+__device__ __forceinline__ unsigned long long pack_word(unsigned tag, float v) {
+    return (static_cast<unsigned long long>(tag) << 32) | __float_as_uint(v);
+}
+
+__device__ __forceinline__ void st_relaxed_v2(unsigned long long *p, unsigned long long a,
+                                              unsigned long long b) {
+    asm volatile("st.relaxed.gpu.global.v2.b64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
+}
+
+__device__ __forceinline__ void ld_relaxed_v2(const unsigned long long *p, unsigned long long &a,
+                                              unsigned long long &b) {
+    asm volatile("ld.relaxed.gpu.global.v2.b64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+template <int N>
+__device__ __forceinline__ float pick(const float (&r)[N], int m) {
+    float v = 0.f;
+#pragma unroll
+    for (int j = 0; j < N; ++j) v = (j == m) ? r[j] : v;
+    return v;
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void st_relaxed_b64(unsigned long long *p, unsigned long long a) {
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(a) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed_b64(const unsigned long long *p) {
+    unsigned long long a;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(a) : "l"(p) : "memory");
+    return a;
+}
+
+// mbarrier (shared::cta) primitives; waits are bounded by a cycle budget.
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase with the given parity to complete; false (and the timeout status bit) once
+// `budget` cycles have passed.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, long long budget, int *status) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > budget) {
+            atomicOr(status, kDevErrTimeout);
+            return false;
+        }
+    }
+    return true;
+}
+
+// Ampere-style asynchronous 16-byte global -> shared copies (L2 only).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Bulk (TMA, non-tensor) shared -> global stores tracked by per-thread bulk groups.
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void bulk_store(void *gmem, const void *smem, unsigned bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gmem), "r"(smem_u32(smem)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+template <int N, bool NORM>
+struct Section {
+    static constexpr int D = ilog2(N);
+
+    // Steps 1-2: zero-state reduction of the lane, in place.  After it, register m
+    // holds v_i[m] for the level i at which row m is eliminated (levels 1..D).
+    static __device__ __forceinline__ void reduce(float (&r)[N], const SecCoef &c) {
+        // first level, both parities (divide and conquer), taps of B(z) A(-z)
+#pragma unroll
+        for (int m = N - 1; m >= 0; --m) {
+            float v = NORM ? r[m] : c.t0 * r[m];
+            if (m >= 1) v = fmaf(c.t1, r[m - 1], v);
+            if (m >= 2) v = fmaf(c.t2, r[m - 2], v);
+            if (m >= 3) v = fmaf(c.t3, r[m - 3], v);
+            if (m >= 4) v = fmaf(c.t4, r[m - 4], v);
+            r[m] = v;
+        }
+        // levels 1 -> D on each chain (descending m keeps v_i[m - 2^(i+1)] unmodified)
+#pragma unroll
+        for (int i = 1; i < D; ++i) {
+            const int s = 1 << i;
+#pragma unroll
+            for (int par = 1; par >= 0; --par) {
+                const int first = par ? 2 * s - 1 : 2 * s - 2;
+#pragma unroll
+                for (int m = N - 2 + par; m >= first; m -= 2 * s) {
+                    float v = fmaf(c.ne[i], r[m - s], r[m]);
+                    if (m - 2 * s >= 0) v = fmaf(c.f[i], r[m - 2 * s], v);
+                    r[m] = v;
+                }
+            }
+        }
+    }
+
+    // Step 5: back substitution with the lane's incoming state z (scaled domain).
+    static __device__ __forceinline__ void back_substitute(float (&r)[N], const SecCoef &c, float z1, float z2) {
+        r[N - 1] = fmaf(c.qo[D][0], z1, fmaf(c.qo[D][1], z2, r[N - 1]));
+        r[N - 2] = fmaf(c.qe[D][0], z1, fmaf(c.qe[D][1], z2, r[N - 2]));
+#pragma unroll
+        for (int i = D - 1; i >= 1; --i) {
+            const int s = 1 << i;
+#pragma unroll
+            for (int par = 1; par >= 0; --par) {
+                const int first = par ? s - 1 : s - 2;
+#pragma unroll
+                for (int m = first; m < N; m += 2 * s) {
+                    float v = r[m];
+                    if (m == first) {
+                        v = par ? fmaf(c.qo[i][0], z1, fmaf(c.qo[i][1], z2, v))
+                                : fmaf(c.qe[i][0], z1, fmaf(c.qe[i][1], z2, v));
+                    }
+                    if (m - s >= 0) v = fmaf(c.ne[i], r[m - s], v);
+                    if (m - 2 * s >= 0) v = fmaf(c.nf[i], r[m - 2 * s], v);
+                    r[m] = v;
+                }
+            }
+        }
+    }
+};
+
+}  // namespace sosk

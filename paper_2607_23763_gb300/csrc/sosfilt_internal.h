@@ -24,6 +24,10 @@ constexpr int kGrpPowStride = kPow32 + kMaxLBM + 1;
 //   [6 + 3s] lookback rounds (low 32 bits) and waits (high 32 bits) of section s
 //   [28] before stage-out   [29] end   [30] SM id
 constexpr int kTraceSlots = 32;
+// Phase trace of the cascade kernel, per tile: [0] tile + 1, coordinator: [1] stash observed,
+// [2] tile carry folded, [3] incoming state resolved, [4] group states posted, [5] lookback
+// windows (low 32 bits) and waits (high 32 bits); warp 0: [6] pass start, [7] pass end,
+// [8] before waiting for the group state, [9] group state observed, [10] output issued; [11] SM id.
 
 // Device status bits (sticky, OR-ed by the kernels).
 constexpr int kDevErrTimeout = 1;
@@ -66,6 +70,49 @@ struct PassParams {
     long long trace_blocks;     // capacity of trace in blocks
     SecCoef sec[kMaxPass];
 };
+
+// ---- persistent kernel with one carry per tile for the whole cascade (sosfilt_cascade.cuh)
+constexpr int kMaxWin = 16;  // lookback windows of 32 tiles
+
+template <int K, int N>
+struct CasParams {
+    const float *x;
+    float *y;
+    long long n, G, n_tiles;    // samples, groups, tiles (W groups each)
+    const float *zi;            // device [K][2] initial state of this pass (true domain) or nullptr
+    float *zf;                  // device [K][2] final state of this pass or nullptr
+    float gain;                 // input multiplier (product of all b0 when normalized; first pass only)
+    unsigned long long *desc;   // [n_tiles][2K] tagged carry words
+    unsigned long long *ticket;
+    unsigned long long ticket_base;
+    unsigned int epoch;
+    int *status;
+    long long spin_budget;
+    int aligned;                // x and y 16-byte aligned
+    const float *tab;           // (M_N)^lane [32][MS], A_C, A_T^(2^k) (k < 5), A_T^(32 w) (w < kMaxWin)
+    unsigned long long *trace;  // nullptr, or [n_tiles][kTraceSlots] phase trace (see kCasTrace*)
+    long long trace_tiles;
+    SecCoef sec[K];
+    float H[2 * K][N];          // output at lane sample m of the zero-input cascade from unit state j
+    float A_tail[2 * K * (K + 1)];  // cascade transition over the last group's real samples (packed)
+};
+
+// Launch one pass of the cascade kernel (explicit specializations in sosfilt_cascade_n*.cu).
+template <int K, int N>
+cudaError_t launch_cascade(bool norm, const CasParams<K, N> &p, long long grid, cudaStream_t s);
+#define SOSK_DECLARE_CASCADE(K, N) \
+    template <>                    \
+    cudaError_t launch_cascade<K, N>(bool norm, const CasParams<K, N> &p, long long grid, cudaStream_t s);
+#define SOSK_DECLARE_CASCADE_N(N)                                                                    \
+    SOSK_DECLARE_CASCADE(1, N) SOSK_DECLARE_CASCADE(2, N) SOSK_DECLARE_CASCADE(3, N)                 \
+    SOSK_DECLARE_CASCADE(4, N) SOSK_DECLARE_CASCADE(5, N) SOSK_DECLARE_CASCADE(6, N)                 \
+    SOSK_DECLARE_CASCADE(7, N) SOSK_DECLARE_CASCADE(8, N)
+SOSK_DECLARE_CASCADE_N(32)
+SOSK_DECLARE_CASCADE_N(64)
+// Thread blocks of the cascade kernel that fit on one SM (0 if unavailable).
+int cascade_blocks_per_sm(int K, int N, bool norm);
+int cascade_warps(int N);       // compute warps (groups) per block
+size_t cascade_smem(int K, int N);
 
 // Launch one pass.  Returns cudaSuccess or the launch error.
 // lbm: predecessors read per lookback round / 32 (0 = the default for N).

@@ -65,24 +65,30 @@ SIZES = [1, 2, 3, 5, 31, 32, 33, 127, 511, 512, 513, 1023, 1024, 1025, 2047, 204
          3 * 2048 + 77, 40000, 100003]
 
 
-@pytest.mark.parametrize("N", [32, 64, 128])
+CARRY_CASCADE, CARRY_SECTION = 1, 2
+# (carry scheme, N): the cascade carry runs N = 32 and 64; per-section carries also N = 128
+SCHEMES = [(CARRY_CASCADE, 32), (CARRY_CASCADE, 64), (CARRY_SECTION, 32), (CARRY_SECTION, 64),
+           (CARRY_SECTION, 128)]
+
+
+@pytest.mark.parametrize("carry,N", SCHEMES)
 @pytest.mark.parametrize("n", SIZES)
-def test_order16_butterworth_sizes(dev, N, n):
+def test_order16_butterworth_sizes(dev, carry, N, n):
     sos = designs.butter_lowpass(16, 0.05)
     x = workloads.normal_f32(1, n)
     zi = np.random.default_rng(n).standard_normal((8, 2)) * 0.01
-    _run_check(sos, x, dev, zi=zi, tuning={"N": N})
+    _run_check(sos, x, dev, zi=zi, tuning={"N": N, "carry": carry})
 
 
 @pytest.mark.parametrize("K", [1, 2, 3, 4, 5, 6, 7, 8])
-@pytest.mark.parametrize("N", [32, 64, 128])
-def test_every_section_count(dev, K, N):
+@pytest.mark.parametrize("carry,N", SCHEMES)
+def test_every_section_count(dev, K, carry, N):
     u = workloads.uniform_f64(100 + K, 3 * K, stream=1).reshape(K, 3)
     sos = designs.random_sections(u)
     n = 5 * 32 * N + 123
     x = workloads.normal_f32(200 + K, n)
     zi = np.random.default_rng(K).standard_normal((K, 2)) * 0.1
-    _run_check(sos, x, dev, zi=zi, tuning={"N": N}, random_mix=True)
+    _run_check(sos, x, dev, zi=zi, tuning={"N": N, "carry": carry}, random_mix=True)
 
 
 def test_config1_full_size(dev):
@@ -93,34 +99,40 @@ def test_config1_full_size(dev):
     assert err < 1e-5
 
 
-def test_more_than_eight_sections_two_passes(dev):
+@pytest.mark.parametrize("carry", [CARRY_CASCADE, CARRY_SECTION])
+def test_more_than_eight_sections_two_passes(dev, carry):
     u = workloads.uniform_f64(77, 3 * 12, stream=1).reshape(12, 3)
     sos = designs.random_sections(u)
     x = workloads.normal_f32(78, 50000)
-    _run_check(sos, x, dev, zi=np.random.default_rng(3).standard_normal((12, 2)) * 0.1, random_mix=True)
+    _run_check(sos, x, dev, zi=np.random.default_rng(3).standard_normal((12, 2)) * 0.1, random_mix=True,
+               tuning={"carry": carry})
 
 
-def test_zero_b0_section_uses_general_taps(dev):
+@pytest.mark.parametrize("carry", [CARRY_CASCADE, CARRY_SECTION])
+def test_zero_b0_section_uses_general_taps(dev, carry):
     sos = designs.butter_lowpass(8, 0.2)
     sos[1, 0] = 0.0  # b0 = 0 for one section: no b0 normalization possible
     x = workloads.normal_f32(9, 20000)
-    _run_check(sos, x, dev)
+    _run_check(sos, x, dev, tuning={"carry": carry})
 
 
-def test_in_place_and_unaligned(dev):
+@pytest.mark.parametrize("carry", [CARRY_CASCADE, CARRY_SECTION])
+def test_in_place_and_unaligned(dev, carry):
     sos = designs.butter_lowpass(8, 0.1)
     x = workloads.normal_f32(5, 33333)
-    _run_check(sos, x, dev, in_place=True)
-    _run_check(sos, x, dev, offset=1)
-    _run_check(sos, x, dev, offset=3, in_place=True)
+    t = {"carry": carry}
+    _run_check(sos, x, dev, in_place=True, tuning=t)
+    _run_check(sos, x, dev, offset=1, tuning=t)
+    _run_check(sos, x, dev, offset=3, in_place=True, tuning=t)
 
 
-def test_resonator_bank_precision(dev):
+@pytest.mark.parametrize("carry", [CARRY_CASCADE, CARRY_SECTION])
+def test_resonator_bank_precision(dev, carry):
     """Poles at radius 0.999: bound 2e-3."""
     sos = designs.resonator_bank()
     n = 1 << 20
     x = workloads.normal_f32(4, n, sin_amp=1.0, sin_omega=0.32 * np.pi)
-    err = _run_check(sos, x, dev)
+    err = _run_check(sos, x, dev, tuning={"carry": carry})
     print(f"resonator bank rel err {err:.3e}")
 
 
