@@ -171,6 +171,8 @@ def bench_ours(args):
         tuning["N"] = args.N
     if args.lbw:
         tuning["lookback_width"] = args.lbw
+    if args.carry:
+        tuning["carry"] = args.carry
     tuning = tuning or None
     f = SosFilter(sos, tuning=tuning)
     x = torch.from_numpy(x_host).to(dev)
@@ -258,6 +260,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--N", type=int, default=0, help="samples per thread (16/32/64); 0 = library default")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--carry", type=int, default=0, help="1 = one carry per tile for the cascade, 2 = per section")
     ap.add_argument("--lbw", type=int, default=0, help="lookback width (predecessor blocks per round / 32); 0 = default")
     ap.add_argument("--order", type=int, default=16, help="filter order (16 = the workload; others for sweeps)")
     ap.add_argument("--log2n", type=int, default=28,

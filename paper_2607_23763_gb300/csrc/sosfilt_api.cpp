@@ -302,8 +302,12 @@ int lane_stride(int kp) {
     const int nf = packed_floats(kp);
     return ((nf / 4) & 1) ? nf : nf + 4;
 }
+// Table block of one pass: (M_N)^lane [32][stride], (A_T)^lane [32][stride] (packed), A_C dense
+// column-major (these are copied to shared memory), then A_T dense and (A_T)^(32 w) dense for
+// w = 1..kMaxWin (read from global memory).
 int table_floats(int kp) {
-    return 32 * lane_stride(kp) + (1 + 5 + sosk::kMaxWin) * packed_floats(kp) + 2 * (2 * kp) * (2 * kp);
+    const int full = (2 * kp) * (2 * kp);
+    return 2 * 32 * lane_stride(kp) + 2 * full + sosk::kMaxWin * full;
 }
 
 void dense_colmajor_into(const DMat &m, float *dst) {
@@ -350,29 +354,24 @@ sos_status build_cascade(sos_filter *f, int N, CasTables &ct) {
         const DMat MN = dpow(ps.M1, N);
         const DMat AC = dpow(MN, 32);
         const DMat AT = dpow(AC, W);
-        const int nf = packed_floats(kp), ms = lane_stride(kp);
+        const int ms = lane_stride(kp), full = S * S;
         std::vector<float> tab(table_floats(kp), 0.f);
-        DMat L = deye(S);
+        DMat L = deye(S), LT = deye(S);
         for (int l = 0; l < 32; ++l) {
             pack_into(L, kp, &tab[static_cast<size_t>(l) * ms]);
+            pack_into(LT, kp, &tab[static_cast<size_t>(32 + l) * ms]);
             L = dmul(L, MN);
+            LT = dmul(LT, AT);
         }
-        float *p_ac = &tab[32 * static_cast<size_t>(ms)];
-        pack_into(AC, kp, p_ac);
-        DMat P2 = AT;
-        for (int k = 0; k < 5; ++k) {
-            pack_into(P2, kp, p_ac + nf * (1 + k));
-            P2 = dmul(P2, P2);
-        }
+        float *p_dense = &tab[64 * static_cast<size_t>(ms)];
+        dense_colmajor_into(AC, p_dense);
+        dense_colmajor_into(AT, p_dense + full);
         const DMat AT32 = dpow(AT, 32);
-        DMat Pw = deye(S);
-        for (int w = 0; w < sosk::kMaxWin; ++w) {
-            pack_into(Pw, kp, p_ac + nf * (6 + w));
+        DMat Pw = AT32;
+        for (int w = 1; w <= sosk::kMaxWin; ++w) {
+            dense_colmajor_into(Pw, p_dense + full * (1 + w));
             Pw = dmul(Pw, AT32);
         }
-        float *p_dense = p_ac + nf * (6 + sosk::kMaxWin);
-        dense_colmajor_into(AC, p_dense);
-        dense_colmajor_into(AT, p_dense + S * S);
         if (cudaMalloc(&ps.d_tab, tab.size() * sizeof(float)) != cudaSuccess) return SOS_ENOMEM;
         if (cudaMemcpy(ps.d_tab, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
             return SOS_ECUDA;
@@ -551,7 +550,9 @@ sos_status launch_cascade_any(int K, sos_filter *f, CasPass &ps, const sosk::Sec
 // One carry per tile for the whole cascade (sosfilt_cascade.cuh), persistent grid.
 sos_status run_cascade(sos_filter *f, const float *x, float *y, int64_t n, const float *zi, float *zf,
                        cudaStream_t s) {
-    int N = f->tuning.N ? f->tuning.N : 32;
+    // default N from GB300 measurements on 2^28 samples (cascade carry): N = 64 for one section
+    // (HBM-bound, fewer tiles per sample), N = 32 otherwise (more warps to hide the pass's latency)
+    int N = f->tuning.N ? f->tuning.N : (f->K == 1 ? 64 : 32);
     if (N != 32 && N != 64) return SOS_EINVAL;
     const int ci = (N == 32) ? 0 : 1;
     const int ti = table_index(N);

@@ -32,9 +32,13 @@ struct CasDims {
     static constexpr int NF = 4 * NB;                      // floats of one packed matrix
     static constexpr int MS = ((NF / 4) & 1) ? NF : NF + 4;  // per-lane stride: conflict-free 128-bit reads
     static constexpr int FULL = S * S;                     // floats of one dense column-major matrix
-    // table block: (M_N)^lane [32][MS], A_C packed, A_T^(2^k) packed (k < 5), A_T^(32 w) packed
-    // (w < kMaxWin), A_C dense column-major, A_T dense column-major
-    static constexpr int TAB = 32 * MS + (1 + 5 + kMaxWin) * NF + 2 * FULL;
+    static constexpr int P2 = S <= 2 ? 2 : S <= 4 ? 4 : S <= 8 ? 8 : 16;  // S rounded up to a power of 2
+    static constexpr int SH = 5 - (P2 == 2 ? 1 : P2 == 4 ? 2 : P2 == 8 ? 3 : 4);  // lane >> SH = word
+    // table block copied to shared memory: (M_N)^lane [32][MS], (A_T)^lane [32][MS] (packed),
+    // A_C dense column-major; then, in global memory only, A_T dense and (A_T)^(32 w) dense for
+    // w = 1..kMaxWin
+    static constexpr int TAB = 2 * 32 * MS + FULL;
+    static constexpr int TAB_GLOBAL = TAB + (1 + kMaxWin) * FULL;
 };
 
 // y = A x for a packed lower block-triangular A (block (s, t), s >= t, at s(s+1)/2 + t, row-major).
@@ -48,6 +52,25 @@ __device__ __forceinline__ void packed_mv(const float *__restrict__ A, const flo
             const float4 B = *reinterpret_cast<const float4 *>(A + 4 * (s * (s + 1) / 2 + t));
             y0 = fmaf(B.x, x[2 * t], fmaf(B.y, x[2 * t + 1], y0));
             y1 = fmaf(B.z, x[2 * t], fmaf(B.w, x[2 * t + 1], y1));
+        }
+        y[2 * s] = y0;
+        y[2 * s + 1] = y1;
+    }
+}
+
+// y = A x with both A (packed) and x in shared memory (x read as word pairs, broadcast).
+template <int K>
+__device__ __forceinline__ void packed_mv_sx(const float *__restrict__ A, const float *__restrict__ x,
+                                             float (&y)[2 * K]) {
+#pragma unroll
+    for (int s = 0; s < K; ++s) {
+        float y0 = 0.f, y1 = 0.f;
+#pragma unroll
+        for (int t = 0; t <= s; ++t) {
+            const float4 B = *reinterpret_cast<const float4 *>(A + 4 * (s * (s + 1) / 2 + t));
+            const float2 xt = *reinterpret_cast<const float2 *>(x + 2 * t);
+            y0 = fmaf(B.x, xt.x, fmaf(B.y, xt.y, y0));
+            y1 = fmaf(B.z, xt.x, fmaf(B.w, xt.y, y1));
         }
         y[2 * s] = y0;
         y[2 * s + 1] = y1;
@@ -79,6 +102,27 @@ __device__ __forceinline__ float lane_mv(const float *__restrict__ A, float xi, 
 #pragma unroll
     for (int j = 0; j < S; ++j) y = fmaf(A[j * S + row], __shfl_sync(0xffffffffu, xi, j), y);
     return y;
+}
+
+// Sum t (S words per lane) over the 32 lanes, in place; lane l receives word (l >> SH) of the sum
+// (recursive halving: P2/2 + P2/4 + ... + 1 exchanges, then butterflies over the remaining lanes).
+template <int S, int P2, int SH>
+__device__ __forceinline__ float reduce_scatter(float (&t)[S], int lane) {
+#pragma unroll
+    for (int h = P2 / 2, off = 16; h >= 1; h /= 2, off /= 2) {
+        const bool up = (lane & off) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const float lo = i < S ? t[i] : 0.f;
+            const float hi = (h + i) < S ? t[h + i] : 0.f;
+            const float send = up ? lo : hi;
+            const float keep = up ? hi : lo;
+            if (i < S) t[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+    }
+#pragma unroll
+    for (int off = (1 << SH) / 2; off >= 1; off /= 2) t[0] += __shfl_xor_sync(0xffffffffu, t[0], off);
+    return t[0];
 }
 
 template <int S>
@@ -140,7 +184,7 @@ __device__ __forceinline__ void cascade_zero_state(float (&r)[N], const SecCoef 
 }
 
 template <int K, int N, bool NORM, int W>
-__global__ void __launch_bounds__((W + 1) * 32, 2) sos_cascade_kernel(const __grid_constant__ CasParams<K, N> p) {
+__global__ void __launch_bounds__((W + 1) * 32) __maxnreg__(N <= 32 ? 96 : 168) sos_cascade_kernel(const __grid_constant__ CasParams<K, N> p) {
     using Dm = CasDims<K>;
     constexpr int S = Dm::S, NF = Dm::NF, MS = Dm::MS;
     constexpr int P = N + 4;  // padded row pitch (floats): conflict-free 128-bit row access
@@ -148,12 +192,10 @@ __global__ void __launch_bounds__((W + 1) * 32, 2) sos_cascade_kernel(const __gr
     extern __shared__ float4 smem4[];
     float *rows = reinterpret_cast<float *>(smem4);    // [2][W][32][P]: prefetch X, stash Y
     float *sMl = rows + 2 * W * kL * P;                // [32][MS]: (M_N)^lane
-    float *sAC = sMl + kL * MS;                        // A_C
-    float *sApow = sAC + NF;                           // A_T^(2^k), k = 0..4
-    float *sAwin = sApow + 5 * NF;                     // A_T^(32 w), w = 0..kMaxWin-1
-    float *sACd = sAwin + kMaxWin * NF;                // A_C dense column-major
-    float *sATd = sACd + Dm::FULL;                     // A_T dense column-major
-    float *a_buf = sATd + Dm::FULL;                    // [2][W][S] local carries of the groups
+    float *sATl = sMl + kL * MS;                       // [32][MS]: (A_T)^lane
+    float *sACd = sATl + kL * MS;                      // A_C dense column-major
+    const float *gATd = p.tab + Dm::TAB;               // A_T dense column-major (global, L1-resident)
+    float *a_buf = sACd + Dm::FULL;                    // [2][W][S] local carries of the groups
     float *z_buf = a_buf + 2 * W * S;                  // [2][W][S] incoming states of the groups
     float *zs_tail = z_buf + 2 * W * S;                // [S] zero-state final state (last group)
     float *agg = zs_tail + S;                          // [2][S] tile carry under zero incoming state
@@ -228,16 +270,13 @@ __global__ void __launch_bounds__((W + 1) * 32, 2) sos_cascade_kernel(const __gr
             float tmp[S];
             if (tr) tr[2] = global_ns();
             unsigned long long *dcur = p.desc + static_cast<size_t>(cur) * S;
-            float Z[S];
+            float zi_lane = 0.f;  // word `lane` of the tile's incoming state (lanes < S)
             unsigned n_win = 0, n_wait = 0;
             if (cur == 0) {
-#pragma unroll
-                for (int i = 0; i < S; ++i) Z[i] = zinit(i);
+                zi_lane = zinit(lane < S ? lane : 0);
             } else {
                 // ---- decoupled lookback over tiles, 32 predecessors per round (local carry posted
                 // by the folding compute warp)
-#pragma unroll
-                for (int i = 0; i < S; ++i) Z[i] = 0.f;
                 const long long t_start = clock64();
                 int win = 0;
                 for (;;) {
@@ -278,30 +317,24 @@ __global__ void __launch_bounds__((W + 1) * 32, 2) sos_cascade_kernel(const __gr
 #pragma unroll
                         for (int i = 0; i < S; ++i) v[i] = 0.f;
                     }
-                    // sum_k A_T^k v_k over the window by a tree of uniform powers A_T^(2^r)
-#pragma unroll
-                    for (int r = 0; r < 5; ++r) {
-                        float u[S];
-#pragma unroll
-                        for (int i = 0; i < S; ++i) u[i] = __shfl_down_sync(0xffffffffu, v[i], 1 << r);
-                        if ((lane & ((2 << r) - 1)) == 0) {
-                            packed_mv<K>(sApow + r * NF, u, tmp);
-#pragma unroll
-                            for (int i = 0; i < S; ++i) v[i] += tmp[i];
-                        }
-                    }
-#pragma unroll
-                    for (int i = 0; i < S; ++i) v[i] = __shfl_sync(0xffffffffu, v[i], 0);
+                    // sum over the window of (A_T)^k v_k: each lane applies its own power, then a
+                    // reduce-scatter leaves word i of the sum in lane i
+                    packed_mv<K>(sATl + lane * MS, v, tmp);
+                    float part = reduce_scatter<S, Dm::P2, Dm::SH>(tmp, lane);
+                    part = __shfl_sync(0xffffffffu, part, (lane < S ? lane : 0) << Dm::SH);
                     if (win == 0) {
-#pragma unroll
-                        for (int i = 0; i < S; ++i) Z[i] += v[i];
+                        zi_lane += part;
                     } else {
-                        packed_mv<K>(sAwin + win * NF, v, tmp);
+                        // (A_T)^(32 win) from the global table (rarely needed)
+                        const float *Aw = p.tab + Dm::TAB + win * Dm::FULL;
+                        float y = 0.f;
+                        const int row = lane < S ? lane : 0;
 #pragma unroll
-                        for (int i = 0; i < S; ++i) Z[i] += tmp[i];
+                        for (int jj = 0; jj < S; ++jj) y = fmaf(__ldg(Aw + jj * S + row), __shfl_sync(0xffffffffu, part, jj), y);
+                        zi_lane += y;
                     }
                     if (j < 32) break;
-                    if (++win >= kMaxWin) {  // predecessors too far behind: report and give up
+                    if (++win > kMaxWin) {  // predecessors too far behind: report and give up
                         if (lane == 0) atomicOr(p.status, kDevErrTimeout);
                         break;
                     }
@@ -311,9 +344,14 @@ __global__ void __launch_bounds__((W + 1) * 32, 2) sos_cascade_kernel(const __gr
                 tr[3] = global_ns();
                 tr[5] = (static_cast<unsigned long long>(n_wait) << 32) | n_win;
             }
-            float zi_lane = lane_select<S>(Z, lane < S ? lane : 0);  // lane-parallel from here on
             if (cur + 1 < p.n_tiles) {
-                const float gl = lane_mv<S>(sATd, zi_lane, lane) + acc_i;  // A_T Z + tile carry
+                float gl = acc_i;  // A_T Z + tile carry
+                {
+                    const int row = lane < S ? lane : 0;
+#pragma unroll
+                    for (int jj = 0; jj < S; ++jj)
+                        gl = fmaf(__ldg(gATd + jj * S + row), __shfl_sync(0xffffffffu, zi_lane, jj), gl);
+                }
                 if (lane < S) st_relaxed_b64(dcur + lane, pack_word(tagG, gl));
             }
             // incoming state of each group of the tile: Z_0 = Z, Z_{w+1} = A_C Z_w + a_w
@@ -375,10 +413,8 @@ __global__ void __launch_bounds__((W + 1) * 32, 2) sos_cascade_kernel(const __gr
         wtrace(tile, 9);
         const long long g = tile * W + w;
         const float *zb = z_buf + ((jt & 1) * W + w) * S;
-        float Z[S], dz[S];
-#pragma unroll
-        for (int i = 0; i < S; ++i) Z[i] = zb[i];
-        packed_mv<K>(sMl + lane * MS, Z, dz);  // lane's incoming cascade state (M_N)^lane Z
+        float dz[S];
+        packed_mv_sx<K>(sMl + lane * MS, zb, dz);  // lane's incoming cascade state (M_N)^lane Z
         float *row = Y + lane * P;
 #pragma unroll
         for (int q = 0; q < N / 4; ++q) {
@@ -392,7 +428,9 @@ __global__ void __launch_bounds__((W + 1) * 32, 2) sos_cascade_kernel(const __gr
             *reinterpret_cast<float4 *>(row + 4 * q) = make_float4(e[0], e[1], e[2], e[3]);
         }
         if (want_zf && g == g_last && lane == lane_last) {
-            float zt[S];
+            float Z[S], zt[S];
+#pragma unroll
+            for (int i = 0; i < S; ++i) Z[i] = zb[i];
             packed_mv_param<K>(p.A_tail, Z, zt);
 #pragma unroll
             for (int s = 0; s < K; ++s) {
