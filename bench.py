@@ -29,7 +29,11 @@ ORDER = 16
 WN = 0.05
 SEED = 1
 BYTES_PER_SAMPLE = 8  # 4 B read + 4 B written: the algorithmic traffic of the filter (Sec. IV-C, Eq. 28)
-CPU_SAMPLE = 1 << 24  # bounded oracle sample (about 10-30 s of one host core at order 16)
+CPU_SAMPLE = 1 << 24  # oracle sample per step of the reference arm
+# DRAM bytes (read + write) of one launch of the timed kernel on the 2^28 workload: an ncu capture
+# of the same kernel on 2^26 samples scaled by 4 (profiles/sos_cascade_order16_2p26_traffic.md).
+# Must be re-captured (or set to None) whenever the kernel changes.
+TRAFFIC_BYTES_2P28 = 1.931e9
 
 
 def _peaks():
@@ -136,18 +140,18 @@ def bench_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline_leg():
+def cpu_baseline_leg(x_host):
+    """The float64 oracle over the whole workload (one pass, one host core, output not kept)."""
     import oracle
-    import workloads
     from workloads import designs
     sos = designs.butter_lowpass(ORDER, WN)
-    x = workloads.normal_f32(SEED, CPU_SAMPLE)
-    oracle.sosfilt(sos, x[:1024])
+    oracle.sosfilt(sos, x_host[:1024])
     t0 = time.perf_counter()
-    oracle.sosfilt(sos, x)
+    oracle.sosfilt(sos, x_host, keep_output=False)
     dt = time.perf_counter() - t0
-    return {"value": CPU_SAMPLE / dt / 1e9, "unit": "GS/s", "cores": 1, "kind": "oracle",
-            "sample": f"first 2^{int(np.log2(CPU_SAMPLE))} samples of the workload, one host core, {dt:.1f} s"}
+    n = x_host.shape[0]
+    return {"value": n / dt / 1e9, "unit": "GS/s", "cores": 1, "kind": "oracle",
+            "sample": f"the whole workload (2^{int(np.log2(n))} samples) once on one host core, {dt:.1f} s"}
 
 
 def bench_ours(args):
@@ -205,24 +209,23 @@ def bench_ours(args):
     gss = N_SAMPLES * world / (ms_step * 1e-3) / 1e9
     assert f.sync_status() == 0
 
-    # end to end: pinned host input -> device -> filter -> pinned host output, every step
+    # end to end through the C ABI with host buffers: sos_filter_run_host copies the pinned input
+    # in, filters and copies the output back in overlapping chunks, every step
     xh = torch.from_numpy(x_host).pin_memory()
     yh = torch.empty_like(xh).pin_memory()
     for _ in range(2):
-        x.copy_(xh, non_blocking=True)
-        f.run(x, y)
-        yh.copy_(y, non_blocking=True)
+        f.run_host(xh, yh)
     barrier()
     e_steps = max(3, min(args.steps, 10))
     t0 = time.perf_counter()
-    start.record(stream)
     for _ in range(e_steps):
-        x.copy_(xh, non_blocking=True)
-        f.run(x, y)
-        yh.copy_(y, non_blocking=True)
-    stop.record(stream)
+        f.run_host(xh, yh)
     barrier()
-    e_ms = start.elapsed_time(stop) / e_steps
+    e_ms = (time.perf_counter() - t0) * 1e3 / e_steps
+    if world > 1:
+        t = torch.tensor([e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e_ms = float(t.item())
     e_gss = N_SAMPLES * world / (e_ms * 1e-3) / 1e9
 
     hbm_peak, peak_kind = _peaks()
@@ -236,15 +239,18 @@ def bench_ours(args):
                    "N": args.N or "default", "L": 32, "l2": "inputs and outputs larger than L2 (1 GiB each)",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind,
-                     "kernel": "sos_dccr_kernel<8,N,true,4>"},
+                     "frac": achieved / hbm_peak,
+                     "traffic": TRAFFIC_BYTES_2P28 if (N_SAMPLES == 1 << 28 and ORDER == 16 and not args.N
+                                                       and not args.carry) else None,
+                     "peak_kind": peak_kind,
+                     "kernel": "sos_cascade_kernel (8 sections, N = 32 samples per lane, 8 groups per block)"},
         "e2e": {"value": e_gss, "unit": "GS/s", "h2d_bytes_per_step": 4 * N_SAMPLES,
                 "d2h_bytes_per_step": 4 * N_SAMPLES},
         "gpu_launches": args.steps,
         "clocks": clocks,
     }
     if rank == 0 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline_leg()
+        line["cpu_baseline"] = cpu_baseline_leg(x_host)
     if rank == 0:
         print(json.dumps(line), flush=True)
     f.close()

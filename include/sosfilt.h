@@ -124,6 +124,25 @@ sos_status sos_filter_run(sos_filter *f, const float *x_dev, float *y_dev, int64
                           float *zf_dev, void *stream);
 
 /*
+ * Filter a signal held in HOST memory.  The library copies it to the device,
+ * filters it and copies the result back in chunks, overlapping the
+ * host->device copy of chunk i+1, the filtering of chunk i (sos_filter_run
+ * with the state carried on the device from chunk to chunk, so the output
+ * equals one call over the whole signal) and the device->host copy of chunk
+ * i-1 on three library streams.  Synchronous: returns when y_host holds the
+ * output.
+ *   x_host, y_host  host float32[n]; may be equal; pinned memory (cudaHostAlloc
+ *                   or torch's pin_memory) lets the copies run at full speed
+ *   zi_host         host float32[K][2] initial state or NULL (zeros)
+ *   zf_host         host float32[K][2] receives the final state, or NULL
+ *   chunk_samples   samples per chunk, 0 = 2^24; the library keeps three device
+ *                   buffers of this size per filter after the first call
+ * Errors: SOS_EINVAL, SOS_ENOMEM, SOS_ECUDA; SOS_ETIMEOUT as for sos_filter_run.
+ */
+sos_status sos_filter_run_host(sos_filter *f, const float *x_host, float *y_host, int64_t n, const float *zi_host,
+                               float *zf_host, int64_t chunk_samples);
+
+/*
  * Filter many independent signals of uneven length and order in one
  * persistent launch over a global queue of (signal, group) tiles, with
  * lookback chains kept per signal.  Zero initial state for every signal.

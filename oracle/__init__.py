@@ -59,10 +59,11 @@ def _ptr(a):
     return None if a is None else a.ctypes.data
 
 
-def sosfilt(sos, x, zi=None, return_state: bool = False):
+def sosfilt(sos, x, zi=None, return_state: bool = False, keep_output: bool = True):
     """Filter x (float32 or float64, 1-D) through the cascade ``sos`` [K][5] in float64.
 
-    Returns y (float64) and, if ``return_state``, the final state zf [K][2].
+    Returns y (float64) and, if ``return_state``, the final state zf [K][2].  With
+    ``keep_output=False`` no output array is written (y is None): for timing runs.
     """
     lib = _load()
     sos = np.ascontiguousarray(np.asarray(sos, dtype=np.float64).reshape(-1, 5))
@@ -71,7 +72,7 @@ def sosfilt(sos, x, zi=None, return_state: bool = False):
     if x.dtype not in (np.float32, np.float64):
         x = x.astype(np.float64)
     n = x.shape[0]
-    y = np.empty(n, dtype=np.float64)
+    y = np.empty(n, dtype=np.float64) if keep_output else None
     zf = np.empty((k, 2), dtype=np.float64)
     zi_arr = None if zi is None else np.ascontiguousarray(np.asarray(zi, dtype=np.float64).reshape(k, 2))
     fn = lib.oracle_sosfilt_f32 if x.dtype == np.float32 else lib.oracle_sosfilt_f64

@@ -24,7 +24,7 @@ STATUS_NAMES = {0: "SOS_OK", -1: "SOS_EINVAL", -2: "SOS_ENOMEM", -3: "SOS_ECUDA"
 EXPORTED = (
     "sos_filter_create", "sos_filter_destroy", "sos_filter_run", "sos_filter_run_batch",
     "sos_filter_stream_push", "sos_filter_stream_state", "sos_filter_sync_status", "sos_filter_trace",
-    "sos_status_string",
+    "sos_filter_run_host", "sos_status_string",
 )
 
 
@@ -67,6 +67,7 @@ def load_library(path: str | None = None):
         lib.sos_filter_stream_state.argtypes = [vp, vp, vp, c_int]
         lib.sos_filter_sync_status.argtypes = [vp]
         lib.sos_filter_trace.argtypes = [vp, vp, i64]
+        lib.sos_filter_run_host.argtypes = [vp, vp, vp, i64, vp, vp, i64]
         lib.sos_status_string.argtypes = [c_int]
         lib.sos_status_string.restype = ctypes.c_char_p
         for name in EXPORTED:
@@ -144,6 +145,30 @@ class SosFilter:
                                         None if zf is None else _dptr(zf, "zf"), _stream_handle(stream)),
                "sos_filter_run")
         return y
+
+    def run_host(self, x, y=None, zi=None, chunk: int = 0, return_state: bool = False):
+        """Filter a signal in host memory (numpy float32 or pinned CPU tensor); returns y (same kind).
+
+        Copies in, filters and copies out in overlapping chunks inside the library.
+        """
+        import torch
+        if isinstance(x, torch.Tensor):
+            if x.is_cuda or x.dtype != torch.float32 or not x.is_contiguous():
+                raise TypeError("x must be a contiguous float32 CPU tensor")
+            if y is None:
+                y = torch.empty_like(x, pin_memory=x.is_pinned())
+            xp, yp, n = x.data_ptr(), y.data_ptr(), x.numel()
+        else:
+            x = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+            if y is None:
+                y = np.empty_like(x)
+            xp, yp, n = x.ctypes.data, y.ctypes.data, x.size
+        zi_arr = None if zi is None else np.ascontiguousarray(np.asarray(zi, dtype=np.float32).reshape(self.K, 2))
+        zf = np.empty((self.K, 2), dtype=np.float32) if return_state else None
+        _check(self._lib.sos_filter_run_host(self._h, xp, yp, n, None if zi_arr is None else zi_arr.ctypes.data,
+                                             None if zf is None else zf.ctypes.data, int(chunk)),
+               "sos_filter_run_host")
+        return (y, zf) if return_state else y
 
     def stream_push(self, x, y=None, stream=None):
         import torch

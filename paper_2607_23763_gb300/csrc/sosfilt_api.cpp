@@ -148,6 +148,12 @@ struct sos_filter {
     cudaStream_t last_stream = nullptr;
     unsigned long long *trace = nullptr;
     long long trace_blocks = 0;
+    // host-buffer pipeline (sos_filter_run_host), created on first use
+    cudaStream_t hs[3] = {nullptr, nullptr, nullptr};  // copy in, filter, copy out
+    cudaEvent_t ev_in[3] = {}, ev_done[3] = {}, ev_out[3] = {};
+    float *hbuf[3] = {nullptr, nullptr, nullptr};
+    long long hbuf_samples = 0;
+    float *d_hstate = nullptr;  // [K][2]
     std::mutex mu;
 };
 
@@ -732,6 +738,14 @@ sos_status sos_filter_destroy(sos_filter *f) {
     if (f->d_ticket) cudaFree(f->d_ticket);
     if (f->d_status) cudaFree(f->d_status);
     if (f->d_state) cudaFree(f->d_state);
+    for (int i = 0; i < 3; ++i) {
+        if (f->hs[i]) cudaStreamDestroy(f->hs[i]);
+        if (f->ev_in[i]) cudaEventDestroy(f->ev_in[i]);
+        if (f->ev_done[i]) cudaEventDestroy(f->ev_done[i]);
+        if (f->ev_out[i]) cudaEventDestroy(f->ev_out[i]);
+        if (f->hbuf[i]) cudaFree(f->hbuf[i]);
+    }
+    if (f->d_hstate) cudaFree(f->d_hstate);
     delete f;
     return SOS_OK;
 }
@@ -741,6 +755,67 @@ sos_status sos_filter_run(sos_filter *f, const float *x_dev, float *y_dev, int64
     if (!f) return SOS_EINVAL;
     std::lock_guard<std::mutex> lk(f->mu);
     return run_impl(f, x_dev, y_dev, n, zi_dev, zf_dev, static_cast<cudaStream_t>(stream));
+}
+
+sos_status sos_filter_run_host(sos_filter *f, const float *x_host, float *y_host, int64_t n, const float *zi_host,
+                               float *zf_host, int64_t chunk_samples) {
+    if (!f || n < 0 || chunk_samples < 0 || (n > 0 && (!x_host || !y_host))) return SOS_EINVAL;
+    std::lock_guard<std::mutex> lk(f->mu);
+    if (cudaSetDevice(f->device) != cudaSuccess) return SOS_ECUDA;
+    const long long chunk = chunk_samples ? chunk_samples : (1LL << 24);
+    if (!f->hs[0]) {
+        for (int i = 0; i < 3; ++i) {
+            if (cudaStreamCreateWithFlags(&f->hs[i], cudaStreamNonBlocking) != cudaSuccess) return SOS_ECUDA;
+            if (cudaEventCreateWithFlags(&f->ev_in[i], cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&f->ev_done[i], cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&f->ev_out[i], cudaEventDisableTiming) != cudaSuccess)
+                return SOS_ECUDA;
+        }
+        if (cudaMalloc(&f->d_hstate, sizeof(float) * 2 * f->K) != cudaSuccess) return SOS_ENOMEM;
+    }
+    if (f->hbuf_samples < chunk) {
+        for (int i = 0; i < 3; ++i) {
+            if (f->hbuf[i]) cudaFree(f->hbuf[i]);
+            f->hbuf[i] = nullptr;
+        }
+        f->hbuf_samples = 0;
+        for (int i = 0; i < 3; ++i)
+            if (cudaMalloc(&f->hbuf[i], sizeof(float) * chunk) != cudaSuccess) return SOS_ENOMEM;
+        f->hbuf_samples = chunk;
+    }
+    cudaStream_t sin = f->hs[0], sc = f->hs[1], sout = f->hs[2];
+    const size_t zbytes = sizeof(float) * 2 * f->K;
+    cudaError_t e = zi_host ? cudaMemcpyAsync(f->d_hstate, zi_host, zbytes, cudaMemcpyHostToDevice, sc)
+                            : cudaMemsetAsync(f->d_hstate, 0, zbytes, sc);
+    if (e != cudaSuccess) return SOS_ECUDA;
+    const long long nchunks = (n + chunk - 1) / chunk;
+    for (long long i = 0; i < nchunks; ++i) {
+        const int b = static_cast<int>(i % 3);
+        const long long off = i * chunk;
+        const long long len = (n - off) < chunk ? (n - off) : chunk;
+        const size_t bytes = sizeof(float) * static_cast<size_t>(len);
+        if (i >= 3 && cudaStreamWaitEvent(sin, f->ev_out[b], 0) != cudaSuccess) return SOS_ECUDA;
+        if (cudaMemcpyAsync(f->hbuf[b], x_host + off, bytes, cudaMemcpyHostToDevice, sin) != cudaSuccess)
+            return SOS_ECUDA;
+        if (cudaEventRecord(f->ev_in[b], sin) != cudaSuccess) return SOS_ECUDA;
+        if (cudaStreamWaitEvent(sc, f->ev_in[b], 0) != cudaSuccess) return SOS_ECUDA;
+        const sos_status st = run_impl(f, f->hbuf[b], f->hbuf[b], len, f->d_hstate, f->d_hstate, sc);
+        if (st != SOS_OK) return st;
+        if (cudaEventRecord(f->ev_done[b], sc) != cudaSuccess) return SOS_ECUDA;
+        if (cudaStreamWaitEvent(sout, f->ev_done[b], 0) != cudaSuccess) return SOS_ECUDA;
+        if (cudaMemcpyAsync(y_host + off, f->hbuf[b], bytes, cudaMemcpyDeviceToHost, sout) != cudaSuccess)
+            return SOS_ECUDA;
+        if (cudaEventRecord(f->ev_out[b], sout) != cudaSuccess) return SOS_ECUDA;
+    }
+    if (zf_host) {
+        if (cudaStreamSynchronize(sc) != cudaSuccess) return SOS_ECUDA;
+        if (cudaMemcpy(zf_host, f->d_hstate, zbytes, cudaMemcpyDeviceToHost) != cudaSuccess) return SOS_ECUDA;
+    }
+    if (cudaStreamSynchronize(sout) != cudaSuccess || cudaStreamSynchronize(sc) != cudaSuccess) return SOS_ECUDA;
+    f->last_stream = sc;
+    int h = 0;
+    if (cudaMemcpy(&h, f->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SOS_ECUDA;
+    return (h & sosk::kDevErrTimeout) ? SOS_ETIMEOUT : SOS_OK;
 }
 
 sos_status sos_filter_run_batch(int n_signals, sos_filter *const *filters, const float *const *x_dev,
