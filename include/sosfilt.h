@@ -192,6 +192,31 @@ sos_status sos_filter_sync_status(sos_filter *f);
  */
 sos_status sos_filter_trace(sos_filter *f, uint64_t *buf_dev, int64_t capacity_blocks);
 
+/*
+ * sos_filter_run: the same filtering, for callers that cannot allocate device memory
+ * while they filter.  (The paper has no counterpart; this is a library service.)  A
+ * real-time thread, such as an audio or radio receive loop, must not call cudaMalloc or
+ * cudaFree in its processing loop, because those calls can block and synchronize the
+ * device; other applications hand out all device memory at start-up.  Such a caller
+ * creates the filter (sos_filter_create allocates its tables once) and then filters
+ * with this entry point, which calls no cudaMalloc, cudaFree or other allocating routine:
+ * the scratch memory of a run (lookback descriptors and ticket counter) lives in one
+ * fixed array of 4 MiB + 256 B in the library's device code, which every GPU that loads
+ * the library holds until the process exits.
+ *   Arguments and results are those of sos_filter_run (always the cascade carry with the
+ *   library's default N).
+ *   n            at most SOS_NOALLOC_MAX_SAMPLES samples per call, else SOS_EBUDGET
+ *   The first call on a device looks up the array's device address on the current device
+ *   (a one-time set-up); make that first call before any stream capture.
+ *   All calls on a device share the array and its last contents: the ticket counter is
+ *   reset at the start of each pass and descriptors carry a per-call tag, so nothing needs
+ *   clearing by the caller, but calls that overlap on the GPU (different streams, or
+ *   different host threads without ordering) race and must be serialized by the caller.
+ */
+#define SOS_NOALLOC_MAX_SAMPLES (1LL << 28)
+sos_status sos_filter_run_noalloc(sos_filter *f, const float *x_dev, float *y_dev, int64_t n,
+                                  const float *zi_dev, float *zf_dev, void *stream);
+
 /* Human-readable name of a status code (static storage). */
 const char *sos_status_string(sos_status s);
 

@@ -24,7 +24,7 @@ STATUS_NAMES = {0: "SOS_OK", -1: "SOS_EINVAL", -2: "SOS_ENOMEM", -3: "SOS_ECUDA"
 EXPORTED = (
     "sos_filter_create", "sos_filter_destroy", "sos_filter_run", "sos_filter_run_batch",
     "sos_filter_stream_push", "sos_filter_stream_state", "sos_filter_sync_status", "sos_filter_trace",
-    "sos_filter_run_host", "sos_status_string",
+    "sos_filter_run_host", "sos_filter_run_noalloc", "sos_status_string",
 )
 
 
@@ -68,6 +68,7 @@ def load_library(path: str | None = None):
         lib.sos_filter_sync_status.argtypes = [vp]
         lib.sos_filter_trace.argtypes = [vp, vp, i64]
         lib.sos_filter_run_host.argtypes = [vp, vp, vp, i64, vp, vp, i64]
+        lib.sos_filter_run_noalloc.argtypes = [vp, vp, vp, i64, vp, vp, vp]
         lib.sos_status_string.argtypes = [c_int]
         lib.sos_status_string.restype = ctypes.c_char_p
         for name in EXPORTED:
@@ -144,6 +145,17 @@ class SosFilter:
                                         None if zi is None else _dptr(zi, "zi"),
                                         None if zf is None else _dptr(zf, "zf"), _stream_handle(stream)),
                "sos_filter_run")
+        return y
+
+    def run_noalloc(self, x, y, zi=None, zf=None, stream=None):
+        """Like run(), but allocates nothing on the device (scratch in the library's fixed array).
+
+        y must be supplied; at most 2^28 samples per call; calls must not overlap on the GPU.
+        """
+        _check(self._lib.sos_filter_run_noalloc(self._h, _dptr(x, "x"), _dptr(y, "y"), x.numel(),
+                                                None if zi is None else _dptr(zi, "zi"),
+                                                None if zf is None else _dptr(zf, "zf"), _stream_handle(stream)),
+               "sos_filter_run_noalloc")
         return y
 
     def run_host(self, x, y=None, zi=None, chunk: int = 0, return_state: bool = False):

@@ -114,6 +114,13 @@ int cascade_blocks_per_sm(int K, int N, bool norm);
 int cascade_warps(int N);       // compute warps (groups) per block
 size_t cascade_smem(int K, int N);
 
+// Device memory for the lookback descriptors and the ticket counter of one cascade run.
+struct Scratch {
+    unsigned long long *desc;
+    size_t desc_words;
+    unsigned long long *ticket;
+};
+
 // Launch one pass.  Returns cudaSuccess or the launch error.
 // lbm: predecessors read per lookback round / 32 (0 = the default for N).
 cudaError_t launch_dccr(int K, int N, bool norm, int lbm, const PassParams &p, long long grid, cudaStream_t s);

@@ -1,0 +1,68 @@
+// sos_filter_run_noalloc: the cascade-carry filter run with its scratch memory (lookback
+// descriptors and ticket counter) in one file-scope device array instead of library
+// allocations.  For callers that cannot allocate device memory while they filter: a real-time
+// thread (an audio or radio receive loop) must not call cudaMalloc/cudaFree, which can block
+// and synchronize the device, and some applications hand out all device memory at start-up.
+// Such callers create the filter object once during set-up and then filter with this entry
+// point, which calls no cudaMalloc, cudaFree or other allocating routine.
+#include <cstdint>
+#include <mutex>
+
+#include <cuda_runtime.h>
+
+#include "sosfilt.h"
+#include "sosfilt_internal.h"
+
+namespace sosk {
+int filter_device(const sos_filter *f);
+sos_status run_cascade_scratch(sos_filter *f, const float *x, float *y, int64_t n, const float *zi, float *zf,
+                               cudaStream_t s, const Scratch &sc, unsigned (*next_epoch)(int, cudaStream_t));
+}  // namespace sosk
+
+namespace {
+
+// Word 0: ticket counter; words 32..: lookback descriptors (tag << 32 | float bits).  Sized for
+// SOS_NOALLOC_MAX_SAMPLES samples per call (tiles of 8192 samples, up to 16 words each).
+constexpr size_t kDescWords = (static_cast<size_t>(SOS_NOALLOC_MAX_SAMPLES) / 8192) * 16;
+constexpr size_t kScratchWords = 32 + kDescWords;
+
+static __device__ __align__(256) unsigned long long g_noalloc_scratch[kScratchWords];
+
+std::mutex g_mu;
+unsigned long long *g_ptr[64] = {nullptr};  // device address of g_noalloc_scratch, per device
+unsigned g_epoch[64] = {0};                 // last epoch used on that device (tags are never 0)
+
+// Tag of the next pass on device dev (called with g_mu held).
+unsigned next_epoch_dev(int dev, cudaStream_t s) {
+    unsigned e = (g_epoch[dev] + 1) & 0x3fffffffu;
+    if (e == 0) {  // wrapped: clear old tags so that no stale descriptor can match
+        cudaMemsetAsync(g_ptr[dev] + 32, 0, kDescWords * sizeof(unsigned long long), s);
+        e = 1;
+    }
+    g_epoch[dev] = e;
+    return e;
+}
+
+}  // namespace
+
+extern "C" sos_status sos_filter_run_noalloc(sos_filter *f, const float *x_dev, float *y_dev, int64_t n,
+                                             const float *zi_dev, float *zf_dev, void *stream) {
+    if (!f || n < 0) return SOS_EINVAL;
+    if (n > SOS_NOALLOC_MAX_SAMPLES) return SOS_EBUDGET;
+    const int dev = sosk::filter_device(f);
+    if (dev < 0 || dev >= 64) return SOS_EINVAL;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (cudaSetDevice(dev) != cudaSuccess) return SOS_ECUDA;
+    if (!g_ptr[dev]) {
+        // one-time set-up on this device, with it current: the array's device address
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return SOS_ECUDA;
+        g_ptr[dev] = static_cast<unsigned long long *>(ptr);
+    }
+    sosk::Scratch sc;
+    sc.ticket = g_ptr[dev];
+    sc.desc = g_ptr[dev] + 32;
+    sc.desc_words = kDescWords;
+    return sosk::run_cascade_scratch(f, x_dev, y_dev, n, zi_dev, zf_dev, static_cast<cudaStream_t>(stream), sc,
+                                     next_epoch_dev);
+}

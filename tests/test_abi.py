@@ -30,7 +30,7 @@ def test_header_declares_the_abi():
     assert _declared() == sorted([
         "sos_filter_create", "sos_filter_destroy", "sos_filter_run", "sos_filter_run_batch",
         "sos_filter_stream_push", "sos_filter_stream_state", "sos_filter_sync_status", "sos_filter_trace",
-        "sos_filter_run_host", "sos_status_string"])
+        "sos_filter_run_host", "sos_filter_run_noalloc", "sos_status_string"])
 
 
 def test_library_exports_every_declared_symbol(lib):
@@ -67,6 +67,7 @@ def test_create_rejects_bad_arguments_before_touching_a_device(lib):
     assert lib.sos_filter_sync_status(None) == -1
     assert lib.sos_filter_trace(None, None, 0) == -1
     assert lib.sos_filter_run_host(None, None, None, 0, None, None, 0) == -1
+    assert lib.sos_filter_run_noalloc(None, None, None, 0, None, None, None) == -1
     assert lib.sos_filter_destroy(None) == 0
     assert lib.sos_filter_run_batch(0, None, None, None, None, None) == 0
     assert lib.sos_filter_run_batch(-1, None, None, None, None, None) == -1
