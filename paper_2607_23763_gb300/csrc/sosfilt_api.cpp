@@ -273,6 +273,19 @@ void build_tables(sos_filter *f, int N, NTables &t, std::vector<float4> &lane_po
         fill(cta_pow, mpow(TC, sosk::kWarps));
         s.zscale = static_cast<float>(f->zscale[k]);
         s.zscale_inv = static_cast<float>(1.0 / f->zscale[k]);
+        auto dup = [](float v) { return float2{v, v}; };
+        s.p_t0 = dup(s.t0);
+        s.p_t1 = dup(s.t1);
+        s.p_t2 = dup(s.t2);
+        s.p_t3 = dup(s.t3);
+        s.p_t4 = dup(s.t4);
+        for (int i = 0; i <= sosk::kMaxD; ++i) {
+            s.p_ne[i] = dup(s.ne[i]);
+            s.p_f[i] = dup(s.f[i]);
+            s.p_nf[i] = dup(s.nf[i]);
+            s.p_q0[i] = float2{s.qe[i][0], s.qo[i][0]};
+            s.p_q1[i] = float2{s.qe[i][1], s.qo[i][1]};
+        }
     }
 }
 

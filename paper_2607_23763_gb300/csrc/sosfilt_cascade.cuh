@@ -133,53 +133,68 @@ __device__ __forceinline__ float lane_select(const float (&v)[S], int i) {
     return r;
 }
 
-// Zero-state pass of one group through the K sections (registers only).
+// Zero-state pass of one group through section s (registers only); the lane's N samples are held as
+// N/2 (even, odd) pairs so both divide-and-conquer chains share packed FMAs.
+template <int N, bool NORM>
+__device__ __forceinline__ void section_zero_state(float2 (&P)[N / 2], const SecCoef &c, int s, float *a_out,
+                                                   int lane, bool tail_capture, int m_last, float *zs) {
+    constexpr int H = N / 2;
+    float xin_m = 0.f, xin_m1 = 0.f;
+    if (tail_capture) {
+        xin_m = pick_pair<H>(P, m_last);
+        xin_m1 = pick_pair<H>(P, m_last > 0 ? m_last - 1 : 0);
+    }
+    const float xs1 = P[H - 1].y, xs2 = P[H - 1].x;
+    SectionPair<N, NORM>::reduce(P, c);
+    const float yo = P[H - 1].y, ye = P[H - 1].x;
+    float t1 = fmaf(c.b1, xs1, fmaf(c.b2, xs2, -fmaf(c.a1, yo, c.a2 * ye)));
+    float t2 = fmaf(c.b2, xs1, -c.a2 * yo);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const float u1 = __shfl_up_sync(0xffffffffu, t1, 1 << k);
+        const float u2 = __shfl_up_sync(0xffffffffu, t2, 1 << k);
+        if (lane >= (1 << k)) {
+            t1 = fmaf(c.tn[k][0], u1, fmaf(c.tn[k][1], u2, t1));
+            t2 = fmaf(c.tn[k][2], u1, fmaf(c.tn[k][3], u2, t2));
+        }
+    }
+    float zx1 = __shfl_up_sync(0xffffffffu, t1, 1);
+    float zx2 = __shfl_up_sync(0xffffffffu, t2, 1);
+    if (lane == 0) zx1 = zx2 = 0.f;
+    if (lane == 31) {
+        a_out[2 * s] = t1;
+        a_out[2 * s + 1] = t2;
+    }
+    SectionPair<N, NORM>::back_substitute(P, c, zx1, zx2);
+    if (tail_capture) {
+        // transposed direct form II state after the signal's last sample (zero-state part)
+        const float ym = pick_pair<H>(P, m_last);
+        float f1;
+        if (m_last > 0) {
+            const float ym1 = pick_pair<H>(P, m_last - 1);
+            f1 = c.b1 * xin_m + c.b2 * xin_m1 - c.a1 * ym - c.a2 * ym1;
+        } else {
+            f1 = c.b1 * xin_m - c.a1 * ym + zx2;
+        }
+        zs[2 * s] = f1;
+        zs[2 * s + 1] = c.b2 * xin_m - c.a2 * ym;
+    }
+}
+
+// Zero-state pass of one group through the K sections.  Beyond two sections the loop over sections
+// stays rolled: one copy of the section code keeps the instruction footprint inside the cache
+// (unrolled, orders 8 and 16 stalled on instruction fetch).
 template <int K, int N, bool NORM>
-__device__ __forceinline__ void cascade_zero_state(float (&r)[N], const SecCoef *sec, float *a_out, int lane,
+__device__ __forceinline__ void cascade_zero_state(float2 (&P)[N / 2], const SecCoef *sec, float *a_out, int lane,
                                                    bool tail_capture, int m_last, float *zs) {
+    if constexpr (K <= 2) {
 #pragma unroll
-    for (int s = 0; s < K; ++s) {
-        const SecCoef &c = sec[s];
-        float xin_m = 0.f, xin_m1 = 0.f;
-        if (tail_capture) {
-            xin_m = pick<N>(r, m_last);
-            xin_m1 = pick<N>(r, m_last > 0 ? m_last - 1 : 0);
-        }
-        const float xs1 = r[N - 1], xs2 = r[N - 2];
-        Section<N, NORM>::reduce(r, c);
-        const float yo = r[N - 1], ye = r[N - 2];
-        float t1 = fmaf(c.b1, xs1, fmaf(c.b2, xs2, -fmaf(c.a1, yo, c.a2 * ye)));
-        float t2 = fmaf(c.b2, xs1, -c.a2 * yo);
-#pragma unroll
-        for (int k = 0; k < 5; ++k) {
-            const float u1 = __shfl_up_sync(0xffffffffu, t1, 1 << k);
-            const float u2 = __shfl_up_sync(0xffffffffu, t2, 1 << k);
-            if (lane >= (1 << k)) {
-                t1 = fmaf(c.tn[k][0], u1, fmaf(c.tn[k][1], u2, t1));
-                t2 = fmaf(c.tn[k][2], u1, fmaf(c.tn[k][3], u2, t2));
-            }
-        }
-        float zx1 = __shfl_up_sync(0xffffffffu, t1, 1);
-        float zx2 = __shfl_up_sync(0xffffffffu, t2, 1);
-        if (lane == 0) zx1 = zx2 = 0.f;
-        if (lane == 31) {
-            a_out[2 * s] = t1;
-            a_out[2 * s + 1] = t2;
-        }
-        Section<N, NORM>::back_substitute(r, c, zx1, zx2);
-        if (tail_capture) {
-            // transposed direct form II state after the signal's last sample (zero-state part)
-            const float ym = pick<N>(r, m_last);
-            float f1;
-            if (m_last > 0) {
-                const float ym1 = pick<N>(r, m_last - 1);
-                f1 = c.b1 * xin_m + c.b2 * xin_m1 - c.a1 * ym - c.a2 * ym1;
-            } else {
-                f1 = c.b1 * xin_m - c.a1 * ym + zx2;
-            }
-            zs[2 * s] = f1;
-            zs[2 * s + 1] = c.b2 * xin_m - c.a2 * ym;
-        }
+        for (int s = 0; s < K; ++s)
+            section_zero_state<N, NORM>(P, sec[s], s, a_out, lane, tail_capture, m_last, zs);
+    } else {
+#pragma unroll 1
+        for (int s = 0; s < K; ++s)
+            section_zero_state<N, NORM>(P, sec[s], s, a_out, lane, tail_capture, m_last, zs);
     }
 }
 
@@ -255,6 +270,7 @@ __global__ void __launch_bounds__((W + 1) * 32) __maxnreg__(N <= 32 ? 96 : 168) 
             if (cur < 0) break;
 
             if (!mbar_wait(&bar_local[it & 1], (it >> 1) & 1, budget, p.status)) break;
+
             unsigned long long *tr = (p.trace && lane == 0 && cur < p.trace_tiles)
                                          ? p.trace + static_cast<size_t>(cur) * kTraceSlots
                                          : nullptr;
@@ -310,6 +326,7 @@ __global__ void __launch_bounds__((W + 1) * 32) __maxnreg__(N <= 32 ? 96 : 168) 
                             if (lane == 0) atomicOr(p.status, kDevErrTimeout);
                             break;
                         }
+                        __nanosleep(64);  // leave the issue slots to the computing warps meanwhile
                         continue;
                     }
                     ++n_win;
@@ -416,16 +433,20 @@ __global__ void __launch_bounds__((W + 1) * 32) __maxnreg__(N <= 32 ? 96 : 168) 
         float dz[S];
         packed_mv_sx<K>(sMl + lane * MS, zb, dz);  // lane's incoming cascade state (M_N)^lane Z
         float *row = Y + lane * P;
+        float2 dd[S];
+#pragma unroll
+        for (int j = 0; j < S; ++j) dd[j] = make_float2(dz[j], dz[j]);
 #pragma unroll
         for (int q = 0; q < N / 4; ++q) {
-            float4 v = *reinterpret_cast<float4 *>(row + 4 * q);
-            float e[4] = {v.x, v.y, v.z, v.w};
+            const float4 v = *reinterpret_cast<float4 *>(row + 4 * q);
+            float2 e0 = make_float2(v.x, v.y), e1 = make_float2(v.z, v.w);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-#pragma unroll
-                for (int j = 0; j < S; ++j) e[k] = fmaf(p.H[j][4 * q + k], dz[j], e[k]);
+            for (int j = 0; j < S; ++j) {
+                const float2 *hj = reinterpret_cast<const float2 *>(p.H[j]);
+                e0 = __ffma2_rn(hj[2 * q], dd[j], e0);
+                e1 = __ffma2_rn(hj[2 * q + 1], dd[j], e1);
             }
-            *reinterpret_cast<float4 *>(row + 4 * q) = make_float4(e[0], e[1], e[2], e[3]);
+            *reinterpret_cast<float4 *>(row + 4 * q) = make_float4(e0.x, e0.y, e1.x, e1.y);
         }
         if (want_zf && g == g_last && lane == lane_last) {
             float Z[S], zt[S];
@@ -474,18 +495,17 @@ __global__ void __launch_bounds__((W + 1) * 32) __maxnreg__(N <= 32 ? 96 : 168) 
         const long long g = tile * W + w;
         cp_async_wait_all();
         __syncwarp();
-        float r[N];
+        float2 r[N / 2];
 #pragma unroll
         for (int j = 0; j < N / 4; ++j) {
             const float4 v = *reinterpret_cast<const float4 *>(X + lane * P + 4 * j);
-            r[4 * j + 0] = v.x;
-            r[4 * j + 1] = v.y;
-            r[4 * j + 2] = v.z;
-            r[4 * j + 3] = v.w;
+            r[2 * j + 0] = make_float2(v.x, v.y);
+            r[2 * j + 1] = make_float2(v.z, v.w);
         }
         if (NORM) {
+            const float2 gg = make_float2(p.gain, p.gain);
 #pragma unroll
-            for (int m = 0; m < N; ++m) r[m] *= p.gain;
+            for (int j = 0; j < N / 2; ++j) r[j] = __fmul2_rn(r[j], gg);
         }
         __syncwarp();
         if (!mbar_wait(&bar_ticket[(it + 1) & 3], ((it + 1) >> 2) & 1, budget, p.status)) {
@@ -540,7 +560,7 @@ __global__ void __launch_bounds__((W + 1) * 32) __maxnreg__(N <= 32 ? 96 : 168) 
 #pragma unroll
         for (int j = 0; j < N / 4; ++j)
             *reinterpret_cast<float4 *>(Y + lane * P + 4 * j) =
-                make_float4(r[4 * j + 0], r[4 * j + 1], r[4 * j + 2], r[4 * j + 3]);
+                make_float4(r[2 * j].x, r[2 * j].y, r[2 * j + 1].x, r[2 * j + 1].y);
         __syncwarp();
         prev = tile;
         if (next < 0) break;

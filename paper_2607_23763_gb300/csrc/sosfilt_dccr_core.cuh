@@ -39,6 +39,20 @@ __device__ __forceinline__ float pick(const float (&r)[N], int m) {
     return v;
 }
 
+// Sample m of a lane held as (even, odd) pairs.
+template <int H>
+__device__ __forceinline__ float pick_pair(const float2 (&P)[H], int m) {
+    // component-wise selects: a select of whole pairs is turned into a dynamically indexed (local
+    // memory) array by the compiler
+    float v = 0.f;
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+        v = (m == 2 * j) ? P[j].x : v;
+        v = (m == 2 * j + 1) ? P[j].y : v;
+    }
+    return v;
+}
+
 __device__ __forceinline__ unsigned smem_u32(const void *p) {
     return static_cast<unsigned>(__cvta_generic_to_shared(p));
 }
@@ -73,12 +87,26 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned 
     return ok != 0;
 }
 
+// try_wait that may suspend the warp in hardware for up to `hint_ns` until the phase completes, so
+// that a waiting warp takes no issue slots from the computing ones.
+__device__ __forceinline__ bool mbar_try_wait_sleep(unsigned long long *bar, unsigned parity, unsigned hint_ns) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
+constexpr unsigned kSuspendHintNs = 200000;  // upper bound of one hardware suspension (0.2 ms)
+
 // Wait for the phase with the given parity to complete; false (and the timeout status bit) once
-// `budget` cycles have passed.
+// `budget` cycles have passed.  Every retry suspends the warp (bounded by kSuspendHintNs).
 __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, long long budget, int *status) {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
+    while (!mbar_try_wait_sleep(bar, parity, kSuspendHintNs)) {
         if (clock64() - t0 > budget) {
             atomicOr(status, kDevErrTimeout);
             return false;
@@ -160,6 +188,63 @@ struct Section {
                     if (m - 2 * s >= 0) v = fmaf(c.nf[i], r[m - 2 * s], v);
                     r[m] = v;
                 }
+            }
+        }
+    }
+};
+
+// The same solve with the lane's samples held as (even, odd) pairs P[j] = (x[2j], x[2j+1]): the two
+// divide-and-conquer chains run side by side in packed f32x2 FMAs (sm_100+), one instruction for
+// the matching samples of both chains.  Same operations and rounding as Section.
+template <int N, bool NORM>
+struct SectionPair {
+    static constexpr int D = ilog2(N);
+    static constexpr int H = N / 2;
+
+    static __device__ __forceinline__ void reduce(float2 (&P)[H], const SecCoef &c) {
+        // first level on every sample: v1 = B(z) A(-z) x; the odd taps need the shifted pairs
+        // (x[2j-1], x[2j]), built from neighbouring registers
+#pragma unroll
+        for (int j = H - 1; j >= 0; --j) {
+            const float2 A = P[j];
+            float2 v = NORM ? A : __fmul2_rn(c.p_t0, A);
+            const float2 Bp = (j >= 1) ? P[j - 1] : make_float2(0.f, 0.f);
+            v = __ffma2_rn(c.p_t1, make_float2(Bp.y, A.x), v);
+            if (j >= 1) v = __ffma2_rn(c.p_t2, Bp, v);
+            if (j >= 1) {
+                const float2 Cp = (j >= 2) ? P[j - 2] : make_float2(0.f, 0.f);
+                v = __ffma2_rn(c.p_t3, make_float2(Cp.y, Bp.x), v);
+                if (j >= 2) v = __ffma2_rn(c.p_t4, Cp, v);
+            }
+            P[j] = v;
+        }
+        // levels i -> i+1 on both chains at once: pair j holds (m-1, m) with m = -1 mod 2^(i+1)
+#pragma unroll
+        for (int i = 1; i < D; ++i) {
+            const int s = 1 << i;
+#pragma unroll
+            for (int j = H - 1; j >= s - 1; j -= s) {
+                float2 v = __ffma2_rn(c.p_ne[i], P[j - s / 2], P[j]);
+                if (j - s >= 0) v = __ffma2_rn(c.p_f[i], P[j - s], v);
+                P[j] = v;
+            }
+        }
+    }
+
+    static __device__ __forceinline__ void back_substitute(float2 (&P)[H], const SecCoef &c, float z1, float z2) {
+        const float2 zz1 = make_float2(z1, z1), zz2 = make_float2(z2, z2);
+        P[H - 1] = __ffma2_rn(c.p_q0[D], zz1, __ffma2_rn(c.p_q1[D], zz2, P[H - 1]));
+#pragma unroll
+        for (int i = D - 1; i >= 1; --i) {
+            const int s = 1 << i;
+            const int first = s / 2 - 1;
+#pragma unroll
+            for (int j = first; j < H; j += s) {
+                float2 v = P[j];
+                if (j == first) v = __ffma2_rn(c.p_q0[i], zz1, __ffma2_rn(c.p_q1[i], zz2, v));
+                if (j - s / 2 >= 0) v = __ffma2_rn(c.p_ne[i], P[j - s / 2], v);
+                if (j - s >= 0) v = __ffma2_rn(c.p_nf[i], P[j - s], v);
+                P[j] = v;
             }
         }
     }

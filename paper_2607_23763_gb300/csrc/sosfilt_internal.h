@@ -35,6 +35,12 @@ constexpr int kDevErrTimeout = 1;
 // Per-section tables, float32, derived in float64 on the host for one N.
 // Level i of the reduction holds y[m] + e_i y[m - 2^i] + f_i y[m - 2^(i+1)] = v_i[m].
 struct SecCoef {
+    // the same coefficients duplicated into (even, odd) pairs for packed f32x2 FMAs on the two
+    // divide-and-conquer chains
+    float2 p_t0, p_t1, p_t2, p_t3, p_t4;
+    float2 p_ne[kMaxD + 1], p_f[kMaxD + 1], p_nf[kMaxD + 1];
+    float2 p_q0[kMaxD + 1];         // (qe[i][0], qo[i][0]): state injection, z1 part
+    float2 p_q1[kMaxD + 1];         // (qe[i][1], qo[i][1]): state injection, z2 part
     float t0, t1, t2, t3, t4;       // first-level taps of B(z) A(-z) (Eq. 23 when b0 = 1)
     float b1, b2, a1, a2;           // section coefficients used by the terminal state (b / b0 when normalized)
     float ne[kMaxD + 1];            // -e_i, i = 1..D-1
@@ -93,7 +99,7 @@ struct CasParams {
     unsigned long long *trace;  // nullptr, or [n_tiles][kTraceSlots] phase trace (see kCasTrace*)
     long long trace_tiles;
     SecCoef sec[K];
-    float H[2 * K][N];          // output at lane sample m of the zero-input cascade from unit state j
+    alignas(8) float H[2 * K][N];        // output at lane sample m of the zero-input cascade from unit state j
     float A_tail[2 * K * (K + 1)];  // cascade transition over the last group's real samples (packed)
 };
 
