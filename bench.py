@@ -177,6 +177,8 @@ def bench_ours(args):
         tuning["lookback_width"] = args.lbw
     if args.carry:
         tuning["carry"] = args.carry
+    if args.solver:
+        tuning["solver"] = args.solver
     tuning = tuning or None
     f = SosFilter(sos, tuning=tuning)
     x = torch.from_numpy(x_host).to(dev)
@@ -267,6 +269,7 @@ def main():
     ap.add_argument("--N", type=int, default=0, help="samples per thread (16/32/64); 0 = library default")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--carry", type=int, default=0, help="1 = one carry per tile for the cascade, 2 = per section")
+    ap.add_argument("--solver", type=int, default=0, help="1 = cyclic reduction, 2 = PH factorization; 0 = default")
     ap.add_argument("--lbw", type=int, default=0, help="lookback width (predecessor blocks per round / 32); 0 = default")
     ap.add_argument("--order", type=int, default=16, help="filter order (16 = the workload; others for sweeps)")
     ap.add_argument("--log2n", type=int, default=28,

@@ -65,6 +65,16 @@ enum {
     SOS_CARRY_SECTION = 2  /* one decoupled lookback per section, as in Sec. IV-B */
 };
 
+/* Solvers of a group's zero-state response (see sos_tuning.solver). */
+enum {
+    SOS_SOLVER_DEFAULT = 0, /* the library's choice: SOS_SOLVER_CR */
+    SOS_SOLVER_CR = 1,      /* divide-and-conquer cyclic reduction per section (Sec. II-D, II-E,
+                               Eqs. 14-23); both carry schemes */
+    SOS_SOLVER_PH = 2       /* PH factorization (Sec. II-C): per-lane particular solutions from zero
+                               state, a lane scan of the whole cascade state and one homogeneous
+                               correction for lane and group states; cascade carry only, N = 32 */
+};
+
 /*
  * Launch configuration.  Any field left 0 selects the library's default for
  * that field (the built-in per-order table).
@@ -81,12 +91,16 @@ enum {
  *                      round, in units of 32: 1, 2, 4, 8 or 16 (values other than
  *                      the default for N exist for 8-section passes with b0 != 0)
  *   carry              SOS_CARRY_DEFAULT, SOS_CARRY_CASCADE or SOS_CARRY_SECTION
+ *   solver             SOS_SOLVER_DEFAULT (= SOS_SOLVER_CR), SOS_SOLVER_CR or SOS_SOLVER_PH;
+ *                      SOS_SOLVER_PH takes N = 0 or 32, carry SOS_CARRY_DEFAULT or
+ *                      SOS_CARRY_CASCADE and lookback_width 0
  */
 typedef struct {
     int N, L, groups_per_cta, threads_per_group, fp64_carry;
     long long spin_budget_cycles;
     int lookback_width;
     int carry;
+    int solver;
 } sos_tuning;
 
 /*

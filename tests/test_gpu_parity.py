@@ -66,29 +66,37 @@ SIZES = [1, 2, 3, 5, 31, 32, 33, 127, 511, 512, 513, 1023, 1024, 1025, 2047, 204
 
 
 CARRY_CASCADE, CARRY_SECTION = 1, 2
-# (carry scheme, N): the cascade carry runs N = 32 and 64; per-section carries also N = 128
-SCHEMES = [(CARRY_CASCADE, 32), (CARRY_CASCADE, 64), (CARRY_SECTION, 32), (CARRY_SECTION, 64),
-           (CARRY_SECTION, 128)]
+SOLVER_CR, SOLVER_PH = 1, 2
+# solver and launch configuration: PH factorization (N = 32, cascade carry); cyclic reduction with
+# the cascade carry at N = 32 and 64, and with per-section carries at N = 32, 64 and 128
+SCHEMES = [{"solver": SOLVER_PH}, {"carry": CARRY_CASCADE, "N": 32}, {"carry": CARRY_CASCADE, "N": 64},
+           {"carry": CARRY_SECTION, "N": 32}, {"carry": CARRY_SECTION, "N": 64},
+           {"carry": CARRY_SECTION, "N": 128}]
+SCHEME_IDS = ["ph", "cr-cascade-32", "cr-cascade-64", "cr-section-32", "cr-section-64", "cr-section-128"]
+# one setting per kernel: PH, cyclic reduction with the cascade carry, with per-section carries
+KERNELS = [{"solver": SOLVER_PH}, {"carry": CARRY_CASCADE}, {"carry": CARRY_SECTION}]
+KERNEL_IDS = ["ph", "cr-cascade", "cr-section"]
 
 
-@pytest.mark.parametrize("carry,N", SCHEMES)
+@pytest.mark.parametrize("tuning", SCHEMES, ids=SCHEME_IDS)
 @pytest.mark.parametrize("n", SIZES)
-def test_order16_butterworth_sizes(dev, carry, N, n):
+def test_order16_butterworth_sizes(dev, tuning, n):
     sos = designs.butter_lowpass(16, 0.05)
     x = workloads.normal_f32(1, n)
     zi = np.random.default_rng(n).standard_normal((8, 2)) * 0.01
-    _run_check(sos, x, dev, zi=zi, tuning={"N": N, "carry": carry})
+    _run_check(sos, x, dev, zi=zi, tuning=tuning)
 
 
 @pytest.mark.parametrize("K", [1, 2, 3, 4, 5, 6, 7, 8])
-@pytest.mark.parametrize("carry,N", SCHEMES)
-def test_every_section_count(dev, K, carry, N):
+@pytest.mark.parametrize("tuning", SCHEMES, ids=SCHEME_IDS)
+def test_every_section_count(dev, K, tuning):
     u = workloads.uniform_f64(100 + K, 3 * K, stream=1).reshape(K, 3)
     sos = designs.random_sections(u)
-    n = 5 * 32 * N + 123
+    # several tiles and a ragged tail (PH tiles hold 8 groups of 1024 samples)
+    n = 5 * 32 * tuning.get("N", 32) * (2 if tuning.get("solver") == SOLVER_PH else 1) + 123
     x = workloads.normal_f32(200 + K, n)
     zi = np.random.default_rng(K).standard_normal((K, 2)) * 0.1
-    _run_check(sos, x, dev, zi=zi, tuning={"N": N, "carry": carry}, random_mix=True)
+    _run_check(sos, x, dev, zi=zi, tuning=tuning, random_mix=True)
 
 
 def test_config1_full_size(dev):
@@ -99,40 +107,40 @@ def test_config1_full_size(dev):
     assert err < 1e-5
 
 
-@pytest.mark.parametrize("carry", [CARRY_CASCADE, CARRY_SECTION])
-def test_more_than_eight_sections_two_passes(dev, carry):
+@pytest.mark.parametrize("tuning", KERNELS, ids=KERNEL_IDS)
+def test_more_than_eight_sections_two_passes(dev, tuning):
     u = workloads.uniform_f64(77, 3 * 12, stream=1).reshape(12, 3)
     sos = designs.random_sections(u)
     x = workloads.normal_f32(78, 50000)
     _run_check(sos, x, dev, zi=np.random.default_rng(3).standard_normal((12, 2)) * 0.1, random_mix=True,
-               tuning={"carry": carry})
+               tuning=tuning)
 
 
-@pytest.mark.parametrize("carry", [CARRY_CASCADE, CARRY_SECTION])
-def test_zero_b0_section_uses_general_taps(dev, carry):
+@pytest.mark.parametrize("tuning", KERNELS, ids=KERNEL_IDS)
+def test_zero_b0_section_uses_general_taps(dev, tuning):
     sos = designs.butter_lowpass(8, 0.2)
     sos[1, 0] = 0.0  # b0 = 0 for one section: no b0 normalization possible
     x = workloads.normal_f32(9, 20000)
-    _run_check(sos, x, dev, tuning={"carry": carry})
+    _run_check(sos, x, dev, tuning=tuning)
 
 
-@pytest.mark.parametrize("carry", [CARRY_CASCADE, CARRY_SECTION])
-def test_in_place_and_unaligned(dev, carry):
+@pytest.mark.parametrize("tuning", KERNELS, ids=KERNEL_IDS)
+def test_in_place_and_unaligned(dev, tuning):
     sos = designs.butter_lowpass(8, 0.1)
     x = workloads.normal_f32(5, 33333)
-    t = {"carry": carry}
+    t = tuning
     _run_check(sos, x, dev, in_place=True, tuning=t)
     _run_check(sos, x, dev, offset=1, tuning=t)
     _run_check(sos, x, dev, offset=3, in_place=True, tuning=t)
 
 
-@pytest.mark.parametrize("carry", [CARRY_CASCADE, CARRY_SECTION])
-def test_resonator_bank_precision(dev, carry):
+@pytest.mark.parametrize("tuning", KERNELS, ids=KERNEL_IDS)
+def test_resonator_bank_precision(dev, tuning):
     """Poles at radius 0.999: bound 2e-3."""
     sos = designs.resonator_bank()
     n = 1 << 20
     x = workloads.normal_f32(4, n, sin_amp=1.0, sin_omega=0.32 * np.pi)
-    err = _run_check(sos, x, dev, tuning={"carry": carry})
+    err = _run_check(sos, x, dev, tuning=tuning)
     print(f"resonator bank rel err {err:.3e}")
 
 

@@ -1,0 +1,44 @@
+"""The float64 model of the PH-factorization kernel's decomposition agrees with the oracle.
+
+This pins the algebra of the PH kernel (lane particular solutions, the cascade lane scan through
+the coupling blocks of M_N, tile folding, one homogeneous correction, the final state) on the CPU,
+independently of the CUDA code.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from workloads import designs
+
+from . import ph_model as PM
+
+
+@pytest.mark.parametrize("K,n,W", [(1, 3 * 1024 + 5, 8), (2, 1, 8), (3, 9000, 2), (8, 40000, 8),
+                                   (8, 8 * 1024 * 3 + 1, 8), (5, 2047, 4)])
+def test_ph_model_matches_oracle(K, n, W):
+    sos = designs.butter_lowpass(2 * K, 0.05) if K > 1 else designs.butter_lowpass(2, 0.2)
+    x = workloads.normal_f32(1, n)
+    zi = np.random.default_rng(K).standard_normal((K, 2)) * 0.1
+    y, zf = PM.ph_filter(sos, x, zi=zi, W=W)
+    y_ref, zf_ref = oracle.sosfilt(sos, x, zi=zi, return_state=True)
+    assert np.abs(y - y_ref).max() <= 1e-12 * np.abs(y_ref).max()
+    assert np.abs(zf - zf_ref.reshape(-1)).max() <= 1e-12 * max(1.0, np.abs(zf_ref).max())
+
+
+def test_ph_model_random_sections_and_resonators():
+    for sos in (designs.random_sections(workloads.uniform_f64(7, 12).reshape(4, 3)), designs.resonator_bank()):
+        x = workloads.normal_f32(3, 5000)
+        y, _ = PM.ph_filter(sos, x)
+        y_ref = oracle.sosfilt(sos, x)
+        assert np.abs(y - y_ref).max() <= 1e-9 * np.abs(y_ref).max()
+
+
+def test_coupling_blocks_are_lower_triangular():
+    # the cascade transition is block lower-triangular: a section's state never feeds an earlier one
+    sos = designs.butter_lowpass(8, 0.1)
+    M1, _ = PM.tables([tuple(r) for r in sos], 32)
+    K = sos.shape[0]
+    for k in range(K):
+        for j in range(k + 1, K):
+            assert np.all(M1[2 * k:2 * k + 2, 2 * j:2 * j + 2] == 0.0)
