@@ -157,17 +157,43 @@ sos_status sos_filter_run_host(sos_filter *f, const float *x_host, float *y_host
                                float *zf_host, int64_t chunk_samples);
 
 /*
- * Filter many independent signals of uneven length and order in one
- * persistent launch over a global queue of (signal, group) tiles, with
- * lookback chains kept per signal.  Zero initial state for every signal.
+ * Filter many independent signals of uneven length and order: the signals with
+ * the same section count (and the same b0 handling) share one persistent
+ * launch over a global queue of (signal, tile) work items, tiles of 8 groups
+ * of 1024 samples, with the lookback chains of Sec. IV-B kept per signal (a
+ * chain ends at its signal's first tile).  The launches of the different
+ * section counts run concurrently on library streams forked from and joined
+ * back into `stream`.  Zero initial state for every signal.
  *   n_signals  >= 0
- *   filters    host array [n_signals] of filter objects (may repeat)
+ *   filters    host array [n_signals] of filter objects (may repeat), all on one device
  *   x_dev      host array [n_signals] of device input pointers
  *   y_dev      host array [n_signals] of device output pointers (in place allowed)
  *   n          host array [n_signals] of lengths (>= 0)
+ * Filters of more than 8 sections are filtered one by one (sos_filter_run).
+ * The library keeps four scratch sets per device (signal descriptors, lookback
+ * descriptors); a call waits on the host until the device has finished the
+ * batch that used its scratch set four calls earlier, so batch calls must not
+ * be made while `stream` is being captured into a CUDA graph.  Calls on one
+ * device are serialized on the host.  Device-side errors: sos_batch_sync_status.
  */
 sos_status sos_filter_run_batch(int n_signals, sos_filter *const *filters, const float *const *x_dev,
                                 float *const *y_dev, const int64_t *n, void *stream);
+
+/*
+ * sos_filter_run_batch with an initial and a final state per signal (the form
+ * the serving loop uses to keep every stream's cascade state on the device).
+ *   zi_dev  host array [n_signals] of device float32[K][2] initial states, or
+ *           NULL (all zero); an entry may be NULL (zero)
+ *   zf_dev  host array [n_signals] of device float32[K][2] final states, or NULL;
+ *           an entry may be NULL.  zf_dev[i] must not alias zi_dev[i].
+ */
+sos_status sos_filter_run_batch_ex(int n_signals, sos_filter *const *filters, const float *const *x_dev,
+                                   float *const *y_dev, const int64_t *n, const float *const *zi_dev,
+                                   float *const *zf_dev, void *stream);
+
+/* Synchronize the device and return the sticky status of its batched runs
+ * (SOS_ETIMEOUT after a lookback wait ran out of time). */
+sos_status sos_batch_sync_status(int device);
 
 /*
  * Continue filtering from the filter's resident device state (a [K][2]

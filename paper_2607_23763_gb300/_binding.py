@@ -24,7 +24,8 @@ STATUS_NAMES = {0: "SOS_OK", -1: "SOS_EINVAL", -2: "SOS_ENOMEM", -3: "SOS_ECUDA"
 EXPORTED = (
     "sos_filter_create", "sos_filter_destroy", "sos_filter_run", "sos_filter_run_batch",
     "sos_filter_stream_push", "sos_filter_stream_state", "sos_filter_sync_status", "sos_filter_trace",
-    "sos_filter_run_host", "sos_filter_run_noalloc", "sos_status_string",
+    "sos_filter_run_host", "sos_filter_run_noalloc", "sos_filter_run_batch_ex", "sos_batch_sync_status",
+    "sos_status_string",
 )
 
 
@@ -64,6 +65,8 @@ def load_library(path: str | None = None):
         lib.sos_filter_destroy.argtypes = [vp]
         lib.sos_filter_run.argtypes = [vp, vp, vp, i64, vp, vp, vp]
         lib.sos_filter_run_batch.argtypes = [c_int, vp, vp, vp, vp, vp]
+        lib.sos_filter_run_batch_ex.argtypes = [c_int, vp, vp, vp, vp, vp, vp, vp]
+        lib.sos_batch_sync_status.argtypes = [c_int]
         lib.sos_filter_stream_push.argtypes = [vp, vp, vp, i64, vp]
         lib.sos_filter_stream_state.argtypes = [vp, vp, vp, c_int]
         lib.sos_filter_sync_status.argtypes = [vp]
@@ -215,8 +218,12 @@ class SosFilter:
         return int(self._lib.sos_filter_sync_status(self._h))
 
 
-def run_batch(filters, xs, ys=None, stream=None):
-    """Filter many signals (each with its own filter object), zero initial state."""
+def run_batch(filters, xs, ys=None, zis=None, zfs=None, stream=None):
+    """Filter many signals (each with its own filter object) in one batched call.
+
+    ``zis``/``zfs``: optional lists of float32 CUDA tensors [K][2] (entries may be None) for the initial
+    and final states; without them every signal starts from zero state (sos_filter_run_batch).
+    """
     import torch
     lib = load_library()
     n = len(xs)
@@ -226,6 +233,22 @@ def run_batch(filters, xs, ys=None, stream=None):
     hx = (ctypes.c_void_p * n)(*[_dptr(x, "x") for x in xs])
     hy = (ctypes.c_void_p * n)(*[_dptr(y, "y") for y in ys])
     hn = (ctypes.c_int64 * n)(*[x.numel() for x in xs])
-    _check(lib.sos_filter_run_batch(n, ctypes.addressof(hf), ctypes.addressof(hx), ctypes.addressof(hy),
-                                    ctypes.addressof(hn), _stream_handle(stream)), "sos_filter_run_batch")
+    if zis is None and zfs is None:
+        _check(lib.sos_filter_run_batch(n, ctypes.addressof(hf), ctypes.addressof(hx), ctypes.addressof(hy),
+                                        ctypes.addressof(hn), _stream_handle(stream)), "sos_filter_run_batch")
+        return ys
+    def ptrs(ts, name):
+        if ts is None:
+            return None
+        return (ctypes.c_void_p * n)(*[None if t is None else _dptr(t, name) for t in ts])
+    hzi, hzf = ptrs(zis, "zi"), ptrs(zfs, "zf")
+    _check(lib.sos_filter_run_batch_ex(n, ctypes.addressof(hf), ctypes.addressof(hx), ctypes.addressof(hy),
+                                       ctypes.addressof(hn), None if hzi is None else ctypes.addressof(hzi),
+                                       None if hzf is None else ctypes.addressof(hzf), _stream_handle(stream)),
+           "sos_filter_run_batch_ex")
     return ys
+
+
+def batch_sync_status(device: int = 0) -> int:
+    """Synchronize the device and return the sticky status of its batched runs."""
+    return int(load_library().sos_batch_sync_status(int(device)))

@@ -121,6 +121,9 @@ struct CasPass {
     float *d_tab = nullptr;    // device table block (CasDims<kp>::TAB floats)
     long long tail_p = -1;     // position for which A_tail is cached
     std::vector<float> A_tail; // packed transition over tail_p + 1 samples
+    // N = kBatchN only: device copies for the multi-signal kernel
+    sosk::SecCoef *d_sec = nullptr;  // [kp] section tables
+    float *d_H = nullptr;            // [2 kp][N] output basis
 };
 
 struct CasTables {
@@ -353,6 +356,8 @@ void dense_colmajor_into(const DMat &m, float *dst) {
         for (int i = 0; i < m.n; ++i) dst[static_cast<size_t>(j) * m.n + i] = static_cast<float>(m.at(i, j));
 }
 
+int table_index(int N);
+
 // Transitions and output basis of every pass for one N, in float64, uploaded once.
 sos_status build_cascade(sos_filter *f, int N, CasTables &ct) {
     ct.N = N;
@@ -413,6 +418,15 @@ sos_status build_cascade(sos_filter *f, int N, CasTables &ct) {
         if (cudaMalloc(&ps.d_tab, tab.size() * sizeof(float)) != cudaSuccess) return SOS_ENOMEM;
         if (cudaMemcpy(ps.d_tab, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
             return SOS_ECUDA;
+        if (N == sosk::kBatchN) {
+            const NTables &nt = f->tables[table_index(N)];
+            if (cudaMalloc(&ps.d_sec, sizeof(sosk::SecCoef) * kp) != cudaSuccess ||
+                cudaMalloc(&ps.d_H, sizeof(float) * ps.H.size()) != cudaSuccess)
+                return SOS_ENOMEM;
+            if (cudaMemcpy(ps.d_sec, &nt.sec[k0], sizeof(sosk::SecCoef) * kp, cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemcpy(ps.d_H, ps.H.data(), sizeof(float) * ps.H.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+                return SOS_ECUDA;
+        }
         ct.passes.push_back(std::move(ps));
     }
     return SOS_OK;
@@ -901,6 +915,282 @@ sos_status run_impl(sos_filter *f, const float *x, float *y, int64_t n, const fl
     return run_cascade(f, x, y, n, zi, zf, s);
 }
 
+// ---- multi-signal runs (sosfilt_batch.cuh)
+constexpr int kBatchSlots = 4;     // batches whose scratch may be in use on the device at once
+constexpr int kBatchClasses = 16;  // (K, normalized) classes: K = 1..8, b0-normalized or not
+
+// Scratch of one batch in flight: signal descriptors, tile -> signal map, tail transitions, lookback
+// descriptors and ticket counters of its class launches; pinned host staging for the uploads.
+struct BatchSlot {
+    sosk::BatchSig *d_sigs = nullptr, *h_sigs = nullptr;
+    size_t sigs_cap = 0;
+    int *d_tile_sig = nullptr, *h_tile_sig = nullptr;
+    size_t tiles_cap = 0;
+    float *d_atail = nullptr, *h_atail = nullptr;
+    size_t atail_cap = 0;
+    unsigned long long *d_desc = nullptr;
+    size_t desc_cap = 0;
+    unsigned long long *d_ticket = nullptr;  // [kBatchClasses]
+    cudaEvent_t done = nullptr;
+    bool pending = false;
+};
+
+struct BatchCtx {
+    int device = -1;
+    std::mutex mu;
+    BatchSlot slot[kBatchSlots];
+    int next = 0;
+    cudaStream_t side[kBatchClasses] = {};
+    cudaEvent_t fork = nullptr, join[kBatchClasses] = {};
+    int *d_status = nullptr;
+    unsigned epoch = 0;
+};
+
+BatchCtx *batch_ctx(int device) {
+    static std::mutex mu;
+    static BatchCtx *ctx[64] = {nullptr};
+    if (device < 0 || device >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!ctx[device]) {
+        BatchCtx *c = new (std::nothrow) BatchCtx();
+        if (!c) return nullptr;
+        c->device = device;
+        bool ok = cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) == cudaSuccess &&
+                  cudaMalloc(&c->d_status, sizeof(int)) == cudaSuccess &&
+                  cudaMemset(c->d_status, 0, sizeof(int)) == cudaSuccess;
+        for (int i = 0; ok && i < kBatchClasses; ++i)
+            ok = cudaStreamCreateWithFlags(&c->side[i], cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&c->join[i], cudaEventDisableTiming) == cudaSuccess;
+        for (int i = 0; ok && i < kBatchSlots; ++i)
+            ok = cudaEventCreateWithFlags(&c->slot[i].done, cudaEventDisableTiming) == cudaSuccess &&
+                 cudaMalloc(&c->slot[i].d_ticket, sizeof(unsigned long long) * kBatchClasses) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            return nullptr;  // leaked on failure; the device is unusable anyway
+        }
+        ctx[device] = c;
+    }
+    return ctx[device];
+}
+
+// Grow a device/pinned-host pair to hold `want` elements.
+template <class T>
+bool grow_pair(T *&d, T *&h, size_t &cap, size_t want) {
+    if (want <= cap) return true;
+    size_t n = cap ? cap : 256;
+    while (n < want) n *= 2;
+    if (d) cudaFree(d);
+    if (h) cudaFreeHost(h);
+    d = nullptr;
+    h = nullptr;
+    cap = 0;
+    if (cudaMalloc(&d, n * sizeof(T)) != cudaSuccess || cudaMallocHost(&h, n * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cap = n;
+    return true;
+}
+
+template <int K>
+sos_status launch_batch_class(bool norm, const sosk::BatchParams<K> &bp, long long grid, cudaStream_t s) {
+    return sosk::launch_batch<K>(norm, bp, grid, s) == cudaSuccess ? SOS_OK : SOS_ECUDA;
+}
+
+sos_status launch_batch_any(int K, bool norm, const sosk::BatchSig *sigs, const int *tile_sig, long long n_tiles,
+                            unsigned long long *desc, unsigned long long *ticket, unsigned epoch, int *status,
+                            long long budget, long long grid, cudaStream_t s) {
+    switch (K) {
+#define SOSK_CASE(k)                                                                              \
+    case k: {                                                                                     \
+        sosk::BatchParams<k> bp{sigs, tile_sig, n_tiles, desc, ticket, 0ULL, epoch, status, budget}; \
+        return launch_batch_class<k>(norm, bp, grid, s);                                          \
+    }
+        SOSK_CASE(1) SOSK_CASE(2) SOSK_CASE(3) SOSK_CASE(4) SOSK_CASE(5) SOSK_CASE(6) SOSK_CASE(7) SOSK_CASE(8)
+#undef SOSK_CASE
+        default: return SOS_EINVAL;
+    }
+}
+
+// All signals of a batch in one persistent launch per (K, normalized) class; the class launches run
+// on forked streams, joined back into `s`.  Filters of more than eight sections run one by one.
+sos_status run_batch_impl(int n_signals, sos_filter *const *filters, const float *const *x, float *const *y,
+                          const int64_t *n, const float *const *zi, float *const *zf, cudaStream_t s) {
+    if (n_signals < 0) return SOS_EINVAL;
+    if (n_signals == 0) return SOS_OK;
+    if (!filters || !x || !y || !n) return SOS_EINVAL;
+    int device = -1;
+    for (int i = 0; i < n_signals; ++i) {
+        sos_filter *f = filters[i];
+        if (!f || n[i] < 0 || (n[i] > 0 && (!x[i] || !y[i]))) return SOS_EINVAL;
+        if (x[i] != y[i] && n[i] > 0 && ranges_overlap(x[i], y[i], n[i])) return SOS_EINVAL;
+        if (device < 0) device = f->device;
+        if (f->device != device) return SOS_EINVAL;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return SOS_ECUDA;
+    BatchCtx *ctx = batch_ctx(device);
+    if (!ctx) return SOS_ENOMEM;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+
+    constexpr long long C = 32LL * sosk::kBatchN;
+    constexpr long long W = sosk::kBatchW;
+    // classes and sizes
+    std::vector<int> cls(n_signals, -1);
+    long long cls_sigs[kBatchClasses] = {0}, cls_tiles[kBatchClasses] = {0}, cls_atail[kBatchClasses] = {0};
+    for (int i = 0; i < n_signals; ++i) {
+        sos_filter *f = filters[i];
+        if (n[i] == 0) {
+            if (zf && zf[i]) {
+                std::lock_guard<std::mutex> fl(f->mu);
+                const size_t b = sizeof(float) * 2 * f->K;
+                cudaError_t e = (zi && zi[i]) ? cudaMemcpyAsync(zf[i], zi[i], b, cudaMemcpyDeviceToDevice, s)
+                                              : cudaMemsetAsync(zf[i], 0, b, s);
+                if (e != cudaSuccess) return SOS_ECUDA;
+            }
+            continue;
+        }
+        if (f->K > sosk::kMaxPass) {
+            std::lock_guard<std::mutex> fl(f->mu);
+            sos_status st = run_impl(f, x[i], y[i], n[i], zi ? zi[i] : nullptr, zf ? zf[i] : nullptr, s);
+            if (st != SOS_OK) return st;
+            continue;
+        }
+        const int c = (f->K - 1) * 2 + (f->norm ? 1 : 0);
+        cls[i] = c;
+        cls_sigs[c] += 1;
+        const long long G = (n[i] + C - 1) / C;
+        cls_tiles[c] += (G + W - 1) / W;
+        if (zf && zf[i]) cls_atail[c] += packed_floats(f->K);
+    }
+    long long sig_off[kBatchClasses + 1] = {0}, tile_off[kBatchClasses + 1] = {0}, atail_off[kBatchClasses + 1] = {0},
+              desc_off[kBatchClasses + 1] = {0};
+    for (int c = 0; c < kBatchClasses; ++c) {
+        sig_off[c + 1] = sig_off[c] + cls_sigs[c];
+        tile_off[c + 1] = tile_off[c] + cls_tiles[c];
+        atail_off[c + 1] = atail_off[c] + cls_atail[c];
+        desc_off[c + 1] = desc_off[c] + cls_tiles[c] * 2 * (c / 2 + 1);
+    }
+    if (sig_off[kBatchClasses] == 0) return SOS_OK;
+
+    // a free scratch slot (its previous batch has completed on the device)
+    BatchSlot &sl = ctx->slot[ctx->next];
+    ctx->next = (ctx->next + 1) % kBatchSlots;
+    if (sl.pending && cudaEventSynchronize(sl.done) != cudaSuccess) return SOS_ECUDA;
+    sl.pending = false;
+    if (!grow_pair(sl.d_sigs, sl.h_sigs, sl.sigs_cap, sig_off[kBatchClasses]) ||
+        !grow_pair(sl.d_tile_sig, sl.h_tile_sig, sl.tiles_cap, tile_off[kBatchClasses]) ||
+        !grow_pair(sl.d_atail, sl.h_atail, sl.atail_cap, atail_off[kBatchClasses] + 1))
+        return SOS_ENOMEM;
+    if (static_cast<size_t>(desc_off[kBatchClasses]) > sl.desc_cap) {
+        if (sl.d_desc) {
+            cudaFree(sl.d_desc);
+            sl.d_desc = nullptr;
+            sl.desc_cap = 0;
+        }
+        const size_t want = static_cast<size_t>(desc_off[kBatchClasses]) * 2;
+        if (cudaMalloc(&sl.d_desc, want * sizeof(unsigned long long)) != cudaSuccess) {
+            cudaGetLastError();
+            return SOS_ENOMEM;
+        }
+        if (cudaMemsetAsync(sl.d_desc, 0, want * sizeof(unsigned long long), s) != cudaSuccess) return SOS_ECUDA;
+        sl.desc_cap = want;
+    }
+
+    // descriptors and the tile -> signal map, class by class
+    long long fill_sig[kBatchClasses], fill_tile[kBatchClasses], fill_atail[kBatchClasses];
+    for (int c = 0; c < kBatchClasses; ++c) {
+        fill_sig[c] = sig_off[c];
+        fill_tile[c] = tile_off[c];
+        fill_atail[c] = atail_off[c];
+    }
+    for (int i = 0; i < n_signals; ++i) {
+        const int c = cls[i];
+        if (c < 0) continue;
+        sos_filter *f = filters[i];
+        CasPass &ps = f->cas[0].passes[0];  // N = 32: the batch kernel's tables
+        const long long G = (n[i] + C - 1) / C;
+        const long long nt = (G + W - 1) / W;
+        const long long si = fill_sig[c]++;
+        sosk::BatchSig &b = sl.h_sigs[si];
+        b.x = x[i];
+        b.y = y[i];
+        b.n = n[i];
+        b.G = G;
+        b.tile0 = fill_tile[c] - tile_off[c];
+        b.zi = zi ? zi[i] : nullptr;
+        b.zf = zf ? zf[i] : nullptr;
+        b.sec = ps.d_sec;
+        b.H = ps.d_H;
+        b.tab = ps.d_tab;
+        b.A_tail = nullptr;
+        b.gain = static_cast<float>(f->gain);
+        b.aligned = (reinterpret_cast<uintptr_t>(x[i]) % 16 == 0 && reinterpret_cast<uintptr_t>(y[i]) % 16 == 0) ? 1 : 0;
+        if (b.zf) {
+            const long long tp = n[i] - 1 - (G - 1) * C;  // last real sample inside the last group
+            std::lock_guard<std::mutex> fl(f->mu);
+            if (ps.tail_p != tp) {
+                ps.A_tail.assign(packed_floats(f->K), 0.f);
+                pack_into(dpow(ps.M1, tp + 1), f->K, ps.A_tail.data());
+                ps.tail_p = tp;
+            }
+            std::memcpy(sl.h_atail + fill_atail[c], ps.A_tail.data(), sizeof(float) * packed_floats(f->K));
+            b.A_tail = sl.d_atail + fill_atail[c];
+            fill_atail[c] += packed_floats(f->K);
+        }
+        const long long local = si - sig_off[c];
+        for (long long t = 0; t < nt; ++t) sl.h_tile_sig[fill_tile[c]++] = static_cast<int>(local);
+    }
+    auto up = [&](void *d, const void *h, size_t bytes) {
+        return bytes == 0 || cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, s) == cudaSuccess;
+    };
+    if (!up(sl.d_sigs, sl.h_sigs, sizeof(sosk::BatchSig) * sig_off[kBatchClasses]) ||
+        !up(sl.d_tile_sig, sl.h_tile_sig, sizeof(int) * tile_off[kBatchClasses]) ||
+        !up(sl.d_atail, sl.h_atail, sizeof(float) * atail_off[kBatchClasses]) ||
+        cudaMemsetAsync(sl.d_ticket, 0, sizeof(unsigned long long) * kBatchClasses, s) != cudaSuccess)
+        return SOS_ECUDA;
+
+    // one persistent launch per class on its own stream, forked from and joined into s
+    if (cudaEventRecord(ctx->fork, s) != cudaSuccess) return SOS_ECUDA;
+    const long long budget = kDefaultSpinBudget;
+    for (int c = 0; c < kBatchClasses; ++c) {
+        if (cls_sigs[c] == 0) continue;
+        const int K = c / 2 + 1;
+        const bool norm = (c & 1) != 0;
+        cudaStream_t cs = ctx->side[c];
+        if (cudaStreamWaitEvent(cs, ctx->fork, 0) != cudaSuccess) return SOS_ECUDA;
+        ctx->epoch = (ctx->epoch + 1) & 0x3fffffffu;
+        if (ctx->epoch == 0) {  // wrapped: clear stale tags of every slot's descriptors
+            for (auto &o : ctx->slot)
+                if (o.d_desc) cudaMemsetAsync(o.d_desc, 0, o.desc_cap * sizeof(unsigned long long), cs);
+            ctx->epoch = 1;
+        }
+        const int bps = sosk::batch_blocks_per_sm(K, norm);
+        if (bps <= 0) return SOS_ECUDA;
+        long long grid = static_cast<long long>(bps) * sm_count(device);
+        if (grid > cls_tiles[c]) grid = cls_tiles[c];
+        sos_status st = launch_batch_any(K, norm, sl.d_sigs + sig_off[c], sl.d_tile_sig + tile_off[c], cls_tiles[c],
+                                         sl.d_desc + desc_off[c], sl.d_ticket + c, ctx->epoch, ctx->d_status, budget,
+                                         grid, cs);
+        if (st != SOS_OK) return st;
+        if (cudaEventRecord(ctx->join[c], cs) != cudaSuccess || cudaStreamWaitEvent(s, ctx->join[c], 0) != cudaSuccess)
+            return SOS_ECUDA;
+    }
+    if (cudaEventRecord(sl.done, s) != cudaSuccess) return SOS_ECUDA;
+    sl.pending = true;
+    for (int i = 0; i < n_signals; ++i)
+        if (filters[i]) filters[i]->last_stream = s;
+    return SOS_OK;
+}
+
+// Sticky device status of the batch context of a device (SOS_ETIMEOUT after a lookback timeout).
+sos_status batch_status(int device) {
+    BatchCtx *ctx = batch_ctx(device);
+    if (!ctx) return SOS_ENOMEM;
+    int h = 0;
+    if (cudaMemcpy(&h, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SOS_ECUDA;
+    return (h & sosk::kDevErrTimeout) ? SOS_ETIMEOUT : SOS_OK;
+}
+
 }  // namespace
 
 namespace sosk {
@@ -1084,8 +1374,11 @@ sos_status sos_filter_destroy(sos_filter *f) {
         if (t.d_cta_pow) cudaFree(t.d_cta_pow);
     }
     for (auto &ct : f->cas)
-        for (auto &ps : ct.passes)
+        for (auto &ps : ct.passes) {
             if (ps.d_tab) cudaFree(ps.d_tab);
+            if (ps.d_sec) cudaFree(ps.d_sec);
+            if (ps.d_H) cudaFree(ps.d_H);
+        }
     for (auto &ps : f->ph)
         if (ps.d_tab) cudaFree(ps.d_tab);
     if (f->d_desc) cudaFree(f->d_desc);
@@ -1175,17 +1468,18 @@ sos_status sos_filter_run_host(sos_filter *f, const float *x_host, float *y_host
 
 sos_status sos_filter_run_batch(int n_signals, sos_filter *const *filters, const float *const *x_dev,
                                 float *const *y_dev, const int64_t *n, void *stream) {
-    if (n_signals < 0) return SOS_EINVAL;
-    if (n_signals == 0) return SOS_OK;
-    if (!filters || !x_dev || !y_dev || !n) return SOS_EINVAL;
-    for (int i = 0; i < n_signals; ++i) {
-        if (!filters[i]) return SOS_EINVAL;
-        std::lock_guard<std::mutex> lk(filters[i]->mu);
-        sos_status st = run_impl(filters[i], x_dev[i], y_dev[i], n[i], nullptr, nullptr,
-                                 static_cast<cudaStream_t>(stream));
-        if (st != SOS_OK) return st;
-    }
-    return SOS_OK;
+    return run_batch_impl(n_signals, filters, x_dev, y_dev, n, nullptr, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+sos_status sos_filter_run_batch_ex(int n_signals, sos_filter *const *filters, const float *const *x_dev,
+                                   float *const *y_dev, const int64_t *n, const float *const *zi_dev,
+                                   float *const *zf_dev, void *stream) {
+    return run_batch_impl(n_signals, filters, x_dev, y_dev, n, zi_dev, zf_dev, static_cast<cudaStream_t>(stream));
+}
+
+sos_status sos_batch_sync_status(int device) {
+    if (cudaSetDevice(device) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return SOS_ECUDA;
+    return batch_status(device);
 }
 
 sos_status sos_filter_stream_push(sos_filter *f, const float *x_dev, float *y_dev, int64_t n, void *stream) {

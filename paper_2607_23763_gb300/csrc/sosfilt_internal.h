@@ -169,6 +169,49 @@ SOSK_DECLARE_PH(1) SOSK_DECLARE_PH(2) SOSK_DECLARE_PH(3) SOSK_DECLARE_PH(4)
 SOSK_DECLARE_PH(5) SOSK_DECLARE_PH(6) SOSK_DECLARE_PH(7) SOSK_DECLARE_PH(8)
 int ph_blocks_per_sm(int K, bool norm);
 
+// ---- multi-signal persistent kernel (sosfilt_batch.cuh): the cascade-carry cyclic-reduction
+// kernel over a global queue of (signal, tile) work items
+constexpr int kBatchN = 32;  // samples per lane
+constexpr int kBatchW = 8;   // groups (compute warps) per tile
+
+// One signal of a batch (device array, built by the host for each batched run).
+struct BatchSig {
+    const float *x;
+    float *y;
+    long long n, G;        // samples, groups of 32 kBatchN samples
+    long long tile0;       // first global tile of the signal; its tiles are tile0 .. tile0 + ceil(G / W) - 1
+    const float *zi;       // device [K][2] initial state (true domain) or nullptr
+    float *zf;             // device [K][2] final state or nullptr
+    const SecCoef *sec;    // device [K] section tables for N = kBatchN
+    const float *H;        // device [2K][kBatchN] zero-input output basis
+    const float *tab;      // device table block (CasDims<K>::TAB_GLOBAL floats)
+    const float *A_tail;   // device packed transition over the last group's real samples, or nullptr
+    float gain;            // input multiplier (product of the b0 when normalized)
+    int aligned;           // x and y 16-byte aligned
+};
+
+template <int K>
+struct BatchParams {
+    const BatchSig *sigs;
+    const int *tile_sig;        // [n_tiles] signal of each global tile
+    long long n_tiles;
+    unsigned long long *desc;   // [n_tiles][2K] tagged carry words
+    unsigned long long *ticket;
+    unsigned long long ticket_base;
+    unsigned int epoch;
+    int *status;
+    long long spin_budget;
+};
+
+template <int K>
+cudaError_t launch_batch(bool norm, const BatchParams<K> &p, long long grid, cudaStream_t s);
+#define SOSK_DECLARE_BATCH(K) \
+    template <>               \
+    cudaError_t launch_batch<K>(bool norm, const BatchParams<K> &p, long long grid, cudaStream_t s);
+SOSK_DECLARE_BATCH(1) SOSK_DECLARE_BATCH(2) SOSK_DECLARE_BATCH(3) SOSK_DECLARE_BATCH(4)
+SOSK_DECLARE_BATCH(5) SOSK_DECLARE_BATCH(6) SOSK_DECLARE_BATCH(7) SOSK_DECLARE_BATCH(8)
+int batch_blocks_per_sm(int K, bool norm);
+
 // Device memory for the lookback descriptors and the ticket counter of one cascade run.
 struct Scratch {
     unsigned long long *desc;

@@ -30,7 +30,8 @@ def test_header_declares_the_abi():
     assert _declared() == sorted([
         "sos_filter_create", "sos_filter_destroy", "sos_filter_run", "sos_filter_run_batch",
         "sos_filter_stream_push", "sos_filter_stream_state", "sos_filter_sync_status", "sos_filter_trace",
-        "sos_filter_run_host", "sos_filter_run_noalloc", "sos_status_string"])
+        "sos_filter_run_host", "sos_filter_run_noalloc", "sos_filter_run_batch_ex", "sos_batch_sync_status",
+        "sos_status_string"])
 
 
 def test_library_exports_every_declared_symbol(lib):

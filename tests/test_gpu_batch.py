@@ -1,0 +1,155 @@
+"""GPU parity of the batched runs (sos_filter_run_batch / _ex) against the float64 oracle.
+
+The multi-signal kernel keeps one lookback chain per signal inside one persistent launch per
+section count; these tests mix section counts, lengths (ragged tails, signals shorter than a tile,
+several tiles), b0 handling, in-place and unaligned buffers, initial and final states, and filters
+of more than eight sections (filtered one by one), and check every signal against the oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from workloads import designs
+
+from ._tol import bound
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def dev():
+    from paper_2607_23763_gb300 import build
+    build.build()
+    return torch.device("cuda:0")
+
+
+def _rel(a, b):
+    return oracle.rel_err(a, b)
+
+
+def _zerr(zf, zf_ref):
+    return float(np.abs(np.asarray(zf, np.float64) - zf_ref).max() / max(1e-30, np.abs(zf_ref).max()))
+
+
+LENGTHS = [1, 2, 31, 32, 33, 1023, 1024, 1025, 8191, 8192, 8193, 3 * 8192 + 1, 50000, 123457]
+
+
+def _mix(n_signals, seed):
+    rng = np.random.default_rng(seed)
+    items = []
+    for i in range(n_signals):
+        K = int(rng.integers(1, 9))
+        sos = designs.random_sections(workloads.uniform_f64(seed * 1000 + i, 3 * K, stream=1).reshape(K, 3))
+        if i % 7 == 3:
+            sos[0, 0] = 0.0  # b0 = 0: the general (not b0-normalized) tables
+        n = LENGTHS[i % len(LENGTHS)]
+        x = workloads.normal_f32(seed * 1000 + i, n)
+        zi = rng.standard_normal((K, 2)) * 0.1
+        items.append((sos, x, zi))
+    return items
+
+
+def test_batch_mixed_orders_lengths_states(dev):
+    from paper_2607_23763_gb300 import SosFilter, run_batch, batch_sync_status
+    items = _mix(56, 3)
+    # a 12-section filter in the mix (more than one pass: filtered on its own)
+    sos12 = designs.random_sections(workloads.uniform_f64(99, 36, stream=1).reshape(12, 3))
+    items.append((sos12, workloads.normal_f32(99, 20000), np.random.default_rng(9).standard_normal((12, 2)) * 0.1))
+    fs, xs, ys, zis, zfs = [], [], [], [], []
+    for i, (sos, x, zi) in enumerate(items):
+        fs.append(SosFilter(sos))
+        off = 1 if i % 11 == 5 else 0  # some unaligned buffers
+        buf = torch.zeros(len(x) + off, device=dev)
+        buf[off:] = torch.from_numpy(x).to(dev)
+        xd = buf[off:]
+        xs.append(xd)
+        ys.append(xd if i % 5 == 2 else torch.empty_like(xd))  # some in place
+        zis.append(torch.from_numpy(zi.astype(np.float32)).to(dev))
+        zfs.append(torch.full((sos.shape[0], 2), float("nan"), device=dev))
+    run_batch(fs, xs, ys, zis=zis, zfs=zfs)
+    torch.cuda.synchronize()
+    assert batch_sync_status(0) == 0
+    for (sos, x, zi), y, zf in zip(items, ys, zfs):
+        y_ref, zf_ref = oracle.sosfilt(sos, x, zi=zi.astype(np.float32).astype(np.float64), return_state=True)
+        tol = bound(sos, x, y_ref, random_mix=True)
+        err = _rel(y.cpu().numpy(), y_ref)
+        assert err < tol, (sos.shape[0], len(x), err, tol)
+        assert _zerr(zf.cpu().numpy(), zf_ref) < 10 * tol, (sos.shape[0], len(x))
+    for f in fs:
+        f.close()
+
+
+def test_batch_alone_equals_mix(dev):
+    """Each signal filtered alone (sos_filter_run) and inside a batch gives the same result."""
+    from paper_2607_23763_gb300 import SosFilter, run_batch
+    items = _mix(24, 5)
+    fs = [SosFilter(sos) for sos, _, _ in items]
+    xs = [torch.from_numpy(x).to(dev) for _, x, _ in items]
+    ys_mix = run_batch(fs, xs)
+    ys_alone = [f.run(x) for f, x in zip(fs, xs)]
+    torch.cuda.synchronize()
+    for (sos, x, _), a, b in zip(items, ys_alone, ys_mix):
+        y_ref = oracle.sosfilt(sos, x)
+        tol = bound(sos, x, y_ref, random_mix=True)
+        assert _rel(a.cpu().numpy(), y_ref) < tol
+        assert _rel(b.cpu().numpy(), y_ref) < tol
+        peak = max(1e-30, float(np.abs(y_ref).max()))
+        assert float((a - b).abs().max()) / peak < 2 * tol
+    for f in fs:
+        f.close()
+
+
+def test_batch_repeated_calls_reuse_scratch(dev):
+    """More calls than scratch sets in flight, back to back on one stream."""
+    from paper_2607_23763_gb300 import SosFilter, run_batch
+    items = _mix(10, 8)
+    fs = [SosFilter(sos) for sos, _, _ in items]
+    xs = [torch.from_numpy(x).to(dev) for _, x, _ in items]
+    outs = [run_batch(fs, xs) for _ in range(9)]
+    torch.cuda.synchronize()
+    for ys in outs[1:]:
+        for a, b in zip(outs[0], ys):
+            assert torch.isfinite(b).all()
+            assert float((a - b).abs().max()) <= 1e-3 * max(1e-30, float(a.abs().max()))
+    for f in fs:
+        f.close()
+
+
+def test_batched_mix_full_size_sampled(dev):
+    """The batched mix at full size (4096 signals, lengths 2^10..2^22, orders 2..16, random
+    sections) in one batched call, as the benchmark times it; every 16th signal checked against
+    the oracle (whole signal up to 2^18 samples, else windows restarted early with zero state)."""
+    from paper_2607_23763_gb300 import SosFilter, run_batch, batch_sync_status
+    n_sig = 4096
+    specs = [workloads.batched_signal(i) for i in range(n_sig)]
+    fs = [SosFilter(sos) for sos, _, _ in specs]
+    xs, hosts = [], {}
+    for i, (sos, n, seed) in enumerate(specs):
+        xh = workloads.normal_f32(seed, n)
+        if i % 16 == 0:
+            hosts[i] = xh
+        xs.append(torch.from_numpy(xh).to(dev))
+    ys = run_batch(fs, xs)
+    torch.cuda.synchronize()
+    assert batch_sync_status(0) == 0
+    rng = np.random.default_rng(4)
+    for i, xh in hosts.items():
+        sos, n, _ = specs[i]
+        y = ys[i]
+        if n <= 1 << 18:
+            y_ref = oracle.sosfilt(sos, xh)
+            assert _rel(y.cpu().numpy(), y_ref) < bound(sos, xh, y_ref, random_mix=True), (i, n)
+        else:
+            settle = 6000  # 0.995^6000 < 1e-13
+            for a in [0, n - 4096] + [int(v) for v in rng.integers(0, n - 4096, 3)]:
+                a0 = max(0, a - settle)
+                xw = xh[a0:a + 4096]
+                ref_w = oracle.sosfilt(sos, xw)
+                tol = bound(sos, xw, ref_w, random_mix=True)
+                got = y[a:a + 4096].cpu().numpy()
+                assert _rel(got, ref_w[a - a0:]) < tol, (i, n, a)
+    for f in fs:
+        f.close()

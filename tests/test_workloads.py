@@ -114,3 +114,33 @@ def test_random_sections():
         w = np.linspace(0, math.pi, 4001)
         peak = max(abs(_h(row[None], wi)) for wi in w)
         assert peak <= 1.0 + 1e-3
+
+
+def test_batched_mix_recipe():
+    orders, lens = [], []
+    for i in range(400):
+        sos, n, seed = workloads.batched_signal(i)
+        K = sos.shape[0]
+        orders.append(2 * K)
+        lens.append(n)
+        assert seed == 1000 + i
+        assert 2 ** 10 - 1 <= n <= 2 ** 22 + 1
+        assert designs.max_pole_radius(sos) < 0.9951
+    assert set(orders) == {2, 4, 8, 16}
+    # log-uniform lengths: the median of log2 length near 16
+    assert 15.0 < np.median(np.log2(lens)) < 17.0
+    # deterministic
+    a, b = workloads.batched_signal(7), workloads.batched_signal(7)
+    assert a[1] == b[1] and np.array_equal(a[0], b[0])
+
+
+def test_serving_mix_recipe():
+    from collections import Counter
+    cnt = Counter(2 * workloads.serving_stream(s).shape[0] for s in range(2000))
+    for order, share in zip(workloads.SERVE_ORDERS, workloads.SERVE_ORDER_SHARES):
+        assert abs(cnt[order] / 2000 - share) < 0.04
+    lens = [workloads.serving_chunk_len(s, c) for s in range(50) for c in range(20)]
+    assert min(lens) >= 4096 and max(lens) <= 65536
+    assert abs(np.mean(lens) - (4096 + 65536) / 2) < 2500
+    assert np.array_equal(workloads.serving_chunk(3, 5, 100), workloads.serving_chunk(3, 5, 100))
+    assert not np.array_equal(workloads.serving_chunk(3, 5, 100), workloads.serving_chunk(3, 6, 100))

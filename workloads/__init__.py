@@ -86,6 +86,48 @@ def uniform_f64(seed: int, n: int, stream: int = 0) -> np.ndarray:
     return out
 
 
+# ---------------------------------------------------------------------------
+# Mixes of many signals (batched runs) and many streams (serving).
+
+BATCH_ORDERS = (2, 4, 8, 16)
+SERVE_ORDERS = (2, 4, 8, 16)
+SERVE_ORDER_SHARES = (0.40, 0.30, 0.20, 0.10)
+
+
+def batched_signal(i: int, seed_base: int = 1000, log2_min: float = 10.0, log2_max: float = 22.0):
+    """Signal i of the batched mix: (sos, length, input seed).
+
+    Order uniform over {2, 4, 8, 16}; length round(2^U) with U uniform in [log2_min, log2_max];
+    random stable sections (``designs.random_sections``); input N(0,1) from seed seed_base + i.
+    """
+    u = uniform_f64(seed_base + i, 2 + 3 * 8, stream=1)
+    order = BATCH_ORDERS[min(3, int(u[0] * 4))]
+    n = int(round(2.0 ** (log2_min + (log2_max - log2_min) * u[1])))
+    K = order // 2
+    sos = designs.random_sections(u[2:2 + 3 * K].reshape(K, 3))
+    return sos, n, seed_base + i
+
+
+def serving_stream(sid: int, seed_base: int = 500000):
+    """Stream sid of the serving mix: sos with order 2/4/8/16 at 40/30/20/10 %, random sections."""
+    u = uniform_f64(seed_base + sid, 1 + 3 * 8, stream=2)
+    c = np.cumsum(SERVE_ORDER_SHARES)
+    order = SERVE_ORDERS[int(np.searchsorted(c, u[0], side="right"))]
+    K = order // 2
+    return designs.random_sections(u[1:1 + 3 * K].reshape(K, 3))
+
+
+def serving_chunk_len(sid: int, chunk: int, seed_base: int = 500000, lo: int = 4096, hi: int = 65536) -> int:
+    """Length of chunk `chunk` of stream sid: uniform integer in [lo, hi]."""
+    u = uniform_f64(seed_base + sid, 1, stream=(3 << 32) + chunk)[0]
+    return lo + min(hi - lo, int(u * (hi - lo + 1)))
+
+
+def serving_chunk(sid: int, chunk: int, n: int, seed_base: int = 500000) -> np.ndarray:
+    """Input of chunk `chunk` of stream sid: n samples of N(0,1)."""
+    return normal_f32(seed_base + sid, n, stream=(4 << 32) + chunk)
+
+
 def philox4x32_10_c(ctr, key) -> list[int]:
     """One Philox4x32-10 block through the C generator (for known-answer tests)."""
     lib = _load()
