@@ -260,12 +260,140 @@ def bench_ours(args):
         dist.destroy_process_group()
 
 
+def bench_batched(args):
+    """Batched mix: 4096 signals (orders 2/4/8/16, lengths 2^10..2^22) in one sos_filter_run_batch call
+    per step; GS/s of the whole batch, and its ratio to the plain kernel's rate at each signal's order."""
+    import torch
+
+    import workloads
+    from workloads import designs
+    from paper_2607_23763_gb300 import SosFilter, run_batch, batch_sync_status
+
+    torch.cuda.set_device(0)
+    n_sig = 4096
+    specs = [workloads.batched_signal(i) for i in range(n_sig)]
+    fs = [SosFilter(sos) for sos, _, _ in specs]
+    xs = [torch.from_numpy(workloads.normal_f32(seed, n)).cuda() for _, n, seed in specs]
+    ys = [torch.empty_like(x) for x in xs]
+    total = sum(n for _, n, _ in specs)
+    for _ in range(args.warmup):
+        run_batch(fs, xs, ys)
+    torch.cuda.synchronize()
+    assert batch_sync_status(0) == 0
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            run_batch(fs, xs, ys)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    assert batch_sync_status(0) == 0
+    # the plain single-signal kernel's rate per order on 2^28 samples
+    x = torch.from_numpy(workloads.normal_f32(1, 1 << 28)).cuda()
+    y = torch.empty_like(x)
+    rate = {}
+    for K in (1, 2, 4, 8):
+        f = SosFilter(designs.random_sections(workloads.uniform_f64(7, 3 * K, stream=1).reshape(K, 3)))
+        for _ in range(3):
+            f.run(x, y)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(5):
+            f.run(x, y)
+        b.record(stream)
+        torch.cuda.synchronize()
+        rate[K] = (1 << 28) / (a.elapsed_time(b) / 5) / 1e6
+        f.close()
+    plain_ms = sum(n / rate[sos.shape[0]] / 1e6 for sos, n, _ in specs)
+    gss = total / ms / 1e6
+    line = {"metric": "GS/s", "value": gss, "unit": "GS/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "batched mix: 4096 float32 signals, lengths round(2^U), U~U[10,22], orders "
+                                   "uniform over {2,4,8,16}, random stable sections, N(0,1) input, seeds 1000+i",
+                       "samples": total, "l2": "inputs and outputs larger than L2"},
+            "vs_plain_kernel": plain_ms / ms,
+            "plain_gss_by_order": {str(2 * k): v for k, v in rate.items()},
+            "gpu_launches": 4 * args.steps, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
+def bench_serving(args):
+    """Serving mix: streams with orders 2/4/8/16 at 40/30/20/10 %, chunks of U[4096, 65536] samples.
+    Capacity = closed loop (every chunk queued at t = 0); then Poisson arrivals at 80 % of capacity;
+    latency = completion - scheduled arrival; p50/p99 over the requests after a 10 % warm-up."""
+    import numpy as np
+    import torch
+
+    import workloads
+    from paper_2607_23763_gb300 import SosServer
+
+    torch.cuda.set_device(0)
+    n_streams = args.streams
+    per_stream = args.chunks_per_stream
+    srv = SosServer(budget_bytes=16 << 30)
+    t0 = time.perf_counter()
+    sids = [srv.add_stream(workloads.serving_stream(s)) for s in range(n_streams)]
+    t_setup = time.perf_counter() - t0
+    hi = 65536
+    pool = torch.from_numpy(workloads.normal_f32(77, 1 << 24)).cuda()  # chunk inputs are windows of this pool
+    out = torch.empty(n_streams * hi, device="cuda")
+    rng = np.random.default_rng(5)
+
+    def requests(n_req, arrivals):
+        sid = rng.integers(0, n_streams, n_req)
+        lens = np.array([workloads.serving_chunk_len(int(s), int(c)) for s, c in
+                         zip(sid, rng.integers(0, 1 << 20, n_req))], dtype=np.int64)
+        off = rng.integers(0, pool.numel() - hi, n_req)
+        xp = pool.data_ptr() + 4 * off
+        yp = out.data_ptr() + 4 * (sid * hi)
+        lat = srv.replay([sids[s] for s in sid], xp, yp, lens, arrivals)
+        return lens, lat
+
+    # closed loop: capacity
+    n_cap = n_streams * per_stream
+    lens, lat = requests(n_cap, np.zeros(n_cap))
+    capacity = lens.sum() / lat.max() / 1e9
+    # open loop: Poisson arrivals at 80 % of capacity
+    mean_len = (4096 + hi) / 2
+    rate = 0.8 * capacity * 1e9 / mean_len
+    n_open = max(args.open_requests, 1000)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_open))
+    lens, lat = requests(n_open, arrivals)
+    keep = slice(n_open // 10, None)
+    p50, p99 = np.percentile(lat[keep] * 1e3, [50, 99])
+    wall = arrivals[-1] + lat[-1]
+    gss = lens.sum() / wall / 1e9
+    st = srv.stats()
+    srv.close()
+    line = {"metric": "GS/s", "value": gss, "unit": "GS/s", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"serving mix: {n_streams} streams, orders 2/4/8/16 at 40/30/20/10 %, chunks "
+                                   "U[4096, 65536] float32 samples, Poisson arrivals at 80 % of measured capacity, "
+                                   "16 GiB budget, state resident on the device",
+                       "open_loop_requests": n_open, "closed_loop_requests": n_cap},
+            "capacity_gss": capacity, "offered_gss": 0.8 * capacity,
+            "latency_ms": {"p50": p50, "p99": p99, "max": float(lat.max() * 1e3)},
+            "batches": st["batches"], "max_batch": st["max_batch_seen"], "setup_s": t_setup}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="plain", choices=["plain", "batched", "serving"],
+                    help="plain = the order-16 single-signal workload (default); batched / serving mixes")
+    ap.add_argument("--streams", type=int, default=10000, help="serving: streams")
+    ap.add_argument("--chunks-per-stream", type=int, default=10, help="serving: closed-loop chunks per stream")
+    ap.add_argument("--open-requests", type=int, default=110000, help="serving: open-loop requests")
     ap.add_argument("--N", type=int, default=0, help="samples per thread (16/32/64); 0 = library default")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--carry", type=int, default=0, help="1 = one carry per tile for the cascade, 2 = per section")
@@ -286,6 +414,10 @@ def main():
         WORKLOAD = WORKLOAD.replace("2^28", f"2^{args.log2n}")
     if args.impl == "reference":
         bench_reference(args)
+    elif args.workload == "batched":
+        bench_batched(args)
+    elif args.workload == "serving":
+        bench_serving(args)
     else:
         bench_ours(args)
 

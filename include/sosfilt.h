@@ -118,7 +118,7 @@ sos_status sos_filter_create(int n_sections, const double *sos, const float *zi,
                              sos_filter **out);
 
 /* Release a filter and its device memory.  NULL is a no-op.  Synchronizes the
- * device work the library enqueued for this filter before freeing. */
+ * device (every stream) before freeing, so that no enqueued run still reads it. */
 sos_status sos_filter_destroy(sos_filter *f);
 
 /*
@@ -256,6 +256,70 @@ sos_status sos_filter_trace(sos_filter *f, uint64_t *buf_dev, int64_t capacity_b
 #define SOS_NOALLOC_MAX_SAMPLES (1LL << 28)
 sos_status sos_filter_run_noalloc(sos_filter *f, const float *x_dev, float *y_dev, int64_t n,
                                   const float *zi_dev, float *zf_dev, void *stream);
+
+/*
+ * Serving: a request loop with continuous batching over many streams (a
+ * library service built on sos_filter_run_batch_ex; the paper's method is the
+ * per-batch filtering).  Every stream is a cascade whose [K][2] state stays on
+ * the device between chunks, so a stream's next chunk continues from its last
+ * one with no host round trip.  Requests name caller-owned device buffers; a
+ * scheduler thread admits the oldest ready chunks (at most one chunk of a
+ * stream in flight, chunks of a stream in submission order) while the bytes in
+ * flight (8 per sample, 4 in place) stay within the budget, issues each batch
+ * on one of `max_inflight` CUDA streams so that batches overlap on the device,
+ * and records completions from a host function behind each batch.  Requests
+ * that arrive while others are on the device join the next batch as soon as
+ * budget and a batch slot free up.
+ */
+typedef struct sos_server sos_server;
+
+typedef struct {
+    int64_t budget_bytes; /* device bytes of chunks in flight; 0 = 16 GiB */
+    int max_batch;        /* chunks per batch; 0 = 4096 */
+    int max_inflight;     /* batches in flight on the device (1..4); 0 = 3 */
+} sos_server_config;
+
+typedef struct {
+    uint64_t request_id;
+    int stream_id;
+    int status;        /* sos_status of the request */
+    int64_t n;         /* samples */
+    double t_submit;   /* host steady-clock seconds: submission (or scheduled arrival, replay) */
+    double t_start;    /* admitted into a batch */
+    double t_done;     /* completion observed (host function behind the batch) */
+} sos_completion;
+
+typedef struct {
+    int64_t submitted, completed, rejected, batches, max_batch_seen, samples_done, inflight_bytes;
+} sos_server_stats;
+
+/* Create a server on the current device (NULL cfg = defaults). */
+sos_status sos_server_create(const sos_server_config *cfg, sos_server **out);
+/* Finish every queued request, then release the server, its streams and their states. */
+sos_status sos_server_destroy(sos_server *s);
+/* Add a stream: K sections `sos` [K][5] (as sos_filter_create), initial state zi [K][2] (host,
+ * NULL = zeros); *stream_id receives its index.  Allocates device memory. */
+sos_status sos_server_add_stream(sos_server *s, int n_sections, const double *sos, const float *zi, int *stream_id);
+/* Queue chunk x_dev[n] -> y_dev[n] (device buffers, may be equal; they must stay valid until the
+ * request completes) for a stream.  Errors: SOS_EINVAL, SOS_EBUDGET (chunk larger than the budget). */
+sos_status sos_server_submit(sos_server *s, int stream_id, const float *x_dev, float *y_dev, int64_t n,
+                             uint64_t *request_id);
+/* Move up to `max` completions to out (oldest first), waiting up to wait_ms for one if none is
+ * ready.  Returns the first error of any batch (sticky) or SOS_OK. */
+sos_status sos_server_poll(sos_server *s, sos_completion *out, int max, int *n_out, int wait_ms);
+/* Wait until every queued request has completed. */
+sos_status sos_server_drain(sos_server *s);
+/* Copy a stream's resident state [K][2] to the host after its queued chunks have completed. */
+sos_status sos_server_stream_state(sos_server *s, int stream_id, float *z_host);
+sos_status sos_server_get_stats(sos_server *s, sos_server_stats *out);
+/*
+ * Load replay for measurements: request i (stream stream_ids[i], buffers x_dev[i] -> y_dev[i],
+ * n[i] samples) arrives t_arrival[i] seconds after the call (non-decreasing); latency[i] receives
+ * its completion time minus its scheduled arrival.  Returns when all have completed.  The caller
+ * must not submit or poll on the server meanwhile (the replay consumes the completion queue).
+ */
+sos_status sos_server_replay(sos_server *s, int64_t n_req, const int32_t *stream_ids, const float *const *x_dev,
+                             float *const *y_dev, const int64_t *n, const double *t_arrival, double *latency);
 
 /* Human-readable name of a status code (static storage). */
 const char *sos_status_string(sos_status s);

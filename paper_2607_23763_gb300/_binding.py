@@ -25,6 +25,8 @@ EXPORTED = (
     "sos_filter_create", "sos_filter_destroy", "sos_filter_run", "sos_filter_run_batch",
     "sos_filter_stream_push", "sos_filter_stream_state", "sos_filter_sync_status", "sos_filter_trace",
     "sos_filter_run_host", "sos_filter_run_noalloc", "sos_filter_run_batch_ex", "sos_batch_sync_status",
+    "sos_server_create", "sos_server_destroy", "sos_server_add_stream", "sos_server_submit", "sos_server_poll",
+    "sos_server_drain", "sos_server_stream_state", "sos_server_get_stats", "sos_server_replay",
     "sos_status_string",
 )
 
@@ -67,6 +69,15 @@ def load_library(path: str | None = None):
         lib.sos_filter_run_batch.argtypes = [c_int, vp, vp, vp, vp, vp]
         lib.sos_filter_run_batch_ex.argtypes = [c_int, vp, vp, vp, vp, vp, vp, vp]
         lib.sos_batch_sync_status.argtypes = [c_int]
+        lib.sos_server_create.argtypes = [vp, ctypes.POINTER(vp)]
+        lib.sos_server_destroy.argtypes = [vp]
+        lib.sos_server_add_stream.argtypes = [vp, c_int, vp, vp, ctypes.POINTER(c_int)]
+        lib.sos_server_submit.argtypes = [vp, c_int, vp, vp, i64, ctypes.POINTER(ctypes.c_uint64)]
+        lib.sos_server_poll.argtypes = [vp, vp, c_int, ctypes.POINTER(c_int), c_int]
+        lib.sos_server_drain.argtypes = [vp]
+        lib.sos_server_stream_state.argtypes = [vp, c_int, vp]
+        lib.sos_server_get_stats.argtypes = [vp, vp]
+        lib.sos_server_replay.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
         lib.sos_filter_stream_push.argtypes = [vp, vp, vp, i64, vp]
         lib.sos_filter_stream_state.argtypes = [vp, vp, vp, c_int]
         lib.sos_filter_sync_status.argtypes = [vp]
@@ -252,3 +263,106 @@ def run_batch(filters, xs, ys=None, zis=None, zfs=None, stream=None):
 def batch_sync_status(device: int = 0) -> int:
     """Synchronize the device and return the sticky status of its batched runs."""
     return int(load_library().sos_batch_sync_status(int(device)))
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_int64), ("max_batch", ctypes.c_int), ("max_inflight", ctypes.c_int)]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("request_id", ctypes.c_uint64), ("stream_id", ctypes.c_int), ("status", ctypes.c_int),
+                ("n", ctypes.c_int64), ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("submitted", "completed", "rejected", "batches", "max_batch_seen",
+                                             "samples_done", "inflight_bytes")]
+
+
+class SosServer:
+    """Serving loop with continuous batching (sos_server_* in include/sosfilt.h).
+
+    Streams keep their cascade state on the device between chunks; chunks name device tensors that
+    must stay alive until they complete.
+    """
+
+    def __init__(self, budget_bytes: int = 0, max_batch: int = 0, max_inflight: int = 0):
+        self._lib = load_library()
+        cfg = ServerConfig(int(budget_bytes), int(max_batch), int(max_inflight))
+        h = ctypes.c_void_p()
+        _check(self._lib.sos_server_create(ctypes.addressof(cfg), ctypes.byref(h)), "sos_server_create")
+        self._h = h
+        self._keep = {}  # request id -> tensors kept alive until completion
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.sos_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            self._keep.clear()
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_stream(self, sos, zi=None) -> int:
+        sos = np.ascontiguousarray(np.asarray(sos, dtype=np.float64).reshape(-1, 5))
+        K = sos.shape[0]
+        zi_arr = None if zi is None else np.ascontiguousarray(np.asarray(zi, dtype=np.float32).reshape(K, 2))
+        sid = ctypes.c_int()
+        _check(self._lib.sos_server_add_stream(self._h, K, sos.ctypes.data,
+                                               None if zi_arr is None else zi_arr.ctypes.data, ctypes.byref(sid)),
+               "sos_server_add_stream")
+        return sid.value
+
+    def submit(self, stream_id: int, x, y=None) -> int:
+        import torch
+        if y is None:
+            y = torch.empty_like(x)
+        rid = ctypes.c_uint64()
+        _check(self._lib.sos_server_submit(self._h, int(stream_id), _dptr(x, "x"), _dptr(y, "y"), x.numel(),
+                                           ctypes.byref(rid)), "sos_server_submit")
+        self._keep[rid.value] = (x, y)
+        return rid.value
+
+    def output(self, request_id: int):
+        return self._keep[request_id][1]
+
+    def poll(self, max_n: int = 1024, wait_ms: int = 0):
+        """Completed requests as dicts (request_id, stream_id, status, n, t_submit, t_start, t_done)."""
+        buf = (Completion * max_n)()
+        n = ctypes.c_int()
+        _check(self._lib.sos_server_poll(self._h, ctypes.addressof(buf), max_n, ctypes.byref(n), int(wait_ms)),
+               "sos_server_poll")
+        return [{f: getattr(buf[i], f) for f, _ in Completion._fields_} for i in range(n.value)]
+
+    def drain(self):
+        _check(self._lib.sos_server_drain(self._h), "sos_server_drain")
+
+    def stream_state(self, stream_id: int, K: int) -> np.ndarray:
+        z = np.empty((K, 2), dtype=np.float32)
+        _check(self._lib.sos_server_stream_state(self._h, int(stream_id), z.ctypes.data), "sos_server_stream_state")
+        return z
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(self._lib.sos_server_get_stats(self._h, ctypes.addressof(st)), "sos_server_get_stats")
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def replay(self, stream_ids, x_ptrs, y_ptrs, lengths, t_arrival):
+        """Replay requests at the given arrival offsets (seconds); returns per-request latency (s).
+
+        x_ptrs / y_ptrs are integer device addresses (the caller keeps the memory alive).
+        """
+        m = len(stream_ids)
+        sid = np.ascontiguousarray(np.asarray(stream_ids, dtype=np.int32))
+        xp = np.ascontiguousarray(np.asarray(x_ptrs, dtype=np.uint64))
+        yp = np.ascontiguousarray(np.asarray(y_ptrs, dtype=np.uint64))
+        ln = np.ascontiguousarray(np.asarray(lengths, dtype=np.int64))
+        ta = np.ascontiguousarray(np.asarray(t_arrival, dtype=np.float64))
+        lat = np.empty(m, dtype=np.float64)
+        _check(self._lib.sos_server_replay(self._h, m, sid.ctypes.data, xp.ctypes.data, yp.ctypes.data,
+                                           ln.ctypes.data, ta.ctypes.data, lat.ctypes.data), "sos_server_replay")
+        return lat

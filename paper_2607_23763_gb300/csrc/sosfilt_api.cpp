@@ -124,6 +124,7 @@ struct CasPass {
     // N = kBatchN only: device copies for the multi-signal kernel
     sosk::SecCoef *d_sec = nullptr;  // [kp] section tables
     float *d_H = nullptr;            // [2 kp][N] output basis
+    float *d_Mm = nullptr;           // [N][packed] one-sample transition powers M1^(m+1), m < N
 };
 
 struct CasTables {
@@ -420,11 +421,20 @@ sos_status build_cascade(sos_filter *f, int N, CasTables &ct) {
             return SOS_ECUDA;
         if (N == sosk::kBatchN) {
             const NTables &nt = f->tables[table_index(N)];
+            const int nf = packed_floats(kp);
+            std::vector<float> mm(static_cast<size_t>(N) * nf, 0.f);
+            DMat P = ps.M1;
+            for (int m = 0; m < N; ++m) {
+                pack_into(P, kp, &mm[static_cast<size_t>(m) * nf]);
+                P = dmul(P, ps.M1);
+            }
             if (cudaMalloc(&ps.d_sec, sizeof(sosk::SecCoef) * kp) != cudaSuccess ||
-                cudaMalloc(&ps.d_H, sizeof(float) * ps.H.size()) != cudaSuccess)
+                cudaMalloc(&ps.d_H, sizeof(float) * ps.H.size()) != cudaSuccess ||
+                cudaMalloc(&ps.d_Mm, sizeof(float) * mm.size()) != cudaSuccess)
                 return SOS_ENOMEM;
             if (cudaMemcpy(ps.d_sec, &nt.sec[k0], sizeof(sosk::SecCoef) * kp, cudaMemcpyHostToDevice) != cudaSuccess ||
-                cudaMemcpy(ps.d_H, ps.H.data(), sizeof(float) * ps.H.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+                cudaMemcpy(ps.d_H, ps.H.data(), sizeof(float) * ps.H.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemcpy(ps.d_Mm, mm.data(), sizeof(float) * mm.size(), cudaMemcpyHostToDevice) != cudaSuccess)
                 return SOS_ECUDA;
         }
         ct.passes.push_back(std::move(ps));
@@ -919,20 +929,20 @@ sos_status run_impl(sos_filter *f, const float *x, float *y, int64_t n, const fl
 constexpr int kBatchSlots = 4;     // batches whose scratch may be in use on the device at once
 constexpr int kBatchClasses = 16;  // (K, normalized) classes: K = 1..8, b0-normalized or not
 
-// Scratch of one batch in flight: signal descriptors, tile -> signal map, tail transitions, lookback
-// descriptors and ticket counters of its class launches; pinned host staging for the uploads.
+// Scratch of one batch in flight: signal descriptors and the tile -> signal map (one upload from
+// pinned staging), lookback descriptors and ticket counters of its class launches.
 struct BatchSlot {
-    sosk::BatchSig *d_sigs = nullptr, *h_sigs = nullptr;
-    size_t sigs_cap = 0;
-    int *d_tile_sig = nullptr, *h_tile_sig = nullptr;
-    size_t tiles_cap = 0;
-    float *d_atail = nullptr, *h_atail = nullptr;
-    size_t atail_cap = 0;
+    unsigned char *d_up = nullptr, *h_up = nullptr;  // [descriptors][tile -> signal map]
+    size_t up_cap = 0;
     unsigned long long *d_desc = nullptr;
     size_t desc_cap = 0;
     unsigned long long *d_ticket = nullptr;  // [kBatchClasses]
     cudaEvent_t done = nullptr;
     bool pending = false;
+    // class launches of this slot's batch run on their own streams, so that batches issued on
+    // different caller streams overlap on the device
+    cudaStream_t side[kBatchClasses] = {};
+    cudaEvent_t fork = nullptr, join[kBatchClasses] = {};
 };
 
 struct BatchCtx {
@@ -940,8 +950,6 @@ struct BatchCtx {
     std::mutex mu;
     BatchSlot slot[kBatchSlots];
     int next = 0;
-    cudaStream_t side[kBatchClasses] = {};
-    cudaEvent_t fork = nullptr, join[kBatchClasses] = {};
     int *d_status = nullptr;
     unsigned epoch = 0;
 };
@@ -955,15 +963,17 @@ BatchCtx *batch_ctx(int device) {
         BatchCtx *c = new (std::nothrow) BatchCtx();
         if (!c) return nullptr;
         c->device = device;
-        bool ok = cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) == cudaSuccess &&
-                  cudaMalloc(&c->d_status, sizeof(int)) == cudaSuccess &&
+        bool ok = cudaMalloc(&c->d_status, sizeof(int)) == cudaSuccess &&
                   cudaMemset(c->d_status, 0, sizeof(int)) == cudaSuccess;
-        for (int i = 0; ok && i < kBatchClasses; ++i)
-            ok = cudaStreamCreateWithFlags(&c->side[i], cudaStreamNonBlocking) == cudaSuccess &&
-                 cudaEventCreateWithFlags(&c->join[i], cudaEventDisableTiming) == cudaSuccess;
-        for (int i = 0; ok && i < kBatchSlots; ++i)
-            ok = cudaEventCreateWithFlags(&c->slot[i].done, cudaEventDisableTiming) == cudaSuccess &&
-                 cudaMalloc(&c->slot[i].d_ticket, sizeof(unsigned long long) * kBatchClasses) == cudaSuccess;
+        for (int i = 0; ok && i < kBatchSlots; ++i) {
+            BatchSlot &sl = c->slot[i];
+            ok = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&sl.fork, cudaEventDisableTiming) == cudaSuccess &&
+                 cudaMalloc(&sl.d_ticket, sizeof(unsigned long long) * kBatchClasses) == cudaSuccess;
+            for (int k = 0; ok && k < kBatchClasses; ++k)
+                ok = cudaStreamCreateWithFlags(&sl.side[k], cudaStreamNonBlocking) == cudaSuccess &&
+                     cudaEventCreateWithFlags(&sl.join[k], cudaEventDisableTiming) == cudaSuccess;
+        }
         if (!ok) {
             cudaGetLastError();
             return nullptr;  // leaked on failure; the device is unusable anyway
@@ -971,25 +981,6 @@ BatchCtx *batch_ctx(int device) {
         ctx[device] = c;
     }
     return ctx[device];
-}
-
-// Grow a device/pinned-host pair to hold `want` elements.
-template <class T>
-bool grow_pair(T *&d, T *&h, size_t &cap, size_t want) {
-    if (want <= cap) return true;
-    size_t n = cap ? cap : 256;
-    while (n < want) n *= 2;
-    if (d) cudaFree(d);
-    if (h) cudaFreeHost(h);
-    d = nullptr;
-    h = nullptr;
-    cap = 0;
-    if (cudaMalloc(&d, n * sizeof(T)) != cudaSuccess || cudaMallocHost(&h, n * sizeof(T)) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    cap = n;
-    return true;
 }
 
 template <int K>
@@ -1036,12 +1027,11 @@ sos_status run_batch_impl(int n_signals, sos_filter *const *filters, const float
     constexpr long long W = sosk::kBatchW;
     // classes and sizes
     std::vector<int> cls(n_signals, -1);
-    long long cls_sigs[kBatchClasses] = {0}, cls_tiles[kBatchClasses] = {0}, cls_atail[kBatchClasses] = {0};
+    long long cls_sigs[kBatchClasses] = {0}, cls_tiles[kBatchClasses] = {0};
     for (int i = 0; i < n_signals; ++i) {
         sos_filter *f = filters[i];
         if (n[i] == 0) {
             if (zf && zf[i]) {
-                std::lock_guard<std::mutex> fl(f->mu);
                 const size_t b = sizeof(float) * 2 * f->K;
                 cudaError_t e = (zi && zi[i]) ? cudaMemcpyAsync(zf[i], zi[i], b, cudaMemcpyDeviceToDevice, s)
                                               : cudaMemsetAsync(zf[i], 0, b, s);
@@ -1060,15 +1050,14 @@ sos_status run_batch_impl(int n_signals, sos_filter *const *filters, const float
         cls_sigs[c] += 1;
         const long long G = (n[i] + C - 1) / C;
         cls_tiles[c] += (G + W - 1) / W;
-        if (zf && zf[i]) cls_atail[c] += packed_floats(f->K);
     }
-    long long sig_off[kBatchClasses + 1] = {0}, tile_off[kBatchClasses + 1] = {0}, atail_off[kBatchClasses + 1] = {0},
-              desc_off[kBatchClasses + 1] = {0};
+    long long sig_off[kBatchClasses + 1] = {0}, tile_off[kBatchClasses + 1] = {0}, desc_off[kBatchClasses + 1] = {0};
+    int n_cls = 0;
     for (int c = 0; c < kBatchClasses; ++c) {
         sig_off[c + 1] = sig_off[c] + cls_sigs[c];
         tile_off[c + 1] = tile_off[c] + cls_tiles[c];
-        atail_off[c + 1] = atail_off[c] + cls_atail[c];
         desc_off[c + 1] = desc_off[c] + cls_tiles[c] * 2 * (c / 2 + 1);
+        if (cls_sigs[c]) ++n_cls;
     }
     if (sig_off[kBatchClasses] == 0) return SOS_OK;
 
@@ -1077,10 +1066,21 @@ sos_status run_batch_impl(int n_signals, sos_filter *const *filters, const float
     ctx->next = (ctx->next + 1) % kBatchSlots;
     if (sl.pending && cudaEventSynchronize(sl.done) != cudaSuccess) return SOS_ECUDA;
     sl.pending = false;
-    if (!grow_pair(sl.d_sigs, sl.h_sigs, sl.sigs_cap, sig_off[kBatchClasses]) ||
-        !grow_pair(sl.d_tile_sig, sl.h_tile_sig, sl.tiles_cap, tile_off[kBatchClasses]) ||
-        !grow_pair(sl.d_atail, sl.h_atail, sl.atail_cap, atail_off[kBatchClasses] + 1))
-        return SOS_ENOMEM;
+    const size_t sig_bytes = sizeof(sosk::BatchSig) * sig_off[kBatchClasses];
+    const size_t up_bytes = sig_bytes + sizeof(int) * tile_off[kBatchClasses];
+    if (up_bytes > sl.up_cap) {
+        size_t cap = sl.up_cap ? sl.up_cap : 1 << 16;
+        while (cap < up_bytes) cap *= 2;
+        if (sl.d_up) cudaFree(sl.d_up);
+        if (sl.h_up) cudaFreeHost(sl.h_up);
+        sl.d_up = sl.h_up = nullptr;
+        sl.up_cap = 0;
+        if (cudaMalloc(&sl.d_up, cap) != cudaSuccess || cudaMallocHost(&sl.h_up, cap) != cudaSuccess) {
+            cudaGetLastError();
+            return SOS_ENOMEM;
+        }
+        sl.up_cap = cap;
+    }
     if (static_cast<size_t>(desc_off[kBatchClasses]) > sl.desc_cap) {
         if (sl.d_desc) {
             cudaFree(sl.d_desc);
@@ -1095,23 +1095,26 @@ sos_status run_batch_impl(int n_signals, sos_filter *const *filters, const float
         if (cudaMemsetAsync(sl.d_desc, 0, want * sizeof(unsigned long long), s) != cudaSuccess) return SOS_ECUDA;
         sl.desc_cap = want;
     }
+    sosk::BatchSig *h_sigs = reinterpret_cast<sosk::BatchSig *>(sl.h_up);
+    int *h_tile_sig = reinterpret_cast<int *>(sl.h_up + sig_bytes);
+    const sosk::BatchSig *d_sigs = reinterpret_cast<const sosk::BatchSig *>(sl.d_up);
+    const int *d_tile_sig = reinterpret_cast<const int *>(sl.d_up + sig_bytes);
 
     // descriptors and the tile -> signal map, class by class
-    long long fill_sig[kBatchClasses], fill_tile[kBatchClasses], fill_atail[kBatchClasses];
+    long long fill_sig[kBatchClasses], fill_tile[kBatchClasses];
     for (int c = 0; c < kBatchClasses; ++c) {
         fill_sig[c] = sig_off[c];
         fill_tile[c] = tile_off[c];
-        fill_atail[c] = atail_off[c];
     }
     for (int i = 0; i < n_signals; ++i) {
         const int c = cls[i];
         if (c < 0) continue;
         sos_filter *f = filters[i];
-        CasPass &ps = f->cas[0].passes[0];  // N = 32: the batch kernel's tables
+        const CasPass &ps = f->cas[0].passes[0];  // N = 32: the batch kernel's tables (read only)
         const long long G = (n[i] + C - 1) / C;
         const long long nt = (G + W - 1) / W;
         const long long si = fill_sig[c]++;
-        sosk::BatchSig &b = sl.h_sigs[si];
+        sosk::BatchSig &b = h_sigs[si];
         b.x = x[i];
         b.y = y[i];
         b.n = n[i];
@@ -1122,42 +1125,27 @@ sos_status run_batch_impl(int n_signals, sos_filter *const *filters, const float
         b.sec = ps.d_sec;
         b.H = ps.d_H;
         b.tab = ps.d_tab;
-        b.A_tail = nullptr;
+        b.Mm = ps.d_Mm;
         b.gain = static_cast<float>(f->gain);
         b.aligned = (reinterpret_cast<uintptr_t>(x[i]) % 16 == 0 && reinterpret_cast<uintptr_t>(y[i]) % 16 == 0) ? 1 : 0;
-        if (b.zf) {
-            const long long tp = n[i] - 1 - (G - 1) * C;  // last real sample inside the last group
-            std::lock_guard<std::mutex> fl(f->mu);
-            if (ps.tail_p != tp) {
-                ps.A_tail.assign(packed_floats(f->K), 0.f);
-                pack_into(dpow(ps.M1, tp + 1), f->K, ps.A_tail.data());
-                ps.tail_p = tp;
-            }
-            std::memcpy(sl.h_atail + fill_atail[c], ps.A_tail.data(), sizeof(float) * packed_floats(f->K));
-            b.A_tail = sl.d_atail + fill_atail[c];
-            fill_atail[c] += packed_floats(f->K);
-        }
-        const long long local = si - sig_off[c];
-        for (long long t = 0; t < nt; ++t) sl.h_tile_sig[fill_tile[c]++] = static_cast<int>(local);
+        const int local = static_cast<int>(si - sig_off[c]);
+        for (long long t = 0; t < nt; ++t) h_tile_sig[fill_tile[c]++] = local;
     }
-    auto up = [&](void *d, const void *h, size_t bytes) {
-        return bytes == 0 || cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, s) == cudaSuccess;
-    };
-    if (!up(sl.d_sigs, sl.h_sigs, sizeof(sosk::BatchSig) * sig_off[kBatchClasses]) ||
-        !up(sl.d_tile_sig, sl.h_tile_sig, sizeof(int) * tile_off[kBatchClasses]) ||
-        !up(sl.d_atail, sl.h_atail, sizeof(float) * atail_off[kBatchClasses]) ||
+    if (cudaMemcpyAsync(sl.d_up, sl.h_up, up_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemsetAsync(sl.d_ticket, 0, sizeof(unsigned long long) * kBatchClasses, s) != cudaSuccess)
         return SOS_ECUDA;
 
-    // one persistent launch per class on its own stream, forked from and joined into s
-    if (cudaEventRecord(ctx->fork, s) != cudaSuccess) return SOS_ECUDA;
+    // one persistent launch per class, each on its own stream forked from and joined into s (a
+    // single class runs on s itself)
+    const bool fork = n_cls > 1;
+    if (fork && cudaEventRecord(sl.fork, s) != cudaSuccess) return SOS_ECUDA;
     const long long budget = kDefaultSpinBudget;
     for (int c = 0; c < kBatchClasses; ++c) {
         if (cls_sigs[c] == 0) continue;
         const int K = c / 2 + 1;
         const bool norm = (c & 1) != 0;
-        cudaStream_t cs = ctx->side[c];
-        if (cudaStreamWaitEvent(cs, ctx->fork, 0) != cudaSuccess) return SOS_ECUDA;
+        cudaStream_t cs = fork ? sl.side[c] : s;
+        if (fork && cudaStreamWaitEvent(cs, sl.fork, 0) != cudaSuccess) return SOS_ECUDA;
         ctx->epoch = (ctx->epoch + 1) & 0x3fffffffu;
         if (ctx->epoch == 0) {  // wrapped: clear stale tags of every slot's descriptors
             for (auto &o : ctx->slot)
@@ -1168,17 +1156,16 @@ sos_status run_batch_impl(int n_signals, sos_filter *const *filters, const float
         if (bps <= 0) return SOS_ECUDA;
         long long grid = static_cast<long long>(bps) * sm_count(device);
         if (grid > cls_tiles[c]) grid = cls_tiles[c];
-        sos_status st = launch_batch_any(K, norm, sl.d_sigs + sig_off[c], sl.d_tile_sig + tile_off[c], cls_tiles[c],
+        sos_status st = launch_batch_any(K, norm, d_sigs + sig_off[c], d_tile_sig + tile_off[c], cls_tiles[c],
                                          sl.d_desc + desc_off[c], sl.d_ticket + c, ctx->epoch, ctx->d_status, budget,
                                          grid, cs);
         if (st != SOS_OK) return st;
-        if (cudaEventRecord(ctx->join[c], cs) != cudaSuccess || cudaStreamWaitEvent(s, ctx->join[c], 0) != cudaSuccess)
+        if (fork && (cudaEventRecord(sl.join[c], cs) != cudaSuccess ||
+                     cudaStreamWaitEvent(s, sl.join[c], 0) != cudaSuccess))
             return SOS_ECUDA;
     }
     if (cudaEventRecord(sl.done, s) != cudaSuccess) return SOS_ECUDA;
     sl.pending = true;
-    for (int i = 0; i < n_signals; ++i)
-        if (filters[i]) filters[i]->last_stream = s;
     return SOS_OK;
 }
 
@@ -1367,7 +1354,9 @@ sos_status sos_filter_create(int n_sections, const double *sos, const float *zi,
 sos_status sos_filter_destroy(sos_filter *f) {
     if (!f) return SOS_OK;
     cudaSetDevice(f->device);
-    if (f->last_stream) cudaStreamSynchronize(f->last_stream);
+    // the device, not the last stream: that stream may be gone, and batched runs may still read this
+    // filter's tables on library streams
+    cudaDeviceSynchronize();
     for (auto &t : f->tables) {
         if (t.d_lane_pow) cudaFree(t.d_lane_pow);
         if (t.d_grp_pow) cudaFree(t.d_grp_pow);
@@ -1378,6 +1367,7 @@ sos_status sos_filter_destroy(sos_filter *f) {
             if (ps.d_tab) cudaFree(ps.d_tab);
             if (ps.d_sec) cudaFree(ps.d_sec);
             if (ps.d_H) cudaFree(ps.d_H);
+            if (ps.d_Mm) cudaFree(ps.d_Mm);
         }
     for (auto &ps : f->ph)
         if (ps.d_tab) cudaFree(ps.d_tab);

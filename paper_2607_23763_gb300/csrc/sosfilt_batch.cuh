@@ -280,10 +280,10 @@ __global__ void __maxnreg__(96) sos_batch_kernel(const __grid_constant__ BatchPa
         if (g == G - 1 && sg->zf) {
             const long long p_last = sg->n - 1 - (G - 1) * C;
             if (lane == static_cast<int>(p_last / N)) {
-                float Z[S], zt[S];
-#pragma unroll
-                for (int i = 0; i < S; ++i) Z[i] = zb[i];
-                packed_mv_gr<K>(sg->A_tail, Z, zt);
+                // the lane's incoming state from Z is dz = (M_N)^lane Z; carried over the lane's
+                // samples up to the last one: M1^(m_last + 1) dz
+                float zt[S];
+                packed_mv_gr<K>(sg->Mm + static_cast<int>(p_last % N) * Dm::NF, dz, zt);
                 const float *zs = zs_tail + (jt & 1) * S;
                 float *zf = sg->zf;
                 const SecCoef *sec = sg->sec;

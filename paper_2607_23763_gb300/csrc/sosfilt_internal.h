@@ -185,7 +185,7 @@ struct BatchSig {
     const SecCoef *sec;    // device [K] section tables for N = kBatchN
     const float *H;        // device [2K][kBatchN] zero-input output basis
     const float *tab;      // device table block (CasDims<K>::TAB_GLOBAL floats)
-    const float *A_tail;   // device packed transition over the last group's real samples, or nullptr
+    const float *Mm;       // device [kBatchN][2K(K+1)] packed one-sample transition powers M1^(m+1)
     float gain;            // input multiplier (product of the b0 when normalized)
     int aligned;           // x and y 16-byte aligned
 };

@@ -31,6 +31,8 @@ def test_header_declares_the_abi():
         "sos_filter_create", "sos_filter_destroy", "sos_filter_run", "sos_filter_run_batch",
         "sos_filter_stream_push", "sos_filter_stream_state", "sos_filter_sync_status", "sos_filter_trace",
         "sos_filter_run_host", "sos_filter_run_noalloc", "sos_filter_run_batch_ex", "sos_batch_sync_status",
+        "sos_server_create", "sos_server_destroy", "sos_server_add_stream", "sos_server_submit", "sos_server_poll",
+        "sos_server_drain", "sos_server_stream_state", "sos_server_get_stats", "sos_server_replay",
         "sos_status_string"])
 
 
