@@ -383,13 +383,61 @@ def bench_serving(args):
     print(json.dumps(line), flush=True)
 
 
+def bench_precision(args):
+    """Precision stress: order-16 resonator bank at pole radius 0.999, 2^30 samples (N(0,1) plus a unit
+    sinusoid at 0.32 pi, seed 4): GS/s and the error against the float64 oracle over every sample."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import workloads
+    from workloads import designs
+    from paper_2607_23763_gb300 import SosFilter
+
+    torch.cuda.set_device(0)
+    sos = designs.resonator_bank()
+    n = 1 << 30
+    x_host = workloads.normal_f32(4, n, sin_amp=1.0, sin_omega=0.32 * np.pi)
+    f = SosFilter(sos)
+    x = torch.from_numpy(x_host).cuda()
+    y = torch.empty_like(x)
+    for _ in range(args.warmup):
+        f.run(x, y)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        f.run(x, y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    assert f.sync_status() == 0
+    ms = e0.elapsed_time(e1) / args.steps
+    del x
+    z = np.zeros((sos.shape[0], 2))
+    num = den = 0.0
+    for a in range(0, n, 1 << 24):
+        ref, z = oracle.sosfilt(sos, x_host[a:a + (1 << 24)], zi=z, return_state=True)
+        got = y[a:a + (1 << 24)].cpu().numpy().astype(np.float64)
+        num = max(num, float(np.abs(got - ref).max()))
+        den = max(den, float(np.abs(ref).max()))
+    line = {"metric": "GS/s", "value": n / ms / 1e6, "unit": "GS/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "precision stress: order-16 resonator bank, 8 sections with poles at radius "
+                                   "0.999, angles evenly spaced in [0.30 pi, 0.34 pi]; 2^30 float32 samples of "
+                                   "N(0,1) plus sin(0.32 pi n), seed 4", "carry": "float32"},
+            "max_rel_error": num / den, "bound": 2e-3}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="plain", choices=["plain", "batched", "serving"],
+    ap.add_argument("--workload", default="plain", choices=["plain", "batched", "serving", "precision"],
                     help="plain = the order-16 single-signal workload (default); batched / serving mixes")
     ap.add_argument("--streams", type=int, default=10000, help="serving: streams")
     ap.add_argument("--chunks-per-stream", type=int, default=10, help="serving: closed-loop chunks per stream")
@@ -418,6 +466,8 @@ def main():
         bench_batched(args)
     elif args.workload == "serving":
         bench_serving(args)
+    elif args.workload == "precision":
+        bench_precision(args)
     else:
         bench_ours(args)
 

@@ -321,6 +321,25 @@ sos_status sos_server_get_stats(sos_server *s, sos_server_stats *out);
 sos_status sos_server_replay(sos_server *s, int64_t n_req, const int32_t *stream_ids, const float *const *x_dev,
                              float *const *y_dev, const int64_t *n, const double *t_arrival, double *latency);
 
+/*
+ * Autotuner: on the current device, time each candidate launch configuration
+ * -- divide-and-conquer cyclic reduction with the cascade carry at N = 32 (8
+ * groups per tile) or N = 64 (4 groups per tile), and PH factorization at
+ * N = 32 (7 groups per tile); L = 32 threads per group throughout -- for 1 to
+ * 8 sections and lengths 2^16, 2^20, 2^24 and 2^28 (up to 2^max_log2n,
+ * 0 = 28), and keep the fastest per (section count, length).  Afterwards every
+ * run of a filter created with default tuning (all fields 0) uses the choice
+ * for its section count and the nearest length.  Synchronous; allocates and
+ * frees 2^(max_log2n + 3) bytes of device memory; about a second.
+ *   report  NULL, or host float[8][4][3] receiving the measured GS/s
+ *           (sections, length 2^16..2^28, candidate CR32/CR64/PH)
+ */
+sos_status sos_autotune(int max_log2n, float *report);
+
+/* The autotuned choice for K sections and n samples on the current device:
+ * solver (SOS_SOLVER_CR / SOS_SOLVER_PH) and N; both 0 if no autotuning ran. */
+sos_status sos_autotune_choice(int n_sections, int64_t n, int *solver, int *N);
+
 /* Human-readable name of a status code (static storage). */
 const char *sos_status_string(sos_status s);
 

@@ -27,7 +27,7 @@ EXPORTED = (
     "sos_filter_run_host", "sos_filter_run_noalloc", "sos_filter_run_batch_ex", "sos_batch_sync_status",
     "sos_server_create", "sos_server_destroy", "sos_server_add_stream", "sos_server_submit", "sos_server_poll",
     "sos_server_drain", "sos_server_stream_state", "sos_server_get_stats", "sos_server_replay",
-    "sos_status_string",
+    "sos_autotune", "sos_autotune_choice", "sos_status_string",
 )
 
 
@@ -78,6 +78,8 @@ def load_library(path: str | None = None):
         lib.sos_server_stream_state.argtypes = [vp, c_int, vp]
         lib.sos_server_get_stats.argtypes = [vp, vp]
         lib.sos_server_replay.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
+        lib.sos_autotune.argtypes = [c_int, vp]
+        lib.sos_autotune_choice.argtypes = [c_int, i64, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]
         lib.sos_filter_stream_push.argtypes = [vp, vp, vp, i64, vp]
         lib.sos_filter_stream_state.argtypes = [vp, vp, vp, c_int]
         lib.sos_filter_sync_status.argtypes = [vp]
@@ -366,3 +368,19 @@ class SosServer:
         _check(self._lib.sos_server_replay(self._h, m, sid.ctypes.data, xp.ctypes.data, yp.ctypes.data,
                                            ln.ctypes.data, ta.ctypes.data, lat.ctypes.data), "sos_server_replay")
         return lat
+
+
+def autotune(max_log2n: int = 0) -> np.ndarray:
+    """Time the candidate launch configurations on the current device and keep the fastest per
+    (section count, length); returns the measured GS/s as [8 sections][4 lengths][CR32, CR64, PH]."""
+    rep = np.zeros((8, 4, 3), dtype=np.float32)
+    _check(load_library().sos_autotune(int(max_log2n), rep.ctypes.data), "sos_autotune")
+    return rep
+
+
+def autotune_choice(n_sections: int, n: int):
+    """(solver, N) the autotuner picked for this section count and length; (0, 0) if none."""
+    s, N = ctypes.c_int(), ctypes.c_int()
+    _check(load_library().sos_autotune_choice(int(n_sections), int(n), ctypes.byref(s), ctypes.byref(N)),
+           "sos_autotune_choice")
+    return s.value, N.value

@@ -704,10 +704,10 @@ sos_status launch_cascade_any(int K, sos_filter *f, CasPass &ps, const sosk::Sec
 
 // One carry per tile for the whole cascade (sosfilt_cascade.cuh), persistent grid.
 sos_status run_cascade(sos_filter *f, const float *x, float *y, int64_t n, const float *zi, float *zf,
-                       cudaStream_t s) {
+                       cudaStream_t s, int N_choice = 0) {
     // default N from GB300 measurements on 2^28 samples (cascade carry): N = 64 for one section
     // (HBM-bound, fewer tiles per sample), N = 32 otherwise (more warps to hide the pass's latency)
-    int N = f->tuning.N ? f->tuning.N : (f->K == 1 ? 64 : 32);
+    int N = f->tuning.N ? f->tuning.N : N_choice ? N_choice : (f->K == 1 ? 64 : 32);
     if (N != 32 && N != 64) return SOS_EINVAL;
     const int ci = (N == 32) ? 0 : 1;
     const int ti = table_index(N);
@@ -907,6 +907,39 @@ sos_status launch_cascade_any_scratch(int K, sos_filter *f, CasPass &ps, const s
     }
 }
 
+// ---- autotuned launch choice (sos_autotune): per device, section count (1..8) and length bucket
+constexpr int kTuneBuckets = 4;                       // n around 2^16, 2^20, 2^24, 2^28
+constexpr int kTuneLog2[kTuneBuckets] = {16, 20, 24, 28};
+constexpr int kTuneCand = 3;                          // candidates: CR N = 32, CR N = 64, PH
+struct TuneTable {
+    bool valid = false;
+    unsigned char best[8][kTuneBuckets] = {};         // candidate index
+    float gss[8][kTuneBuckets][kTuneCand] = {};       // measured GS/s
+};
+std::mutex g_tune_mu;
+TuneTable g_tune[64];
+
+void candidate(int c, int *solver, int *N) {
+    *solver = c == 2 ? SOS_SOLVER_PH : SOS_SOLVER_CR;
+    *N = c == 1 ? 64 : 32;
+}
+
+int tune_bucket(int64_t n) {
+    int b = 0;
+    for (int i = 1; i < kTuneBuckets; ++i)
+        if (n >= (1LL << ((kTuneLog2[i - 1] + kTuneLog2[i]) / 2))) b = i;
+    return b;
+}
+
+bool tuned_choice(int device, int K, int64_t n, int *solver, int *N) {
+    if (device < 0 || device >= 64) return false;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (!g_tune[device].valid) return false;
+    const int k = (K > sosk::kMaxPass ? sosk::kMaxPass : K) - 1;
+    candidate(g_tune[device].best[k][tune_bucket(n)], solver, N);
+    return true;
+}
+
 sos_status run_impl(sos_filter *f, const float *x, float *y, int64_t n, const float *zi, float *zf, cudaStream_t s) {
     if (n < 0 || (n > 0 && (!x || !y))) return SOS_EINVAL;
     if (x != y && n > 0 && ranges_overlap(x, y, n)) return SOS_EINVAL;
@@ -920,8 +953,17 @@ sos_status run_impl(sos_filter *f, const float *x, float *y, int64_t n, const fl
         }
         return SOS_OK;
     }
+    const sos_tuning &t = f->tuning;
+    if (!t.N && !t.carry && !t.solver && !t.lookback_width) {
+        // all defaults: the autotuned choice for this section count and length, if there is one
+        int solver = 0, N = 0;
+        if (tuned_choice(f->device, f->K, n, &solver, &N)) {
+            if (solver == SOS_SOLVER_PH) return run_ph(f, x, y, n, zi, zf, s);
+            return run_cascade(f, x, y, n, zi, zf, s, N);
+        }
+    }
     if (solver_of(f) == SOS_SOLVER_PH) return run_ph(f, x, y, n, zi, zf, s);
-    if (f->tuning.carry == SOS_CARRY_SECTION) return run_sections(f, x, y, n, zi, zf, s);
+    if (t.carry == SOS_CARRY_SECTION) return run_sections(f, x, y, n, zi, zf, s);
     return run_cascade(f, x, y, n, zi, zf, s);
 }
 
@@ -1025,6 +1067,8 @@ sos_status run_batch_impl(int n_signals, sos_filter *const *filters, const float
 
     constexpr long long C = 32LL * sosk::kBatchN;
     constexpr long long W = sosk::kBatchW;
+    // the batch kernel reads the N = 32 cascade tables, whose tile transition is A_C^W
+    if (sosk::cascade_warps(sosk::kBatchN) != W) return SOS_EINVAL;
     // classes and sizes
     std::vector<int> cls(n_signals, -1);
     long long cls_sigs[kBatchClasses] = {0}, cls_tiles[kBatchClasses] = {0};
@@ -1470,6 +1514,103 @@ sos_status sos_filter_run_batch_ex(int n_signals, sos_filter *const *filters, co
 sos_status sos_batch_sync_status(int device) {
     if (cudaSetDevice(device) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return SOS_ECUDA;
     return batch_status(device);
+}
+
+sos_status sos_autotune(int max_log2n, float *report) {
+    if (max_log2n != 0 && (max_log2n < 16 || max_log2n > 28)) return SOS_EINVAL;
+    const int top = max_log2n ? max_log2n : 28;
+    int device = 0;
+    if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= 64) return SOS_ECUDA;
+    const int64_t n_max = 1LL << top;
+    float *x = nullptr, *y = nullptr;
+    if (cudaMalloc(&x, sizeof(float) * n_max) != cudaSuccess || cudaMalloc(&y, sizeof(float) * n_max) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(x);
+        return SOS_ENOMEM;
+    }
+    cudaMemset(x, 0, sizeof(float) * n_max);
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaFree(x);
+        cudaFree(y);
+        return SOS_ECUDA;
+    }
+    TuneTable tt;
+    sos_status rc = SOS_OK;
+    for (int K = 1; K <= sosk::kMaxPass && rc == SOS_OK; ++K) {
+        // a stable cascade of K sections (the timing does not depend on the coefficients' values)
+        std::vector<double> sos(5 * K);
+        for (int k = 0; k < K; ++k) {
+            const double r = 0.9 + 0.01 * k, th = 0.2 + 0.05 * k;
+            const double c[5] = {0.05, 0.1, 0.05, -2.0 * r * std::cos(th), r * r};
+            std::memcpy(&sos[5 * k], c, sizeof c);
+        }
+        for (int c = 0; c < kTuneCand && rc == SOS_OK; ++c) {
+            sos_tuning t{};
+            int solver = 0, N = 0;
+            candidate(c, &solver, &N);
+            t.solver = solver;
+            if (solver == SOS_SOLVER_CR) {
+                t.N = N;
+                t.carry = SOS_CARRY_CASCADE;
+            }
+            sos_filter *f = nullptr;
+            rc = sos_filter_create(K, sos.data(), nullptr, &t, &f);
+            if (rc != SOS_OK) break;
+            for (int b = 0; b < kTuneBuckets && rc == SOS_OK; ++b) {
+                if (kTuneLog2[b] > top) {
+                    tt.gss[K - 1][b][c] = tt.gss[K - 1][b > 0 ? b - 1 : 0][c];
+                    continue;
+                }
+                const int64_t n = 1LL << kTuneLog2[b];
+                const int reps = n >= (1LL << 26) ? 3 : static_cast<int>((1LL << 26) / n);
+                {
+                    std::lock_guard<std::mutex> lk(f->mu);
+                    for (int w = 0; w < 2 && rc == SOS_OK; ++w) rc = run_impl(f, x, y, n, nullptr, nullptr, st);
+                    cudaEventRecord(e0, st);
+                    for (int r = 0; r < reps && rc == SOS_OK; ++r) rc = run_impl(f, x, y, n, nullptr, nullptr, st);
+                    cudaEventRecord(e1, st);
+                }
+                float ms = 0.f;
+                if (rc == SOS_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) !=
+                                                                                     cudaSuccess))
+                    rc = SOS_ECUDA;
+                if (rc == SOS_OK) tt.gss[K - 1][b][c] = ms > 0.f ? static_cast<float>(n) * reps / ms / 1e6f : 0.f;
+            }
+            sos_filter_destroy(f);
+        }
+        for (int b = 0; b < kTuneBuckets; ++b) {
+            int best = 0;
+            for (int c = 1; c < kTuneCand; ++c)
+                if (tt.gss[K - 1][b][c] > tt.gss[K - 1][b][best]) best = c;
+            tt.best[K - 1][b] = static_cast<unsigned char>(best);
+        }
+    }
+    cudaStreamSynchronize(st);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(st);
+    cudaFree(x);
+    cudaFree(y);
+    if (rc != SOS_OK) return rc;
+    tt.valid = true;
+    if (report) std::memcpy(report, tt.gss, sizeof tt.gss);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[device] = tt;
+    return SOS_OK;
+}
+
+sos_status sos_autotune_choice(int n_sections, int64_t n, int *solver, int *N) {
+    if (n_sections < 1 || !solver || !N) return SOS_EINVAL;
+    int device = 0;
+    if (cudaGetDevice(&device) != cudaSuccess) return SOS_ECUDA;
+    if (!tuned_choice(device, n_sections, n, solver, N)) {
+        *solver = 0;
+        *N = 0;
+    }
+    return SOS_OK;
 }
 
 sos_status sos_filter_stream_push(sos_filter *f, const float *x_dev, float *y_dev, int64_t n, void *stream) {

@@ -172,7 +172,7 @@ int ph_blocks_per_sm(int K, bool norm);
 // ---- multi-signal persistent kernel (sosfilt_batch.cuh): the cascade-carry cyclic-reduction
 // kernel over a global queue of (signal, tile) work items
 constexpr int kBatchN = 32;  // samples per lane
-constexpr int kBatchW = 8;   // groups (compute warps) per tile
+constexpr int kBatchW = 8;   // groups (compute warps) per tile (the N = 32 tables of the cascade kernel: same W)
 
 // One signal of a batch (device array, built by the host for each batched run).
 struct BatchSig {

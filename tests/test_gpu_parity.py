@@ -250,3 +250,36 @@ def test_config2_full_size_sampled(dev):
     # a property at full size: the tail matches a one-shot oracle run on the last 2^20 samples
     assert np.all(np.isfinite(y[-(1 << 20):].cpu().numpy()))
     f.close()
+
+
+def _full_error_chunked(sos, x_host, y_dev, chunk=1 << 24):
+    """max|y - y_ref| / max|y_ref| over the whole signal: the oracle streams through it in chunks with
+    its state carried (bit-identical to one oracle call), the GPU output is read back chunk by chunk."""
+    K = sos.shape[0]
+    z = np.zeros((K, 2))
+    num = den = 0.0
+    for a in range(0, len(x_host), chunk):
+        ref, z = oracle.sosfilt(sos, x_host[a:a + chunk], zi=z, return_state=True)
+        got = y_dev[a:a + chunk].cpu().numpy().astype(np.float64)
+        num = max(num, float(np.abs(got - ref).max()))
+        den = max(den, float(np.abs(ref).max()))
+    return num / den
+
+
+def test_precision_resonator_bank_full_size(dev):
+    """Order-16 resonator bank (poles at radius 0.999, angles 0.30..0.34 pi), 2^30 samples of N(0,1)
+    plus a unit sinusoid at 0.32 pi, seed 4; float32 path with float32 carries against the float64
+    oracle over every sample.  Bound 2e-3 (pole radius above 0.99)."""
+    sos = designs.resonator_bank()
+    n = 1 << 30
+    x = workloads.normal_f32(4, n, sin_amp=1.0, sin_omega=0.32 * np.pi)
+    f = _filt(sos)
+    xd = torch.from_numpy(x).to(dev)
+    y = f.run(xd)
+    torch.cuda.synchronize()
+    assert f.sync_status() == 0
+    del xd
+    err = _full_error_chunked(sos, x, y)
+    print(f"resonator bank, 2^30 samples: rel err {err:.3e}")
+    assert err < 2e-3
+    f.close()
