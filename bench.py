@@ -291,6 +291,29 @@ def bench_batched(args):
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     assert batch_sync_status(0) == 0
+    # the same batch as a prepared plan captured into a CUDA graph, replayed
+    from paper_2607_23763_gb300 import BatchPlan
+    plan = BatchPlan(fs, xs, ys)
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        plan.launch(side)
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        plan.launch()
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        graph.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    graph_ms = e0.elapsed_time(e1) / args.steps
+    assert plan.status() == 0
+    plan.close()
     # the plain single-signal kernel's rate per order on 2^28 samples
     x = torch.from_numpy(workloads.normal_f32(1, 1 << 28)).cuda()
     y = torch.empty_like(x)
@@ -317,6 +340,7 @@ def bench_batched(args):
                                    "uniform over {2,4,8,16}, random stable sections, N(0,1) input, seeds 1000+i",
                        "samples": total, "l2": "inputs and outputs larger than L2"},
             "vs_plain_kernel": plain_ms / ms,
+            "cuda_graph": {"value": total / graph_ms / 1e6, "ms_per_step": graph_ms, "vs_plain_kernel": plain_ms / graph_ms},
             "plain_gss_by_order": {str(2 * k): v for k, v in rate.items()},
             "gpu_launches": 4 * args.steps, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)

@@ -191,6 +191,28 @@ sos_status sos_filter_run_batch_ex(int n_signals, sos_filter *const *filters, co
                                    float *const *y_dev, const int64_t *n, const float *const *zi_dev,
                                    float *const *zf_dev, void *stream);
 
+/*
+ * A prepared batch for repeated runs and CUDA graphs: the signal descriptors
+ * and lookback workspace of a fixed set of signals (arguments as
+ * sos_filter_run_batch_ex; every n > 0, at most 8 sections per filter) are
+ * uploaded once.  sos_batch_plan_launch enqueues the batch on `stream` with no
+ * host synchronization and no host-side work per signal (a reset of the
+ * plan's descriptors and tickets, then one persistent launch per class on the
+ * plan's own streams, forked from and joined back into `stream`), so it may be
+ * captured into a CUDA graph and the graph replayed.  Launches of one plan
+ * must not overlap on the device (they share its workspace).  The buffers and
+ * filters named at creation must outlive the plan.
+ */
+typedef struct sos_batch_plan sos_batch_plan;
+sos_status sos_batch_plan_create(int n_signals, sos_filter *const *filters, const float *const *x_dev,
+                                 float *const *y_dev, const int64_t *n, const float *const *zi_dev,
+                                 float *const *zf_dev, sos_batch_plan **out);
+sos_status sos_batch_plan_launch(sos_batch_plan *plan, void *stream);
+/* Synchronize the device and return the plan's sticky device status. */
+sos_status sos_batch_plan_status(sos_batch_plan *plan);
+/* Synchronizes the device, then releases the plan. */
+sos_status sos_batch_plan_destroy(sos_batch_plan *plan);
+
 /* Synchronize the device and return the sticky status of its batched runs
  * (SOS_ETIMEOUT after a lookback wait ran out of time). */
 sos_status sos_batch_sync_status(int device);

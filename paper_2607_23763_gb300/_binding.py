@@ -27,7 +27,8 @@ EXPORTED = (
     "sos_filter_run_host", "sos_filter_run_noalloc", "sos_filter_run_batch_ex", "sos_batch_sync_status",
     "sos_server_create", "sos_server_destroy", "sos_server_add_stream", "sos_server_submit", "sos_server_poll",
     "sos_server_drain", "sos_server_stream_state", "sos_server_get_stats", "sos_server_replay",
-    "sos_autotune", "sos_autotune_choice", "sos_status_string",
+    "sos_autotune", "sos_autotune_choice", "sos_batch_plan_create", "sos_batch_plan_launch",
+    "sos_batch_plan_status", "sos_batch_plan_destroy", "sos_status_string",
 )
 
 
@@ -79,6 +80,10 @@ def load_library(path: str | None = None):
         lib.sos_server_get_stats.argtypes = [vp, vp]
         lib.sos_server_replay.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
         lib.sos_autotune.argtypes = [c_int, vp]
+        lib.sos_batch_plan_create.argtypes = [c_int, vp, vp, vp, vp, vp, vp, ctypes.POINTER(vp)]
+        lib.sos_batch_plan_launch.argtypes = [vp, vp]
+        lib.sos_batch_plan_status.argtypes = [vp]
+        lib.sos_batch_plan_destroy.argtypes = [vp]
         lib.sos_autotune_choice.argtypes = [c_int, i64, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]
         lib.sos_filter_stream_push.argtypes = [vp, vp, vp, i64, vp]
         lib.sos_filter_stream_state.argtypes = [vp, vp, vp, c_int]
@@ -384,3 +389,47 @@ def autotune_choice(n_sections: int, n: int):
     _check(load_library().sos_autotune_choice(int(n_sections), int(n), ctypes.byref(s), ctypes.byref(N)),
            "sos_autotune_choice")
     return s.value, N.value
+
+
+class BatchPlan:
+    """A prepared batch (sos_batch_plan_*): launch() enqueues it with no host-side work, so it can be
+    captured into a CUDA graph (torch.cuda.graph) and replayed.  Keeps its tensors and filters alive."""
+
+    def __init__(self, filters, xs, ys=None, zis=None, zfs=None):
+        import torch
+        self._lib = load_library()
+        n = len(xs)
+        if ys is None:
+            ys = [torch.empty_like(x) for x in xs]
+        self.filters, self.xs, self.ys, self.zis, self.zfs = list(filters), list(xs), list(ys), zis, zfs
+        hf = (ctypes.c_void_p * n)(*[f.handle for f in filters])
+        hx = (ctypes.c_void_p * n)(*[_dptr(x, "x") for x in xs])
+        hy = (ctypes.c_void_p * n)(*[_dptr(y, "y") for y in ys])
+        hn = (ctypes.c_int64 * n)(*[x.numel() for x in xs])
+        def ptrs(ts, name):
+            return None if ts is None else (ctypes.c_void_p * n)(*[None if t is None else _dptr(t, name) for t in ts])
+        hzi, hzf = ptrs(zis, "zi"), ptrs(zfs, "zf")
+        h = ctypes.c_void_p()
+        _check(self._lib.sos_batch_plan_create(n, ctypes.addressof(hf), ctypes.addressof(hx), ctypes.addressof(hy),
+                                               ctypes.addressof(hn), None if hzi is None else ctypes.addressof(hzi),
+                                               None if hzf is None else ctypes.addressof(hzf), ctypes.byref(h)),
+               "sos_batch_plan_create")
+        self._h = h
+
+    def launch(self, stream=None):
+        _check(self._lib.sos_batch_plan_launch(self._h, _stream_handle(stream)), "sos_batch_plan_launch")
+        return self.ys
+
+    def status(self) -> int:
+        return int(self._lib.sos_batch_plan_status(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.sos_batch_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1213,6 +1213,142 @@ sos_status run_batch_impl(int n_signals, sos_filter *const *filters, const float
     return SOS_OK;
 }
 
+}  // namespace
+
+// A prepared batch (sos_batch_plan_*): descriptors uploaded once, launches enqueue no host work.
+struct sos_batch_plan {
+    int device = -1;
+    int n_cls = 0;
+    int K[kBatchClasses] = {};
+    bool norm[kBatchClasses] = {};
+    long long tiles[kBatchClasses] = {};
+    long long grid[kBatchClasses] = {};
+    const sosk::BatchSig *sigs[kBatchClasses] = {};
+    const int *tile_sig[kBatchClasses] = {};
+    unsigned long long *desc[kBatchClasses] = {};
+    unsigned char *d_up = nullptr;            // descriptors and tile -> signal maps
+    unsigned long long *d_desc = nullptr;     // lookback descriptors of every class
+    size_t desc_words = 0;
+    unsigned long long *d_ticket = nullptr;   // [kBatchClasses]
+    int *d_status = nullptr;
+    cudaStream_t side[kBatchClasses] = {};
+    cudaEvent_t fork = nullptr, join[kBatchClasses] = {};
+};
+
+namespace {
+
+void plan_free(sos_batch_plan *p) {
+    if (!p) return;
+    cudaSetDevice(p->device);
+    cudaDeviceSynchronize();
+    if (p->d_up) cudaFree(p->d_up);
+    if (p->d_desc) cudaFree(p->d_desc);
+    if (p->d_ticket) cudaFree(p->d_ticket);
+    if (p->d_status) cudaFree(p->d_status);
+    for (int c = 0; c < kBatchClasses; ++c) {
+        if (p->side[c]) cudaStreamDestroy(p->side[c]);
+        if (p->join[c]) cudaEventDestroy(p->join[c]);
+    }
+    if (p->fork) cudaEventDestroy(p->fork);
+    delete p;
+}
+
+sos_status plan_create(int n_signals, sos_filter *const *filters, const float *const *x, float *const *y,
+                       const int64_t *n, const float *const *zi, float *const *zf, sos_batch_plan **out) {
+    if (!out || n_signals <= 0 || !filters || !x || !y || !n) return SOS_EINVAL;
+    *out = nullptr;
+    constexpr long long C = 32LL * sosk::kBatchN;
+    constexpr long long W = sosk::kBatchW;
+    if (sosk::cascade_warps(sosk::kBatchN) != W) return SOS_EINVAL;
+    int device = filters[0] ? filters[0]->device : -1;
+    long long cls_sigs[kBatchClasses] = {0}, cls_tiles[kBatchClasses] = {0};
+    std::vector<int> cls(n_signals);
+    for (int i = 0; i < n_signals; ++i) {
+        sos_filter *f = filters[i];
+        if (!f || f->device != device || n[i] <= 0 || !x[i] || !y[i] || f->K > sosk::kMaxPass) return SOS_EINVAL;
+        if (x[i] != y[i] && ranges_overlap(x[i], y[i], n[i])) return SOS_EINVAL;
+        const int c = (f->K - 1) * 2 + (f->norm ? 1 : 0);
+        cls[i] = c;
+        cls_sigs[c] += 1;
+        const long long G = (n[i] + C - 1) / C;
+        cls_tiles[c] += (G + W - 1) / W;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return SOS_ECUDA;
+    long long sig_off[kBatchClasses + 1] = {0}, tile_off[kBatchClasses + 1] = {0}, desc_off[kBatchClasses + 1] = {0};
+    for (int c = 0; c < kBatchClasses; ++c) {
+        sig_off[c + 1] = sig_off[c] + cls_sigs[c];
+        tile_off[c + 1] = tile_off[c] + cls_tiles[c];
+        desc_off[c + 1] = desc_off[c] + cls_tiles[c] * 2 * (c / 2 + 1);
+    }
+    const size_t sig_bytes = sizeof(sosk::BatchSig) * sig_off[kBatchClasses];
+    const size_t up_bytes = sig_bytes + sizeof(int) * tile_off[kBatchClasses];
+    std::vector<unsigned char> up(up_bytes);
+    sosk::BatchSig *h_sigs = reinterpret_cast<sosk::BatchSig *>(up.data());
+    int *h_tile_sig = reinterpret_cast<int *>(up.data() + sig_bytes);
+    long long fill_sig[kBatchClasses], fill_tile[kBatchClasses];
+    for (int c = 0; c < kBatchClasses; ++c) {
+        fill_sig[c] = sig_off[c];
+        fill_tile[c] = tile_off[c];
+    }
+    for (int i = 0; i < n_signals; ++i) {
+        const int c = cls[i];
+        sos_filter *f = filters[i];
+        const CasPass &ps = f->cas[0].passes[0];
+        const long long G = (n[i] + C - 1) / C;
+        const long long nt = (G + W - 1) / W;
+        const long long si = fill_sig[c]++;
+        sosk::BatchSig &b = h_sigs[si];
+        b.x = x[i];
+        b.y = y[i];
+        b.n = n[i];
+        b.G = G;
+        b.tile0 = fill_tile[c] - tile_off[c];
+        b.zi = zi ? zi[i] : nullptr;
+        b.zf = zf ? zf[i] : nullptr;
+        b.sec = ps.d_sec;
+        b.H = ps.d_H;
+        b.tab = ps.d_tab;
+        b.Mm = ps.d_Mm;
+        b.gain = static_cast<float>(f->gain);
+        b.aligned = (reinterpret_cast<uintptr_t>(x[i]) % 16 == 0 && reinterpret_cast<uintptr_t>(y[i]) % 16 == 0) ? 1 : 0;
+        const int local = static_cast<int>(si - sig_off[c]);
+        for (long long t = 0; t < nt; ++t) h_tile_sig[fill_tile[c]++] = local;
+    }
+    sos_batch_plan *p = new (std::nothrow) sos_batch_plan();
+    if (!p) return SOS_ENOMEM;
+    p->device = device;
+    p->desc_words = static_cast<size_t>(desc_off[kBatchClasses]);
+    bool ok = cudaMalloc(&p->d_up, up_bytes) == cudaSuccess &&
+              cudaMalloc(&p->d_desc, sizeof(unsigned long long) * (p->desc_words + 1)) == cudaSuccess &&
+              cudaMalloc(&p->d_ticket, sizeof(unsigned long long) * kBatchClasses) == cudaSuccess &&
+              cudaMalloc(&p->d_status, sizeof(int)) == cudaSuccess &&
+              cudaMemcpy(p->d_up, up.data(), up_bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemset(p->d_status, 0, sizeof(int)) == cudaSuccess &&
+              cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int c = 0; ok && c < kBatchClasses; ++c) {
+        if (!cls_sigs[c]) continue;
+        const int K = c / 2 + 1;
+        const int bps = sosk::batch_blocks_per_sm(K, (c & 1) != 0);
+        ok = bps > 0 && cudaStreamCreateWithFlags(&p->side[c], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&p->join[c], cudaEventDisableTiming) == cudaSuccess;
+        p->K[c] = K;
+        p->norm[c] = (c & 1) != 0;
+        p->tiles[c] = cls_tiles[c];
+        p->grid[c] = std::min<long long>(static_cast<long long>(bps) * sm_count(device), cls_tiles[c]);
+        p->sigs[c] = reinterpret_cast<const sosk::BatchSig *>(p->d_up) + sig_off[c];
+        p->tile_sig[c] = reinterpret_cast<const int *>(p->d_up + sig_bytes) + tile_off[c];
+        p->desc[c] = p->d_desc + desc_off[c];
+        p->n_cls += 1;
+    }
+    if (!ok) {
+        cudaGetLastError();
+        plan_free(p);
+        return SOS_ENOMEM;
+    }
+    *out = p;
+    return SOS_OK;
+}
+
 // Sticky device status of the batch context of a device (SOS_ETIMEOUT after a lookback timeout).
 sos_status batch_status(int device) {
     BatchCtx *ctx = batch_ctx(device);
@@ -1509,6 +1645,48 @@ sos_status sos_filter_run_batch_ex(int n_signals, sos_filter *const *filters, co
                                    float *const *y_dev, const int64_t *n, const float *const *zi_dev,
                                    float *const *zf_dev, void *stream) {
     return run_batch_impl(n_signals, filters, x_dev, y_dev, n, zi_dev, zf_dev, static_cast<cudaStream_t>(stream));
+}
+
+sos_status sos_batch_plan_create(int n_signals, sos_filter *const *filters, const float *const *x_dev,
+                                 float *const *y_dev, const int64_t *n, const float *const *zi_dev,
+                                 float *const *zf_dev, sos_batch_plan **out) {
+    return plan_create(n_signals, filters, x_dev, y_dev, n, zi_dev, zf_dev, out);
+}
+
+sos_status sos_batch_plan_launch(sos_batch_plan *p, void *stream) {
+    if (!p) return SOS_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaSetDevice(p->device) != cudaSuccess) return SOS_ECUDA;
+    // fresh descriptors (tag 0 never matches) and tickets each launch: a launch enqueues no host work
+    // and may be captured into a CUDA graph and replayed
+    if (cudaMemsetAsync(p->d_desc, 0, sizeof(unsigned long long) * p->desc_words, s) != cudaSuccess ||
+        cudaMemsetAsync(p->d_ticket, 0, sizeof(unsigned long long) * kBatchClasses, s) != cudaSuccess ||
+        cudaEventRecord(p->fork, s) != cudaSuccess)
+        return SOS_ECUDA;
+    for (int c = 0; c < kBatchClasses; ++c) {
+        if (!p->tiles[c]) continue;
+        cudaStream_t cs = p->side[c];
+        if (cudaStreamWaitEvent(cs, p->fork, 0) != cudaSuccess) return SOS_ECUDA;
+        sos_status st = launch_batch_any(p->K[c], p->norm[c], p->sigs[c], p->tile_sig[c], p->tiles[c], p->desc[c],
+                                         p->d_ticket + c, 1u, p->d_status, kDefaultSpinBudget, p->grid[c], cs);
+        if (st != SOS_OK) return st;
+        if (cudaEventRecord(p->join[c], cs) != cudaSuccess || cudaStreamWaitEvent(s, p->join[c], 0) != cudaSuccess)
+            return SOS_ECUDA;
+    }
+    return SOS_OK;
+}
+
+sos_status sos_batch_plan_status(sos_batch_plan *p) {
+    if (!p) return SOS_EINVAL;
+    if (cudaSetDevice(p->device) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return SOS_ECUDA;
+    int h = 0;
+    if (cudaMemcpy(&h, p->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SOS_ECUDA;
+    return (h & sosk::kDevErrTimeout) ? SOS_ETIMEOUT : SOS_OK;
+}
+
+sos_status sos_batch_plan_destroy(sos_batch_plan *p) {
+    plan_free(p);
+    return SOS_OK;
 }
 
 sos_status sos_batch_sync_status(int device) {

@@ -153,3 +153,43 @@ def test_batched_mix_full_size_sampled(dev):
                 assert _rel(got, ref_w[a - a0:]) < tol, (i, n, a)
     for f in fs:
         f.close()
+
+
+def test_batch_plan_launch_and_cuda_graph_replay(dev):
+    """A prepared batch launched directly, then captured into a CUDA graph and replayed: every replay
+    gives the oracle's output (descriptors and tickets are reset inside the captured work)."""
+    from paper_2607_23763_gb300 import SosFilter, BatchPlan
+    items = [it for it in _mix(30, 11) if len(it[1]) > 0]
+    fs = [SosFilter(sos) for sos, _, _ in items if sos.shape[0] <= 8]
+    items = [it for it in items if it[0].shape[0] <= 8]
+    xs = [torch.from_numpy(x).to(dev) for _, x, _ in items]
+    plan = BatchPlan(fs, xs)
+    refs = [oracle.sosfilt(sos, x) for sos, x, _ in items]
+
+    def check():
+        torch.cuda.synchronize()
+        assert plan.status() == 0
+        for (sos, x, _), y, ref in zip(items, plan.ys, refs):
+            assert _rel(y.cpu().numpy(), ref) < bound(sos, x, ref, random_mix=True)
+
+    plan.launch()
+    check()
+    for y in plan.ys:
+        y.zero_()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        plan.launch(s)  # warm-up on the capture stream
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g):
+        plan.launch()
+    for _ in range(3):
+        for y in plan.ys:
+            y.zero_()
+        g.replay()
+        check()
+    plan.close()
+    for f in fs:
+        f.close()
