@@ -33,7 +33,7 @@ CPU_SAMPLE = 1 << 24  # oracle sample per step of the reference arm
 # DRAM bytes (read + write) of one launch of the timed kernel on the 2^28 workload: an ncu capture
 # of the same kernel on 2^26 samples scaled by 4 (profiles/sos_cascade_order16_2p26_traffic.md).
 # Must be re-captured (or set to None) whenever the kernel changes.
-TRAFFIC_BYTES_2P28 = 1.931e9
+TRAFFIC_BYTES_2P28 = 1.936e9
 
 
 def _peaks():
@@ -170,6 +170,13 @@ def bench_ours(args):
 
     sos = designs.butter_lowpass(ORDER, WN)
     x_host = workloads.normal_f32(SEED, N_SAMPLES)
+    choice = None
+    if not args.no_autotune and not (args.N or args.carry or args.solver or args.lbw):
+        # the library's autotuner picks the launch configuration per order and length (outside the
+        # timed region); the filter below, with default tuning, then runs its choice
+        from paper_2607_23763_gb300 import autotune, autotune_choice
+        autotune()
+        choice = autotune_choice(ORDER // 2, N_SAMPLES)
     tuning = {}
     if args.N:
         tuning["N"] = args.N
@@ -238,14 +245,22 @@ def bench_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "samples": N_SAMPLES, "sections": ORDER // 2,
-                   "N": args.N or "default", "L": 32, "l2": "inputs and outputs larger than L2 (1 GiB each)",
+                   "N": args.N or (choice[1] if choice else "default"), "L": 32,
+                   "solver": ("PH" if choice[0] == 2 else "CR") if choice else ("PH" if args.solver == 2 else "CR"),
+                   "autotuned": choice is not None,
+                   "l2": "inputs and outputs larger than L2 (1 GiB each)",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak,
+                     # the captured kernel: cyclic reduction, cascade carry, N = 32 (the default and the
+                     # autotuner's choice for this workload)
                      "traffic": TRAFFIC_BYTES_2P28 if (N_SAMPLES == 1 << 28 and ORDER == 16 and not args.N
-                                                       and not args.carry) else None,
+                                                       and not args.carry and not args.solver
+                                                       and (choice is None or choice == (1, 32))) else None,
                      "peak_kind": peak_kind,
-                     "kernel": "sos_cascade_kernel (8 sections, N = 32 samples per lane, 8 groups per block)"},
+                     "kernel": ("sos_ph_kernel (8 sections, N = 32, 7 groups per block)"
+                                if (choice and choice[0] == 2) or args.solver == 2 else
+                                "sos_cascade_kernel (8 sections, N = 32 samples per lane, 8 groups per block)")},
         "e2e": {"value": e_gss, "unit": "GS/s", "h2d_bytes_per_step": 4 * N_SAMPLES,
                 "d2h_bytes_per_step": 4 * N_SAMPLES},
         "gpu_launches": args.steps,
@@ -468,6 +483,8 @@ def main():
     ap.add_argument("--open-requests", type=int, default=110000, help="serving: open-loop requests")
     ap.add_argument("--N", type=int, default=0, help="samples per thread (16/32/64); 0 = library default")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip the autotuner (profiling runs: a fixed sequence of launches)")
     ap.add_argument("--carry", type=int, default=0, help="1 = one carry per tile for the cascade, 2 = per section")
     ap.add_argument("--solver", type=int, default=0, help="1 = cyclic reduction, 2 = PH factorization; 0 = default")
     ap.add_argument("--lbw", type=int, default=0, help="lookback width (predecessor blocks per round / 32); 0 = default")
