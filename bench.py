@@ -110,6 +110,22 @@ def _dist():
     return world, rank, local
 
 
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The largest of every rank's value (the job's time is its slowest replica's); no-op at one rank."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(samples_per_rank: int, world: int, ms_max: float) -> float:
+    """Whole-job GS/s of `world` independent replicas (weak scaling): all samples over the slowest time."""
+    return samples_per_rank * world / (ms_max * 1e-3) / 1e9
+
+
 def bench_reference(args):
     """The float64 CPU oracle on the host cores, bounded sample of the same workload."""
     world, rank, _ = _dist()
@@ -209,13 +225,9 @@ def bench_ours(args):
             f.run(x, y)
         stop.record(stream)
         barrier()
-    ms = start.elapsed_time(stop)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(start.elapsed_time(stop), world, dev)
     ms_step = ms / args.steps
-    gss = N_SAMPLES * world / (ms_step * 1e-3) / 1e9
+    gss = replica_rate(N_SAMPLES, world, ms_step)
     assert f.sync_status() == 0
 
     # end to end through the C ABI with host buffers: sos_filter_run_host copies the pinned input
@@ -230,12 +242,8 @@ def bench_ours(args):
     for _ in range(e_steps):
         f.run_host(xh, yh)
     barrier()
-    e_ms = (time.perf_counter() - t0) * 1e3 / e_steps
-    if world > 1:
-        t = torch.tensor([e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e_ms = float(t.item())
-    e_gss = N_SAMPLES * world / (e_ms * 1e-3) / 1e9
+    e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / e_steps, world, dev)
+    e_gss = replica_rate(N_SAMPLES, world, e_ms)
 
     hbm_peak, peak_kind = _peaks()
     achieved = BYTES_PER_SAMPLE * N_SAMPLES / (ms_step * 1e-3) / 1e9

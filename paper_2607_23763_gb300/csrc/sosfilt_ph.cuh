@@ -4,7 +4,7 @@
 // A tile is W = kPhWc consecutive groups of C = 32 N samples (N = kPhN); compute warp w of a thread
 // block filters group w of the tile, lane l the samples l N .. l N + N - 1.  Per tile:
 //   1. particular solution: every lane runs its N samples through the whole cascade from zero state
-//      (the forward substitution of Sec. II-C with zero initial blocks), as a wavefront: eight
+//      (the forward substitution of Sec. II-C with zero initial blocks), as a wavefront: four or eight
 //      samples at a time pass through all K sections, whose direct-form histories (x[-1], x[-2],
 //      w[-1], w[-2]) stay in registers; the samples themselves stay in the lane's row of shared
 //      memory and are overwritten in place by the particular output.
