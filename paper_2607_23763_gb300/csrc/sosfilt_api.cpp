@@ -29,6 +29,14 @@ size_t cascade_smem(int K, int N) { return N == 32 ? cascade_smem_32(K) : N == 6
 int ph_blocks_per_sm_a(int K, bool norm);
 int ph_blocks_per_sm_b(int K, bool norm);
 int ph_blocks_per_sm(int K, bool norm) { return K <= 4 ? ph_blocks_per_sm_a(K, norm) : ph_blocks_per_sm_b(K, norm); }
+int lane_blocks_per_sm_n32a(int K, bool norm);
+int lane_blocks_per_sm_n32b(int K, bool norm);
+int lane_blocks_per_sm_n64a(int K, bool norm);
+int lane_blocks_per_sm_n64b(int K, bool norm);
+int lane_blocks_per_sm(int K, int N, bool norm) {
+    if (N == 32) return K <= 4 ? lane_blocks_per_sm_n32a(K, norm) : lane_blocks_per_sm_n32b(K, norm);
+    return K <= 4 ? lane_blocks_per_sm_n64a(K, norm) : lane_blocks_per_sm_n64b(K, norm);
+}
 }  // namespace sosk
 
 namespace {
@@ -145,6 +153,18 @@ struct PhPass {
     std::vector<float> A_tail;     // packed transition over tail_m + 1 samples
 };
 
+// One pass (<= 8 sections) of the skewed-pass PH kernel (sosfilt_lane.cuh) for one N.
+struct LanePass {
+    int k0 = 0, kp = 0, N = 0;
+    std::vector<double> coef;        // [kp][5] as the kernel applies them
+    DMat M1;                         // one-sample zero-input transition of the pass's cascade state
+    std::vector<sosk::LaneSec> sec;  // [kp]
+    std::vector<float> MX;           // coupling blocks of M_N, row-major 2x2, kp (kp - 1) / 2 of them
+    float *d_tab = nullptr;          // device table block (LaneDims<kp, N>::TAB_GLOBAL floats)
+    int tail_m = -1;                 // m_last for which A_tail is cached
+    std::vector<float> A_tail;       // packed transition over tail_m + 1 samples
+};
+
 }  // namespace
 
 struct sos_filter {
@@ -158,6 +178,7 @@ struct sos_filter {
     NTables tables[kNumN];
     CasTables cas[2];  // N = 32, 64
     std::vector<PhPass> ph;  // PH-factorization passes
+    std::vector<LanePass> lane[2];  // skewed-pass PH kernel, N = 32 and N = 64
     // workspace
     unsigned long long *d_desc = nullptr;
     size_t desc_groups = 0;  // capacity in groups (per section slot)
@@ -535,6 +556,107 @@ sos_status build_ph(sos_filter *f) {
     return SOS_OK;
 }
 
+// Tables of the skewed-pass PH kernel for one N (32 or 64), in float64, uploaded once.  Layout of
+// the device block as LaneDims<kp, N>: (M_N)^lane [32][stride], (A_T)^lane [32][stride] (packed),
+// A_C dense column-major, the output basis in chunks [N / 4][2 kp][4] (H_j(4 c + q)), A_T dense and
+// (A_T)^(32 w) dense for w = 1..kMaxWin.
+sos_status build_lane(sos_filter *f, int N, std::vector<LanePass> &out) {
+    constexpr int W = sosk::kLaneW;
+    out.clear();
+    for (int k0 = 0; k0 < f->K; k0 += sosk::kMaxPass) {
+        LanePass ps;
+        ps.k0 = k0;
+        ps.N = N;
+        ps.kp = (f->K - k0) < sosk::kMaxPass ? (f->K - k0) : sosk::kMaxPass;
+        const int kp = ps.kp, S = 2 * kp;
+        ps.coef.resize(5 * kp);
+        for (int j = 0; j < kp; ++j) {
+            const double *c = &f->sos[5 * (k0 + j)];
+            double b0 = c[0], b1 = c[1], b2 = c[2];
+            if (f->norm) {
+                b1 /= b0;
+                b2 /= b0;
+                b0 = 1.0;
+            }
+            ps.coef[5 * j + 0] = b0;
+            ps.coef[5 * j + 1] = b1;
+            ps.coef[5 * j + 2] = b2;
+            ps.coef[5 * j + 3] = c[3];
+            ps.coef[5 * j + 4] = c[4];
+        }
+        ps.M1 = DMat(S);
+        std::vector<double> H(static_cast<size_t>(S) * N, 0.0);
+        for (int j = 0; j < S; ++j) {
+            std::vector<double> z(S, 0.0);
+            z[j] = 1.0;
+            cascade_step(ps.coef, kp, z, 0.0);
+            for (int i = 0; i < S; ++i) ps.M1.at(i, j) = z[i];
+            std::vector<double> h(S, 0.0);
+            h[j] = 1.0;
+            for (int m = 0; m < N; ++m) H[static_cast<size_t>(j) * N + m] = cascade_step(ps.coef, kp, h, 0.0);
+        }
+        const DMat MN = dpow(ps.M1, N);
+        const DMat AC = dpow(MN, 32);
+        const DMat AT = dpow(AC, W);
+        auto f32 = [](double v) { return static_cast<float>(v); };
+        ps.sec.assign(kp, sosk::LaneSec{});
+        for (int j = 0; j < kp; ++j) {
+            sosk::LaneSec &c = ps.sec[j];
+            const double b0 = ps.coef[5 * j], b1 = ps.coef[5 * j + 1], b2 = ps.coef[5 * j + 2];
+            const double a1 = ps.coef[5 * j + 3], a2 = ps.coef[5 * j + 4];
+            c.c = float4{f32(b1), f32(b2), f32(-a1), f32(-a2)};
+            // transposed direct form II state after sample m from the direct form II history:
+            // z1 = b1 x - a1 y + z2[-1] and z2 = b2 x - a2 y with x = u + a1 u[-1] + a2 u[-2] and
+            // y = b0 u + b1 u[-1] + b2 u[-2]; the u[-2] terms cancel
+            c.g = float4{f32(b1 - b0 * a1), f32(b2 - b0 * a2), f32(b2 - b0 * a2), f32(a1 * b2 - a2 * b1)};
+            Mat P{MN.at(2 * j, 2 * j), MN.at(2 * j, 2 * j + 1), MN.at(2 * j + 1, 2 * j), MN.at(2 * j + 1, 2 * j + 1)};
+            for (int r = 0; r < 5; ++r) {
+                c.tn[r] = float4{f32(P.a), f32(P.b), f32(P.c), f32(P.d)};
+                P = mul(P, P);
+            }
+            c.b0 = f32(b0);
+            c.zscale = f32(f->zscale[k0 + j]);
+            c.zscale_inv = f32(1.0 / f->zscale[k0 + j]);
+        }
+        ps.MX.assign(kp > 1 ? 2 * kp * (kp - 1) : 4, 0.f);
+        for (int k = 1; k < kp; ++k)
+            for (int j = 0; j < k; ++j) {
+                float *b = &ps.MX[4 * (k * (k - 1) / 2 + j)];
+                b[0] = f32(MN.at(2 * k, 2 * j));
+                b[1] = f32(MN.at(2 * k, 2 * j + 1));
+                b[2] = f32(MN.at(2 * k + 1, 2 * j));
+                b[3] = f32(MN.at(2 * k + 1, 2 * j + 1));
+            }
+        const int ms = lane_stride(kp), full = S * S;
+        const size_t off_ac = 64 * static_cast<size_t>(ms), off_h = off_ac + full, off_at = off_h + N * S;
+        std::vector<float> tab(off_at + (1 + sosk::kMaxWin) * full, 0.f);
+        DMat L = deye(S), LT = deye(S);
+        for (int l = 0; l < 32; ++l) {
+            pack_into(L, kp, &tab[static_cast<size_t>(l) * ms]);
+            pack_into(LT, kp, &tab[static_cast<size_t>(32 + l) * ms]);
+            L = dmul(L, MN);
+            LT = dmul(LT, AT);
+        }
+        dense_colmajor_into(AC, &tab[off_ac]);
+        for (int c = 0; c < N / 4; ++c)
+            for (int j = 0; j < S; ++j)
+                for (int q = 0; q < 4; ++q)
+                    tab[off_h + (static_cast<size_t>(c) * S + j) * 4 + q] = f32(H[static_cast<size_t>(j) * N + 4 * c + q]);
+        dense_colmajor_into(AT, &tab[off_at]);
+        const DMat AT32 = dpow(AT, 32);
+        DMat Pw = AT32;
+        for (int w = 1; w <= sosk::kMaxWin; ++w) {
+            dense_colmajor_into(Pw, &tab[off_at + static_cast<size_t>(full) * w]);
+            Pw = dmul(Pw, AT32);
+        }
+        if (cudaMalloc(&ps.d_tab, tab.size() * sizeof(float)) != cudaSuccess) return SOS_ENOMEM;
+        if (cudaMemcpy(ps.d_tab, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+            return SOS_ECUDA;
+        out.push_back(std::move(ps));
+    }
+    return SOS_OK;
+}
+
 int table_index(int N) {
     for (int i = 0; i < kNumN; ++i)
         if (kSupportedN[i] == N) return i;
@@ -843,6 +965,94 @@ sos_status run_ph(sos_filter *f, const float *x, float *y, int64_t n, const floa
     return SOS_OK;
 }
 
+// ---- skewed-pass PH kernel (sosfilt_lane.cuh)
+template <int K, int N>
+sos_status launch_lane_pass(sos_filter *f, LanePass &ps, const float *x, float *y, long long n, long long G,
+                            long long n_tiles, long long grid, const float *zi, float *zf, bool first, bool aligned,
+                            cudaStream_t s) {
+    static_assert(K >= 1 && K <= sosk::kMaxPass, "pass size");
+    auto p = std::make_unique<sosk::LaneParams<K>>();
+    std::memset(p.get(), 0, sizeof(*p));
+    p->x = x;
+    p->y = y;
+    p->n = n;
+    p->G = G;
+    p->n_tiles = n_tiles;
+    p->zi = zi;
+    p->zf = zf;
+    p->gain = first ? static_cast<float>(f->gain) : 1.0f;
+    p->desc = f->d_desc;
+    p->ticket = f->d_ticket;
+    p->ticket_base = f->ticket_base;
+    p->epoch = next_epoch(f, s);
+    p->status = f->d_status;
+    p->spin_budget = f->tuning.spin_budget_cycles ? f->tuning.spin_budget_cycles : kDefaultSpinBudget;
+    p->aligned = aligned ? 1 : 0;
+    p->tab = ps.d_tab;
+    for (int j = 0; j < K; ++j) p->sec[j] = ps.sec[j];
+    std::memcpy(p->MX, ps.MX.data(), sizeof(float) * ps.MX.size());
+    const long long C = 32LL * N;
+    const int m_last = static_cast<int>((n - 1 - (G - 1) * C) % N);
+    p->m_last = m_last;
+    if (zf) {
+        if (ps.tail_m != m_last) {
+            ps.A_tail.assign(packed_floats(K), 0.f);
+            pack_into(dpow(ps.M1, m_last + 1), K, ps.A_tail.data());
+            ps.tail_m = m_last;
+        }
+        std::memcpy(p->A_tail, ps.A_tail.data(), sizeof(float) * packed_floats(K));
+    }
+    cudaError_t e = sosk::launch_lane<K, N>(f->norm, *p, grid, s);
+    if (e != cudaSuccess) return SOS_ECUDA;
+    f->ticket_base += static_cast<unsigned long long>(n_tiles + grid);
+    return SOS_OK;
+}
+
+template <int N>
+sos_status launch_lane_any(int K, sos_filter *f, LanePass &ps, const float *x, float *y, long long n, long long G,
+                           long long n_tiles, long long grid, const float *zi, float *zf, bool first, bool aligned,
+                           cudaStream_t s) {
+    switch (K) {
+#define SOSK_CASE(k) \
+    case k: return launch_lane_pass<k, N>(f, ps, x, y, n, G, n_tiles, grid, zi, zf, first, aligned, s);
+        SOSK_CASE(1) SOSK_CASE(2) SOSK_CASE(3) SOSK_CASE(4) SOSK_CASE(5) SOSK_CASE(6) SOSK_CASE(7) SOSK_CASE(8)
+#undef SOSK_CASE
+        default: return SOS_EINVAL;
+    }
+}
+
+// PH factorization with the skewed particular pass, one carry per tile for the whole cascade,
+// persistent grid.
+sos_status run_lane(sos_filter *f, const float *x, float *y, int64_t n, const float *zi, float *zf, cudaStream_t s,
+                    int N_choice = 0) {
+    const int N = f->tuning.N ? f->tuning.N : N_choice ? N_choice : 64;
+    if (N != 32 && N != 64) return SOS_EINVAL;
+    auto &passes = f->lane[N == 32 ? 0 : 1];
+    const long long C = 32LL * N;
+    const long long W = sosk::kLaneW;
+    const long long G = (n + C - 1) / C;
+    const long long n_tiles = (G + W - 1) / W;
+    sos_status st = ensure_desc(f, G, s);
+    if (st != SOS_OK) return st;
+    const bool aligned = (reinterpret_cast<uintptr_t>(x) % 16 == 0) && (reinterpret_cast<uintptr_t>(y) % 16 == 0);
+    const float *src = x;
+    for (auto &ps : passes) {
+        const int bps = sosk::lane_blocks_per_sm(ps.kp, N, f->norm);
+        if (bps <= 0) return SOS_ECUDA;
+        long long grid = static_cast<long long>(bps) * sm_count(f->device);
+        if (grid > n_tiles) grid = n_tiles;
+        if (N == 32)
+            st = launch_lane_any<32>(ps.kp, f, ps, src, y, n, G, n_tiles, grid, zi ? zi + 2 * ps.k0 : nullptr,
+                                     zf ? zf + 2 * ps.k0 : nullptr, ps.k0 == 0, aligned, s);
+        else
+            st = launch_lane_any<64>(ps.kp, f, ps, src, y, n, G, n_tiles, grid, zi ? zi + 2 * ps.k0 : nullptr,
+                                     zf ? zf + 2 * ps.k0 : nullptr, ps.k0 == 0, aligned, s);
+        if (st != SOS_OK) return st;
+        src = y;
+    }
+    return SOS_OK;
+}
+
 // Solver of a run: the tuning's choice, by default divide-and-conquer cyclic reduction (faster than
 // the PH kernel at every order on GB300: 154 vs 130 GS/s at order 16, 540 vs 430 at order 2).
 int solver_of(const sos_filter *f) {
@@ -921,7 +1131,7 @@ TuneTable g_tune[64];
 
 void candidate(int c, int *solver, int *N) {
     *solver = c == 2 ? SOS_SOLVER_PH : SOS_SOLVER_CR;
-    *N = c == 1 ? 64 : 32;
+    *N = c == 0 ? 32 : 64;
 }
 
 int tune_bucket(int64_t n) {
@@ -958,11 +1168,11 @@ sos_status run_impl(sos_filter *f, const float *x, float *y, int64_t n, const fl
         // all defaults: the autotuned choice for this section count and length, if there is one
         int solver = 0, N = 0;
         if (tuned_choice(f->device, f->K, n, &solver, &N)) {
-            if (solver == SOS_SOLVER_PH) return run_ph(f, x, y, n, zi, zf, s);
+            if (solver == SOS_SOLVER_PH) return run_lane(f, x, y, n, zi, zf, s, N);
             return run_cascade(f, x, y, n, zi, zf, s, N);
         }
     }
-    if (solver_of(f) == SOS_SOLVER_PH) return run_ph(f, x, y, n, zi, zf, s);
+    if (solver_of(f) == SOS_SOLVER_PH) return run_lane(f, x, y, n, zi, zf, s);
     if (t.carry == SOS_CARRY_SECTION) return run_sections(f, x, y, n, zi, zf, s);
     return run_cascade(f, x, y, n, zi, zf, s);
 }
@@ -1447,7 +1657,7 @@ sos_status sos_filter_create(int n_sections, const double *sos, const float *zi,
         if (t->solver != SOS_SOLVER_DEFAULT && t->solver != SOS_SOLVER_CR && t->solver != SOS_SOLVER_PH)
             return SOS_EINVAL;
         if (t->solver == SOS_SOLVER_PH &&
-            ((t->N && t->N != sosk::kPhN) || t->carry == SOS_CARRY_SECTION || t->lookback_width))
+            ((t->N && t->N != 32 && t->N != 64) || t->carry == SOS_CARRY_SECTION || t->lookback_width))
             return SOS_EINVAL;
     }
     for (int k = 0; k < n_sections; ++k) {
@@ -1506,6 +1716,7 @@ sos_status sos_filter_create(int n_sections, const double *sos, const float *zi,
     }
     for (int i = 0; i < 2 && st == SOS_OK; ++i) st = build_cascade(f, i == 0 ? 32 : 64, f->cas[i]);
     if (st == SOS_OK) st = build_ph(f);
+    for (int i = 0; i < 2 && st == SOS_OK; ++i) st = build_lane(f, i == 0 ? 32 : 64, f->lane[i]);
     if (st == SOS_OK) {
         if (cudaMalloc(&f->d_ticket, sizeof(unsigned long long)) != cudaSuccess ||
             cudaMalloc(&f->d_status, sizeof(int)) != cudaSuccess ||
@@ -1551,6 +1762,9 @@ sos_status sos_filter_destroy(sos_filter *f) {
         }
     for (auto &ps : f->ph)
         if (ps.d_tab) cudaFree(ps.d_tab);
+    for (auto &v : f->lane)
+        for (auto &ps : v)
+            if (ps.d_tab) cudaFree(ps.d_tab);
     if (f->d_desc) cudaFree(f->d_desc);
     if (f->d_sring) cudaFree(f->d_sring);
     if (f->d_ticket) cudaFree(f->d_ticket);
@@ -1730,10 +1944,8 @@ sos_status sos_autotune(int max_log2n, float *report) {
             int solver = 0, N = 0;
             candidate(c, &solver, &N);
             t.solver = solver;
-            if (solver == SOS_SOLVER_CR) {
-                t.N = N;
-                t.carry = SOS_CARRY_CASCADE;
-            }
+            t.N = N;
+            if (solver == SOS_SOLVER_CR) t.carry = SOS_CARRY_CASCADE;
             sos_filter *f = nullptr;
             rc = sos_filter_create(K, sos.data(), nullptr, &t, &f);
             if (rc != SOS_OK) break;

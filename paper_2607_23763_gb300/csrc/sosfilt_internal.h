@@ -169,6 +169,55 @@ SOSK_DECLARE_PH(1) SOSK_DECLARE_PH(2) SOSK_DECLARE_PH(3) SOSK_DECLARE_PH(4)
 SOSK_DECLARE_PH(5) SOSK_DECLARE_PH(6) SOSK_DECLARE_PH(7) SOSK_DECLARE_PH(8)
 int ph_blocks_per_sm(int K, bool norm);
 
+// ---- PH-factorization kernel with a skewed direct-form-II particular pass (sosfilt_lane.cuh)
+constexpr int kLaneW = 7;  // compute warps per block, one group each; a tile is kLaneW groups
+
+// Per-section constants of the skewed-pass kernel, in the kernel's domain (b / b0 and b0 = 1 when
+// normalized; carried state = zscale * true state).
+struct LaneSec {
+    float4 c;      // b1, b2, -a1, -a2
+    float4 g;      // direct-form-II history (u[m], u[m-1]) -> transposed direct-form-II state after
+                   // sample m: z1 = g.x u[m] + g.y u[m-1], z2 = g.z u[m] + g.w u[m-1]
+    float4 tn[5];  // (T^N)^(2^r), r = 0..4, row-major 2x2, T the section's one-sample transition
+    float b0, zscale, zscale_inv, pad;
+};
+
+template <int K>
+struct LaneParams {
+    const float *x;
+    float *y;
+    long long n, G, n_tiles;    // samples, groups of 32 N samples, tiles of kLaneW groups
+    const float *zi;            // device [K][2] initial state of this pass (true domain) or nullptr
+    float *zf;                  // device [K][2] final state of this pass or nullptr
+    float gain;                 // input multiplier (product of all b0 when normalized; first pass only)
+    unsigned long long *desc;   // [n_tiles][2K] tagged carry words
+    unsigned long long *ticket;
+    unsigned long long ticket_base;
+    unsigned int epoch;
+    int *status;
+    long long spin_budget;
+    int aligned;                // x and y 16-byte aligned
+    int m_last;                 // position of the signal's last sample inside its lane
+    const float *tab;           // global table block, layout LaneDims<K, N>
+    LaneSec sec[K];
+    // blocks (k, j), j < k, of the lane transition M_N, row-major 2x2 at k (k - 1) / 2 + j
+    float4 MX[K > 1 ? K * (K - 1) / 2 : 1];
+    float A_tail[2 * K * (K + 1)];  // packed cascade transition over m_last + 1 samples
+};
+
+template <int K, int N>
+cudaError_t launch_lane(bool norm, const LaneParams<K> &p, long long grid, cudaStream_t s);
+#define SOSK_DECLARE_LANE(K, N) \
+    template <>                 \
+    cudaError_t launch_lane<K, N>(bool norm, const LaneParams<K> &p, long long grid, cudaStream_t s);
+#define SOSK_DECLARE_LANE_N(N)                                                                       \
+    SOSK_DECLARE_LANE(1, N) SOSK_DECLARE_LANE(2, N) SOSK_DECLARE_LANE(3, N) SOSK_DECLARE_LANE(4, N) \
+    SOSK_DECLARE_LANE(5, N) SOSK_DECLARE_LANE(6, N) SOSK_DECLARE_LANE(7, N) SOSK_DECLARE_LANE(8, N)
+SOSK_DECLARE_LANE_N(32)
+SOSK_DECLARE_LANE_N(64)
+// Thread blocks of the skewed-pass kernel that fit on one SM (0 if unavailable).
+int lane_blocks_per_sm(int K, int N, bool norm);
+
 // ---- multi-signal persistent kernel (sosfilt_batch.cuh): the cascade-carry cyclic-reduction
 // kernel over a global queue of (signal, tile) work items
 constexpr int kBatchN = 32;  // samples per lane

@@ -1,0 +1,574 @@
+// Persistent single-signal kernel: PH factorization of every lane's block (Sec. II-C) with lanes
+// of N = 64 samples, a skewed direct-form-II particular pass and a column-wise correction, sm_103a.
+//
+// A tile is W = kLaneW consecutive groups of C = 32 N samples; compute warp w of a thread block
+// filters group w of the tile, lane l the samples l N .. l N + N - 1.  Per tile:
+//   1. particular solution: every lane runs its N samples through the K sections from zero state.
+//      The sections run skewed: at step i section s takes sample i - s, its input being section
+//      s - 1's output of step i - 1, so the K section updates of one step are independent and
+//      keep the FMA pipe busy without any wait on the previous section.  Each section is a direct
+//      form II recurrence (u = x - a1 u[-1] - a2 u[-2], y = b0 u + b1 u[-1] + b2 u[-2]): four FMAs
+//      per sample when b0 = 1.  Zero state is the same in every realisation, so the form only
+//      matters for the lane's terminal state, which is converted to transposed direct form II
+//      once per lane.  The samples stay in the lane's row of shared memory and are overwritten in
+//      place by the particular output.
+//   2. lane scan (Sec. II-C's recursive doubling over the 32 lanes) on the whole cascade state,
+//      section by section: M_N is block lower-triangular, so section k's words are scanned with its
+//      own (T^N)^(2^r) once the lower sections' lane states are folded in through M_N's coupling
+//      blocks.  Lane 31's inclusive state is the group's local carry.
+//   3. a coordinator warp folds the tile's local carries, publishes the tile carry, resolves the
+//      tile's incoming 2K-word state by decoupled lookback over tiles (Sec. IV-B, Eq. 25 on the
+//      cascade state) and derives every group's incoming state Z.
+//   4. homogeneous correction (Eq. 24 once for the whole cascade): lane l's true incoming state is
+//      S_l + (M_N)^l Z, and sample m of its row gains sum_j H_j(m) [S_l + (M_N)^l Z]_j.  The rows'
+//      states go to shared memory and the correction runs across the rows: each lane takes four
+//      consecutive samples of one row, so its 4 x 2K basis values H_j(m) stay in registers and
+//      every corrected float4 leaves in a fully coalesced store.
+// Tile t is corrected after the particular pass of tile t + 1, so the coordinator has one pass to
+// resolve it.  Tiles come from an ascending ticket counter (Sec. IV-A).  The next tile's input is
+// loaded into registers during the pass (coalesced 128-bit loads) and stashed into the warp's free
+// row buffer at the start of the next iteration.
+#pragma once
+#include "sosfilt_cascade.cuh"
+
+namespace sosk {
+
+template <int K, int N>
+struct LaneDims {
+    static constexpr int S = 2 * K;
+    static constexpr int NB = K * (K + 1) / 2;
+    static constexpr int NF = 4 * NB;  // floats of one packed lower block-triangular matrix
+    // per-lane stride of the packed powers: an odd number of 16-byte words (conflict-free rows)
+    static constexpr int MS = ((NF / 4) & 1) ? NF : NF + 4;
+    static constexpr int FULL = S * S;
+    static constexpr int P2 = S <= 2 ? 2 : S <= 4 ? 4 : S <= 8 ? 8 : 16;
+    static constexpr int SH = 5 - (P2 == 2 ? 1 : P2 == 4 ? 2 : P2 == 8 ? 3 : 4);
+    static constexpr int CH = N / 4;   // float4 chunks of a row
+    static constexpr int RPS = 32 / CH;  // rows per step of the column-wise correction
+    // row-state pitch: S rounded up to whole 16-byte words, an odd number of them
+    static constexpr int S4 = (S + 3) / 4;
+    static constexpr int RSP = 4 * ((S4 & 1) ? S4 : S4 + 1);
+    // table block (copied to shared memory up to OFF_AT): (M_N)^lane [32][MS], (A_T)^lane [32][MS],
+    // A_C dense column-major, H chunks [CH][S][4] (H_j(4c + q)); global only: A_T dense and
+    // (A_T)^(32 w) dense for w = 1..kMaxWin
+    static constexpr int OFF_ATL = 32 * MS;
+    static constexpr int OFF_AC = 64 * MS;
+    static constexpr int OFF_H = OFF_AC + FULL;
+    static constexpr int OFF_AT = OFF_H + N * S;
+    static constexpr int TAB = OFF_AT;
+    static constexpr int TAB_GLOBAL = OFF_AT + (1 + kMaxWin) * FULL;
+};
+
+// One step of section s in direct form II: u = x - a1 u[-1] - a2 u[-2], output b0 u + b1 u[-1] +
+// b2 u[-2] (the history is updated in place).  The a2 term is taken first, so only one FMA follows
+// the arrival of u[-1] on the recurrence.
+template <bool NORM>
+__device__ __forceinline__ float df2_step(const LaneSec &c, float &u1, float &u2, float x) {
+    const float t = fmaf(c.c.w, u2, x);
+    const float u = fmaf(c.c.z, u1, t);
+    const float w = fmaf(c.c.x, u1, fmaf(c.c.y, u2, NORM ? u : c.b0 * u));
+    u2 = u1;
+    u1 = u;
+    return w;
+}
+
+// Particular solution of the lane's row (N samples, in place) through all K sections from zero
+// state, sections skewed by one sample each; t receives the terminal state (transposed direct form
+// II).  With CAPTURE, the lane with cap_lane set writes its state after sample m_last to cap.
+template <int K, int N, bool NORM, bool CAPTURE>
+__device__ __forceinline__ void lane_particular(const LaneParams<K> &p, float *row, float gain, float (&t)[2 * K],
+                                                int m_last, bool cap_lane, float *cap) {
+    constexpr int D = K - 1;             // skew of the last section
+    constexpr int R0 = (4 - (D & 3)) & 3;  // a step group's first output sits R0 samples into its block
+    float u1[K], u2[K], pipe[K];
+#pragma unroll
+    for (int s = 0; s < K; ++s) u1[s] = u2[s] = pipe[s] = 0.f;
+    float cu1[K], cu2[K];  // captured history (CAPTURE only)
+#pragma unroll
+    for (int s = 0; s < K; ++s) cu1[s] = cu2[s] = 0.f;
+    const int m_cap = (CAPTURE && cap_lane) ? m_last : -(1 << 20);
+    float carry[R0 > 0 ? R0 : 1];
+#pragma unroll
+    for (int r = 0; r < (R0 > 0 ? R0 : 1); ++r) carry[r] = 0.f;
+
+    float4 xn = *reinterpret_cast<const float4 *>(row);
+#pragma unroll 1
+    for (int i0 = 0; i0 < N; i0 += 4) {
+        const float4 xv = xn;
+        if (i0 + 4 < N) xn = *reinterpret_cast<const float4 *>(row + i0 + 4);
+        const float xs[4] = {xv.x, xv.y, xv.z, xv.w};
+        float out[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            // step i0 + j: from the last section down, so that pipe[s - 1] is read before it is
+            // overwritten with this step's output of section s - 1
+#pragma unroll
+            for (int s = K - 1; s >= 0; --s) {
+                const float xin = (s == 0) ? (NORM ? xs[j] * gain : xs[j]) : pipe[s - 1];
+                const float w = df2_step<NORM>(p.sec[s], u1[s], u2[s], xin);
+                if (s == K - 1)
+                    out[j] = w;
+                else
+                    pipe[s] = w;
+                if constexpr (CAPTURE) {
+                    const bool hit = (i0 + j - s) == m_cap;
+                    cu1[s] = hit ? u1[s] : cu1[s];
+                    cu2[s] = hit ? u2[s] : cu2[s];
+                }
+            }
+        }
+        // out[j] is sample i0 + j - D; the aligned block at b = i0 - D - R0 is complete
+        const int b = i0 - D - R0;
+        if (b >= 0) {
+            float blk[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) blk[r] = r < R0 ? carry[r] : out[r - R0];
+            *reinterpret_cast<float4 *>(row + b) = make_float4(blk[0], blk[1], blk[2], blk[3]);
+        }
+#pragma unroll
+        for (int r = 0; r < R0; ++r) carry[r] = out[4 - R0 + r];
+    }
+    // drain: steps N .. N + D - 1, in which only the sections s > step - N are still running
+    if constexpr (D > 0) {
+        float tail[R0 + D];
+#pragma unroll
+        for (int r = 0; r < R0; ++r) tail[r] = carry[r];
+#pragma unroll
+        for (int e = 0; e < D; ++e) {
+#pragma unroll
+            for (int s = K - 1; s >= e + 1; --s) {
+                const float w = df2_step<NORM>(p.sec[s], u1[s], u2[s], pipe[s - 1]);
+                if (s == K - 1)
+                    tail[R0 + e] = w;
+                else
+                    pipe[s] = w;
+                if constexpr (CAPTURE) {
+                    const bool hit = (N + e - s) == m_cap;
+                    cu1[s] = hit ? u1[s] : cu1[s];
+                    cu2[s] = hit ? u2[s] : cu2[s];
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < (R0 + D) / 4; ++r)
+            *reinterpret_cast<float4 *>(row + N - D - R0 + 4 * r) =
+                make_float4(tail[4 * r], tail[4 * r + 1], tail[4 * r + 2], tail[4 * r + 3]);
+    } else {
+        (void)carry;
+    }
+    // transposed direct form II state from the last two u values of every section
+#pragma unroll
+    for (int s = 0; s < K; ++s) {
+        const float4 g = p.sec[s].g;
+        t[2 * s] = fmaf(g.x, u1[s], g.y * u2[s]);
+        t[2 * s + 1] = fmaf(g.z, u1[s], g.w * u2[s]);
+    }
+    if constexpr (CAPTURE) {
+        if (cap_lane) {
+#pragma unroll
+            for (int s = 0; s < K; ++s) {
+                const float4 g = p.sec[s].g;
+                cap[2 * s] = fmaf(g.x, cu1[s], g.y * cu2[s]);
+                cap[2 * s + 1] = fmaf(g.z, cu1[s], g.w * cu2[s]);
+            }
+        }
+    }
+}
+
+// Cascade lane scan: from the lanes' terminal particular states t, the lane's exclusive incoming
+// state S (relative to zero group state) and, in lane 31, the group's local carry a_out.
+template <int K>
+__device__ __forceinline__ void lane_scan(const LaneParams<K> &p, const float (&t)[2 * K], float (&S)[2 * K],
+                                          float *a_out, int lane) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float u1 = t[2 * k], u2 = t[2 * k + 1];
+#pragma unroll
+        for (int j = 0; j < k; ++j) {
+            const float4 b = p.MX[k * (k - 1) / 2 + j];
+            u1 = fmaf(b.x, S[2 * j], fmaf(b.y, S[2 * j + 1], u1));
+            u2 = fmaf(b.z, S[2 * j], fmaf(b.w, S[2 * j + 1], u2));
+        }
+#pragma unroll
+        for (int r = 0; r < 5; ++r) {
+            const float o1 = __shfl_up_sync(0xffffffffu, u1, 1 << r);
+            const float o2 = __shfl_up_sync(0xffffffffu, u2, 1 << r);
+            const float4 tn = p.sec[k].tn[r];
+            if (lane >= (1 << r)) {
+                u1 = fmaf(tn.x, o1, fmaf(tn.y, o2, u1));
+                u2 = fmaf(tn.z, o1, fmaf(tn.w, o2, u2));
+            }
+        }
+        float s1 = __shfl_up_sync(0xffffffffu, u1, 1), s2 = __shfl_up_sync(0xffffffffu, u2, 1);
+        if (lane == 0) s1 = s2 = 0.f;
+        S[2 * k] = s1;
+        S[2 * k + 1] = s2;
+        if (lane == 31) {
+            a_out[2 * k] = u1;
+            a_out[2 * k + 1] = u2;
+        }
+    }
+}
+
+// y += A x for a packed lower block-triangular A and x in shared memory (x read as word pairs,
+// broadcast).
+template <int K>
+__device__ __forceinline__ void lane_state_mv(const float *__restrict__ A, const float *__restrict__ x,
+                                              float (&y)[2 * K]) {
+#pragma unroll
+    for (int s = 0; s < K; ++s) {
+        float y0 = y[2 * s], y1 = y[2 * s + 1];
+#pragma unroll
+        for (int q = 0; q <= s; ++q) {
+            const float4 B = *reinterpret_cast<const float4 *>(A + 4 * (s * (s + 1) / 2 + q));
+            const float2 xq = *reinterpret_cast<const float2 *>(x + 2 * q);
+            y0 = fmaf(B.x, xq.x, fmaf(B.y, xq.y, y0));
+            y1 = fmaf(B.z, xq.x, fmaf(B.w, xq.y, y1));
+        }
+        y[2 * s] = y0;
+        y[2 * s + 1] = y1;
+    }
+}
+
+template <int K, int N, bool NORM>
+__global__ void __launch_bounds__((kLaneW + 1) * 32, 1) sos_lane_kernel(const __grid_constant__ LaneParams<K> p) {
+    using Dm = LaneDims<K, N>;
+    constexpr int S = Dm::S, MS = Dm::MS, W = kLaneW, CH = Dm::CH, RPS = Dm::RPS, RSP = Dm::RSP;
+    constexpr int P = N + 4;  // padded row pitch (floats): conflict-free 128-bit row access
+    constexpr int C = N * kL;
+    extern __shared__ float4 smem4[];
+    float *rows = reinterpret_cast<float *>(smem4);  // [W][2][32][P]: two row buffers per warp
+    float *tab = rows + W * 2 * kL * P;              // table block, layout LaneDims
+    float *sML = tab;                                // (M_N)^lane [32][MS]
+    float *sATl = tab + Dm::OFF_ATL;                 // (A_T)^lane [32][MS]
+    float *sACd = tab + Dm::OFF_AC;                  // A_C dense column-major
+    const float4 *sH4 = reinterpret_cast<const float4 *>(tab + Dm::OFF_H);  // [CH][S] float4
+    float *rowst = tab + Dm::TAB;                    // [W][32][RSP] rows' true incoming states
+    float *a_buf = rowst + W * kL * RSP;             // [2][W][S] local carries
+    float *z_buf = a_buf + 2 * W * S;                // [2][W][S] incoming states
+    float *agg = z_buf + 2 * W * S;                  // [2][S] tile carry under zero incoming state
+    float *zs_tail = agg + 2 * S;                    // [S] lane-local state after the last sample
+    const float *gATd = p.tab + Dm::OFF_AT;          // A_T dense (global, L1-resident)
+    // tiles alternate between two slots; the incoming-state barrier has one per slot, so that it
+    // never runs two phases ahead of a waiter
+    __shared__ unsigned long long bar_local[2], bar_zready[2], bar_ticket[4];
+    __shared__ long long ring[4];
+    __shared__ int fold_count[2];
+    __shared__ int tickets_exhausted;
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const long long budget = p.spin_budget;
+
+    {
+        const float4 *src = reinterpret_cast<const float4 *>(p.tab);
+        float4 *dst = reinterpret_cast<float4 *>(tab);
+        for (int i = threadIdx.x; i < Dm::TAB / 4; i += blockDim.x) dst[i] = __ldg(src + i);
+    }
+    auto draw_ticket = [&]() -> long long {
+        if (tickets_exhausted) return -1;
+        long long t = static_cast<long long>(atomicAdd(p.ticket, 1ULL) - p.ticket_base);
+        if (t >= p.n_tiles) {
+            tickets_exhausted = 1;
+            t = -1;
+        }
+        return t;
+    };
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&bar_local[i], 1);
+            mbar_init(&bar_zready[i], 1);
+            fold_count[i] = 0;
+        }
+        tickets_exhausted = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) mbar_init(&bar_ticket[i], 1);
+        ring[0] = draw_ticket();
+        ring[1] = draw_ticket();
+        mbar_arrive(&bar_ticket[0]);
+        mbar_arrive(&bar_ticket[1]);
+    }
+    __syncthreads();
+
+    if (warp == 0) {
+        // ------------------------------------------------------------------ coordinator warp
+        const unsigned tagL = (p.epoch << 2) | 1u, tagG = (p.epoch << 2) | 2u;
+        auto zinit = [&](int i) -> float { return p.zi ? p.zi[i] * p.sec[i >> 1].zscale : 0.f; };
+        unsigned it = 0;
+        for (;;) {
+            const unsigned slot = it & 1;
+            if (!mbar_wait(&bar_ticket[it & 3], (it >> 2) & 1, budget, p.status)) break;
+            const long long cur = ring[it & 3];
+            if (cur < 0) break;
+            if (!mbar_wait(&bar_local[slot], (it >> 1) & 1, budget, p.status)) break;
+            const float *abuf = a_buf + slot * W * S;
+            const float acc_i = agg[slot * S + (lane < S ? lane : 0)];
+            float tmp[S];
+            unsigned long long *dcur = p.desc + static_cast<size_t>(cur) * S;
+            float zi_lane = 0.f;
+            if (cur == 0) {
+                zi_lane = zinit(lane < S ? lane : 0);
+            } else {
+                // decoupled lookback over tiles, 32 predecessors per round
+                const long long t_start = clock64();
+                int win = 0;
+                for (;;) {
+                    const long long pred = cur - 1 - 32LL * win - lane;
+                    float v[S];
+                    int st;
+                    if (pred >= 0) {
+                        const unsigned long long *dp = p.desc + static_cast<size_t>(pred) * S;
+                        bool allG = true, allL = true;
+#pragma unroll
+                        for (int i = 0; i < S; ++i) {
+                            const unsigned long long wd = ld_relaxed_b64(dp + i);
+                            const unsigned tg = static_cast<unsigned>(wd >> 32);
+                            allG = allG && (tg == tagG);
+                            allL = allL && (tg == tagL);
+                            v[i] = __uint_as_float(static_cast<unsigned>(wd));
+                        }
+                        st = allG ? 2 : (allL ? 1 : 0);
+                    } else {
+                        st = 2;  // the signal's initial state is the resolved carry of tile -1
+#pragma unroll
+                        for (int i = 0; i < S; ++i) v[i] = (pred == -1) ? zinit(i) : 0.f;
+                    }
+                    const unsigned glob = __ballot_sync(0xffffffffu, st == 2);
+                    const unsigned inv = __ballot_sync(0xffffffffu, st == 0);
+                    const int j = glob ? __ffs(glob) - 1 : 32;
+                    const unsigned need = (j >= 31) ? 0xffffffffu : ((2u << j) - 1u);
+                    if (inv & need) {
+                        if (__any_sync(0xffffffffu, (clock64() - t_start) > budget)) {
+                            if (lane == 0) atomicOr(p.status, kDevErrTimeout);
+                            break;
+                        }
+                        __nanosleep(64);
+                        continue;
+                    }
+                    if (lane > j) {
+#pragma unroll
+                        for (int i = 0; i < S; ++i) v[i] = 0.f;
+                    }
+                    packed_mv<K>(sATl + lane * MS, v, tmp);
+                    float part = reduce_scatter<S, Dm::P2, Dm::SH>(tmp, lane);
+                    part = __shfl_sync(0xffffffffu, part, (lane < S ? lane : 0) << Dm::SH);
+                    if (win == 0) {
+                        zi_lane += part;
+                    } else {
+                        const float *Aw = gATd + win * Dm::FULL;
+                        float y = 0.f;
+                        const int row = lane < S ? lane : 0;
+#pragma unroll
+                        for (int jj = 0; jj < S; ++jj)
+                            y = fmaf(__ldg(Aw + jj * S + row), __shfl_sync(0xffffffffu, part, jj), y);
+                        zi_lane += y;
+                    }
+                    if (j < 32) break;
+                    if (++win > kMaxWin) {
+                        if (lane == 0) atomicOr(p.status, kDevErrTimeout);
+                        break;
+                    }
+                }
+            }
+            if (cur + 1 < p.n_tiles) {
+                float gl = acc_i;  // A_T Z + tile carry
+                const int row = lane < S ? lane : 0;
+#pragma unroll
+                for (int jj = 0; jj < S; ++jj)
+                    gl = fmaf(__ldg(gATd + jj * S + row), __shfl_sync(0xffffffffu, zi_lane, jj), gl);
+                if (lane < S) st_relaxed_b64(dcur + lane, pack_word(tagG, gl));
+            }
+            // incoming state of each group of the tile: Z_0 = Z, Z_{v+1} = A_C Z_v + a_v
+            float *zb = z_buf + slot * W * S;
+#pragma unroll 1
+            for (int v = 0; v < W; ++v) {
+                if (lane < S) zb[v * S + lane] = zi_lane;
+                if (v + 1 < W) zi_lane = lane_mv<S>(sACd, zi_lane, lane) + abuf[v * S + (lane < S ? lane : 0)];
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bar_zready[slot]);
+            ++it;
+        }
+        return;
+    }
+
+    // ---------------------------------------------------------------------- compute warps
+    const int w = warp - 1;
+    float *B0 = rows + w * 2 * kL * P;  // the warp's two row buffers (B0, B0 + 32 P)
+    float *RS = rowst + w * kL * RSP;
+    const bool want_zf = p.zf != nullptr;
+    const long long g_last = p.G - 1;
+    const long long p_last = p.n - 1 - g_last * C;
+    const int lane_last = static_cast<int>(p_last / N);
+    const int m_last = p.m_last;
+
+    // the group's samples, coalesced: chunk j of the lane holds samples 4 (32 j + lane) .. + 3
+    float4 xq[CH];
+    auto load_regs = [&](long long tile) {
+        const long long base = (tile * W + w) * C;
+        const long long avail = p.n - base;
+        if (avail >= C && p.aligned) {
+#pragma unroll
+            for (int j = 0; j < CH; ++j) xq[j] = __ldcs(reinterpret_cast<const float4 *>(p.x + base) + j * 32 + lane);
+        } else {
+#pragma unroll
+            for (int j = 0; j < CH; ++j) {
+                const int off = 4 * (j * 32 + lane);
+                const float *src = p.x + base + off;
+                xq[j].x = (off + 0 < avail) ? __ldcs(src + 0) : 0.f;
+                xq[j].y = (off + 1 < avail) ? __ldcs(src + 1) : 0.f;
+                xq[j].z = (off + 2 < avail) ? __ldcs(src + 2) : 0.f;
+                xq[j].w = (off + 3 < avail) ? __ldcs(src + 3) : 0.f;
+            }
+        }
+    };
+
+    // Correction of the tile of iteration jt, whose particular output is in buffer Y and whose
+    // lanes' scan states are Sl: rows' true states to shared memory, then four samples per lane
+    // across the rows, stored straight to y.
+    auto correct_and_store = [&](long long tile, unsigned jt, const float *Y, const float (&Sl)[S]) -> bool {
+        const unsigned slot = jt & 1;
+        if (!mbar_wait(&bar_zready[slot], (jt >> 1) & 1, budget, p.status)) return false;
+        const long long g = tile * W + w;
+        float st[S];
+#pragma unroll
+        for (int j = 0; j < S; ++j) st[j] = Sl[j];
+        lane_state_mv<K>(sML + lane * MS, z_buf + (slot * W + w) * S, st);
+        if (want_zf && g == g_last && lane == lane_last) {
+            // final state: lane-local state after the last sample plus the transition of the lane's
+            // incoming state over the samples up to it
+            float zt[S];
+            packed_mv_param<K>(p.A_tail, st, zt);
+#pragma unroll
+            for (int s = 0; s < K; ++s) {
+                const float inv = p.sec[s].zscale_inv;
+                p.zf[2 * s] = (zs_tail[2 * s] + zt[2 * s]) * inv;
+                p.zf[2 * s + 1] = (zs_tail[2 * s + 1] + zt[2 * s + 1]) * inv;
+            }
+        }
+        if (g >= p.G) return true;
+#pragma unroll
+        for (int j = 0; j < S; j += 2)
+            *reinterpret_cast<float2 *>(RS + lane * RSP + j) = make_float2(st[j], st[j + 1]);
+        __syncwarp();
+        const int c = lane % CH, rsub = lane / CH;
+        float4 h[S];
+#pragma unroll
+        for (int j = 0; j < S; ++j) h[j] = sH4[c * S + j];
+        const long long base = g * C;
+        const long long avail = p.n - base;
+        const bool full = avail >= C && p.aligned;
+#pragma unroll 2
+        for (int r0 = 0; r0 < kL; r0 += RPS) {
+            const int r = r0 + rsub;
+            float4 v = *reinterpret_cast<const float4 *>(Y + r * P + 4 * c);
+            const float *sr = RS + r * RSP;
+#pragma unroll
+            for (int j = 0; j < S; j += 2) {
+                const float2 z = *reinterpret_cast<const float2 *>(sr + j);
+                v.x = fmaf(h[j].x, z.x, fmaf(h[j + 1].x, z.y, v.x));
+                v.y = fmaf(h[j].y, z.x, fmaf(h[j + 1].y, z.y, v.y));
+                v.z = fmaf(h[j].z, z.x, fmaf(h[j + 1].z, z.y, v.z));
+                v.w = fmaf(h[j].w, z.x, fmaf(h[j + 1].w, z.y, v.w));
+            }
+            const int off = r * N + 4 * c;
+            if (full) {
+                __stcs(reinterpret_cast<float4 *>(p.y + base + off), v);
+            } else {
+                float *dst = p.y + base + off;
+                if (off + 0 < avail) dst[0] = v.x;
+                if (off + 1 < avail) dst[1] = v.y;
+                if (off + 2 < avail) dst[2] = v.z;
+                if (off + 3 < avail) dst[3] = v.w;
+            }
+        }
+        __syncwarp();
+        return true;
+    };
+
+    if (!mbar_wait(&bar_ticket[0], 0, budget, p.status)) return;
+    long long tile = ring[0];
+    if (tile < 0) return;
+    load_regs(tile);
+    unsigned it = 0;
+    long long prev = -1;
+    float Sprev[S];
+#pragma unroll
+    for (int j = 0; j < S; ++j) Sprev[j] = 0.f;
+    bool ok = true;
+    for (;;) {
+        const long long g = tile * W + w;
+        const unsigned slot = it & 1;
+        float *X = B0 + slot * kL * P;  // this tile's rows; the other buffer holds the previous tile
+        // stash the prefetched samples as rows (lane l: samples l N .. l N + N - 1)
+#pragma unroll
+        for (int j = 0; j < CH; ++j) {
+            const int off = 4 * (j * 32 + lane);
+            *reinterpret_cast<float4 *>(X + (off / N) * P + (off % N)) = xq[j];
+        }
+        __syncwarp();
+        if (!mbar_wait(&bar_ticket[(it + 1) & 3], ((it + 1) >> 2) & 1, budget, p.status)) {
+            ok = false;
+            break;
+        }
+        const long long next = ring[(it + 1) & 3];
+        if (next >= 0) load_regs(next);
+
+        float t[S], Sl[S];
+        if (want_zf && g == g_last)
+            lane_particular<K, N, NORM, true>(p, X + lane * P, p.gain, t, m_last, lane == lane_last, zs_tail);
+        else
+            lane_particular<K, N, NORM, false>(p, X + lane * P, p.gain, t, m_last, false, nullptr);
+        lane_scan<K>(p, t, Sl, a_buf + (slot * W + w) * S, lane);
+        {
+            // the last warp of the tile to finish folds the groups' local carries (c = a_0;
+            // c = A_C c + a_v), posts the tile's carry and draws the ticket two tiles ahead
+            __syncwarp();
+            int old = 0;
+            if (lane == 0) {
+                __threadfence_block();
+                old = atomicAdd(&fold_count[slot], 1);
+            }
+            old = __shfl_sync(0xffffffffu, old, 0);
+            if (old == W - 1) {
+                __threadfence_block();
+                const float *abt = a_buf + slot * W * S;
+                const int li = lane < S ? lane : 0;
+                float c = abt[li];
+#pragma unroll 1
+                for (int v = 1; v < W; ++v) c = lane_mv<S>(sACd, c, lane) + abt[v * S + li];
+                if (tile > 0 && lane < S)
+                    st_relaxed_b64(p.desc + static_cast<size_t>(tile) * S + lane, pack_word((p.epoch << 2) | 1u, c));
+                if (lane < S) agg[slot * S + lane] = c;
+                if (lane == 0) {
+                    fold_count[slot] = 0;
+                    ring[(it + 2) & 3] = draw_ticket();
+                    mbar_arrive(&bar_ticket[(it + 2) & 3]);
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bar_local[slot]);
+            }
+        }
+        if (prev >= 0 && !correct_and_store(prev, it - 1, B0 + (slot ^ 1) * kL * P, Sprev)) {
+            ok = false;
+            break;
+        }
+#pragma unroll
+        for (int j = 0; j < S; ++j) Sprev[j] = Sl[j];
+        prev = tile;
+        if (next < 0) break;
+        tile = next;
+        ++it;
+    }
+    if (ok) correct_and_store(prev, it, B0 + (it & 1) * kL * P, Sprev);
+}
+
+template <int K, int N>
+constexpr size_t lane_smem_bytes() {
+    using Dm = LaneDims<K, N>;
+    constexpr int W = kLaneW;
+    return sizeof(float) * (static_cast<size_t>(W) * 2 * kL * (N + 4) + Dm::TAB + W * kL * Dm::RSP +
+                            4 * W * Dm::S + 2 * Dm::S + ((Dm::S + 3) / 4) * 4);
+}
+
+}  // namespace sosk

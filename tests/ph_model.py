@@ -134,3 +134,45 @@ def ph_filter(sos, x, zi=None, N=32, L=32, W=8):
     l_last, m_last = divmod(p_last, N)
     zf = states[(G - 1) * L + l_last, m_last] + np.linalg.matrix_power(M1, m_last + 1) @ true_state[G - 1, l_last]
     return y, zf
+
+
+def particular_skewed_df2(coef, xb, m_cap=None):
+    """The skewed-pass kernel's particular solution of every lane block (rows of xb): direct form II
+    sections (u = x - a1 u[-1] - a2 u[-2], w = b0 u + b1 u[-1] + b2 u[-2]) run skewed, section k
+    taking sample i - k at step i with section k-1's output of step i-1 as input, every step visiting
+    the sections from the last down.  Returns the outputs, the terminal transposed-direct-form-II
+    states converted from the last two u of each section, and (with m_cap) the converted state after
+    sample m_cap."""
+    K = len(coef)
+    nl, N = xb.shape
+    x = xb.astype(np.float64)
+    u1 = np.zeros((K, nl))
+    u2 = np.zeros((K, nl))
+    pipe = np.zeros((K, nl))
+    cap = np.zeros((K, 2, nl))
+    out = np.zeros((nl, N))
+    for i in range(N + K - 1):
+        for k in range(K - 1, -1, -1):
+            m = i - k
+            if m < 0 or m >= N:
+                continue
+            b0, b1, b2, a1, a2 = coef[k]
+            xin = x[:, i] if k == 0 else pipe[k - 1]
+            u = xin - a2 * u2[k] - a1 * u1[k]
+            w = b0 * u + b1 * u1[k] + b2 * u2[k]
+            u2[k], u1[k] = u1[k], u
+            if k == K - 1:
+                out[:, m] = w
+            else:
+                pipe[k] = w
+            if m_cap is not None and m == m_cap:
+                cap[k, 0], cap[k, 1] = u1[k], u2[k]
+
+    def convert(ua, ub):
+        z = np.zeros((nl, 2 * K))
+        for k, (b0, b1, b2, a1, a2) in enumerate(coef):
+            z[:, 2 * k] = (b1 - b0 * a1) * ua[k] + (b2 - b0 * a2) * ub[k]
+            z[:, 2 * k + 1] = (b2 - b0 * a2) * ua[k] + (a1 * b2 - a2 * b1) * ub[k]
+        return z
+
+    return out, convert(u1, u2), (convert(cap[:, 0], cap[:, 1]) if m_cap is not None else None)

@@ -23,7 +23,7 @@ def test_autotune_choices_and_parity():
     for K in (1, 2, 4, 8):
         for n in (1000, 1 << 16, 3 << 20, 1 << 27):
             solver, N = autotune_choice(K, n)
-            assert (solver, N) in ((1, 32), (1, 64), (2, 32)), (K, n, solver, N)
+            assert (solver, N) in ((1, 32), (1, 64), (2, 64)), (K, n, solver, N)
     for K, n in ((1, 70001), (2, 1 << 16), (4, 300000), (8, 1 << 20)):
         sos = designs.butter_lowpass(2 * K, 0.05 if K > 1 else 0.2)
         x = workloads.normal_f32(K, n)

@@ -67,12 +67,15 @@ SIZES = [1, 2, 3, 5, 31, 32, 33, 127, 511, 512, 513, 1023, 1024, 1025, 2047, 204
 
 CARRY_CASCADE, CARRY_SECTION = 1, 2
 SOLVER_CR, SOLVER_PH = 1, 2
-# solver and launch configuration: PH factorization (N = 32, cascade carry); cyclic reduction with
-# the cascade carry at N = 32 and 64, and with per-section carries at N = 32, 64 and 128
-SCHEMES = [{"solver": SOLVER_PH}, {"carry": CARRY_CASCADE, "N": 32}, {"carry": CARRY_CASCADE, "N": 64},
-           {"carry": CARRY_SECTION, "N": 32}, {"carry": CARRY_SECTION, "N": 64},
+# solver and launch configuration: PH factorization (skewed particular pass) at N = 64 and 32;
+# cyclic reduction with the cascade carry at N = 32 and 64, and with per-section carries at N = 32,
+# 64 and 128
+SCHEMES = [{"solver": SOLVER_PH}, {"solver": SOLVER_PH, "N": 32}, {"carry": CARRY_CASCADE, "N": 32},
+           {"carry": CARRY_CASCADE, "N": 64}, {"carry": CARRY_SECTION, "N": 32}, {"carry": CARRY_SECTION, "N": 64},
            {"carry": CARRY_SECTION, "N": 128}]
-SCHEME_IDS = ["ph", "cr-cascade-32", "cr-cascade-64", "cr-section-32", "cr-section-64", "cr-section-128"]
+SCHEME_IDS = ["ph-64", "ph-32", "cr-cascade-32", "cr-cascade-64", "cr-section-32", "cr-section-64",
+              "cr-section-128"]
+PH_W = 7  # groups per PH tile
 # one setting per kernel: PH, cyclic reduction with the cascade carry, with per-section carries
 KERNELS = [{"solver": SOLVER_PH}, {"carry": CARRY_CASCADE}, {"carry": CARRY_SECTION}]
 KERNEL_IDS = ["ph", "cr-cascade", "cr-section"]
@@ -92,8 +95,11 @@ def test_order16_butterworth_sizes(dev, tuning, n):
 def test_every_section_count(dev, K, tuning):
     u = workloads.uniform_f64(100 + K, 3 * K, stream=1).reshape(K, 3)
     sos = designs.random_sections(u)
-    # several tiles and a ragged tail (PH tiles hold 8 groups of 1024 samples)
-    n = 5 * 32 * tuning.get("N", 32) * (2 if tuning.get("solver") == SOLVER_PH else 1) + 123
+    # several tiles and a ragged tail
+    if tuning.get("solver") == SOLVER_PH:
+        n = 3 * PH_W * 32 * tuning.get("N", 64) + 123
+    else:
+        n = 5 * 32 * tuning.get("N", 32) + 123
     x = workloads.normal_f32(200 + K, n)
     zi = np.random.default_rng(K).standard_normal((K, 2)) * 0.1
     _run_check(sos, x, dev, zi=zi, tuning=tuning, random_mix=True)

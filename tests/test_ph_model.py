@@ -42,3 +42,26 @@ def test_coupling_blocks_are_lower_triangular():
     for k in range(K):
         for j in range(k + 1, K):
             assert np.all(M1[2 * k:2 * k + 2, 2 * j:2 * j + 2] == 0.0)
+
+
+@pytest.mark.parametrize("K", [1, 2, 3, 5, 8])
+@pytest.mark.parametrize("unit_b0", [True, False])
+def test_skewed_df2_particular_matches_transposed_form(K, unit_b0):
+    # the skewed-pass kernel's particular solution (direct form II, sections skewed by one sample,
+    # terminal state converted to transposed direct form II) equals the section-by-section
+    # transposed-form particular solution, outputs and states, at the end and after any sample
+    rows = workloads.uniform_f64(20 + K, 5 * K).reshape(K, 5)
+    sos = designs.random_sections(rows[:, :3])
+    if not unit_b0:
+        sos[:, :3] *= 0.5 + rows[:, 3:4]
+    coef = [tuple(r) for r in sos]
+    if unit_b0:
+        coef = [(1.0, b1 / b0, b2 / b0, a1, a2) for (b0, b1, b2, a1, a2) in coef]
+    xb = workloads.normal_f32(40 + K, 6 * 64).reshape(6, 64)
+    w_ref, states = PM.particular(coef, xb)
+    for m_cap in (0, 1, 17, 63):
+        w, t, cap = PM.particular_skewed_df2(coef, xb, m_cap=m_cap)
+        scale = max(1.0, np.abs(states).max())
+        assert np.abs(w - w_ref).max() <= 1e-11 * np.abs(w_ref).max()
+        assert np.abs(t - states[:, -1]).max() <= 1e-11 * scale
+        assert np.abs(cap - states[:, m_cap]).max() <= 1e-11 * scale
