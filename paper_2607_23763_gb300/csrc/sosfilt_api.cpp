@@ -160,6 +160,7 @@ struct LanePass {
     DMat M1;                         // one-sample zero-input transition of the pass's cascade state
     std::vector<sosk::LaneSec> sec;  // [kp]
     std::vector<float> MX;           // coupling blocks of M_N, row-major 2x2, kp (kp - 1) / 2 of them
+    std::vector<float> H;            // [2 kp][N] zero-input output basis
     float *d_tab = nullptr;          // device table block (LaneDims<kp, N>::TAB_GLOBAL floats)
     int tail_m = -1;                 // m_last for which A_tail is cached
     std::vector<float> A_tail;       // packed transition over tail_m + 1 samples
@@ -557,9 +558,9 @@ sos_status build_ph(sos_filter *f) {
 }
 
 // Tables of the skewed-pass PH kernel for one N (32 or 64), in float64, uploaded once.  Layout of
-// the device block as LaneDims<kp, N>: (M_N)^lane [32][stride], (A_T)^lane [32][stride] (packed),
-// A_C dense column-major, the output basis in chunks [N / 4][2 kp][4] (H_j(4 c + q)), A_T dense and
-// (A_T)^(32 w) dense for w = 1..kMaxWin.
+// the device block as LaneDims<kp, N>: (M_N)^lane [32][stride], (A_T)^(Q lane) [32][stride]
+// (packed; Q = kLaneQ), A_C dense column-major, the output basis [2 kp][N] (chunks of four samples),
+// A_T dense, A_T packed [stride], then (A_T)^(32 Q w) dense for w = 1..kMaxWin.
 sos_status build_lane(sos_filter *f, int N, std::vector<LanePass> &out) {
     constexpr int W = sosk::kLaneW;
     out.clear();
@@ -585,7 +586,7 @@ sos_status build_lane(sos_filter *f, int N, std::vector<LanePass> &out) {
             ps.coef[5 * j + 4] = c[4];
         }
         ps.M1 = DMat(S);
-        std::vector<double> H(static_cast<size_t>(S) * N, 0.0);
+        ps.H.assign(static_cast<size_t>(S) * N, 0.f);
         for (int j = 0; j < S; ++j) {
             std::vector<double> z(S, 0.0);
             z[j] = 1.0;
@@ -593,7 +594,8 @@ sos_status build_lane(sos_filter *f, int N, std::vector<LanePass> &out) {
             for (int i = 0; i < S; ++i) ps.M1.at(i, j) = z[i];
             std::vector<double> h(S, 0.0);
             h[j] = 1.0;
-            for (int m = 0; m < N; ++m) H[static_cast<size_t>(j) * N + m] = cascade_step(ps.coef, kp, h, 0.0);
+            for (int m = 0; m < N; ++m)
+                ps.H[static_cast<size_t>(j) * N + m] = static_cast<float>(cascade_step(ps.coef, kp, h, 0.0));
         }
         const DMat MN = dpow(ps.M1, N);
         const DMat AC = dpow(MN, 32);
@@ -629,25 +631,26 @@ sos_status build_lane(sos_filter *f, int N, std::vector<LanePass> &out) {
             }
         const int ms = lane_stride(kp), full = S * S;
         const size_t off_ac = 64 * static_cast<size_t>(ms), off_h = off_ac + full, off_at = off_h + N * S;
-        std::vector<float> tab(off_at + (1 + sosk::kMaxWin) * full, 0.f);
+        const size_t off_atp = off_at + full, off_aw = off_atp + ms;
+        std::vector<float> tab(off_aw + sosk::kMaxWin * full, 0.f);
+        const DMat ATQ = dpow(AT, sosk::kLaneQ);
         DMat L = deye(S), LT = deye(S);
         for (int l = 0; l < 32; ++l) {
             pack_into(L, kp, &tab[static_cast<size_t>(l) * ms]);
             pack_into(LT, kp, &tab[static_cast<size_t>(32 + l) * ms]);
             L = dmul(L, MN);
-            LT = dmul(LT, AT);
+            LT = dmul(LT, ATQ);
         }
         dense_colmajor_into(AC, &tab[off_ac]);
-        for (int c = 0; c < N / 4; ++c)
-            for (int j = 0; j < S; ++j)
-                for (int q = 0; q < 4; ++q)
-                    tab[off_h + (static_cast<size_t>(c) * S + j) * 4 + q] = f32(H[static_cast<size_t>(j) * N + 4 * c + q]);
+        for (int j = 0; j < S; ++j)
+            for (int m = 0; m < N; ++m) tab[off_h + static_cast<size_t>(j) * N + m] = ps.H[static_cast<size_t>(j) * N + m];
         dense_colmajor_into(AT, &tab[off_at]);
-        const DMat AT32 = dpow(AT, 32);
-        DMat Pw = AT32;
+        pack_into(AT, kp, &tab[off_atp]);
+        const DMat ATW = dpow(ATQ, 32);
+        DMat Pw = ATW;
         for (int w = 1; w <= sosk::kMaxWin; ++w) {
-            dense_colmajor_into(Pw, &tab[off_at + static_cast<size_t>(full) * w]);
-            Pw = dmul(Pw, AT32);
+            dense_colmajor_into(Pw, &tab[off_aw + static_cast<size_t>(full) * (w - 1)]);
+            Pw = dmul(Pw, ATW);
         }
         if (cudaMalloc(&ps.d_tab, tab.size() * sizeof(float)) != cudaSuccess) return SOS_ENOMEM;
         if (cudaMemcpy(ps.d_tab, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
@@ -989,6 +992,8 @@ sos_status launch_lane_pass(sos_filter *f, LanePass &ps, const float *x, float *
     p->spin_budget = f->tuning.spin_budget_cycles ? f->tuning.spin_budget_cycles : kDefaultSpinBudget;
     p->aligned = aligned ? 1 : 0;
     p->tab = ps.d_tab;
+    p->trace = f->trace;
+    p->trace_tiles = f->trace_blocks;
     for (int j = 0; j < K; ++j) p->sec[j] = ps.sec[j];
     std::memcpy(p->MX, ps.MX.data(), sizeof(float) * ps.MX.size());
     const long long C = 32LL * N;

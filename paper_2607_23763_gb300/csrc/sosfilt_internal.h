@@ -171,6 +171,7 @@ int ph_blocks_per_sm(int K, bool norm);
 
 // ---- PH-factorization kernel with a skewed direct-form-II particular pass (sosfilt_lane.cuh)
 constexpr int kLaneW = 7;  // compute warps per block, one group each; a tile is kLaneW groups
+constexpr int kLaneQ = 1;  // predecessors per lane and lookback round (rounds of 32 kLaneQ tiles)
 
 // Per-section constants of the skewed-pass kernel, in the kernel's domain (b / b0 and b0 = 1 when
 // normalized; carried state = zscale * true state).
@@ -199,12 +200,19 @@ struct LaneParams {
     int aligned;                // x and y 16-byte aligned
     int m_last;                 // position of the signal's last sample inside its lane
     const float *tab;           // global table block, layout LaneDims<K, N>
+    unsigned long long *trace;  // nullptr, or [n_tiles][kTraceSlots] phase trace (kLaneTrace*)
+    long long trace_tiles;
     LaneSec sec[K];
     // blocks (k, j), j < k, of the lane transition M_N, row-major 2x2 at k (k - 1) / 2 + j
     float4 MX[K > 1 ? K * (K - 1) / 2 : 1];
     float A_tail[2 * K * (K + 1)];  // packed cascade transition over m_last + 1 samples
 };
 
+// Phase trace of the skewed-pass kernel, per tile (global timer, ns): [0] tile + 1; coordinator:
+// [1] tile folded, [2] incoming state resolved, [3] group states posted; first compute warp:
+// [4] iteration start, [5] next ticket known, [6] particular pass done, [7] lane scan done, [8] fold
+// done; correction of the tile: [9] start, [10] group state observed, [11] row states stored,
+// [12] stored; [13] SM id; [14] stash start, [15] input stashed.
 template <int K, int N>
 cudaError_t launch_lane(bool norm, const LaneParams<K> &p, long long grid, cudaStream_t s);
 #define SOSK_DECLARE_LANE(K, N) \

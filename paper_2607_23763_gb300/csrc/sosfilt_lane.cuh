@@ -18,14 +18,16 @@
 //      blocks.  Lane 31's inclusive state is the group's local carry.
 //   3. a coordinator warp folds the tile's local carries, publishes the tile carry, resolves the
 //      tile's incoming 2K-word state by decoupled lookback over tiles (Sec. IV-B, Eq. 25 on the
-//      cascade state) and derives every group's incoming state Z.
+//      cascade state) and derives every group's incoming state Z.  A lookback round covers 32 Q
+//      predecessors (Q per lane, combined by Horner's rule with A_T).
 //   4. homogeneous correction (Eq. 24 once for the whole cascade): lane l's true incoming state is
 //      S_l + (M_N)^l Z, and sample m of its row gains sum_j H_j(m) [S_l + (M_N)^l Z]_j.  The rows'
 //      states go to shared memory and the correction runs across the rows: each lane takes four
-//      consecutive samples of one row, so its 4 x 2K basis values H_j(m) stay in registers and
-//      every corrected float4 leaves in a fully coalesced store.
-// Tile t is corrected after the particular pass of tile t + 1, so the coordinator has one pass to
-// resolve it.  Tiles come from an ascending ticket counter (Sec. IV-A).  The next tile's input is
+//      consecutive samples of one row, so its 4 x 2K basis values H_j(m) stay in registers, the
+//      loop stays small (no unrolled basis in the instruction stream) and every corrected float4
+//      leaves in a fully coalesced store.
+// Tile t is corrected after the particular pass and lane scan of tile t + 1, so the coordinator has
+// one pass to resolve it.  Tiles come from an ascending ticket counter (Sec. IV-A).  The next tile's input is
 // loaded into registers during the pass (coalesced 128-bit loads) and stashed into the warp's free
 // row buffer at the start of the next iteration.
 #pragma once
@@ -43,20 +45,23 @@ struct LaneDims {
     static constexpr int FULL = S * S;
     static constexpr int P2 = S <= 2 ? 2 : S <= 4 ? 4 : S <= 8 ? 8 : 16;
     static constexpr int SH = 5 - (P2 == 2 ? 1 : P2 == 4 ? 2 : P2 == 8 ? 3 : 4);
-    static constexpr int CH = N / 4;   // float4 chunks of a row
+    static constexpr int CH = N / 4;     // float4 chunks of a row
     static constexpr int RPS = 32 / CH;  // rows per step of the column-wise correction
     // row-state pitch: S rounded up to whole 16-byte words, an odd number of them
     static constexpr int S4 = (S + 3) / 4;
     static constexpr int RSP = 4 * ((S4 & 1) ? S4 : S4 + 1);
-    // table block (copied to shared memory up to OFF_AT): (M_N)^lane [32][MS], (A_T)^lane [32][MS],
-    // A_C dense column-major, H chunks [CH][S][4] (H_j(4c + q)); global only: A_T dense and
-    // (A_T)^(32 w) dense for w = 1..kMaxWin
+    // table block (copied to shared memory up to TAB): (M_N)^lane [32][MS], (A_T)^(Q lane) [32][MS]
+    // (Q = kLaneQ predecessors per lane and lookback round), A_C dense column-major, the basis in
+    // chunks [S][CH][4] (H_j(4c + q)), A_T dense, A_T packed [MS]; global only: (A_T)^(32 Q w)
+    // dense for w = 1..kMaxWin
     static constexpr int OFF_ATL = 32 * MS;
     static constexpr int OFF_AC = 64 * MS;
     static constexpr int OFF_H = OFF_AC + FULL;
     static constexpr int OFF_AT = OFF_H + N * S;
-    static constexpr int TAB = OFF_AT;
-    static constexpr int TAB_GLOBAL = OFF_AT + (1 + kMaxWin) * FULL;
+    static constexpr int OFF_ATP = OFF_AT + FULL;
+    static constexpr int TAB = OFF_ATP + MS;
+    static constexpr int OFF_AW = TAB;
+    static constexpr int TAB_GLOBAL = OFF_AW + kMaxWin * FULL;
 };
 
 // One step of section s in direct form II: u = x - a1 u[-1] - a2 u[-2], output b0 u + b1 u[-1] +
@@ -242,17 +247,19 @@ __global__ void __launch_bounds__((kLaneW + 1) * 32, 1) sos_lane_kernel(const __
     float *sML = tab;                                // (M_N)^lane [32][MS]
     float *sATl = tab + Dm::OFF_ATL;                 // (A_T)^lane [32][MS]
     float *sACd = tab + Dm::OFF_AC;                  // A_C dense column-major
-    const float4 *sH4 = reinterpret_cast<const float4 *>(tab + Dm::OFF_H);  // [CH][S] float4
+    const float4 *sH4 = reinterpret_cast<const float4 *>(tab + Dm::OFF_H);  // [S][CH] float4
     float *rowst = tab + Dm::TAB;                    // [W][32][RSP] rows' true incoming states
     float *a_buf = rowst + W * kL * RSP;             // [2][W][S] local carries
     float *z_buf = a_buf + 2 * W * S;                // [2][W][S] incoming states
     float *agg = z_buf + 2 * W * S;                  // [2][S] tile carry under zero incoming state
     float *zs_tail = agg + 2 * S;                    // [S] lane-local state after the last sample
-    const float *gATd = p.tab + Dm::OFF_AT;          // A_T dense (global, L1-resident)
+    const float *sATd = tab + Dm::OFF_AT;            // A_T dense column-major
+    const float *sATp = tab + Dm::OFF_ATP;           // A_T packed
+    const float *gAW = p.tab + Dm::OFF_AW;           // (A_T)^(32 Q w), w = 1.., dense (global)
     // tiles alternate between two slots; the incoming-state barrier has one per slot, so that it
     // never runs two phases ahead of a waiter
-    __shared__ unsigned long long bar_local[2], bar_zready[2], bar_ticket[4];
-    __shared__ long long ring[4];
+    __shared__ unsigned long long bar_local[2], bar_zready[2], bar_ticket[8];
+    __shared__ long long ring[8];
     __shared__ int fold_count[2];
     __shared__ int tickets_exhausted;
 
@@ -282,11 +289,13 @@ __global__ void __launch_bounds__((kLaneW + 1) * 32, 1) sos_lane_kernel(const __
         }
         tickets_exhausted = 0;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) mbar_init(&bar_ticket[i], 1);
-        ring[0] = draw_ticket();
-        ring[1] = draw_ticket();
-        mbar_arrive(&bar_ticket[0]);
-        mbar_arrive(&bar_ticket[1]);
+        for (int i = 0; i < 8; ++i) mbar_init(&bar_ticket[i], 1);
+        // tickets of iterations 0..2; the fold of iteration k draws that of k + 3
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            ring[i] = draw_ticket();
+            mbar_arrive(&bar_ticket[i]);
+        }
     }
     __syncthreads();
 
@@ -297,10 +306,19 @@ __global__ void __launch_bounds__((kLaneW + 1) * 32, 1) sos_lane_kernel(const __
         unsigned it = 0;
         for (;;) {
             const unsigned slot = it & 1;
-            if (!mbar_wait(&bar_ticket[it & 3], (it >> 2) & 1, budget, p.status)) break;
-            const long long cur = ring[it & 3];
+            if (!mbar_wait(&bar_ticket[it & 7], (it >> 3) & 1, budget, p.status)) break;
+            const long long cur = ring[it & 7];
             if (cur < 0) break;
             if (!mbar_wait(&bar_local[slot], (it >> 1) & 1, budget, p.status)) break;
+            unsigned long long *tr =
+                (p.trace && lane == 0 && cur < p.trace_tiles) ? p.trace + static_cast<size_t>(cur) * kTraceSlots : nullptr;
+            if (tr) {
+                unsigned smid;
+                asm volatile("mov.u32 %0, %smid;" : "=r"(smid));
+                tr[0] = static_cast<unsigned long long>(cur) + 1;
+                tr[1] = global_ns();
+                tr[13] = smid;
+            }
             const float *abuf = a_buf + slot * W * S;
             const float acc_i = agg[slot * S + (lane < S ? lane : 0)];
             float tmp[S];
@@ -309,53 +327,85 @@ __global__ void __launch_bounds__((kLaneW + 1) * 32, 1) sos_lane_kernel(const __
             if (cur == 0) {
                 zi_lane = zinit(lane < S ? lane : 0);
             } else {
-                // decoupled lookback over tiles, 32 predecessors per round
+                // decoupled lookback over tiles, 32 Q predecessors per round: lane l takes the
+                // predecessors at distance 32 Q win + Q l + i + 1, i < Q
+                constexpr int Q = kLaneQ;
                 const long long t_start = clock64();
                 int win = 0;
                 for (;;) {
-                    const long long pred = cur - 1 - 32LL * win - lane;
-                    float v[S];
-                    int st;
-                    if (pred >= 0) {
-                        const unsigned long long *dp = p.desc + static_cast<size_t>(pred) * S;
-                        bool allG = true, allL = true;
+                    const long long pbase = cur - 1 - 32LL * Q * win - static_cast<long long>(Q) * lane;
+                    float v[Q][S];
+                    int stq[Q];
 #pragma unroll
-                        for (int i = 0; i < S; ++i) {
-                            const unsigned long long wd = ld_relaxed_b64(dp + i);
-                            const unsigned tg = static_cast<unsigned>(wd >> 32);
-                            allG = allG && (tg == tagG);
-                            allL = allL && (tg == tagL);
-                            v[i] = __uint_as_float(static_cast<unsigned>(wd));
+                    for (int i = 0; i < Q; ++i) {
+                        const long long pred = pbase - i;
+                        if (pred >= 0) {
+                            const unsigned long long *dp = p.desc + static_cast<size_t>(pred) * S;
+                            bool allG = true, allL = true;
+#pragma unroll
+                            for (int q = 0; q < S; q += 2) {
+                                unsigned long long a, b;
+                                ld_relaxed_v2(dp + q, a, b);
+                                const unsigned ta = static_cast<unsigned>(a >> 32), tb = static_cast<unsigned>(b >> 32);
+                                allG = allG && ta == tagG && tb == tagG;
+                                allL = allL && ta == tagL && tb == tagL;
+                                v[i][q] = __uint_as_float(static_cast<unsigned>(a));
+                                v[i][q + 1] = __uint_as_float(static_cast<unsigned>(b));
+                            }
+                            stq[i] = allG ? 2 : (allL ? 1 : 0);
+                        } else {
+                            stq[i] = 2;  // the signal's initial state is the resolved carry of tile -1
+#pragma unroll
+                            for (int q = 0; q < S; ++q) v[i][q] = (pred == -1) ? zinit(q) : 0.f;
                         }
-                        st = allG ? 2 : (allL ? 1 : 0);
-                    } else {
-                        st = 2;  // the signal's initial state is the resolved carry of tile -1
-#pragma unroll
-                        for (int i = 0; i < S; ++i) v[i] = (pred == -1) ? zinit(i) : 0.f;
                     }
-                    const unsigned glob = __ballot_sync(0xffffffffu, st == 2);
-                    const unsigned inv = __ballot_sync(0xffffffffu, st == 0);
+                    int ig = Q;  // the lane's nearest resolved predecessor
+                    bool lane_ok = true;
+#pragma unroll
+                    for (int i = Q - 1; i >= 0; --i) ig = stq[i] == 2 ? i : ig;
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) lane_ok = lane_ok && (i > ig || stq[i] != 0);
+                    const unsigned glob = __ballot_sync(0xffffffffu, ig < Q);
                     const int j = glob ? __ffs(glob) - 1 : 32;
                     const unsigned need = (j >= 31) ? 0xffffffffu : ((2u << j) - 1u);
-                    if (inv & need) {
+                    if (__ballot_sync(0xffffffffu, !lane_ok) & need) {
                         if (__any_sync(0xffffffffu, (clock64() - t_start) > budget)) {
                             if (lane == 0) atomicOr(p.status, kDevErrTimeout);
                             break;
                         }
+                        // a short nap: the successors' lookbacks wait on this tile's result
                         __nanosleep(64);
                         continue;
                     }
-                    if (lane > j) {
+                    // the lane's predecessors up to the nearest resolved one, by Horner's rule:
+                    // acc = sum_i (A_T)^i v_i
+                    float acc[S];
 #pragma unroll
-                        for (int i = 0; i < S; ++i) v[i] = 0.f;
+                    for (int i = 0; i < Q; ++i) {
+                        const bool inc = lane < j || (lane == j && i <= ig);
+                        if (!inc) {
+#pragma unroll
+                            for (int q = 0; q < S; ++q) v[i][q] = 0.f;
+                        }
                     }
-                    packed_mv<K>(sATl + lane * MS, v, tmp);
+#pragma unroll
+                    for (int q = 0; q < S; ++q) acc[q] = v[Q - 1][q];
+#pragma unroll
+                    for (int i = Q - 2; i >= 0; --i) {
+                        float t2[S];
+                        packed_mv<K>(sATp, acc, t2);
+#pragma unroll
+                        for (int q = 0; q < S; ++q) acc[q] = t2[q] + v[i][q];
+                    }
+                    // sum over the lanes of (A_T)^(Q lane) acc_lane: each lane applies its own power,
+                    // then a reduce-scatter leaves word i of the sum in lane i
+                    packed_mv<K>(sATl + lane * MS, acc, tmp);
                     float part = reduce_scatter<S, Dm::P2, Dm::SH>(tmp, lane);
                     part = __shfl_sync(0xffffffffu, part, (lane < S ? lane : 0) << Dm::SH);
                     if (win == 0) {
                         zi_lane += part;
                     } else {
-                        const float *Aw = gATd + win * Dm::FULL;
+                        const float *Aw = gAW + (win - 1) * Dm::FULL;
                         float y = 0.f;
                         const int row = lane < S ? lane : 0;
 #pragma unroll
@@ -364,18 +414,15 @@ __global__ void __launch_bounds__((kLaneW + 1) * 32, 1) sos_lane_kernel(const __
                         zi_lane += y;
                     }
                     if (j < 32) break;
-                    if (++win > kMaxWin) {
+                    if (++win > kMaxWin) {  // predecessors too far behind: report and give up
                         if (lane == 0) atomicOr(p.status, kDevErrTimeout);
                         break;
                     }
                 }
             }
+            if (tr) tr[2] = global_ns();
             if (cur + 1 < p.n_tiles) {
-                float gl = acc_i;  // A_T Z + tile carry
-                const int row = lane < S ? lane : 0;
-#pragma unroll
-                for (int jj = 0; jj < S; ++jj)
-                    gl = fmaf(__ldg(gATd + jj * S + row), __shfl_sync(0xffffffffu, zi_lane, jj), gl);
+                const float gl = lane_mv<S>(sATd, zi_lane, lane) + acc_i;  // A_T Z + tile carry
                 if (lane < S) st_relaxed_b64(dcur + lane, pack_word(tagG, gl));
             }
             // incoming state of each group of the tile: Z_0 = Z, Z_{v+1} = A_C Z_v + a_v
@@ -387,6 +434,7 @@ __global__ void __launch_bounds__((kLaneW + 1) * 32, 1) sos_lane_kernel(const __
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&bar_zready[slot]);
+            if (tr) tr[3] = global_ns();
             ++it;
         }
         return;
@@ -395,13 +443,16 @@ __global__ void __launch_bounds__((kLaneW + 1) * 32, 1) sos_lane_kernel(const __
     // ---------------------------------------------------------------------- compute warps
     const int w = warp - 1;
     float *B0 = rows + w * 2 * kL * P;  // the warp's two row buffers (B0, B0 + 32 P)
-    float *RS = rowst + w * kL * RSP;
     const bool want_zf = p.zf != nullptr;
     const long long g_last = p.G - 1;
     const long long p_last = p.n - 1 - g_last * C;
     const int lane_last = static_cast<int>(p_last / N);
     const int m_last = p.m_last;
 
+    auto wtrace = [&](long long tile, int slot) {
+        if (p.trace && w == 0 && lane == 0 && tile < p.trace_tiles)
+            p.trace[static_cast<size_t>(tile) * kTraceSlots + slot] = global_ns();
+    };
     // the group's samples, coalesced: chunk j of the lane holds samples 4 (32 j + lane) .. + 3
     float4 xq[CH];
     auto load_regs = [&](long long tile) {
@@ -428,7 +479,9 @@ __global__ void __launch_bounds__((kLaneW + 1) * 32, 1) sos_lane_kernel(const __
     // across the rows, stored straight to y.
     auto correct_and_store = [&](long long tile, unsigned jt, const float *Y, const float (&Sl)[S]) -> bool {
         const unsigned slot = jt & 1;
+        wtrace(tile, 9);
         if (!mbar_wait(&bar_zready[slot], (jt >> 1) & 1, budget, p.status)) return false;
+        wtrace(tile, 10);
         const long long g = tile * W + w;
         float st[S];
 #pragma unroll
@@ -447,14 +500,16 @@ __global__ void __launch_bounds__((kLaneW + 1) * 32, 1) sos_lane_kernel(const __
             }
         }
         if (g >= p.G) return true;
+        float *RS = rowst + w * kL * RSP;
 #pragma unroll
         for (int j = 0; j < S; j += 2)
             *reinterpret_cast<float2 *>(RS + lane * RSP + j) = make_float2(st[j], st[j + 1]);
         __syncwarp();
+        wtrace(tile, 11);
         const int c = lane % CH, rsub = lane / CH;
         float4 h[S];
 #pragma unroll
-        for (int j = 0; j < S; ++j) h[j] = sH4[c * S + j];
+        for (int j = 0; j < S; ++j) h[j] = sH4[j * CH + c];
         const long long base = g * C;
         const long long avail = p.n - base;
         const bool full = avail >= C && p.aligned;
@@ -483,6 +538,7 @@ __global__ void __launch_bounds__((kLaneW + 1) * 32, 1) sos_lane_kernel(const __
             }
         }
         __syncwarp();
+        wtrace(tile, 12);
         return true;
     };
 
@@ -500,18 +556,22 @@ __global__ void __launch_bounds__((kLaneW + 1) * 32, 1) sos_lane_kernel(const __
         const long long g = tile * W + w;
         const unsigned slot = it & 1;
         float *X = B0 + slot * kL * P;  // this tile's rows; the other buffer holds the previous tile
+        wtrace(tile, 4);
         // stash the prefetched samples as rows (lane l: samples l N .. l N + N - 1)
+        wtrace(tile, 14);
 #pragma unroll
         for (int j = 0; j < CH; ++j) {
             const int off = 4 * (j * 32 + lane);
             *reinterpret_cast<float4 *>(X + (off / N) * P + (off % N)) = xq[j];
         }
         __syncwarp();
-        if (!mbar_wait(&bar_ticket[(it + 1) & 3], ((it + 1) >> 2) & 1, budget, p.status)) {
+        wtrace(tile, 15);
+        if (!mbar_wait(&bar_ticket[(it + 1) & 7], ((it + 1) >> 3) & 1, budget, p.status)) {
             ok = false;
             break;
         }
-        const long long next = ring[(it + 1) & 3];
+        const long long next = ring[(it + 1) & 7];
+        wtrace(tile, 5);
         if (next >= 0) load_regs(next);
 
         float t[S], Sl[S];
@@ -519,10 +579,12 @@ __global__ void __launch_bounds__((kLaneW + 1) * 32, 1) sos_lane_kernel(const __
             lane_particular<K, N, NORM, true>(p, X + lane * P, p.gain, t, m_last, lane == lane_last, zs_tail);
         else
             lane_particular<K, N, NORM, false>(p, X + lane * P, p.gain, t, m_last, false, nullptr);
+        wtrace(tile, 6);
         lane_scan<K>(p, t, Sl, a_buf + (slot * W + w) * S, lane);
+        wtrace(tile, 7);
         {
             // the last warp of the tile to finish folds the groups' local carries (c = a_0;
-            // c = A_C c + a_v), posts the tile's carry and draws the ticket two tiles ahead
+            // c = A_C c + a_v), posts the tile's carry and draws the ticket three tiles ahead
             __syncwarp();
             int old = 0;
             if (lane == 0) {
@@ -542,13 +604,14 @@ __global__ void __launch_bounds__((kLaneW + 1) * 32, 1) sos_lane_kernel(const __
                 if (lane < S) agg[slot * S + lane] = c;
                 if (lane == 0) {
                     fold_count[slot] = 0;
-                    ring[(it + 2) & 3] = draw_ticket();
-                    mbar_arrive(&bar_ticket[(it + 2) & 3]);
+                    ring[(it + 3) & 7] = draw_ticket();
+                    mbar_arrive(&bar_ticket[(it + 3) & 7]);
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&bar_local[slot]);
             }
         }
+        wtrace(tile, 8);
         if (prev >= 0 && !correct_and_store(prev, it - 1, B0 + (slot ^ 1) * kL * P, Sprev)) {
             ok = false;
             break;
