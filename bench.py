@@ -30,10 +30,19 @@ WN = 0.05
 SEED = 1
 BYTES_PER_SAMPLE = 8  # 4 B read + 4 B written: the algorithmic traffic of the filter (Sec. IV-C, Eq. 28)
 CPU_SAMPLE = 1 << 24  # oracle sample per step of the reference arm
-# DRAM bytes (read + write) of one launch of the timed kernel on the 2^28 workload: an ncu capture
-# of the same kernel on 2^26 samples scaled by 4 (profiles/sos_cascade_order16_2p26_traffic.md).
-# Must be re-captured (or set to None) whenever the kernel changes.
-TRAFFIC_BYTES_2P28 = 1.936e9
+# DRAM bytes (read + write) of one launch of the timed kernel on the 2^28 workload, per (solver, N):
+# an ncu capture of the same kernel on 2^26 samples scaled by 4 (profiles/, named for the kernel).
+# An entry must be re-captured (or removed) whenever its kernel changes.
+TRAFFIC_BYTES_2P28 = {
+    # profiles/sos_lane_order16_2p26_traffic.md: 268,906,240 B read + 211,674,368 B written at 2^26
+    (2, 64): 4 * (268906240 + 211674368),
+}
+KERNEL_NAMES = {
+    (2, 64): "sos_lane_kernel (PH factorization, 8 sections, N = 64 samples per lane, 7 groups per block)",
+    (2, 32): "sos_lane_kernel (PH factorization, 8 sections, N = 32 samples per lane, 7 groups per block)",
+    (1, 32): "sos_cascade_kernel (cyclic reduction, 8 sections, N = 32 samples per lane, 8 groups per block)",
+    (1, 64): "sos_cascade_kernel (cyclic reduction, 8 sections, N = 64 samples per lane, 4 groups per block)",
+}
 
 
 def _peaks():
@@ -193,6 +202,8 @@ def bench_ours(args):
         from paper_2607_23763_gb300 import autotune, autotune_choice
         autotune()
         choice = autotune_choice(ORDER // 2, N_SAMPLES)
+        if choice == (0, 0):
+            choice = None
     tuning = {}
     if args.N:
         tuning["N"] = args.N
@@ -245,6 +256,16 @@ def bench_ours(args):
     e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / e_steps, world, dev)
     e_gss = replica_rate(N_SAMPLES, world, e_ms)
 
+    # the kernel that ran: the autotuner's choice, else the tuning's (the library default is PH at
+    # N = 64; a carry scheme or lookback width selects cyclic reduction, by default at N = 32)
+    if choice:
+        kid = tuple(choice)
+    elif args.solver:
+        kid = (args.solver, args.N or (64 if args.solver == 2 else 32))
+    elif args.carry or args.lbw:
+        kid = (1, args.N or 32)
+    else:
+        kid = (2, args.N or 64)
     hbm_peak, peak_kind = _peaks()
     achieved = BYTES_PER_SAMPLE * N_SAMPLES / (ms_step * 1e-3) / 1e9
     clocks = clk.summary()
@@ -253,22 +274,16 @@ def bench_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "samples": N_SAMPLES, "sections": ORDER // 2,
-                   "N": args.N or (choice[1] if choice else "default"), "L": 32,
-                   "solver": ("PH" if choice[0] == 2 else "CR") if choice else ("PH" if args.solver == 2 else "CR"),
+                   "N": kid[1], "L": 32, "solver": "PH" if kid[0] == 2 else "CR",
                    "autotuned": choice is not None,
                    "l2": "inputs and outputs larger than L2 (1 GiB each)",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak,
-                     # the captured kernel: cyclic reduction, cascade carry, N = 32 (the default and the
-                     # autotuner's choice for this workload)
-                     "traffic": TRAFFIC_BYTES_2P28 if (N_SAMPLES == 1 << 28 and ORDER == 16 and not args.N
-                                                       and not args.carry and not args.solver
-                                                       and (choice is None or choice == (1, 32))) else None,
+                     "traffic": (TRAFFIC_BYTES_2P28.get(kid) if (N_SAMPLES == 1 << 28 and ORDER == 16
+                                                                 and not args.lbw and args.carry != 2) else None),
                      "peak_kind": peak_kind,
-                     "kernel": ("sos_ph_kernel (8 sections, N = 32, 7 groups per block)"
-                                if (choice and choice[0] == 2) or args.solver == 2 else
-                                "sos_cascade_kernel (8 sections, N = 32 samples per lane, 8 groups per block)")},
+                     "kernel": KERNEL_NAMES.get(kid, str(kid))},
         "e2e": {"value": e_gss, "unit": "GS/s", "h2d_bytes_per_step": 4 * N_SAMPLES,
                 "d2h_bytes_per_step": 4 * N_SAMPLES},
         "gpu_launches": args.steps,

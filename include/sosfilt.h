@@ -67,12 +67,15 @@ enum {
 
 /* Solvers of a group's zero-state response (see sos_tuning.solver). */
 enum {
-    SOS_SOLVER_DEFAULT = 0, /* the library's choice: SOS_SOLVER_CR */
+    SOS_SOLVER_DEFAULT = 0, /* the library's choice: SOS_SOLVER_PH, or SOS_SOLVER_CR when the
+                               tuning sets a carry scheme, a lookback width or N = 128 */
     SOS_SOLVER_CR = 1,      /* divide-and-conquer cyclic reduction per section (Sec. II-D, II-E,
                                Eqs. 14-23); both carry schemes */
     SOS_SOLVER_PH = 2       /* PH factorization (Sec. II-C): per-lane particular solutions from zero
-                               state, a lane scan of the whole cascade state and one homogeneous
-                               correction for lane and group states; cascade carry only, N = 32 */
+                               state (the sections skewed one sample apart so that their updates
+                               are independent), a lane scan of the whole cascade state and one
+                               homogeneous correction for lane and group states; cascade carry
+                               only, N = 32 or 64 (default 64) */
 };
 
 /*
@@ -91,8 +94,8 @@ enum {
  *                      round, in units of 32: 1, 2, 4, 8 or 16 (values other than
  *                      the default for N exist for 8-section passes with b0 != 0)
  *   carry              SOS_CARRY_DEFAULT, SOS_CARRY_CASCADE or SOS_CARRY_SECTION
- *   solver             SOS_SOLVER_DEFAULT (= SOS_SOLVER_CR), SOS_SOLVER_CR or SOS_SOLVER_PH;
- *                      SOS_SOLVER_PH takes N = 0 or 32, carry SOS_CARRY_DEFAULT or
+ *   solver             SOS_SOLVER_DEFAULT, SOS_SOLVER_CR or SOS_SOLVER_PH (see SOS_SOLVER_*);
+ *                      SOS_SOLVER_PH takes N = 0, 32 or 64, carry SOS_CARRY_DEFAULT or
  *                      SOS_CARRY_CASCADE and lookback_width 0
  */
 typedef struct {
@@ -347,7 +350,7 @@ sos_status sos_server_replay(sos_server *s, int64_t n_req, const int32_t *stream
  * Autotuner: on the current device, time each candidate launch configuration
  * -- divide-and-conquer cyclic reduction with the cascade carry at N = 32 (8
  * groups per tile) or N = 64 (4 groups per tile), and PH factorization at
- * N = 32 (7 groups per tile); L = 32 threads per group throughout -- for 1 to
+ * N = 64 (7 groups per tile); L = 32 threads per group throughout -- for 1 to
  * 8 sections and lengths 2^16, 2^20, 2^24 and 2^28 (up to 2^max_log2n,
  * 0 = 28), and keep the fastest per (section count, length).  Afterwards every
  * run of a filter created with default tuning (all fields 0) uses the choice

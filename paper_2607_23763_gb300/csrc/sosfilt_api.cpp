@@ -1058,11 +1058,15 @@ sos_status run_lane(sos_filter *f, const float *x, float *y, int64_t n, const fl
     return SOS_OK;
 }
 
-// Solver of a run: the tuning's choice, by default divide-and-conquer cyclic reduction (faster than
-// the PH kernel at every order on GB300: 154 vs 130 GS/s at order 16, 540 vs 430 at order 2).
+// Solver of a run: the tuning's choice; by default PH factorization with the skewed particular
+// pass (faster than cyclic reduction at every order on GB300 at 2^28 samples: 227 vs 154 GS/s at
+// order 16, 606 vs 540 at order 2), unless the tuning asks for what only cyclic reduction has (a
+// carry scheme, a lookback width, N = 128).
 int solver_of(const sos_filter *f) {
     const sos_tuning &t = f->tuning;
-    return t.solver ? t.solver : SOS_SOLVER_CR;
+    if (t.solver) return t.solver;
+    if (t.carry || t.lookback_width || t.N == 128) return SOS_SOLVER_CR;
+    return SOS_SOLVER_PH;
 }
 
 // ---- cascade run with caller-provided scratch (used by sos_filter_run_noalloc only)
