@@ -26,9 +26,6 @@ int cascade_blocks_per_sm(int K, int N, bool norm) {
 }
 int cascade_warps(int N) { return N == 32 ? 8 : 4; }
 size_t cascade_smem(int K, int N) { return N == 32 ? cascade_smem_32(K) : N == 64 ? cascade_smem_64(K) : 0; }
-int ph_blocks_per_sm_a(int K, bool norm);
-int ph_blocks_per_sm_b(int K, bool norm);
-int ph_blocks_per_sm(int K, bool norm) { return K <= 4 ? ph_blocks_per_sm_a(K, norm) : ph_blocks_per_sm_b(K, norm); }
 int lane_blocks_per_sm_n32a(int K, bool norm);
 int lane_blocks_per_sm_n32b(int K, bool norm);
 int lane_blocks_per_sm_n64a(int K, bool norm);
@@ -140,19 +137,6 @@ struct CasTables {
     std::vector<CasPass> passes;
 };
 
-// One pass (<= 8 sections) of the PH-factorization kernel (N = kPhN, tiles of kPhWc groups).
-struct PhPass {
-    int k0 = 0, kp = 0;
-    std::vector<double> coef;      // [kp][5] as the kernel applies them
-    DMat M1;                       // one-sample zero-input transition of the pass's cascade state
-    std::vector<sosk::PhSec> sec;  // [kp]
-    std::vector<float> MX;         // coupling blocks of M_N, row-major 2x2, kp (kp - 1) / 2 of them
-    std::vector<float> H;          // [2 kp][kPhN] zero-input output basis
-    float *d_tab = nullptr;        // device table block (PhDims<kp>::TAB_GLOBAL floats)
-    int tail_m = -1;               // m_last for which A_tail is cached
-    std::vector<float> A_tail;     // packed transition over tail_m + 1 samples
-};
-
 // One pass (<= 8 sections) of the skewed-pass PH kernel (sosfilt_lane.cuh) for one N.
 struct LanePass {
     int k0 = 0, kp = 0, N = 0;
@@ -178,13 +162,10 @@ struct sos_filter {
     sos_tuning tuning{};
     NTables tables[kNumN];
     CasTables cas[2];  // N = 32, 64
-    std::vector<PhPass> ph;  // PH-factorization passes
     std::vector<LanePass> lane[2];  // skewed-pass PH kernel, N = 32 and N = 64
     // workspace
     unsigned long long *d_desc = nullptr;
     size_t desc_groups = 0;  // capacity in groups (per section slot)
-    float2 *d_sring = nullptr;  // PH kernel: lanes' scan states of the tiles in flight, per block
-    size_t sring_bytes = 0;
     unsigned long long *d_ticket = nullptr;
     unsigned long long ticket_base = 0;
     unsigned int epoch = 0;
@@ -460,99 +441,6 @@ sos_status build_cascade(sos_filter *f, int N, CasTables &ct) {
                 return SOS_ECUDA;
         }
         ct.passes.push_back(std::move(ps));
-    }
-    return SOS_OK;
-}
-
-int ph_table_floats(int kp) {
-    const int S = 2 * kp, full = S * S;
-    return 2 * 32 * lane_stride(kp) + full + (1 + sosk::kMaxWin) * full;
-}
-
-// Tables of the PH-factorization kernel, in float64, uploaded once.
-sos_status build_ph(sos_filter *f) {
-    constexpr int N = sosk::kPhN, W = sosk::kPhWc;
-    f->ph.clear();
-    for (int k0 = 0; k0 < f->K; k0 += sosk::kMaxPass) {
-        PhPass ps;
-        ps.k0 = k0;
-        ps.kp = (f->K - k0) < sosk::kMaxPass ? (f->K - k0) : sosk::kMaxPass;
-        const int kp = ps.kp, S = 2 * kp;
-        ps.coef.resize(5 * kp);
-        for (int j = 0; j < kp; ++j) {
-            const double *c = &f->sos[5 * (k0 + j)];
-            double b0 = c[0], b1 = c[1], b2 = c[2];
-            if (f->norm) {
-                b1 /= b0;
-                b2 /= b0;
-                b0 = 1.0;
-            }
-            ps.coef[5 * j + 0] = b0;
-            ps.coef[5 * j + 1] = b1;
-            ps.coef[5 * j + 2] = b2;
-            ps.coef[5 * j + 3] = c[3];
-            ps.coef[5 * j + 4] = c[4];
-        }
-        ps.M1 = DMat(S);
-        ps.H.assign(static_cast<size_t>(S) * N, 0.f);
-        for (int j = 0; j < S; ++j) {
-            std::vector<double> z(S, 0.0);
-            z[j] = 1.0;
-            cascade_step(ps.coef, kp, z, 0.0);
-            for (int i = 0; i < S; ++i) ps.M1.at(i, j) = z[i];
-            std::vector<double> h(S, 0.0);
-            h[j] = 1.0;
-            for (int m = 0; m < N; ++m)
-                ps.H[static_cast<size_t>(j) * N + m] = static_cast<float>(cascade_step(ps.coef, kp, h, 0.0));
-        }
-        const DMat MN = dpow(ps.M1, N);
-        const DMat AC = dpow(MN, 32);
-        const DMat AT = dpow(AC, W);
-        auto f32 = [](double v) { return static_cast<float>(v); };
-        ps.sec.assign(kp, sosk::PhSec{});
-        for (int j = 0; j < kp; ++j) {
-            sosk::PhSec &c = ps.sec[j];
-            c.c0 = float4{f32(ps.coef[5 * j + 0]), f32(ps.coef[5 * j + 1]), f32(ps.coef[5 * j + 2]),
-                          f32(-ps.coef[5 * j + 3])};
-            c.c1 = float4{f32(-ps.coef[5 * j + 4]), f32(f->zscale[k0 + j]), f32(1.0 / f->zscale[k0 + j]), 0.f};
-            // the diagonal block of M_N is the section's own transition T^N; powers by squaring
-            Mat P{MN.at(2 * j, 2 * j), MN.at(2 * j, 2 * j + 1), MN.at(2 * j + 1, 2 * j), MN.at(2 * j + 1, 2 * j + 1)};
-            for (int r = 0; r < 5; ++r) {
-                c.tn[r] = float4{f32(P.a), f32(P.b), f32(P.c), f32(P.d)};
-                P = mul(P, P);
-            }
-        }
-        ps.MX.assign(kp > 1 ? 2 * kp * (kp - 1) : 4, 0.f);
-        for (int k = 1; k < kp; ++k)
-            for (int j = 0; j < k; ++j) {
-                float *b = &ps.MX[4 * (k * (k - 1) / 2 + j)];
-                b[0] = f32(MN.at(2 * k, 2 * j));
-                b[1] = f32(MN.at(2 * k, 2 * j + 1));
-                b[2] = f32(MN.at(2 * k + 1, 2 * j));
-                b[3] = f32(MN.at(2 * k + 1, 2 * j + 1));
-            }
-        const int ms = lane_stride(kp), full = S * S;  // lane stride as in PhDims<kp>::MS
-        std::vector<float> tab(ph_table_floats(kp), 0.f);
-        DMat L = deye(S), LT = deye(S);
-        for (int l = 0; l < 32; ++l) {
-            pack_into(L, kp, &tab[static_cast<size_t>(l) * ms]);
-            pack_into(LT, kp, &tab[static_cast<size_t>(32 + l) * ms]);
-            L = dmul(L, MN);
-            LT = dmul(LT, AT);
-        }
-        float *p_dense = &tab[64 * static_cast<size_t>(ms)];
-        dense_colmajor_into(AC, p_dense);
-        dense_colmajor_into(AT, p_dense + full);
-        const DMat AT32 = dpow(AT, 32);
-        DMat Pw = AT32;
-        for (int w = 1; w <= sosk::kMaxWin; ++w) {
-            dense_colmajor_into(Pw, p_dense + full * (1 + w));
-            Pw = dmul(Pw, AT32);
-        }
-        if (cudaMalloc(&ps.d_tab, tab.size() * sizeof(float)) != cudaSuccess) return SOS_ENOMEM;
-        if (cudaMemcpy(ps.d_tab, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
-            return SOS_ECUDA;
-        f->ph.push_back(std::move(ps));
     }
     return SOS_OK;
 }
@@ -857,111 +745,6 @@ sos_status run_cascade(sos_filter *f, const float *x, float *y, int64_t n, const
             st = launch_cascade_any<64>(ps.kp, f, ps, &f->tables[ti].sec[ps.k0], src, y, n, G, n_tiles, grid,
                                         zi ? zi + 2 * ps.k0 : nullptr, zf ? zf + 2 * ps.k0 : nullptr, ps.k0 == 0,
                                         aligned, s);
-        if (st != SOS_OK) return st;
-        src = y;
-    }
-    return SOS_OK;
-}
-
-// ---- PH-factorization kernel (sosfilt_ph.cuh)
-template <int K>
-sos_status launch_ph_pass(sos_filter *f, PhPass &ps, const float *x, float *y, long long n, long long G,
-                          long long n_tiles, long long grid, const float *zi, float *zf, bool first, bool aligned,
-                          cudaStream_t s) {
-    static_assert(K >= 1 && K <= sosk::kMaxPass, "pass size");
-    constexpr int N = sosk::kPhN;
-    auto p = std::make_unique<sosk::PhParams<K>>();
-    std::memset(p.get(), 0, sizeof(*p));
-    p->x = x;
-    p->y = y;
-    p->n = n;
-    p->G = G;
-    p->n_tiles = n_tiles;
-    p->zi = zi;
-    p->zf = zf;
-    p->gain = first ? static_cast<float>(f->gain) : 1.0f;
-    p->desc = f->d_desc;
-    p->ticket = f->d_ticket;
-    p->ticket_base = f->ticket_base;
-    p->epoch = next_epoch(f, s);
-    p->status = f->d_status;
-    p->spin_budget = f->tuning.spin_budget_cycles ? f->tuning.spin_budget_cycles : kDefaultSpinBudget;
-    p->aligned = aligned ? 1 : 0;
-    p->tab = ps.d_tab;
-    p->sring = f->d_sring;
-    p->trace = f->trace;
-    p->trace_tiles = f->trace_blocks;
-    for (int j = 0; j < K; ++j) p->sec[j] = ps.sec[j];
-    std::memcpy(p->MX, ps.MX.data(), sizeof(float) * ps.MX.size());
-    for (int j = 0; j < 2 * K; ++j)
-        for (int m = 0; m < N; ++m) p->H[j][m] = ps.H[static_cast<size_t>(j) * N + m];
-    const long long C = 32LL * N;
-    const int m_last = static_cast<int>((n - 1 - (G - 1) * C) % N);
-    p->m_last = m_last;
-    if (zf) {
-        if (ps.tail_m != m_last) {
-            ps.A_tail.assign(packed_floats(K), 0.f);
-            pack_into(dpow(ps.M1, m_last + 1), K, ps.A_tail.data());
-            ps.tail_m = m_last;
-        }
-        std::memcpy(p->A_tail, ps.A_tail.data(), sizeof(float) * packed_floats(K));
-    }
-    cudaError_t e = sosk::launch_ph<K>(f->norm, *p, grid, s);
-    if (e != cudaSuccess) return SOS_ECUDA;
-    f->ticket_base += static_cast<unsigned long long>(n_tiles + grid);
-    return SOS_OK;
-}
-
-sos_status launch_ph_any(int K, sos_filter *f, PhPass &ps, const float *x, float *y, long long n, long long G,
-                         long long n_tiles, long long grid, const float *zi, float *zf, bool first, bool aligned,
-                         cudaStream_t s) {
-    switch (K) {
-#define SOSK_CASE(k) \
-    case k: return launch_ph_pass<k>(f, ps, x, y, n, G, n_tiles, grid, zi, zf, first, aligned, s);
-        SOSK_CASE(1) SOSK_CASE(2) SOSK_CASE(3) SOSK_CASE(4) SOSK_CASE(5) SOSK_CASE(6) SOSK_CASE(7) SOSK_CASE(8)
-#undef SOSK_CASE
-        default: return SOS_EINVAL;
-    }
-}
-
-// PH factorization with one carry per tile for the whole cascade, persistent grid.
-sos_status run_ph(sos_filter *f, const float *x, float *y, int64_t n, const float *zi, float *zf, cudaStream_t s) {
-    const long long C = 32LL * sosk::kPhN;
-    const long long W = sosk::kPhWc;
-    const long long G = (n + C - 1) / C;
-    const long long n_tiles = (G + W - 1) / W;
-    sos_status st = ensure_desc(f, G, s);
-    if (st != SOS_OK) return st;
-    const bool aligned = (reinterpret_cast<uintptr_t>(x) % 16 == 0) && (reinterpret_cast<uintptr_t>(y) % 16 == 0);
-    // scan-state ring: [grid][kPhR][kPhWc][K][32] float2 for the largest pass
-    size_t ring_need = 0;
-    for (auto &ps : f->ph) {
-        const int bps = sosk::ph_blocks_per_sm(ps.kp, f->norm);
-        if (bps <= 0) return SOS_ECUDA;
-        const size_t b = static_cast<size_t>(bps) * sm_count(f->device) * sosk::kPhR * sosk::kPhWc * ps.kp * 32 *
-                         sizeof(float2);
-        if (b > ring_need) ring_need = b;
-    }
-    if (ring_need > f->sring_bytes) {
-        if (f->d_sring) {
-            cudaStreamSynchronize(s);
-            cudaFree(f->d_sring);
-            f->d_sring = nullptr;
-            f->sring_bytes = 0;
-        }
-        if (cudaMalloc(&f->d_sring, ring_need) != cudaSuccess) {
-            cudaGetLastError();
-            return SOS_ENOMEM;
-        }
-        f->sring_bytes = ring_need;
-    }
-    const float *src = x;
-    for (auto &ps : f->ph) {
-        const int bps = sosk::ph_blocks_per_sm(ps.kp, f->norm);
-        long long grid = static_cast<long long>(bps) * sm_count(f->device);
-        if (grid > n_tiles) grid = n_tiles;
-        st = launch_ph_any(ps.kp, f, ps, src, y, n, G, n_tiles, grid, zi ? zi + 2 * ps.k0 : nullptr,
-                           zf ? zf + 2 * ps.k0 : nullptr, ps.k0 == 0, aligned, s);
         if (st != SOS_OK) return st;
         src = y;
     }
@@ -1724,7 +1507,6 @@ sos_status sos_filter_create(int n_sections, const double *sos, const float *zi,
             st = SOS_ECUDA;
     }
     for (int i = 0; i < 2 && st == SOS_OK; ++i) st = build_cascade(f, i == 0 ? 32 : 64, f->cas[i]);
-    if (st == SOS_OK) st = build_ph(f);
     for (int i = 0; i < 2 && st == SOS_OK; ++i) st = build_lane(f, i == 0 ? 32 : 64, f->lane[i]);
     if (st == SOS_OK) {
         if (cudaMalloc(&f->d_ticket, sizeof(unsigned long long)) != cudaSuccess ||
@@ -1769,13 +1551,10 @@ sos_status sos_filter_destroy(sos_filter *f) {
             if (ps.d_H) cudaFree(ps.d_H);
             if (ps.d_Mm) cudaFree(ps.d_Mm);
         }
-    for (auto &ps : f->ph)
-        if (ps.d_tab) cudaFree(ps.d_tab);
     for (auto &v : f->lane)
         for (auto &ps : v)
             if (ps.d_tab) cudaFree(ps.d_tab);
     if (f->d_desc) cudaFree(f->d_desc);
-    if (f->d_sring) cudaFree(f->d_sring);
     if (f->d_ticket) cudaFree(f->d_ticket);
     if (f->d_status) cudaFree(f->d_status);
     if (f->d_state) cudaFree(f->d_state);

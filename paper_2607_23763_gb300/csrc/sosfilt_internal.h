@@ -120,55 +120,6 @@ int cascade_blocks_per_sm(int K, int N, bool norm);
 int cascade_warps(int N);       // compute warps (groups) per block
 size_t cascade_smem(int K, int N);
 
-// ---- PH-factorization kernel with one carry per tile for the whole cascade (sosfilt_ph.cuh)
-constexpr int kPhN = 32;   // samples per lane per group
-constexpr int kPhWc = 7;   // compute warps per block, one group each; a tile is kPhWc groups
-constexpr int kPhR = 3;    // tiles in flight per block: tile t is corrected after the pass of t + kPhR - 1
-
-// Per-section constants of the PH pass (copied to shared memory by every thread block).
-struct PhSec {
-    float4 c0;          // b0, b1, b2, -a1 in the kernel's domain (b / b0 and b0 = 1 when normalized)
-    float4 c1;          // -a2, zscale, 1 / zscale, 0 (carried state = zscale * true state)
-    float4 tn[5];       // (T^N)^(2^r), r = 0..4, row-major 2x2, T = [[-a1, 1], [-a2, 0]]
-};
-
-template <int K>
-struct PhParams {
-    const float *x;
-    float *y;
-    long long n, G, n_tiles;    // samples, groups of 32 kPhN samples, tiles of kPhWc groups
-    const float *zi;            // device [K][2] initial state of this pass (true domain) or nullptr
-    float *zf;                  // device [K][2] final state of this pass or nullptr
-    float gain;                 // input multiplier (product of all b0 when normalized; first pass only)
-    unsigned long long *desc;   // [n_tiles][2K] tagged carry words
-    unsigned long long *ticket;
-    unsigned long long ticket_base;
-    unsigned int epoch;
-    int *status;
-    long long spin_budget;
-    int aligned;                // x and y 16-byte aligned
-    int m_last;                 // position of the signal's last sample inside its lane
-    const float *tab;           // global table block, layout PhDims<K>
-    float2 *sring;              // [grid][kPhR][kPhWc][K][32] lanes' scan states of the tiles in flight
-    unsigned long long *trace;  // nullptr, or [n_tiles][kTraceSlots] phase trace
-    long long trace_tiles;
-    PhSec sec[K];
-    // blocks (k, j), j < k, of the lane transition M_N = (one-sample cascade transition)^N,
-    // row-major 2x2 at k (k - 1) / 2 + j; they couple the lane states of different sections
-    float4 MX[K > 1 ? K * (K - 1) / 2 : 1];
-    float H[2 * K][kPhN];           // output at lane sample m of the zero-input cascade from unit state j
-    float A_tail[2 * K * (K + 1)];  // packed cascade transition over m_last + 1 samples
-};
-
-template <int K>
-cudaError_t launch_ph(bool norm, const PhParams<K> &p, long long grid, cudaStream_t s);
-#define SOSK_DECLARE_PH(K) \
-    template <>            \
-    cudaError_t launch_ph<K>(bool norm, const PhParams<K> &p, long long grid, cudaStream_t s);
-SOSK_DECLARE_PH(1) SOSK_DECLARE_PH(2) SOSK_DECLARE_PH(3) SOSK_DECLARE_PH(4)
-SOSK_DECLARE_PH(5) SOSK_DECLARE_PH(6) SOSK_DECLARE_PH(7) SOSK_DECLARE_PH(8)
-int ph_blocks_per_sm(int K, bool norm);
-
 // ---- PH-factorization kernel with a skewed direct-form-II particular pass (sosfilt_lane.cuh)
 constexpr int kLaneW = 7;  // compute warps per block, one group each; a tile is kLaneW groups
 constexpr int kLaneQ = 1;  // predecessors per lane and lookback round (rounds of 32 kLaneQ tiles)
