@@ -126,10 +126,6 @@ struct CasPass {
     float *d_tab = nullptr;    // device table block (CasDims<kp>::TAB floats)
     long long tail_p = -1;     // position for which A_tail is cached
     std::vector<float> A_tail; // packed transition over tail_p + 1 samples
-    // N = kBatchN only: device copies for the multi-signal kernel
-    sosk::SecCoef *d_sec = nullptr;  // [kp] section tables
-    float *d_H = nullptr;            // [2 kp][N] output basis
-    float *d_Mm = nullptr;           // [N][packed] one-sample transition powers M1^(m+1), m < N
 };
 
 struct CasTables {
@@ -146,6 +142,10 @@ struct LanePass {
     std::vector<float> MX;           // coupling blocks of M_N, row-major 2x2, kp (kp - 1) / 2 of them
     std::vector<float> H;            // [2 kp][N] zero-input output basis
     float *d_tab = nullptr;          // device table block (LaneDims<kp, N>::TAB_GLOBAL floats)
+    // N = kBatchN only: device copies for the multi-signal kernel
+    sosk::LaneSec *d_sec = nullptr;  // [kp] section constants
+    float4 *d_MX = nullptr;          // coupling blocks of M_N
+    float *d_Mm = nullptr;           // [N][packed] one-sample transition powers M1^(m+1), m < N
     int tail_m = -1;                 // m_last for which A_tail is cached
     std::vector<float> A_tail;       // packed transition over tail_m + 1 samples
 };
@@ -422,24 +422,6 @@ sos_status build_cascade(sos_filter *f, int N, CasTables &ct) {
         if (cudaMalloc(&ps.d_tab, tab.size() * sizeof(float)) != cudaSuccess) return SOS_ENOMEM;
         if (cudaMemcpy(ps.d_tab, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
             return SOS_ECUDA;
-        if (N == sosk::kBatchN) {
-            const NTables &nt = f->tables[table_index(N)];
-            const int nf = packed_floats(kp);
-            std::vector<float> mm(static_cast<size_t>(N) * nf, 0.f);
-            DMat P = ps.M1;
-            for (int m = 0; m < N; ++m) {
-                pack_into(P, kp, &mm[static_cast<size_t>(m) * nf]);
-                P = dmul(P, ps.M1);
-            }
-            if (cudaMalloc(&ps.d_sec, sizeof(sosk::SecCoef) * kp) != cudaSuccess ||
-                cudaMalloc(&ps.d_H, sizeof(float) * ps.H.size()) != cudaSuccess ||
-                cudaMalloc(&ps.d_Mm, sizeof(float) * mm.size()) != cudaSuccess)
-                return SOS_ENOMEM;
-            if (cudaMemcpy(ps.d_sec, &nt.sec[k0], sizeof(sosk::SecCoef) * kp, cudaMemcpyHostToDevice) != cudaSuccess ||
-                cudaMemcpy(ps.d_H, ps.H.data(), sizeof(float) * ps.H.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-                cudaMemcpy(ps.d_Mm, mm.data(), sizeof(float) * mm.size(), cudaMemcpyHostToDevice) != cudaSuccess)
-                return SOS_ECUDA;
-        }
         ct.passes.push_back(std::move(ps));
     }
     return SOS_OK;
@@ -543,6 +525,23 @@ sos_status build_lane(sos_filter *f, int N, std::vector<LanePass> &out) {
         if (cudaMalloc(&ps.d_tab, tab.size() * sizeof(float)) != cudaSuccess) return SOS_ENOMEM;
         if (cudaMemcpy(ps.d_tab, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
             return SOS_ECUDA;
+        if (N == sosk::kBatchN) {
+            const int nf = packed_floats(kp);
+            std::vector<float> mm(static_cast<size_t>(N) * nf, 0.f);
+            DMat Pm = ps.M1;
+            for (int m = 0; m < N; ++m) {
+                pack_into(Pm, kp, &mm[static_cast<size_t>(m) * nf]);
+                Pm = dmul(Pm, ps.M1);
+            }
+            if (cudaMalloc(&ps.d_sec, sizeof(sosk::LaneSec) * kp) != cudaSuccess ||
+                cudaMalloc(&ps.d_MX, sizeof(float) * ps.MX.size()) != cudaSuccess ||
+                cudaMalloc(&ps.d_Mm, sizeof(float) * mm.size()) != cudaSuccess)
+                return SOS_ENOMEM;
+            if (cudaMemcpy(ps.d_sec, ps.sec.data(), sizeof(sosk::LaneSec) * kp, cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemcpy(ps.d_MX, ps.MX.data(), sizeof(float) * ps.MX.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemcpy(ps.d_Mm, mm.data(), sizeof(float) * mm.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+                return SOS_ECUDA;
+        }
         out.push_back(std::move(ps));
     }
     return SOS_OK;
@@ -1069,8 +1068,6 @@ sos_status run_batch_impl(int n_signals, sos_filter *const *filters, const float
 
     constexpr long long C = 32LL * sosk::kBatchN;
     constexpr long long W = sosk::kBatchW;
-    // the batch kernel reads the N = 32 cascade tables, whose tile transition is A_C^W
-    if (sosk::cascade_warps(sosk::kBatchN) != W) return SOS_EINVAL;
     // classes and sizes
     std::vector<int> cls(n_signals, -1);
     long long cls_sigs[kBatchClasses] = {0}, cls_tiles[kBatchClasses] = {0};
@@ -1156,7 +1153,7 @@ sos_status run_batch_impl(int n_signals, sos_filter *const *filters, const float
         const int c = cls[i];
         if (c < 0) continue;
         sos_filter *f = filters[i];
-        const CasPass &ps = f->cas[0].passes[0];  // N = 32: the batch kernel's tables (read only)
+        const LanePass &ps = f->lane[1][0];  // N = kBatchN: the batch kernel's tables (read only)
         const long long G = (n[i] + C - 1) / C;
         const long long nt = (G + W - 1) / W;
         const long long si = fill_sig[c]++;
@@ -1169,7 +1166,7 @@ sos_status run_batch_impl(int n_signals, sos_filter *const *filters, const float
         b.zi = zi ? zi[i] : nullptr;
         b.zf = zf ? zf[i] : nullptr;
         b.sec = ps.d_sec;
-        b.H = ps.d_H;
+        b.MX = ps.d_MX;
         b.tab = ps.d_tab;
         b.Mm = ps.d_Mm;
         b.gain = static_cast<float>(f->gain);
@@ -1261,7 +1258,6 @@ sos_status plan_create(int n_signals, sos_filter *const *filters, const float *c
     *out = nullptr;
     constexpr long long C = 32LL * sosk::kBatchN;
     constexpr long long W = sosk::kBatchW;
-    if (sosk::cascade_warps(sosk::kBatchN) != W) return SOS_EINVAL;
     int device = filters[0] ? filters[0]->device : -1;
     long long cls_sigs[kBatchClasses] = {0}, cls_tiles[kBatchClasses] = {0};
     std::vector<int> cls(n_signals);
@@ -1295,7 +1291,7 @@ sos_status plan_create(int n_signals, sos_filter *const *filters, const float *c
     for (int i = 0; i < n_signals; ++i) {
         const int c = cls[i];
         sos_filter *f = filters[i];
-        const CasPass &ps = f->cas[0].passes[0];
+        const LanePass &ps = f->lane[1][0];  // N = kBatchN: the batch kernel's tables (read only)
         const long long G = (n[i] + C - 1) / C;
         const long long nt = (G + W - 1) / W;
         const long long si = fill_sig[c]++;
@@ -1308,7 +1304,7 @@ sos_status plan_create(int n_signals, sos_filter *const *filters, const float *c
         b.zi = zi ? zi[i] : nullptr;
         b.zf = zf ? zf[i] : nullptr;
         b.sec = ps.d_sec;
-        b.H = ps.d_H;
+        b.MX = ps.d_MX;
         b.tab = ps.d_tab;
         b.Mm = ps.d_Mm;
         b.gain = static_cast<float>(f->gain);
@@ -1547,13 +1543,14 @@ sos_status sos_filter_destroy(sos_filter *f) {
     for (auto &ct : f->cas)
         for (auto &ps : ct.passes) {
             if (ps.d_tab) cudaFree(ps.d_tab);
-            if (ps.d_sec) cudaFree(ps.d_sec);
-            if (ps.d_H) cudaFree(ps.d_H);
-            if (ps.d_Mm) cudaFree(ps.d_Mm);
         }
     for (auto &v : f->lane)
-        for (auto &ps : v)
+        for (auto &ps : v) {
             if (ps.d_tab) cudaFree(ps.d_tab);
+            if (ps.d_sec) cudaFree(ps.d_sec);
+            if (ps.d_MX) cudaFree(ps.d_MX);
+            if (ps.d_Mm) cudaFree(ps.d_Mm);
+        }
     if (f->d_desc) cudaFree(f->d_desc);
     if (f->d_ticket) cudaFree(f->d_ticket);
     if (f->d_status) cudaFree(f->d_status);

@@ -4,17 +4,18 @@
 // The work of every signal is cut into tiles of W = kBatchW groups of C = 32 N samples
 // (N = kBatchN); the tiles of all signals of the launch form one queue, drawn in ascending order
 // from a ticket counter (Sec. IV-A), so that tile t's predecessors within its signal are held by
-// running or finished blocks.  Each tile is filtered as by the single-signal cascade kernel
-// (sosfilt_cascade.cuh): a zero-state pass per group (divide-and-conquer cyclic reduction per
-// section, Sec. II-E, lanes scanned inside the warp), a coordinator warp that folds the groups'
-// local carries, resolves the tile's incoming 2K-word state by decoupled lookback (Sec. IV-B,
-// Eq. 25 on the cascade state) and derives the groups' incoming states, and the homogeneous
-// correction of Eq. 24 applied once for the cascade.  What changes is that lookback chains are
-// kept per signal (a chain ends at its signal's first tile, whose incoming state is the signal's
-// initial state) and that every per-signal quantity (pointers, length, section tables, output
-// basis, transition tables) comes from the signal's descriptor in global memory.
+// running or finished blocks.  Each tile is filtered as by the single-signal PH kernel
+// (sosfilt_lane.cuh): a skewed direct-form-II particular pass per lane (Sec. II-C), the cascade lane
+// scan, a coordinator warp that folds the groups' local carries, resolves the tile's incoming
+// 2K-word state by decoupled lookback (Sec. IV-B, Eq. 25 on the cascade state) and derives the
+// groups' incoming states, and the homogeneous correction of Eq. 24 applied once for the cascade.
+// What changes is that lookback chains are kept per signal (a chain ends at its signal's first
+// tile, whose incoming state is the signal's initial state); that every per-signal quantity
+// (pointers, length, section constants, transition tables, output basis) comes from the signal's
+// descriptor in global memory, the recurrence coefficients going to registers once per tile; and
+// that the next tile's input is staged by cp.async into a third row buffer of the warp.
 #pragma once
-#include "sosfilt_cascade.cuh"
+#include "sosfilt_lane.cuh"
 
 namespace sosk {
 
@@ -66,20 +67,22 @@ __device__ __forceinline__ float lane_mv_g(const float *__restrict__ A, float xi
 }
 
 template <int K, bool NORM>
-__global__ void __maxnreg__(96) sos_batch_kernel(const __grid_constant__ BatchParams<K> p) {
-    using Dm = CasDims<K>;
-    constexpr int S = Dm::S, MS = Dm::MS, N = kBatchN, W = kBatchW;
+__global__ void __launch_bounds__((kBatchW + 1) * 32, 1) sos_batch_kernel(const __grid_constant__ BatchParams<K> p) {
+    using Dm = LaneDims<K, kBatchN>;
+    constexpr int S = Dm::S, MS = Dm::MS, N = kBatchN, W = kBatchW, CH = Dm::CH, RPS = Dm::RPS, RSP = Dm::RSP;
     constexpr int P = N + 4;  // padded row pitch (floats): conflict-free 128-bit row access
     constexpr int C = N * kL;
+    constexpr int SZ = ((S + 3) / 4) * 4;
     extern __shared__ float4 smem4[];
-    float *rows = reinterpret_cast<float *>(smem4);  // [2][W][32][P]: prefetch X, stash Y
-    float *a_buf = rows + 2 * W * kL * P;            // [2][W][S] local carries of the groups
+    float *rows = reinterpret_cast<float *>(smem4);  // [W][3][32][P]: three row buffers per warp
+    float *rowst = rows + W * 3 * kL * P;            // [W][32][RSP] rows' true incoming states
+    float *a_buf = rowst + W * kL * RSP;             // [2][W][S] local carries of the groups
     float *z_buf = a_buf + 2 * W * S;                // [2][W][S] incoming states of the groups
-    float *zs_tail = z_buf + 2 * W * S;              // [2][S] zero-state final state (a signal's last group)
-    float *agg = zs_tail + 2 * S;                    // [2][S] tile carry under zero incoming state
-    __shared__ unsigned long long bar_local[2], bar_zready[2], bar_ticket[4];
-    __shared__ long long ring[4];
-    __shared__ int ring_sig[4];
+    float *agg = z_buf + 2 * W * S;                  // [2][S] tile carry under zero incoming state
+    float *zs_tail = agg + 2 * S;                    // [2][SZ] lane-local state after a signal's last sample
+    __shared__ unsigned long long bar_local[2], bar_zready[2], bar_ticket[8];
+    __shared__ long long ring[8];
+    __shared__ int ring_sig[8];
     __shared__ int fold_count[2];
     __shared__ int tickets_exhausted;
 
@@ -87,9 +90,9 @@ __global__ void __maxnreg__(96) sos_batch_kernel(const __grid_constant__ BatchPa
     const int warp = threadIdx.x >> 5;
     const long long budget = p.spin_budget;
 
-    // Tickets: tile of iteration k in ring[k & 3] with its signal in ring_sig[k & 3], posted on
-    // bar_ticket[k & 3] (phase (k >> 2) & 1).  Thread 0 draws the first two; afterwards the folding
-    // warp of iteration k draws k + 2.
+    // Tickets: tile of iteration k in ring[k & 7] with its signal in ring_sig[k & 7], posted on
+    // bar_ticket[k & 7] (phase (k >> 3) & 1).  Thread 0 draws the first three; afterwards the folding
+    // warp of iteration k draws k + 3.
     auto draw_ticket = [&](int slot) {
         long long t = -1;
         if (!tickets_exhausted) {
@@ -103,18 +106,19 @@ __global__ void __maxnreg__(96) sos_batch_kernel(const __grid_constant__ BatchPa
         ring_sig[slot] = t >= 0 ? __ldg(p.tile_sig + t) : -1;
     };
     if (threadIdx.x == 0) {
-        mbar_init(&bar_local[0], 1);
-        mbar_init(&bar_local[1], 1);
-        mbar_init(&bar_zready[0], 1);
-        mbar_init(&bar_zready[1], 1);
-        fold_count[0] = fold_count[1] = 0;
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&bar_local[i], 1);
+            mbar_init(&bar_zready[i], 1);
+            fold_count[i] = 0;
+        }
         tickets_exhausted = 0;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) mbar_init(&bar_ticket[i], 1);
-        draw_ticket(0);
-        draw_ticket(1);
-        mbar_arrive(&bar_ticket[0]);
-        mbar_arrive(&bar_ticket[1]);
+        for (int i = 0; i < 8; ++i) mbar_init(&bar_ticket[i], 1);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            draw_ticket(i);
+            mbar_arrive(&bar_ticket[i]);
+        }
     }
     __syncthreads();
 
@@ -123,20 +127,20 @@ __global__ void __maxnreg__(96) sos_batch_kernel(const __grid_constant__ BatchPa
         const unsigned tagL = (p.epoch << 2) | 1u, tagG = (p.epoch << 2) | 2u;
         unsigned it = 0;
         for (;;) {
-            if (!mbar_wait(&bar_ticket[it & 3], (it >> 2) & 1, budget, p.status)) break;
-            const long long cur = ring[it & 3];
+            const unsigned slot = it & 1;
+            if (!mbar_wait(&bar_ticket[it & 7], (it >> 3) & 1, budget, p.status)) break;
+            const long long cur = ring[it & 7];
             if (cur < 0) break;
-            const BatchSig *sg = p.sigs + ring_sig[it & 3];
+            const BatchSig *sg = p.sigs + ring_sig[it & 7];
             const long long tile0 = sg->tile0;
             const float *tab = sg->tab;
-            const float *gATd = tab + Dm::TAB;
             const float *zi = sg->zi;
-            const SecCoef *sec = sg->sec;
+            const LaneSec *sec = sg->sec;
             // initial state of the signal (scaled domain), word i
-            auto zinit = [&](int i) -> float { return zi ? zi[i] * sec[i >> 1].zscale : 0.f; };
-            if (!mbar_wait(&bar_local[it & 1], (it >> 1) & 1, budget, p.status)) break;
-            const float *abuf = a_buf + (it & 1) * W * S;
-            const float acc_i = agg[(it & 1) * S + (lane < S ? lane : 0)];
+            auto zinit = [&](int i) -> float { return zi ? zi[i] * __ldg(&sec[i >> 1].zscale) : 0.f; };
+            if (!mbar_wait(&bar_local[slot], (it >> 1) & 1, budget, p.status)) break;
+            const float *abuf = a_buf + slot * W * S;
+            const float acc_i = agg[slot * S + (lane < S ? lane : 0)];
             float tmp[S];
             unsigned long long *dcur = p.desc + static_cast<size_t>(cur) * S;
             float zi_lane = 0.f;
@@ -154,12 +158,14 @@ __global__ void __maxnreg__(96) sos_batch_kernel(const __grid_constant__ BatchPa
                         const unsigned long long *dp = p.desc + static_cast<size_t>(pred) * S;
                         bool allG = true, allL = true;
 #pragma unroll
-                        for (int i = 0; i < S; ++i) {
-                            const unsigned long long wd = ld_relaxed_b64(dp + i);
-                            const unsigned tg = static_cast<unsigned>(wd >> 32);
-                            allG = allG && (tg == tagG);
-                            allL = allL && (tg == tagL);
-                            v[i] = __uint_as_float(static_cast<unsigned>(wd));
+                        for (int q = 0; q < S; q += 2) {
+                            unsigned long long a, b;
+                            ld_relaxed_v2(dp + q, a, b);
+                            const unsigned ta = static_cast<unsigned>(a >> 32), tb = static_cast<unsigned>(b >> 32);
+                            allG = allG && ta == tagG && tb == tagG;
+                            allL = allL && ta == tagL && tb == tagL;
+                            v[q] = __uint_as_float(static_cast<unsigned>(a));
+                            v[q + 1] = __uint_as_float(static_cast<unsigned>(b));
                         }
                         st = allG ? 2 : (allL ? 1 : 0);
                     } else {
@@ -184,15 +190,13 @@ __global__ void __maxnreg__(96) sos_batch_kernel(const __grid_constant__ BatchPa
                         for (int i = 0; i < S; ++i) v[i] = 0.f;
                     }
                     // sum over the window of (A_T)^k v_k (lane's own power), reduce-scattered
-                    packed_mv_gr<K>(tab + (32 + lane) * MS, v, tmp);
+                    packed_mv_gr<K>(tab + Dm::OFF_ATL + lane * MS, v, tmp);
                     float part = reduce_scatter<S, Dm::P2, Dm::SH>(tmp, lane);
                     part = __shfl_sync(0xffffffffu, part, (lane < S ? lane : 0) << Dm::SH);
-                    if (win == 0) {
+                    if (win == 0)
                         zi_lane += part;
-                    } else {
-                        const float *Aw = gATd + win * Dm::FULL;
-                        zi_lane += lane_mv_g<S>(Aw, part, lane);
-                    }
+                    else
+                        zi_lane += lane_mv_g<S>(tab + Dm::OFF_AW + (win - 1) * Dm::FULL, part, lane);
                     if (j < 32) break;
                     if (++win > kMaxWin) {
                         if (lane == 0) atomicOr(p.status, kDevErrTimeout);
@@ -202,19 +206,19 @@ __global__ void __maxnreg__(96) sos_batch_kernel(const __grid_constant__ BatchPa
             }
             if (cur + 1 < p.n_tiles) {
                 // the resolved carry A_T Z + tile carry (read by the signal's next tile only)
-                const float gl = lane_mv_g<S>(gATd, zi_lane, lane) + acc_i;
+                const float gl = lane_mv_g<S>(tab + Dm::OFF_AT, zi_lane, lane) + acc_i;
                 if (lane < S) st_relaxed_b64(dcur + lane, pack_word(tagG, gl));
             }
-            // incoming state of each group of the tile: Z_0 = Z, Z_{w+1} = A_C Z_w + a_w
-            const float *ACd = tab + 64 * MS;
-            float *zb = z_buf + (it & 1) * W * S;
+            // incoming state of each group of the tile: Z_0 = Z, Z_{v+1} = A_C Z_v + a_v
+            float *zb = z_buf + slot * W * S;
 #pragma unroll 1
-            for (int w = 0; w < W; ++w) {
-                if (lane < S) zb[w * S + lane] = zi_lane;
-                if (w + 1 < W) zi_lane = lane_mv_g<S>(ACd, zi_lane, lane) + abuf[w * S + (lane < S ? lane : 0)];
+            for (int v = 0; v < W; ++v) {
+                if (lane < S) zb[v * S + lane] = zi_lane;
+                if (v + 1 < W)
+                    zi_lane = lane_mv_g<S>(tab + Dm::OFF_AC, zi_lane, lane) + abuf[v * S + (lane < S ? lane : 0)];
             }
             __syncwarp();
-            if (lane == 0) mbar_arrive(&bar_zready[it & 1]);  // one barrier per tile parity
+            if (lane == 0) mbar_arrive(&bar_zready[slot]);  // one barrier per tile parity
             ++it;
         }
         return;
@@ -222,26 +226,26 @@ __global__ void __maxnreg__(96) sos_batch_kernel(const __grid_constant__ BatchPa
 
     // ---------------------------------------------------------------------- compute warps
     const int w = warp - 1;
-    float *X = rows + w * kL * P;
-    float *Y = rows + (W + w) * kL * P;
+    float *B0 = rows + w * 3 * kL * P;  // the warp's three row buffers
+    float *RS = rowst + w * kL * RSP;
 
     // group w of global tile `tile` belongs to signal sg; its index within the signal is
     // (tile - tile0) W + w
-    auto issue_load = [&](long long tile, const BatchSig *sg) {
+    auto issue_load = [&](long long tile, const BatchSig *sg, float *X) {
         const long long g = (tile - sg->tile0) * W + w;
         const long long base = g * C;
         const long long avail = sg->n - base;
         const float *x = sg->x;
         if (avail >= C && sg->aligned) {
 #pragma unroll
-            for (int j = 0; j < N / 4; ++j) {
+            for (int j = 0; j < CH; ++j) {
                 const int off = 4 * (j * 32 + lane);
                 cp_async16(X + (off / N) * P + (off % N), x + base + off);
             }
             cp_async_commit();
         } else {
 #pragma unroll
-            for (int j = 0; j < N / 4; ++j) {
+            for (int j = 0; j < CH; ++j) {
                 const int off = 4 * (j * 32 + lane);
                 float4 v;
                 v.x = (off + 0 < avail) ? __ldcs(x + base + off + 0) : 0.f;
@@ -253,69 +257,75 @@ __global__ void __maxnreg__(96) sos_batch_kernel(const __grid_constant__ BatchPa
         }
     };
 
-    auto correct_and_store = [&](long long tile, int sig, unsigned jt) -> bool {
-        if (!mbar_wait(&bar_zready[jt & 1], (jt >> 1) & 1, budget, p.status)) return false;
+    // Correction of the tile of iteration jt (signal sig), whose particular output is in buffer Y
+    // and whose lanes' scan states are Sl: rows' true states to shared memory, then four samples per
+    // lane across the rows, stored straight to y.
+    auto correct_and_store = [&](long long tile, int sig, unsigned jt, const float *Y, const float (&Sl)[S]) -> bool {
+        const unsigned slot = jt & 1;
+        if (!mbar_wait(&bar_zready[slot], (jt >> 1) & 1, budget, p.status)) return false;
         const BatchSig *sg = p.sigs + sig;
         const long long g = (tile - sg->tile0) * W + w;
         const long long G = sg->G;
-        const float *zb = z_buf + ((jt & 1) * W + w) * S;
-        float dz[S];
-        packed_mv_gs<K>(sg->tab + lane * MS, zb, dz);  // lane's incoming cascade state (M_N)^lane Z
-        float *row = Y + lane * P;
-        const float2 *H = reinterpret_cast<const float2 *>(sg->H);
-        float2 dd[S];
+        float st[S];
+        packed_mv_gs<K>(sg->tab + lane * MS, z_buf + (slot * W + w) * S, st);  // (M_N)^lane Z
 #pragma unroll
-        for (int j = 0; j < S; ++j) dd[j] = make_float2(dz[j], dz[j]);
-#pragma unroll
-        for (int q = 0; q < N / 4; ++q) {
-            const float4 v = *reinterpret_cast<float4 *>(row + 4 * q);
-            float2 e0 = make_float2(v.x, v.y), e1 = make_float2(v.z, v.w);
-#pragma unroll
-            for (int j = 0; j < S; ++j) {
-                e0 = __ffma2_rn(__ldg(H + j * (N / 2) + 2 * q), dd[j], e0);
-                e1 = __ffma2_rn(__ldg(H + j * (N / 2) + 2 * q + 1), dd[j], e1);
-            }
-            *reinterpret_cast<float4 *>(row + 4 * q) = make_float4(e0.x, e0.y, e1.x, e1.y);
-        }
+        for (int j = 0; j < S; ++j) st[j] += Sl[j];
         if (g == G - 1 && sg->zf) {
             const long long p_last = sg->n - 1 - (G - 1) * C;
             if (lane == static_cast<int>(p_last / N)) {
-                // the lane's incoming state from Z is dz = (M_N)^lane Z; carried over the lane's
-                // samples up to the last one: M1^(m_last + 1) dz
+                // final state: lane-local state after the last sample plus the transition of the
+                // lane's incoming state over the samples up to it, M1^(m_last + 1) st
                 float zt[S];
-                packed_mv_gr<K>(sg->Mm + static_cast<int>(p_last % N) * Dm::NF, dz, zt);
-                const float *zs = zs_tail + (jt & 1) * S;
+                packed_mv_gr<K>(sg->Mm + static_cast<int>(p_last % N) * Dm::NF, st, zt);
+                const float *zs = zs_tail + slot * SZ;
                 float *zf = sg->zf;
-                const SecCoef *sec = sg->sec;
 #pragma unroll
                 for (int s = 0; s < K; ++s) {
-                    const float inv = sec[s].zscale_inv;
+                    const float inv = __ldg(&sg->sec[s].zscale_inv);
                     zf[2 * s] = (zs[2 * s] + zt[2 * s]) * inv;
                     zf[2 * s + 1] = (zs[2 * s + 1] + zt[2 * s + 1]) * inv;
                 }
             }
         }
-        if (g < G) {
-            const long long base = g * C;
-            const long long avail = sg->n - base;
-            float *y = sg->y;
-            if (avail >= C && sg->aligned) {
-                fence_proxy_async_smem();
-                bulk_store(y + base + lane * N, row, N * 4);
-                bulk_commit();
-            } else {
-                __syncwarp();
+        if (g >= G) return true;
 #pragma unroll
-                for (int j = 0; j < N / 4; ++j) {
-                    const int off = 4 * (j * 32 + lane);
-                    const float4 v = *reinterpret_cast<const float4 *>(Y + (off / N) * P + (off % N));
-                    if (off + 0 < avail) __stcs(y + base + off + 0, v.x);
-                    if (off + 1 < avail) __stcs(y + base + off + 1, v.y);
-                    if (off + 2 < avail) __stcs(y + base + off + 2, v.z);
-                    if (off + 3 < avail) __stcs(y + base + off + 3, v.w);
-                }
+        for (int j = 0; j < S; j += 2)
+            *reinterpret_cast<float2 *>(RS + lane * RSP + j) = make_float2(st[j], st[j + 1]);
+        __syncwarp();
+        const int c = lane % CH, rsub = lane / CH;
+        const float4 *H4 = reinterpret_cast<const float4 *>(sg->tab + Dm::OFF_H);
+        float4 h[S];
+#pragma unroll
+        for (int j = 0; j < S; ++j) h[j] = __ldg(H4 + j * CH + c);
+        const long long base = g * C;
+        const long long avail = sg->n - base;
+        const bool full = avail >= C && sg->aligned;
+        float *y = sg->y;
+#pragma unroll 2
+        for (int r0 = 0; r0 < kL; r0 += RPS) {
+            const int r = r0 + rsub;
+            float4 v = *reinterpret_cast<const float4 *>(Y + r * P + 4 * c);
+            const float *sr = RS + r * RSP;
+#pragma unroll
+            for (int j = 0; j < S; j += 2) {
+                const float2 z = *reinterpret_cast<const float2 *>(sr + j);
+                v.x = fmaf(h[j].x, z.x, fmaf(h[j + 1].x, z.y, v.x));
+                v.y = fmaf(h[j].y, z.x, fmaf(h[j + 1].y, z.y, v.y));
+                v.z = fmaf(h[j].z, z.x, fmaf(h[j + 1].z, z.y, v.z));
+                v.w = fmaf(h[j].w, z.x, fmaf(h[j + 1].w, z.y, v.w));
+            }
+            const int off = r * N + 4 * c;
+            if (full) {
+                __stcs(reinterpret_cast<float4 *>(y + base + off), v);
+            } else {
+                float *dst = y + base + off;
+                if (off + 0 < avail) __stcs(dst + 0, v.x);
+                if (off + 1 < avail) __stcs(dst + 1, v.y);
+                if (off + 2 < avail) __stcs(dst + 2, v.z);
+                if (off + 3 < avail) __stcs(dst + 3, v.w);
             }
         }
+        __syncwarp();
         return true;
     };
 
@@ -323,103 +333,97 @@ __global__ void __maxnreg__(96) sos_batch_kernel(const __grid_constant__ BatchPa
     long long tile = ring[0];
     int sig = ring_sig[0];
     if (tile < 0) return;
-    issue_load(tile, p.sigs + sig);
+    issue_load(tile, p.sigs + sig, B0);
     unsigned it = 0;
     long long prev = -1;
     int prev_sig = -1;
+    float Sprev[S];
+#pragma unroll
+    for (int j = 0; j < S; ++j) Sprev[j] = 0.f;
     bool ok = true;
+    int cur_buf = 0;  // buffer of this iteration's tile; the next tile goes to (cur_buf + 1) % 3
     for (;;) {
+        const unsigned slot = it & 1;
         const BatchSig *sg = p.sigs + sig;
         const long long g = (tile - sg->tile0) * W + w;
         const long long G = sg->G;
+        float *X = B0 + cur_buf * kL * P;
+        const int nxt_buf = cur_buf == 2 ? 0 : cur_buf + 1;
+        const int prv_buf = cur_buf == 0 ? 2 : cur_buf - 1;
         cp_async_wait_all();
         __syncwarp();
-        float2 r[N / 2];
-#pragma unroll
-        for (int j = 0; j < N / 4; ++j) {
-            const float4 v = *reinterpret_cast<const float4 *>(X + lane * P + 4 * j);
-            r[2 * j + 0] = make_float2(v.x, v.y);
-            r[2 * j + 1] = make_float2(v.z, v.w);
-        }
-        if (NORM) {
-            const float gn = sg->gain;
-            const float2 gg = make_float2(gn, gn);
-#pragma unroll
-            for (int j = 0; j < N / 2; ++j) r[j] = __fmul2_rn(r[j], gg);
-        }
-        __syncwarp();
-        if (!mbar_wait(&bar_ticket[(it + 1) & 3], ((it + 1) >> 2) & 1, budget, p.status)) {
+        if (!mbar_wait(&bar_ticket[(it + 1) & 7], ((it + 1) >> 3) & 1, budget, p.status)) {
             ok = false;
             break;
         }
-        const long long next = ring[(it + 1) & 3];
-        const int next_sig = ring_sig[(it + 1) & 3];
-        if (next >= 0) issue_load(next, p.sigs + next_sig);
+        const long long next = ring[(it + 1) & 7];
+        const int next_sig = ring_sig[(it + 1) & 7];
+        if (next >= 0) issue_load(next, p.sigs + next_sig, B0 + nxt_buf * kL * P);
 
+        float t[S], Sl[S];
         {
-            const bool cap = (g == G - 1) && sg->zf != nullptr;
+            const RegSecs<K, NORM> cs(sg->sec, sg->MX);
             const long long p_last = sg->n - 1 - (G - 1) * C;
-            cascade_zero_state<K, N, NORM>(r, sg->sec, a_buf + ((it & 1) * W + w) * S, lane,
-                                           cap && lane == static_cast<int>(p_last / N), static_cast<int>(p_last % N),
-                                           zs_tail + (it & 1) * S);
+            if (g == G - 1 && sg->zf)
+                lane_particular<K, N, NORM, true>(cs, X + lane * P, sg->gain, t, static_cast<int>(p_last % N),
+                                                  lane == static_cast<int>(p_last / N), zs_tail + slot * SZ);
+            else
+                lane_particular<K, N, NORM, false>(cs, X + lane * P, sg->gain, t, 0, false, nullptr);
+            lane_scan<K>(cs, t, Sl, a_buf + (slot * W + w) * S, lane);
         }
         {
             // the last warp of the tile to finish folds the groups' local carries (c = a_0;
-            // c = A_C c + a_w), posts the tile's carry and draws the ticket two tiles ahead
+            // c = A_C c + a_v), posts the tile's carry and draws the ticket three tiles ahead
             __syncwarp();
             int old = 0;
             if (lane == 0) {
                 __threadfence_block();
-                old = atomicAdd(&fold_count[it & 1], 1);
+                old = atomicAdd(&fold_count[slot], 1);
             }
             old = __shfl_sync(0xffffffffu, old, 0);
             if (old == W - 1) {
                 __threadfence_block();
-                const float *ab = a_buf + (it & 1) * W * S;
-                const float *ACd = sg->tab + 64 * MS;
+                const float *ab = a_buf + slot * W * S;
+                const float *ACd = sg->tab + Dm::OFF_AC;
                 const int li = lane < S ? lane : 0;
                 float c = ab[li];
 #pragma unroll 1
                 for (int v = 1; v < W; ++v) c = lane_mv_g<S>(ACd, c, lane) + ab[v * S + li];
                 if (tile > sg->tile0 && lane < S)
                     st_relaxed_b64(p.desc + static_cast<size_t>(tile) * S + lane, pack_word((p.epoch << 2) | 1u, c));
-                if (lane < S) agg[(it & 1) * S + lane] = c;
+                if (lane < S) agg[slot * S + lane] = c;
                 if (lane == 0) {
-                    fold_count[it & 1] = 0;
-                    draw_ticket((it + 2) & 3);
-                    mbar_arrive(&bar_ticket[(it + 2) & 3]);
+                    fold_count[slot] = 0;
+                    draw_ticket((it + 3) & 7);
+                    mbar_arrive(&bar_ticket[(it + 3) & 7]);
                 }
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&bar_local[it & 1]);
+                if (lane == 0) mbar_arrive(&bar_local[slot]);
             }
         }
-
-        if (prev >= 0 && !correct_and_store(prev, prev_sig, it - 1)) {
+        if (prev >= 0 && !correct_and_store(prev, prev_sig, it - 1, B0 + prv_buf * kL * P, Sprev)) {
             ok = false;
             break;
         }
-        bulk_wait_read0();
-        __syncwarp();
 #pragma unroll
-        for (int j = 0; j < N / 4; ++j)
-            *reinterpret_cast<float4 *>(Y + lane * P + 4 * j) =
-                make_float4(r[2 * j].x, r[2 * j].y, r[2 * j + 1].x, r[2 * j + 1].y);
-        __syncwarp();
+        for (int j = 0; j < S; ++j) Sprev[j] = Sl[j];
         prev = tile;
         prev_sig = sig;
         if (next < 0) break;
         tile = next;
         sig = next_sig;
+        cur_buf = nxt_buf;
         ++it;
     }
-    if (ok) correct_and_store(prev, prev_sig, it);
-    bulk_wait0();
+    if (ok) correct_and_store(prev, prev_sig, it, B0 + cur_buf * kL * P, Sprev);
+    cp_async_wait_all();
 }
 
 template <int K>
 constexpr size_t batch_smem_bytes() {
-    using Dm = CasDims<K>;
-    return sizeof(float) * (static_cast<size_t>(2) * kBatchW * kL * (kBatchN + 4) + 4 * kBatchW * Dm::S + 4 * Dm::S);
+    using Dm = LaneDims<K, kBatchN>;
+    return sizeof(float) * (static_cast<size_t>(kBatchW) * 3 * kL * (kBatchN + 4) + kBatchW * kL * Dm::RSP +
+                            4 * kBatchW * Dm::S + 2 * Dm::S + 2 * ((Dm::S + 3) / 4) * 4);
 }
 
 }  // namespace sosk

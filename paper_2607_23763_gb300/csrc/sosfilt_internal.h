@@ -177,10 +177,10 @@ SOSK_DECLARE_LANE_N(64)
 // Thread blocks of the skewed-pass kernel that fit on one SM (0 if unavailable).
 int lane_blocks_per_sm(int K, int N, bool norm);
 
-// ---- multi-signal persistent kernel (sosfilt_batch.cuh): the cascade-carry cyclic-reduction
-// kernel over a global queue of (signal, tile) work items
-constexpr int kBatchN = 32;  // samples per lane
-constexpr int kBatchW = 8;   // groups (compute warps) per tile (the N = 32 tables of the cascade kernel: same W)
+// ---- multi-signal persistent kernel (sosfilt_batch.cuh): the PH kernel with a skewed particular
+// pass over a global queue of (signal, tile) work items
+constexpr int kBatchN = 64;      // samples per lane
+constexpr int kBatchW = kLaneW;  // groups (compute warps) per tile: the N = 64 tables of the PH kernel
 
 // One signal of a batch (device array, built by the host for each batched run).
 struct BatchSig {
@@ -190,9 +190,9 @@ struct BatchSig {
     long long tile0;       // first global tile of the signal; its tiles are tile0 .. tile0 + ceil(G / W) - 1
     const float *zi;       // device [K][2] initial state (true domain) or nullptr
     float *zf;             // device [K][2] final state or nullptr
-    const SecCoef *sec;    // device [K] section tables for N = kBatchN
-    const float *H;        // device [2K][kBatchN] zero-input output basis
-    const float *tab;      // device table block (CasDims<K>::TAB_GLOBAL floats)
+    const LaneSec *sec;    // device [K] section constants for N = kBatchN
+    const float4 *MX;      // device coupling blocks of M_N (as LaneParams::MX)
+    const float *tab;      // device table block (LaneDims<K, kBatchN>::TAB_GLOBAL floats)
     const float *Mm;       // device [kBatchN][2K(K+1)] packed one-sample transition powers M1^(m+1)
     float gain;            // input multiplier (product of the b0 when normalized)
     int aligned;           // x and y 16-byte aligned

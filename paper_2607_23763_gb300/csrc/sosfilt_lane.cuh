@@ -64,14 +64,48 @@ struct LaneDims {
     static constexpr int TAB_GLOBAL = OFF_AW + kMaxWin * FULL;
 };
 
-// One step of section s in direct form II: u = x - a1 u[-1] - a2 u[-2], output b0 u + b1 u[-1] +
-// b2 u[-2] (the history is updated in place).  The a2 term is taken first, so only one FMA follows
-// the arrival of u[-1] on the recurrence.
+// Section constants as the passes read them.  ParamSecs: the kernel parameters of a single-signal
+// launch (compile-time section index: constant-bank operands).  RegSecs: one signal of a batch, the
+// recurrence coefficients loaded into registers once per tile and the rest read through the
+// read-only cache.
+template <int K>
+struct ParamSecs {
+    const LaneParams<K> &p;
+    __device__ __forceinline__ float4 c(int s) const { return p.sec[s].c; }
+    __device__ __forceinline__ float b0(int s) const { return p.sec[s].b0; }
+    __device__ __forceinline__ float4 g(int s) const { return p.sec[s].g; }
+    __device__ __forceinline__ float4 tn(int s, int r) const { return p.sec[s].tn[r]; }
+    __device__ __forceinline__ float4 mx(int i) const { return p.MX[i]; }
+};
+
+template <int K, bool NORM>
+struct RegSecs {
+    const LaneSec *sec;
+    const float4 *MX;
+    float4 cc[K];
+    float bb[K];
+    __device__ __forceinline__ RegSecs(const LaneSec *s_, const float4 *mx_) : sec(s_), MX(mx_) {
+#pragma unroll
+        for (int s = 0; s < K; ++s) {
+            cc[s] = __ldg(&sec[s].c);
+            bb[s] = NORM ? 1.f : __ldg(&sec[s].b0);
+        }
+    }
+    __device__ __forceinline__ float4 c(int s) const { return cc[s]; }
+    __device__ __forceinline__ float b0(int s) const { return bb[s]; }
+    __device__ __forceinline__ float4 g(int s) const { return __ldg(&sec[s].g); }
+    __device__ __forceinline__ float4 tn(int s, int r) const { return __ldg(&sec[s].tn[r]); }
+    __device__ __forceinline__ float4 mx(int i) const { return __ldg(MX + i); }
+};
+
+// One step of a section in direct form II: u = x - a1 u[-1] - a2 u[-2], output b0 u + b1 u[-1] +
+// b2 u[-2] (the history is updated in place); c = (b1, b2, -a1, -a2).  The a2 term is taken first,
+// so only one FMA follows the arrival of u[-1] on the recurrence.
 template <bool NORM>
-__device__ __forceinline__ float df2_step(const LaneSec &c, float &u1, float &u2, float x) {
-    const float t = fmaf(c.c.w, u2, x);
-    const float u = fmaf(c.c.z, u1, t);
-    const float w = fmaf(c.c.x, u1, fmaf(c.c.y, u2, NORM ? u : c.b0 * u));
+__device__ __forceinline__ float df2_step(const float4 c, float b0, float &u1, float &u2, float x) {
+    const float t = fmaf(c.w, u2, x);
+    const float u = fmaf(c.z, u1, t);
+    const float w = fmaf(c.x, u1, fmaf(c.y, u2, NORM ? u : b0 * u));
     u2 = u1;
     u1 = u;
     return w;
@@ -80,8 +114,8 @@ __device__ __forceinline__ float df2_step(const LaneSec &c, float &u1, float &u2
 // Particular solution of the lane's row (N samples, in place) through all K sections from zero
 // state, sections skewed by one sample each; t receives the terminal state (transposed direct form
 // II).  With CAPTURE, the lane with cap_lane set writes its state after sample m_last to cap.
-template <int K, int N, bool NORM, bool CAPTURE>
-__device__ __forceinline__ void lane_particular(const LaneParams<K> &p, float *row, float gain, float (&t)[2 * K],
+template <int K, int N, bool NORM, bool CAPTURE, class Secs>
+__device__ __forceinline__ void lane_particular(const Secs &cs, float *row, float gain, float (&t)[2 * K],
                                                 int m_last, bool cap_lane, float *cap) {
     constexpr int D = K - 1;             // skew of the last section
     constexpr int R0 = (4 - (D & 3)) & 3;  // a step group's first output sits R0 samples into its block
@@ -110,7 +144,7 @@ __device__ __forceinline__ void lane_particular(const LaneParams<K> &p, float *r
 #pragma unroll
             for (int s = K - 1; s >= 0; --s) {
                 const float xin = (s == 0) ? (NORM ? xs[j] * gain : xs[j]) : pipe[s - 1];
-                const float w = df2_step<NORM>(p.sec[s], u1[s], u2[s], xin);
+                const float w = df2_step<NORM>(cs.c(s), cs.b0(s), u1[s], u2[s], xin);
                 if (s == K - 1)
                     out[j] = w;
                 else
@@ -142,7 +176,7 @@ __device__ __forceinline__ void lane_particular(const LaneParams<K> &p, float *r
         for (int e = 0; e < D; ++e) {
 #pragma unroll
             for (int s = K - 1; s >= e + 1; --s) {
-                const float w = df2_step<NORM>(p.sec[s], u1[s], u2[s], pipe[s - 1]);
+                const float w = df2_step<NORM>(cs.c(s), cs.b0(s), u1[s], u2[s], pipe[s - 1]);
                 if (s == K - 1)
                     tail[R0 + e] = w;
                 else
@@ -164,7 +198,7 @@ __device__ __forceinline__ void lane_particular(const LaneParams<K> &p, float *r
     // transposed direct form II state from the last two u values of every section
 #pragma unroll
     for (int s = 0; s < K; ++s) {
-        const float4 g = p.sec[s].g;
+        const float4 g = cs.g(s);
         t[2 * s] = fmaf(g.x, u1[s], g.y * u2[s]);
         t[2 * s + 1] = fmaf(g.z, u1[s], g.w * u2[s]);
     }
@@ -172,7 +206,7 @@ __device__ __forceinline__ void lane_particular(const LaneParams<K> &p, float *r
         if (cap_lane) {
 #pragma unroll
             for (int s = 0; s < K; ++s) {
-                const float4 g = p.sec[s].g;
+                const float4 g = cs.g(s);
                 cap[2 * s] = fmaf(g.x, cu1[s], g.y * cu2[s]);
                 cap[2 * s + 1] = fmaf(g.z, cu1[s], g.w * cu2[s]);
             }
@@ -182,15 +216,15 @@ __device__ __forceinline__ void lane_particular(const LaneParams<K> &p, float *r
 
 // Cascade lane scan: from the lanes' terminal particular states t, the lane's exclusive incoming
 // state S (relative to zero group state) and, in lane 31, the group's local carry a_out.
-template <int K>
-__device__ __forceinline__ void lane_scan(const LaneParams<K> &p, const float (&t)[2 * K], float (&S)[2 * K],
-                                          float *a_out, int lane) {
+template <int K, class Secs>
+__device__ __forceinline__ void lane_scan(const Secs &cs, const float (&t)[2 * K], float (&S)[2 * K], float *a_out,
+                                          int lane) {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         float u1 = t[2 * k], u2 = t[2 * k + 1];
 #pragma unroll
         for (int j = 0; j < k; ++j) {
-            const float4 b = p.MX[k * (k - 1) / 2 + j];
+            const float4 b = cs.mx(k * (k - 1) / 2 + j);
             u1 = fmaf(b.x, S[2 * j], fmaf(b.y, S[2 * j + 1], u1));
             u2 = fmaf(b.z, S[2 * j], fmaf(b.w, S[2 * j + 1], u2));
         }
@@ -198,7 +232,7 @@ __device__ __forceinline__ void lane_scan(const LaneParams<K> &p, const float (&
         for (int r = 0; r < 5; ++r) {
             const float o1 = __shfl_up_sync(0xffffffffu, u1, 1 << r);
             const float o2 = __shfl_up_sync(0xffffffffu, u2, 1 << r);
-            const float4 tn = p.sec[k].tn[r];
+            const float4 tn = cs.tn(k, r);
             if (lane >= (1 << r)) {
                 u1 = fmaf(tn.x, o1, fmaf(tn.y, o2, u1));
                 u2 = fmaf(tn.z, o1, fmaf(tn.w, o2, u2));
@@ -575,12 +609,13 @@ __global__ void __launch_bounds__((kLaneW + 1) * 32, 1) sos_lane_kernel(const __
         if (next >= 0) load_regs(next);
 
         float t[S], Sl[S];
+        const ParamSecs<K> cs{p};
         if (want_zf && g == g_last)
-            lane_particular<K, N, NORM, true>(p, X + lane * P, p.gain, t, m_last, lane == lane_last, zs_tail);
+            lane_particular<K, N, NORM, true>(cs, X + lane * P, p.gain, t, m_last, lane == lane_last, zs_tail);
         else
-            lane_particular<K, N, NORM, false>(p, X + lane * P, p.gain, t, m_last, false, nullptr);
+            lane_particular<K, N, NORM, false>(cs, X + lane * P, p.gain, t, m_last, false, nullptr);
         wtrace(tile, 6);
-        lane_scan<K>(p, t, Sl, a_buf + (slot * W + w) * S, lane);
+        lane_scan<K>(cs, t, Sl, a_buf + (slot * W + w) * S, lane);
         wtrace(tile, 7);
         {
             // the last warp of the tile to finish folds the groups' local carries (c = a_0;
