@@ -268,6 +268,13 @@ def bench_ours(args):
         kid = (2, args.N or 64)
     hbm_peak, peak_kind = _peaks()
     achieved = BYTES_PER_SAMPLE * N_SAMPLES / (ms_step * 1e-3) / 1e9
+    # the FP32 roof the method meets first at high order: its FMAs per sample (PH: 4K for the
+    # particular pass with b0 = 1 plus 2K for the correction; cyclic reduction: 8K + 2K, Sec. IV-C)
+    # against 152 SMs x 128 FP32 lanes x the maximum SM clock (one FMA per lane per cycle)
+    K = ORDER // 2
+    fma_per_sample = 6 * K if kid[0] == 2 else 10 * K
+    alu_peak = 152 * 128 * 2.070e9 / 1e12
+    alu_achieved = fma_per_sample * N_SAMPLES / (ms_step * 1e-3) / 1e12
     clocks = clk.summary()
     line = {
         "metric": "GS/s", "value": gss, "unit": "GS/s", "n_gpus": world, "steps": args.steps,
@@ -284,6 +291,9 @@ def bench_ours(args):
                                                                  and not args.lbw and args.carry != 2) else None),
                      "peak_kind": peak_kind,
                      "kernel": KERNEL_NAMES.get(kid, str(kid))},
+        "roofline_alu": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "TFMA/s",
+                         "frac": alu_achieved / alu_peak, "fma_per_sample": fma_per_sample,
+                         "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz"},
         "e2e": {"value": e_gss, "unit": "GS/s", "h2d_bytes_per_step": 4 * N_SAMPLES,
                 "d2h_bytes_per_step": 4 * N_SAMPLES},
         "gpu_launches": args.steps,
