@@ -66,10 +66,29 @@ __device__ __forceinline__ float lane_mv_g(const float *__restrict__ A, float xi
     return y;
 }
 
+// Row `lane` of a dense column-major S x S matrix in global memory, into registers (one latency
+// for a chain of products with the same matrix).
+template <int S>
+__device__ __forceinline__ void load_row_g(const float *__restrict__ A, int lane, float (&r)[S]) {
+    const int row = lane < S ? lane : 0;
+#pragma unroll
+    for (int j = 0; j < S; ++j) r[j] = __ldg(A + j * S + row);
+}
+
+// Lane-parallel y = A x with lane i holding row i of A (load_row_g) and x_i.
+template <int S>
+__device__ __forceinline__ float lane_mv_rows(const float (&r)[S], float xi) {
+    float y = 0.f;
+#pragma unroll
+    for (int j = 0; j < S; ++j) y = fmaf(r[j], __shfl_sync(0xffffffffu, xi, j), y);
+    return y;
+}
+
 template <int K, bool NORM>
 __global__ void __launch_bounds__((kBatchW + 1) * 32, 1) sos_batch_kernel(const __grid_constant__ BatchParams<K> p) {
     using Dm = LaneDims<K, kBatchN>;
-    constexpr int S = Dm::S, MS = Dm::MS, N = kBatchN, W = kBatchW, CH = Dm::CH, RPS = Dm::RPS, RSP = Dm::RSP;
+    constexpr int S = Dm::S, MS = Dm::MS, N = kBatchN, W = kBatchW, CH = Dm::LQ, RPS = Dm::RPS, RSP = Dm::RSP;
+    static_assert(Dm::V == 4 && Dm::CC == CH, "the batch kernel corrects four samples per lane and step");
     constexpr int P = N + 4;  // padded row pitch (floats): conflict-free 128-bit row access
     constexpr int C = N * kL;
     constexpr int SZ = ((S + 3) / 4) * 4;
@@ -138,6 +157,10 @@ __global__ void __launch_bounds__((kBatchW + 1) * 32, 1) sos_batch_kernel(const 
             const LaneSec *sec = sg->sec;
             // initial state of the signal (scaled domain), word i
             auto zinit = [&](int i) -> float { return zi ? zi[i] * __ldg(&sec[i >> 1].zscale) : 0.f; };
+            // rows of A_C and A_T for this lane, loaded while the tile's groups are still running
+            float acr[S], atr[S];
+            load_row_g<S>(tab + Dm::OFF_AC, lane, acr);
+            load_row_g<S>(tab + Dm::OFF_AT, lane, atr);
             if (!mbar_wait(&bar_local[slot], (it >> 1) & 1, budget, p.status)) break;
             const float *abuf = a_buf + slot * W * S;
             const float acc_i = agg[slot * S + (lane < S ? lane : 0)];
@@ -206,7 +229,7 @@ __global__ void __launch_bounds__((kBatchW + 1) * 32, 1) sos_batch_kernel(const 
             }
             if (cur + 1 < p.n_tiles) {
                 // the resolved carry A_T Z + tile carry (read by the signal's next tile only)
-                const float gl = lane_mv_g<S>(tab + Dm::OFF_AT, zi_lane, lane) + acc_i;
+                const float gl = lane_mv_rows<S>(atr, zi_lane) + acc_i;
                 if (lane < S) st_relaxed_b64(dcur + lane, pack_word(tagG, gl));
             }
             // incoming state of each group of the tile: Z_0 = Z, Z_{v+1} = A_C Z_v + a_v
@@ -214,8 +237,7 @@ __global__ void __launch_bounds__((kBatchW + 1) * 32, 1) sos_batch_kernel(const 
 #pragma unroll 1
             for (int v = 0; v < W; ++v) {
                 if (lane < S) zb[v * S + lane] = zi_lane;
-                if (v + 1 < W)
-                    zi_lane = lane_mv_g<S>(tab + Dm::OFF_AC, zi_lane, lane) + abuf[v * S + (lane < S ? lane : 0)];
+                if (v + 1 < W) zi_lane = lane_mv_rows<S>(acr, zi_lane) + abuf[v * S + (lane < S ? lane : 0)];
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&bar_zready[slot]);  // one barrier per tile parity
@@ -384,11 +406,12 @@ __global__ void __launch_bounds__((kBatchW + 1) * 32, 1) sos_batch_kernel(const 
             if (old == W - 1) {
                 __threadfence_block();
                 const float *ab = a_buf + slot * W * S;
-                const float *ACd = sg->tab + Dm::OFF_AC;
+                float acr[S];
+                load_row_g<S>(sg->tab + Dm::OFF_AC, lane, acr);
                 const int li = lane < S ? lane : 0;
                 float c = ab[li];
 #pragma unroll 1
-                for (int v = 1; v < W; ++v) c = lane_mv_g<S>(ACd, c, lane) + ab[v * S + li];
+                for (int v = 1; v < W; ++v) c = lane_mv_rows<S>(acr, c) + ab[v * S + li];
                 if (tile > sg->tile0 && lane < S)
                     st_relaxed_b64(p.desc + static_cast<size_t>(tile) * S + lane, pack_word((p.epoch << 2) | 1u, c));
                 if (lane < S) agg[slot * S + lane] = c;

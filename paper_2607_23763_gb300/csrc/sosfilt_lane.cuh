@@ -45,14 +45,18 @@ struct LaneDims {
     static constexpr int FULL = S * S;
     static constexpr int P2 = S <= 2 ? 2 : S <= 4 ? 4 : S <= 8 ? 8 : 16;
     static constexpr int SH = 5 - (P2 == 2 ? 1 : P2 == 4 ? 2 : P2 == 8 ? 3 : 4);
-    static constexpr int CH = N / 4;     // float4 chunks of a row
-    static constexpr int RPS = 32 / CH;  // rows per step of the column-wise correction
+    static constexpr int LQ = N / 4;             // 128-bit loads per lane per group
+    static constexpr int BPS = N == 32 ? 2 : 1;  // thread blocks per SM (N = 32: 4 warps per scheduler)
+    static constexpr int V = N == 32 ? 2 : 4;    // samples per lane and step of the column-wise correction
+    static constexpr int CC = N / V;             // correction chunks per row
+    static constexpr int RPS = 32 / CC;          // rows per step of the column-wise correction
+    static constexpr bool ATL_SHARED = BPS == 1;  // (A_T)^lane in shared memory (else read from L1/L2)
     // row-state pitch: S rounded up to whole 16-byte words, an odd number of them
     static constexpr int S4 = (S + 3) / 4;
     static constexpr int RSP = 4 * ((S4 & 1) ? S4 : S4 + 1);
     // table block (copied to shared memory up to TAB): (M_N)^lane [32][MS], (A_T)^(Q lane) [32][MS]
     // (Q = kLaneQ predecessors per lane and lookback round), A_C dense column-major, the basis in
-    // chunks [S][CH][4] (H_j(4c + q)), A_T dense, A_T packed [MS]; global only: (A_T)^(32 Q w)
+    // [S][N] (read in chunks of V samples), A_T dense, A_T packed [MS]; global only: (A_T)^(32 Q w)
     // dense for w = 1..kMaxWin
     static constexpr int OFF_ATL = 32 * MS;
     static constexpr int OFF_AC = 64 * MS;
@@ -62,6 +66,9 @@ struct LaneDims {
     static constexpr int TAB = OFF_ATP + MS;
     static constexpr int OFF_AW = TAB;
     static constexpr int TAB_GLOBAL = OFF_AW + kMaxWin * FULL;
+    // the shared-memory copy: (M_N)^lane, (A_T)^lane when ATL_SHARED, then A_C .. A_T packed
+    static constexpr int SM_AC = ATL_SHARED ? OFF_AC : OFF_ATL;
+    static constexpr int SM_TAB = SM_AC + (TAB - OFF_AC);
 };
 
 // Section constants as the passes read them.  ParamSecs: the kernel parameters of a single-signal
@@ -111,6 +118,11 @@ __device__ __forceinline__ float df2_step(const float4 c, float b0, float &u1, f
     return w;
 }
 
+template <bool B>
+struct CapTag {
+    static constexpr bool value = B;
+};
+
 // Particular solution of the lane's row (N samples, in place) through all K sections from zero
 // state, sections skewed by one sample each; t receives the terminal state (transposed direct form
 // II).  With CAPTURE, the lane with cap_lane set writes its state after sample m_last to cap.
@@ -131,8 +143,9 @@ __device__ __forceinline__ void lane_particular(const Secs &cs, float *row, floa
     for (int r = 0; r < (R0 > 0 ? R0 : 1); ++r) carry[r] = 0.f;
 
     float4 xn = *reinterpret_cast<const float4 *>(row);
-#pragma unroll 1
-    for (int i0 = 0; i0 < N; i0 += 4) {
+    // steps i0 .. i0 + 3; with CAP the lane records each section's history after sample m_cap
+    auto step_group = [&](int i0, auto cap_tag) {
+        constexpr bool CAP = decltype(cap_tag)::value;
         const float4 xv = xn;
         if (i0 + 4 < N) xn = *reinterpret_cast<const float4 *>(row + i0 + 4);
         const float xs[4] = {xv.x, xv.y, xv.z, xv.w};
@@ -149,7 +162,7 @@ __device__ __forceinline__ void lane_particular(const Secs &cs, float *row, floa
                     out[j] = w;
                 else
                     pipe[s] = w;
-                if constexpr (CAPTURE) {
+                if constexpr (CAP) {
                     const bool hit = (i0 + j - s) == m_cap;
                     cu1[s] = hit ? u1[s] : cu1[s];
                     cu2[s] = hit ? u2[s] : cu2[s];
@@ -166,6 +179,22 @@ __device__ __forceinline__ void lane_particular(const Secs &cs, float *row, floa
         }
 #pragma unroll
         for (int r = 0; r < R0; ++r) carry[r] = out[4 - R0 + r];
+    };
+    if constexpr (!CAPTURE) {
+#pragma unroll 1
+        for (int i0 = 0; i0 < N; i0 += 4) step_group(i0, CapTag<false>{});
+    } else {
+        // only the step groups in which some section passes sample m_last record (section s at step
+        // m_last + s); the bounds depend on m_last alone, the same in every lane of the warp
+        const int lo = (m_last / 4) * 4;
+        const int hi = min(N, ((m_last + K - 1) / 4) * 4 + 4);
+        int i0 = 0;
+#pragma unroll 1
+        for (; i0 < lo; i0 += 4) step_group(i0, CapTag<false>{});
+#pragma unroll 1
+        for (; i0 < hi; i0 += 4) step_group(i0, CapTag<true>{});
+#pragma unroll 1
+        for (; i0 < N; i0 += 4) step_group(i0, CapTag<false>{});
     }
     // drain: steps N .. N + D - 1, in which only the sections s > step - N are still running
     if constexpr (D > 0) {
@@ -270,25 +299,27 @@ __device__ __forceinline__ void lane_state_mv(const float *__restrict__ A, const
 }
 
 template <int K, int N, bool NORM>
-__global__ void __launch_bounds__((kLaneW + 1) * 32, 1) sos_lane_kernel(const __grid_constant__ LaneParams<K> p) {
+__global__ void __launch_bounds__((kLaneW + 1) * 32, LaneDims<K, N>::BPS)
+    sos_lane_kernel(const __grid_constant__ LaneParams<K> p) {
     using Dm = LaneDims<K, N>;
-    constexpr int S = Dm::S, MS = Dm::MS, W = kLaneW, CH = Dm::CH, RPS = Dm::RPS, RSP = Dm::RSP;
+    constexpr int S = Dm::S, MS = Dm::MS, W = kLaneW, LQ = Dm::LQ, V = Dm::V, CC = Dm::CC, RPS = Dm::RPS,
+                  RSP = Dm::RSP;
     constexpr int P = N + 4;  // padded row pitch (floats): conflict-free 128-bit row access
     constexpr int C = N * kL;
     extern __shared__ float4 smem4[];
     float *rows = reinterpret_cast<float *>(smem4);  // [W][2][32][P]: two row buffers per warp
-    float *tab = rows + W * 2 * kL * P;              // table block, layout LaneDims
+    float *tab = rows + W * 2 * kL * P;              // shared copy of the table block (SM_TAB floats)
     float *sML = tab;                                // (M_N)^lane [32][MS]
-    float *sATl = tab + Dm::OFF_ATL;                 // (A_T)^lane [32][MS]
-    float *sACd = tab + Dm::OFF_AC;                  // A_C dense column-major
-    const float4 *sH4 = reinterpret_cast<const float4 *>(tab + Dm::OFF_H);  // [S][CH] float4
-    float *rowst = tab + Dm::TAB;                    // [W][32][RSP] rows' true incoming states
+    const float *sATl = Dm::ATL_SHARED ? tab + Dm::OFF_ATL : p.tab + Dm::OFF_ATL;  // (A_T)^lane [32][MS]
+    float *sACd = tab + Dm::SM_AC;                   // A_C dense column-major
+    const float *sH = tab + Dm::SM_AC + (Dm::OFF_H - Dm::OFF_AC);  // basis [S][N]
+    float *rowst = tab + Dm::SM_TAB;                 // [W][32][RSP] rows' true incoming states
     float *a_buf = rowst + W * kL * RSP;             // [2][W][S] local carries
     float *z_buf = a_buf + 2 * W * S;                // [2][W][S] incoming states
     float *agg = z_buf + 2 * W * S;                  // [2][S] tile carry under zero incoming state
     float *zs_tail = agg + 2 * S;                    // [S] lane-local state after the last sample
-    const float *sATd = tab + Dm::OFF_AT;            // A_T dense column-major
-    const float *sATp = tab + Dm::OFF_ATP;           // A_T packed
+    const float *sATd = tab + Dm::SM_AC + (Dm::OFF_AT - Dm::OFF_AC);    // A_T dense column-major
+    const float *sATp = tab + Dm::SM_AC + (Dm::OFF_ATP - Dm::OFF_AC);   // A_T packed
     const float *gAW = p.tab + Dm::OFF_AW;           // (A_T)^(32 Q w), w = 1.., dense (global)
     // tiles alternate between two slots; the incoming-state barrier has one per slot, so that it
     // never runs two phases ahead of a waiter
@@ -304,7 +335,10 @@ __global__ void __launch_bounds__((kLaneW + 1) * 32, 1) sos_lane_kernel(const __
     {
         const float4 *src = reinterpret_cast<const float4 *>(p.tab);
         float4 *dst = reinterpret_cast<float4 *>(tab);
-        for (int i = threadIdx.x; i < Dm::TAB / 4; i += blockDim.x) dst[i] = __ldg(src + i);
+        constexpr int HEAD = (Dm::ATL_SHARED ? Dm::OFF_AC : Dm::OFF_ATL) / 4;  // float4s copied as they are
+        for (int i = threadIdx.x; i < HEAD; i += blockDim.x) dst[i] = __ldg(src + i);
+        for (int i = threadIdx.x; i < (Dm::TAB - Dm::OFF_AC) / 4; i += blockDim.x)
+            dst[Dm::SM_AC / 4 + i] = __ldg(src + Dm::OFF_AC / 4 + i);
     }
     auto draw_ticket = [&]() -> long long {
         if (tickets_exhausted) return -1;
@@ -488,16 +522,16 @@ __global__ void __launch_bounds__((kLaneW + 1) * 32, 1) sos_lane_kernel(const __
             p.trace[static_cast<size_t>(tile) * kTraceSlots + slot] = global_ns();
     };
     // the group's samples, coalesced: chunk j of the lane holds samples 4 (32 j + lane) .. + 3
-    float4 xq[CH];
+    float4 xq[LQ];
     auto load_regs = [&](long long tile) {
         const long long base = (tile * W + w) * C;
         const long long avail = p.n - base;
         if (avail >= C && p.aligned) {
 #pragma unroll
-            for (int j = 0; j < CH; ++j) xq[j] = __ldcs(reinterpret_cast<const float4 *>(p.x + base) + j * 32 + lane);
+            for (int j = 0; j < LQ; ++j) xq[j] = __ldcs(reinterpret_cast<const float4 *>(p.x + base) + j * 32 + lane);
         } else {
 #pragma unroll
-            for (int j = 0; j < CH; ++j) {
+            for (int j = 0; j < LQ; ++j) {
                 const int off = 4 * (j * 32 + lane);
                 const float *src = p.x + base + off;
                 xq[j].x = (off + 0 < avail) ? __ldcs(src + 0) : 0.f;
@@ -540,35 +574,50 @@ __global__ void __launch_bounds__((kLaneW + 1) * 32, 1) sos_lane_kernel(const __
             *reinterpret_cast<float2 *>(RS + lane * RSP + j) = make_float2(st[j], st[j + 1]);
         __syncwarp();
         wtrace(tile, 11);
-        const int c = lane % CH, rsub = lane / CH;
-        float4 h[S];
+        const int c = lane % CC, rsub = lane / CC;
+        float h[S][V];  // the lane's basis values H_j(V c + q)
 #pragma unroll
-        for (int j = 0; j < S; ++j) h[j] = sH4[j * CH + c];
+        for (int j = 0; j < S; ++j) {
+            if constexpr (V == 4) {
+                const float4 t4 = *reinterpret_cast<const float4 *>(sH + j * N + 4 * c);
+                h[j][0] = t4.x, h[j][1] = t4.y, h[j][2] = t4.z, h[j][3] = t4.w;
+            } else {
+                const float2 t2 = *reinterpret_cast<const float2 *>(sH + j * N + 2 * c);
+                h[j][0] = t2.x, h[j][1] = t2.y;
+            }
+        }
         const long long base = g * C;
         const long long avail = p.n - base;
         const bool full = avail >= C && p.aligned;
 #pragma unroll 2
         for (int r0 = 0; r0 < kL; r0 += RPS) {
             const int r = r0 + rsub;
-            float4 v = *reinterpret_cast<const float4 *>(Y + r * P + 4 * c);
+            float v[V];
+            if constexpr (V == 4) {
+                const float4 t4 = *reinterpret_cast<const float4 *>(Y + r * P + 4 * c);
+                v[0] = t4.x, v[1] = t4.y, v[2] = t4.z, v[3] = t4.w;
+            } else {
+                const float2 t2 = *reinterpret_cast<const float2 *>(Y + r * P + 2 * c);
+                v[0] = t2.x, v[1] = t2.y;
+            }
             const float *sr = RS + r * RSP;
 #pragma unroll
             for (int j = 0; j < S; j += 2) {
                 const float2 z = *reinterpret_cast<const float2 *>(sr + j);
-                v.x = fmaf(h[j].x, z.x, fmaf(h[j + 1].x, z.y, v.x));
-                v.y = fmaf(h[j].y, z.x, fmaf(h[j + 1].y, z.y, v.y));
-                v.z = fmaf(h[j].z, z.x, fmaf(h[j + 1].z, z.y, v.z));
-                v.w = fmaf(h[j].w, z.x, fmaf(h[j + 1].w, z.y, v.w));
+#pragma unroll
+                for (int q = 0; q < V; ++q) v[q] = fmaf(h[j][q], z.x, fmaf(h[j + 1][q], z.y, v[q]));
             }
-            const int off = r * N + 4 * c;
+            const int off = r * N + V * c;
             if (full) {
-                __stcs(reinterpret_cast<float4 *>(p.y + base + off), v);
+                if constexpr (V == 4)
+                    __stcs(reinterpret_cast<float4 *>(p.y + base + off), make_float4(v[0], v[1], v[2], v[3]));
+                else
+                    __stcs(reinterpret_cast<float2 *>(p.y + base + off), make_float2(v[0], v[1]));
             } else {
                 float *dst = p.y + base + off;
-                if (off + 0 < avail) dst[0] = v.x;
-                if (off + 1 < avail) dst[1] = v.y;
-                if (off + 2 < avail) dst[2] = v.z;
-                if (off + 3 < avail) dst[3] = v.w;
+#pragma unroll
+                for (int q = 0; q < V; ++q)
+                    if (off + q < avail) dst[q] = v[q];
             }
         }
         __syncwarp();
@@ -594,7 +643,7 @@ __global__ void __launch_bounds__((kLaneW + 1) * 32, 1) sos_lane_kernel(const __
         // stash the prefetched samples as rows (lane l: samples l N .. l N + N - 1)
         wtrace(tile, 14);
 #pragma unroll
-        for (int j = 0; j < CH; ++j) {
+        for (int j = 0; j < LQ; ++j) {
             const int off = 4 * (j * 32 + lane);
             *reinterpret_cast<float4 *>(X + (off / N) * P + (off % N)) = xq[j];
         }
@@ -665,7 +714,7 @@ template <int K, int N>
 constexpr size_t lane_smem_bytes() {
     using Dm = LaneDims<K, N>;
     constexpr int W = kLaneW;
-    return sizeof(float) * (static_cast<size_t>(W) * 2 * kL * (N + 4) + Dm::TAB + W * kL * Dm::RSP +
+    return sizeof(float) * (static_cast<size_t>(W) * 2 * kL * (N + 4) + Dm::SM_TAB + W * kL * Dm::RSP +
                             4 * W * Dm::S + 2 * Dm::S + ((Dm::S + 3) / 4) * 4);
 }
 
