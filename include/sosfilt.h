@@ -239,7 +239,13 @@ sos_status sos_filter_stream_push(sos_filter *f, const float *x_dev, float *y_de
  */
 sos_status sos_filter_stream_state(sos_filter *f, float *z_out, const float *z_in, int on_device);
 
-/* Synchronize the filter's last stream and return the sticky device status. */
+/*
+ * Synchronize the filter's last stream and return the sticky device status.  SOS_ETIMEOUT means
+ * that a device wait (a lookback or barrier wait) ran past sos_tuning.spin_budget_cycles: the
+ * kernel recorded it and returned early, so the outputs and final states of the runs issued since
+ * then are undefined.  Reporting it clears it: the call then resets the filter's status word and
+ * ticket counter, so that the runs issued after it are valid again.
+ */
 sos_status sos_filter_sync_status(sos_filter *f);
 
 /*

@@ -1833,7 +1833,14 @@ sos_status sos_filter_sync_status(sos_filter *f) {
     if (cudaStreamSynchronize(f->last_stream) != cudaSuccess) return SOS_ECUDA;
     int h = 0;
     if (cudaMemcpy(&h, f->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SOS_ECUDA;
-    if (h & sosk::kDevErrTimeout) return SOS_ETIMEOUT;
+    if (h & sosk::kDevErrTimeout) {
+        // a launch that gave up consumed fewer tickets than the host counted: start the counter over
+        if (cudaDeviceSynchronize() != cudaSuccess || cudaMemset(f->d_status, 0, sizeof(int)) != cudaSuccess ||
+            cudaMemset(f->d_ticket, 0, sizeof(unsigned long long)) != cudaSuccess)
+            return SOS_ECUDA;
+        f->ticket_base = 0;
+        return SOS_ETIMEOUT;
+    }
     return SOS_OK;
 }
 

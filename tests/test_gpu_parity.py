@@ -289,3 +289,26 @@ def test_precision_resonator_bank_full_size(dev):
     print(f"resonator bank, 2^30 samples: rel err {err:.3e}")
     assert err < 2e-3
     f.close()
+
+
+@pytest.mark.parametrize("tuning", KERNELS, ids=KERNEL_IDS)
+def test_wait_budget_expiry_reports_timeout_and_recovers(dev, tuning):
+    """Every device wait is bounded: with a budget of a few cycles the lookback and barrier waits run
+    out, the kernel records SOS_ETIMEOUT and returns (the context stays usable), sync_status reports
+    it once, and the next run of the same filter is correct again."""
+    from paper_2607_23763_gb300 import SosFilter
+    SOS_ETIMEOUT = -4
+    sos = designs.butter_lowpass(16, 0.05)
+    x = workloads.normal_f32(61, 40 * 14336 + 77)
+    xd = torch.from_numpy(x).to(dev)
+    f = SosFilter(sos, tuning=dict(tuning, spin_budget_cycles=1))
+    f.run(xd)
+    assert f.sync_status() == SOS_ETIMEOUT
+    f.close()
+    # a filter with the default budget on the same context: correct results
+    g = _filt(sos, tuning=tuning)
+    y = g.run(xd)
+    assert g.sync_status() == 0
+    y_ref = oracle.sosfilt(sos, x)
+    assert _rel(y.cpu().numpy(), y_ref) < 1e-4
+    g.close()
