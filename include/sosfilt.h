@@ -97,6 +97,12 @@ enum {
  *   solver             SOS_SOLVER_DEFAULT, SOS_SOLVER_CR or SOS_SOLVER_PH (see SOS_SOLVER_*);
  *                      SOS_SOLVER_PH takes N = 0, 32 or 64, carry SOS_CARRY_DEFAULT or
  *                      SOS_CARRY_CASCADE and lookback_width 0
+ *   deterministic      0 (default) or 1.  By default a tile's incoming state is composed from
+ *                      whichever predecessor's resolved carry its lookback meets first (Sec.
+ *                      IV-B), so results may differ run to run in the last ulps.  With 1 every
+ *                      tile composes from the resolved carry of a fixed anchor tile (the last
+ *                      multiple of 32 before it) and the local carries after it: outputs are
+ *                      bit-identical from run to run.  PH solver only (the default solver).
  */
 typedef struct {
     int N, L, groups_per_cta, threads_per_group, fp64_carry;
@@ -104,6 +110,7 @@ typedef struct {
     int lookback_width;
     int carry;
     int solver;
+    int deterministic;
 } sos_tuning;
 
 /*

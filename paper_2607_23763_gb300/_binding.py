@@ -42,7 +42,7 @@ class Tuning(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int), ("L", ctypes.c_int), ("groups_per_cta", ctypes.c_int),
                 ("threads_per_group", ctypes.c_int), ("fp64_carry", ctypes.c_int),
                 ("spin_budget_cycles", ctypes.c_longlong), ("lookback_width", ctypes.c_int),
-                ("carry", ctypes.c_int), ("solver", ctypes.c_int)]
+                ("carry", ctypes.c_int), ("solver", ctypes.c_int), ("deterministic", ctypes.c_int)]
 
 
 CARRY_DEFAULT, CARRY_CASCADE, CARRY_SECTION = 0, 1, 2

@@ -773,6 +773,7 @@ sos_status launch_lane_pass(sos_filter *f, LanePass &ps, const float *x, float *
     p->status = f->d_status;
     p->spin_budget = f->tuning.spin_budget_cycles ? f->tuning.spin_budget_cycles : kDefaultSpinBudget;
     p->aligned = aligned ? 1 : 0;
+    p->deterministic = f->tuning.deterministic;
     p->tab = ps.d_tab;
     p->trace = f->trace;
     p->trace_tiles = f->trace_blocks;
@@ -955,7 +956,7 @@ sos_status run_impl(sos_filter *f, const float *x, float *y, int64_t n, const fl
         return SOS_OK;
     }
     const sos_tuning &t = f->tuning;
-    if (!t.N && !t.carry && !t.solver && !t.lookback_width) {
+    if (!t.N && !t.carry && !t.solver && !t.lookback_width && !t.deterministic) {
         // all defaults: the autotuned choice for this section count and length, if there is one
         int solver = 0, N = 0;
         if (tuned_choice(f->device, f->K, n, &solver, &N)) {
@@ -1446,6 +1447,9 @@ sos_status sos_filter_create(int n_sections, const double *sos, const float *zi,
             return SOS_EINVAL;
         if (t->solver == SOS_SOLVER_PH &&
             ((t->N && t->N != 32 && t->N != 64) || t->carry == SOS_CARRY_SECTION || t->lookback_width))
+            return SOS_EINVAL;
+        if (t->deterministic != 0 && t->deterministic != 1) return SOS_EINVAL;
+        if (t->deterministic && (t->solver == SOS_SOLVER_CR || t->carry || t->lookback_width || t->N == 128))
             return SOS_EINVAL;
     }
     for (int k = 0; k < n_sections; ++k) {

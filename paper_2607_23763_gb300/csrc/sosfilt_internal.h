@@ -150,6 +150,7 @@ struct LaneParams {
     long long spin_budget;
     int aligned;                // x and y 16-byte aligned
     int m_last;                 // position of the signal's last sample inside its lane
+    int deterministic;          // fixed lookback composition (descriptors [n_tiles][2][2K]: local, resolved)
     const float *tab;           // global table block, layout LaneDims<K, N>
     unsigned long long *trace;  // nullptr, or [n_tiles][kTraceSlots] phase trace (kLaneTrace*)
     long long trace_tiles;

@@ -390,10 +390,50 @@ __global__ void __launch_bounds__((kLaneW + 1) * 32, LaneDims<K, N>::BPS)
             const float *abuf = a_buf + slot * W * S;
             const float acc_i = agg[slot * S + (lane < S ? lane : 0)];
             float tmp[S];
-            unsigned long long *dcur = p.desc + static_cast<size_t>(cur) * S;
+            // descriptor of a tile: its carry words (local, then overwritten by the resolved carry), or
+            // in the deterministic mode two slots, local then resolved
+            const int dstride = p.deterministic ? 2 * S : S;
+            unsigned long long *dcur = p.desc + static_cast<size_t>(cur) * dstride + (p.deterministic ? S : 0);
             float zi_lane = 0.f;
             if (cur == 0) {
                 zi_lane = zinit(lane < S ? lane : 0);
+            } else if (p.deterministic) {
+                // fixed composition: the resolved carry of the anchor tile a (the last multiple of 32
+                // before cur) and the local carries of tiles a + 1 .. cur - 1, whichever of them have
+                // resolved meanwhile, so that the sum does not depend on timing
+                const long long a = ((cur - 1) / 32) * 32;
+                const int ja = static_cast<int>(cur - 1 - a);  // the anchor's lane
+                const long long pred = cur - 1 - lane;
+                const long long t_start = clock64();
+                float v[S];
+                for (;;) {
+                    bool ok = true;
+                    if (lane <= ja) {
+                        const unsigned want = lane == ja ? tagG : tagL;
+                        const unsigned long long *dp =
+                            p.desc + static_cast<size_t>(pred) * 2 * S + (lane == ja ? S : 0);
+#pragma unroll
+                        for (int q = 0; q < S; q += 2) {
+                            unsigned long long x0, x1;
+                            ld_relaxed_v2(dp + q, x0, x1);
+                            ok = ok && static_cast<unsigned>(x0 >> 32) == want && static_cast<unsigned>(x1 >> 32) == want;
+                            v[q] = __uint_as_float(static_cast<unsigned>(x0));
+                            v[q + 1] = __uint_as_float(static_cast<unsigned>(x1));
+                        }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < S; ++q) v[q] = 0.f;
+                    }
+                    if (__all_sync(0xffffffffu, ok)) break;
+                    if (__any_sync(0xffffffffu, (clock64() - t_start) > budget)) {
+                        if (lane == 0) atomicOr(p.status, kDevErrTimeout);
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+                packed_mv<K>(sATl + lane * MS, v, tmp);
+                float part = reduce_scatter<S, Dm::P2, Dm::SH>(tmp, lane);
+                zi_lane = __shfl_sync(0xffffffffu, part, (lane < S ? lane : 0) << Dm::SH);
             } else {
                 // decoupled lookback over tiles, 32 Q predecessors per round: lane l takes the
                 // predecessors at distance 32 Q win + Q l + i + 1, i < Q
@@ -684,7 +724,8 @@ __global__ void __launch_bounds__((kLaneW + 1) * 32, LaneDims<K, N>::BPS)
 #pragma unroll 1
                 for (int v = 1; v < W; ++v) c = lane_mv<S>(sACd, c, lane) + abt[v * S + li];
                 if (tile > 0 && lane < S)
-                    st_relaxed_b64(p.desc + static_cast<size_t>(tile) * S + lane, pack_word((p.epoch << 2) | 1u, c));
+                    st_relaxed_b64(p.desc + static_cast<size_t>(tile) * (p.deterministic ? 2 * S : S) + lane,
+                                   pack_word((p.epoch << 2) | 1u, c));
                 if (lane < S) agg[slot * S + lane] = c;
                 if (lane == 0) {
                     fold_count[slot] = 0;
