@@ -97,12 +97,14 @@ enum {
  *   solver             SOS_SOLVER_DEFAULT, SOS_SOLVER_CR or SOS_SOLVER_PH (see SOS_SOLVER_*);
  *                      SOS_SOLVER_PH takes N = 0, 32 or 64, carry SOS_CARRY_DEFAULT or
  *                      SOS_CARRY_CASCADE and lookback_width 0
- *   deterministic      0 (default) or 1.  By default a tile's incoming state is composed from
- *                      whichever predecessor's resolved carry its lookback meets first (Sec.
- *                      IV-B), so results may differ run to run in the last ulps.  With 1 every
- *                      tile composes from the resolved carry of a fixed anchor tile (the last
- *                      multiple of 32 before it) and the local carries after it: outputs are
- *                      bit-identical from run to run.  PH solver only (the default solver).
+ *   deterministic      0 or 1.  The PH solver (and batched runs) always compose a tile's
+ *                      incoming state the same way -- the resolved carry of a fixed anchor tile
+ *                      (the last multiple of 32 before it) and the local carries after it -- so
+ *                      their outputs are bit-identical from run to run.  Cyclic reduction composes
+ *                      from whichever predecessor's resolved carry its lookback meets first (Sec.
+ *                      IV-B) and may differ in the last ulps; 1 requests reproducible results and
+ *                      is rejected with SOS_EINVAL together with settings that select cyclic
+ *                      reduction.
  */
 typedef struct {
     int N, L, groups_per_cta, threads_per_group, fp64_carry;

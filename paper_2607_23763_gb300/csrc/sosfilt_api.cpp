@@ -428,9 +428,8 @@ sos_status build_cascade(sos_filter *f, int N, CasTables &ct) {
 }
 
 // Tables of the skewed-pass PH kernel for one N (32 or 64), in float64, uploaded once.  Layout of
-// the device block as LaneDims<kp, N>: (M_N)^lane [32][stride], (A_T)^(Q lane) [32][stride]
-// (packed; Q = kLaneQ), A_C dense column-major, the output basis [2 kp][N] (chunks of four samples),
-// A_T dense, A_T packed [stride], then (A_T)^(32 Q w) dense for w = 1..kMaxWin.
+// the device block as LaneDims<kp, N>: (M_N)^lane [32][stride], (A_T)^lane [32][stride] (packed),
+// A_C dense column-major, the output basis [2 kp][N], A_T dense.
 sos_status build_lane(sos_filter *f, int N, std::vector<LanePass> &out) {
     constexpr int W = sosk::kLaneW;
     out.clear();
@@ -501,27 +500,18 @@ sos_status build_lane(sos_filter *f, int N, std::vector<LanePass> &out) {
             }
         const int ms = lane_stride(kp), full = S * S;
         const size_t off_ac = 64 * static_cast<size_t>(ms), off_h = off_ac + full, off_at = off_h + N * S;
-        const size_t off_atp = off_at + full, off_aw = off_atp + ms;
-        std::vector<float> tab(off_aw + sosk::kMaxWin * full, 0.f);
-        const DMat ATQ = dpow(AT, sosk::kLaneQ);
+        std::vector<float> tab(off_at + full, 0.f);
         DMat L = deye(S), LT = deye(S);
         for (int l = 0; l < 32; ++l) {
             pack_into(L, kp, &tab[static_cast<size_t>(l) * ms]);
             pack_into(LT, kp, &tab[static_cast<size_t>(32 + l) * ms]);
             L = dmul(L, MN);
-            LT = dmul(LT, ATQ);
+            LT = dmul(LT, AT);
         }
         dense_colmajor_into(AC, &tab[off_ac]);
         for (int j = 0; j < S; ++j)
             for (int m = 0; m < N; ++m) tab[off_h + static_cast<size_t>(j) * N + m] = ps.H[static_cast<size_t>(j) * N + m];
         dense_colmajor_into(AT, &tab[off_at]);
-        pack_into(AT, kp, &tab[off_atp]);
-        const DMat ATW = dpow(ATQ, 32);
-        DMat Pw = ATW;
-        for (int w = 1; w <= sosk::kMaxWin; ++w) {
-            dense_colmajor_into(Pw, &tab[off_aw + static_cast<size_t>(full) * (w - 1)]);
-            Pw = dmul(Pw, ATW);
-        }
         if (cudaMalloc(&ps.d_tab, tab.size() * sizeof(float)) != cudaSuccess) return SOS_ENOMEM;
         if (cudaMemcpy(ps.d_tab, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
             return SOS_ECUDA;
@@ -773,7 +763,6 @@ sos_status launch_lane_pass(sos_filter *f, LanePass &ps, const float *x, float *
     p->status = f->d_status;
     p->spin_budget = f->tuning.spin_budget_cycles ? f->tuning.spin_budget_cycles : kDefaultSpinBudget;
     p->aligned = aligned ? 1 : 0;
-    p->deterministic = f->tuning.deterministic;
     p->tab = ps.d_tab;
     p->trace = f->trace;
     p->trace_tiles = f->trace_blocks;
@@ -956,7 +945,7 @@ sos_status run_impl(sos_filter *f, const float *x, float *y, int64_t n, const fl
         return SOS_OK;
     }
     const sos_tuning &t = f->tuning;
-    if (!t.N && !t.carry && !t.solver && !t.lookback_width && !t.deterministic) {
+    if (!t.N && !t.carry && !t.solver && !t.lookback_width) {
         // all defaults: the autotuned choice for this section count and length, if there is one
         int solver = 0, N = 0;
         if (tuned_choice(f->device, f->K, n, &solver, &N)) {
@@ -1100,7 +1089,7 @@ sos_status run_batch_impl(int n_signals, sos_filter *const *filters, const float
     for (int c = 0; c < kBatchClasses; ++c) {
         sig_off[c + 1] = sig_off[c] + cls_sigs[c];
         tile_off[c + 1] = tile_off[c] + cls_tiles[c];
-        desc_off[c + 1] = desc_off[c] + cls_tiles[c] * 2 * (c / 2 + 1);
+        desc_off[c + 1] = desc_off[c] + cls_tiles[c] * 4 * (c / 2 + 1);  // [tiles][2][2K]
         if (cls_sigs[c]) ++n_cls;
     }
     if (sig_off[kBatchClasses] == 0) return SOS_OK;
@@ -1277,7 +1266,7 @@ sos_status plan_create(int n_signals, sos_filter *const *filters, const float *c
     for (int c = 0; c < kBatchClasses; ++c) {
         sig_off[c + 1] = sig_off[c] + cls_sigs[c];
         tile_off[c + 1] = tile_off[c] + cls_tiles[c];
-        desc_off[c + 1] = desc_off[c] + cls_tiles[c] * 2 * (c / 2 + 1);
+        desc_off[c + 1] = desc_off[c] + cls_tiles[c] * 4 * (c / 2 + 1);  // [tiles][2][2K]
     }
     const size_t sig_bytes = sizeof(sosk::BatchSig) * sig_off[kBatchClasses];
     const size_t up_bytes = sig_bytes + sizeof(int) * tile_off[kBatchClasses];

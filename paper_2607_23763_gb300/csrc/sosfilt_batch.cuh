@@ -9,8 +9,8 @@
 // scan, a coordinator warp that folds the groups' local carries, resolves the tile's incoming
 // 2K-word state by decoupled lookback (Sec. IV-B, Eq. 25 on the cascade state) and derives the
 // groups' incoming states, and the homogeneous correction of Eq. 24 applied once for the cascade.
-// What changes is that lookback chains are kept per signal (a chain ends at its signal's first
-// tile, whose incoming state is the signal's initial state); that every per-signal quantity
+// What changes is that lookback chains are kept per signal (the anchors count from the signal's
+// first tile, whose incoming state is the signal's initial state); that every per-signal quantity
 // (pointers, length, section constants, transition tables, output basis) comes from the signal's
 // descriptor in global memory, the recurrence coefficients going to registers once per tile; and
 // that the next tile's input is staged by cp.async into a third row buffer of the warp.
@@ -165,67 +165,47 @@ __global__ void __launch_bounds__((kBatchW + 1) * 32, 1) sos_batch_kernel(const 
             const float *abuf = a_buf + slot * W * S;
             const float acc_i = agg[slot * S + (lane < S ? lane : 0)];
             float tmp[S];
-            unsigned long long *dcur = p.desc + static_cast<size_t>(cur) * S;
+            unsigned long long *dcur = p.desc + static_cast<size_t>(cur) * 2 * S + S;  // resolved slot
             float zi_lane = 0.f;
             if (cur == tile0) {
                 zi_lane = zinit(lane < S ? lane : 0);
             } else {
-                // decoupled lookback over the signal's tiles, 32 predecessors per round
+                // decoupled lookback over the signal's tiles with a fixed composition: the resolved
+                // carry of the anchor (the signal's last tile at a multiple of 32 from its first) and
+                // the local carries after it, so that outputs are reproducible bit for bit
+                const long long a = tile0 + ((cur - 1 - tile0) / 32) * 32;
+                const int ja = static_cast<int>(cur - 1 - a);  // the anchor's lane
+                const long long pred = cur - 1 - lane;
                 const long long t_start = clock64();
-                int win = 0;
+                float v[S];
                 for (;;) {
-                    const long long pred = cur - 1 - 32LL * win - lane;
-                    float v[S];
-                    int st;
-                    if (pred >= tile0) {
-                        const unsigned long long *dp = p.desc + static_cast<size_t>(pred) * S;
-                        bool allG = true, allL = true;
+                    bool ok = true;
+                    if (lane <= ja) {
+                        const unsigned want = lane == ja ? tagG : tagL;
+                        const unsigned long long *dp = p.desc + static_cast<size_t>(pred) * 2 * S + (lane == ja ? S : 0);
 #pragma unroll
                         for (int q = 0; q < S; q += 2) {
-                            unsigned long long a, b;
-                            ld_relaxed_v2(dp + q, a, b);
-                            const unsigned ta = static_cast<unsigned>(a >> 32), tb = static_cast<unsigned>(b >> 32);
-                            allG = allG && ta == tagG && tb == tagG;
-                            allL = allL && ta == tagL && tb == tagL;
-                            v[q] = __uint_as_float(static_cast<unsigned>(a));
-                            v[q + 1] = __uint_as_float(static_cast<unsigned>(b));
+                            unsigned long long x0, x1;
+                            ld_relaxed_v2(dp + q, x0, x1);
+                            ok = ok && static_cast<unsigned>(x0 >> 32) == want && static_cast<unsigned>(x1 >> 32) == want;
+                            v[q] = __uint_as_float(static_cast<unsigned>(x0));
+                            v[q + 1] = __uint_as_float(static_cast<unsigned>(x1));
                         }
-                        st = allG ? 2 : (allL ? 1 : 0);
                     } else {
-                        st = 2;  // the signal's initial state is the resolved carry of its tile -1
 #pragma unroll
-                        for (int i = 0; i < S; ++i) v[i] = (pred == tile0 - 1) ? zinit(i) : 0.f;
+                        for (int q = 0; q < S; ++q) v[q] = 0.f;
                     }
-                    const unsigned glob = __ballot_sync(0xffffffffu, st == 2);
-                    const unsigned inv = __ballot_sync(0xffffffffu, st == 0);
-                    const int j = glob ? __ffs(glob) - 1 : 32;
-                    const unsigned need = (j >= 31) ? 0xffffffffu : ((2u << j) - 1u);
-                    if (inv & need) {
-                        if (__any_sync(0xffffffffu, (clock64() - t_start) > budget)) {
-                            if (lane == 0) atomicOr(p.status, kDevErrTimeout);
-                            break;
-                        }
-                        __nanosleep(64);
-                        continue;
-                    }
-                    if (lane > j) {
-#pragma unroll
-                        for (int i = 0; i < S; ++i) v[i] = 0.f;
-                    }
-                    // sum over the window of (A_T)^k v_k (lane's own power), reduce-scattered
-                    packed_mv_gr<K>(tab + Dm::OFF_ATL + lane * MS, v, tmp);
-                    float part = reduce_scatter<S, Dm::P2, Dm::SH>(tmp, lane);
-                    part = __shfl_sync(0xffffffffu, part, (lane < S ? lane : 0) << Dm::SH);
-                    if (win == 0)
-                        zi_lane += part;
-                    else
-                        zi_lane += lane_mv_g<S>(tab + Dm::OFF_AW + (win - 1) * Dm::FULL, part, lane);
-                    if (j < 32) break;
-                    if (++win > kMaxWin) {
+                    if (__all_sync(0xffffffffu, ok)) break;
+                    if (__any_sync(0xffffffffu, (clock64() - t_start) > budget)) {
                         if (lane == 0) atomicOr(p.status, kDevErrTimeout);
                         break;
                     }
+                    __nanosleep(64);
                 }
+                // sum over the window of (A_T)^k v_k (lane's own power), reduce-scattered
+                packed_mv_gr<K>(tab + Dm::OFF_ATL + lane * MS, v, tmp);
+                const float part = reduce_scatter<S, Dm::P2, Dm::SH>(tmp, lane);
+                zi_lane = __shfl_sync(0xffffffffu, part, (lane < S ? lane : 0) << Dm::SH);
             }
             if (cur + 1 < p.n_tiles) {
                 // the resolved carry A_T Z + tile carry (read by the signal's next tile only)
@@ -413,7 +393,7 @@ __global__ void __launch_bounds__((kBatchW + 1) * 32, 1) sos_batch_kernel(const 
 #pragma unroll 1
                 for (int v = 1; v < W; ++v) c = lane_mv_rows<S>(acr, c) + ab[v * S + li];
                 if (tile > sg->tile0 && lane < S)
-                    st_relaxed_b64(p.desc + static_cast<size_t>(tile) * S + lane, pack_word((p.epoch << 2) | 1u, c));
+                    st_relaxed_b64(p.desc + static_cast<size_t>(tile) * 2 * S + lane, pack_word((p.epoch << 2) | 1u, c));
                 if (lane < S) agg[slot * S + lane] = c;
                 if (lane == 0) {
                     fold_count[slot] = 0;

@@ -122,7 +122,6 @@ size_t cascade_smem(int K, int N);
 
 // ---- PH-factorization kernel with a skewed direct-form-II particular pass (sosfilt_lane.cuh)
 constexpr int kLaneW = 7;  // compute warps per block, one group each; a tile is kLaneW groups
-constexpr int kLaneQ = 1;  // predecessors per lane and lookback round (rounds of 32 kLaneQ tiles)
 
 // Per-section constants of the skewed-pass kernel, in the kernel's domain (b / b0 and b0 = 1 when
 // normalized; carried state = zscale * true state).
@@ -142,7 +141,7 @@ struct LaneParams {
     const float *zi;            // device [K][2] initial state of this pass (true domain) or nullptr
     float *zf;                  // device [K][2] final state of this pass or nullptr
     float gain;                 // input multiplier (product of all b0 when normalized; first pass only)
-    unsigned long long *desc;   // [n_tiles][2K] tagged carry words
+    unsigned long long *desc;   // [n_tiles][2][2K] tagged carry words: local, resolved
     unsigned long long *ticket;
     unsigned long long ticket_base;
     unsigned int epoch;
@@ -150,7 +149,6 @@ struct LaneParams {
     long long spin_budget;
     int aligned;                // x and y 16-byte aligned
     int m_last;                 // position of the signal's last sample inside its lane
-    int deterministic;          // fixed lookback composition (descriptors [n_tiles][2][2K]: local, resolved)
     const float *tab;           // global table block, layout LaneDims<K, N>
     unsigned long long *trace;  // nullptr, or [n_tiles][kTraceSlots] phase trace (kLaneTrace*)
     long long trace_tiles;
@@ -204,7 +202,7 @@ struct BatchParams {
     const BatchSig *sigs;
     const int *tile_sig;        // [n_tiles] signal of each global tile
     long long n_tiles;
-    unsigned long long *desc;   // [n_tiles][2K] tagged carry words
+    unsigned long long *desc;   // [n_tiles][2][2K] tagged carry words: local, resolved
     unsigned long long *ticket;
     unsigned long long ticket_base;
     unsigned int epoch;

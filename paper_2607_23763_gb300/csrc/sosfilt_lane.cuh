@@ -18,8 +18,9 @@
 //      blocks.  Lane 31's inclusive state is the group's local carry.
 //   3. a coordinator warp folds the tile's local carries, publishes the tile carry, resolves the
 //      tile's incoming 2K-word state by decoupled lookback over tiles (Sec. IV-B, Eq. 25 on the
-//      cascade state) and derives every group's incoming state Z.  A lookback round covers 32 Q
-//      predecessors (Q per lane, combined by Horner's rule with A_T).
+//      cascade state) and derives every group's incoming state Z.  The composition is fixed: the
+//      resolved carry of the last tile at a multiple of 32 and the local carries after it, so
+//      that outputs are reproducible bit for bit.
 //   4. homogeneous correction (Eq. 24 once for the whole cascade): lane l's true incoming state is
 //      S_l + (M_N)^l Z, and sample m of its row gains sum_j H_j(m) [S_l + (M_N)^l Z]_j.  The rows'
 //      states go to shared memory and the correction runs across the rows: each lane takes four
@@ -54,19 +55,15 @@ struct LaneDims {
     // row-state pitch: S rounded up to whole 16-byte words, an odd number of them
     static constexpr int S4 = (S + 3) / 4;
     static constexpr int RSP = 4 * ((S4 & 1) ? S4 : S4 + 1);
-    // table block (copied to shared memory up to TAB): (M_N)^lane [32][MS], (A_T)^(Q lane) [32][MS]
-    // (Q = kLaneQ predecessors per lane and lookback round), A_C dense column-major, the basis in
-    // [S][N] (read in chunks of V samples), A_T dense, A_T packed [MS]; global only: (A_T)^(32 Q w)
-    // dense for w = 1..kMaxWin
+    // table block: (M_N)^lane [32][MS], (A_T)^lane [32][MS], A_C dense column-major, the basis
+    // [S][N] (read in chunks of V samples), A_T dense
     static constexpr int OFF_ATL = 32 * MS;
     static constexpr int OFF_AC = 64 * MS;
     static constexpr int OFF_H = OFF_AC + FULL;
     static constexpr int OFF_AT = OFF_H + N * S;
-    static constexpr int OFF_ATP = OFF_AT + FULL;
-    static constexpr int TAB = OFF_ATP + MS;
-    static constexpr int OFF_AW = TAB;
-    static constexpr int TAB_GLOBAL = OFF_AW + kMaxWin * FULL;
-    // the shared-memory copy: (M_N)^lane, (A_T)^lane when ATL_SHARED, then A_C .. A_T packed
+    static constexpr int TAB = OFF_AT + FULL;
+    static constexpr int TAB_GLOBAL = TAB;
+    // the shared-memory copy: (M_N)^lane, (A_T)^lane when ATL_SHARED, then A_C .. A_T
     static constexpr int SM_AC = ATL_SHARED ? OFF_AC : OFF_ATL;
     static constexpr int SM_TAB = SM_AC + (TAB - OFF_AC);
 };
@@ -319,8 +316,6 @@ __global__ void __launch_bounds__((kLaneW + 1) * 32, LaneDims<K, N>::BPS)
     float *agg = z_buf + 2 * W * S;                  // [2][S] tile carry under zero incoming state
     float *zs_tail = agg + 2 * S;                    // [S] lane-local state after the last sample
     const float *sATd = tab + Dm::SM_AC + (Dm::OFF_AT - Dm::OFF_AC);    // A_T dense column-major
-    const float *sATp = tab + Dm::SM_AC + (Dm::OFF_ATP - Dm::OFF_AC);   // A_T packed
-    const float *gAW = p.tab + Dm::OFF_AW;           // (A_T)^(32 Q w), w = 1.., dense (global)
     // tiles alternate between two slots; the incoming-state barrier has one per slot, so that it
     // never runs two phases ahead of a waiter
     __shared__ unsigned long long bar_local[2], bar_zready[2], bar_ticket[8];
@@ -390,17 +385,18 @@ __global__ void __launch_bounds__((kLaneW + 1) * 32, LaneDims<K, N>::BPS)
             const float *abuf = a_buf + slot * W * S;
             const float acc_i = agg[slot * S + (lane < S ? lane : 0)];
             float tmp[S];
-            // descriptor of a tile: its carry words (local, then overwritten by the resolved carry), or
-            // in the deterministic mode two slots, local then resolved
-            const int dstride = p.deterministic ? 2 * S : S;
-            unsigned long long *dcur = p.desc + static_cast<size_t>(cur) * dstride + (p.deterministic ? S : 0);
+            // descriptor of a tile: two slots of 2K tagged words, its local carry (posted by the fold)
+            // and its resolved carry (posted below)
+            unsigned long long *dcur = p.desc + static_cast<size_t>(cur) * 2 * S + S;
             float zi_lane = 0.f;
             if (cur == 0) {
                 zi_lane = zinit(lane < S ? lane : 0);
-            } else if (p.deterministic) {
-                // fixed composition: the resolved carry of the anchor tile a (the last multiple of 32
-                // before cur) and the local carries of tiles a + 1 .. cur - 1, whichever of them have
-                // resolved meanwhile, so that the sum does not depend on timing
+            } else {
+                // decoupled lookback with a fixed composition: the resolved carry of the anchor tile a
+                // (the last multiple of 32 before cur) and the local carries of tiles a + 1 .. cur - 1,
+                // whichever of them have resolved meanwhile, so that the sum does not depend on timing
+                // and outputs are reproducible bit for bit; the anchors form a chain of one hop per 32
+                // tiles
                 const long long a = ((cur - 1) / 32) * 32;
                 const int ja = static_cast<int>(cur - 1 - a);  // the anchor's lane
                 const long long pred = cur - 1 - lane;
@@ -410,8 +406,7 @@ __global__ void __launch_bounds__((kLaneW + 1) * 32, LaneDims<K, N>::BPS)
                     bool ok = true;
                     if (lane <= ja) {
                         const unsigned want = lane == ja ? tagG : tagL;
-                        const unsigned long long *dp =
-                            p.desc + static_cast<size_t>(pred) * 2 * S + (lane == ja ? S : 0);
+                        const unsigned long long *dp = p.desc + static_cast<size_t>(pred) * 2 * S + (lane == ja ? S : 0);
 #pragma unroll
                         for (int q = 0; q < S; q += 2) {
                             unsigned long long x0, x1;
@@ -429,104 +424,13 @@ __global__ void __launch_bounds__((kLaneW + 1) * 32, LaneDims<K, N>::BPS)
                         if (lane == 0) atomicOr(p.status, kDevErrTimeout);
                         break;
                     }
-                    __nanosleep(64);
+                    __nanosleep(64);  // a short nap: the successors' lookbacks wait on this tile
                 }
+                // sum over the window of (A_T)^k v_k: each lane applies its own power, then a
+                // reduce-scatter leaves word i of the sum in lane i
                 packed_mv<K>(sATl + lane * MS, v, tmp);
-                float part = reduce_scatter<S, Dm::P2, Dm::SH>(tmp, lane);
+                const float part = reduce_scatter<S, Dm::P2, Dm::SH>(tmp, lane);
                 zi_lane = __shfl_sync(0xffffffffu, part, (lane < S ? lane : 0) << Dm::SH);
-            } else {
-                // decoupled lookback over tiles, 32 Q predecessors per round: lane l takes the
-                // predecessors at distance 32 Q win + Q l + i + 1, i < Q
-                constexpr int Q = kLaneQ;
-                const long long t_start = clock64();
-                int win = 0;
-                for (;;) {
-                    const long long pbase = cur - 1 - 32LL * Q * win - static_cast<long long>(Q) * lane;
-                    float v[Q][S];
-                    int stq[Q];
-#pragma unroll
-                    for (int i = 0; i < Q; ++i) {
-                        const long long pred = pbase - i;
-                        if (pred >= 0) {
-                            const unsigned long long *dp = p.desc + static_cast<size_t>(pred) * S;
-                            bool allG = true, allL = true;
-#pragma unroll
-                            for (int q = 0; q < S; q += 2) {
-                                unsigned long long a, b;
-                                ld_relaxed_v2(dp + q, a, b);
-                                const unsigned ta = static_cast<unsigned>(a >> 32), tb = static_cast<unsigned>(b >> 32);
-                                allG = allG && ta == tagG && tb == tagG;
-                                allL = allL && ta == tagL && tb == tagL;
-                                v[i][q] = __uint_as_float(static_cast<unsigned>(a));
-                                v[i][q + 1] = __uint_as_float(static_cast<unsigned>(b));
-                            }
-                            stq[i] = allG ? 2 : (allL ? 1 : 0);
-                        } else {
-                            stq[i] = 2;  // the signal's initial state is the resolved carry of tile -1
-#pragma unroll
-                            for (int q = 0; q < S; ++q) v[i][q] = (pred == -1) ? zinit(q) : 0.f;
-                        }
-                    }
-                    int ig = Q;  // the lane's nearest resolved predecessor
-                    bool lane_ok = true;
-#pragma unroll
-                    for (int i = Q - 1; i >= 0; --i) ig = stq[i] == 2 ? i : ig;
-#pragma unroll
-                    for (int i = 0; i < Q; ++i) lane_ok = lane_ok && (i > ig || stq[i] != 0);
-                    const unsigned glob = __ballot_sync(0xffffffffu, ig < Q);
-                    const int j = glob ? __ffs(glob) - 1 : 32;
-                    const unsigned need = (j >= 31) ? 0xffffffffu : ((2u << j) - 1u);
-                    if (__ballot_sync(0xffffffffu, !lane_ok) & need) {
-                        if (__any_sync(0xffffffffu, (clock64() - t_start) > budget)) {
-                            if (lane == 0) atomicOr(p.status, kDevErrTimeout);
-                            break;
-                        }
-                        // a short nap: the successors' lookbacks wait on this tile's result
-                        __nanosleep(64);
-                        continue;
-                    }
-                    // the lane's predecessors up to the nearest resolved one, by Horner's rule:
-                    // acc = sum_i (A_T)^i v_i
-                    float acc[S];
-#pragma unroll
-                    for (int i = 0; i < Q; ++i) {
-                        const bool inc = lane < j || (lane == j && i <= ig);
-                        if (!inc) {
-#pragma unroll
-                            for (int q = 0; q < S; ++q) v[i][q] = 0.f;
-                        }
-                    }
-#pragma unroll
-                    for (int q = 0; q < S; ++q) acc[q] = v[Q - 1][q];
-#pragma unroll
-                    for (int i = Q - 2; i >= 0; --i) {
-                        float t2[S];
-                        packed_mv<K>(sATp, acc, t2);
-#pragma unroll
-                        for (int q = 0; q < S; ++q) acc[q] = t2[q] + v[i][q];
-                    }
-                    // sum over the lanes of (A_T)^(Q lane) acc_lane: each lane applies its own power,
-                    // then a reduce-scatter leaves word i of the sum in lane i
-                    packed_mv<K>(sATl + lane * MS, acc, tmp);
-                    float part = reduce_scatter<S, Dm::P2, Dm::SH>(tmp, lane);
-                    part = __shfl_sync(0xffffffffu, part, (lane < S ? lane : 0) << Dm::SH);
-                    if (win == 0) {
-                        zi_lane += part;
-                    } else {
-                        const float *Aw = gAW + (win - 1) * Dm::FULL;
-                        float y = 0.f;
-                        const int row = lane < S ? lane : 0;
-#pragma unroll
-                        for (int jj = 0; jj < S; ++jj)
-                            y = fmaf(__ldg(Aw + jj * S + row), __shfl_sync(0xffffffffu, part, jj), y);
-                        zi_lane += y;
-                    }
-                    if (j < 32) break;
-                    if (++win > kMaxWin) {  // predecessors too far behind: report and give up
-                        if (lane == 0) atomicOr(p.status, kDevErrTimeout);
-                        break;
-                    }
-                }
             }
             if (tr) tr[2] = global_ns();
             if (cur + 1 < p.n_tiles) {
@@ -724,8 +628,7 @@ __global__ void __launch_bounds__((kLaneW + 1) * 32, LaneDims<K, N>::BPS)
 #pragma unroll 1
                 for (int v = 1; v < W; ++v) c = lane_mv<S>(sACd, c, lane) + abt[v * S + li];
                 if (tile > 0 && lane < S)
-                    st_relaxed_b64(p.desc + static_cast<size_t>(tile) * (p.deterministic ? 2 * S : S) + lane,
-                                   pack_word((p.epoch << 2) | 1u, c));
+                    st_relaxed_b64(p.desc + static_cast<size_t>(tile) * 2 * S + lane, pack_word((p.epoch << 2) | 1u, c));
                 if (lane < S) agg[slot * S + lane] = c;
                 if (lane == 0) {
                     fold_count[slot] = 0;

@@ -112,8 +112,9 @@ def test_batch_repeated_calls_reuse_scratch(dev):
     torch.cuda.synchronize()
     for ys in outs[1:]:
         for a, b in zip(outs[0], ys):
+            # batched runs compose every tile's incoming state the same way: bit-identical repeats
             assert torch.isfinite(b).all()
-            assert float((a - b).abs().max()) <= 1e-3 * max(1e-30, float(a.abs().max()))
+            assert torch.equal(a, b)
     for f in fs:
         f.close()
 
