@@ -56,16 +56,6 @@ __device__ __forceinline__ void packed_mv_gr(const float *__restrict__ A, const 
     }
 }
 
-// Lane-parallel y = A x for a dense column-major S x S matrix in global memory.
-template <int S>
-__device__ __forceinline__ float lane_mv_g(const float *__restrict__ A, float xi, int lane) {
-    float y = 0.f;
-    const int row = lane < S ? lane : 0;
-#pragma unroll
-    for (int j = 0; j < S; ++j) y = fmaf(__ldg(A + j * S + row), __shfl_sync(0xffffffffu, xi, j), y);
-    return y;
-}
-
 // Row `lane` of a dense column-major S x S matrix in global memory, into registers (one latency
 // for a chain of products with the same matrix).
 template <int S>

@@ -125,14 +125,6 @@ __device__ __forceinline__ float reduce_scatter(float (&t)[S], int lane) {
     return t[0];
 }
 
-template <int S>
-__device__ __forceinline__ float lane_select(const float (&v)[S], int i) {
-    float r = 0.f;
-#pragma unroll
-    for (int k = 0; k < S; ++k) r = (k == i) ? v[k] : r;
-    return r;
-}
-
 // Zero-state pass of one group through section s (registers only); the lane's N samples are held as
 // N/2 (even, odd) pairs so both divide-and-conquer chains share packed FMAs.
 template <int N, bool NORM>

@@ -115,25 +115,6 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
     return true;
 }
 
-// Wait for the phase with the given parity, sleeping with exponential backoff (up to max_ns)
-// between polls so that waiting warps leave the issue slots to the computing ones; false (and the
-// timeout status bit) once `budget` cycles have passed.
-__device__ __forceinline__ bool mbar_wait_backoff(unsigned long long *bar, unsigned parity, long long budget,
-                                                  int *status, unsigned max_ns) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const long long t0 = clock64();
-    unsigned ns = 32;
-    for (;;) {
-        __nanosleep(ns);
-        if (mbar_try_wait(bar, parity)) return true;
-        if (clock64() - t0 > budget) {
-            atomicOr(status, kDevErrTimeout);
-            return false;
-        }
-        ns = ns < max_ns ? 2 * ns : max_ns;
-    }
-}
-
 // Ampere-style asynchronous 16-byte global -> shared copies (L2 only).
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
