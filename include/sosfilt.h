@@ -281,10 +281,10 @@ sos_status sos_filter_trace(sos_filter *f, uint64_t *buf_dev, int64_t capacity_b
  * creates the filter (sos_filter_create allocates its tables once) and then filters
  * with this entry point, which calls no cudaMalloc, cudaFree or other allocating routine:
  * the scratch memory of a run (lookback descriptors and ticket counter) lives in one
- * fixed array of 4 MiB + 256 B in the library's device code, which every GPU that loads
- * the library holds until the process exits.
- *   Arguments and results are those of sos_filter_run (always the cascade carry with the
- *   library's default N).
+ * fixed array of 4.6 MiB in the library's device code, which every GPU that loads the
+ * library holds until the process exits.
+ *   Arguments and results are those of sos_filter_run (always the default solver, PH
+ *   factorization at N = 64, whose outputs are bit-identical from run to run).
  *   n            at most SOS_NOALLOC_MAX_SAMPLES samples per call, else SOS_EBUDGET
  *   The first call on a device looks up the array's device address on the current device
  *   (a one-time set-up); make that first call before any stream capture.

@@ -744,7 +744,7 @@ sos_status run_cascade(sos_filter *f, const float *x, float *y, int64_t n, const
 template <int K, int N>
 sos_status launch_lane_pass(sos_filter *f, LanePass &ps, const float *x, float *y, long long n, long long G,
                             long long n_tiles, long long grid, const float *zi, float *zf, bool first, bool aligned,
-                            cudaStream_t s) {
+                            cudaStream_t s, const sosk::Scratch *sc = nullptr, unsigned sc_epoch = 0) {
     static_assert(K >= 1 && K <= sosk::kMaxPass, "pass size");
     auto p = std::make_unique<sosk::LaneParams<K>>();
     std::memset(p.get(), 0, sizeof(*p));
@@ -756,10 +756,19 @@ sos_status launch_lane_pass(sos_filter *f, LanePass &ps, const float *x, float *
     p->zi = zi;
     p->zf = zf;
     p->gain = first ? static_cast<float>(f->gain) : 1.0f;
-    p->desc = f->d_desc;
-    p->ticket = f->d_ticket;
-    p->ticket_base = f->ticket_base;
-    p->epoch = next_epoch(f, s);
+    if (sc) {
+        // caller-provided scratch (sos_filter_run_noalloc): its ticket counter starts from zero
+        if (cudaMemsetAsync(sc->ticket, 0, sizeof(unsigned long long), s) != cudaSuccess) return SOS_ECUDA;
+        p->desc = sc->desc;
+        p->ticket = sc->ticket;
+        p->ticket_base = 0;
+        p->epoch = sc_epoch;
+    } else {
+        p->desc = f->d_desc;
+        p->ticket = f->d_ticket;
+        p->ticket_base = f->ticket_base;
+        p->epoch = next_epoch(f, s);
+    }
     p->status = f->d_status;
     p->spin_budget = f->tuning.spin_budget_cycles ? f->tuning.spin_budget_cycles : kDefaultSpinBudget;
     p->aligned = aligned ? 1 : 0;
@@ -781,17 +790,17 @@ sos_status launch_lane_pass(sos_filter *f, LanePass &ps, const float *x, float *
     }
     cudaError_t e = sosk::launch_lane<K, N>(f->norm, *p, grid, s);
     if (e != cudaSuccess) return SOS_ECUDA;
-    f->ticket_base += static_cast<unsigned long long>(n_tiles + grid);
+    if (!sc) f->ticket_base += static_cast<unsigned long long>(n_tiles + grid);
     return SOS_OK;
 }
 
 template <int N>
 sos_status launch_lane_any(int K, sos_filter *f, LanePass &ps, const float *x, float *y, long long n, long long G,
                            long long n_tiles, long long grid, const float *zi, float *zf, bool first, bool aligned,
-                           cudaStream_t s) {
+                           cudaStream_t s, const sosk::Scratch *sc = nullptr, unsigned sc_epoch = 0) {
     switch (K) {
 #define SOSK_CASE(k) \
-    case k: return launch_lane_pass<k, N>(f, ps, x, y, n, G, n_tiles, grid, zi, zf, first, aligned, s);
+    case k: return launch_lane_pass<k, N>(f, ps, x, y, n, G, n_tiles, grid, zi, zf, first, aligned, s, sc, sc_epoch);
         SOSK_CASE(1) SOSK_CASE(2) SOSK_CASE(3) SOSK_CASE(4) SOSK_CASE(5) SOSK_CASE(6) SOSK_CASE(7) SOSK_CASE(8)
 #undef SOSK_CASE
         default: return SOS_EINVAL;
@@ -839,63 +848,6 @@ int solver_of(const sos_filter *f) {
     if (t.solver) return t.solver;
     if (t.carry || t.lookback_width || t.N == 128) return SOS_SOLVER_CR;
     return SOS_SOLVER_PH;
-}
-
-// ---- cascade run with caller-provided scratch (used by sos_filter_run_noalloc only)
-template <int K, int N>
-sos_status launch_cascade_pass_scratch(sos_filter *f, CasPass &ps, const sosk::SecCoef *sec, const float *x,
-                                       float *y, long long n, long long G, long long n_tiles, long long grid,
-                                       const float *zi, float *zf, bool first, bool aligned,
-                                       const sosk::Scratch &sc, unsigned epoch, cudaStream_t s) {
-    auto p = std::make_unique<sosk::CasParams<K, N>>();
-    std::memset(p.get(), 0, sizeof(*p));
-    p->x = x;
-    p->y = y;
-    p->n = n;
-    p->G = G;
-    p->n_tiles = n_tiles;
-    p->zi = zi;
-    p->zf = zf;
-    p->gain = first ? static_cast<float>(f->gain) : 1.0f;
-    p->desc = sc.desc;
-    p->ticket = sc.ticket;
-    p->ticket_base = 0;
-    p->epoch = epoch;
-    p->status = f->d_status;
-    p->spin_budget = f->tuning.spin_budget_cycles ? f->tuning.spin_budget_cycles : kDefaultSpinBudget;
-    p->aligned = aligned ? 1 : 0;
-    p->tab = ps.d_tab;
-    for (int j = 0; j < K; ++j) p->sec[j] = sec[j];
-    for (int j = 0; j < 2 * K; ++j)
-        for (int m = 0; m < N; ++m) p->H[j][m] = ps.H[static_cast<size_t>(j) * N + m];
-    if (zf) {
-        const long long C = 32LL * N;
-        const long long tp = n - 1 - (G - 1) * C;
-        if (ps.tail_p != tp) {
-            ps.A_tail.assign(packed_floats(K), 0.f);
-            pack_into(dpow(ps.M1, tp + 1), K, ps.A_tail.data());
-            ps.tail_p = tp;
-        }
-        std::memcpy(p->A_tail, ps.A_tail.data(), sizeof(float) * packed_floats(K));
-    }
-    if (cudaMemsetAsync(sc.ticket, 0, sizeof(unsigned long long), s) != cudaSuccess) return SOS_ECUDA;
-    return sosk::launch_cascade<K, N>(f->norm, *p, grid, s) == cudaSuccess ? SOS_OK : SOS_ECUDA;
-}
-
-template <int N>
-sos_status launch_cascade_any_scratch(int K, sos_filter *f, CasPass &ps, const sosk::SecCoef *sec, const float *x,
-                                      float *y, long long n, long long G, long long n_tiles, long long grid,
-                                      const float *zi, float *zf, bool first, bool aligned,
-                                      const sosk::Scratch &sc, unsigned epoch, cudaStream_t s) {
-    switch (K) {
-#define SOSK_CASE(k)                                                                                      \
-    case k:                                                                                               \
-        return launch_cascade_pass_scratch<k, N>(f, ps, sec, x, y, n, G, n_tiles, grid, zi, zf, first, aligned, \
-                                                 sc, epoch, s);
-        SOSK_CASE(1) SOSK_CASE(2) SOSK_CASE(3) SOSK_CASE(4) SOSK_CASE(5) SOSK_CASE(6) SOSK_CASE(7) SOSK_CASE(8)
-#undef SOSK_CASE
-        default: return SOS_EINVAL;
-    }
 }
 
 // ---- autotuned launch choice (sos_autotune): per device, section count (1..8) and length bucket
@@ -1353,8 +1305,8 @@ namespace sosk {
 // memory (sc); every pass takes a fresh epoch from next_epoch.  Allocates nothing.
 int filter_device(const sos_filter *f) { return f->device; }
 
-sos_status run_cascade_scratch(sos_filter *f, const float *x, float *y, int64_t n, const float *zi, float *zf,
-                               cudaStream_t s, const Scratch &sc, unsigned (*next_epoch)(int, cudaStream_t)) {
+sos_status run_lane_scratch(sos_filter *f, const float *x, float *y, int64_t n, const float *zi, float *zf,
+                            cudaStream_t s, const Scratch &sc, unsigned (*next_epoch)(int, cudaStream_t)) {
     if (!f || n < 0 || (n > 0 && (!x || !y))) return SOS_EINVAL;
     if (x != y && n > 0 && ranges_overlap(x, y, n)) return SOS_EINVAL;
     if (cudaSetDevice(f->device) != cudaSuccess) return SOS_ECUDA;
@@ -1367,31 +1319,24 @@ sos_status run_cascade_scratch(sos_filter *f, const float *x, float *y, int64_t 
         }
         return SOS_OK;
     }
-    const int N = f->K == 1 ? 64 : 32;  // the library defaults of the cascade carry
-    const int ci = (N == 32) ? 0 : 1;
-    const int ti = table_index(N);
+    // the default solver (PH factorization, N = 64) with the descriptors and ticket counter in sc
+    constexpr int N = 64;
     const long long C = 32LL * N;
-    const long long W = cascade_warps(N);
+    const long long W = kLaneW;
     const long long G = (n + C - 1) / C;
     const long long n_tiles = (G + W - 1) / W;
-    if (static_cast<size_t>(n_tiles) * 2 * kMaxPass > sc.desc_words) return SOS_EBUDGET;
+    if (static_cast<size_t>(n_tiles) * 2 * 2 * kMaxPass > sc.desc_words) return SOS_EBUDGET;
     const bool aligned = (reinterpret_cast<uintptr_t>(x) % 16 == 0) && (reinterpret_cast<uintptr_t>(y) % 16 == 0);
     const float *src = x;
-    for (auto &ps : f->cas[ci].passes) {
-        const int bps = cascade_blocks_per_sm(ps.kp, N, f->norm);
+    for (auto &ps : f->lane[1]) {
+        const int bps = lane_blocks_per_sm(ps.kp, N, f->norm);
         if (bps <= 0) return SOS_ECUDA;
         long long grid = static_cast<long long>(bps) * sm_count(f->device);
         if (grid > n_tiles) grid = n_tiles;
         const unsigned epoch = next_epoch(f->device, s);
-        sos_status st;
-        if (N == 32)
-            st = launch_cascade_any_scratch<32>(ps.kp, f, ps, &f->tables[ti].sec[ps.k0], src, y, n, G, n_tiles, grid,
-                                                zi ? zi + 2 * ps.k0 : nullptr, zf ? zf + 2 * ps.k0 : nullptr,
-                                                ps.k0 == 0, aligned, sc, epoch, s);
-        else
-            st = launch_cascade_any_scratch<64>(ps.kp, f, ps, &f->tables[ti].sec[ps.k0], src, y, n, G, n_tiles, grid,
-                                                zi ? zi + 2 * ps.k0 : nullptr, zf ? zf + 2 * ps.k0 : nullptr,
-                                                ps.k0 == 0, aligned, sc, epoch, s);
+        const sos_status st = launch_lane_any<64>(ps.kp, f, ps, src, y, n, G, n_tiles, grid,
+                                                  zi ? zi + 2 * ps.k0 : nullptr, zf ? zf + 2 * ps.k0 : nullptr,
+                                                  ps.k0 == 0, aligned, s, &sc, epoch);
         if (st != SOS_OK) return st;
         src = y;
     }

@@ -1,4 +1,4 @@
-// sos_filter_run_noalloc: the cascade-carry filter run with its scratch memory (lookback
+// sos_filter_run_noalloc: the default filter run (PH factorization) with its scratch memory (lookback
 // descriptors and ticket counter) in one file-scope device array instead of library
 // allocations.  For callers that cannot allocate device memory while they filter: a real-time
 // thread (an audio or radio receive loop) must not call cudaMalloc/cudaFree, which can block
@@ -15,15 +15,17 @@
 
 namespace sosk {
 int filter_device(const sos_filter *f);
-sos_status run_cascade_scratch(sos_filter *f, const float *x, float *y, int64_t n, const float *zi, float *zf,
-                               cudaStream_t s, const Scratch &sc, unsigned (*next_epoch)(int, cudaStream_t));
+sos_status run_lane_scratch(sos_filter *f, const float *x, float *y, int64_t n, const float *zi, float *zf,
+                            cudaStream_t s, const Scratch &sc, unsigned (*next_epoch)(int, cudaStream_t));
 }  // namespace sosk
 
 namespace {
 
 // Word 0: ticket counter; words 32..: lookback descriptors (tag << 32 | float bits).  Sized for
-// SOS_NOALLOC_MAX_SAMPLES samples per call (tiles of 8192 samples, up to 16 words each).
-constexpr size_t kDescWords = (static_cast<size_t>(SOS_NOALLOC_MAX_SAMPLES) / 8192) * 16;
+// SOS_NOALLOC_MAX_SAMPLES samples per call (PH tiles of 7 x 2048 samples, two slots of up to 16
+// words each).
+constexpr size_t kDescWords =
+    (static_cast<size_t>(SOS_NOALLOC_MAX_SAMPLES) / (sosk::kLaneW * sosk::kL * 64) + 1) * 2 * 2 * sosk::kMaxPass;
 constexpr size_t kScratchWords = 32 + kDescWords;
 
 static __device__ __align__(256) unsigned long long g_noalloc_scratch[kScratchWords];
@@ -63,6 +65,6 @@ extern "C" sos_status sos_filter_run_noalloc(sos_filter *f, const float *x_dev, 
     sc.ticket = g_ptr[dev];
     sc.desc = g_ptr[dev] + 32;
     sc.desc_words = kDescWords;
-    return sosk::run_cascade_scratch(f, x_dev, y_dev, n, zi_dev, zf_dev, static_cast<cudaStream_t>(stream), sc,
-                                     next_epoch_dev);
+    return sosk::run_lane_scratch(f, x_dev, y_dev, n, zi_dev, zf_dev, static_cast<cudaStream_t>(stream), sc,
+                                  next_epoch_dev);
 }
