@@ -197,8 +197,8 @@ __global__ void __launch_bounds__((kBatchW + 1) * 32, 1) sos_batch_kernel(const 
                 const float part = reduce_scatter<S, Dm::P2, Dm::SH>(tmp, lane);
                 zi_lane = __shfl_sync(0xffffffffu, part, (lane < S ? lane : 0) << Dm::SH);
             }
-            if (cur + 1 < p.n_tiles) {
-                // the resolved carry A_T Z + tile carry (read by the signal's next tile only)
+            if (((cur - tile0) & 31) == 0 && cur + 1 < p.n_tiles) {
+                // the resolved carry A_T Z + tile carry (read only at the signal's anchor tiles)
                 const float gl = lane_mv_rows<S>(atr, zi_lane) + acc_i;
                 if (lane < S) st_relaxed_b64(dcur + lane, pack_word(tagG, gl));
             }

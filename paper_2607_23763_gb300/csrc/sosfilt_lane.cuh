@@ -433,8 +433,9 @@ __global__ void __launch_bounds__((kLaneW + 1) * 32, LaneDims<K, N>::BPS)
                 zi_lane = __shfl_sync(0xffffffffu, part, (lane < S ? lane : 0) << Dm::SH);
             }
             if (tr) tr[2] = global_ns();
-            if (cur + 1 < p.n_tiles) {
-                const float gl = lane_mv<S>(sATd, zi_lane, lane) + acc_i;  // A_T Z + tile carry
+            if ((cur & 31) == 0 && cur + 1 < p.n_tiles) {
+                // only anchor tiles' resolved carries are read: A_T Z + tile carry
+                const float gl = lane_mv<S>(sATd, zi_lane, lane) + acc_i;
                 if (lane < S) st_relaxed_b64(dcur + lane, pack_word(tagG, gl));
             }
             // incoming state of each group of the tile: Z_0 = Z, Z_{v+1} = A_C Z_v + a_v
