@@ -76,8 +76,11 @@ def particular(coef, xb):
     return w, states
 
 
-def ph_filter(sos, x, zi=None, N=32, L=32, W=8):
-    """Filter x as the kernel does; returns (y, zf)."""
+def ph_filter(sos, x, zi=None, N=32, L=32, W=8, anchored=False):
+    """Filter x as the kernel does; returns (y, zf).  With anchored, a tile's incoming state is
+    composed as the PH kernels' lookback does it: the resolved carry of the anchor tile (the last
+    multiple of 32 before it) and the local carries of the tiles after the anchor, each carried
+    forward with its power of A_T; only anchors resolve (inclusive = A_T Z + local carry)."""
     coef = [tuple(float(v) for v in row) for row in np.asarray(sos, dtype=np.float64).reshape(-1, 5)]
     K = len(coef)
     S = 2 * K
@@ -109,18 +112,42 @@ def ph_filter(sos, x, zi=None, N=32, L=32, W=8):
     # tiles of W groups, then the groups of each tile
     n_tiles = -(-G // W)
     Zg = np.zeros((G, S))
-    Zt = np.zeros(S) if zi is None else np.asarray(zi, dtype=np.float64).reshape(S).copy()
+    z0 = np.zeros(S) if zi is None else np.asarray(zi, dtype=np.float64).reshape(S).copy()
+    local = np.zeros((n_tiles, S))  # tile carries under zero incoming state (the fold)
     for tt in range(n_tiles):
-        z = Zt.copy()
         c = None
         for v in range(W):
             g = tt * W + v
             ag = a[g] if g < G else np.zeros(S)
+            c = ag.copy() if c is None else AC @ c + ag
+        local[tt] = c
+    Ztile = np.zeros((n_tiles, S))
+    if anchored:
+        resolved = {}
+        ATp = [np.linalg.matrix_power(AT, d) for d in range(33)]
+        for tt in range(n_tiles):
+            if tt == 0:
+                Ztile[tt] = z0
+            else:
+                anchor = ((tt - 1) // 32) * 32
+                z = ATp[tt - 1 - anchor] @ resolved[anchor]
+                for pred in range(anchor + 1, tt):
+                    z = z + ATp[tt - 1 - pred] @ local[pred]
+                Ztile[tt] = z
+            if tt % 32 == 0:
+                resolved[tt] = AT @ Ztile[tt] + local[tt]
+    else:
+        Zt = z0
+        for tt in range(n_tiles):
+            Ztile[tt] = Zt
+            Zt = AT @ Zt + local[tt]
+    for tt in range(n_tiles):
+        z = Ztile[tt].copy()
+        for v in range(W):
+            g = tt * W + v
             if g < G:
                 Zg[g] = z
-            z = AC @ z + ag
-            c = ag.copy() if c is None else AC @ c + ag
-        Zt = AT @ Zt + c
+                z = AC @ z + a[g]
     # correction, one pass over the samples
     Ml = [np.linalg.matrix_power(MN, l) for l in range(L)]
     y = w.reshape(G, L, N).copy()

@@ -65,3 +65,20 @@ def test_skewed_df2_particular_matches_transposed_form(K, unit_b0):
         assert np.abs(w - w_ref).max() <= 1e-11 * np.abs(w_ref).max()
         assert np.abs(t - states[:, -1]).max() <= 1e-11 * scale
         assert np.abs(cap - states[:, m_cap]).max() <= 1e-11 * scale
+
+
+@pytest.mark.parametrize("n_tiles", [1, 2, 31, 32, 33, 64, 65, 97])
+def test_anchored_lookback_composition_matches_oracle(n_tiles):
+    # the PH kernels' fixed lookback composition (resolved carry of the last tile at a multiple of
+    # 32 plus the local carries after it) reproduces the sequential carry: small groups (N = 4,
+    # L = 4, W = 2) so that many tiles, across several anchors, stay cheap
+    sos = designs.butter_lowpass(6, 0.1)
+    n = n_tiles * 4 * 4 * 2 - 3
+    x = workloads.normal_f32(90 + n_tiles, n)
+    zi = np.random.default_rng(n_tiles).standard_normal((3, 2)) * 0.1
+    y, zf = PM.ph_filter(sos, x, zi=zi, N=4, L=4, W=2, anchored=True)
+    y_seq, zf_seq = PM.ph_filter(sos, x, zi=zi, N=4, L=4, W=2)
+    y_ref, zf_ref = oracle.sosfilt(sos, x, zi=zi, return_state=True)
+    assert np.abs(y - y_ref).max() <= 1e-11 * np.abs(y_ref).max()
+    assert np.abs(zf - zf_ref.reshape(-1)).max() <= 1e-11 * max(1.0, np.abs(zf_ref).max())
+    assert np.abs(y - y_seq).max() <= 1e-12 * np.abs(y_ref).max()
