@@ -179,6 +179,23 @@ def cpu_baseline_leg(x_host):
             "sample": f"the whole workload (2^{int(np.log2(n))} samples) once on one host core, {dt:.1f} s"}
 
 
+def cpu_wavefront_leg(x_host):
+    """The float64 oracle run as the multi-core wavefront of Sec. III-A on the host cores (one thread
+    per section at most: more would only wait), over a bounded sample of the workload; its output is
+    bit-identical to the one-core oracle's."""
+    import oracle
+    from workloads import designs
+    sos = designs.butter_lowpass(ORDER, WN)
+    threads = max(1, min(_cores(), ORDER // 2))
+    n = min(x_host.shape[0], 1 << 24)
+    oracle.sosfilt_wavefront(sos, x_host[:4096], threads=threads, block=8192)
+    t0 = time.perf_counter()
+    oracle.sosfilt_wavefront(sos, x_host[:n], threads=threads, block=8192, keep_output=False)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt / 1e9, "unit": "GS/s", "cores": threads, "kind": "oracle, multi-core wavefront",
+            "sample": f"first 2^{int(np.log2(n))} samples, groups of 8192 samples, {threads} threads, {dt:.2f} s"}
+
+
 def bench_ours(args):
     import torch
     import torch.distributed as dist
@@ -304,6 +321,7 @@ def bench_ours(args):
     }
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline_leg(x_host)
+        line["cpu_wavefront"] = cpu_wavefront_leg(x_host)
     if rank == 0:
         print(json.dumps(line), flush=True)
     f.close()

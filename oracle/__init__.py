@@ -23,6 +23,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sosfilt_oracle.c")
+_SRC_WAVE = os.path.join(_HERE, "sosfilt_wavefront.c")
 _LIB_PATH = os.path.join(_HERE, "_liboracle.so")
 _lib = None
 _lock = threading.Lock()
@@ -30,10 +31,12 @@ _lock = threading.Lock()
 
 def build(force: bool = False) -> str:
     """Compile the C oracle (-O2, no fast-math) into an in-tree shared library."""
-    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+    srcs = [_SRC, _SRC_WAVE]
+    if not force and os.path.exists(_LIB_PATH) and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(f)
+                                                        for f in srcs):
         return _LIB_PATH
     tmp = _LIB_PATH + ".tmp"
-    subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC], check=True)
+    subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-pthread", "-o", tmp, *srcs], check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -51,6 +54,8 @@ def _load():
                 fn.restype = ctypes.c_int
             lib.oracle_sosfilt_batch_f32.argtypes = [ctypes.c_int, vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_int]
             lib.oracle_sosfilt_batch_f32.restype = ctypes.c_int
+            lib.oracle_sosfilt_wavefront_f32.argtypes = [ctypes.c_int, vp, vp, i64, vp, vp, vp, i64, ctypes.c_int]
+            lib.oracle_sosfilt_wavefront_f32.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -106,6 +111,26 @@ def sosfilt_batch(sos_list, x_list, threads: int = 1, want_y: bool = True):
     ys = [y_all[o:o + n] for o, n in zip(x_off, ns)] if want_y else None
     zfs = [zf_all[o:o + k] for o, k in zip(sos_off, ks)]
     return ys, zfs
+
+
+def sosfilt_wavefront(sos, x, zi=None, return_state: bool = False, threads: int = 1, block: int = 4096,
+                      keep_output: bool = True):
+    """The same filtering as ``sosfilt`` for float32 x, run as the multi-core wavefront of Sec. III-A
+    (groups of ``block`` samples carried through the sections by ``threads`` host threads).  Output
+    and final state are bit-identical to ``sosfilt``'s."""
+    lib = _load()
+    sos = np.ascontiguousarray(np.asarray(sos, dtype=np.float64).reshape(-1, 5))
+    k = sos.shape[0]
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    n = x.shape[0]
+    y = np.empty(n, dtype=np.float64) if keep_output else None
+    zf = np.empty((k, 2), dtype=np.float64)
+    zi_arr = None if zi is None else np.ascontiguousarray(np.asarray(zi, dtype=np.float64).reshape(k, 2))
+    rc = lib.oracle_sosfilt_wavefront_f32(k, _ptr(sos), _ptr(x), n, _ptr(zi_arr), _ptr(y), _ptr(zf), int(block),
+                                          int(threads))
+    if rc != 0:
+        raise ValueError(f"oracle rejected the arguments or ran out of memory (code {rc})")
+    return (y, zf) if return_state else y
 
 
 def rel_err(y, y_ref) -> float:

@@ -252,3 +252,19 @@ def test_pins_catch_planted_mistakes(kind):
         v = _dense_section(sos[s], v, zi[s])
     caught = caught or not np.allclose(bad(sos, xx, zi=zi), v, atol=1e-9)
     assert caught, kind
+
+
+@pytest.mark.parametrize("K", [1, 2, 3, 8])
+@pytest.mark.parametrize("threads", [1, 2, 5])
+def test_wavefront_host_baseline_is_bit_identical(K, threads):
+    # the multi-core wavefront (Sec. III-A) hands each section's state from group to group in order,
+    # so it must reproduce the sequential oracle exactly, output and final state
+    from workloads import designs
+    sos = designs.random_sections(np.random.default_rng(K).uniform(size=(K, 3)))
+    zi = np.random.default_rng(100 + K).standard_normal((K, 2)) * 0.1
+    for n, block in [(0, 64), (1, 64), (63, 64), (64, 64), (5 * 64 + 3, 64), (20000, 4096)]:
+        x = np.random.default_rng(n + K).standard_normal(n).astype(np.float32)
+        y, zf = oracle.sosfilt(sos, x, zi=zi, return_state=True)
+        y2, zf2 = oracle.sosfilt_wavefront(sos, x, zi=zi, return_state=True, threads=threads, block=block)
+        assert np.array_equal(y, y2)
+        assert np.array_equal(zf, zf2)
