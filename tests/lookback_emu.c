@@ -1,0 +1,167 @@
+/*
+ * Host-thread emulation of the lookback protocol of the PH kernels (a test aid; it shares no code
+ * with the CUDA library).  Tiles are drawn from an ascending ticket counter by T worker threads
+ * (Sec. IV-A).  Tile t publishes its local carry in slot 0 of its descriptor, tagged words of
+ * (epoch << 2 | 1, float bits); it then composes its incoming state from the resolved carry of its
+ * anchor tile a = 32 floor((t - 1) / 32) (slot 1, tag epoch << 2 | 2) and the local carries of
+ * tiles a + 1 .. t - 1, with bounded spins, and an anchor tile publishes its resolved carry
+ * A_T Z + local.  Tile 0 starts from z0.  A tile whose number equals `silent` never publishes
+ * (failure injection): its successors' waits run out, set the status word and return.
+ *
+ * The composition is evaluated by Horner's rule from the anchor in float32, the same operations in
+ * the same order as emu_reference(), so a correct protocol gives bit-identical results whatever
+ * the interleaving of the threads.
+ */
+#include <pthread.h>
+#include <sched.h>
+#include <stdatomic.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+    int S;
+    int64_t n_tiles;
+    unsigned epoch;
+    _Atomic uint64_t *desc;  /* [n_tiles][2][S] */
+    const float *local;      /* [n_tiles][S] local carries */
+    const float *AT;         /* [S][S] row-major tile transition */
+    const float *z0;         /* [S] */
+    float *Z;                /* [n_tiles][S] incoming states (output) */
+    _Atomic int64_t ticket;
+    _Atomic int status;      /* 1: a wait ran out */
+    int64_t spin_limit;      /* polls before a wait gives up */
+    int64_t silent;          /* tile that never publishes, or -1 */
+} emu_ctx;
+
+static uint64_t pack(unsigned tag, float v) {
+    uint32_t b;
+    memcpy(&b, &v, sizeof b);
+    return ((uint64_t)tag << 32) | b;
+}
+
+static float payload(uint64_t w) {
+    uint32_t b = (uint32_t)w;
+    float v;
+    memcpy(&v, &b, sizeof v);
+    return v;
+}
+
+/* y = A x (S x S row-major), then y += b */
+static void mv_add(int S, const float *A, const float *x, const float *b, float *y) {
+    for (int i = 0; i < S; ++i) {
+        float acc = 0.f;
+        for (int j = 0; j < S; ++j) acc = acc + A[i * S + j] * x[j];
+        y[i] = acc + b[i];
+    }
+}
+
+/* Waits until every word of the S-word slot carries `tag` and copies the payloads; 0 on timeout. */
+static int wait_slot(emu_ctx *c, int64_t tile, int slot, unsigned tag, float *out) {
+    _Atomic uint64_t *w = c->desc + ((size_t)tile * 2 + (size_t)slot) * (size_t)c->S;
+    for (int64_t spin = 0;; ++spin) {
+        int ok = 1;
+        for (int i = 0; i < c->S; ++i) {
+            const uint64_t v = atomic_load_explicit(&w[i], memory_order_acquire);
+            if ((unsigned)(v >> 32) != tag) {
+                ok = 0;
+                break;
+            }
+            out[i] = payload(v);
+        }
+        if (ok) return 1;
+        if (spin >= c->spin_limit) return 0;
+        sched_yield();
+    }
+}
+
+static void publish(emu_ctx *c, int64_t tile, int slot, unsigned tag, const float *v) {
+    _Atomic uint64_t *w = c->desc + ((size_t)tile * 2 + (size_t)slot) * (size_t)c->S;
+    for (int i = 0; i < c->S; ++i) atomic_store_explicit(&w[i], pack(tag, v[i]), memory_order_release);
+}
+
+static void *emu_worker(void *arg) {
+    emu_ctx *c = (emu_ctx *)arg;
+    const int S = c->S;
+    const unsigned tagL = (c->epoch << 2) | 1u, tagG = (c->epoch << 2) | 2u;
+    float acc[64], v[64], tmp[64];
+    for (;;) {
+        const int64_t t = atomic_fetch_add(&c->ticket, 1);
+        if (t >= c->n_tiles || atomic_load(&c->status)) break;
+        if (t == c->silent) continue;  /* this tile's worker "dies" before publishing anything */
+        const float *loc = c->local + (size_t)t * S;
+        if (t > 0) publish(c, t, 0, tagL, loc);
+        if (t == 0) {
+            memcpy(acc, c->z0, sizeof(float) * (size_t)S);
+        } else {
+            const int64_t a = ((t - 1) / 32) * 32;
+            if (!wait_slot(c, a, 1, tagG, acc)) {
+                atomic_store(&c->status, 1);
+                break;
+            }
+            for (int64_t p = a + 1; p < t; ++p) {
+                if (!wait_slot(c, p, 0, tagL, v)) {
+                    atomic_store(&c->status, 1);
+                    return NULL;
+                }
+                mv_add(S, c->AT, acc, v, tmp);
+                memcpy(acc, tmp, sizeof(float) * (size_t)S);
+            }
+        }
+        memcpy(c->Z + (size_t)t * S, acc, sizeof(float) * (size_t)S);
+        if (t % 32 == 0 && t + 1 < c->n_tiles) {
+            mv_add(S, c->AT, acc, loc, tmp);
+            publish(c, t, 1, tagG, tmp);
+        }
+    }
+    return NULL;
+}
+
+/* One launch of the protocol over `desc` (kept by the caller between launches: its old tags must
+ * not be mistaken for this epoch's).  Returns 0, or 1 when some wait ran out. */
+int emu_run(int S, int64_t n_tiles, unsigned epoch, uint64_t *desc, const float *local, const float *AT,
+            const float *z0, float *Z, int threads, int64_t spin_limit, int64_t silent) {
+    if (S < 1 || S > 64 || n_tiles < 0 || threads < 1 || threads > 64) return -1;
+    emu_ctx c;
+    memset(&c, 0, sizeof c);
+    c.S = S;
+    c.n_tiles = n_tiles;
+    c.epoch = epoch;
+    c.desc = (_Atomic uint64_t *)desc;
+    c.local = local;
+    c.AT = AT;
+    c.z0 = z0;
+    c.Z = Z;
+    atomic_init(&c.ticket, 0);
+    atomic_init(&c.status, 0);
+    c.spin_limit = spin_limit;
+    c.silent = silent;
+    pthread_t tid[64];
+    int made = 0;
+    for (int i = 1; i < threads; ++i)
+        if (pthread_create(&tid[made], NULL, emu_worker, &c) == 0) ++made;
+    emu_worker(&c);
+    for (int i = 0; i < made; ++i) pthread_join(tid[i], NULL);
+    return atomic_load(&c.status);
+}
+
+/* The same composition evaluated tile after tile on one thread. */
+void emu_reference(int S, int64_t n_tiles, const float *local, const float *AT, const float *z0, float *Z) {
+    float *res = (float *)malloc(sizeof(float) * (size_t)S * (size_t)(n_tiles > 0 ? n_tiles : 1));
+    float acc[64], tmp[64];
+    for (int64_t t = 0; t < n_tiles; ++t) {
+        if (t == 0) {
+            memcpy(acc, z0, sizeof(float) * (size_t)S);
+        } else {
+            const int64_t a = ((t - 1) / 32) * 32;
+            memcpy(acc, res + (size_t)a * S, sizeof(float) * (size_t)S);
+            for (int64_t p = a + 1; p < t; ++p) {
+                mv_add(S, AT, acc, local + (size_t)p * S, tmp);
+                memcpy(acc, tmp, sizeof(float) * (size_t)S);
+            }
+        }
+        memcpy(Z + (size_t)t * S, acc, sizeof(float) * (size_t)S);
+        if (t % 32 == 0) mv_add(S, AT, acc, local + (size_t)t * S, res + (size_t)t * S);
+    }
+    free(res);
+}

@@ -1,0 +1,90 @@
+"""Host-thread emulation of the PH kernels' lookback protocol (tests/lookback_emu.c).
+
+Worker threads draw tiles from an ascending ticket counter, publish tagged local carries, compose
+each tile's incoming state from its anchor's resolved carry and the local carries after it with
+bounded spins, and publish resolved carries at anchors.  The tests check that any interleaving
+gives the single-thread result bit for bit, that stale tags of an earlier launch over the same
+descriptor memory are never taken, and that a tile which never publishes makes its successors'
+waits run out and return (no hang) with the status set.
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lookback_emu.c")
+_LIB = os.path.join(_HERE, "_build", "liblookback_emu.so")
+
+
+@pytest.fixture(scope="module")
+def emu():
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp"
+        subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC], check=True)
+        os.replace(tmp, _LIB)
+    lib = ctypes.CDLL(_LIB)
+    vp, i64 = ctypes.c_void_p, ctypes.c_int64
+    lib.emu_run.argtypes = [ctypes.c_int, i64, ctypes.c_uint, vp, vp, vp, vp, vp, ctypes.c_int, i64, i64]
+    lib.emu_run.restype = ctypes.c_int
+    lib.emu_reference.argtypes = [ctypes.c_int, i64, vp, vp, vp, vp]
+    return lib
+
+
+def _case(S, n_tiles, seed):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((S, S)).astype(np.float32)
+    A *= np.float32(0.9 / max(1e-6, np.abs(np.linalg.eigvals(A.astype(np.float64))).max()))
+    local = rng.standard_normal((n_tiles, S)).astype(np.float32)
+    z0 = rng.standard_normal(S).astype(np.float32)
+    return np.ascontiguousarray(A), local, z0
+
+
+def _p(a):
+    return a.ctypes.data
+
+
+@pytest.mark.parametrize("S,n_tiles,threads", [(2, 1, 4), (4, 33, 3), (16, 200, 8), (16, 97, 1), (6, 64, 16)])
+def test_any_interleaving_gives_the_serial_result(emu, S, n_tiles, threads):
+    A, local, z0 = _case(S, n_tiles, S * 1000 + n_tiles)
+    ref = np.zeros((n_tiles, S), dtype=np.float32)
+    emu.emu_reference(S, n_tiles, _p(local), _p(A), _p(z0), _p(ref))
+    desc = np.zeros(n_tiles * 2 * S, dtype=np.uint64)
+    for epoch in (1, 2, 3):  # the same descriptor memory, launch after launch
+        Z = np.full((n_tiles, S), np.nan, dtype=np.float32)
+        rc = emu.emu_run(S, n_tiles, epoch, _p(desc), _p(local), _p(A), _p(z0), _p(Z), threads, 1 << 22, -1)
+        assert rc == 0
+        assert np.array_equal(Z, ref)
+
+
+def test_stale_tags_of_an_earlier_launch_are_not_taken(emu):
+    # a launch over different carries leaves tagged words behind; the next launch, with the next
+    # epoch, must not compose any of them
+    S, n_tiles = 8, 150
+    A, local, z0 = _case(S, n_tiles, 7)
+    desc = np.zeros(n_tiles * 2 * S, dtype=np.uint64)
+    other = (local * 3 + 1).astype(np.float32)
+    Z = np.zeros((n_tiles, S), dtype=np.float32)
+    assert emu.emu_run(S, n_tiles, 5, _p(desc), _p(other), _p(A), _p(z0), _p(Z), 6, 1 << 22, -1) == 0
+    ref = np.zeros((n_tiles, S), dtype=np.float32)
+    emu.emu_reference(S, n_tiles, _p(local), _p(A), _p(z0), _p(ref))
+    Z2 = np.zeros((n_tiles, S), dtype=np.float32)
+    assert emu.emu_run(S, n_tiles, 6, _p(desc), _p(local), _p(A), _p(z0), _p(Z2), 6, 1 << 22, -1) == 0
+    assert np.array_equal(Z2, ref)
+
+
+@pytest.mark.parametrize("silent", [0, 5, 32, 40])
+def test_a_tile_that_never_publishes_times_out_its_successors(emu, silent):
+    S, n_tiles = 4, 120
+    A, local, z0 = _case(S, n_tiles, 11)
+    desc = np.zeros(n_tiles * 2 * S, dtype=np.uint64)
+    ref = np.zeros((n_tiles, S), dtype=np.float32)
+    emu.emu_reference(S, n_tiles, _p(local), _p(A), _p(z0), _p(ref))
+    Z = np.full((n_tiles, S), np.nan, dtype=np.float32)
+    rc = emu.emu_run(S, n_tiles, 1, _p(desc), _p(local), _p(A), _p(z0), _p(Z), 4, 2000, silent)
+    assert rc == 1  # the waits ran out and every worker returned
+    # tiles before the silent one never depended on it
+    assert np.array_equal(Z[:silent], ref[:silent])
