@@ -75,3 +75,34 @@ def test_create_rejects_bad_arguments_before_touching_a_device(lib):
     assert lib.sos_filter_destroy(None) == 0
     assert lib.sos_filter_run_batch(0, None, None, None, None, None) == 0
     assert lib.sos_filter_run_batch(-1, None, None, None, None, None) == -1
+
+
+def test_ctypes_structures_match_the_header_layout():
+    """Every struct the binding mirrors has the header's size and field offsets (compiled with the
+    host C compiler from include/sosfilt.h, no device needed)."""
+    import shutil
+    import subprocess
+    from paper_2607_23763_gb300 import _binding as B
+    if not shutil.which("gcc"):
+        pytest.skip("no host C compiler")
+    structs = {"sos_tuning": B.Tuning, "sos_server_config": B.ServerConfig, "sos_completion": B.Completion,
+               "sos_server_stats": B.ServerStats}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "sosfilt.h"', 'int main(void) {']
+    for cname, cls in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append("return 0; }")
+    build_dir = os.path.join(ROOT, "tests", "_build")
+    os.makedirs(build_dir, exist_ok=True)
+    src = os.path.join(build_dir, "layout.c")
+    with open(src, "w") as fh:
+        fh.write("\n".join(lines))
+    exe = os.path.join(build_dir, "layout")
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", exe, src], check=True)
+    out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, cls in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
