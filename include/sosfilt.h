@@ -259,16 +259,24 @@ sos_status sos_filter_sync_status(sos_filter *f);
 
 /*
  * Phase trace for diagnostics (no counterpart in the paper's method; it
- * measures where a block's time goes: stage-in, each section's carry
- * publication and resolution, stage-out).  When buf_dev is non-NULL, every
- * following launch on this filter has thread 0 of each thread block write 32
- * uint64 words at buf_dev[32 * ticket ...] for tickets < capacity_blocks:
- *   [0] ticket + 1, [1] start, [2] after drawing the ticket, [3] after stage-in,
- *   [4 + 3s] block carry of section s published, [5 + 3s] incoming state of
- *   section s known, [6 + 3s] lookback rounds (low 32 bits) and waits (high
- *   32 bits), [28] before stage-out, [29] end, [30] SM id;
- * times are the device global timer in ns.  buf_dev = NULL switches it off.
- * The caller owns the buffer.  Errors: SOS_EINVAL for capacity < 0.
+ * measures where a tile's time goes).  When buf_dev is non-NULL, every
+ * following launch on this filter writes 32 uint64 words per work item at
+ * buf_dev[32 * i ...] for items i < capacity_blocks; times are the device
+ * global timer in ns.  The items and slots depend on the kernel:
+ *   PH solver (per tile): [0] tile + 1; coordinator: [1] lookback start,
+ *     [2] incoming state resolved, [3] group states posted; first compute warp:
+ *     [4] iteration start, [5] next ticket known, [6] particular pass done,
+ *     [7] lane scan done, [8] fold done, [9] correction start, [10] group state
+ *     observed, [11] row states stored, [12] stored, [14]/[15] input stash;
+ *     [13] SM id.
+ *   cyclic reduction, cascade carry (per tile): see the kernel's source.
+ *   cyclic reduction, per-section carries (per ticket): [0] ticket + 1,
+ *     [1] start, [2] after drawing the ticket, [3] after stage-in, [4 + 3s]
+ *     block carry of section s published, [5 + 3s] incoming state of section s
+ *     known, [6 + 3s] lookback rounds (low 32 bits) and waits (high 32 bits),
+ *     [28] before stage-out, [29] end, [30] SM id.
+ * buf_dev = NULL switches it off.  The caller owns the buffer.  Errors:
+ * SOS_EINVAL for capacity < 0.
  */
 sos_status sos_filter_trace(sos_filter *f, uint64_t *buf_dev, int64_t capacity_blocks);
 

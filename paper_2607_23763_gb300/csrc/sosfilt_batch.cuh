@@ -192,7 +192,7 @@ __global__ void __launch_bounds__((kBatchW + 1) * 32, 1) sos_batch_kernel(const 
                     }
                     __nanosleep(64);
                 }
-                // sum over the window of (A_T)^k v_k (lane's own power), reduce-scattered
+                // sum over the predecessors of (A_T)^k v_k (lane's own power), reduce-scattered
                 packed_mv_gr<K>(tab + Dm::OFF_ATL + lane * MS, v, tmp);
                 const float part = reduce_scatter<S, Dm::P2, Dm::SH>(tmp, lane);
                 zi_lane = __shfl_sync(0xffffffffu, part, (lane < S ? lane : 0) << Dm::SH);

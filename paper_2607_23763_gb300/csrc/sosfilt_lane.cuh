@@ -1,5 +1,6 @@
 // Persistent single-signal kernel: PH factorization of every lane's block (Sec. II-C) with lanes
-// of N = 64 samples, a skewed direct-form-II particular pass and a column-wise correction, sm_103a.
+// of N = 64 samples (32 as an option, two blocks per SM), a skewed direct-form-II particular pass
+// and a column-wise correction, sm_103a.
 //
 // A tile is W = kLaneW consecutive groups of C = 32 N samples; compute warp w of a thread block
 // filters group w of the tile, lane l the samples l N .. l N + N - 1.  Per tile:
@@ -23,14 +24,14 @@
 //      that outputs are reproducible bit for bit.
 //   4. homogeneous correction (Eq. 24 once for the whole cascade): lane l's true incoming state is
 //      S_l + (M_N)^l Z, and sample m of its row gains sum_j H_j(m) [S_l + (M_N)^l Z]_j.  The rows'
-//      states go to shared memory and the correction runs across the rows: each lane takes four
-//      consecutive samples of one row, so its 4 x 2K basis values H_j(m) stay in registers, the
-//      loop stays small (no unrolled basis in the instruction stream) and every corrected float4
-//      leaves in a fully coalesced store.
+//      states go to shared memory and the correction runs across the rows: each lane takes V = 4
+//      (N = 32: 2) consecutive samples of one row, so its V x 2K basis values H_j(m) stay in
+//      registers, the loop stays small (no unrolled basis in the instruction stream) and every
+//      corrected vector leaves in a fully coalesced store.
 // Tile t is corrected after the particular pass and lane scan of tile t + 1, so the coordinator has
-// one pass to resolve it.  Tiles come from an ascending ticket counter (Sec. IV-A).  The next tile's input is
-// loaded into registers during the pass (coalesced 128-bit loads) and stashed into the warp's free
-// row buffer at the start of the next iteration.
+// one pass to resolve it.  Tiles come from an ascending ticket counter (Sec. IV-A).  The next
+// tile's input is loaded into registers during the pass (coalesced 128-bit loads) and stashed into
+// the warp's free row buffer at the start of the next iteration.
 #pragma once
 #include "sosfilt_cascade.cuh"
 
@@ -426,7 +427,7 @@ __global__ void __launch_bounds__((kLaneW + 1) * 32, LaneDims<K, N>::BPS)
                     }
                     __nanosleep(64);  // a short nap: the successors' lookbacks wait on this tile
                 }
-                // sum over the window of (A_T)^k v_k: each lane applies its own power, then a
+                // sum over the predecessors of (A_T)^k v_k: each lane applies its own power, then a
                 // reduce-scatter leaves word i of the sum in lane i
                 packed_mv<K>(sATl + lane * MS, v, tmp);
                 const float part = reduce_scatter<S, Dm::P2, Dm::SH>(tmp, lane);
