@@ -206,7 +206,7 @@ __global__ void __launch_bounds__((W + 1) * 32) __maxnreg__(N <= 32 ? 96 : 168) 
     float *z_buf = a_buf + 2 * W * S;                  // [2][W][S] incoming states of the groups
     float *zs_tail = z_buf + 2 * W * S;                // [S] zero-state final state (last group)
     float *agg = zs_tail + S;                          // [2][S] tile carry under zero incoming state
-    __shared__ unsigned long long bar_local[2], bar_zready, bar_ticket[4];
+    __shared__ unsigned long long bar_local[2], bar_zready[2], bar_ticket[4];
     __shared__ long long ring[4];
     __shared__ int fold_count[2];
     __shared__ int tickets_exhausted;
@@ -238,7 +238,8 @@ __global__ void __launch_bounds__((W + 1) * 32) __maxnreg__(N <= 32 ? 96 : 168) 
         mbar_init(&bar_local[1], 1);
         fold_count[0] = fold_count[1] = 0;
         tickets_exhausted = 0;
-        mbar_init(&bar_zready, 1);
+        mbar_init(&bar_zready[0], 1);
+        mbar_init(&bar_zready[1], 1);
 #pragma unroll
         for (int i = 0; i < 4; ++i) mbar_init(&bar_ticket[i], 1);
         ring[0] = draw_ticket();
@@ -371,7 +372,7 @@ __global__ void __launch_bounds__((W + 1) * 32) __maxnreg__(N <= 32 ? 96 : 168) 
                 if (w + 1 < W) zi_lane = lane_mv<S>(sACd, zi_lane, lane) + abuf[w * S + (lane < S ? lane : 0)];
             }
             __syncwarp();
-            if (lane == 0) mbar_arrive(&bar_zready);
+            if (lane == 0) mbar_arrive(&bar_zready[it & 1]);  // one barrier per tile parity
             if (tr) tr[4] = global_ns();
             ++it;
         }
@@ -418,7 +419,7 @@ __global__ void __launch_bounds__((W + 1) * 32) __maxnreg__(N <= 32 ? 96 : 168) 
     };
     auto correct_and_store = [&](long long tile, unsigned jt) -> bool {
         wtrace(tile, 8);
-        if (!mbar_wait(&bar_zready, jt & 1, budget, p.status)) return false;
+        if (!mbar_wait(&bar_zready[jt & 1], (jt >> 1) & 1, budget, p.status)) return false;
         wtrace(tile, 9);
         const long long g = tile * W + w;
         const float *zb = z_buf + ((jt & 1) * W + w) * S;
