@@ -10,7 +10,9 @@ Pins (tests/test_oracle_pins.py) tie it to the mathematics, not to itself:
 closed-form impulse responses, steady-state sinusoid gain, linearity, zero
 input, chunked == one-shot, dense solves of the banded system and of the
 permuted block system of Eqs. 2-3, and scipy.signal.sosfilt as an
-independent library routine.
+independent library routine.  tests/test_golden_paper_filters.py runs it on
+the paper's benchmark designs and reproduces what Sec. IV-F reports about
+their float32 realisations.
 """
 from __future__ import annotations
 

@@ -1,6 +1,7 @@
 """Pins of the seeded input generators and the filter designs (inputs shared by both sides)."""
 import cmath
 import math
+import os
 
 import numpy as np
 import pytest
@@ -9,13 +10,25 @@ import workloads
 from workloads import designs
 
 
-# Philox4x32-10 known-answer vectors published with Random123 (Salmon et al., SC'11).
-KAT = [
-    ((0, 0, 0, 0), (0, 0), (0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8)),
-    ((0xFFFFFFFF,) * 4, (0xFFFFFFFF,) * 2, (0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD)),
-    ((0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344), (0xA4093822, 0x299F31D0),
-     (0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1)),
-]
+def _load_kat():
+    """Philox4x32-10 known-answer vectors published with Random123 (Salmon et al., SC'11)."""
+    rows = []
+    path = os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            w = [int(v, 16) for v in line.split()]
+            assert len(w) == 10, line
+            rows.append((tuple(w[0:4]), tuple(w[4:6]), tuple(w[6:10])))
+    return rows
+
+
+KAT = _load_kat()
+
+
+def test_kat_fixture_complete():
+    assert len(KAT) == 3
 
 
 @pytest.mark.parametrize("ctr,key,out", KAT)
