@@ -1,0 +1,53 @@
+"""Host side of the benchmark: the CPU-baseline leg's chunked oracle pass and the accuracy measure
+it reports for the timed run's output (CPU only; the device output is stood in for by a CPU tensor)."""
+import numpy as np
+import pytest
+import torch
+
+import bench
+import oracle
+import workloads
+from workloads import designs
+
+
+@pytest.fixture(scope="module")
+def case():
+    sos = designs.butter_lowpass(4, 0.2)
+    x = workloads.normal_f32(5, 5000)
+    y_ref = oracle.sosfilt(sos, x)
+    return sos, x, y_ref
+
+
+def test_chunked_pass_reports_float32_rounding_only(case):
+    sos, x, y_ref = case
+    y = torch.from_numpy(y_ref.astype(np.float32))
+    base, acc = bench.cpu_baseline_leg(sos, x, y, chunk=1024)
+    # the state carried between chunks makes the chunked oracle equal the one-pass one: the only
+    # difference left is the float32 rounding of the stand-in output
+    assert acc["max_rel_error"] < 1e-7
+    assert acc["bound"] == 1e-4
+    assert base["cores"] == 1 and base["kind"] == "oracle" and base["value"] > 0
+
+
+@pytest.mark.parametrize("where", [0, 1023, 1024, 4999])
+def test_planted_error_is_found_anywhere(case, where):
+    sos, x, y_ref = case
+    y = torch.from_numpy(y_ref.astype(np.float32))
+    peak = float(np.abs(y_ref).max())
+    y[where] += np.float32(0.01 * peak)
+    _, acc = bench.cpu_baseline_leg(sos, x, y, chunk=1024)
+    assert acc["max_rel_error"] == pytest.approx(0.01, rel=1e-3)
+
+
+def test_without_output_only_times(case):
+    sos, x, _ = case
+    base, acc = bench.cpu_baseline_leg(sos, x)
+    assert acc is None and base["value"] > 0
+
+
+def test_bound_follows_the_pole_radius():
+    x = workloads.normal_f32(6, 2048)
+    sos = designs.resonator_bank()
+    y = torch.from_numpy(oracle.sosfilt(sos, x).astype(np.float32))
+    _, acc = bench.cpu_baseline_leg(sos, x, y, chunk=512)
+    assert acc["bound"] == 2e-3 and acc["max_rel_error"] < 1e-6
