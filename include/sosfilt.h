@@ -103,8 +103,8 @@ enum {
  *                      their outputs are bit-identical from run to run.  Cyclic reduction composes
  *                      from whichever predecessor's resolved carry its lookback meets first (Sec.
  *                      IV-B) and may differ in the last ulps; 1 requests reproducible results and
- *                      is rejected with SOS_EINVAL together with settings that select cyclic
- *                      reduction.
+ *                      is rejected with SOS_EINVAL together with solver SOS_SOLVER_CR, a carry
+ *                      other than SOS_CARRY_DEFAULT, a lookback width or N = 128.
  */
 typedef struct {
     int N, L, groups_per_cta, threads_per_group, fp64_carry;

@@ -106,3 +106,82 @@ def test_ctypes_structures_match_the_header_layout():
         assert got[(cname, "size")] == ctypes.sizeof(cls), cname
         for fname, _ in cls._fields_:
             assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
+
+
+def _tuning_valid(N, carry, solver, lw, det):
+    """sos_filter_create's verdict on a tuning, written from the sos_tuning documentation in
+    include/sosfilt.h (not from the implementation)."""
+    if N not in (0, 32, 64, 128) or carry not in (0, 1, 2) or solver not in (0, 1, 2):
+        return False
+    if lw not in (0, 1, 2, 4, 8, 16) or det not in (0, 1):
+        return False
+    if carry in (0, 1) and N not in (0, 32, 64):  # the cascade carry (also the default) takes 32 or 64
+        return False
+    if solver == 2 and (N == 128 or carry == 2 or lw):
+        return False
+    if det and (solver == 1 or carry or lw or N == 128):
+        return False
+    return True
+
+
+def _create_verdict(lib, sos, tuning):
+    h = ctypes.c_void_p()
+    rc = lib.sos_filter_create(sos.shape[0], sos.ctypes.data, None, ctypes.byref(tuning), ctypes.byref(h))
+    if rc == 0:
+        lib.sos_filter_destroy(h)
+    else:
+        assert h.value is None
+    return rc
+
+
+def test_tuning_validation_matches_the_header(lib):
+    """Every combination of the tuning's selector fields: argument errors come back as SOS_EINVAL
+    before a device is touched; the rest pass validation (and then fail, without a GPU, only at the
+    first CUDA call, or succeed on a GPU)."""
+    from paper_2607_23763_gb300._binding import Tuning
+    sos = np.array([[1.0, 0.5, 0.25, -0.5, 0.25], [0.5, 0.0, -0.5, 0.1, 0.2]])
+    seen = {True: 0, False: 0}
+    for N in (0, 24, 32, 64, 128):
+        for carry in (0, 1, 2, 3):
+            for solver in (0, 1, 2, 3):
+                for lw in (0, 1, 3, 16):
+                    for det in (0, 1, 2):
+                        t = Tuning(N=N, carry=carry, solver=solver, lookback_width=lw, deterministic=det)
+                        want = _tuning_valid(N, carry, solver, lw, det)
+                        rc = _create_verdict(lib, sos, t)
+                        assert (rc != -1) == want, (N, carry, solver, lw, det, rc)
+                        assert rc in ((0, -2, -3) if want else (-1,)), rc
+                        seen[want] += 1
+    assert seen[True] > 50 and seen[False] > 500
+    # the reserved and fixed fields
+    for t in (Tuning(L=16), Tuning(threads_per_group=64), Tuning(groups_per_cta=2), Tuning(fp64_carry=1),
+              Tuning(spin_budget_cycles=-1)):
+        assert _create_verdict(lib, sos, t) == -1
+    for t in (Tuning(L=32), Tuning(threads_per_group=32), Tuning(spin_budget_cycles=1 << 20)):
+        assert _create_verdict(lib, sos, t) != -1
+
+
+def test_stability_triangle_is_the_unit_circle(lib):
+    """A section is accepted exactly when both roots of z^2 + a1 z + a2 lie inside the unit circle
+    (np.roots), on a seeded scatter over and around the stability triangle, away from its edges."""
+    rng = np.random.default_rng(7)
+    n_in = n_out = 0
+    for a1, a2 in rng.uniform([-2.6, -1.4], [2.6, 1.4], size=(3000, 2)):
+        margin = min(abs(abs(a2) - 1.0), abs(abs(a1) - (1.0 + a2)))
+        if margin < 1e-6:
+            continue
+        stable = float(np.max(np.abs(np.roots([1.0, a1, a2])))) < 1.0
+        sos = np.array([[1.0, 2.0, 1.0, a1, a2]])
+        h = ctypes.c_void_p()
+        rc = lib.sos_filter_create(1, sos.ctypes.data, None, None, ctypes.byref(h))
+        if rc == 0:
+            lib.sos_filter_destroy(h)
+        assert (rc != -5) == stable, (a1, a2, rc)
+        n_in += stable
+        n_out += not stable
+    assert n_in > 500 and n_out > 500
+    # on the edges: a pole on the unit circle is rejected
+    for a1, a2 in ((0.0, 1.0), (0.0, -1.0), (1.5, 0.5), (-1.5, 0.5), (2.0, 1.0)):
+        sos = np.array([[1.0, 2.0, 1.0, a1, a2]])
+        h = ctypes.c_void_p()
+        assert lib.sos_filter_create(1, sos.ctypes.data, None, None, ctypes.byref(h)) == -5
