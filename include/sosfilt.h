@@ -365,6 +365,8 @@ sos_status sos_server_get_stats(sos_server *s, sos_server_stats *out);
  * n[i] samples) arrives t_arrival[i] seconds after the call (non-decreasing); latency[i] receives
  * its completion time minus its scheduled arrival.  Returns when all have completed.  The caller
  * must not submit or poll on the server meanwhile (the replay consumes the completion queue).
+ * Errors, found before any request is queued: SOS_EINVAL (NULL arrays or buffers, a bad stream id,
+ * n[i] <= 0), SOS_EBUDGET (a chunk larger than the budget).
  */
 sos_status sos_server_replay(sos_server *s, int64_t n_req, const int32_t *stream_ids, const float *const *x_dev,
                              float *const *y_dev, const int64_t *n, const double *t_arrival, double *latency);

@@ -350,6 +350,21 @@ sos_status sos_server_replay(sos_server *s, int64_t n_req, const int32_t *stream
                              float *const *y_dev, const int64_t *n, const double *t_arrival, double *latency) {
     if (!s || n_req < 0 || (n_req > 0 && (!stream_ids || !x_dev || !y_dev || !n || !t_arrival || !latency)))
         return SOS_EINVAL;
+    {
+        // every request is checked before the first is queued: a chunk larger than the budget could
+        // never be admitted, and the replay would not end
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (int64_t j = 0; j < n_req; ++j) {
+            const int sid = stream_ids[j];
+            if (sid < 0 || sid >= static_cast<int>(s->streams.size()) || n[j] <= 0 || !x_dev[j] || !y_dev[j])
+                return SOS_EINVAL;
+            Req r;
+            r.x = x_dev[j];
+            r.y = y_dev[j];
+            r.n = n[j];
+            if (req_bytes(r) > s->cfg.budget_bytes) return SOS_EBUDGET;
+        }
+    }
     std::vector<uint64_t> ids(n_req, 0);
     const double t0 = now_s();
     int64_t i = 0;
@@ -364,7 +379,6 @@ sos_status sos_server_replay(sos_server *s, int64_t n_req, const int32_t *stream
         std::lock_guard<std::mutex> lk(s->mu);
         for (; i < n_req && t_arrival[i] <= t; ++i) {
             const int sid = stream_ids[i];
-            if (sid < 0 || sid >= static_cast<int>(s->streams.size()) || n[i] <= 0) return SOS_EINVAL;
             Req r;
             r.id = s->next_id++;
             r.sid = sid;
