@@ -163,7 +163,8 @@ sos_status sos_filter_run(sos_filter *f, const float *x_dev, float *y_dev, int64
  *   zf_host         host float32[K][2] receives the final state, or NULL
  *   chunk_samples   samples per chunk, 0 = 2^24; the library keeps three device
  *                   buffers of this size per filter after the first call
- * Errors: SOS_EINVAL, SOS_ENOMEM, SOS_ECUDA; SOS_ETIMEOUT as for sos_filter_run.
+ * Errors: SOS_EINVAL, SOS_ENOMEM, SOS_ECUDA; SOS_ETIMEOUT when a device wait of this call (or of
+ * an earlier unreported run) ran out of time, reported and cleared as by sos_filter_sync_status.
  */
 sos_status sos_filter_run_host(sos_filter *f, const float *x_host, float *y_host, int64_t n, const float *zi_host,
                                float *zf_host, int64_t chunk_samples);

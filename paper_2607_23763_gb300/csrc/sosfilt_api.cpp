@@ -1289,6 +1289,20 @@ sos_status plan_create(int n_signals, sos_filter *const *filters, const float *c
     return SOS_OK;
 }
 
+// Status of a filter's finished work.  A launch that gave up on a wait (SOS_ETIMEOUT) consumed fewer
+// tickets than the host counted, so once reported the status word and the ticket counter start over
+// and later runs are valid again.
+sos_status take_filter_status(sos_filter *f) {
+    int h = 0;
+    if (cudaMemcpy(&h, f->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SOS_ECUDA;
+    if (!(h & sosk::kDevErrTimeout)) return SOS_OK;
+    if (cudaDeviceSynchronize() != cudaSuccess || cudaMemset(f->d_status, 0, sizeof(int)) != cudaSuccess ||
+        cudaMemset(f->d_ticket, 0, sizeof(unsigned long long)) != cudaSuccess)
+        return SOS_ECUDA;
+    f->ticket_base = 0;
+    return SOS_ETIMEOUT;
+}
+
 // Sticky device status of the batch context of a device (SOS_ETIMEOUT after a lookback timeout).
 sos_status batch_status(int device) {
     BatchCtx *ctx = batch_ctx(device);
@@ -1568,9 +1582,7 @@ sos_status sos_filter_run_host(sos_filter *f, const float *x_host, float *y_host
     }
     if (cudaStreamSynchronize(sout) != cudaSuccess || cudaStreamSynchronize(sc) != cudaSuccess) return SOS_ECUDA;
     f->last_stream = sc;
-    int h = 0;
-    if (cudaMemcpy(&h, f->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SOS_ECUDA;
-    return (h & sosk::kDevErrTimeout) ? SOS_ETIMEOUT : SOS_OK;
+    return take_filter_status(f);  // reported once, as by sos_filter_sync_status
 }
 
 sos_status sos_filter_run_batch(int n_signals, sos_filter *const *filters, const float *const *x_dev,
@@ -1769,17 +1781,7 @@ sos_status sos_filter_sync_status(sos_filter *f) {
     std::lock_guard<std::mutex> lk(f->mu);
     if (cudaSetDevice(f->device) != cudaSuccess) return SOS_ECUDA;
     if (cudaStreamSynchronize(f->last_stream) != cudaSuccess) return SOS_ECUDA;
-    int h = 0;
-    if (cudaMemcpy(&h, f->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SOS_ECUDA;
-    if (h & sosk::kDevErrTimeout) {
-        // a launch that gave up consumed fewer tickets than the host counted: start the counter over
-        if (cudaDeviceSynchronize() != cudaSuccess || cudaMemset(f->d_status, 0, sizeof(int)) != cudaSuccess ||
-            cudaMemset(f->d_ticket, 0, sizeof(unsigned long long)) != cudaSuccess)
-            return SOS_ECUDA;
-        f->ticket_base = 0;
-        return SOS_ETIMEOUT;
-    }
-    return SOS_OK;
+    return take_filter_status(f);
 }
 
 }  // extern "C"
