@@ -11,6 +11,12 @@
  * The composition is evaluated by Horner's rule from the anchor in float32, the same operations in
  * the same order as emu_reference(), so a correct protocol gives bit-identical results whatever
  * the interleaving of the threads.
+ *
+ * The batched form (emu_run_batch) is the batch kernel's: the tiles of several signals share one
+ * ticket queue (a tile -> signal map, each signal's tiles consecutive from its first tile t0), and
+ * each signal keeps its own chain -- its first tile starts from the signal's initial state, the
+ * anchors are t0 + 32 floor((t - 1 - t0) / 32), and its tiles compose with the signal's own
+ * transition.
  */
 #include <pthread.h>
 #include <sched.h>
@@ -25,8 +31,10 @@ typedef struct {
     unsigned epoch;
     _Atomic uint64_t *desc;  /* [n_tiles][2][S] */
     const float *local;      /* [n_tiles][S] local carries */
-    const float *AT;         /* [S][S] row-major tile transition */
-    const float *z0;         /* [S] */
+    const float *AT;         /* [signals][S][S] row-major tile transition of each signal */
+    const float *z0;         /* [signals][S] initial state of each signal */
+    const int *tile_sig;     /* [n_tiles] signal of each tile */
+    const int64_t *tile0;    /* [signals] first tile of each signal */
     float *Z;                /* [n_tiles][S] incoming states (output) */
     _Atomic int64_t ticket;
     _Atomic int status;      /* 1: a wait ran out */
@@ -89,12 +97,15 @@ static void *emu_worker(void *arg) {
         const int64_t t = atomic_fetch_add(&c->ticket, 1);
         if (t >= c->n_tiles || atomic_load(&c->status)) break;
         if (t == c->silent) continue;  /* this tile's worker "dies" before publishing anything */
+        const int sig = c->tile_sig[t];
+        const int64_t t0 = c->tile0[sig];
+        const float *A = c->AT + (size_t)sig * S * S;
         const float *loc = c->local + (size_t)t * S;
-        if (t > 0) publish(c, t, 0, tagL, loc);
-        if (t == 0) {
-            memcpy(acc, c->z0, sizeof(float) * (size_t)S);
+        if (t > t0) publish(c, t, 0, tagL, loc);
+        if (t == t0) {
+            memcpy(acc, c->z0 + (size_t)sig * S, sizeof(float) * (size_t)S);
         } else {
-            const int64_t a = ((t - 1) / 32) * 32;
+            const int64_t a = t0 + ((t - 1 - t0) / 32) * 32;
             if (!wait_slot(c, a, 1, tagG, acc)) {
                 atomic_store(&c->status, 1);
                 break;
@@ -104,23 +115,24 @@ static void *emu_worker(void *arg) {
                     atomic_store(&c->status, 1);
                     return NULL;
                 }
-                mv_add(S, c->AT, acc, v, tmp);
+                mv_add(S, A, acc, v, tmp);
                 memcpy(acc, tmp, sizeof(float) * (size_t)S);
             }
         }
         memcpy(c->Z + (size_t)t * S, acc, sizeof(float) * (size_t)S);
-        if (t % 32 == 0 && t + 1 < c->n_tiles) {
-            mv_add(S, c->AT, acc, loc, tmp);
+        if ((t - t0) % 32 == 0 && t + 1 < c->n_tiles) {
+            mv_add(S, A, acc, loc, tmp);
             publish(c, t, 1, tagG, tmp);
         }
     }
     return NULL;
 }
 
-/* One launch of the protocol over `desc` (kept by the caller between launches: its old tags must
- * not be mistaken for this epoch's).  Returns 0, or 1 when some wait ran out. */
-int emu_run(int S, int64_t n_tiles, unsigned epoch, uint64_t *desc, const float *local, const float *AT,
-            const float *z0, float *Z, int threads, int64_t spin_limit, int64_t silent) {
+/* One launch of the batched protocol over `desc` (kept by the caller between launches: its old
+ * tags must not be mistaken for this epoch's).  Returns 0, or 1 when some wait ran out. */
+int emu_run_batch(int S, int64_t n_tiles, unsigned epoch, uint64_t *desc, const float *local, const float *AT,
+                  const float *z0, const int *tile_sig, const int64_t *tile0, float *Z, int threads,
+                  int64_t spin_limit, int64_t silent) {
     if (S < 1 || S > 64 || n_tiles < 0 || threads < 1 || threads > 64) return -1;
     emu_ctx c;
     memset(&c, 0, sizeof c);
@@ -131,6 +143,8 @@ int emu_run(int S, int64_t n_tiles, unsigned epoch, uint64_t *desc, const float 
     c.local = local;
     c.AT = AT;
     c.z0 = z0;
+    c.tile_sig = tile_sig;
+    c.tile0 = tile0;
     c.Z = Z;
     atomic_init(&c.ticket, 0);
     atomic_init(&c.status, 0);
@@ -145,23 +159,45 @@ int emu_run(int S, int64_t n_tiles, unsigned epoch, uint64_t *desc, const float 
     return atomic_load(&c.status);
 }
 
-/* The same composition evaluated tile after tile on one thread. */
-void emu_reference(int S, int64_t n_tiles, const float *local, const float *AT, const float *z0, float *Z) {
-    float *res = (float *)malloc(sizeof(float) * (size_t)S * (size_t)(n_tiles > 0 ? n_tiles : 1));
+/* One signal: every tile maps to signal 0, whose first tile is 0. */
+int emu_run(int S, int64_t n_tiles, unsigned epoch, uint64_t *desc, const float *local, const float *AT,
+            const float *z0, float *Z, int threads, int64_t spin_limit, int64_t silent) {
+    if (n_tiles < 0) return -1;
+    int *ts = (int *)calloc((size_t)(n_tiles > 0 ? n_tiles : 1), sizeof(int));
+    if (!ts) return -1;
+    const int64_t t0 = 0;
+    const int rc = emu_run_batch(S, n_tiles, epoch, desc, local, AT, z0, ts, &t0, Z, threads, spin_limit, silent);
+    free(ts);
+    return rc;
+}
+
+/* The same composition evaluated signal by signal, tile after tile, on one thread. */
+void emu_reference_batch(int S, int n_signals, const int64_t *tile0, const int64_t *n_sig_tiles, const float *local,
+                         const float *AT, const float *z0, float *Z) {
     float acc[64], tmp[64];
-    for (int64_t t = 0; t < n_tiles; ++t) {
-        if (t == 0) {
-            memcpy(acc, z0, sizeof(float) * (size_t)S);
-        } else {
-            const int64_t a = ((t - 1) / 32) * 32;
-            memcpy(acc, res + (size_t)a * S, sizeof(float) * (size_t)S);
-            for (int64_t p = a + 1; p < t; ++p) {
-                mv_add(S, AT, acc, local + (size_t)p * S, tmp);
-                memcpy(acc, tmp, sizeof(float) * (size_t)S);
+    for (int sig = 0; sig < n_signals; ++sig) {
+        const int64_t t0 = tile0[sig], nt = n_sig_tiles[sig];
+        const float *A = AT + (size_t)sig * S * S;
+        float *res = (float *)malloc(sizeof(float) * (size_t)S * (size_t)(nt > 0 ? nt : 1));
+        for (int64_t r = 0; r < nt; ++r) {  /* r: tile number within the signal */
+            if (r == 0) {
+                memcpy(acc, z0 + (size_t)sig * S, sizeof(float) * (size_t)S);
+            } else {
+                const int64_t a = ((r - 1) / 32) * 32;
+                memcpy(acc, res + (size_t)a * S, sizeof(float) * (size_t)S);
+                for (int64_t p = a + 1; p < r; ++p) {
+                    mv_add(S, A, acc, local + (size_t)(t0 + p) * S, tmp);
+                    memcpy(acc, tmp, sizeof(float) * (size_t)S);
+                }
             }
+            memcpy(Z + (size_t)(t0 + r) * S, acc, sizeof(float) * (size_t)S);
+            if (r % 32 == 0) mv_add(S, A, acc, local + (size_t)(t0 + r) * S, res + (size_t)r * S);
         }
-        memcpy(Z + (size_t)t * S, acc, sizeof(float) * (size_t)S);
-        if (t % 32 == 0) mv_add(S, AT, acc, local + (size_t)t * S, res + (size_t)t * S);
+        free(res);
     }
-    free(res);
+}
+
+void emu_reference(int S, int64_t n_tiles, const float *local, const float *AT, const float *z0, float *Z) {
+    const int64_t t0 = 0;
+    emu_reference_batch(S, 1, &t0, &n_tiles, local, AT, z0, Z);
 }

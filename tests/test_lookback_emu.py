@@ -5,7 +5,9 @@ each tile's incoming state from its anchor's resolved carry and the local carrie
 bounded spins, and publish resolved carries at anchors.  The tests check that any interleaving
 gives the single-thread result bit for bit, that stale tags of an earlier launch over the same
 descriptor memory are never taken, and that a tile which never publishes makes its successors'
-waits run out and return (no hang) with the status set.
+waits run out and return (no hang) with the status set.  The batched form shares one ticket queue
+among the tiles of several signals, each signal with its own chain, anchors and transition, as the
+batch kernel does.
 """
 import ctypes
 import os
@@ -31,6 +33,9 @@ def emu():
     lib.emu_run.argtypes = [ctypes.c_int, i64, ctypes.c_uint, vp, vp, vp, vp, vp, ctypes.c_int, i64, i64]
     lib.emu_run.restype = ctypes.c_int
     lib.emu_reference.argtypes = [ctypes.c_int, i64, vp, vp, vp, vp]
+    lib.emu_run_batch.argtypes = [ctypes.c_int, i64, ctypes.c_uint, vp, vp, vp, vp, vp, vp, vp, ctypes.c_int, i64, i64]
+    lib.emu_run_batch.restype = ctypes.c_int
+    lib.emu_reference_batch.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp, vp]
     return lib
 
 
@@ -88,3 +93,78 @@ def test_a_tile_that_never_publishes_times_out_its_successors(emu, silent):
     assert rc == 1  # the waits ran out and every worker returned
     # tiles before the silent one never depended on it
     assert np.array_equal(Z[:silent], ref[:silent])
+
+
+def _batch_case(S, sig_tiles, seed):
+    rng = np.random.default_rng(seed)
+    n_sig = len(sig_tiles)
+    AT = np.empty((n_sig, S, S), dtype=np.float32)
+    for k in range(n_sig):
+        A = rng.standard_normal((S, S))
+        AT[k] = (A * (0.9 / max(1e-6, np.abs(np.linalg.eigvals(A)).max()))).astype(np.float32)
+    tile0 = np.concatenate([[0], np.cumsum(sig_tiles)[:-1]]).astype(np.int64)
+    n_tiles = int(np.sum(sig_tiles))
+    tile_sig = np.repeat(np.arange(n_sig, dtype=np.int32), sig_tiles)
+    local = rng.standard_normal((n_tiles, S)).astype(np.float32)
+    z0 = rng.standard_normal((n_sig, S)).astype(np.float32)
+    return AT, tile0, np.asarray(sig_tiles, dtype=np.int64), n_tiles, tile_sig, local, z0
+
+
+@pytest.mark.parametrize("S,sig_tiles,threads", [
+    (4, [1, 31, 32, 33, 65, 1, 64], 6),
+    (16, [97, 3, 40], 8),
+    (2, [1] * 50, 4),
+    (8, [200], 1),
+])
+def test_batched_chains_give_each_signal_its_serial_result(emu, S, sig_tiles, threads):
+    AT, tile0, nst, n_tiles, tile_sig, local, z0 = _batch_case(S, sig_tiles, S + len(sig_tiles))
+    ref = np.zeros((n_tiles, S), dtype=np.float32)
+    emu.emu_reference_batch(S, len(sig_tiles), _p(tile0), _p(nst), _p(local), _p(AT), _p(z0), _p(ref))
+    desc = np.zeros(n_tiles * 2 * S, dtype=np.uint64)
+    for epoch in (1, 2):
+        Z = np.full((n_tiles, S), np.nan, dtype=np.float32)
+        rc = emu.emu_run_batch(S, n_tiles, epoch, _p(desc), _p(local), _p(AT), _p(z0), _p(tile_sig), _p(tile0),
+                               _p(Z), threads, 1 << 22, -1)
+        assert rc == 0
+        assert np.array_equal(Z, ref)
+    # each signal's chain is the single-signal protocol on its own tiles
+    for k, (t0, nt) in enumerate(zip(tile0, nst)):
+        one = np.zeros((nt, S), dtype=np.float32)
+        emu.emu_reference(S, int(nt), _p(np.ascontiguousarray(local[t0:t0 + nt])), _p(np.ascontiguousarray(AT[k])),
+                          _p(np.ascontiguousarray(z0[k])), _p(one))
+        assert np.array_equal(ref[t0:t0 + nt], one), k
+
+
+def test_batched_chains_do_not_cross_signals(emu):
+    """The first tile of every signal starts from that signal's own initial state, whatever the tile
+    before it in the queue holds; changing one signal's carries changes no other signal's result."""
+    S, sig_tiles = 4, [33, 20, 70]
+    AT, tile0, nst, n_tiles, tile_sig, local, z0 = _batch_case(S, sig_tiles, 3)
+    desc = np.zeros(n_tiles * 2 * S, dtype=np.uint64)
+    Z1 = np.zeros((n_tiles, S), dtype=np.float32)
+    assert emu.emu_run_batch(S, n_tiles, 1, _p(desc), _p(local), _p(AT), _p(z0), _p(tile_sig), _p(tile0),
+                             _p(Z1), 5, 1 << 22, -1) == 0
+    local2 = local.copy()
+    local2[tile0[1]:tile0[1] + nst[1]] *= 7  # only the second signal's carries
+    Z2 = np.zeros((n_tiles, S), dtype=np.float32)
+    assert emu.emu_run_batch(S, n_tiles, 2, _p(desc), _p(local2), _p(AT), _p(z0), _p(tile_sig), _p(tile0),
+                             _p(Z2), 5, 1 << 22, -1) == 0
+    s1 = slice(tile0[1], tile0[1] + nst[1])
+    assert np.array_equal(np.delete(Z1, np.r_[s1], axis=0), np.delete(Z2, np.r_[s1], axis=0))
+    assert not np.array_equal(Z1[s1][1:], Z2[s1][1:])
+    for k in range(3):
+        assert np.array_equal(Z1[tile0[k]], z0[k])
+
+
+def test_batched_silent_tile_times_out_only_later_work(emu):
+    S, sig_tiles = 4, [40, 50, 30]
+    AT, tile0, nst, n_tiles, tile_sig, local, z0 = _batch_case(S, sig_tiles, 9)
+    ref = np.zeros((n_tiles, S), dtype=np.float32)
+    emu.emu_reference_batch(S, 3, _p(tile0), _p(nst), _p(local), _p(AT), _p(z0), _p(ref))
+    silent = int(tile0[1] + 5)
+    desc = np.zeros(n_tiles * 2 * S, dtype=np.uint64)
+    Z = np.full((n_tiles, S), np.nan, dtype=np.float32)
+    rc = emu.emu_run_batch(S, n_tiles, 1, _p(desc), _p(local), _p(AT), _p(z0), _p(tile_sig), _p(tile0), _p(Z),
+                           4, 2000, silent)
+    assert rc == 1
+    assert np.array_equal(Z[:silent], ref[:silent])  # the first signal and the silent tile's predecessors
