@@ -171,15 +171,19 @@ def cpu_baseline_leg(sos, x_host, y_dev=None, chunk: int = 1 << 24):
     It runs in chunks of ``chunk`` samples with the state carried between them (bit-identical to one
     pass), and only the oracle calls are timed.  Given the device output ``y_dev`` of the timed run
     (a tensor), the same pass also yields the accuracy measure of Sec. IV-F over every sample,
-    max|y - y_ref| / max|y_ref|, against the design's bound.  Returns (baseline, accuracy or None).
+    max|y - y_ref| / max|y_ref|, against the design's bound, and (untimed) the same measure against
+    the oracle run on the coefficients rounded to float32, which leaves out the part of the error
+    that the rounding of the coefficients alone causes.  Returns (baseline, accuracy or None).
     """
     import oracle
     from workloads import designs
     oracle.sosfilt(sos, x_host[:1024])  # load the oracle outside the timed calls
     n = x_host.shape[0]
     keep = y_dev is not None
+    sos32 = np.asarray(sos, dtype=np.float32).astype(np.float64)
     z = np.zeros((sos.shape[0], 2))
-    dt = num = den = 0.0
+    z32 = np.zeros((sos.shape[0], 2))
+    dt = num = den = num32 = den32 = 0.0
     for a in range(0, n, chunk):
         t0 = time.perf_counter()
         ref, z = oracle.sosfilt(sos, x_host[a:a + chunk], zi=z, return_state=True, keep_output=keep)
@@ -188,12 +192,16 @@ def cpu_baseline_leg(sos, x_host, y_dev=None, chunk: int = 1 << 24):
             got = y_dev[a:a + chunk].cpu().numpy().astype(np.float64)
             num = max(num, float(np.abs(got - ref).max()))
             den = max(den, float(np.abs(ref).max()))
+            ref32, z32 = oracle.sosfilt(sos32, x_host[a:a + chunk], zi=z32, return_state=True)
+            num32 = max(num32, float(np.abs(got - ref32).max()))
+            den32 = max(den32, float(np.abs(ref32).max()))
     base = {"value": n / dt / 1e9, "unit": "GS/s", "cores": 1, "kind": "oracle",
             "sample": f"the whole workload (2^{int(np.log2(n))} samples) once on one host core, {dt:.1f} s"}
     acc = None
     if keep:
         acc = {"max_rel_error": num / den if den > 0 else num, "bound": designs.tolerance_for(sos),
-               "measure": "max|y - y_oracle| / max|y_oracle| over every sample of the timed run's output"}
+               "measure": "max|y - y_oracle| / max|y_oracle| over every sample of the timed run's output",
+               "max_rel_error_vs_f32_coefficients": num32 / den32 if den32 > 0 else num32}
     return base, acc
 
 

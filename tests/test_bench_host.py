@@ -26,6 +26,9 @@ def test_chunked_pass_reports_float32_rounding_only(case):
     # difference left is the float32 rounding of the stand-in output
     assert acc["max_rel_error"] < 1e-7
     assert acc["bound"] == 1e-4
+    # against the oracle on float32-rounded coefficients the stand-in differs by that rounding
+    y32 = oracle.sosfilt(np.asarray(sos, np.float32).astype(np.float64), x)
+    assert acc["max_rel_error_vs_f32_coefficients"] == pytest.approx(oracle.rel_err(y.numpy(), y32), rel=1e-9)
     assert base["cores"] == 1 and base["kind"] == "oracle" and base["value"] > 0
 
 
