@@ -54,3 +54,31 @@ def test_bound_follows_the_pole_radius():
     y = torch.from_numpy(oracle.sosfilt(sos, x).astype(np.float32))
     _, acc = bench.cpu_baseline_leg(sos, x, y, chunk=512)
     assert acc["bound"] == 2e-3 and acc["max_rel_error"] < 1e-6
+
+
+def _run_bench(args, env_extra=None):
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, **(env_extra or {}))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), *args], capture_output=True, text=True,
+                         env=env, timeout=300, check=True).stdout
+    lines = [ln for ln in out.splitlines() if ln.startswith("{")]
+    return [json.loads(ln) for ln in lines]
+
+
+def test_reference_arm_prints_one_contract_line():
+    (line,) = _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "3"])
+    assert line["impl"] == "reference" and line["unit"] == "GS/s" and line["value"] > 0
+    assert line["steps"] == 1 and line["warmup"] == 3 and line["higher_is_better"] is True
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": "GS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert "2^28" in line["config"]["workload"]
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    assert _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "3"],
+                      {"WORLD_SIZE": "2", "RANK": "1", "LOCAL_RANK": "1"}) == []
