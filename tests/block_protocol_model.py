@@ -14,7 +14,11 @@ random schedules:
   posts the groups' incoming states in slot k mod NS, announced on incoming-state barrier k mod NZ
   (NZ = NS in the kernels: one barrier per slot);
 * the correction of the tile of iteration k runs in iteration k + D - 1 of each compute warp, from
-  row buffer k mod D, after that warp's fold of its own later tile.
+  row buffer k mod D, after that warp's fold of its own later tile;
+* the samples of the next tile go to row buffer (k + 1) mod D: held in registers and stored at the
+  start of iteration k + 1 (the kernels), or, with `load="after_correction"`, loaded straight into
+  that buffer once the correction of iteration k has freed it (`load="early"` issues that load
+  before the correction: a planted mistake).
 
 mbarrier waits are on a phase parity: a wait for phase m of a barrier that has already completed
 phase m + 1 waits for another phase, which never comes.  Every wait therefore checks that its
@@ -32,7 +36,7 @@ class Hazard(Exception):
     """A schedule under which the protocol would misbehave on the GPU."""
 
 
-def run_block(W, n_tiles, *, R=8, A=3, D=2, NS=2, NZ=2, seed=0, max_steps=500000):
+def run_block(W, n_tiles, *, R=8, A=3, D=2, NS=2, NZ=2, load="registers", seed=0, max_steps=500000):
     """One block taking every tile of a launch of `n_tiles` tiles.  Raises Hazard on a violation."""
     rng = random.Random(seed)
     bar_ticket = [0] * R        # completed phases per barrier
@@ -120,13 +124,25 @@ def run_block(W, n_tiles, *, R=8, A=3, D=2, NS=2, NZ=2, seed=0, max_steps=500000
             rows[j % D] = None
             corrected.append((t, w))
 
-        k = 0
-        while True:
+        def land(k, t):  # the samples of tile t arrive in the buffer of iteration k
             if rows[k % D] is not None:
-                raise Hazard(f"warp {w}, iteration {k}: buffer {k % D} still holds tile {rows[k % D]}")
-            rows[k % D] = tile
+                raise Hazard(f"warp {w}: tile {t} lands in buffer {k % D}, which still holds tile {rows[k % D]}")
+            rows[k % D] = t
+
+        k = 0
+        landed = load == "registers"
+        if not landed:
+            land(0, tile)
+        while True:
+            if landed:
+                land(k, tile)
+            landed = load == "registers"
             yield from wait(bar_ticket, (k + 1) % R, (k + 1) // R, w)
             nxt = take_ticket(k + 1, w)
+            if load == "early" and nxt >= 0:
+                land(k + 1, nxt)
+            elif load == "after_correction" and nxt >= 0 and len(pending) < D - 1:
+                land(k + 1, nxt)  # the buffer is free from the start
             yield from pause(10)  # the pass over the group and the lane scan
             s = k % NS
             if a_slot[s][w] is not None and not a_consumed[s]:
@@ -143,6 +159,8 @@ def run_block(W, n_tiles, *, R=8, A=3, D=2, NS=2, NZ=2, seed=0, max_steps=500000
             yield from pause(4)  # between the fold and the wait for the incoming states
             if len(pending) == D:
                 yield from correct(*pending.pop(0))
+                if load == "after_correction" and nxt >= 0:
+                    land(k + 1, nxt)
             if nxt < 0:
                 break
             tile = nxt

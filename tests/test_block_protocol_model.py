@@ -57,6 +57,14 @@ def test_a_deeper_pipeline_with_four_slots_is_hazard_free():
     assert _hazards(R=8, A=3, D=3, NS=4, NZ=4) == []
 
 
+def test_loading_into_the_buffer_the_correction_freed_is_hazard_free():
+    # the next tile's samples go straight into the row buffer the correction has just read
+    assert _hazards(R=8, A=3, D=2, NS=2, NZ=2, load="after_correction") == []
+    # issued before that correction, the load would overwrite a tile still to be corrected
+    found = _hazards(R=8, A=3, D=2, NS=2, NZ=2, load="early")
+    assert found and any("still holds" in f for f in found)
+
+
 def test_every_tile_is_corrected_once_for_empty_and_single_tile_launches():
     for n_tiles in (0, 1, 2):
         for W in (1, 7):
