@@ -354,7 +354,9 @@ sos_status sos_server_add_stream(sos_server *s, int n_sections, const double *so
 sos_status sos_server_submit(sos_server *s, int stream_id, const float *x_dev, float *y_dev, int64_t n,
                              uint64_t *request_id);
 /* Move up to `max` completions to out (oldest first), waiting up to wait_ms for one if none is
- * ready.  Returns the first error of any batch (sticky) or SOS_OK. */
+ * ready.  Returns the first error of any batch (sticky) or SOS_OK.  The requests of a batch that
+ * could not be issued complete with its error, and their streams keep the state they had before
+ * it (the next chunk continues as if the failed one had been skipped). */
 sos_status sos_server_poll(sos_server *s, sos_completion *out, int max, int *n_out, int wait_ms);
 /* Wait until every queued request has completed. */
 sos_status sos_server_drain(sos_server *s);

@@ -116,6 +116,7 @@ void scheduler(sos_server *s) {
     std::vector<const float *> xs, zis;
     std::vector<float *> ys, zfs;
     std::vector<int64_t> ns;
+    std::vector<int> sids;  // the batch's streams (the batch itself may be gone once it completes)
     std::unique_lock<std::mutex> lk(s->mu);
     for (;;) {
         if (s->stop && s->queued == 0) break;
@@ -161,9 +162,11 @@ void scheduler(sos_server *s) {
         ns.resize(m);
         zis.resize(m);
         zfs.resize(m);
+        sids.resize(m);
         for (size_t i = 0; i < m; ++i) {
             Req &r = b->reqs[i];
             Stream &st = s->streams[r.sid];
+            sids[i] = r.sid;
             fs[i] = st.f;
             xs[i] = r.x;
             ys[i] = r.y;
@@ -181,7 +184,12 @@ void scheduler(sos_server *s) {
             for (Req &r : b->reqs) r.status = st;
         const bool queued_ok = cudaLaunchHostFunc(cs, batch_done, b) == cudaSuccess;
         lk.lock();
-        if (st != SOS_OK && s->sticky == SOS_OK) s->sticky = st;
+        if (st != SOS_OK) {
+            if (s->sticky == SOS_OK) s->sticky = st;
+            // the batch did not run: its streams keep the state they had before it (only this
+            // thread admits chunks, so none of them is in another batch meanwhile)
+            for (int sid : sids) s->streams[sid].cur ^= 1;
+        }
         if (!queued_ok) {  // complete it here so that pollers and the budget are not stuck
             if (s->sticky == SOS_OK) s->sticky = SOS_ECUDA;
             for (Req &r : b->reqs) r.status = SOS_ECUDA;

@@ -62,6 +62,7 @@ std::mutex g_mu;
 int g_batches_now = 0, g_batches_max = 0;
 long long g_bytes_now = 0, g_bytes_max = 0, g_batches_total = 0;
 int g_delay_us = 200;
+int g_fail_next = 0;  // batched runs still to fail with SOS_ECUDA
 }  // namespace
 
 cudaError_t cudaSetDevice(int) { return cudaSuccess; }
@@ -128,6 +129,13 @@ sos_status sos_filter_destroy(sos_filter *f) {
 sos_status sos_filter_run_batch_ex(int m, sos_filter *const *fs, const float *const *x, float *const *y,
                                    const int64_t *n, const float *const *zi, float *const *zf, void *stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (g_fail_next > 0) {
+            g_fail_next -= 1;
+            return SOS_ECUDA;  // nothing enqueued, as when a launch is refused
+        }
+    }
     struct Sig {
         sos_filter *f;
         const float *x, *zi;
@@ -178,15 +186,20 @@ sos_status sos_filter_run_batch_ex(int m, sos_filter *const *fs, const float *co
 }
 
 // Test hooks: the largest number of batches and bytes in flight at once since the last reset, the
-// batches run, and the simulated run time of a batch.
+// batches run, the simulated run time of a batch, and batched runs made to fail.
 void host_stats(long long *out) {
     std::lock_guard<std::mutex> lk(g_mu);
     out[0] = g_batches_max;
     out[1] = g_bytes_max;
     out[2] = g_batches_total;
 }
+void host_fail_next(int n) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_fail_next = n;
+}
 void host_reset(int delay_us) {
     std::lock_guard<std::mutex> lk(g_mu);
+    g_fail_next = 0;
     g_batches_max = g_batches_now;
     g_bytes_max = g_bytes_now;
     g_batches_total = 0;

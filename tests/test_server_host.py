@@ -6,7 +6,8 @@ batched run filters in float64 and keeps float32 states between chunks, as the l
 records how many batches and bytes were in flight at once.  The tests check admission by the
 memory budget, one chunk in flight per stream and the chunks of a stream in order, batches that
 overlap, rejection of chunks larger than the budget, the up-front checks of a replay, the resident
-state, and that destroying the server finishes its queued work.
+state, a failed batch reported on its requests and as the server's sticky status, and that
+destroying the server finishes its queued work.
 """
 import ctypes
 import os
@@ -51,6 +52,7 @@ def lib():
     L.sos_server_replay.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
     L.host_stats.argtypes = [vp]
     L.host_reset.argtypes = [c_int]
+    L.host_fail_next.argtypes = [c_int]
     return L
 
 
@@ -229,3 +231,41 @@ def test_destroy_finishes_the_queued_work(lib):
         assert srv.submit(sids[i % 3], x, y)[0] == SOS_OK
     srv.close()  # returns once every queued chunk has run
     assert all(np.isfinite(y).all() for y in ys)
+
+
+def test_a_failed_batch_is_reported_and_its_streams_keep_their_state(lib):
+    SOS_ECUDA = -3
+    srv = Server(lib, budget=1 << 20, max_batch=4, max_inflight=1, delay_us=100)
+    sos = designs.butter_lowpass(4, 0.2)
+    sids = [srv.add(sos) for _ in range(2)]
+    lib.host_fail_next(1)  # the first batch is refused
+    xs = [workloads.normal_f32(80 + i, 600) for i in range(6)]
+    ys = [np.full_like(x, np.nan) for x in xs]
+    rid_of = {}
+    for i in range(6):
+        rc, rid = srv.submit(sids[i % 2], xs[i], ys[i])
+        assert rc == SOS_OK
+        rid_of[rid] = i
+    out = (Completion * 16)()
+    status = {}
+    while len(status) < 6:
+        k = ctypes.c_int()
+        rc = lib.sos_server_poll(srv.h, out, 16, ctypes.byref(k), 100)
+        status.update({rid_of[c.request_id]: c.status for c in out[:k.value]})
+    assert rc == SOS_ECUDA  # the first error of any batch, sticky
+    assert lib.sos_server_drain(srv.h) == SOS_ECUDA
+    failed = sorted(i for i, st in status.items() if st != SOS_OK)
+    assert failed and all(status[i] == SOS_ECUDA for i in failed)
+    assert all(i < 4 for i in failed)  # the first batch held at most the first chunk of each stream
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == 6 and st["inflight_bytes"] == 0
+    # each stream continues from its state before the failed chunk, as if that chunk were skipped
+    for s in range(2):
+        z = np.zeros((2, 2))
+        for i in range(s, 6, 2):
+            if i in failed:
+                assert np.isnan(ys[i]).all()
+                continue
+            y_ref, z = oracle.sosfilt(sos, xs[i], zi=z, return_state=True)
+            assert oracle.rel_err(ys[i], y_ref) < 1e-5, i
