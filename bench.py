@@ -355,6 +355,30 @@ def bench_ours(args):
         dist.destroy_process_group()
 
 
+def batch_sample_leg(specs, xs, ys, n_sample: int = 64):
+    """The float64 oracle over the first `n_sample` signals of a batched mix (one host core): its
+    rate, and each signal's error max|y - y_oracle| / max|y_oracle| against the bound the GPU tests
+    apply to random mixes (the plain bound, widened where float32 arithmetic itself cannot reach it:
+    tests/_tol.py).  `xs` are the host inputs, `ys` the outputs of the timed run (tensors)."""
+    import oracle
+    from tests import _tol
+    errs, within, dt, total = [], 0, 0.0, 0
+    for (sos, n, _), x, y in zip(specs[:n_sample], xs[:n_sample], ys[:n_sample]):
+        t0 = time.perf_counter()
+        ref = oracle.sosfilt(sos, x)
+        dt += time.perf_counter() - t0
+        total += n
+        err = oracle.rel_err(y.cpu().numpy(), ref)
+        errs.append(err)
+        within += err < _tol.bound(sos, x, ref, random_mix=True)
+    base = {"value": total / dt / 1e9, "unit": "GS/s", "cores": 1, "kind": "oracle",
+            "sample": f"the first {len(errs)} signals of the mix ({total} samples), one host core, {dt:.1f} s"}
+    acc = {"signals": len(errs), "within_bound": int(within), "max_rel_error": float(max(errs)),
+           "median_rel_error": float(np.median(errs)),
+           "measure": "per signal max|y - y_oracle| / max|y_oracle|, bound as in the GPU tests for random mixes"}
+    return base, acc
+
+
 def bench_batched(args):
     """Batched mix: 4096 signals (orders 2/4/8/16, lengths 2^10..2^22) in one sos_filter_run_batch call
     per step; GS/s of the whole batch, and its ratio to the plain kernel's rate at each signal's order."""
@@ -368,7 +392,12 @@ def bench_batched(args):
     n_sig = 4096
     specs = [workloads.batched_signal(i) for i in range(n_sig)]
     fs = [SosFilter(sos) for sos, _, _ in specs]
-    xs = [torch.from_numpy(workloads.normal_f32(seed, n)).cuda() for _, n, seed in specs]
+    xs, xs_host = [], []  # host copies kept only for the CPU leg's sample
+    for i, (_, n, seed) in enumerate(specs):
+        x = workloads.normal_f32(seed, n)
+        xs.append(torch.from_numpy(x).cuda())
+        if i < 64:
+            xs_host.append(x)
     ys = [torch.empty_like(x) for x in xs]
     total = sum(n for _, n, _ in specs)
     for _ in range(args.warmup):
@@ -438,6 +467,8 @@ def bench_batched(args):
             "cuda_graph": {"value": total / graph_ms / 1e6, "ms_per_step": graph_ms, "vs_plain_kernel": plain_ms / graph_ms},
             "plain_gss_by_order": {str(2 * k): v for k, v in rate.items()},
             "gpu_launches": 4 * args.steps, "clocks": clk.summary()}
+    if not args.no_cpu:
+        line["cpu_baseline"], line["accuracy"] = batch_sample_leg(specs, xs_host, ys)
     print(json.dumps(line), flush=True)
 
 

@@ -82,3 +82,14 @@ def test_reference_arm_prints_one_contract_line():
 def test_reference_arm_other_ranks_exit_quietly():
     assert _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "3"],
                       {"WORLD_SIZE": "2", "RANK": "1", "LOCAL_RANK": "1"}) == []
+
+
+def test_batched_sample_leg_counts_signals_within_their_bound():
+    specs = [(sos, min(n, 20000), seed) for sos, n, seed in (workloads.batched_signal(i) for i in range(10))]
+    xs = [workloads.normal_f32(seed, n) for _, n, seed in specs]
+    ys = [torch.from_numpy(oracle.sosfilt(sos, x).astype(np.float32)) for (sos, _, _), x in zip(specs, xs)]
+    ys[3][len(ys[3]) // 2] += 1.0  # one signal's output off by far more than its bound
+    base, acc = bench.batch_sample_leg(specs, xs, ys, n_sample=8)
+    assert acc["signals"] == 8 and acc["within_bound"] == 7
+    assert acc["max_rel_error"] > 1e-3 and acc["median_rel_error"] < 1e-6
+    assert base["kind"] == "oracle" and base["cores"] == 1 and base["value"] > 0
