@@ -1,0 +1,204 @@
+// Host stand-ins below the library's host code (sosfilt_api.cpp) for tests without a GPU: the CUDA
+// runtime (host memory, streams that run their work at once) and the kernel launchers.  Test
+// infrastructure only.
+//
+// A launcher records its launch (which kernel, K, N, b0 handling, grid, and a copy of its parameter
+// block) and applies a marker in place of the filter: every output sample is twice its input, and
+// word 0 of the final state is word 0 of the initial state plus the samples processed (the other
+// words are copied).  So a test can tell that every sample went through exactly one launch per pass
+// and that states were chained, and can read the tables the host built from the recorded
+// parameters (their pointers are host memory here).
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <set>
+#include <vector>
+
+#include "cuda_runtime.h"
+#include "sosfilt.h"
+#include "sosfilt_internal.h"
+
+struct host_stream {
+    int id;
+};
+struct host_event {
+    int id;
+};
+
+namespace {
+struct Launch {
+    int kind, K, N, norm;
+    long long grid;
+    std::vector<unsigned char> params;
+};
+std::vector<Launch> g_launches;
+
+template <class P>
+void record(int kind, int K, int N, bool norm, long long grid, const P &p) {
+    Launch l{kind, K, N, norm ? 1 : 0, grid, {}};
+    l.params.resize(sizeof(P));
+    std::memcpy(l.params.data(), &p, sizeof(P));
+    g_launches.push_back(std::move(l));
+}
+
+void mark(const float *x, float *y, long long n, const float *zi, float *zf, int K) {
+    for (long long i = 0; i < n; ++i) y[i] = 2.0f * x[i];
+    if (zf)
+        for (int j = 0; j < 2 * K; ++j) zf[j] = (zi ? zi[j] : 0.0f) + (j == 0 ? static_cast<float>(n) : 0.0f);
+}
+}  // namespace
+
+cudaError_t cudaSetDevice(int) { return cudaSuccess; }
+cudaError_t cudaGetDevice(int *d) {
+    *d = 0;
+    return cudaSuccess;
+}
+cudaError_t cudaGetLastError(void) { return cudaSuccess; }
+cudaError_t cudaDeviceSynchronize(void) { return cudaSuccess; }
+cudaError_t cudaDeviceGetAttribute(int *v, cudaDeviceAttr, int) {
+    *v = 4;  // a small "GPU": four SMs
+    return cudaSuccess;
+}
+cudaError_t cudaMalloc(void **p, size_t bytes) {
+    *p = std::calloc(1, bytes ? bytes : 1);
+    return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+}
+cudaError_t cudaFree(void *p) {
+    std::free(p);
+    return cudaSuccess;
+}
+cudaError_t cudaMallocHost(void **p, size_t bytes) { return cudaMalloc(p, bytes); }
+cudaError_t cudaFreeHost(void *p) { return cudaFree(p); }
+cudaError_t cudaMemcpy(void *dst, const void *src, size_t bytes, cudaMemcpyKind) {
+    std::memmove(dst, src, bytes);
+    return cudaSuccess;
+}
+cudaError_t cudaMemcpyAsync(void *dst, const void *src, size_t bytes, cudaMemcpyKind k, cudaStream_t) {
+    return cudaMemcpy(dst, src, bytes, k);
+}
+cudaError_t cudaMemset(void *dst, int v, size_t bytes) {
+    std::memset(dst, v, bytes);
+    return cudaSuccess;
+}
+cudaError_t cudaMemsetAsync(void *dst, int v, size_t bytes, cudaStream_t) { return cudaMemset(dst, v, bytes); }
+cudaError_t cudaStreamCreateWithFlags(cudaStream_t *s, unsigned) {
+    *s = new host_stream{0};
+    return cudaSuccess;
+}
+cudaError_t cudaStreamSynchronize(cudaStream_t) { return cudaSuccess; }
+cudaError_t cudaStreamDestroy(cudaStream_t s) {
+    delete s;
+    return cudaSuccess;
+}
+cudaError_t cudaStreamWaitEvent(cudaStream_t, cudaEvent_t, unsigned) { return cudaSuccess; }
+cudaError_t cudaEventCreate(cudaEvent_t *e) {
+    *e = new host_event{0};
+    return cudaSuccess;
+}
+cudaError_t cudaEventCreateWithFlags(cudaEvent_t *e, unsigned) { return cudaEventCreate(e); }
+cudaError_t cudaEventRecord(cudaEvent_t, cudaStream_t) { return cudaSuccess; }
+cudaError_t cudaEventSynchronize(cudaEvent_t) { return cudaSuccess; }
+cudaError_t cudaEventDestroy(cudaEvent_t e) {
+    delete e;
+    return cudaSuccess;
+}
+cudaError_t cudaEventElapsedTime(float *ms, cudaEvent_t, cudaEvent_t) {
+    *ms = 1.0f;
+    return cudaSuccess;
+}
+
+namespace sosk {
+
+bool dccr_available(int, int, bool, int) { return true; }
+int cascade_blocks_per_sm_32(int, bool) { return 1; }
+int cascade_blocks_per_sm_64(int, bool) { return 1; }
+size_t cascade_smem_32(int) { return 0; }
+size_t cascade_smem_64(int) { return 0; }
+int lane_blocks_per_sm_n32a(int, bool) { return 2; }
+int lane_blocks_per_sm_n32b(int, bool) { return 2; }
+int lane_blocks_per_sm_n64a(int, bool) { return 1; }
+int lane_blocks_per_sm_n64b(int, bool) { return 1; }
+int batch_blocks_per_sm(int, bool) { return 1; }
+int default_lbm(int N) { return N <= 32 ? 4 : N == 64 ? 2 : 1; }
+
+cudaError_t launch_dccr(int K, int N, bool norm, int, const PassParams &p, long long grid, cudaStream_t) {
+    record(4, K, N, norm, grid, p);
+    mark(p.x, p.y, p.n, p.zi, p.zf, K);
+    return cudaSuccess;
+}
+
+#define HOST_LANE(K, N)                                                                             \
+    template <>                                                                                     \
+    cudaError_t launch_lane<K, N>(bool norm, const LaneParams<K> &p, long long grid, cudaStream_t) { \
+        record(1, K, N, norm, grid, p);                                                             \
+        mark(p.x, p.y, p.n, p.zi, p.zf, K);                                                         \
+        return cudaSuccess;                                                                         \
+    }
+#define HOST_CAS(K, N)                                                                                \
+    template <>                                                                                       \
+    cudaError_t launch_cascade<K, N>(bool norm, const CasParams<K, N> &p, long long grid, cudaStream_t) { \
+        record(2, K, N, norm, grid, p);                                                               \
+        mark(p.x, p.y, p.n, p.zi, p.zf, K);                                                           \
+        return cudaSuccess;                                                                           \
+    }
+#define HOST_BATCH(K)                                                                                \
+    template <>                                                                                      \
+    cudaError_t launch_batch<K>(bool norm, const BatchParams<K> &p, long long grid, cudaStream_t) {   \
+        record(3, K, 64, norm, grid, p);                                                             \
+        std::set<int> sigs(p.tile_sig, p.tile_sig + p.n_tiles);                                      \
+        for (int i : sigs) {                                                                         \
+            const BatchSig &g = p.sigs[i];                                                           \
+            mark(g.x, g.y, g.n, g.zi, g.zf, K);                                                      \
+        }                                                                                            \
+        return cudaSuccess;                                                                          \
+    }
+#define HOST_ALL(K) HOST_LANE(K, 32) HOST_LANE(K, 64) HOST_CAS(K, 32) HOST_CAS(K, 64) HOST_BATCH(K)
+HOST_ALL(1) HOST_ALL(2) HOST_ALL(3) HOST_ALL(4) HOST_ALL(5) HOST_ALL(6) HOST_ALL(7) HOST_ALL(8)
+
+}  // namespace sosk
+
+// Test hooks.
+extern "C" {
+void host_reset(void) { g_launches.clear(); }
+int host_launches(void) { return static_cast<int>(g_launches.size()); }
+// kind (1 PH lane, 2 cyclic-reduction cascade, 3 batch, 4 per-section cyclic reduction), K, N,
+// b0 normalization, grid; returns the parameter block's size and copies up to cap bytes of it
+long long host_launch(int i, int *info, long long *grid, void *params, long long cap) {
+    const Launch &l = g_launches.at(static_cast<size_t>(i));
+    info[0] = l.kind;
+    info[1] = l.K;
+    info[2] = l.N;
+    info[3] = l.norm;
+    *grid = l.grid;
+    const long long n = static_cast<long long>(l.params.size());
+    if (params) std::memcpy(params, l.params.data(), static_cast<size_t>(n < cap ? n : cap));
+    return n;
+}
+// byte offsets in LaneParams<K>: x, y, n, G, n_tiles, zi, zf, gain, m_last, tab, sec, MX, A_tail
+#define LANE_OFFS(K)                                                                                          \
+    case K: {                                                                                                 \
+        using P = sosk::LaneParams<K>;                                                                        \
+        const long long o[] = {offsetof(P, x),    offsetof(P, y),   offsetof(P, n),  offsetof(P, G),          \
+                               offsetof(P, n_tiles), offsetof(P, zi), offsetof(P, zf), offsetof(P, gain),     \
+                               offsetof(P, m_last), offsetof(P, tab), offsetof(P, sec), offsetof(P, MX),      \
+                               offsetof(P, A_tail)};                                                          \
+        std::memcpy(out, o, sizeof o);                                                                        \
+        return static_cast<long long>(sizeof(P));                                                             \
+    }
+long long host_lane_layout(int K, long long *out) {
+    switch (K) {
+        LANE_OFFS(1) LANE_OFFS(2) LANE_OFFS(3) LANE_OFFS(4) LANE_OFFS(5) LANE_OFFS(6) LANE_OFFS(7) LANE_OFFS(8)
+        default: return -1;
+    }
+}
+// sizeof(LaneSec), sizeof(BatchSig) and the byte offsets in BatchSig: x, y, n, G, tile0, zi, zf,
+// tab, gain; in BatchParams<1>: sigs, tile_sig, n_tiles
+void host_batch_layout(long long *out) {
+    using B = sosk::BatchSig;
+    using P = sosk::BatchParams<1>;
+    const long long o[] = {sizeof(sosk::LaneSec), sizeof(B), offsetof(B, x), offsetof(B, y), offsetof(B, n),
+                           offsetof(B, G), offsetof(B, tile0), offsetof(B, zi), offsetof(B, zf), offsetof(B, tab),
+                           offsetof(B, gain), offsetof(P, sigs), offsetof(P, tile_sig), offsetof(P, n_tiles)};
+    std::memcpy(out, o, sizeof o);
+}
+}

@@ -1,0 +1,350 @@
+"""The library's host code on the CPU: sosfilt_api.cpp compiled against host stand-ins for the CUDA
+runtime and the kernel launchers (tests/api_host/).
+
+The stand-in launchers record each launch and, in place of the filter, write twice the input to the
+output and add the samples processed to word 0 of the state.  That is enough to check, without a
+GPU:
+
+* the host precompute of the PH kernel: section constants, coupling blocks,
+  lane and tile transition powers, the output basis and the input gain, against a float64
+  derivation here from the transposed-direct-form-II recurrence (Eq. 1);
+* which kernel a tuning selects, and the passes of a cascade of more than eight sections;
+* the host-buffer pipeline of sos_filter_run_host: every sample passes through exactly one launch
+  and the state is chained through the chunks, for ragged lengths and chunk sizes;
+* the batched run's plan: one launch per (section count, b0 handling) class, each signal's tiles
+  consecutive in the tile -> signal map, and each signal's buffers and length in its descriptor.
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import workloads
+from paper_2607_23763_gb300._binding import Tuning
+from workloads import designs
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_ROOT = os.path.dirname(_HERE)
+_CSRC = os.path.join(_ROOT, "paper_2607_23763_gb300", "csrc")
+_SRCS = [os.path.join(_HERE, "api_host", "api_host.cpp"), os.path.join(_CSRC, "sosfilt_api.cpp")]
+_DEPS = _SRCS + [os.path.join(_HERE, "api_host", "cuda_runtime.h"), os.path.join(_ROOT, "include", "sosfilt.h"),
+                 os.path.join(_CSRC, "sosfilt_internal.h")]
+_LIB = os.path.join(_HERE, "_build", "libapi_host.so")
+N64, W, C64 = 64, 7, 32 * 64
+KIND_LANE, KIND_CASCADE, KIND_BATCH, KIND_SECTION = 1, 2, 3, 4
+
+
+@pytest.fixture(scope="module")
+def lib():
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if not os.path.exists(_LIB) or any(os.path.getmtime(d) > os.path.getmtime(_LIB) for d in _DEPS):
+        tmp = _LIB + ".tmp"
+        subprocess.run(["g++", "-std=c++17", "-O1", "-fPIC", "-shared", "-pthread",
+                        "-I", os.path.join(_HERE, "api_host"), "-I", os.path.join(_ROOT, "include"), "-I", _CSRC,
+                        "-o", tmp, *_SRCS], check=True)
+        os.replace(tmp, _LIB)
+    L = ctypes.CDLL(_LIB)
+    vp, i64, c_int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    L.sos_filter_create.argtypes = [c_int, vp, vp, vp, ctypes.POINTER(vp)]
+    L.sos_filter_destroy.argtypes = [vp]
+    L.sos_filter_run.argtypes = [vp, vp, vp, i64, vp, vp, vp]
+    L.sos_filter_run_host.argtypes = [vp, vp, vp, i64, vp, vp, i64]
+    L.sos_filter_run_batch_ex.argtypes = [c_int, vp, vp, vp, vp, vp, vp, vp]
+    L.host_launch.argtypes = [c_int, vp, ctypes.POINTER(ctypes.c_longlong), vp, ctypes.c_longlong]
+    L.host_launch.restype = ctypes.c_longlong
+    L.host_lane_layout.argtypes = [c_int, vp]
+    L.host_lane_layout.restype = ctypes.c_longlong
+    L.host_batch_layout.argtypes = [vp]
+    return L
+
+
+def _create(L, sos, tuning=None):
+    sos = np.ascontiguousarray(sos, dtype=np.float64)
+    h = ctypes.c_void_p()
+    t = Tuning(**tuning) if tuning else None
+    rc = L.sos_filter_create(sos.shape[0], sos.ctypes.data, None, None if t is None else ctypes.addressof(t),
+                             ctypes.byref(h))
+    assert rc == 0, rc
+    return h
+
+
+def _launches(L):
+    out = []
+    for i in range(L.host_launches()):
+        info = (ctypes.c_int * 4)()
+        grid = ctypes.c_longlong()
+        size = L.host_launch(i, info, ctypes.byref(grid), None, 0)
+        buf = (ctypes.c_ubyte * size)()
+        L.host_launch(i, info, ctypes.byref(grid), buf, size)
+        out.append({"kind": info[0], "K": info[1], "N": info[2], "norm": info[3], "grid": grid.value,
+                    "raw": bytes(buf)})
+    return out
+
+
+def _at(raw, off, dtype, count=1):
+    return np.frombuffer(raw, dtype=dtype, count=count, offset=off)
+
+
+def _mem(addr, dtype, count):
+    return np.ctypeslib.as_array((ctypes.c_byte * (np.dtype(dtype).itemsize * count)).from_address(addr)).view(dtype)
+
+
+# ---------------------------------------------------------------- float64 derivations (Eq. 1)
+
+def _normalised(sos):
+    sos = np.asarray(sos, dtype=np.float64)
+    norm = bool(np.all(sos[:, 0] != 0))
+    c = sos.copy()
+    if norm:
+        c[:, 1] /= c[:, 0]
+        c[:, 2] /= c[:, 0]
+        c[:, 0] = 1.0
+    return c, norm
+
+
+def _step(c, z, x=0.0):
+    """One sample through the cascade in transposed direct form II; z is updated in place."""
+    v = x
+    for k, (b0, b1, b2, a1, a2) in enumerate(c):
+        y = b0 * v + z[2 * k]
+        z[2 * k] = b1 * v - a1 * y + z[2 * k + 1]
+        z[2 * k + 1] = b2 * v - a2 * y
+        v = y
+    return v
+
+
+def _transition_and_basis(c, N):
+    S = 2 * len(c)
+    M1 = np.zeros((S, S))
+    H = np.zeros((S, N))
+    for j in range(S):
+        z = np.zeros(S)
+        z[j] = 1.0
+        _step(c, z)
+        M1[:, j] = z
+        z = np.zeros(S)
+        z[j] = 1.0
+        for m in range(N):
+            H[j, m] = _step(c, z)
+    return M1, H
+
+
+def _packed(M, K):
+    out = []
+    for s in range(K):
+        for t in range(s + 1):
+            out += [M[2 * s, 2 * t], M[2 * s, 2 * t + 1], M[2 * s + 1, 2 * t], M[2 * s + 1, 2 * t + 1]]
+    return np.array(out)
+
+
+def _close(got, want, what, seen=0.0):
+    """float32 tables against float64 values: 2e-6 of the largest entry, plus float64 rounding of
+    the products that formed them (1e-12 of `seen`, the largest intermediate entry)."""
+    got = np.asarray(got, dtype=np.float64)
+    want = np.asarray(want, dtype=np.float64)
+    bound = 2e-6 * max(1e-30, float(np.abs(want).max())) + 1e-12 * seen
+    err = float(np.abs(got - want).max())
+    assert err <= bound, f"{what}: error {err:.3e} above {bound:.3e}"
+
+
+# ---------------------------------------------------------------- tests
+
+DESIGNS = {
+    "butter2": designs.butter_lowpass(2, 0.2),
+    "butter8": designs.butter_lowpass(8, 0.1),
+    "butter16": designs.butter_lowpass(16, 0.05),
+    "random5": designs.random_sections(workloads.uniform_f64(3, 15, stream=1).reshape(5, 3)),
+    "resonators": designs.resonator_bank(),
+}
+
+
+@pytest.mark.parametrize("name", list(DESIGNS))
+def test_ph_tables_match_a_float64_derivation(lib, name):
+    sos = DESIGNS[name]
+    K = sos.shape[0]
+    f = _create(lib, sos)
+    n = 3 * W * C64 + 5
+    x = workloads.normal_f32(1, n)
+    y = np.empty_like(x)
+    lib.host_reset()
+    assert lib.sos_filter_run(f, x.ctypes.data, y.ctypes.data, n, None, None, None) == 0
+    (l,) = _launches(lib)
+    assert (l["kind"], l["K"], l["N"]) == (KIND_LANE, K, N64)
+    offs = (ctypes.c_longlong * 13)()
+    size = lib.host_lane_layout(K, offs)
+    assert size == len(l["raw"])
+    o = dict(zip(["x", "y", "n", "G", "n_tiles", "zi", "zf", "gain", "m_last", "tab", "sec", "MX", "A_tail"], offs))
+    raw = l["raw"]
+    G = -(-n // C64)
+    assert _at(raw, o["n"], np.int64)[0] == n and _at(raw, o["G"], np.int64)[0] == G
+    assert _at(raw, o["n_tiles"], np.int64)[0] == -(-G // W)
+    assert _at(raw, o["x"], np.uint64)[0] == x.ctypes.data and _at(raw, o["y"], np.uint64)[0] == y.ctypes.data
+
+    c, norm = _normalised(sos)
+    assert bool(l["norm"]) == norm
+    assert _at(raw, o["gain"], np.float32)[0] == pytest.approx(np.prod(sos[:, 0]) if norm else 1.0, rel=1e-6)
+    M1, H = _transition_and_basis(c, N64)
+    MN = np.linalg.matrix_power(M1, N64)
+    AC = np.linalg.matrix_power(MN, 32)
+    AT = np.linalg.matrix_power(AC, W)
+    S = 2 * K
+    # section constants (LaneSec: c, g, tn[5] as float4, then b0, zscale, zscale_inv, pad)
+    sec = _at(raw, o["sec"], np.float32, 32 * K).reshape(K, 32)
+    for j, (b0, b1, b2, a1, a2) in enumerate(c):
+        _close(sec[j, 0:4], [b1, b2, -a1, -a2], f"{name} c[{j}]")
+        _close(sec[j, 4:8], [b1 - b0 * a1, b2 - b0 * a2, b2 - b0 * a2, a1 * b2 - a2 * b1], f"{name} g[{j}]")
+        P = MN[2 * j:2 * j + 2, 2 * j:2 * j + 2]
+        for r in range(5):
+            _close(sec[j, 8 + 4 * r:12 + 4 * r], P.reshape(-1), f"{name} tn[{j}][{r}]")
+            P = P @ P
+        zscale = np.prod(sos[j + 1:, 0]) if norm else 1.0
+        _close(sec[j, 28:30], [b0, zscale], f"{name} b0, zscale[{j}]")
+    # coupling blocks of M_N
+    if K > 1:
+        MX = _at(raw, o["MX"], np.float32, 2 * K * (K - 1)).reshape(-1, 4)
+        for k in range(1, K):
+            for j in range(k):
+                _close(MX[k * (k - 1) // 2 + j], MN[2 * k:2 * k + 2, 2 * j:2 * j + 2].reshape(-1), f"{name} MX")
+    # the table block: (M_N)^l and (A_T)^l packed, A_C, the basis H, A_T (column-major)
+    nf = 2 * K * (K + 1)
+    ms = nf if (nf // 4) % 2 else nf + 4
+    full = S * S
+    tab = _mem(int(_at(raw, o["tab"], np.uint64)[0]), np.float32, 64 * ms + 2 * full + N64 * S)
+    # (the resonator bank's normalized sections couple with gains near 1e9, so the powers pass
+    # through entries near 1e10 before they cancel: its float64 rounding is relative to those)
+    Ml, Tl = np.eye(S), np.eye(S)
+    seen_m = seen_t = 1.0
+    for lane in range(32):
+        seen_m, seen_t = max(seen_m, np.abs(Ml).max()), max(seen_t, np.abs(Tl).max())
+        _close(tab[lane * ms:lane * ms + nf], _packed(Ml, K), f"{name} (M_N)^{lane}", seen_m)
+        _close(tab[(32 + lane) * ms:(32 + lane) * ms + nf], _packed(Tl, K), f"{name} (A_T)^{lane}", seen_t)
+        Ml, Tl = Ml @ MN, Tl @ AT
+    off = 64 * ms
+    _close(tab[off:off + full], AC.T.reshape(-1), f"{name} A_C")
+    _close(tab[off + full:off + full + S * N64], H.reshape(-1), f"{name} basis")
+    _close(tab[off + full + S * N64:off + 2 * full + S * N64], AT.T.reshape(-1), f"{name} A_T")
+    lib.sos_filter_destroy(f)
+
+
+@pytest.mark.parametrize("tuning,kind,N", [
+    (None, KIND_LANE, 64), ({"N": 32}, KIND_LANE, 32), ({"deterministic": 1}, KIND_LANE, 64),
+    ({"solver": 1}, KIND_CASCADE, 32), ({"solver": 1, "N": 64}, KIND_CASCADE, 64),
+    ({"carry": 2, "N": 32}, KIND_SECTION, 32), ({"carry": 2, "N": 128}, KIND_SECTION, 128),
+])
+def test_a_tuning_selects_its_kernel(lib, tuning, kind, N):
+    f = _create(lib, designs.butter_lowpass(8, 0.2), tuning)
+    x = workloads.normal_f32(2, 50000)
+    y = np.empty_like(x)
+    lib.host_reset()
+    assert lib.sos_filter_run(f, x.ctypes.data, y.ctypes.data, x.size, None, None, None) == 0
+    ls = _launches(lib)
+    assert {(l["kind"], l["N"]) for l in ls} == {(kind, N)}
+    np.testing.assert_array_equal(y, 2 * x * (1 if kind != KIND_SECTION else 2 ** (len(ls) - 1)))
+    lib.sos_filter_destroy(f)
+
+
+def test_more_than_eight_sections_run_in_passes(lib):
+    sos = designs.random_sections(workloads.uniform_f64(5, 36, stream=1).reshape(12, 3))
+    f = _create(lib, sos)
+    x = workloads.normal_f32(3, 30000)
+    y = np.empty_like(x)
+    zi = np.arange(24, dtype=np.float32).reshape(12, 2)
+    zf = np.zeros_like(zi)
+    lib.host_reset()
+    assert lib.sos_filter_run(f, x.ctypes.data, y.ctypes.data, x.size, zi.ctypes.data, zf.ctypes.data, None) == 0
+    ls = _launches(lib)
+    assert [(l["kind"], l["K"]) for l in ls] == [(KIND_LANE, 8), (KIND_LANE, 4)]
+    np.testing.assert_array_equal(y, 4 * x)  # the second pass filters the first one's output
+    # each pass carries its own sections' states: word 0 of each pass's state advanced by n
+    want = zi.copy()
+    want[0, 0] += x.size
+    want[8, 0] += x.size
+    np.testing.assert_array_equal(zf, want)
+    lib.sos_filter_destroy(f)
+
+
+@pytest.mark.parametrize("n,chunk", [(0, 1000), (1, 1000), (999, 1000), (1000, 1000), (1001, 1000),
+                                     (3 * 4096 + 5, 4096), (10007, 64), (20000, 20000 // 3)])
+def test_run_host_passes_every_sample_once_and_chains_the_state(lib, n, chunk):
+    f = _create(lib, designs.butter_lowpass(4, 0.2))
+    x = workloads.normal_f32(4, n) if n else np.zeros(0, np.float32)
+    y = np.full_like(x, np.nan)
+    zi = np.array([[0.5, 1.0], [2.0, 3.0]], dtype=np.float32)
+    zf = np.full_like(zi, np.nan)
+    lib.host_reset()
+    rc = lib.sos_filter_run_host(f, x.ctypes.data if n else None, y.ctypes.data if n else None, n,
+                                 zi.ctypes.data, zf.ctypes.data, chunk)
+    assert rc == 0
+    np.testing.assert_array_equal(y, 2 * x)
+    assert lib.host_launches() == -(-n // chunk)
+    want = zi.copy()
+    want[0, 0] += n
+    np.testing.assert_array_equal(zf, want)
+    lib.sos_filter_destroy(f)
+
+
+def test_batched_plan_groups_signals_by_class_with_consecutive_tiles(lib):
+    rng = np.random.default_rng(9)
+    specs = []
+    for i in range(40):
+        K = [1, 2, 4, 8][i % 4]
+        sos = designs.random_sections(workloads.uniform_f64(100 + i, 3 * K, stream=1).reshape(K, 3))
+        if i % 5 == 0:
+            sos[0, 0] = 0.0  # b0 = 0: the general (not normalized) class
+        n = int(rng.choice([0, 1, 2047, 2048, 2049, 14336, 14337, 40000, 100003]))
+        specs.append((sos, n))
+    fs = [_create(lib, sos) for sos, _ in specs]
+    xs = [workloads.normal_f32(200 + i, n) if n else np.zeros(1, np.float32) for i, (_, n) in enumerate(specs)]
+    ys = [np.full_like(x, np.nan) for x in xs]
+    zis = [np.full((sos.shape[0], 2), 0.25 * i, dtype=np.float32) for i, (sos, _) in enumerate(specs)]
+    zfs = [np.full_like(z, np.nan) for z in zis]
+    m = len(specs)
+    arr = lambda vals: (ctypes.c_void_p * m)(*vals)
+    lens = (ctypes.c_int64 * m)(*[n for _, n in specs])
+    lib.host_reset()
+    rc = lib.sos_filter_run_batch_ex(m, arr([h.value for h in fs]), arr([x.ctypes.data for x in xs]),
+                                     arr([y.ctypes.data for y in ys]), lens, arr([z.ctypes.data for z in zis]),
+                                     arr([z.ctypes.data for z in zfs]), None)
+    assert rc == 0
+    lay = (ctypes.c_longlong * 14)()
+    lib.host_batch_layout(lay)
+    _, sig_size, ox, oy, on, oG, ot0, ozi, ozf, otab, ogain, p_sigs, p_tile_sig, p_ntiles = lay
+    launches = _launches(lib)
+    assert all(l["kind"] == KIND_BATCH for l in launches)
+    seen = []
+    for l in launches:
+        raw = l["raw"]
+        n_tiles = int(_at(raw, p_ntiles, np.int64)[0])
+        tile_sig = _mem(int(_at(raw, p_tile_sig, np.uint64)[0]), np.int32, n_tiles)
+        n_sig = int(tile_sig.max()) + 1
+        sigs = bytes(_mem(int(_at(raw, p_sigs, np.uint64)[0]), np.uint8, n_sig * sig_size))
+        tiles = 0
+        for k in range(n_sig):
+            b = sigs[k * sig_size:(k + 1) * sig_size]
+            i = next(j for j, x in enumerate(xs) if x.ctypes.data == _at(b, ox, np.uint64)[0])
+            sos, n = specs[i]
+            G = -(-n // C64)
+            nt = -(-G // W)
+            assert _at(b, on, np.int64)[0] == n and _at(b, oG, np.int64)[0] == G
+            assert _at(b, oy, np.uint64)[0] == ys[i].ctypes.data
+            assert _at(b, ozi, np.uint64)[0] == zis[i].ctypes.data and _at(b, ozf, np.uint64)[0] == zfs[i].ctypes.data
+            t0 = int(_at(b, ot0, np.int64)[0])
+            assert np.all(tile_sig[t0:t0 + nt] == k), i  # the signal's tiles are consecutive
+            assert (l["K"], l["norm"]) == (sos.shape[0], int(np.all(sos[:, 0] != 0)))
+            tiles += nt
+            seen.append(i)
+        assert tiles == n_tiles  # the map holds exactly the class's signals' tiles
+    # every signal with samples is in exactly one class launch; the empty ones copy their state
+    assert sorted(seen) == [i for i, (_, n) in enumerate(specs) if n > 0]  # once each
+    for i, (sos, n) in enumerate(specs):
+        if n:
+            np.testing.assert_array_equal(ys[i], 2 * xs[i])
+            want = zis[i].copy()
+            want[0, 0] += n
+            np.testing.assert_array_equal(zfs[i], want)
+        else:
+            np.testing.assert_array_equal(zfs[i], zis[i])
+    for h in fs:
+        lib.sos_filter_destroy(h)
