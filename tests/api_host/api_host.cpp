@@ -191,6 +191,17 @@ long long host_lane_layout(int K, long long *out) {
         default: return -1;
     }
 }
+// sizeof(SecCoef) and the byte offsets in SecCoef: t0, b1, ne, f, nf, qo, qe, tn, tc, zscale; in
+// PassParams: sec, lane_pow, grp_pow, cta_pow, n_sec, gain, n
+void host_pass_layout(long long *out) {
+    using S = sosk::SecCoef;
+    using P = sosk::PassParams;
+    const long long o[] = {sizeof(S), offsetof(S, t0), offsetof(S, b1), offsetof(S, ne), offsetof(S, f),
+                           offsetof(S, nf), offsetof(S, qo), offsetof(S, qe), offsetof(S, tn), offsetof(S, tc),
+                           offsetof(S, zscale), offsetof(P, sec), offsetof(P, lane_pow), offsetof(P, grp_pow),
+                           offsetof(P, cta_pow), offsetof(P, n_sec), offsetof(P, gain), offsetof(P, n)};
+    std::memcpy(out, o, sizeof o);
+}
 // sizeof(LaneSec), sizeof(BatchSig) and the byte offsets in BatchSig: x, y, n, G, tile0, zi, zf,
 // tab, gain; in BatchParams<1>: sigs, tile_sig, n_tiles
 void host_batch_layout(long long *out) {

@@ -348,3 +348,99 @@ def test_batched_plan_groups_signals_by_class_with_consecutive_tiles(lib):
             np.testing.assert_array_equal(zfs[i], zis[i])
     for h in fs:
         lib.sos_filter_destroy(h)
+
+
+@pytest.mark.parametrize("name", ["butter2", "butter16", "random5"])
+@pytest.mark.parametrize("N", [32, 64, 128])
+def test_cyclic_reduction_tables_match_the_float64_model(lib, name, N):
+    """The per-section tables of the divide-and-conquer cyclic reduction (Eqs. 14-23) against the
+    float64 step model, which the dense solves pin to the oracle."""
+    from . import dccr_model as M
+    sos = DESIGNS[name]
+    K = sos.shape[0]
+    f = _create(lib, sos, {"carry": 2, "N": N})
+    x = workloads.normal_f32(5, 5 * 32 * N + 7)
+    y = np.empty_like(x)
+    lib.host_reset()
+    assert lib.sos_filter_run(f, x.ctypes.data, y.ctypes.data, x.size, None, None, None) == 0
+    (l,) = _launches(lib)
+    assert (l["kind"], l["K"], l["N"]) == (KIND_SECTION, K, N)
+    lay = (ctypes.c_longlong * 18)()
+    lib.host_pass_layout(lay)
+    (sz, o_t0, o_b1, o_ne, o_f, o_nf, o_qo, o_qe, o_tn, o_tc, o_zs,
+     p_sec, p_lane, p_grp, p_cta, p_nsec, p_gain, p_n) = lay
+    raw = l["raw"]
+    assert _at(raw, p_nsec, np.int32)[0] == K and _at(raw, p_n, np.int64)[0] == x.size
+    c, norm = _normalised(sos)
+    D = int(np.log2(N))
+    lane_pow = _mem(int(_at(raw, p_lane, np.uint64)[0]), np.float32, K * 32 * 4).reshape(K, 32, 4)
+    for k, (b0, b1, b2, a1, a2) in enumerate(c):
+        sec = raw[p_sec + k * sz:p_sec + (k + 1) * sz]
+        _close(_at(sec, o_t0, np.float32, 5), M.first_level_taps(b0, b1, b2, a1, a2), f"{name} taps[{k}]")
+        _close(_at(sec, o_b1, np.float32, 4), [b1, b2, a1, a2], f"{name} b1 b2 a1 a2[{k}]")
+        e, fl = M.level_coeffs(a1, a2, D)
+        for i in range(1, D):
+            _close(_at(sec, o_ne + 4 * i, np.float32), [-e[i]], f"{name} -e_{i}")
+            _close(_at(sec, o_f + 4 * i, np.float32), [fl[i]], f"{name} f_{i}")
+            _close(_at(sec, o_nf + 4 * i, np.float32), [-fl[i]], f"{name} -f_{i}")
+        Q = M.q_tables(a1, a2, D)
+        q = lambda lev, m: Q[lev][m] if 0 <= m < len(Q[lev]) else 0.0
+        for lev in range(1, D + 1):
+            mo, me = (1 << lev) - 1, (1 << lev) - 2
+            _close(_at(sec, o_qo + 8 * lev, np.float32, 2), [q(lev, mo), q(lev, mo - 1)], f"{name} qo_{lev}")
+            _close(_at(sec, o_qe + 8 * lev, np.float32, 2), [q(lev, me), q(lev, me - 1)], f"{name} qe_{lev}")
+        T = M.transition(a1, a2)
+        TN = np.linalg.matrix_power(T, N)
+        P = TN
+        for r in range(5):
+            _close(_at(sec, o_tn + 16 * r, np.float32, 4), P.reshape(-1), f"{name} tn_{r}")
+            P = P @ P
+        Ll = np.eye(2)
+        for lane in range(32):
+            _close(lane_pow[k, lane], Ll.reshape(-1), f"{name} (T^N)^{lane}")
+            Ll = Ll @ TN
+        TC = Ll
+        Wp = np.eye(2)
+        for w in range(5):
+            _close(_at(sec, o_tc + 16 * w, np.float32, 4), Wp.reshape(-1), f"{name} (T^C)^{w}")
+            Wp = Wp @ TC
+        zscale = np.prod(sos[k + 1:, 0]) if norm else 1.0
+        _close(_at(sec, o_zs, np.float32), [zscale], f"{name} zscale[{k}]")
+    lib.sos_filter_destroy(f)
+
+
+def test_stream_push_continues_the_resident_state(lib):
+    lib.sos_filter_stream_push.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int64, ctypes.c_void_p]
+    lib.sos_filter_stream_state.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int]
+    f = _create(lib, designs.butter_lowpass(6, 0.2))
+    z_in = np.arange(6, dtype=np.float32).reshape(3, 2)
+    assert lib.sos_filter_stream_state(f, None, z_in.ctypes.data, 0) == 0
+    total = 0
+    for n in (1, 2048, 14336 * 2 + 3, 0, 777):
+        x = workloads.normal_f32(10 + n, n) if n else np.zeros(1, np.float32)
+        y = np.full_like(x, np.nan)
+        assert lib.sos_filter_stream_push(f, x.ctypes.data, y.ctypes.data, n, None) == 0
+        if n:
+            np.testing.assert_array_equal(y, 2 * x)
+        total += n
+    z = np.full((3, 2), np.nan, dtype=np.float32)
+    assert lib.sos_filter_stream_state(f, z.ctypes.data, None, 0) == 0
+    want = z_in.copy()
+    want[0, 0] += total
+    np.testing.assert_array_equal(z, want)
+    lib.sos_filter_destroy(f)
+
+
+def test_empty_run_copies_the_state_and_overlaps_are_rejected(lib):
+    f = _create(lib, designs.butter_lowpass(4, 0.2))
+    zi = np.array([[1.5, -2.0], [3.0, 4.0]], dtype=np.float32)
+    zf = np.zeros_like(zi)
+    lib.host_reset()
+    assert lib.sos_filter_run(f, None, None, 0, zi.ctypes.data, zf.ctypes.data, None) == 0
+    assert lib.host_launches() == 0
+    np.testing.assert_array_equal(zf, zi)
+    buf = workloads.normal_f32(6, 5000)
+    # in place is allowed; a partial overlap is an argument error
+    assert lib.sos_filter_run(f, buf.ctypes.data, buf.ctypes.data, 4000, None, None, None) == 0
+    assert lib.sos_filter_run(f, buf.ctypes.data, buf.ctypes.data + 4 * 100, 4000, None, None, None) == -1
+    lib.sos_filter_destroy(f)
