@@ -444,3 +444,29 @@ def test_empty_run_copies_the_state_and_overlaps_are_rejected(lib):
     assert lib.sos_filter_run(f, buf.ctypes.data, buf.ctypes.data, 4000, None, None, None) == 0
     assert lib.sos_filter_run(f, buf.ctypes.data, buf.ctypes.data + 4 * 100, 4000, None, None, None) == -1
     lib.sos_filter_destroy(f)
+
+
+@pytest.mark.parametrize("n", [1, 64, 65, 2047, 2048, 2049, 3 * 14336 + 100, 100003])
+def test_final_state_tail_transition(lib, n):
+    """For the final state the kernel needs the lane position of the last sample and the cascade's
+    transition over the samples up to it: M1^(m_last + 1), recomputed when the position changes."""
+    sos = DESIGNS["butter8"]
+    K = sos.shape[0]
+    f = _create(lib, sos)
+    offs = (ctypes.c_longlong * 13)()
+    lib.host_lane_layout(K, offs)
+    o = dict(zip(["x", "y", "n", "G", "n_tiles", "zi", "zf", "gain", "m_last", "tab", "sec", "MX", "A_tail"], offs))
+    c, _ = _normalised(sos)
+    M1, _ = _transition_and_basis(c, 1)
+    for length in (n, n + 1, n):  # a changed tail, then the first one again
+        x = workloads.normal_f32(7, length)
+        y = np.empty_like(x)
+        zf = np.zeros((K, 2), dtype=np.float32)
+        lib.host_reset()
+        assert lib.sos_filter_run(f, x.ctypes.data, y.ctypes.data, length, None, zf.ctypes.data, None) == 0
+        (l,) = _launches(lib)
+        m_last = (length - 1) % N64  # groups are whole multiples of N samples
+        assert _at(l["raw"], o["m_last"], np.int32)[0] == m_last
+        want = _packed(np.linalg.matrix_power(M1, m_last + 1), K)
+        _close(_at(l["raw"], o["A_tail"], np.float32, 2 * K * (K + 1)), want, f"tail n={length}")
+    lib.sos_filter_destroy(f)
