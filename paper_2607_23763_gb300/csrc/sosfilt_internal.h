@@ -95,7 +95,7 @@ struct CasParams {
     int *status;
     long long spin_budget;
     int aligned;                // x and y 16-byte aligned
-    const float *tab;           // (M_N)^lane [32][MS], A_C, A_T^(2^k) (k < 5), A_T^(32 w) (w < kMaxWin)
+    const float *tab;           // (M_N)^lane, (A_T)^lane [32][MS] packed; A_C, A_T, (A_T)^(32 w) (w = 1..kMaxWin) dense
     unsigned long long *trace;  // nullptr, or [n_tiles][kTraceSlots] phase trace (see kCasTrace*)
     long long trace_tiles;
     SecCoef sec[K];

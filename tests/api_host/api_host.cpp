@@ -191,6 +191,20 @@ long long host_lane_layout(int K, long long *out) {
         default: return -1;
     }
 }
+// byte offsets in CasParams<K, N>: n, G, n_tiles, gain, tab, sec, H, A_tail; returns its size
+#define CAS_OFFS(K, N)                                                                                   \
+    if (k == K && n == N) {                                                                              \
+        using P = sosk::CasParams<K, N>;                                                                 \
+        const long long o[] = {offsetof(P, n),   offsetof(P, G),   offsetof(P, n_tiles), offsetof(P, gain), \
+                               offsetof(P, tab), offsetof(P, sec), offsetof(P, H),       offsetof(P, A_tail)}; \
+        std::memcpy(out, o, sizeof o);                                                                   \
+        return static_cast<long long>(sizeof(P));                                                        \
+    }
+long long host_cas_layout(int k, int n, long long *out) {
+    CAS_OFFS(1, 32) CAS_OFFS(2, 32) CAS_OFFS(5, 32) CAS_OFFS(8, 32)
+    CAS_OFFS(1, 64) CAS_OFFS(2, 64) CAS_OFFS(5, 64) CAS_OFFS(8, 64)
+    return -1;
+}
 // sizeof(SecCoef) and the byte offsets in SecCoef: t0, b1, ne, f, nf, qo, qe, tn, tc, zscale; in
 // PassParams: sec, lane_pow, grp_pow, cta_pow, n_sec, gain, n
 void host_pass_layout(long long *out) {

@@ -470,3 +470,53 @@ def test_final_state_tail_transition(lib, n):
         want = _packed(np.linalg.matrix_power(M1, m_last + 1), K)
         _close(_at(l["raw"], o["A_tail"], np.float32, 2 * K * (K + 1)), want, f"tail n={length}")
     lib.sos_filter_destroy(f)
+
+
+@pytest.mark.parametrize("name", ["butter2", "butter16", "random5"])
+@pytest.mark.parametrize("N", [32, 64])
+def test_cascade_carry_tables_match_a_float64_derivation(lib, name, N):
+    """The whole-cascade carry of the cyclic-reduction kernel: lane and tile transition powers, A_C,
+    A_T and its 32-tile powers for the lookback windows, and the output basis."""
+    sos = DESIGNS[name]
+    K = sos.shape[0]
+    Wc = 8 if N == 32 else 4  # groups per tile of the cascade kernel
+    f = _create(lib, sos, {"solver": 1, "N": N})
+    x = workloads.normal_f32(8, 5 * Wc * 32 * N + 9)
+    y = np.empty_like(x)
+    lib.host_reset()
+    assert lib.sos_filter_run(f, x.ctypes.data, y.ctypes.data, x.size, None, None, None) == 0
+    (l,) = _launches(lib)
+    assert (l["kind"], l["K"], l["N"]) == (KIND_CASCADE, K, N)
+    offs = (ctypes.c_longlong * 8)()
+    assert lib.host_cas_layout(K, N, offs) == len(l["raw"])
+    o_n, o_G, o_nt, o_gain, o_tab, o_sec, o_H, o_tail = offs
+    raw = l["raw"]
+    G = -(-x.size // (32 * N))
+    assert _at(raw, o_G, np.int64)[0] == G and _at(raw, o_nt, np.int64)[0] == -(-G // Wc)
+    c, _ = _normalised(sos)
+    M1, H = _transition_and_basis(c, N)
+    MN = np.linalg.matrix_power(M1, N)
+    AC = np.linalg.matrix_power(MN, 32)
+    AT = np.linalg.matrix_power(AC, Wc)
+    S = 2 * K
+    _close(_at(raw, o_H, np.float32, S * N), H.reshape(-1), f"{name} basis")
+    nf = 2 * K * (K + 1)
+    ms = nf if (nf // 4) % 2 else nf + 4
+    full = S * S
+    tab = _mem(int(_at(raw, o_tab, np.uint64)[0]), np.float32, 64 * ms + 18 * full)
+    Ml, Tl = np.eye(S), np.eye(S)
+    seen_m = seen_t = 1.0
+    for lane in range(32):
+        seen_m, seen_t = max(seen_m, np.abs(Ml).max()), max(seen_t, np.abs(Tl).max())
+        _close(tab[lane * ms:lane * ms + nf], _packed(Ml, K), f"{name} (M_N)^{lane}", seen_m)
+        _close(tab[(32 + lane) * ms:(32 + lane) * ms + nf], _packed(Tl, K), f"{name} (A_T)^{lane}", seen_t)
+        Ml, Tl = Ml @ MN, Tl @ AT
+    d = 64 * ms
+    _close(tab[d:d + full], AC.T.reshape(-1), f"{name} A_C")
+    _close(tab[d + full:d + 2 * full], AT.T.reshape(-1), f"{name} A_T")
+    AT32 = np.linalg.matrix_power(AT, 32)
+    Pw = AT32
+    for w in range(1, 17):
+        _close(tab[d + full * (1 + w):d + full * (2 + w)], Pw.T.reshape(-1), f"{name} (A_T)^(32*{w})")
+        Pw = Pw @ AT32
+    lib.sos_filter_destroy(f)
