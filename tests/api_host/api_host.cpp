@@ -217,13 +217,14 @@ void host_pass_layout(long long *out) {
     std::memcpy(out, o, sizeof o);
 }
 // sizeof(LaneSec), sizeof(BatchSig) and the byte offsets in BatchSig: x, y, n, G, tile0, zi, zf,
-// tab, gain; in BatchParams<1>: sigs, tile_sig, n_tiles
+// tab, gain; in BatchParams<1>: sigs, tile_sig, n_tiles; in BatchSig: sec, MX, Mm
 void host_batch_layout(long long *out) {
     using B = sosk::BatchSig;
     using P = sosk::BatchParams<1>;
     const long long o[] = {sizeof(sosk::LaneSec), sizeof(B), offsetof(B, x), offsetof(B, y), offsetof(B, n),
                            offsetof(B, G), offsetof(B, tile0), offsetof(B, zi), offsetof(B, zf), offsetof(B, tab),
-                           offsetof(B, gain), offsetof(P, sigs), offsetof(P, tile_sig), offsetof(P, n_tiles)};
+                           offsetof(B, gain), offsetof(P, sigs), offsetof(P, tile_sig), offsetof(P, n_tiles),
+                           offsetof(B, sec), offsetof(B, MX), offsetof(B, Mm)};
     std::memcpy(out, o, sizeof o);
 }
 }

@@ -308,9 +308,9 @@ def test_batched_plan_groups_signals_by_class_with_consecutive_tiles(lib):
                                      arr([y.ctypes.data for y in ys]), lens, arr([z.ctypes.data for z in zis]),
                                      arr([z.ctypes.data for z in zfs]), None)
     assert rc == 0
-    lay = (ctypes.c_longlong * 14)()
+    lay = (ctypes.c_longlong * 17)()
     lib.host_batch_layout(lay)
-    _, sig_size, ox, oy, on, oG, ot0, ozi, ozf, otab, ogain, p_sigs, p_tile_sig, p_ntiles = lay
+    _, sig_size, ox, oy, on, oG, ot0, ozi, ozf, otab, ogain, p_sigs, p_tile_sig, p_ntiles, _, _, _ = lay
     launches = _launches(lib)
     assert all(l["kind"] == KIND_BATCH for l in launches)
     seen = []
@@ -519,4 +519,55 @@ def test_cascade_carry_tables_match_a_float64_derivation(lib, name, N):
     for w in range(1, 17):
         _close(tab[d + full * (1 + w):d + full * (2 + w)], Pw.T.reshape(-1), f"{name} (A_T)^(32*{w})")
         Pw = Pw @ AT32
+    lib.sos_filter_destroy(f)
+
+
+def test_batch_tables_match_a_float64_derivation(lib):
+    """A signal of a batch carries its own tables: the PH section constants and coupling blocks, the
+    table block for tiles of seven groups, the gain, and the one-sample transition powers M1^(m+1),
+    m < 64, from which the kernel forms a signal's final state."""
+    sos = DESIGNS["butter8"]
+    K = sos.shape[0]
+    f = _create(lib, sos)
+    x = workloads.normal_f32(12, 3 * W * C64 + 11)
+    y = np.empty_like(x)
+    zf = np.zeros((K, 2), dtype=np.float32)
+    one = lambda v: (ctypes.c_void_p * 1)(v)
+    lib.host_reset()
+    assert lib.sos_filter_run_batch_ex(1, one(f.value), one(x.ctypes.data), one(y.ctypes.data),
+                                       (ctypes.c_int64 * 1)(x.size), None, one(zf.ctypes.data), None) == 0
+    (l,) = _launches(lib)
+    assert (l["kind"], l["K"]) == (KIND_BATCH, K)
+    lay = (ctypes.c_longlong * 17)()
+    lib.host_batch_layout(lay)
+    sec_size, sig_size = lay[0], lay[1]
+    otab, ogain, p_sigs, osec, oMX, oMm = lay[9], lay[10], lay[11], lay[14], lay[15], lay[16]
+    sig = bytes(_mem(int(_at(l["raw"], p_sigs, np.uint64)[0]), np.uint8, sig_size))
+    c, norm = _normalised(sos)
+    M1, H = _transition_and_basis(c, N64)
+    MN = np.linalg.matrix_power(M1, N64)
+    AC = np.linalg.matrix_power(MN, 32)
+    AT = np.linalg.matrix_power(AC, W)
+    S, nf = 2 * K, 2 * K * (K + 1)
+    assert _at(sig, ogain, np.float32)[0] == pytest.approx(np.prod(sos[:, 0]), rel=1e-6)
+    secs = _mem(int(_at(sig, osec, np.uint64)[0]), np.float32, K * sec_size // 4).reshape(K, -1)
+    for j, (b0, b1, b2, a1, a2) in enumerate(c):
+        _close(secs[j, 0:4], [b1, b2, -a1, -a2], f"batch c[{j}]")
+    MX = _mem(int(_at(sig, oMX, np.uint64)[0]), np.float32, 2 * K * (K - 1)).reshape(-1, 4)
+    for k in range(1, K):
+        for j in range(k):
+            _close(MX[k * (k - 1) // 2 + j], MN[2 * k:2 * k + 2, 2 * j:2 * j + 2].reshape(-1), "batch MX")
+    Mm = _mem(int(_at(sig, oMm, np.uint64)[0]), np.float32, N64 * nf).reshape(N64, nf)
+    P = M1.copy()
+    for m in range(N64):
+        _close(Mm[m], _packed(P, K), f"batch M1^{m + 1}")
+        P = P @ M1
+    ms = nf if (nf // 4) % 2 else nf + 4
+    full = S * S
+    tab = _mem(int(_at(sig, otab, np.uint64)[0]), np.float32, 64 * ms + 2 * full + N64 * S)
+    Tl = np.eye(S)
+    for lane in range(32):
+        _close(tab[(32 + lane) * ms:(32 + lane) * ms + nf], _packed(Tl, K), f"batch (A_T)^{lane}")
+        Tl = Tl @ AT
+    _close(tab[64 * ms + full + S * N64:64 * ms + 2 * full + S * N64], AT.T.reshape(-1), "batch A_T")
     lib.sos_filter_destroy(f)
