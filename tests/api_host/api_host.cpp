@@ -7,7 +7,9 @@
 // word 0 of the final state is word 0 of the initial state plus the samples processed (the other
 // words are copied).  So a test can tell that every sample went through exactly one launch per pass
 // and that states were chained, and can read the tables the host built from the recorded
-// parameters (their pointers are host memory here).
+// parameters (their pointers are host memory here).  Events measure simulated time: the sum of a
+// per-(kernel, N, K) cost over the launches recorded between them, so that the autotuner's choice
+// can be steered.
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
@@ -22,7 +24,7 @@ struct host_stream {
     int id;
 };
 struct host_event {
-    int id;
+    size_t mark;  // launches recorded before the event
 };
 
 namespace {
@@ -32,16 +34,23 @@ struct Launch {
     std::vector<unsigned char> params;
 };
 std::vector<Launch> g_launches;
+bool g_light = false;          // record no parameter blocks and skip the marker (timing runs)
+float g_cost[5][3][9] = {};    // simulated time of a launch, ms, by kind, N (32, 64, 128) and K
+
+int n_index(int N) { return N == 32 ? 0 : N == 64 ? 1 : 2; }
 
 template <class P>
 void record(int kind, int K, int N, bool norm, long long grid, const P &p) {
     Launch l{kind, K, N, norm ? 1 : 0, grid, {}};
-    l.params.resize(sizeof(P));
-    std::memcpy(l.params.data(), &p, sizeof(P));
+    if (!g_light) {
+        l.params.resize(sizeof(P));
+        std::memcpy(l.params.data(), &p, sizeof(P));
+    }
     g_launches.push_back(std::move(l));
 }
 
 void mark(const float *x, float *y, long long n, const float *zi, float *zf, int K) {
+    if (g_light) return;
     for (long long i = 0; i < n; ++i) y[i] = 2.0f * x[i];
     if (zf)
         for (int j = 0; j < 2 * K; ++j) zf[j] = (zi ? zi[j] : 0.0f) + (j == 0 ? static_cast<float>(n) : 0.0f);
@@ -96,14 +105,24 @@ cudaError_t cudaEventCreate(cudaEvent_t *e) {
     return cudaSuccess;
 }
 cudaError_t cudaEventCreateWithFlags(cudaEvent_t *e, unsigned) { return cudaEventCreate(e); }
-cudaError_t cudaEventRecord(cudaEvent_t, cudaStream_t) { return cudaSuccess; }
+cudaError_t cudaEventRecord(cudaEvent_t e, cudaStream_t) {
+    e->mark = g_launches.size();
+    return cudaSuccess;
+}
 cudaError_t cudaEventSynchronize(cudaEvent_t) { return cudaSuccess; }
 cudaError_t cudaEventDestroy(cudaEvent_t e) {
     delete e;
     return cudaSuccess;
 }
-cudaError_t cudaEventElapsedTime(float *ms, cudaEvent_t, cudaEvent_t) {
-    *ms = 1.0f;
+// the simulated times of the launches recorded between the two events (1 ms each by default)
+cudaError_t cudaEventElapsedTime(float *ms, cudaEvent_t a, cudaEvent_t b) {
+    double t = 0.0;
+    for (size_t i = a->mark; i < b->mark && i < g_launches.size(); ++i) {
+        const Launch &l = g_launches[i];
+        const float c = g_cost[l.kind][n_index(l.N)][l.K];
+        t += c > 0.f ? c : 1.0;
+    }
+    *ms = static_cast<float>(t);
     return cudaSuccess;
 }
 
@@ -160,6 +179,8 @@ HOST_ALL(1) HOST_ALL(2) HOST_ALL(3) HOST_ALL(4) HOST_ALL(5) HOST_ALL(6) HOST_ALL
 // Test hooks.
 extern "C" {
 void host_reset(void) { g_launches.clear(); }
+void host_set_light(int on) { g_light = on != 0; }
+void host_set_cost(int kind, int N, int K, float ms) { g_cost[kind][n_index(N)][K] = ms; }
 int host_launches(void) { return static_cast<int>(g_launches.size()); }
 // kind (1 PH lane, 2 cyclic-reduction cascade, 3 batch, 4 per-section cyclic reduction), K, N,
 // b0 normalization, grid; returns the parameter block's size and copies up to cap bytes of it

@@ -571,3 +571,63 @@ def test_batch_tables_match_a_float64_derivation(lib):
         Tl = Tl @ AT
     _close(tab[64 * ms + full + S * N64:64 * ms + 2 * full + S * N64], AT.T.reshape(-1), "batch A_T")
     lib.sos_filter_destroy(f)
+
+
+def _tune_costs(lib, fastest):
+    """Simulated launch times: the candidate fastest(K) takes 1 ms per launch, the others 2 and 3."""
+    cands = [(KIND_CASCADE, 32), (KIND_CASCADE, 64), (KIND_LANE, 64)]  # the autotuner's candidates
+    for K in range(1, 9):
+        best = fastest(K)
+        slow = 2.0
+        for c in cands:
+            lib.host_set_cost(c[0], c[1], K, 1.0 if c == best else slow)
+            slow += 0.0 if c == best else 1.0
+
+
+def test_autotuner_choices_drive_the_default_launch(lib):
+    """The autotuner times its three candidates per section count and length bucket and keeps the
+    fastest; default-tuned runs then launch that choice, an explicit tuning still wins."""
+    lib.sos_autotune.argtypes = [ctypes.c_int, ctypes.c_void_p]
+    lib.sos_autotune_choice.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int)]
+    lib.host_set_cost.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float]
+    solver, N = ctypes.c_int(), ctypes.c_int()
+
+    def choice(K, n):
+        assert lib.sos_autotune_choice(K, n, ctypes.byref(solver), ctypes.byref(N)) == 0
+        return solver.value, N.value
+
+    assert choice(4, 1 << 20) == (0, 0)  # nothing tuned yet: the library's defaults
+    report = np.zeros((8, 4, 3), dtype=np.float32)
+    _tune_costs(lib, lambda K: (KIND_CASCADE, 32) if K <= 3 else (KIND_LANE, 64))
+    lib.host_set_light(1)
+    try:
+        assert lib.sos_autotune(16, report.ctypes.data) == 0
+    finally:
+        lib.host_set_light(0)
+    for K in range(1, 9):
+        want = (1, 32) if K <= 3 else (2, 64)
+        for n in (1000, 1 << 16, 1 << 22, 1 << 30):  # buckets above 2^16 repeat the measured one
+            assert choice(K, n) == want, (K, n)
+        assert np.argmax(report[K - 1, 0]) == (0 if K <= 3 else 2)
+        np.testing.assert_array_equal(report[K - 1, 1:], np.repeat(report[K - 1, :1], 3, axis=0))
+    assert choice(12, 1 << 20) == (2, 64)  # more than eight sections: the eight-section choice
+
+    x = workloads.normal_f32(13, 40000)
+    y = np.empty_like(x)
+    for K, tuning, want in [(2, None, (KIND_CASCADE, 32)), (6, None, (KIND_LANE, 64)),
+                            (2, {"solver": 2}, (KIND_LANE, 64))]:
+        f = _create(lib, designs.butter_lowpass(2 * K, 0.2), tuning)
+        lib.host_reset()
+        assert lib.sos_filter_run(f, x.ctypes.data, y.ctypes.data, x.size, None, None, None) == 0
+        assert {(l["kind"], l["N"]) for l in _launches(lib)} == {want}, (K, tuning)
+        lib.sos_filter_destroy(f)
+
+    # leave the library tuned to its untuned defaults (PH, N = 64) for the tests after this one
+    _tune_costs(lib, lambda K: (KIND_LANE, 64))
+    lib.host_set_light(1)
+    try:
+        assert lib.sos_autotune(16, None) == 0
+    finally:
+        lib.host_set_light(0)
+        lib.host_reset()
