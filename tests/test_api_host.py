@@ -400,6 +400,18 @@ def test_cyclic_reduction_tables_match_the_float64_model(lib, name, N):
             _close(lane_pow[k, lane], Ll.reshape(-1), f"{name} (T^N)^{lane}")
             Ll = Ll @ TN
         TC = Ll
+        # group and block transitions for the per-section lookback: S^k (k <= 32), S^(32 i) (i <= 16)
+        stride = 33 + 16 + 1
+        for ptr, S in ((p_grp, TC), (p_cta, np.linalg.matrix_power(TC, 4))):
+            pw = _mem(int(_at(raw, ptr, np.uint64)[0]), np.float32, K * stride * 4).reshape(K, stride, 4)[k]
+            Pk = np.eye(2)
+            for j in range(33):
+                _close(pw[j], Pk.reshape(-1), f"{name} S^{j}")
+                Pk = Pk @ S
+            S32, P32 = np.linalg.matrix_power(S, 32), np.eye(2)
+            for i in range(17):
+                _close(pw[33 + i], P32.reshape(-1), f"{name} S^(32*{i})")
+                P32 = P32 @ S32
         Wp = np.eye(2)
         for w in range(5):
             _close(_at(sec, o_tc + 16 * w, np.float32, 4), Wp.reshape(-1), f"{name} (T^C)^{w}")
@@ -571,6 +583,39 @@ def test_batch_tables_match_a_float64_derivation(lib):
         Tl = Tl @ AT
     _close(tab[64 * ms + full + S * N64:64 * ms + 2 * full + S * N64], AT.T.reshape(-1), "batch A_T")
     lib.sos_filter_destroy(f)
+
+
+def test_batch_plan_launches_reuse_the_uploaded_plan(lib):
+    """A prepared plan uploads its signals once; every launch then runs one class launch per
+    (section count, b0 handling) over the same descriptors."""
+    vp = ctypes.c_void_p
+    lib.sos_batch_plan_create.argtypes = [ctypes.c_int, vp, vp, vp, vp, vp, vp, ctypes.POINTER(vp)]
+    lib.sos_batch_plan_launch.argtypes = [vp, vp]
+    lib.sos_batch_plan_status.argtypes = [vp]
+    lib.sos_batch_plan_destroy.argtypes = [vp]
+    specs = [(designs.butter_lowpass(2 * K, 0.2), n) for K, n in [(1, 5000), (4, 30000), (4, 777), (8, 60000)]]
+    fs = [_create(lib, sos) for sos, _ in specs]
+    xs = [workloads.normal_f32(300 + i, n) for i, (_, n) in enumerate(specs)]
+    ys = [np.full_like(x, np.nan) for x in xs]
+    m = len(specs)
+    arr = lambda vals: (vp * m)(*vals)
+    plan = vp()
+    assert lib.sos_batch_plan_create(m, arr([h.value for h in fs]), arr([x.ctypes.data for x in xs]),
+                                     arr([y.ctypes.data for y in ys]), (ctypes.c_int64 * m)(*[n for _, n in specs]),
+                                     None, None, ctypes.byref(plan)) == 0
+    for rep in range(2):
+        lib.host_reset()
+        for y in ys:
+            y[:] = np.nan
+        assert lib.sos_batch_plan_launch(plan, None) == 0
+        ls = _launches(lib)
+        assert sorted((l["kind"], l["K"]) for l in ls) == [(KIND_BATCH, 1), (KIND_BATCH, 4), (KIND_BATCH, 8)]
+        for x, y in zip(xs, ys):
+            np.testing.assert_array_equal(y, 2 * x)
+    assert lib.sos_batch_plan_status(plan) == 0
+    assert lib.sos_batch_plan_destroy(plan) == 0
+    for h in fs:
+        lib.sos_filter_destroy(h)
 
 
 def _tune_costs(lib, fastest):
