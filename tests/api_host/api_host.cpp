@@ -128,6 +128,9 @@ cudaError_t cudaEventElapsedTime(float *ms, cudaEvent_t a, cudaEvent_t b) {
 
 namespace sosk {
 
+sos_status run_lane_scratch(sos_filter *f, const float *x, float *y, int64_t n, const float *zi, float *zf,
+                            cudaStream_t s, const Scratch &sc, unsigned (*next_epoch)(int, cudaStream_t));
+
 bool dccr_available(int, int, bool, int) { return true; }
 int cascade_blocks_per_sm_32(int, bool) { return 1; }
 int cascade_blocks_per_sm_64(int, bool) { return 1; }
@@ -176,8 +179,25 @@ HOST_ALL(1) HOST_ALL(2) HOST_ALL(3) HOST_ALL(4) HOST_ALL(5) HOST_ALL(6) HOST_ALL
 
 }  // namespace sosk
 
+namespace {
+unsigned g_epoch = 0;
+unsigned scratch_epoch(int, cudaStream_t) { return ++g_epoch; }
+}  // namespace
+
 // Test hooks.
 extern "C" {
+// a run with caller-provided lookback scratch of desc_words words (the path of
+// sos_filter_run_noalloc); writes the scratch addresses used to where[0..1]
+int host_run_scratch(sos_filter *f, const float *x, float *y, long long n, const float *zi, float *zf,
+                     long long desc_words, unsigned long long *where) {
+    std::vector<unsigned long long> desc(static_cast<size_t>(desc_words) + 1), ticket(1, 12345);
+    sosk::Scratch sc{desc.data(), static_cast<size_t>(desc_words), ticket.data()};
+    where[0] = reinterpret_cast<unsigned long long>(desc.data());
+    where[1] = reinterpret_cast<unsigned long long>(ticket.data());
+    const int rc = sosk::run_lane_scratch(f, x, y, n, zi, zf, nullptr, sc, scratch_epoch);
+    where[2] = ticket[0];
+    return rc;
+}
 void host_reset(void) { g_launches.clear(); }
 void host_set_light(int on) { g_light = on != 0; }
 void host_set_cost(int kind, int N, int K, float ms) { g_cost[kind][n_index(N)][K] = ms; }
@@ -195,14 +215,16 @@ long long host_launch(int i, int *info, long long *grid, void *params, long long
     if (params) std::memcpy(params, l.params.data(), static_cast<size_t>(n < cap ? n : cap));
     return n;
 }
-// byte offsets in LaneParams<K>: x, y, n, G, n_tiles, zi, zf, gain, m_last, tab, sec, MX, A_tail
+// byte offsets in LaneParams<K>: x, y, n, G, n_tiles, zi, zf, gain, m_last, tab, sec, MX, A_tail,
+// desc, ticket, ticket_base, epoch
 #define LANE_OFFS(K)                                                                                          \
     case K: {                                                                                                 \
         using P = sosk::LaneParams<K>;                                                                        \
         const long long o[] = {offsetof(P, x),    offsetof(P, y),   offsetof(P, n),  offsetof(P, G),          \
                                offsetof(P, n_tiles), offsetof(P, zi), offsetof(P, zf), offsetof(P, gain),     \
                                offsetof(P, m_last), offsetof(P, tab), offsetof(P, sec), offsetof(P, MX),      \
-                               offsetof(P, A_tail)};                                                          \
+                               offsetof(P, A_tail), offsetof(P, desc), offsetof(P, ticket),                   \
+                               offsetof(P, ticket_base), offsetof(P, epoch)};                                 \
         std::memcpy(out, o, sizeof o);                                                                        \
         return static_cast<long long>(sizeof(P));                                                             \
     }

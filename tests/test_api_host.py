@@ -172,7 +172,7 @@ def test_ph_tables_match_a_float64_derivation(lib, name):
     assert lib.sos_filter_run(f, x.ctypes.data, y.ctypes.data, n, None, None, None) == 0
     (l,) = _launches(lib)
     assert (l["kind"], l["K"], l["N"]) == (KIND_LANE, K, N64)
-    offs = (ctypes.c_longlong * 13)()
+    offs = (ctypes.c_longlong * 17)()
     size = lib.host_lane_layout(K, offs)
     assert size == len(l["raw"])
     o = dict(zip(["x", "y", "n", "G", "n_tiles", "zi", "zf", "gain", "m_last", "tab", "sec", "MX", "A_tail"], offs))
@@ -465,7 +465,7 @@ def test_final_state_tail_transition(lib, n):
     sos = DESIGNS["butter8"]
     K = sos.shape[0]
     f = _create(lib, sos)
-    offs = (ctypes.c_longlong * 13)()
+    offs = (ctypes.c_longlong * 17)()
     lib.host_lane_layout(K, offs)
     o = dict(zip(["x", "y", "n", "G", "n_tiles", "zi", "zf", "gain", "m_last", "tab", "sec", "MX", "A_tail"], offs))
     c, _ = _normalised(sos)
@@ -616,6 +616,39 @@ def test_batch_plan_launches_reuse_the_uploaded_plan(lib):
     assert lib.sos_batch_plan_destroy(plan) == 0
     for h in fs:
         lib.sos_filter_destroy(h)
+
+
+def test_run_with_caller_scratch_allocates_nothing_and_checks_its_size(lib):
+    """The path of sos_filter_run_noalloc: lookback descriptors and ticket counter in caller memory
+    (the counter reset to zero for the launch, ticket base 0), a fresh epoch per pass, and
+    SOS_EBUDGET when the descriptors would not fit."""
+    lib.host_run_scratch.argtypes = [ctypes.c_void_p] * 6 + [ctypes.c_longlong, ctypes.c_void_p]
+    sos = designs.random_sections(workloads.uniform_f64(21, 33, stream=1).reshape(11, 3))  # two passes
+    f = _create(lib, sos)
+    n = 5 * W * C64 + 3
+    x = workloads.normal_f32(14, n)
+    y = np.full_like(x, np.nan)
+    n_tiles = -(-(-(-n // C64)) // W)
+    need = n_tiles * 2 * 2 * 8
+    where = (ctypes.c_ulonglong * 3)()
+    lib.host_reset()
+    assert lib.host_run_scratch(f, x.ctypes.data, y.ctypes.data, n, None, None, need - 1, where) == -6
+    assert lib.host_launches() == 0
+    assert lib.host_run_scratch(f, x.ctypes.data, y.ctypes.data, n, None, None, need, where) == 0
+    np.testing.assert_array_equal(y, 4 * x)
+    ls = _launches(lib)
+    assert [l["K"] for l in ls] == [8, 3]
+    epochs = []
+    for l in ls:
+        offs = (ctypes.c_longlong * 17)()
+        lib.host_lane_layout(l["K"], offs)
+        raw = l["raw"]
+        assert _at(raw, offs[13], np.uint64)[0] == where[0] and _at(raw, offs[14], np.uint64)[0] == where[1]
+        assert _at(raw, offs[15], np.uint64)[0] == 0
+        epochs.append(int(_at(raw, offs[16], np.uint32)[0]))
+    assert where[2] == 0  # the counter was reset for the launch
+    assert len(set(epochs)) == 2 and all(e > 0 for e in epochs)
+    lib.sos_filter_destroy(f)
 
 
 def _tune_costs(lib, fastest):
