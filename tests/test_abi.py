@@ -185,3 +185,24 @@ def test_stability_triangle_is_the_unit_circle(lib):
         sos = np.array([[1.0, 2.0, 1.0, a1, a2]])
         h = ctypes.c_void_p()
         assert lib.sos_filter_create(1, sos.ctypes.data, None, None, ctypes.byref(h)) == -5
+
+
+def test_no_cpu_fallback_without_a_gpu_or_the_library(tmp_path):
+    """The binding fails loudly: a missing library raises, and without a GPU creating a filter
+    raises SosError (SOS_ECUDA) instead of computing on the CPU."""
+    import torch
+
+    from paper_2607_23763_gb300 import _binding as B
+    with pytest.raises(RuntimeError, match="missing"):
+        saved = B._lib
+        B._lib = None
+        try:
+            B.load_library(str(tmp_path / "libsosfilt_absent.so"))
+        finally:
+            B._lib = saved
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present: the GPU tests cover the library's device path")
+    from paper_2607_23763_gb300 import SosError, SosFilter
+    with pytest.raises(SosError) as e:
+        SosFilter(np.array([[1.0, 2.0, 1.0, -0.5, 0.25]]))
+    assert e.value.code == -3 and "SOS_ECUDA" in str(e.value)
