@@ -167,6 +167,7 @@ cudaError_t launch_dccr(int K, int N, bool norm, int, const PassParams &p, long 
     template <>                                                                                      \
     cudaError_t launch_batch<K>(bool norm, const BatchParams<K> &p, long long grid, cudaStream_t) {   \
         record(3, K, 64, norm, grid, p);                                                             \
+        if (g_light) return cudaSuccess;                                                             \
         std::set<int> sigs(p.tile_sig, p.tile_sig + p.n_tiles);                                      \
         for (int i : sigs) {                                                                         \
             const BatchSig &g = p.sigs[i];                                                           \
