@@ -40,7 +40,7 @@ KIND_LANE, KIND_CASCADE, KIND_BATCH, KIND_SECTION = 1, 2, 3, 4
 def lib():
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
     if not os.path.exists(_LIB) or any(os.path.getmtime(d) > os.path.getmtime(_LIB) for d in _DEPS):
-        tmp = _LIB + ".tmp"
+        tmp = f"{_LIB}.{os.getpid()}.tmp"  # parallel test workers build side by side
         subprocess.run(["g++", "-std=c++17", "-O1", "-fPIC", "-shared", "-pthread",
                         "-I", os.path.join(_HERE, "api_host"), "-I", os.path.join(_ROOT, "include"), "-I", _CSRC,
                         "-o", tmp, *_SRCS], check=True)

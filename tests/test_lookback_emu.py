@@ -25,7 +25,7 @@ _LIB = os.path.join(_HERE, "_build", "liblookback_emu.so")
 def emu():
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
     if not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + ".tmp"
+        tmp = f"{_LIB}.{os.getpid()}.tmp"  # parallel test workers build side by side
         subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC], check=True)
         os.replace(tmp, _LIB)
     lib = ctypes.CDLL(_LIB)

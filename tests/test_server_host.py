@@ -34,7 +34,7 @@ SOS_OK, SOS_EINVAL, SOS_EBUDGET = 0, -1, -6
 def lib():
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
     if not os.path.exists(_LIB) or any(os.path.getmtime(d) > os.path.getmtime(_LIB) for d in _DEPS):
-        tmp = _LIB + ".tmp"
+        tmp = f"{_LIB}.{os.getpid()}.tmp"  # parallel test workers build side by side
         subprocess.run(["g++", "-std=c++17", "-O1", "-fPIC", "-shared", "-pthread",
                         "-I", os.path.join(_HERE, "server_host"), "-I", os.path.join(_ROOT, "include"),
                         "-o", tmp, *_SRCS], check=True)
