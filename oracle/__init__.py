@@ -37,7 +37,7 @@ def build(force: bool = False) -> str:
     if not force and os.path.exists(_LIB_PATH) and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(f)
                                                         for f in srcs):
         return _LIB_PATH
-    tmp = _LIB_PATH + ".tmp"
+    tmp = f"{_LIB_PATH}.{os.getpid()}.tmp"
     subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-pthread", "-o", tmp, *srcs], check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH

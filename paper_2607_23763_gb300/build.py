@@ -60,7 +60,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
                 raise RuntimeError(f"nvcc failed on {cmd[-3]}")
     objs = [os.path.join(OBJ, os.path.basename(s) + ".o") for s in srcs]
     if force or jobs or _stale(OUT, objs):
-        tmp = OUT + ".tmp"
+        tmp = f"{OUT}.{os.getpid()}.tmp"
         cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode:

@@ -33,7 +33,7 @@ def build(force: bool = False) -> str:
     """Compile the generator into an in-tree shared library (plain gcc, no arch flags)."""
     if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
         return _LIB_PATH
-    tmp = _LIB_PATH + ".tmp"
+    tmp = f"{_LIB_PATH}.{os.getpid()}.tmp"
     cmd = ["gcc", "-O2", "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
