@@ -217,7 +217,7 @@ long long host_launch(int i, int *info, long long *grid, void *params, long long
     return n;
 }
 // byte offsets in LaneParams<K>: x, y, n, G, n_tiles, zi, zf, gain, m_last, tab, sec, MX, A_tail,
-// desc, ticket, ticket_base, epoch
+// desc, ticket, ticket_base, epoch, spin_budget, trace, trace_tiles, aligned
 #define LANE_OFFS(K)                                                                                          \
     case K: {                                                                                                 \
         using P = sosk::LaneParams<K>;                                                                        \
@@ -225,7 +225,8 @@ long long host_launch(int i, int *info, long long *grid, void *params, long long
                                offsetof(P, n_tiles), offsetof(P, zi), offsetof(P, zf), offsetof(P, gain),     \
                                offsetof(P, m_last), offsetof(P, tab), offsetof(P, sec), offsetof(P, MX),      \
                                offsetof(P, A_tail), offsetof(P, desc), offsetof(P, ticket),                   \
-                               offsetof(P, ticket_base), offsetof(P, epoch)};                                 \
+                               offsetof(P, ticket_base), offsetof(P, epoch), offsetof(P, spin_budget),        \
+                               offsetof(P, trace), offsetof(P, trace_tiles), offsetof(P, aligned)};           \
         std::memcpy(out, o, sizeof o);                                                                        \
         return static_cast<long long>(sizeof(P));                                                             \
     }

@@ -172,7 +172,7 @@ def test_ph_tables_match_a_float64_derivation(lib, name):
     assert lib.sos_filter_run(f, x.ctypes.data, y.ctypes.data, n, None, None, None) == 0
     (l,) = _launches(lib)
     assert (l["kind"], l["K"], l["N"]) == (KIND_LANE, K, N64)
-    offs = (ctypes.c_longlong * 17)()
+    offs = (ctypes.c_longlong * 21)()
     size = lib.host_lane_layout(K, offs)
     assert size == len(l["raw"])
     o = dict(zip(["x", "y", "n", "G", "n_tiles", "zi", "zf", "gain", "m_last", "tab", "sec", "MX", "A_tail"], offs))
@@ -465,7 +465,7 @@ def test_final_state_tail_transition(lib, n):
     sos = DESIGNS["butter8"]
     K = sos.shape[0]
     f = _create(lib, sos)
-    offs = (ctypes.c_longlong * 17)()
+    offs = (ctypes.c_longlong * 21)()
     lib.host_lane_layout(K, offs)
     o = dict(zip(["x", "y", "n", "G", "n_tiles", "zi", "zf", "gain", "m_last", "tab", "sec", "MX", "A_tail"], offs))
     c, _ = _normalised(sos)
@@ -640,7 +640,7 @@ def test_run_with_caller_scratch_allocates_nothing_and_checks_its_size(lib):
     assert [l["K"] for l in ls] == [8, 3]
     epochs = []
     for l in ls:
-        offs = (ctypes.c_longlong * 17)()
+        offs = (ctypes.c_longlong * 21)()
         lib.host_lane_layout(l["K"], offs)
         raw = l["raw"]
         assert _at(raw, offs[13], np.uint64)[0] == where[0] and _at(raw, offs[14], np.uint64)[0] == where[1]
@@ -648,6 +648,39 @@ def test_run_with_caller_scratch_allocates_nothing_and_checks_its_size(lib):
         epochs.append(int(_at(raw, offs[16], np.uint32)[0]))
     assert where[2] == 0  # the counter was reset for the launch
     assert len(set(epochs)) == 2 and all(e > 0 for e in epochs)
+    lib.sos_filter_destroy(f)
+
+
+def test_launch_parameters_follow_the_filter_settings(lib):
+    """The wait budget, the phase-trace buffer, alignment, epochs and the ticket base that a launch
+    receives come from the filter's settings and history."""
+    lib.sos_filter_trace.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
+    K = 4
+    f = _create(lib, designs.butter_lowpass(2 * K, 0.2), {"spin_budget_cycles": 12345})
+    trace = np.zeros((64, 32), dtype=np.uint64)
+    assert lib.sos_filter_trace(f, trace.ctypes.data, 64) == 0
+    n = 2 * W * C64 + 1
+    x = workloads.normal_f32(15, n + 1)
+    y = np.empty_like(x)
+    offs = (ctypes.c_longlong * 21)()
+    lib.host_lane_layout(K, offs)
+    names = ["x", "y", "n", "G", "n_tiles", "zi", "zf", "gain", "m_last", "tab", "sec", "MX", "A_tail", "desc",
+             "ticket", "ticket_base", "epoch", "spin_budget", "trace", "trace_tiles", "aligned"]
+    o = dict(zip(names, offs))
+    lib.host_reset()
+    for src in (x, x[1:]):  # aligned, then 4 bytes off
+        assert lib.sos_filter_run(f, src.ctypes.data, y.ctypes.data, n, None, None, None) == 0
+    first, second = [l["raw"] for l in _launches(lib)]
+    for raw in (first, second):
+        assert _at(raw, o["spin_budget"], np.int64)[0] == 12345
+        assert _at(raw, o["trace"], np.uint64)[0] == trace.ctypes.data and _at(raw, o["trace_tiles"], np.int64)[0] == 64
+    assert _at(first, o["aligned"], np.int32)[0] == 1 and _at(second, o["aligned"], np.int32)[0] == 0
+    # every launch has its own epoch; tickets continue from where the last launch left the counter
+    assert _at(second, o["epoch"], np.uint32)[0] != _at(first, o["epoch"], np.uint32)[0]
+    n_tiles = int(_at(first, o["n_tiles"], np.int64)[0])
+    grid = _launches(lib)[0]["grid"]
+    assert _at(second, o["ticket_base"], np.uint64)[0] == _at(first, o["ticket_base"], np.uint64)[0] + n_tiles + grid
+    assert lib.sos_filter_trace(f, None, 0) == 0
     lib.sos_filter_destroy(f)
 
 
