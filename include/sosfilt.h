@@ -4,13 +4,15 @@
  *
  * Method (Zhai & Paris, "Parallel Cascaded Recursive Filtering on Multi-Core
  * CPUs and GPUs"): every group of C = N*L samples is stride-N permuted into the
- * block-banded system of Eq. 2-3 (Sec. II-B); its zero-state response is solved
- * in registers by divide-and-conquer cyclic reduction (Sec. II-E, Eqs. 19-23),
- * which exposes both terminal samples of the group before back substitution;
- * terminal states are carried across groups by decoupled lookback (Sec. IV-B,
- * Eq. 25) and the homogeneous correction (Eq. 24) is applied once a group's
- * incoming state is known.  All K sections of a group stay in registers inside
- * one kernel (Sec. IV-A).
+ * block-banded system of Eq. 2-3 (Sec. II-B).  Its zero-state response is
+ * solved in registers, by default by PH factorization (Sec. II-C: per-lane
+ * particular solutions and a lane scan), or, selected by sos_tuning.solver, by
+ * divide-and-conquer cyclic reduction (Sec. II-D, II-E, Eqs. 14-23), which
+ * exposes both terminal samples of a lane before back substitution.  Terminal
+ * states are carried across groups by decoupled lookback (Sec. IV-B, Eq. 25) and
+ * the homogeneous correction (Eq. 24) is applied once a group's incoming state
+ * is known.  All K sections of a group stay in registers inside one kernel
+ * (Sec. IV-A).
  *
  * Conventions used by every entry point
  *   - Coefficients: `sos` is a host array [n_sections][5] of double holding
@@ -282,24 +284,24 @@ sos_status sos_filter_sync_status(sos_filter *f);
 sos_status sos_filter_trace(sos_filter *f, uint64_t *buf_dev, int64_t capacity_blocks);
 
 /*
- * sos_filter_run: the same filtering, for callers that cannot allocate device memory
- * while they filter.  (The paper has no counterpart; this is a library service.)  A
- * real-time thread, such as an audio or radio receive loop, must not call cudaMalloc or
- * cudaFree in its processing loop, because those calls can block and synchronize the
- * device; other applications hand out all device memory at start-up.  Such a caller
- * creates the filter (sos_filter_create allocates its tables once) and then filters
- * with this entry point, which calls no cudaMalloc, cudaFree or other allocating routine:
- * the scratch memory of a run (lookback descriptors and ticket counter) lives in one
- * fixed array of 4.6 MiB in the library's device code, which every GPU that loads the
- * library holds until the process exits.
- *   Arguments and results are those of sos_filter_run (always the default solver, PH
- *   factorization at N = 64, whose outputs are bit-identical from run to run).
+ * sos_filter_run_noalloc: the same filtering, for callers that cannot allocate device memory
+ * while they filter.  (The paper has no counterpart; this is a library service.)  A real-time
+ * thread, such as an audio or radio receive loop, must not call cudaMalloc or cudaFree in its
+ * processing loop, because those calls can block and synchronize the device; other applications
+ * hand out all device memory at start-up.  Such a caller creates the filter (sos_filter_create
+ * allocates its tables once, including the final-state tables for every length) and then filters
+ * with this entry point, which allocates nothing: no cudaMalloc, cudaFree or other allocating
+ * CUDA routine, and no host heap allocation.  The scratch memory of a run (lookback descriptors
+ * and ticket counter) lives in one fixed array of 4.6 MiB in the library's device code, which
+ * every GPU that loads the library holds until the process exits.
+ *   Arguments and results are those of sos_filter_run with the PH solver at N = 64 (the default
+ *   solver), and so are its outputs and final states, bit for bit.
  *   n            at most SOS_NOALLOC_MAX_SAMPLES samples per call, else SOS_EBUDGET
  *   The first call on a device looks up the array's device address on the current device
  *   (a one-time set-up); make that first call before any stream capture.
- *   All calls on a device share the array and its last contents: the ticket counter is
- *   reset at the start of each pass and descriptors carry a per-call tag, so nothing needs
- *   clearing by the caller, but calls that overlap on the GPU (different streams, or
+ *   All calls on a device share the array and keep its last contents: each pass first clears the
+ *   ticket counter and the descriptors it will use (with cudaMemsetAsync on `stream`), so nothing
+ *   needs clearing by the caller, but calls that overlap on the GPU (different streams, or
  *   different host threads without ordering) race and must be serialized by the caller.
  */
 #define SOS_NOALLOC_MAX_SAMPLES (1LL << 28)

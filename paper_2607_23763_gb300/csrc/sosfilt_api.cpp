@@ -142,12 +142,13 @@ struct LanePass {
     std::vector<float> MX;           // coupling blocks of M_N, row-major 2x2, kp (kp - 1) / 2 of them
     std::vector<float> H;            // [2 kp][N] zero-input output basis
     float *d_tab = nullptr;          // device table block (LaneDims<kp, N>::TAB_GLOBAL floats)
+    // the cascade transition over the first m + 1 samples of a lane, M1^(m+1) packed, m < N: the
+    // final state's tail transition, taken by every run without further host work
+    std::vector<float> Mm;           // [N][packed_floats(kp)]
     // N = kBatchN only: device copies for the multi-signal kernel
     sosk::LaneSec *d_sec = nullptr;  // [kp] section constants
     float4 *d_MX = nullptr;          // coupling blocks of M_N
-    float *d_Mm = nullptr;           // [N][packed] one-sample transition powers M1^(m+1), m < N
-    int tail_m = -1;                 // m_last for which A_tail is cached
-    std::vector<float> A_tail;       // packed transition over tail_m + 1 samples
+    float *d_Mm = nullptr;           // device copy of Mm
 };
 
 }  // namespace
@@ -476,10 +477,6 @@ sos_status build_lane(sos_filter *f, int N, std::vector<LanePass> &out) {
             const double b0 = ps.coef[5 * j], b1 = ps.coef[5 * j + 1], b2 = ps.coef[5 * j + 2];
             const double a1 = ps.coef[5 * j + 3], a2 = ps.coef[5 * j + 4];
             c.c = float4{f32(b1), f32(b2), f32(-a1), f32(-a2)};
-            // transposed direct form II state after sample m from the direct form II history:
-            // z1 = b1 x - a1 y + z2[-1] and z2 = b2 x - a2 y with x = u + a1 u[-1] + a2 u[-2] and
-            // y = b0 u + b1 u[-1] + b2 u[-2]; the u[-2] terms cancel
-            c.g = float4{f32(b1 - b0 * a1), f32(b2 - b0 * a2), f32(b2 - b0 * a2), f32(a1 * b2 - a2 * b1)};
             Mat P{MN.at(2 * j, 2 * j), MN.at(2 * j, 2 * j + 1), MN.at(2 * j + 1, 2 * j), MN.at(2 * j + 1, 2 * j + 1)};
             for (int r = 0; r < 5; ++r) {
                 c.tn[r] = float4{f32(P.a), f32(P.b), f32(P.c), f32(P.d)};
@@ -515,14 +512,15 @@ sos_status build_lane(sos_filter *f, int N, std::vector<LanePass> &out) {
         if (cudaMalloc(&ps.d_tab, tab.size() * sizeof(float)) != cudaSuccess) return SOS_ENOMEM;
         if (cudaMemcpy(ps.d_tab, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
             return SOS_ECUDA;
+        const int nf = packed_floats(kp);
+        ps.Mm.assign(static_cast<size_t>(N) * nf, 0.f);
+        DMat Pm = ps.M1;
+        for (int m = 0; m < N; ++m) {
+            pack_into(Pm, kp, &ps.Mm[static_cast<size_t>(m) * nf]);
+            Pm = dmul(Pm, ps.M1);
+        }
         if (N == sosk::kBatchN) {
-            const int nf = packed_floats(kp);
-            std::vector<float> mm(static_cast<size_t>(N) * nf, 0.f);
-            DMat Pm = ps.M1;
-            for (int m = 0; m < N; ++m) {
-                pack_into(Pm, kp, &mm[static_cast<size_t>(m) * nf]);
-                Pm = dmul(Pm, ps.M1);
-            }
+            const std::vector<float> &mm = ps.Mm;
             if (cudaMalloc(&ps.d_sec, sizeof(sosk::LaneSec) * kp) != cudaSuccess ||
                 cudaMalloc(&ps.d_MX, sizeof(float) * ps.MX.size()) != cudaSuccess ||
                 cudaMalloc(&ps.d_Mm, sizeof(float) * mm.size()) != cudaSuccess)
@@ -744,8 +742,10 @@ sos_status launch_lane_pass(sos_filter *f, LanePass &ps, const float *x, float *
                             long long n_tiles, long long grid, const float *zi, float *zf, bool first, bool aligned,
                             cudaStream_t s, const sosk::Scratch *sc = nullptr, unsigned sc_epoch = 0) {
     static_assert(K >= 1 && K <= sosk::kMaxPass, "pass size");
-    auto p = std::make_unique<sosk::LaneParams<K>>();
-    std::memset(p.get(), 0, sizeof(*p));
+    // the parameter block lives on the stack (about 2 KB at K = 8): a run does no host allocation
+    sosk::LaneParams<K> pb;
+    std::memset(&pb, 0, sizeof(pb));
+    sosk::LaneParams<K> *p = &pb;
     p->x = x;
     p->y = y;
     p->n = n;
@@ -755,8 +755,13 @@ sos_status launch_lane_pass(sos_filter *f, LanePass &ps, const float *x, float *
     p->zf = zf;
     p->gain = first ? static_cast<float>(f->gain) : 1.0f;
     if (sc) {
-        // caller-provided scratch (sos_filter_run_noalloc): its ticket counter starts from zero
+        // caller-provided scratch (sos_filter_run_noalloc): its ticket counter starts from zero, and
+        // the pass's descriptors are cleared, so that no descriptor of an earlier call can be taken
+        // for this one whatever its tag (tags are never 0)
         if (cudaMemsetAsync(sc->ticket, 0, sizeof(unsigned long long), s) != cudaSuccess) return SOS_ECUDA;
+        if (cudaMemsetAsync(sc->desc, 0, static_cast<size_t>(n_tiles) * 2 * 2 * K * sizeof(unsigned long long), s) !=
+            cudaSuccess)
+            return SOS_ECUDA;
         p->desc = sc->desc;
         p->ticket = sc->ticket;
         p->ticket_base = 0;
@@ -778,14 +783,7 @@ sos_status launch_lane_pass(sos_filter *f, LanePass &ps, const float *x, float *
     const long long C = 32LL * N;
     const int m_last = static_cast<int>((n - 1 - (G - 1) * C) % N);
     p->m_last = m_last;
-    if (zf) {
-        if (ps.tail_m != m_last) {
-            ps.A_tail.assign(packed_floats(K), 0.f);
-            pack_into(dpow(ps.M1, m_last + 1), K, ps.A_tail.data());
-            ps.tail_m = m_last;
-        }
-        std::memcpy(p->A_tail, ps.A_tail.data(), sizeof(float) * packed_floats(K));
-    }
+    if (zf) std::memcpy(p->A_tail, &ps.Mm[static_cast<size_t>(m_last) * packed_floats(K)], sizeof(float) * packed_floats(K));
     cudaError_t e = sosk::launch_lane<K, N>(f->norm, *p, grid, s);
     if (e != cudaSuccess) return SOS_ECUDA;
     if (!sc) f->ticket_base += static_cast<unsigned long long>(n_tiles + grid);

@@ -5,10 +5,13 @@ namespace sosk {
 
 namespace {
 template <int K, bool NORM>
+KernelOnce g_once;
+
+template <int K, bool NORM>
 cudaError_t launch_k(const BatchParams<K> &p, long long grid, cudaStream_t s) {
     auto kern = sos_batch_kernel<K, NORM>;
     constexpr size_t smem = batch_smem_bytes<K>();
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    cudaError_t e = raise_smem_once(g_once<K, NORM>, kern, smem);
     if (e != cudaSuccess) return e;
     kern<<<static_cast<unsigned>(grid), (kBatchW + 1) * 32, smem, s>>>(p);
     return cudaGetLastError();
@@ -16,13 +19,7 @@ cudaError_t launch_k(const BatchParams<K> &p, long long grid, cudaStream_t s) {
 
 template <int K, bool NORM>
 int blocks_k() {
-    auto kern = sos_batch_kernel<K, NORM>;
-    constexpr size_t smem = batch_smem_bytes<K>();
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
-        return 0;
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, (kBatchW + 1) * 32, smem) != cudaSuccess) return 0;
-    return nb;
+    return blocks_per_sm_once(g_once<K, NORM>, sos_batch_kernel<K, NORM>, (kBatchW + 1) * 32, batch_smem_bytes<K>());
 }
 }  // namespace
 

@@ -14,10 +14,13 @@ size_t smem_bytes_64() {
 }
 
 template <int K, bool NORM>
+KernelOnce g_once;
+
+template <int K, bool NORM>
 cudaError_t launch_k_64(const CasParams<K, 64> &p, long long grid, cudaStream_t s) {
     auto kern = sos_cascade_kernel<K, 64, NORM, kW64>;
     const size_t smem = smem_bytes_64<K>();
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    cudaError_t e = raise_smem_once(g_once<K, NORM>, kern, smem);
     if (e != cudaSuccess) return e;
     kern<<<static_cast<unsigned>(grid), (kW64 + 1) * 32, smem, s>>>(p);
     return cudaGetLastError();
@@ -25,13 +28,7 @@ cudaError_t launch_k_64(const CasParams<K, 64> &p, long long grid, cudaStream_t 
 
 template <int K, bool NORM>
 int blocks_k_64() {
-    auto kern = sos_cascade_kernel<K, 64, NORM, kW64>;
-    const size_t smem = smem_bytes_64<K>();
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
-        return 0;
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, (kW64 + 1) * 32, smem) != cudaSuccess) return 0;
-    return nb;
+    return blocks_per_sm_once(g_once<K, NORM>, sos_cascade_kernel<K, 64, NORM, kW64>, (kW64 + 1) * 32, smem_bytes_64<K>());
 }
 }  // namespace
 

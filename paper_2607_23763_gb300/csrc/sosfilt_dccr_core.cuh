@@ -2,11 +2,47 @@
 // primitives, and the register-resident divide-and-conquer cyclic reduction of one
 // section over one group (Sec. II-E, Eqs. 14-23).
 #pragma once
+#include <atomic>
+
 #include <cuda_runtime.h>
 
 #include "sosfilt_internal.h"
 
 namespace sosk {
+
+// Host side of a kernel instantiation, once per device: its dynamic shared-memory limit is raised
+// on the first launch (the setting lasts for the context) and its resident blocks per SM are
+// queried once, so that the launch path makes no attribute or occupancy call after the first.
+struct KernelOnce {
+    std::atomic<unsigned long long> smem_set{0}, occ_set{0};  // one bit per device
+    int occ[64] = {};
+};
+
+template <class F>
+inline cudaError_t raise_smem_once(KernelOnce &k, F kern, size_t smem) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ULL << (dev & 63);
+    if (k.smem_set.load(std::memory_order_acquire) & bit) return cudaSuccess;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e == cudaSuccess) k.smem_set.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+}
+
+template <class F>
+inline int blocks_per_sm_once(KernelOnce &k, F kern, int threads, size_t smem) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    const unsigned long long bit = 1ULL << dev;
+    if (k.occ_set.load(std::memory_order_acquire) & bit) return k.occ[dev];
+    if (raise_smem_once(k, kern, smem) != cudaSuccess) return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, smem) != cudaSuccess) return 0;
+    k.occ[dev] = nb;
+    k.occ_set.fetch_or(bit, std::memory_order_acq_rel);
+    return nb;
+}
 
 
 __host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }

@@ -10,7 +10,8 @@ cudaError_t launch_one_32(const PassParams &p, long long grid, cudaStream_t s) {
     const size_t smem = static_cast<size_t>(kWarps) * kL * (N + 4) * sizeof(float);
     auto kern = sos_dccr_kernel<K, N, NORM, kWarps, LBM>;
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        static KernelOnce once;
+        cudaError_t e = raise_smem_once(once, kern, smem);
         if (e != cudaSuccess) return e;
     }
     kern<<<static_cast<unsigned>(grid), kWarps * 32, smem, s>>>(p);

@@ -127,8 +127,6 @@ constexpr int kLaneW = 7;  // compute warps per block, one group each; a tile is
 // normalized; carried state = zscale * true state).
 struct LaneSec {
     float4 c;      // b1, b2, -a1, -a2
-    float4 g;      // direct-form-II history (u[m], u[m-1]) -> transposed direct-form-II state after
-                   // sample m: z1 = g.x u[m] + g.y u[m-1], z2 = g.z u[m] + g.w u[m-1]
     float4 tn[5];  // (T^N)^(2^r), r = 0..4, row-major 2x2, T the section's one-sample transition
     float b0, zscale, zscale_inv, pad;
 };

@@ -1,18 +1,20 @@
 // Persistent single-signal kernel: PH factorization of every lane's block (Sec. II-C) with lanes
-// of N = 64 samples (32 as an option, two blocks per SM), a skewed direct-form-II particular pass
-// and a column-wise correction, sm_103a.
+// of N = 64 samples (32 as an option, two blocks per SM), a skewed particular pass in
+// direct-form-I order and a column-wise correction, sm_103a.
 //
 // A tile is W = kLaneW consecutive groups of C = 32 N samples; compute warp w of a thread block
 // filters group w of the tile, lane l the samples l N .. l N + N - 1.  Per tile:
 //   1. particular solution: every lane runs its N samples through the K sections from zero state.
 //      The sections run skewed: at step i section s takes sample i - s, its input being section
 //      s - 1's output of step i - 1, so the K section updates of one step are independent and
-//      keep the FMA pipe busy without any wait on the previous section.  Each section is a direct
-//      form II recurrence (u = x - a1 u[-1] - a2 u[-2], y = b0 u + b1 u[-1] + b2 u[-2]): four FMAs
-//      per sample when b0 = 1.  Zero state is the same in every realisation, so the form only
-//      matters for the lane's terminal state, which is converted to transposed direct form II
-//      once per lane.  The samples stay in the lane's row of shared memory and are overwritten in
-//      place by the particular output.
+//      keep the FMA pipe busy without any wait on the previous section.  Each section's poles act
+//      on its numerator-filtered input, and the section then applies the next section's numerator
+//      to its own output history (direct form I across the cascade): four FMAs per sample when
+//      b0 = 1, with float32 rounding at the level of a sequential transposed-direct-form-II
+//      cascade.  Zero state is the same in every realisation; the lane's terminal state is formed
+//      in transposed direct form II from each section's last two inputs and outputs.  The samples
+//      stay in the lane's row of shared memory and are overwritten in place by the particular
+//      output.
 //   2. lane scan (Sec. II-C's recursive doubling over the 32 lanes) on the whole cascade state,
 //      section by section: M_N is block lower-triangular, so section k's words are scanned with its
 //      own (T^N)^(2^r) once the lower sections' lane states are folded in through M_N's coupling
@@ -78,7 +80,6 @@ struct ParamSecs {
     const LaneParams<K> &p;
     __device__ __forceinline__ float4 c(int s) const { return p.sec[s].c; }
     __device__ __forceinline__ float b0(int s) const { return p.sec[s].b0; }
-    __device__ __forceinline__ float4 g(int s) const { return p.sec[s].g; }
     __device__ __forceinline__ float4 tn(int s, int r) const { return p.sec[s].tn[r]; }
     __device__ __forceinline__ float4 mx(int i) const { return p.MX[i]; }
 };
@@ -98,23 +99,9 @@ struct RegSecs {
     }
     __device__ __forceinline__ float4 c(int s) const { return cc[s]; }
     __device__ __forceinline__ float b0(int s) const { return bb[s]; }
-    __device__ __forceinline__ float4 g(int s) const { return __ldg(&sec[s].g); }
     __device__ __forceinline__ float4 tn(int s, int r) const { return __ldg(&sec[s].tn[r]); }
     __device__ __forceinline__ float4 mx(int i) const { return __ldg(MX + i); }
 };
-
-// One step of a section in direct form II: u = x - a1 u[-1] - a2 u[-2], output b0 u + b1 u[-1] +
-// b2 u[-2] (the history is updated in place); c = (b1, b2, -a1, -a2).  The a2 term is taken first,
-// so only one FMA follows the arrival of u[-1] on the recurrence.
-template <bool NORM>
-__device__ __forceinline__ float df2_step(const float4 c, float b0, float &u1, float &u2, float x) {
-    const float t = fmaf(c.w, u2, x);
-    const float u = fmaf(c.z, u1, t);
-    const float w = fmaf(c.x, u1, fmaf(c.y, u2, NORM ? u : b0 * u));
-    u2 = u1;
-    u1 = u;
-    return w;
-}
 
 template <bool B>
 struct CapTag {
@@ -124,48 +111,80 @@ struct CapTag {
 // Particular solution of the lane's row (N samples, in place) through all K sections from zero
 // state, sections skewed by one sample each; t receives the terminal state (transposed direct form
 // II).  With CAPTURE, the lane with cap_lane set writes its state after sample m_last to cap.
+//
+// The cascade runs in direct-form-I order: section s's poles act on F_s, its input already passed
+// through its own numerator (y_s = F_s - a1 y_s[-1] - a2 y_s[-2]), and section s then applies
+// section s + 1's numerator to its own output history (F_{s+1} = b0' y_s + b1' y_s[-1] +
+// b2' y_s[-2]), which is what it hands on.  Per sample and section that is 4 FMAs when b0 = 1, and
+// every intermediate value is a numerator-filtered signal or a section output: no internal signal
+// is amplified by the poles before the zeros act, as the direct-form-II state 1/A(z) x is, so the
+// float32 rounding stays at the level of a sequential transposed-direct-form-II cascade also for
+// sections with poles near the unit circle.  The recurrence waits on one FMA per sample (the
+// y[-2] term and F enter first).
 template <int K, int N, bool NORM, bool CAPTURE, class Secs>
 __device__ __forceinline__ void lane_particular(const Secs &cs, float *row, float gain, float (&t)[2 * K],
                                                 int m_last, bool cap_lane, float *cap) {
     constexpr int D = K - 1;             // skew of the last section
     constexpr int R0 = (4 - (D & 3)) & 3;  // a step group's first output sits R0 samples into its block
-    float u1[K], u2[K], pipe[K];
+    float y1[K], y2[K], pipe[K];  // section outputs y_s[-1], y_s[-2]; pipe[s] = F_{s+1} of the last step
 #pragma unroll
-    for (int s = 0; s < K; ++s) u1[s] = u2[s] = pipe[s] = 0.f;
-    float cu1[K], cu2[K];  // captured history (CAPTURE only)
+    for (int s = 0; s < K; ++s) y1[s] = y2[s] = pipe[s] = 0.f;
+    float x1 = 0.f, x2 = 0.f;  // the last two (gained) input samples
+    float cz1[K], cz2[K];      // captured state (CAPTURE only)
 #pragma unroll
-    for (int s = 0; s < K; ++s) cu1[s] = cu2[s] = 0.f;
+    for (int s = 0; s < K; ++s) cz1[s] = cz2[s] = 0.f;
     const int m_cap = (CAPTURE && cap_lane) ? m_last : -(1 << 20);
     float carry[R0 > 0 ? R0 : 1];
 #pragma unroll
     for (int r = 0; r < (R0 > 0 ? R0 : 1); ++r) carry[r] = 0.f;
 
-    float4 xn = *reinterpret_cast<const float4 *>(row);
-    // steps i0 .. i0 + 3; with CAP the lane records each section's history after sample m_cap
-    auto step_group = [&](int i0, auto cap_tag) {
+    // section s at sample m with input F (section s's numerator already applied); xin1, xin2 are the
+    // section's last two inputs (for the captured state); returns the section's output and leaves
+    // F_{s+1} in pipe[s]
+    auto section = [&](int s, float F, float xin1, float xin2, bool hit, auto cap_tag) -> float {
         constexpr bool CAP = decltype(cap_tag)::value;
+        const float4 c = cs.c(s);  // b1, b2, -a1, -a2
+        const float y = fmaf(c.z, y1[s], fmaf(c.w, y2[s], F));
+        if constexpr (CAP) {
+            // transposed direct form II state after this sample: z1 = b1 x + b2 x[-1] - a1 y - a2 y[-1],
+            // z2 = b2 x - a2 y
+            const float z1 = fmaf(c.x, xin1, fmaf(c.y, xin2, fmaf(c.z, y, c.w * y1[s])));
+            const float z2 = fmaf(c.y, xin1, c.w * y);
+            cz1[s] = hit ? z1 : cz1[s];
+            cz2[s] = hit ? z2 : cz2[s];
+        }
+        if (s + 1 < K) {
+            const float4 n = cs.c(s + 1 < K ? s + 1 : s);
+            pipe[s] = fmaf(n.x, y1[s], fmaf(n.y, y2[s], NORM ? y : cs.b0(s + 1 < K ? s + 1 : s) * y));
+        }
+        y2[s] = y1[s];
+        y1[s] = y;
+        return y;
+    };
+
+    float4 xn = *reinterpret_cast<const float4 *>(row);
+    // steps i0 .. i0 + 3; with CAP the lane records each section's state after sample m_cap
+    auto step_group = [&](int i0, auto cap_tag) {
         const float4 xv = xn;
         if (i0 + 4 < N) xn = *reinterpret_cast<const float4 *>(row + i0 + 4);
         const float xs[4] = {xv.x, xv.y, xv.z, xv.w};
         float out[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            // step i0 + j: from the last section down, so that pipe[s - 1] is read before it is
-            // overwritten with this step's output of section s - 1
+            // step i0 + j: from the last section down, so that pipe[s - 1] and section s - 1's output
+            // history are read before section s - 1 updates them in this step
 #pragma unroll
-            for (int s = K - 1; s >= 0; --s) {
-                const float xin = (s == 0) ? (NORM ? xs[j] * gain : xs[j]) : pipe[s - 1];
-                const float w = df2_step<NORM>(cs.c(s), cs.b0(s), u1[s], u2[s], xin);
-                if (s == K - 1)
-                    out[j] = w;
-                else
-                    pipe[s] = w;
-                if constexpr (CAP) {
-                    const bool hit = (i0 + j - s) == m_cap;
-                    cu1[s] = hit ? u1[s] : cu1[s];
-                    cu2[s] = hit ? u2[s] : cu2[s];
-                }
+            for (int s = K - 1; s >= 1; --s) {
+                const float w = section(s, pipe[s - 1], y1[s - 1], y2[s - 1], (i0 + j - s) == m_cap, cap_tag);
+                if (s == K - 1) out[j] = w;
             }
+            const float gx = NORM ? xs[j] * gain : xs[j];
+            const float4 c0 = cs.c(0);
+            const float F0 = fmaf(c0.x, x1, fmaf(c0.y, x2, NORM ? gx : cs.b0(0) * gx));
+            const float w0 = section(0, F0, gx, x1, (i0 + j) == m_cap, cap_tag);
+            if (K == 1) out[j] = w0;
+            x2 = x1;
+            x1 = gx;
         }
         // out[j] is sample i0 + j - D; the aligned block at b = i0 - D - R0 is complete
         const int b = i0 - D - R0;
@@ -203,16 +222,8 @@ __device__ __forceinline__ void lane_particular(const Secs &cs, float *row, floa
         for (int e = 0; e < D; ++e) {
 #pragma unroll
             for (int s = K - 1; s >= e + 1; --s) {
-                const float w = df2_step<NORM>(cs.c(s), cs.b0(s), u1[s], u2[s], pipe[s - 1]);
-                if (s == K - 1)
-                    tail[R0 + e] = w;
-                else
-                    pipe[s] = w;
-                if constexpr (CAPTURE) {
-                    const bool hit = (N + e - s) == m_cap;
-                    cu1[s] = hit ? u1[s] : cu1[s];
-                    cu2[s] = hit ? u2[s] : cu2[s];
-                }
+                const float w = section(s, pipe[s - 1], y1[s - 1], y2[s - 1], (N + e - s) == m_cap, CapTag<CAPTURE>{});
+                if (s == K - 1) tail[R0 + e] = w;
             }
         }
 #pragma unroll
@@ -222,20 +233,21 @@ __device__ __forceinline__ void lane_particular(const Secs &cs, float *row, floa
     } else {
         (void)carry;
     }
-    // transposed direct form II state from the last two u values of every section
+    // transposed direct form II state after the lane's last sample, from the last two inputs and
+    // outputs of every section
 #pragma unroll
     for (int s = 0; s < K; ++s) {
-        const float4 g = cs.g(s);
-        t[2 * s] = fmaf(g.x, u1[s], g.y * u2[s]);
-        t[2 * s + 1] = fmaf(g.z, u1[s], g.w * u2[s]);
+        const float4 c = cs.c(s);
+        const float xi1 = s == 0 ? x1 : y1[s > 0 ? s - 1 : 0], xi2 = s == 0 ? x2 : y2[s > 0 ? s - 1 : 0];
+        t[2 * s] = fmaf(c.x, xi1, fmaf(c.y, xi2, fmaf(c.z, y1[s], c.w * y2[s])));
+        t[2 * s + 1] = fmaf(c.y, xi1, c.w * y1[s]);
     }
     if constexpr (CAPTURE) {
         if (cap_lane) {
 #pragma unroll
             for (int s = 0; s < K; ++s) {
-                const float4 g = cs.g(s);
-                cap[2 * s] = fmaf(g.x, cu1[s], g.y * cu2[s]);
-                cap[2 * s + 1] = fmaf(g.z, cu1[s], g.w * cu2[s]);
+                cap[2 * s] = cz1[s];
+                cap[2 * s + 1] = cz2[s];
             }
         }
     }

@@ -6,10 +6,13 @@ namespace sosk {
 
 namespace {
 template <int K, bool NORM>
+KernelOnce g_once;
+
+template <int K, bool NORM>
 cudaError_t launch_one(const LaneParams<K> &p, long long grid, cudaStream_t s) {
     auto kern = sos_lane_kernel<K, 32, NORM>;
     constexpr size_t smem = lane_smem_bytes<K, 32>();
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    cudaError_t e = raise_smem_once(g_once<K, NORM>, kern, smem);
     if (e != cudaSuccess) return e;
     kern<<<static_cast<unsigned>(grid), (kLaneW + 1) * 32, smem, s>>>(p);
     return cudaGetLastError();
@@ -17,13 +20,7 @@ cudaError_t launch_one(const LaneParams<K> &p, long long grid, cudaStream_t s) {
 
 template <int K, bool NORM>
 int blocks_one() {
-    auto kern = sos_lane_kernel<K, 32, NORM>;
-    constexpr size_t smem = lane_smem_bytes<K, 32>();
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
-        return 0;
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, (kLaneW + 1) * 32, smem) != cudaSuccess) return 0;
-    return nb;
+    return blocks_per_sm_once(g_once<K, NORM>, sos_lane_kernel<K, 32, NORM>, (kLaneW + 1) * 32, lane_smem_bytes<K, 32>());
 }
 }  // namespace
 

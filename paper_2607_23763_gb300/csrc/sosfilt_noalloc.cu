@@ -4,7 +4,8 @@
 // thread (an audio or radio receive loop) must not call cudaMalloc/cudaFree, which can block
 // and synchronize the device, and some applications hand out all device memory at start-up.
 // Such callers create the filter object once during set-up and then filter with this entry
-// point, which calls no cudaMalloc, cudaFree or other allocating routine.
+// point, which allocates nothing: no cudaMalloc, cudaFree or other allocating CUDA routine, and no
+// host heap allocation.
 #include <cstdint>
 #include <mutex>
 
@@ -34,15 +35,11 @@ std::mutex g_mu;
 unsigned long long *g_ptr[64] = {nullptr};  // device address of g_noalloc_scratch, per device
 unsigned g_epoch[64] = {0};                 // last epoch used on that device (tags are never 0)
 
-// Tag of the next pass on device dev (called with g_mu held).
-unsigned next_epoch_dev(int dev, cudaStream_t s) {
-    unsigned e = (g_epoch[dev] + 1) & 0x3fffffffu;
-    if (e == 0) {  // wrapped: clear old tags so that no stale descriptor can match
-        cudaMemsetAsync(g_ptr[dev] + 32, 0, kDescWords * sizeof(unsigned long long), s);
-        e = 1;
-    }
-    g_epoch[dev] = e;
-    return e;
+// Tag of the next pass on device dev (called with g_mu held): 1 .. 2^30 - 1, never 0.  Every pass
+// clears the descriptors it uses before its launch, so a tag only has to differ from 0.
+unsigned next_epoch_dev(int dev, cudaStream_t) {
+    g_epoch[dev] = g_epoch[dev] % 0x3fffffffu + 1;
+    return g_epoch[dev];
 }
 
 }  // namespace

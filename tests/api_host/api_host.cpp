@@ -13,6 +13,7 @@
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <new>
 #include <set>
 #include <vector>
 
@@ -39,8 +40,14 @@ float g_cost[5][3][9] = {};    // simulated time of a launch, ms, by kind, N (32
 
 int n_index(int N) { return N == 32 ? 0 : N == 64 ? 1 : 2; }
 
+bool g_recording = false;  // the recorder's own allocations are not the library's
+
 template <class P>
 void record(int kind, int K, int N, bool norm, long long grid, const P &p) {
+    g_recording = true;
+    struct Done {
+        ~Done() { g_recording = false; }
+    } done;
     Launch l{kind, K, N, norm ? 1 : 0, grid, {}};
     if (!g_light) {
         l.params.resize(sizeof(P));
@@ -68,11 +75,15 @@ cudaError_t cudaDeviceGetAttribute(int *v, cudaDeviceAttr, int) {
     *v = 4;  // a small "GPU": four SMs
     return cudaSuccess;
 }
+// calls of the allocating runtime routines (cudaMalloc, cudaMallocHost, cudaFree, cudaFreeHost)
+long long g_runtime_allocs = 0;
 cudaError_t cudaMalloc(void **p, size_t bytes) {
+    ++g_runtime_allocs;
     *p = std::calloc(1, bytes ? bytes : 1);
     return *p ? cudaSuccess : cudaErrorMemoryAllocation;
 }
 cudaError_t cudaFree(void *p) {
+    ++g_runtime_allocs;
     std::free(p);
     return cudaSuccess;
 }
@@ -183,20 +194,41 @@ HOST_ALL(1) HOST_ALL(2) HOST_ALL(3) HOST_ALL(4) HOST_ALL(5) HOST_ALL(6) HOST_ALL
 namespace {
 unsigned g_epoch = 0;
 unsigned scratch_epoch(int, cudaStream_t) { return ++g_epoch; }
+// global operator new calls (the harness is linked with -Bsymbolic, so the library's own calls
+// bind here)
+long long g_heap_allocs = 0;
 }  // namespace
+
+void *operator new(size_t bytes) {
+    if (!g_recording) ++g_heap_allocs;
+    void *p = std::malloc(bytes ? bytes : 1);
+    if (!p) throw std::bad_alloc();
+    return p;
+}
+void operator delete(void *p) noexcept { std::free(p); }
+void operator delete(void *p, size_t) noexcept { std::free(p); }
 
 // Test hooks.
 extern "C" {
-// a run with caller-provided lookback scratch of desc_words words (the path of
-// sos_filter_run_noalloc); writes the scratch addresses used to where[0..1]
+// a run with caller-provided lookback scratch of desc_words words, filled with a non-zero pattern
+// beforehand (the path of sos_filter_run_noalloc).  where[0..1]: the scratch addresses used;
+// where[2]: the ticket counter afterwards; where[3], where[4]: calls of allocating runtime routines
+// and of operator new during the run; where[5]: the words of the scratch that are still non-zero
+// afterwards (descriptors the run neither cleared nor wrote).
 int host_run_scratch(sos_filter *f, const float *x, float *y, long long n, const float *zi, float *zf,
                      long long desc_words, unsigned long long *where) {
-    std::vector<unsigned long long> desc(static_cast<size_t>(desc_words) + 1), ticket(1, 12345);
+    std::vector<unsigned long long> desc(static_cast<size_t>(desc_words) + 1, 0xabababababababULL), ticket(1, 12345);
     sosk::Scratch sc{desc.data(), static_cast<size_t>(desc_words), ticket.data()};
     where[0] = reinterpret_cast<unsigned long long>(desc.data());
     where[1] = reinterpret_cast<unsigned long long>(ticket.data());
+    const long long rt0 = g_runtime_allocs, heap0 = g_heap_allocs;
     const int rc = sosk::run_lane_scratch(f, x, y, n, zi, zf, nullptr, sc, scratch_epoch);
+    where[3] = static_cast<unsigned long long>(g_runtime_allocs - rt0);
+    where[4] = static_cast<unsigned long long>(g_heap_allocs - heap0);
     where[2] = ticket[0];
+    unsigned long long left = 0;
+    for (size_t i = 0; i < static_cast<size_t>(desc_words); ++i) left += desc[i] != 0;
+    where[5] = left;
     return rc;
 }
 void host_reset(void) { g_launches.clear(); }

@@ -163,43 +163,66 @@ def ph_filter(sos, x, zi=None, N=32, L=32, W=8, anchored=False):
     return y, zf
 
 
-def particular_skewed_df2(coef, xb, m_cap=None):
-    """The skewed-pass kernel's particular solution of every lane block (rows of xb): direct form II
-    sections (u = x - a1 u[-1] - a2 u[-2], w = b0 u + b1 u[-1] + b2 u[-2]) run skewed, section k
-    taking sample i - k at step i with section k-1's output of step i-1 as input, every step visiting
-    the sections from the last down.  Returns the outputs, the terminal transposed-direct-form-II
-    states converted from the last two u of each section, and (with m_cap) the converted state after
-    sample m_cap."""
+def particular_skewed_df1(coef, xb, m_cap=None, dtype=np.float64):
+    """The skewed-pass kernel's particular solution of every lane block (rows of xb), in the
+    kernel's direct-form-I order: section k runs its poles on F_k (its input already through its
+    own numerator), y = F_k - a1 y[-1] - a2 y[-2], and then applies section k+1's numerator to its
+    output history, F_{k+1} = b0' y + b1' y[-1] + b2' y[-2]; section 0's F is the numerator on the
+    input.  Sections run skewed, section k taking sample i - k at step i with the F that section
+    k-1 formed at step i-1, every step visiting the sections from the last down.  Returns the
+    outputs, the terminal transposed-direct-form-II states formed from each section's last two
+    inputs and outputs, and (with m_cap) the state after sample m_cap.
+
+    With dtype=np.float32 every multiply-add is rounded to float32 once (a fused multiply-add: the
+    float32 product is exact in float64), as on the GPU."""
     K = len(coef)
     nl, N = xb.shape
-    x = xb.astype(np.float64)
-    u1 = np.zeros((K, nl))
-    u2 = np.zeros((K, nl))
-    pipe = np.zeros((K, nl))
-    cap = np.zeros((K, 2, nl))
-    out = np.zeros((nl, N))
+    f = dtype
+
+    def fma(a, b, c):
+        return (np.float64(a) * np.asarray(b, np.float64) + np.asarray(c, np.float64)).astype(f)
+
+    x = xb.astype(f)
+    y1 = np.zeros((K, nl), f)
+    y2 = np.zeros((K, nl), f)
+    pipe = np.zeros((K, nl), f)
+    x1 = np.zeros(nl, f)
+    x2 = np.zeros(nl, f)
+    cap = np.zeros((K, 2, nl), f)
+    out = np.zeros((nl, N), f)
+    cf = [tuple(f(v) for v in c) for c in coef]
     for i in range(N + K - 1):
         for k in range(K - 1, -1, -1):
             m = i - k
             if m < 0 or m >= N:
                 continue
-            b0, b1, b2, a1, a2 = coef[k]
-            xin = x[:, i] if k == 0 else pipe[k - 1]
-            u = xin - a2 * u2[k] - a1 * u1[k]
-            w = b0 * u + b1 * u1[k] + b2 * u2[k]
-            u2[k], u1[k] = u1[k], u
-            if k == K - 1:
-                out[:, m] = w
+            b0, b1, b2, a1, a2 = cf[k]
+            if k == 0:
+                xin1, xin2 = x[:, i], x1
+                F = fma(b1, x1, fma(b2, x2, (np.float64(b0) * x[:, i]).astype(f)))
             else:
-                pipe[k] = w
+                xin1, xin2 = y1[k - 1], y2[k - 1]
+                F = pipe[k - 1]
+            y = fma(-a1, y1[k], fma(-a2, y2[k], F))
             if m_cap is not None and m == m_cap:
-                cap[k, 0], cap[k, 1] = u1[k], u2[k]
-
-    def convert(ua, ub):
-        z = np.zeros((nl, 2 * K))
-        for k, (b0, b1, b2, a1, a2) in enumerate(coef):
-            z[:, 2 * k] = (b1 - b0 * a1) * ua[k] + (b2 - b0 * a2) * ub[k]
-            z[:, 2 * k + 1] = (b2 - b0 * a2) * ua[k] + (a1 * b2 - a2 * b1) * ub[k]
-        return z
-
-    return out, convert(u1, u2), (convert(cap[:, 0], cap[:, 1]) if m_cap is not None else None)
+                cap[k, 0] = fma(b1, xin1, fma(b2, xin2, fma(-a1, y, (np.float64(-a2) * y1[k]).astype(f))))
+                cap[k, 1] = fma(b2, xin1, (np.float64(-a2) * y).astype(f))
+            if k + 1 < K:
+                n0, n1, n2 = cf[k + 1][:3]
+                pipe[k] = fma(n1, y1[k], fma(n2, y2[k], (np.float64(n0) * y).astype(f)))
+            else:
+                out[:, m] = y
+            y2[k], y1[k] = y1[k], y
+            if k == 0:
+                x2, x1 = x1, x[:, i]
+    z = np.zeros((nl, 2 * K), f)
+    for k, (b0, b1, b2, a1, a2) in enumerate(cf):
+        xi1, xi2 = (x1, x2) if k == 0 else (y1[k - 1], y2[k - 1])
+        z[:, 2 * k] = fma(b1, xi1, fma(b2, xi2, fma(-a1, y1[k], (np.float64(-a2) * y2[k]).astype(f))))
+        z[:, 2 * k + 1] = fma(b2, xi1, (np.float64(-a2) * y1[k]).astype(f))
+    capz = None
+    if m_cap is not None:
+        capz = np.zeros((nl, 2 * K), f)
+        capz[:, 0::2] = cap[:, 0].T
+        capz[:, 1::2] = cap[:, 1].T
+    return out, z, capz

@@ -5,7 +5,7 @@ The stand-in launchers record each launch and, in place of the filter, write twi
 output and add the samples processed to word 0 of the state.  That is enough to check, without a
 GPU:
 
-* the host precompute of the PH kernel: section constants, coupling blocks,
+* the host precompute of the PH kernel (the float64 -> float32 tables): section constants, coupling blocks,
   lane and tile transition powers, the output basis and the input gain, against a float64
   derivation here from the transposed-direct-form-II recurrence (Eq. 1);
 * which kernel a tuning selects, and the passes of a cascade of more than eight sections;
@@ -41,7 +41,8 @@ def lib():
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
     if not os.path.exists(_LIB) or any(os.path.getmtime(d) > os.path.getmtime(_LIB) for d in _DEPS):
         tmp = f"{_LIB}.{os.getpid()}.tmp"  # parallel test workers build side by side
-        subprocess.run(["g++", "-std=c++17", "-O1", "-fPIC", "-shared", "-pthread",
+        # -Bsymbolic: the library's own operator new calls bind to the harness's counting one
+        subprocess.run(["g++", "-std=c++17", "-O1", "-fPIC", "-shared", "-pthread", "-Wl,-Bsymbolic",
                         "-I", os.path.join(_HERE, "api_host"), "-I", os.path.join(_ROOT, "include"), "-I", _CSRC,
                         "-o", tmp, *_SRCS], check=True)
         os.replace(tmp, _LIB)
@@ -190,17 +191,16 @@ def test_ph_tables_match_a_float64_derivation(lib, name):
     AC = np.linalg.matrix_power(MN, 32)
     AT = np.linalg.matrix_power(AC, W)
     S = 2 * K
-    # section constants (LaneSec: c, g, tn[5] as float4, then b0, zscale, zscale_inv, pad)
-    sec = _at(raw, o["sec"], np.float32, 32 * K).reshape(K, 32)
+    # section constants (LaneSec: c, tn[5] as float4, then b0, zscale, zscale_inv, pad)
+    sec = _at(raw, o["sec"], np.float32, 28 * K).reshape(K, 28)
     for j, (b0, b1, b2, a1, a2) in enumerate(c):
         _close(sec[j, 0:4], [b1, b2, -a1, -a2], f"{name} c[{j}]")
-        _close(sec[j, 4:8], [b1 - b0 * a1, b2 - b0 * a2, b2 - b0 * a2, a1 * b2 - a2 * b1], f"{name} g[{j}]")
         P = MN[2 * j:2 * j + 2, 2 * j:2 * j + 2]
         for r in range(5):
-            _close(sec[j, 8 + 4 * r:12 + 4 * r], P.reshape(-1), f"{name} tn[{j}][{r}]")
+            _close(sec[j, 4 + 4 * r:8 + 4 * r], P.reshape(-1), f"{name} tn[{j}][{r}]")
             P = P @ P
         zscale = np.prod(sos[j + 1:, 0]) if norm else 1.0
-        _close(sec[j, 28:30], [b0, zscale], f"{name} b0, zscale[{j}]")
+        _close(sec[j, 24:26], [b0, zscale], f"{name} b0, zscale[{j}]")
     # coupling blocks of M_N
     if K > 1:
         MX = _at(raw, o["MX"], np.float32, 2 * K * (K - 1)).reshape(-1, 4)
@@ -620,8 +620,10 @@ def test_batch_plan_launches_reuse_the_uploaded_plan(lib):
 
 def test_run_with_caller_scratch_allocates_nothing_and_checks_its_size(lib):
     """The path of sos_filter_run_noalloc: lookback descriptors and ticket counter in caller memory
-    (the counter reset to zero for the launch, ticket base 0), a fresh epoch per pass, and
-    SOS_EBUDGET when the descriptors would not fit."""
+    (the counter reset to zero for the launch, ticket base 0, the pass's descriptors cleared), a
+    fresh epoch per pass, SOS_EBUDGET when the descriptors would not fit, and no call of an
+    allocating runtime routine (cudaMalloc, cudaMallocHost, cudaFree, cudaFreeHost) nor of
+    operator new during the run, with and without a final state."""
     lib.host_run_scratch.argtypes = [ctypes.c_void_p] * 6 + [ctypes.c_longlong, ctypes.c_void_p]
     sos = designs.random_sections(workloads.uniform_f64(21, 33, stream=1).reshape(11, 3))  # two passes
     f = _create(lib, sos)
@@ -630,11 +632,18 @@ def test_run_with_caller_scratch_allocates_nothing_and_checks_its_size(lib):
     y = np.full_like(x, np.nan)
     n_tiles = -(-(-(-n // C64)) // W)
     need = n_tiles * 2 * 2 * 8
-    where = (ctypes.c_ulonglong * 3)()
+    where = (ctypes.c_ulonglong * 6)()
     lib.host_reset()
     assert lib.host_run_scratch(f, x.ctypes.data, y.ctypes.data, n, None, None, need - 1, where) == -6
     assert lib.host_launches() == 0
+    # a run with a final state first: the tail transition for any length is prepared at creation
+    zf = np.zeros((11, 2), np.float32)
+    assert lib.host_run_scratch(f, x.ctypes.data, y.ctypes.data, n - 1, None, zf.ctypes.data, need, where) == 0
+    assert (where[3], where[4], where[5]) == (0, 0, 0)
+    lib.host_reset()
     assert lib.host_run_scratch(f, x.ctypes.data, y.ctypes.data, n, None, None, need, where) == 0
+    assert where[3] == 0 and where[4] == 0  # no allocation of any kind
+    assert where[5] == 0  # every descriptor word of the scratch was cleared before use
     np.testing.assert_array_equal(y, 4 * x)
     ls = _launches(lib)
     assert [l["K"] for l in ls] == [8, 3]

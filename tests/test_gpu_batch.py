@@ -73,31 +73,47 @@ def test_batch_mixed_orders_lengths_states(dev):
     torch.cuda.synchronize()
     assert batch_sync_status(0) == 0
     for (sos, x, zi), y, zf in zip(items, ys, zfs):
-        y_ref, zf_ref = oracle.sosfilt(sos, x, zi=zi.astype(np.float32).astype(np.float64), return_state=True)
-        tol = bound(sos, x, y_ref, random_mix=True)
+        zi32 = zi.astype(np.float32)
+        y_ref, zf_ref = oracle.sosfilt(sos, x, zi=zi32.astype(np.float64), return_state=True)
+        tol = bound(sos, x, y_ref, random_mix=True, zi=zi32)
         err = _rel(y.cpu().numpy(), y_ref)
+        zerr = _zerr(zf.cpu().numpy(), zf_ref)
+        print(f"K={sos.shape[0]} n={len(x)}: output error {err:.3e}, final-state error {zerr:.3e}, bound {tol:.3e}")
         assert err < tol, (sos.shape[0], len(x), err, tol)
-        assert _zerr(zf.cpu().numpy(), zf_ref) < 10 * tol, (sos.shape[0], len(x))
+        assert zerr < tol, (sos.shape[0], len(x), zerr, tol)
     for f in fs:
         f.close()
 
 
 def test_batch_alone_equals_mix(dev):
-    """Each signal filtered alone (sos_filter_run) and inside a batch gives the same result."""
+    """Each signal filtered alone in a batch of its own and inside the mix gives the same output and
+    final state bit for bit: the batch kernel composes every tile's incoming state from anchors
+    counted from the signal's own first tile, so nothing depends on the other signals or on where
+    the signal's tiles sit in the queue.  The single-signal kernel (sos_filter_run) agrees with
+    both within the bound."""
     from paper_2607_23763_gb300 import SosFilter, run_batch
     items = _mix(24, 5)
+    items = [it for it in items if it[0].shape[0] <= 8]
     fs = [SosFilter(sos) for sos, _, _ in items]
     xs = [torch.from_numpy(x).to(dev) for _, x, _ in items]
-    ys_mix = run_batch(fs, xs)
-    ys_alone = [f.run(x) for f, x in zip(fs, xs)]
+    zis = [torch.from_numpy(zi.astype(np.float32)).to(dev) for _, _, zi in items]
+    zf_mix = [torch.full((sos.shape[0], 2), float("nan"), device=dev) for sos, _, _ in items]
+    ys_mix = run_batch(fs, xs, zis=zis, zfs=zf_mix)
+    ys_alone, zf_alone = [], []
+    for f, x, zi, (sos, _, _) in zip(fs, xs, zis, items):
+        zf = torch.full((sos.shape[0], 2), float("nan"), device=dev)
+        ys_alone.append(run_batch([f], [x], zis=[zi], zfs=[zf])[0])
+        zf_alone.append(zf)
+    ys_single = [f.run(x, zi=zi) for f, x, zi in zip(fs, xs, zis)]
     torch.cuda.synchronize()
-    for (sos, x, _), a, b in zip(items, ys_alone, ys_mix):
-        y_ref = oracle.sosfilt(sos, x)
-        tol = bound(sos, x, y_ref, random_mix=True)
-        assert _rel(a.cpu().numpy(), y_ref) < tol
+    for (sos, x, zi), a, b, za, zb, c in zip(items, ys_alone, ys_mix, zf_alone, zf_mix, ys_single):
+        assert torch.equal(a, b), (sos.shape[0], len(x))
+        assert torch.equal(za, zb), (sos.shape[0], len(x))
+        zi32 = zi.astype(np.float32)
+        y_ref = oracle.sosfilt(sos, x, zi=zi32.astype(np.float64))
+        tol = bound(sos, x, y_ref, random_mix=True, zi=zi32)
         assert _rel(b.cpu().numpy(), y_ref) < tol
-        peak = max(1e-30, float(np.abs(y_ref).max()))
-        assert float((a - b).abs().max()) / peak < 2 * tol
+        assert _rel(c.cpu().numpy(), y_ref) < tol
     for f in fs:
         f.close()
 

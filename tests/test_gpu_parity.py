@@ -2,8 +2,13 @@
 
 Error measure (Sec. IV-F): max|y - y_ref| / max|y_ref| per signal; bound 1e-4 for pole radius
 <= 0.99, 2e-3 beyond (designs.tolerance_for).  The final state is compared with the same
-relative measure against the oracle's final state.
+relative measure, and the same bound, against the oracle's final state.  Random-section cascades
+take the bound of tests/_tol.py: the stated one, widened only to four times the error of a
+sequential float32 cascade where that error itself exceeds it.  Every check prints its error and
+bound.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -49,14 +54,14 @@ def _run_check(sos, x, dev, zi=None, tuning=None, tol=None, in_place=False, offs
     torch.cuda.synchronize()
     assert f.sync_status() == 0
     y_ref, zf_ref = oracle.sosfilt(sos, x, zi=None if zi is None else zi.astype(np.float64), return_state=True)
-    tol = tol or bound(sos, x, y_ref, random_mix=random_mix)
+    tol = tol or bound(sos, x, y_ref, random_mix=random_mix, zi=zi)
     yh = y.cpu().numpy()
     assert np.all(np.isfinite(yh))
     err = _rel(yh, y_ref)
+    zerr = _zerr(zfd.cpu().numpy(), zf_ref) if len(x) else 0.0
+    print(f"K={K} n={len(x)} tuning={tuning}: output error {err:.3e}, final-state error {zerr:.3e}, bound {tol:.3e}")
     assert err < tol, f"output error {err:.3e} >= {tol}"
-    if len(x):
-        zerr = _zerr(zfd.cpu().numpy(), zf_ref)
-        assert zerr < 10 * tol, f"final-state error {zerr:.3e}"
+    assert zerr < tol, f"final-state error {zerr:.3e} >= {tol}"
     f.close()
     return err
 
@@ -105,6 +110,29 @@ def test_every_section_count(dev, K, tuning):
     _run_check(sos, x, dev, zi=zi, tuning=tuning, random_mix=True)
 
 
+def _designed(K):
+    """A designed cascade of K sections: Butterworth low-pass of order 2K (pole radius up to 0.985,
+    bound 1e-4) for even K, the resonator bank of K sections at radius 0.999 (bound 2e-3) for odd K."""
+    if K % 2 == 0 or K == 1:
+        return designs.butter_lowpass(2 * K, 0.05 if K >= 4 else 0.1)
+    return designs.resonator_bank(K)
+
+
+@pytest.mark.parametrize("K", [1, 2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("tuning", SCHEMES, ids=SCHEME_IDS)
+def test_every_section_count_designed_stated_bound(dev, K, tuning):
+    """Butterworth and resonator cascades at every section count, every scheme, a nonzero initial
+    state, several tiles and a ragged tail: the stated bound, no widening."""
+    sos = _designed(K)
+    if tuning.get("solver") == SOLVER_PH:
+        n = 3 * PH_W * 32 * tuning.get("N", 64) + 123
+    else:
+        n = 5 * 32 * tuning.get("N", 32) + 123
+    x = workloads.normal_f32(300 + K, n)
+    zi = np.random.default_rng(30 + K).standard_normal((K, 2)) * 0.1
+    _run_check(sos, x, dev, zi=zi, tuning=tuning, tol=designs.tolerance_for(sos))
+
+
 def test_config1_full_size(dev):
     """Order-2 Butterworth at 0.2 Nyquist, 2^20 samples, seed 0, zero state."""
     sos = designs.butter_lowpass(2, 0.2)
@@ -120,6 +148,10 @@ def test_more_than_eight_sections_two_passes(dev, tuning):
     x = workloads.normal_f32(78, 50000)
     _run_check(sos, x, dev, zi=np.random.default_rng(3).standard_normal((12, 2)) * 0.1, random_mix=True,
                tuning=tuning)
+    # a designed 12-section cascade (Butterworth order 24, pole radius up to 0.98): the stated bound
+    sos = designs.butter_lowpass(24, 0.1)
+    _run_check(sos, x, dev, zi=np.random.default_rng(4).standard_normal((12, 2)) * 0.1, tuning=tuning,
+               tol=designs.tolerance_for(sos))
 
 
 @pytest.mark.parametrize("tuning", KERNELS, ids=KERNEL_IDS)
@@ -175,10 +207,58 @@ def test_stream_push_equals_one_shot(dev):
     zf = f.get_state()
     y_ref, zf_ref = oracle.sosfilt(sos, x, zi=zi.astype(np.float64), return_state=True)
     assert _rel(y, y_ref) < 1e-4
-    assert _zerr(zf, zf_ref) < 1e-3
+    assert _zerr(zf, zf_ref) < 1e-4
     f.set_state(np.zeros((8, 2)))
     assert np.all(f.get_state() == 0)
     f.close()
+
+
+@pytest.mark.parametrize("tuning", KERNELS, ids=KERNEL_IDS)
+def test_checkpoint_export_import_continue(dev, tuning):
+    """Checkpoint round trip: filter the first chunks of a signal by stream_push, export the
+    resident [K][2] state (to the host, and device to device), import it into fresh filter objects
+    (at creation, and by set_state), continue there, and compare the concatenated output and the
+    final state with one oracle run over the whole signal."""
+    from paper_2607_23763_gb300 import SosFilter
+    sos = designs.butter_lowpass(16, 0.05)
+    K = sos.shape[0]
+    x = workloads.normal_f32(23, 120001)
+    zi = (np.random.default_rng(6).standard_normal((K, 2)) * 0.01).astype(np.float32)
+    xd = torch.from_numpy(x).to(dev)
+    cut1, cut2 = 50007, 90000
+    f = SosFilter(sos, zi=zi, tuning=tuning)
+    y1 = torch.cat([f.stream_push(xd[a:b].contiguous()) for a, b in [(0, 20000), (20000, cut1)]])
+    z_host = f.get_state()  # host export, after the pushes complete
+    z_dev = torch.empty(K, 2, device=dev)
+    lib = f._lib
+    assert lib.sos_filter_stream_state(f.handle, ctypes.c_void_p(z_dev.data_ptr()), None, 1) == 0
+    torch.cuda.synchronize()
+    assert np.array_equal(z_dev.cpu().numpy(), z_host)
+    f.close()
+    g = SosFilter(sos, zi=z_host, tuning=tuning)  # import at creation
+    y2 = g.stream_push(xd[cut1:cut2].contiguous())
+    z2 = torch.empty(K, 2, device=dev)
+    assert lib.sos_filter_stream_state(g.handle, ctypes.c_void_p(z2.data_ptr()), None, 1) == 0
+    h = SosFilter(sos, tuning=tuning)
+    assert lib.sos_filter_stream_state(h.handle, None, ctypes.c_void_p(z2.data_ptr()), 1) == 0  # device import
+    y3 = h.stream_push(xd[cut2:].contiguous())
+    y = torch.cat([y1, y2, y3]).cpu().numpy()
+    zf = h.get_state()
+    y_ref, zf_ref = oracle.sosfilt(sos, x, zi=zi.astype(np.float64), return_state=True)
+    tol = designs.tolerance_for(sos)
+    err, zerr = _rel(y, y_ref), _zerr(zf, zf_ref)
+    print(f"checkpoint round trip {tuning}: output error {err:.3e}, final-state error {zerr:.3e}, bound {tol}")
+    assert err < tol and zerr < tol
+    # the same split on one filter with no export gives the same output bit for bit: a checkpoint
+    # carries the whole state
+    if tuning.get("solver") == SOLVER_PH:
+        r = SosFilter(sos, zi=zi, tuning=tuning)
+        yr = torch.cat([r.stream_push(xd[a:b].contiguous()) for a, b in
+                        [(0, 20000), (20000, cut1), (cut1, cut2), (cut2, len(x))]]).cpu().numpy()
+        assert np.array_equal(yr, y)
+        r.close()
+    g.close()
+    h.close()
 
 
 def test_run_host_pipelined_chunks(dev):
@@ -192,7 +272,7 @@ def test_run_host_pipelined_chunks(dev):
     y, zf = f.run_host(xt, zi=zi, chunk=65536 + 13, return_state=True)
     y_ref, zf_ref = oracle.sosfilt(sos, x, zi=zi.astype(np.float64), return_state=True)
     assert _rel(y.numpy(), y_ref) < 1e-4
-    assert _zerr(zf, zf_ref) < 1e-3
+    assert _zerr(zf, zf_ref) < 1e-4
     y2 = f.run_host(x)  # numpy, pageable, default chunk
     assert _rel(y2, oracle.sosfilt(sos, x)) < 1e-4
     f.close()
@@ -341,6 +421,6 @@ def test_deterministic_mode_is_bit_reproducible(dev):
     assert all(np.array_equal(z, states[0]) for z in states)
     y_ref, zf_ref = oracle.sosfilt(sos, x, zi=zi.astype(np.float64), return_state=True)
     assert _rel(outs[0], y_ref) < 1e-4
-    assert _zerr(states[0], zf_ref) < 1e-3
+    assert _zerr(states[0], zf_ref) < 1e-4
     with pytest.raises(SosError):
         SosFilter(sos, tuning={"deterministic": 1, "solver": SOLVER_CR})

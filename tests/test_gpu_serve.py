@@ -81,15 +81,18 @@ def test_serving_alone_and_in_mix_match_oracle(dev):
         x = np.concatenate(chunks)
         y_ref, zf_ref = oracle.sosfilt(sos, x, return_state=True)
         tol = bound(sos, x, y_ref, random_mix=True)
-        assert oracle.rel_err(mix_out[i], y_ref) < tol, i
+        err = oracle.rel_err(mix_out[i], y_ref)
         zerr = np.abs(mix_states[i] - zf_ref).max() / max(1e-30, np.abs(zf_ref).max())
-        assert zerr < 10 * tol, i
-        # the same stream served alone
-        alone, _, _, _ = _serve([(sos, chunks)], dev, budget=4 << 20, interleave=False)
-        peak = max(1e-30, float(np.abs(y_ref).max()))
-        assert np.abs(alone[0] - mix_out[i]).max() / peak < 2 * tol, i
-        if i >= 5:
-            break  # five streams re-served alone suffice; all forty are checked against the oracle
+        print(f"stream {i} K={sos.shape[0]} n={len(x)}: output error {err:.3e}, final-state error {zerr:.3e}, "
+              f"bound {tol:.3e}")
+        assert err < tol, i
+        assert zerr < tol, i
+        if i < 6:
+            # the same stream served alone: the same chunks through the same batch kernel, each
+            # continuing from the resident state, so the same output and state bit for bit
+            alone, alone_states, _, _ = _serve([(sos, chunks)], dev, budget=4 << 20, interleave=False)
+            assert np.array_equal(alone[0], mix_out[i]), i
+            assert np.array_equal(alone_states[0], mix_states[i]), i
 
 
 def test_serving_budget_queues_and_rejects(dev):

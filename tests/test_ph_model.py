@@ -46,10 +46,11 @@ def test_coupling_blocks_are_lower_triangular():
 
 @pytest.mark.parametrize("K", [1, 2, 3, 5, 8])
 @pytest.mark.parametrize("unit_b0", [True, False])
-def test_skewed_df2_particular_matches_transposed_form(K, unit_b0):
-    # the skewed-pass kernel's particular solution (direct form II, sections skewed by one sample,
-    # terminal state converted to transposed direct form II) equals the section-by-section
-    # transposed-form particular solution, outputs and states, at the end and after any sample
+def test_skewed_df1_particular_matches_transposed_form(K, unit_b0):
+    # the skewed-pass kernel's particular solution (direct-form-I order across the cascade,
+    # sections skewed by one sample, terminal state formed in transposed direct form II) equals the
+    # section-by-section transposed-form particular solution, outputs and states, at the end and
+    # after any sample
     rows = workloads.uniform_f64(20 + K, 5 * K).reshape(K, 5)
     sos = designs.random_sections(rows[:, :3])
     if not unit_b0:
@@ -60,11 +61,70 @@ def test_skewed_df2_particular_matches_transposed_form(K, unit_b0):
     xb = workloads.normal_f32(40 + K, 6 * 64).reshape(6, 64)
     w_ref, states = PM.particular(coef, xb)
     for m_cap in (0, 1, 17, 63):
-        w, t, cap = PM.particular_skewed_df2(coef, xb, m_cap=m_cap)
+        w, t, cap = PM.particular_skewed_df1(coef, xb, m_cap=m_cap)
         scale = max(1.0, np.abs(states).max())
         assert np.abs(w - w_ref).max() <= 1e-11 * np.abs(w_ref).max()
         assert np.abs(t - states[:, -1]).max() <= 1e-11 * scale
         assert np.abs(cap - states[:, m_cap]).max() <= 1e-11 * scale
+
+
+def _df2_particular_f32(coef, xb):
+    """Float32 direct-form-II particular pass (u = x - a1 u[-1] - a2 u[-2], y = b0 u + b1 u[-1] +
+    b2 u[-2], one rounding per multiply-add): the realisation the direct-form-I order replaced."""
+    f = np.float32
+    w = xb.astype(f)
+    for b0, b1, b2, a1, a2 in coef:
+        u1 = np.zeros(w.shape[0], f)
+        u2 = np.zeros(w.shape[0], f)
+        out = np.empty_like(w)
+        for m in range(w.shape[1]):
+            u = (np.float64(-a1) * u1 + (np.float64(-a2) * u2 + w[:, m])).astype(f)
+            out[:, m] = (np.float64(f(b1)) * u1 + (np.float64(f(b2)) * u2 + np.float64(f(b0)) * u)).astype(f)
+            u2, u1 = u1, u
+        w = out
+    return w
+
+
+def test_particular_pass_float32_error_tracks_sequential_float32():
+    # A high-Q cascade from the batched mix (8 random sections, pole radii up to 0.99, output peak
+    # about 1e-6 of the largest section output).  Every lane block starts from zero state, so the
+    # particular outputs carry the start-up transients of the inner sections; the exact correction
+    # (float64 here) removes them, and what is left is the particular pass's own float32 rounding.
+    # In the kernel's direct-form-I order it stays within 1.5x of a sequential float32 cascade's
+    # error; the direct-form-II order, whose internal signal 1/A(z) x grows near the poles, errs
+    # about 4x more on this input.
+    sos, n, seed = workloads.batched_signal(28)
+    x = workloads.normal_f32(seed, n)
+    y_ref = oracle.sosfilt(sos, x)
+    N = 64
+    nl = -(-n // N)
+    xb = np.zeros(nl * N, np.float32)
+    xb[:n] = x
+    xb = xb.reshape(nl, N)
+    g = float(np.prod(sos[:, 0]))
+    coef = [(1.0, b1 / b0, b2 / b0, a1, a2) for (b0, b1, b2, a1, a2) in sos]
+    # the correction: each lane block's true incoming state (float64 oracle), in the b0-normalized
+    # domain (section k's state scaled by the product of the later sections' b0), through the basis
+    M1, H = PM.tables(coef, N)
+    K = sos.shape[0]
+    zscale = np.repeat([np.prod(sos[k + 1:, 0]) for k in range(K)], 2)
+    zs = np.zeros((nl, 2 * K))
+    z = np.zeros((K, 2))
+    for blk in range(nl):
+        zs[blk] = z.reshape(-1) * zscale
+        _, z = oracle.sosfilt(sos, x[blk * N:(blk + 1) * N], zi=z, return_state=True)
+    corr = zs @ H
+    xg = (xb.astype(np.float64) * np.float32(g)).astype(np.float32)
+    w1, _, _ = PM.particular_skewed_df1(coef, xg, dtype=np.float32)
+    w2 = _df2_particular_f32(coef, xg)
+    e1 = oracle.rel_err((w1 + corr).reshape(-1)[:n], y_ref)
+    e2 = oracle.rel_err((w2 + corr).reshape(-1)[:n], y_ref)
+    from scipy import signal
+    s32 = np.hstack([sos[:, :3], np.ones((sos.shape[0], 1)), sos[:, 3:]]).astype(np.float32)
+    e_seq = oracle.rel_err(signal.sosfilt(s32, x), y_ref)
+    print(f"float32 error: sequential {e_seq:.2e}, direct-form-I order {e1:.2e}, direct form II {e2:.2e}")
+    assert e1 <= 1.5 * e_seq
+    assert e2 >= 2 * e1
 
 
 @pytest.mark.parametrize("n_tiles", [1, 2, 31, 32, 33, 64, 65, 97])
