@@ -1,10 +1,17 @@
 """Benchmark: cascaded biquad filtering throughput (GS/s) on one GB300.
 
-Workload (default): order-16 Butterworth low-pass (8 sections) at 0.05 of Nyquist, one float32
+Workload (headline): order-16 Butterworth low-pass (8 sections) at 0.05 of Nyquist, one float32
 signal of 2^28 N(0,1) samples from seed 1 -- the plain single-signal kernel at full size.
 A step is one pass of the whole hot path over the signal: one sos_filter_run call (all 8
 sections, one kernel launch).  Inputs (1 GiB) and outputs (1 GiB) are both larger than the
 129 MB L2, so no flush is needed between steps.
+
+The same JSON line also carries the other measured targets, each timed with CUDA events on the
+launching stream: the order-2 plateau (2^29 and 2^30 samples), the order-2 workload at 2^20
+samples over a rotating pool of buffers larger than L2, the cyclic-reduction solver at orders 16
+and 2, the batched mix (per call and replayed from a CUDA graph, with its ratio to the plain
+kernel and per-signal accuracy) and the serving mix (capacity, p50/p99 latency at 80 % load and
+the ratio to the plain kernel).  ``--quick`` prints the headline alone.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the float64 CPU oracle instead,
 on a bounded sample of the same workload.
@@ -31,18 +38,22 @@ SEED = 1
 BYTES_PER_SAMPLE = 8  # 4 B read + 4 B written: the algorithmic traffic of the filter (Sec. IV-C, Eq. 28)
 CPU_SAMPLE = 1 << 24  # oracle sample per step of the reference arm
 # DRAM bytes (read + write) of one launch of the timed kernel on the 2^28 workload, per (solver, N):
-# an ncu capture of the same kernel on 2^26 samples scaled by 4 (profiles/, named for the kernel).
-# An entry must be re-captured (or removed) whenever its kernel changes.
-TRAFFIC_BYTES_2P28 = {
-    # profiles/sos_lane_order16_2p26_traffic.md: 268,912,640 B read + 211,674,112 B written at 2^26
-    (2, 64): 4 * (268912640 + 211674112),
-}
-KERNEL_NAMES = {
-    (2, 64): "sos_lane_kernel (PH factorization, 8 sections, N = 64 samples per lane, 7 groups per block)",
-    (2, 32): "sos_lane_kernel (PH factorization, 8 sections, N = 32 samples per lane, 7 groups per block)",
-    (1, 32): "sos_cascade_kernel (cyclic reduction, 8 sections, N = 32 samples per lane, 8 groups per block)",
-    (1, 64): "sos_cascade_kernel (cyclic reduction, 8 sections, N = 64 samples per lane, 4 groups per block)",
-}
+# an ncu capture of the same kernel on 2^26 samples scaled by 4.  An entry must be re-captured (or
+# removed) whenever its kernel changes.
+TRAFFIC_BYTES_2P28 = {}
+SOLVER_CR, SOLVER_PH = 1, 2
+PH_GROUPS_PER_BLOCK = 7
+CR_GROUPS_PER_BLOCK = {32: 8, 64: 4}
+
+
+def kernel_name(solver: int, N: int, K: int) -> str:
+    """The kernel a run launches, by solver, samples per lane and sections per pass."""
+    k = min(K, 8)
+    if solver == SOLVER_PH:
+        return (f"sos_lane_kernel<{k}, {N}> (PH factorization, {k} sections, N = {N} samples per lane, "
+                f"{PH_GROUPS_PER_BLOCK} groups per block)")
+    return (f"sos_cascade_kernel<{k}, {N}> (cyclic reduction, {k} sections, N = {N} samples per lane, "
+            f"{CR_GROUPS_PER_BLOCK.get(N, '?')} groups per block)")
 
 
 def _peaks():
@@ -222,6 +233,149 @@ def cpu_wavefront_leg(x_host):
             "sample": f"first 2^{int(np.log2(n))} samples, groups of 8192 samples, {threads} threads, {dt:.2f} s"}
 
 
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def time_launches(torch, fn, steps: int, stream) -> float:
+    """Mean ms per call of fn() over `steps` calls, CUDA events on `stream`, synchronized on both
+    sides."""
+    e0, e1 = _events(torch)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(steps):
+        fn(i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def hbm_roofline(samples: int, ms: float, kernel: str, traffic=None):
+    """The roofline object of a launch over `samples` samples taking `ms`: 8 algorithmic bytes per
+    sample against the measured copy bandwidth."""
+    peak, kind = _peaks()
+    achieved = BYTES_PER_SAMPLE * samples / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "peak_kind": kind, "kernel": kernel}
+
+
+def fp32_fma_roof(torch, dev, sm_max_mhz):
+    """Peak FP32 FMA rate of the device: SMs x 128 FP32 lanes x the maximum SM clock (one FMA per lane
+    per cycle), in TFMA/s, with how it was derived."""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = float(sm_max_mhz) if sm_max_mhz else 2070.0
+    return sms * 128 * mhz * 1e6 / 1e12, f"derived: {sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz (max SM clock)"
+
+
+def chosen_kernel(K: int, n: int):
+    """(solver, N) that a default-tuned filter of K sections runs on n samples: the autotuner's choice
+    when it has run in this process, else the library default (PH at N = 64)."""
+    from paper_2607_23763_gb300 import autotune_choice
+    c = autotune_choice(K, n)
+    return tuple(c) if c != (0, 0) else (SOLVER_PH, 64)
+
+
+def plain_rate(torch, sos, x, y, steps: int, warmup: int, tuning=None) -> float:
+    """ms per sos_filter_run of one filter over all of x (both larger than L2)."""
+    from paper_2607_23763_gb300 import SosFilter
+    f = SosFilter(sos, tuning=tuning)
+    for _ in range(warmup):
+        f.run(x, y)
+    ms = time_launches(torch, lambda i: f.run(x, y), steps, torch.cuda.current_stream())
+    assert f.sync_status() == 0
+    f.close()
+    return ms
+
+
+def order2_plateau_leg(torch, dev, steps: int, warmup: int):
+    """The order-2 workload's filter (Butterworth at 0.2 Nyquist) over 2^29 and 2^30 samples; the
+    plateau is the mean of the two rates (the paper's plateau protocol, Sec. IV-F, at GB300 sizes)."""
+    import workloads
+    from workloads import designs
+    sos = designs.butter_lowpass(2, 0.2)
+    n_max = 1 << 30
+    x = torch.from_numpy(workloads.normal_f32(0, n_max)).to(dev)
+    y = torch.empty_like(x)
+    pts = {}
+    for lg in (29, 30):
+        n = 1 << lg
+        ms = plain_rate(torch, sos, x[:n], y[:n], steps, warmup)
+        pts[f"2^{lg}"] = {"value": n / ms / 1e6, "ms_per_launch": ms}
+    del x, y
+    ms_mean = 0.5 * (pts["2^29"]["ms_per_launch"] / 2 + pts["2^30"]["ms_per_launch"] / 4)  # per 2^28 samples
+    value = 0.5 * (pts["2^29"]["value"] + pts["2^30"]["value"])
+    roof = hbm_roofline(1 << 28, ms_mean, kernel_name(*chosen_kernel(1, 1 << 30), 1))
+    roof["achieved"] = value * BYTES_PER_SAMPLE  # mean of the two points' GB/s
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    return {"workload": "order-2 Butterworth lowpass (1 SOS) at 0.2 Nyquist, 1 float32 signal of N(0,1) samples, "
+                        "seed 0, 2^29 and 2^30 samples", "value": value, "unit": "GS/s", "points": pts,
+            "roofline": roof, "target_frac": 0.70}
+
+
+def config1_leg(torch, dev, launches: int = 256, pool: int = 64):
+    """Order-2 Butterworth at 0.2 Nyquist on 2^20 samples (seed 0, zero state): one launch per step,
+    cycling through `pool` input/output pairs (pool x 8 MiB, more than 4x L2) so that no launch finds
+    its input in L2.  Accuracy over the whole output of the first pair."""
+    import oracle
+    import workloads
+    from workloads import designs
+    from paper_2607_23763_gb300 import SosFilter
+    sos = designs.butter_lowpass(2, 0.2)
+    n = 1 << 20
+    xh = workloads.normal_f32(0, n)
+    xs = torch.from_numpy(xh).to(dev).repeat(pool, 1)  # pool copies of the same signal
+    ys = torch.empty_like(xs)
+    f = SosFilter(sos)
+    for i in range(2 * pool):
+        f.run(xs[i % pool], ys[i % pool])
+    ms = time_launches(torch, lambda i: f.run(xs[i % pool], ys[i % pool]), launches, torch.cuda.current_stream())
+    assert f.sync_status() == 0
+    err = oracle.rel_err(ys[0].cpu().numpy(), oracle.sosfilt(sos, xh))
+    f.close()
+    return {"workload": "order-2 Butterworth lowpass (1 SOS) at 0.2 Nyquist, 1 float32 signal of 2^20 N(0,1) "
+                        "samples, seed 0, zero state",
+            "value": n / ms / 1e6, "unit": "GS/s", "ms_per_launch": ms,
+            "l2": f"{pool} input/output pairs of 2^20 samples cycled ({pool * 8} MiB, more than 4x L2)",
+            "launches": launches, "roofline": hbm_roofline(n, ms, kernel_name(*chosen_kernel(1, n), 1)),
+            "accuracy": {"max_rel_error": err, "bound": designs.tolerance_for(sos)}}
+
+
+def cr_solver_leg(torch, dev, x16, y16, steps: int, warmup: int, fma_peak):
+    """The divide-and-conquer cyclic-reduction solver (Sec. II-D/E) on the order-16 workload and on
+    the order-2 filter, 2^28 samples each, at its default N."""
+    import workloads
+    from workloads import designs
+    out = {}
+    for order, wn, x, y in ((16, WN, x16, y16), (2, 0.2, None, None)):
+        sos = designs.butter_lowpass(order, wn)
+        if x is None:
+            x = torch.from_numpy(workloads.normal_f32(0, 1 << 28)).to(dev)
+            y = torch.empty_like(x)
+        K = order // 2
+        N = 64 if K == 1 else 32  # the library's default N of cyclic reduction
+        ms = plain_rate(torch, sos, x, y, steps, warmup, tuning={"solver": SOLVER_CR})
+        n = x.numel()
+        fma = 10 * K
+        out[f"order{order}"] = {"value": n / ms / 1e6, "unit": "GS/s", "ms_per_launch": ms, "N": N,
+                                "roofline": hbm_roofline(n, ms, kernel_name(SOLVER_CR, N, K)),
+                                "roofline_alu": {"bound": "alu", "achieved": fma * n / (ms * 1e-3) / 1e12,
+                                                 "peak": fma_peak, "unit": "TFMA/s",
+                                                 "frac": fma * n / (ms * 1e-3) / 1e12 / fma_peak,
+                                                 "fma_per_sample": fma}}
+    return out
+
+
+def _leg(name, fn, line, *a, **kw):
+    """Run one extra measurement into line[name]; a failure is recorded there and the rest goes on."""
+    t0 = time.perf_counter()
+    try:
+        line[name] = fn(*a, **kw)
+    except Exception as e:  # a failed leg must not cost the headline
+        line[name] = {"error": f"{type(e).__name__}: {e}"}
+    if isinstance(line[name], dict):
+        line[name]["wall_s"] = round(time.perf_counter() - t0, 1)
+
+
 def bench_ours(args):
     import torch
     import torch.distributed as dist
@@ -230,6 +384,7 @@ def bench_ours(args):
     from workloads import designs
     from paper_2607_23763_gb300 import SosFilter
 
+    t_start = time.perf_counter()
     world, rank, local = _dist()
     if world > 1:
         dist.init_process_group("nccl", init_method="env://")
@@ -273,7 +428,7 @@ def bench_ours(args):
         f.run(x, y)
     barrier()
     assert f.sync_status() == 0
-    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start, stop = _events(torch)
     with ClockSampler(local) as clk:
         barrier()
         start.record(stream)
@@ -300,46 +455,40 @@ def bench_ours(args):
     barrier()
     e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / e_steps, world, dev)
     e_gss = replica_rate(N_SAMPLES, world, e_ms)
+    del xh, yh
 
     # the kernel that ran: the autotuner's choice, else the tuning's (the library default is PH at
     # N = 64; a carry scheme or lookback width selects cyclic reduction, by default at N = 32)
     if choice:
         kid = tuple(choice)
     elif args.solver:
-        kid = (args.solver, args.N or (64 if args.solver == 2 else 32))
+        kid = (args.solver, args.N or (64 if args.solver == SOLVER_PH else 32))
     elif args.carry or args.lbw:
-        kid = (1, args.N or 32)
+        kid = (SOLVER_CR, args.N or 32)
     else:
-        kid = (2, args.N or 64)
-    hbm_peak, peak_kind = _peaks()
-    achieved = BYTES_PER_SAMPLE * N_SAMPLES / (ms_step * 1e-3) / 1e9
+        kid = (SOLVER_PH, args.N or 64)
+    K = ORDER // 2
+    clocks = clk.summary()
     # the FP32 roof the method meets first at high order: its FMAs per sample (PH: 4K for the
     # particular pass with b0 = 1 plus 2K for the correction; cyclic reduction: 8K + 2K, Sec. IV-C)
-    # against 152 SMs x 128 FP32 lanes x the maximum SM clock (one FMA per lane per cycle)
-    K = ORDER // 2
-    fma_per_sample = 6 * K if kid[0] == 2 else 10 * K
-    alu_peak = 152 * 128 * 2.070e9 / 1e12
+    fma_per_sample = 6 * K if kid[0] == SOLVER_PH else 10 * K
+    fma_peak, fma_kind = fp32_fma_roof(torch, dev, clocks.get("sm_max_mhz"))
     alu_achieved = fma_per_sample * N_SAMPLES / (ms_step * 1e-3) / 1e12
-    clocks = clk.summary()
+    traffic = (TRAFFIC_BYTES_2P28.get(kid) if (N_SAMPLES == 1 << 28 and ORDER == 16 and not args.lbw
+                                               and args.carry != 2) else None)
     line = {
         "metric": "GS/s", "value": gss, "unit": "GS/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "samples": N_SAMPLES, "sections": ORDER // 2,
-                   "N": kid[1], "L": 32, "solver": "PH" if kid[0] == 2 else "CR",
+        "config": {"workload": WORKLOAD, "samples": N_SAMPLES, "sections": K,
+                   "N": kid[1], "L": 32, "solver": "PH" if kid[0] == SOLVER_PH else "CR",
                    "deterministic": bool(args.deterministic),
                    "autotuned": choice is not None,
                    "l2": "inputs and outputs larger than L2 (1 GiB each)",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak,
-                     "traffic": (TRAFFIC_BYTES_2P28.get(kid) if (N_SAMPLES == 1 << 28 and ORDER == 16
-                                                                 and not args.lbw and args.carry != 2) else None),
-                     "peak_kind": peak_kind,
-                     "kernel": KERNEL_NAMES.get(kid, str(kid))},
-        "roofline_alu": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "TFMA/s",
-                         "frac": alu_achieved / alu_peak, "fma_per_sample": fma_per_sample,
-                         "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz"},
+        "roofline": hbm_roofline(N_SAMPLES, ms_step, kernel_name(kid[0], kid[1], K), traffic),
+        "roofline_alu": {"bound": "alu", "achieved": alu_achieved, "peak": fma_peak, "unit": "TFMA/s",
+                         "frac": alu_achieved / fma_peak, "fma_per_sample": fma_per_sample, "peak_kind": fma_kind},
         "e2e": {"value": e_gss, "unit": "GS/s", "h2d_bytes_per_step": 4 * N_SAMPLES,
                 "d2h_bytes_per_step": 4 * N_SAMPLES},
         "gpu_launches": args.steps,
@@ -348,9 +497,25 @@ def bench_ours(args):
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"], line["accuracy"] = cpu_baseline_leg(sos, x_host, y)
         line["cpu_wavefront"] = cpu_wavefront_leg(x_host)
+    f.close()
+    if rank == 0 and not args.quick:
+        # the other targets, measured on this GPU in the same run (rank 0 only)
+        steps, warm = 10, 3
+        _leg("cr_solver", cr_solver_leg, line, torch, dev, x, y, steps, warm, fma_peak)
+        del x, y
+        torch.cuda.empty_cache()
+        _leg("order2_plateau", order2_plateau_leg, line, torch, dev, steps, warm)
+        torch.cuda.empty_cache()
+        _leg("config1_2p20", config1_leg, line, torch, dev)
+        torch.cuda.empty_cache()
+        plain = {}
+        _leg("batched", batched_leg, line, torch, dev, steps=5, warmup=3, no_cpu=args.no_cpu, plain=plain)
+        torch.cuda.empty_cache()
+        _leg("serving", serving_leg, line, torch, dev, n_streams=args.streams, per_stream=2,
+             n_open=args.serving_open_requests, plain=plain)
+    line["wall_s"] = round(time.perf_counter() - t_start, 1)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    f.close()
     if world > 1:
         dist.destroy_process_group()
 
@@ -379,44 +544,48 @@ def batch_sample_leg(specs, xs, ys, n_sample: int = 64):
     return base, acc
 
 
-def bench_batched(args):
-    """Batched mix: 4096 signals (orders 2/4/8/16, lengths 2^10..2^22) in one sos_filter_run_batch call
-    per step; GS/s of the whole batch, and its ratio to the plain kernel's rate at each signal's order."""
-    import torch
-
+def plain_rates_by_sections(torch, dev, plain: dict, steps: int = 5, warmup: int = 3) -> dict:
+    """The plain single-signal kernel's GS/s on 2^28 samples for 1, 2, 4 and 8 random sections (the
+    orders of the mixes), cached in `plain`."""
+    if plain:
+        return plain
     import workloads
     from workloads import designs
-    from paper_2607_23763_gb300 import SosFilter, run_batch, batch_sync_status
+    x = torch.from_numpy(workloads.normal_f32(1, 1 << 28)).to(dev)
+    y = torch.empty_like(x)
+    for K in (1, 2, 4, 8):
+        sos = designs.random_sections(workloads.uniform_f64(7, 3 * K, stream=1).reshape(K, 3))
+        plain[K] = (1 << 28) / plain_rate(torch, sos, x, y, steps, warmup) / 1e6
+    return plain
 
-    torch.cuda.set_device(0)
+
+def batched_leg(torch, dev, steps: int = 5, warmup: int = 3, no_cpu: bool = False, plain=None):
+    """Batched mix: 4096 signals (orders 2/4/8/16, lengths 2^10..2^22) in one sos_filter_run_batch call
+    per step; GS/s of the whole batch, the same batch as a prepared plan replayed from a CUDA graph,
+    and both as a fraction of the plain kernel's time for the same signals at each signal's order."""
+    import workloads
+    from paper_2607_23763_gb300 import SosFilter, run_batch, batch_sync_status, BatchPlan
+
     n_sig = 4096
     specs = [workloads.batched_signal(i) for i in range(n_sig)]
     fs = [SosFilter(sos) for sos, _, _ in specs]
     xs, xs_host = [], []  # host copies kept only for the CPU leg's sample
     for i, (_, n, seed) in enumerate(specs):
         x = workloads.normal_f32(seed, n)
-        xs.append(torch.from_numpy(x).cuda())
+        xs.append(torch.from_numpy(x).to(dev))
         if i < 64:
             xs_host.append(x)
     ys = [torch.empty_like(x) for x in xs]
     total = sum(n for _, n, _ in specs)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         run_batch(fs, xs, ys)
     torch.cuda.synchronize()
     assert batch_sync_status(0) == 0
     stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(0) as clk:
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(args.steps):
-            run_batch(fs, xs, ys)
-        e1.record(stream)
-        torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
+    with ClockSampler(dev.index or 0) as clk:
+        ms = time_launches(torch, lambda i: run_batch(fs, xs, ys), steps, stream)
     assert batch_sync_status(0) == 0
     # the same batch as a prepared plan captured into a CUDA graph, replayed
-    from paper_2607_23763_gb300 import BatchPlan
     plan = BatchPlan(fs, xs, ys)
     side = torch.cuda.Stream()
     side.wait_stream(stream)
@@ -427,109 +596,153 @@ def bench_batched(args):
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph):
         plan.launch()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         graph.replay()
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(args.steps):
-        graph.replay()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    graph_ms = e0.elapsed_time(e1) / args.steps
+    graph_ms = time_launches(torch, lambda i: graph.replay(), steps, stream)
     assert plan.status() == 0
     plan.close()
-    # the plain single-signal kernel's rate per order on 2^28 samples
-    x = torch.from_numpy(workloads.normal_f32(1, 1 << 28)).cuda()
-    y = torch.empty_like(x)
-    rate = {}
-    for K in (1, 2, 4, 8):
-        f = SosFilter(designs.random_sections(workloads.uniform_f64(7, 3 * K, stream=1).reshape(K, 3)))
-        for _ in range(3):
-            f.run(x, y)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        a.record(stream)
-        for _ in range(5):
-            f.run(x, y)
-        b.record(stream)
-        torch.cuda.synchronize()
-        rate[K] = (1 << 28) / (a.elapsed_time(b) / 5) / 1e6
-        f.close()
+    del graph
+    rate = plain_rates_by_sections(torch, dev, plain if plain is not None else {})
     plain_ms = sum(n / rate[sos.shape[0]] / 1e6 for sos, n, _ in specs)
-    gss = total / ms / 1e6
-    line = {"metric": "GS/s", "value": gss, "unit": "GS/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
-            "config": {"workload": "batched mix: 4096 float32 signals, lengths round(2^U), U~U[10,22], orders "
-                                   "uniform over {2,4,8,16}, random stable sections, N(0,1) input, seeds 1000+i",
-                       "samples": total, "l2": "inputs and outputs larger than L2"},
-            "vs_plain_kernel": plain_ms / ms,
-            "cuda_graph": {"value": total / graph_ms / 1e6, "ms_per_step": graph_ms, "vs_plain_kernel": plain_ms / graph_ms},
-            "plain_gss_by_order": {str(2 * k): v for k, v in rate.items()},
-            "gpu_launches": 4 * args.steps, "clocks": clk.summary()}
-    if not args.no_cpu:
-        line["cpu_baseline"], line["accuracy"] = batch_sample_leg(specs, xs_host, ys)
+    out = {"workload": "batched mix: 4096 float32 signals, lengths round(2^U), U~U[10,22], orders uniform over "
+                       "{2,4,8,16}, random stable sections, N(0,1) input, seeds 1000+i",
+           "samples": total, "l2": "inputs and outputs larger than L2",
+           "value": total / ms / 1e6, "unit": "GS/s", "ms_per_step": ms, "steps": steps,
+           "vs_plain_kernel": plain_ms / ms,
+           "cuda_graph": {"value": total / graph_ms / 1e6, "ms_per_step": graph_ms,
+                          "vs_plain_kernel": plain_ms / graph_ms},
+           "plain_gss_by_order": {str(2 * k): v for k, v in rate.items()},
+           "target_vs_plain": 0.60, "clocks": clk.summary()}
+    if not no_cpu:
+        out["cpu_baseline"], out["accuracy"] = batch_sample_leg(specs, xs_host, ys)
+    for f in fs:
+        f.close()
+    return out
+
+
+def bench_batched(args):
+    import torch
+    torch.cuda.set_device(0)
+    leg = batched_leg(torch, torch.device("cuda", 0), args.steps, args.warmup, args.no_cpu)
+    line = {"metric": "GS/s", "value": leg["value"], "unit": "GS/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": leg["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": leg["workload"], "samples": leg["samples"], "l2": leg["l2"]},
+            "gpu_launches": 4 * args.steps}
+    line.update({k: v for k, v in leg.items() if k not in line and k not in ("workload", "samples", "l2")})
     print(json.dumps(line), flush=True)
 
 
-def bench_serving(args):
+def serving_leg(torch, dev, n_streams: int = 10000, per_stream: int = 10, n_open: int = 110000, plain=None):
     """Serving mix: streams with orders 2/4/8/16 at 40/30/20/10 %, chunks of U[4096, 65536] samples.
     Capacity = closed loop (every chunk queued at t = 0); then Poisson arrivals at 80 % of capacity;
-    latency = completion - scheduled arrival; p50/p99 over the requests after a 10 % warm-up."""
-    import numpy as np
-    import torch
-
+    latency = completion - scheduled arrival; p50/p99 over the requests after a 10 % warm-up.  The
+    capacity is also given as a fraction of the plain kernel's rate for the same chunks (each chunk
+    at the plain 2^28-sample rate of its order)."""
     import workloads
     from paper_2607_23763_gb300 import SosServer
 
-    torch.cuda.set_device(0)
-    n_streams = args.streams
-    per_stream = args.chunks_per_stream
     srv = SosServer(budget_bytes=16 << 30)
     t0 = time.perf_counter()
-    sids = [srv.add_stream(workloads.serving_stream(s)) for s in range(n_streams)]
+    soss = [workloads.serving_stream(s) for s in range(n_streams)]
+    sids = [srv.add_stream(sos) for sos in soss]
     t_setup = time.perf_counter() - t0
     hi = 65536
-    pool = torch.from_numpy(workloads.normal_f32(77, 1 << 24)).cuda()  # chunk inputs are windows of this pool
-    out = torch.empty(n_streams * hi, device="cuda")
+    pool = torch.from_numpy(workloads.normal_f32(77, 1 << 24)).to(dev)  # chunk inputs are windows of this pool
+    out = torch.empty(n_streams * hi, device=dev)
     rng = np.random.default_rng(5)
 
     def requests(n_req, arrivals):
         sid = rng.integers(0, n_streams, n_req)
         lens = np.array([workloads.serving_chunk_len(int(s), int(c)) for s, c in
                          zip(sid, rng.integers(0, 1 << 20, n_req))], dtype=np.int64)
-        off = rng.integers(0, pool.numel() - hi, n_req)
+        off = rng.integers(0, pool.numel() - hi, n_req) // 4 * 4  # chunks start on 16-byte boundaries
         xp = pool.data_ptr() + 4 * off
         yp = out.data_ptr() + 4 * (sid * hi)
         lat = srv.replay([sids[s] for s in sid], xp, yp, lens, arrivals)
-        return lens, lat
+        return sid, lens, lat
 
     # closed loop: capacity
     n_cap = n_streams * per_stream
-    lens, lat = requests(n_cap, np.zeros(n_cap))
-    capacity = lens.sum() / lat.max() / 1e9
+    sid_c, lens_c, lat_c = requests(n_cap, np.zeros(n_cap))
+    capacity = lens_c.sum() / lat_c.max() / 1e9
     # open loop: Poisson arrivals at 80 % of capacity
     mean_len = (4096 + hi) / 2
     rate = 0.8 * capacity * 1e9 / mean_len
-    n_open = max(args.open_requests, 1000)
+    n_open = max(n_open, 1000)
     arrivals = np.cumsum(rng.exponential(1.0 / rate, n_open))
-    lens, lat = requests(n_open, arrivals)
+    _, lens, lat = requests(n_open, arrivals)
     keep = slice(n_open // 10, None)
     p50, p99 = np.percentile(lat[keep] * 1e3, [50, 99])
     wall = arrivals[-1] + lat[-1]
-    gss = lens.sum() / wall / 1e9
     st = srv.stats()
     srv.close()
-    line = {"metric": "GS/s", "value": gss, "unit": "GS/s", "n_gpus": 1, "steps": 1, "warmup": 0,
-            "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+    res = {"workload": f"serving mix: {n_streams} streams, orders 2/4/8/16 at 40/30/20/10 %, chunks U[4096, 65536] "
+                       "float32 samples, Poisson arrivals at 80 % of measured capacity, 16 GiB budget, state "
+                       "resident on the device",
+           "value": lens.sum() / wall / 1e9, "unit": "GS/s", "open_loop_requests": n_open,
+           "closed_loop_requests": n_cap, "capacity_gss": capacity, "offered_gss": 0.8 * capacity,
+           "latency_ms": {"p50": p50, "p99": p99, "max": float(lat.max() * 1e3)},
+           "batches": st["batches"], "max_batch": st["max_batch_seen"], "setup_s": t_setup}
+    if plain is not None:
+        rates = plain_rates_by_sections(torch, dev, plain)
+        plain_s = sum(int(n) / rates[soss[int(s)].shape[0]] / 1e9 for s, n in zip(sid_c, lens_c))
+        res["capacity_vs_plain_kernel"] = plain_s / lat_c.max()
+        res["target_vs_plain"] = 0.60
+    res["one_batch"] = serving_batch_probe(torch, dev, soss, pool)
+    return res
+
+
+def serving_batch_probe(torch, dev, soss, pool, m: int = 4096, reps: int = 3):
+    """Where a serving batch's time goes: one sos_filter_run_batch_ex call over m chunks shaped like
+    the serving mix (the first m streams' filters, chunk lengths U[4096, 65536], states carried), timed
+    on the host (the call itself: planning and launches) and on the device (CUDA events)."""
+    import workloads
+    from paper_2607_23763_gb300 import SosFilter, run_batch, batch_sync_status
+    fs = [SosFilter(sos) for sos in soss[:m]]
+    lens = [workloads.serving_chunk_len(i, 0) for i in range(m)]
+    xs, off = [], 0
+    for n in lens:
+        xs.append(pool[off:off + n])
+        off = (off + n + 3) // 4 * 4
+        if off + 65536 > pool.numel():
+            off = 0
+    ys = [torch.empty(n, device=dev) for n in lens]
+    zs = [torch.zeros(f.K, 2, device=dev) for f in fs]
+    zf = [torch.zeros(f.K, 2, device=dev) for f in fs]
+    from paper_2607_23763_gb300 import BatchPlan
+    for _ in range(2):
+        run_batch(fs, xs, ys, zis=zs, zfs=zf)
+    torch.cuda.synchronize()
+    host = []
+    for _ in range(reps):  # fewer calls than the library's scratch sets: no call waits for the device
+        t0 = time.perf_counter()
+        run_batch(fs, xs, ys, zis=zs, zfs=zf)
+        host.append(time.perf_counter() - t0)
+    torch.cuda.synchronize()
+    assert batch_sync_status(dev.index or 0) == 0
+    # the device's share: the same batch as a prepared plan, whose launches enqueue no host work
+    plan = BatchPlan(fs, xs, ys, zis=zs, zfs=zf)
+    plan.launch()
+    dev_ms = time_launches(torch, lambda i: plan.launch(), reps, torch.cuda.current_stream())
+    assert plan.status() == 0
+    plan.close()
+    for f in fs:
+        f.close()
+    return {"chunks": m, "samples": int(sum(lens)), "host_ms_per_call": 1e3 * float(np.median(host)),
+            "device_ms_per_call": dev_ms, "device_gss": sum(lens) / dev_ms / 1e6}
+
+
+def bench_serving(args):
+    import torch
+    torch.cuda.set_device(0)
+    leg = serving_leg(torch, torch.device("cuda", 0), args.streams, args.chunks_per_stream, args.open_requests, {})
+    line = {"metric": "GS/s", "value": leg["value"], "unit": "GS/s", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"serving mix: {n_streams} streams, orders 2/4/8/16 at 40/30/20/10 %, chunks "
-                                   "U[4096, 65536] float32 samples, Poisson arrivals at 80 % of measured capacity, "
-                                   "16 GiB budget, state resident on the device",
-                       "open_loop_requests": n_open, "closed_loop_requests": n_cap},
-            "capacity_gss": capacity, "offered_gss": 0.8 * capacity,
-            "latency_ms": {"p50": p50, "p99": p99, "max": float(lat.max() * 1e3)},
-            "batches": st["batches"], "max_batch": st["max_batch_seen"], "setup_s": t_setup}
+            "config": {"workload": leg["workload"], "open_loop_requests": leg["open_loop_requests"],
+                       "closed_loop_requests": leg["closed_loop_requests"]}}
+    line.update({k: v for k, v in leg.items() if k not in line and k != "workload"})
     print(json.dumps(line), flush=True)
 
 
@@ -586,6 +799,9 @@ def main():
     ap.add_argument("--streams", type=int, default=10000, help="serving: streams")
     ap.add_argument("--chunks-per-stream", type=int, default=10, help="serving: closed-loop chunks per stream")
     ap.add_argument("--open-requests", type=int, default=110000, help="serving: open-loop requests")
+    ap.add_argument("--serving-open-requests", type=int, default=30000,
+                    help="open-loop requests of the serving measurement inside the default line")
+    ap.add_argument("--quick", action="store_true", help="the headline alone (no extra measurements)")
     ap.add_argument("--N", type=int, default=0, help="samples per thread (16/32/64); 0 = library default")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--no-autotune", action="store_true",

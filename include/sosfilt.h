@@ -152,22 +152,29 @@ sos_status sos_filter_run(sos_filter *f, const float *x_dev, float *y_dev, int64
                           float *zf_dev, void *stream);
 
 /*
- * Filter a signal held in HOST memory.  The library copies it to the device,
- * filters it and copies the result back in chunks, overlapping the
- * host->device copy of chunk i+1, the filtering of chunk i (sos_filter_run
- * with the state carried on the device from chunk to chunk, so the output
- * equals one call over the whole signal) and the device->host copy of chunk
- * i-1 on three library streams.  Synchronous: returns when y_host holds the
- * output.
- *   x_host, y_host  host float32[n]; may be equal; pinned memory (cudaHostAlloc
- *                   or torch's pin_memory) lets the copies run at full speed
+ * Filter a signal held in HOST memory.  Synchronous: returns when y_host holds
+ * the output.  Two ways, chosen by chunk_samples:
+ *   staged (chunk_samples >= 0): the library copies the signal to the device,
+ *     filters it and copies the result back in chunks, overlapping the
+ *     host->device copy of chunk i+1, the filtering of chunk i (sos_filter_run
+ *     with the state carried on the device from chunk to chunk, so the output
+ *     equals one call over the whole signal) and the device->host copy of
+ *     chunk i-1 on three library streams;
+ *   direct (chunk_samples == SOS_HOST_DIRECT): the kernels read x_host and
+ *     write y_host where they are, through their device mappings, in one run:
+ *     no device buffers and no staging copies.  The buffers must be pinned
+ *     (cudaHostAlloc, torch's pin_memory) or registered (cudaHostRegister);
+ *     other host memory is SOS_EINVAL.
+ *   x_host, y_host  host float32[n]; may be equal, any other overlap is SOS_EINVAL;
+ *                   pinned memory lets the staged copies run at full speed
  *   zi_host         host float32[K][2] initial state or NULL (zeros)
  *   zf_host         host float32[K][2] receives the final state, or NULL
- *   chunk_samples   samples per chunk, 0 = 2^24; the library keeps three device
- *                   buffers of this size per filter after the first call
+ *   chunk_samples   staged: samples per chunk, 0 = 2^24; the library keeps three
+ *                   device buffers of this size per filter after the first call
  * Errors: SOS_EINVAL, SOS_ENOMEM, SOS_ECUDA; SOS_ETIMEOUT when a device wait of this call (or of
  * an earlier unreported run) ran out of time, reported and cleared as by sos_filter_sync_status.
  */
+#define SOS_HOST_DIRECT (-1LL)
 sos_status sos_filter_run_host(sos_filter *f, const float *x_host, float *y_host, int64_t n, const float *zi_host,
                                float *zf_host, int64_t chunk_samples);
 

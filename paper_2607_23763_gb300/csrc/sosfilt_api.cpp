@@ -1522,22 +1522,59 @@ sos_status sos_filter_run(sos_filter *f, const float *x_dev, float *y_dev, int64
     return run_impl(f, x_dev, y_dev, n, zi_dev, zf_dev, static_cast<cudaStream_t>(stream));
 }
 
+namespace {
+// Streams, events and the state buffer of the host-buffer paths, created on first use.
+sos_status ensure_host_pipeline(sos_filter *f) {
+    if (f->hs[0]) return SOS_OK;
+    for (int i = 0; i < 3; ++i) {
+        if (cudaStreamCreateWithFlags(&f->hs[i], cudaStreamNonBlocking) != cudaSuccess) return SOS_ECUDA;
+        if (cudaEventCreateWithFlags(&f->ev_in[i], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&f->ev_done[i], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&f->ev_out[i], cudaEventDisableTiming) != cudaSuccess)
+            return SOS_ECUDA;
+    }
+    if (cudaMalloc(&f->d_hstate, sizeof(float) * 2 * f->K) != cudaSuccess) return SOS_ENOMEM;
+    return SOS_OK;
+}
+
+// The kernels read x_host and write y_host in place, through the buffers' device mappings (pinned or
+// registered host memory): no staging copies, the signal crosses the CPU-GPU link once each way.
+sos_status run_host_direct(sos_filter *f, const float *x_host, float *y_host, int64_t n, const float *zi_host,
+                           float *zf_host) {
+    void *dx = nullptr, *dy = nullptr;
+    if (n > 0) {
+        if (cudaHostGetDevicePointer(&dx, const_cast<float *>(x_host), 0) != cudaSuccess ||
+            cudaHostGetDevicePointer(&dy, y_host, 0) != cudaSuccess || !dx || !dy) {
+            cudaGetLastError();
+            return SOS_EINVAL;  // not device-accessible host memory
+        }
+    }
+    cudaStream_t sc = f->hs[1];
+    const size_t zbytes = sizeof(float) * 2 * f->K;
+    cudaError_t e = zi_host ? cudaMemcpyAsync(f->d_hstate, zi_host, zbytes, cudaMemcpyHostToDevice, sc)
+                            : cudaMemsetAsync(f->d_hstate, 0, zbytes, sc);
+    if (e != cudaSuccess) return SOS_ECUDA;
+    const sos_status st = run_impl(f, static_cast<const float *>(dx), static_cast<float *>(dy), n, f->d_hstate,
+                                   f->d_hstate, sc);
+    if (st != SOS_OK) return st;
+    if (zf_host && cudaMemcpyAsync(zf_host, f->d_hstate, zbytes, cudaMemcpyDeviceToHost, sc) != cudaSuccess)
+        return SOS_ECUDA;
+    if (cudaStreamSynchronize(sc) != cudaSuccess) return SOS_ECUDA;
+    f->last_stream = sc;
+    return take_filter_status(f);
+}
+}  // namespace
+
 sos_status sos_filter_run_host(sos_filter *f, const float *x_host, float *y_host, int64_t n, const float *zi_host,
                                float *zf_host, int64_t chunk_samples) {
-    if (!f || n < 0 || chunk_samples < 0 || (n > 0 && (!x_host || !y_host))) return SOS_EINVAL;
+    if (!f || n < 0 || chunk_samples < SOS_HOST_DIRECT || (n > 0 && (!x_host || !y_host))) return SOS_EINVAL;
+    if (x_host != y_host && n > 0 && ranges_overlap(x_host, y_host, n)) return SOS_EINVAL;
     std::lock_guard<std::mutex> lk(f->mu);
     if (cudaSetDevice(f->device) != cudaSuccess) return SOS_ECUDA;
+    sos_status pst = ensure_host_pipeline(f);
+    if (pst != SOS_OK) return pst;
+    if (chunk_samples == SOS_HOST_DIRECT) return run_host_direct(f, x_host, y_host, n, zi_host, zf_host);
     const long long chunk = chunk_samples ? chunk_samples : (1LL << 24);
-    if (!f->hs[0]) {
-        for (int i = 0; i < 3; ++i) {
-            if (cudaStreamCreateWithFlags(&f->hs[i], cudaStreamNonBlocking) != cudaSuccess) return SOS_ECUDA;
-            if (cudaEventCreateWithFlags(&f->ev_in[i], cudaEventDisableTiming) != cudaSuccess ||
-                cudaEventCreateWithFlags(&f->ev_done[i], cudaEventDisableTiming) != cudaSuccess ||
-                cudaEventCreateWithFlags(&f->ev_out[i], cudaEventDisableTiming) != cudaSuccess)
-                return SOS_ECUDA;
-        }
-        if (cudaMalloc(&f->d_hstate, sizeof(float) * 2 * f->K) != cudaSuccess) return SOS_ENOMEM;
-    }
     if (f->hbuf_samples < chunk) {
         for (int i = 0; i < 3; ++i) {
             if (f->hbuf[i]) cudaFree(f->hbuf[i]);

@@ -228,25 +228,31 @@ __global__ void __launch_bounds__((kBatchW + 1) * 32, 1) sos_batch_kernel(const 
         const long long base = g * C;
         const long long avail = sg->n - base;
         const float *x = sg->x;
-        if (avail >= C && sg->aligned) {
+        // every copy is asynchronous, so no warp waits on its loads here: the group's ragged end and
+        // whatever lies past the signal are zero-filled by the copies themselves (no global read;
+        // their source address is the signal's first sample, which always exists)
+        if (sg->aligned) {
 #pragma unroll
             for (int j = 0; j < CH; ++j) {
                 const int off = 4 * (j * 32 + lane);
-                cp_async16(X + (off / N) * P + (off % N), x + base + off);
+                const long long rem = avail - off;
+                const unsigned bytes = rem >= 4 ? 16u : rem > 0 ? static_cast<unsigned>(4 * rem) : 0u;
+                cp_async16_zfill(X + (off / N) * P + (off % N), bytes ? x + base + off : x, bytes);
             }
-            cp_async_commit();
         } else {
+            // a signal that does not start on a 16-byte boundary: one 4-byte copy per sample
 #pragma unroll
             for (int j = 0; j < CH; ++j) {
                 const int off = 4 * (j * 32 + lane);
-                float4 v;
-                v.x = (off + 0 < avail) ? __ldcs(x + base + off + 0) : 0.f;
-                v.y = (off + 1 < avail) ? __ldcs(x + base + off + 1) : 0.f;
-                v.z = (off + 2 < avail) ? __ldcs(x + base + off + 2) : 0.f;
-                v.w = (off + 3 < avail) ? __ldcs(x + base + off + 3) : 0.f;
-                *reinterpret_cast<float4 *>(X + (off / N) * P + (off % N)) = v;
+                float *dst = X + (off / N) * P + (off % N);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const bool in = off + q < avail;
+                    cp_async4_zfill(dst + q, in ? x + base + off + q : x, in ? 4u : 0u);
+                }
             }
         }
+        cp_async_commit();
     };
 
     // Correction of the tile of iteration jt (signal sig), whose particular output is in buffer Y

@@ -155,6 +155,17 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
 }
+// 16-byte copy reading the first src_bytes (0..16) bytes at gmem and zero-filling the rest; with
+// src_bytes = 0 nothing is read (gmem must still be a valid 16-byte aligned address).
+__device__ __forceinline__ void cp_async16_zfill(void *smem, const void *gmem, unsigned src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(smem)), "l"(gmem), "r"(src_bytes)
+                 : "memory");
+}
+// 4-byte copy of one float (src_bytes 4) or a zero (src_bytes 0: nothing is read).
+__device__ __forceinline__ void cp_async4_zfill(void *smem, const void *gmem, unsigned src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(smem)), "l"(gmem), "r"(src_bytes)
+                 : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 

@@ -31,6 +31,7 @@ cudaError_t cudaDeviceGetAttribute(int *value, cudaDeviceAttr attr, int device);
 cudaError_t cudaMalloc(void **ptr, size_t bytes);
 cudaError_t cudaFree(void *ptr);
 cudaError_t cudaMallocHost(void **ptr, size_t bytes);
+cudaError_t cudaHostGetDevicePointer(void **dptr, void *hptr, unsigned flags);
 cudaError_t cudaFreeHost(void *ptr);
 cudaError_t cudaMemcpy(void *dst, const void *src, size_t bytes, cudaMemcpyKind kind);
 cudaError_t cudaMemcpyAsync(void *dst, const void *src, size_t bytes, cudaMemcpyKind kind, cudaStream_t s = nullptr);

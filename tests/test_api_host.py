@@ -285,6 +285,42 @@ def test_run_host_passes_every_sample_once_and_chains_the_state(lib, n, chunk):
     lib.sos_filter_destroy(f)
 
 
+@pytest.mark.parametrize("n", [0, 1, 5 * C64 + 3, 3 * W * C64 + 17])
+def test_run_host_direct_is_one_run_on_the_host_buffers(lib, n):
+    """chunk_samples = SOS_HOST_DIRECT: one run (one launch per pass) whose kernels take the host
+    buffers' device mappings, the initial state in and the final state out; memory without a
+    device mapping and overlapping buffers are rejected before any launch."""
+    SOS_HOST_DIRECT = -1
+    f = _create(lib, designs.butter_lowpass(4, 0.2))
+    x = workloads.normal_f32(4, max(n, 1))[:n] if n else np.zeros(0, np.float32)
+    y = np.full_like(x, np.nan)
+    zi = np.array([[0.5, 1.0], [2.0, 3.0]], dtype=np.float32)
+    zf = np.full_like(zi, np.nan)
+    lib.host_reset()
+    rc = lib.sos_filter_run_host(f, x.ctypes.data if n else None, y.ctypes.data if n else None, n,
+                                 zi.ctypes.data, zf.ctypes.data, SOS_HOST_DIRECT)
+    assert rc == 0
+    ls = _launches(lib)
+    assert len(ls) == (1 if n else 0)
+    if n:
+        offs = (ctypes.c_longlong * 21)()
+        lib.host_lane_layout(2, offs)
+        assert _at(ls[0]["raw"], offs[0], np.uint64)[0] == x.ctypes.data
+        assert _at(ls[0]["raw"], offs[1], np.uint64)[0] == y.ctypes.data
+    np.testing.assert_array_equal(y, 2 * x)
+    want = zi.copy()
+    want[0, 0] += n
+    np.testing.assert_array_equal(zf, want)
+    if n:
+        lib.host_reset()
+        assert lib.sos_filter_run_host(f, 16, y.ctypes.data, n, None, None, SOS_HOST_DIRECT) == -1
+        if n > 1:
+            assert lib.sos_filter_run_host(f, x.ctypes.data, x.ctypes.data + 4, n - 1, None, None, SOS_HOST_DIRECT) == -1
+        assert lib.sos_filter_run_host(f, x.ctypes.data, y.ctypes.data, n, None, None, -2) == -1
+        assert lib.host_launches() == 0
+    lib.sos_filter_destroy(f)
+
+
 def test_batched_plan_groups_signals_by_class_with_consecutive_tiles(lib):
     rng = np.random.default_rng(9)
     specs = []
