@@ -46,6 +46,7 @@ class Tuning(ctypes.Structure):
 
 
 CARRY_DEFAULT, CARRY_CASCADE, CARRY_SECTION = 0, 1, 2
+HOST_DIRECT = -1  # sos_filter_run_host: the kernels read and write the pinned host buffers in place
 SOLVER_DEFAULT, SOLVER_CR, SOLVER_PH = 0, 1, 2
 
 
@@ -183,7 +184,8 @@ class SosFilter:
     def run_host(self, x, y=None, zi=None, chunk: int = 0, return_state: bool = False):
         """Filter a signal in host memory (numpy float32 or pinned CPU tensor); returns y (same kind).
 
-        Copies in, filters and copies out in overlapping chunks inside the library.
+        Copies in, filters and copies out in overlapping chunks inside the library; with
+        ``chunk=HOST_DIRECT`` (pinned tensors only) the kernels work on the host buffers directly.
         """
         import torch
         if isinstance(x, torch.Tensor):

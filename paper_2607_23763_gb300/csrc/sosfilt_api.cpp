@@ -153,9 +153,21 @@ struct LanePass {
 
 }  // namespace
 
+// What a batched run reads of a filter, in one cache line at the front of the filter object: the
+// batch kernel's device tables (N = kBatchN, first pass) and the launch class.
+struct BatchTmpl {
+    const sosk::LaneSec *sec = nullptr;
+    const float4 *MX = nullptr;
+    const float *tab = nullptr;
+    const float *Mm = nullptr;
+    float gain = 1.f;
+    int cls = -1;  // (K - 1) * 2 + b0-normalized, or -1 for more than kMaxPass sections
+};
+
 struct sos_filter {
     int K = 0;
     int device = 0;
+    BatchTmpl bt;
     std::vector<double> sos;  // [K][5]
     bool norm = false;
     double gain = 1.0;
@@ -991,26 +1003,34 @@ sos_status run_batch_impl(int n_signals, sos_filter *const *filters, const float
     if (n_signals < 0) return SOS_EINVAL;
     if (n_signals == 0) return SOS_OK;
     if (!filters || !x || !y || !n) return SOS_EINVAL;
-    int device = -1;
+    constexpr long long C = 32LL * sosk::kBatchN;
+    constexpr long long W = sosk::kBatchW;
+    // arguments, classes and sizes in one pass over the signals (the per-signal work of a call
+    // reads only the front cache line of each filter)
+    const int device = filters[0] ? filters[0]->device : -1;
+    long long cls_sigs[kBatchClasses] = {0}, cls_tiles[kBatchClasses] = {0};
+    bool any_other = false;  // zero-length signals or filters of more than kMaxPass sections
     for (int i = 0; i < n_signals; ++i) {
-        sos_filter *f = filters[i];
+        const sos_filter *f = filters[i];
         if (!f || n[i] < 0 || (n[i] > 0 && (!x[i] || !y[i]))) return SOS_EINVAL;
         if (x[i] != y[i] && n[i] > 0 && ranges_overlap(x[i], y[i], n[i])) return SOS_EINVAL;
-        if (device < 0) device = f->device;
         if (f->device != device) return SOS_EINVAL;
+        const int c = f->bt.cls;
+        if (n[i] == 0 || c < 0) {
+            any_other = true;
+            continue;
+        }
+        cls_sigs[c] += 1;
+        cls_tiles[c] += ((n[i] + C - 1) / C + W - 1) / W;
     }
     if (cudaSetDevice(device) != cudaSuccess) return SOS_ECUDA;
     BatchCtx *ctx = batch_ctx(device);
     if (!ctx) return SOS_ENOMEM;
     std::lock_guard<std::mutex> lk(ctx->mu);
 
-    constexpr long long C = 32LL * sosk::kBatchN;
-    constexpr long long W = sosk::kBatchW;
-    // classes and sizes
-    std::vector<int> cls(n_signals, -1);
-    long long cls_sigs[kBatchClasses] = {0}, cls_tiles[kBatchClasses] = {0};
-    for (int i = 0; i < n_signals; ++i) {
+    for (int i = 0; any_other && i < n_signals; ++i) {
         sos_filter *f = filters[i];
+        if (n[i] != 0 && f->bt.cls >= 0) continue;
         if (n[i] == 0) {
             if (zf && zf[i]) {
                 const size_t b = sizeof(float) * 2 * f->K;
@@ -1020,17 +1040,9 @@ sos_status run_batch_impl(int n_signals, sos_filter *const *filters, const float
             }
             continue;
         }
-        if (f->K > sosk::kMaxPass) {
-            std::lock_guard<std::mutex> fl(f->mu);
-            sos_status st = run_impl(f, x[i], y[i], n[i], zi ? zi[i] : nullptr, zf ? zf[i] : nullptr, s);
-            if (st != SOS_OK) return st;
-            continue;
-        }
-        const int c = (f->K - 1) * 2 + (f->norm ? 1 : 0);
-        cls[i] = c;
-        cls_sigs[c] += 1;
-        const long long G = (n[i] + C - 1) / C;
-        cls_tiles[c] += (G + W - 1) / W;
+        std::lock_guard<std::mutex> fl(f->mu);  // more than kMaxPass sections: filtered on its own
+        sos_status st = run_impl(f, x[i], y[i], n[i], zi ? zi[i] : nullptr, zf ? zf[i] : nullptr, s);
+        if (st != SOS_OK) return st;
     }
     long long sig_off[kBatchClasses + 1] = {0}, tile_off[kBatchClasses + 1] = {0}, desc_off[kBatchClasses + 1] = {0};
     int n_cls = 0;
@@ -1088,10 +1100,9 @@ sos_status run_batch_impl(int n_signals, sos_filter *const *filters, const float
         fill_tile[c] = tile_off[c];
     }
     for (int i = 0; i < n_signals; ++i) {
-        const int c = cls[i];
-        if (c < 0) continue;
-        sos_filter *f = filters[i];
-        const LanePass &ps = f->lane[1][0];  // N = kBatchN: the batch kernel's tables (read only)
+        const BatchTmpl &bt = filters[i]->bt;  // the batch kernel's tables (N = kBatchN), read only
+        const int c = bt.cls;
+        if (c < 0 || n[i] == 0) continue;
         const long long G = (n[i] + C - 1) / C;
         const long long nt = (G + W - 1) / W;
         const long long si = fill_sig[c]++;
@@ -1103,14 +1114,16 @@ sos_status run_batch_impl(int n_signals, sos_filter *const *filters, const float
         b.tile0 = fill_tile[c] - tile_off[c];
         b.zi = zi ? zi[i] : nullptr;
         b.zf = zf ? zf[i] : nullptr;
-        b.sec = ps.d_sec;
-        b.MX = ps.d_MX;
-        b.tab = ps.d_tab;
-        b.Mm = ps.d_Mm;
-        b.gain = static_cast<float>(f->gain);
-        b.aligned = (reinterpret_cast<uintptr_t>(x[i]) % 16 == 0 && reinterpret_cast<uintptr_t>(y[i]) % 16 == 0) ? 1 : 0;
+        b.sec = bt.sec;
+        b.MX = bt.MX;
+        b.tab = bt.tab;
+        b.Mm = bt.Mm;
+        b.gain = bt.gain;
+        b.aligned = ((reinterpret_cast<uintptr_t>(x[i]) | reinterpret_cast<uintptr_t>(y[i])) % 16 == 0) ? 1 : 0;
         const int local = static_cast<int>(si - sig_off[c]);
-        for (long long t = 0; t < nt; ++t) h_tile_sig[fill_tile[c]++] = local;
+        int *tm = h_tile_sig + fill_tile[c];
+        for (long long t = 0; t < nt; ++t) tm[t] = local;
+        fill_tile[c] += nt;
     }
     if (cudaMemcpyAsync(sl.d_up, sl.h_up, up_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemsetAsync(sl.d_ticket, 0, sizeof(unsigned long long) * kBatchClasses, s) != cudaSuccess)
@@ -1452,6 +1465,15 @@ sos_status sos_filter_create(int n_sections, const double *sos, const float *zi,
     }
     for (int i = 0; i < 2 && st == SOS_OK; ++i) st = build_cascade(f, i == 0 ? 32 : 64, f->cas[i]);
     for (int i = 0; i < 2 && st == SOS_OK; ++i) st = build_lane(f, i == 0 ? 32 : 64, f->lane[i]);
+    if (st == SOS_OK) {
+        const LanePass &ps = f->lane[1][0];
+        f->bt.sec = ps.d_sec;
+        f->bt.MX = ps.d_MX;
+        f->bt.tab = ps.d_tab;
+        f->bt.Mm = ps.d_Mm;
+        f->bt.gain = static_cast<float>(f->gain);
+        f->bt.cls = f->K > sosk::kMaxPass ? -1 : (f->K - 1) * 2 + (f->norm ? 1 : 0);
+    }
     if (st == SOS_OK) {
         if (cudaMalloc(&f->d_ticket, sizeof(unsigned long long)) != cudaSuccess ||
             cudaMalloc(&f->d_status, sizeof(int)) != cudaSuccess ||

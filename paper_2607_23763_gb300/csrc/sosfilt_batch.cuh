@@ -5,8 +5,8 @@
 // (N = kBatchN); the tiles of all signals of the launch form one queue, drawn in ascending order
 // from a ticket counter (Sec. IV-A), so that tile t's predecessors within its signal are held by
 // running or finished blocks.  Each tile is filtered as by the single-signal PH kernel
-// (sosfilt_lane.cuh): a skewed direct-form-II particular pass per lane (Sec. II-C), the cascade lane
-// scan, a coordinator warp that folds the groups' local carries, resolves the tile's incoming
+// (sosfilt_lane.cuh): a skewed particular pass per lane in direct-form-I order (Sec. II-C), the
+// cascade lane scan, a coordinator warp that folds the groups' local carries, resolves the tile's incoming
 // 2K-word state by decoupled lookback (Sec. IV-B, Eq. 25 on the cascade state) and derives the
 // groups' incoming states, and the homogeneous correction of Eq. 24 applied once for the cascade.
 // What changes is that lookback chains are kept per signal (the anchors count from the signal's
@@ -228,6 +228,7 @@ __global__ void __launch_bounds__((kBatchW + 1) * 32, 1) sos_batch_kernel(const 
         const long long base = g * C;
         const long long avail = sg->n - base;
         const float *x = sg->x;
+        if (avail <= 0) return;  // a group past the signal's end is not filtered (see below)
         // every copy is asynchronous, so no warp waits on its loads here: the group's ragged end and
         // whatever lies past the signal are zero-filled by the copies themselves (no global read;
         // their source address is the signal's first sample, which always exists)
@@ -359,7 +360,7 @@ __global__ void __launch_bounds__((kBatchW + 1) * 32, 1) sos_batch_kernel(const 
         if (next >= 0) issue_load(next, p.sigs + next_sig, B0 + nxt_buf * kL * P);
 
         float t[S], Sl[S];
-        {
+        if (g < G) {
             const RegSecs<K, NORM> cs(sg->sec, sg->MX);
             const long long p_last = sg->n - 1 - (G - 1) * C;
             if (g == G - 1 && sg->zf)
@@ -368,6 +369,12 @@ __global__ void __launch_bounds__((kBatchW + 1) * 32, 1) sos_batch_kernel(const 
             else
                 lane_particular<K, N, NORM, false>(cs, X + lane * P, sg->gain, t, 0, false, nullptr);
             lane_scan<K>(cs, t, Sl, a_buf + (slot * W + w) * S, lane);
+        } else {
+            // a group past the signal's end (the signal's last tile is not full): nothing to filter,
+            // and its local carry, zero, enters the fold as the carry of zero input
+#pragma unroll
+            for (int j = 0; j < S; ++j) Sl[j] = 0.f;
+            if (lane < S) a_buf[(slot * W + w) * S + lane] = 0.f;
         }
         {
             // the last warp of the tile to finish folds the groups' local carries (c = a_0;

@@ -617,12 +617,20 @@ __global__ void __launch_bounds__((kLaneW + 1) * 32, LaneDims<K, N>::BPS)
 
         float t[S], Sl[S];
         const ParamSecs<K> cs{p};
-        if (want_zf && g == g_last)
-            lane_particular<K, N, NORM, true>(cs, X + lane * P, p.gain, t, m_last, lane == lane_last, zs_tail);
-        else
-            lane_particular<K, N, NORM, false>(cs, X + lane * P, p.gain, t, m_last, false, nullptr);
-        wtrace(tile, 6);
-        lane_scan<K>(cs, t, Sl, a_buf + (slot * W + w) * S, lane);
+        if (g < p.G) {
+            if (want_zf && g == g_last)
+                lane_particular<K, N, NORM, true>(cs, X + lane * P, p.gain, t, m_last, lane == lane_last, zs_tail);
+            else
+                lane_particular<K, N, NORM, false>(cs, X + lane * P, p.gain, t, m_last, false, nullptr);
+            wtrace(tile, 6);
+            lane_scan<K>(cs, t, Sl, a_buf + (slot * W + w) * S, lane);
+        } else {
+            // a group past the signal's end (the last tile is not full): nothing to filter, and its
+            // local carry, zero, enters the fold as the carry of zero input
+#pragma unroll
+            for (int j = 0; j < S; ++j) Sl[j] = 0.f;
+            if (lane < S) a_buf[(slot * W + w) * S + lane] = 0.f;
+        }
         wtrace(tile, 7);
         {
             // the last warp of the tile to finish folds the groups' local carries (c = a_0;

@@ -6,9 +6,9 @@
 // admitted, so chunk i + 1 continues from chunk i's final state without a host round trip.
 // Requests name caller-owned device buffers.  A scheduler thread admits the oldest ready chunks
 // (streams with a queued chunk and none in flight) while the bytes in flight stay inside the
-// memory budget, issues each batch through sos_filter_run_batch_ex on one of a few CUDA streams,
-// so that several batches overlap on the device, and learns of completions from a host function
-// enqueued behind every batch.  New requests are admitted as soon as budget and batch slots free up.
+// memory budget; a launcher thread issues each admitted batch through sos_filter_run_batch_ex on
+// one of a few CUDA streams, so that several batches overlap on the device and admission overlaps
+// with issuing; completions come from a host function enqueued behind every batch.  New requests are admitted as soon as budget and batch slots free up.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -39,6 +39,10 @@ struct Req {
     int64_t n = 0;
     double t_submit = 0, t_start = 0, t_done = 0;
     int status = SOS_OK;
+    // fixed at admission: the stream's filter and the state copies this chunk reads and writes
+    sos_filter *f = nullptr;
+    const float *zi = nullptr;
+    float *zf = nullptr;
 };
 
 struct Stream {
@@ -72,7 +76,10 @@ struct sos_server {
     int next_cs = 0;
     bool stop = false;
     int sticky = SOS_OK;            // first error of a batch launch
-    std::thread sched;
+    std::deque<Batch *> to_launch;  // admitted batches, in admission order, for the launcher thread
+    std::condition_variable cv_launch;
+    bool sched_done = false;        // the scheduler has exited; the launcher drains and exits
+    std::thread sched, launcher;
 };
 
 namespace {
@@ -90,18 +97,27 @@ void CUDART_CB batch_done(void *arg) {
     Batch *b = static_cast<Batch *>(arg);
     sos_server *s = b->srv;
     const double t = now_s();
+    // the completion records are built before the lock is taken; under it, one append and the
+    // streams' bookkeeping
+    std::vector<sos_completion> recs(b->reqs.size());
+    int64_t samples = 0;
+    for (size_t i = 0; i < b->reqs.size(); ++i) {
+        const Req &r = b->reqs[i];
+        recs[i] = sos_completion{r.id, r.sid, r.status, r.n, r.t_submit, r.t_start, t};
+        samples += r.n;
+    }
     {
         std::lock_guard<std::mutex> lk(s->mu);
-        for (Req &r : b->reqs) {
-            r.t_done = t;
-            s->done.push_back(sos_completion{r.id, r.sid, r.status, r.n, r.t_submit, r.t_start, r.t_done});
+        s->done.insert(s->done.end(), recs.begin(), recs.end());
+        for (const Req &r : b->reqs) {
             Stream &st = s->streams[r.sid];
             st.busy = false;
             if (!st.q.empty()) s->ready.push_back(r.sid);
-            s->stats.completed += 1;
-            s->stats.samples_done += r.n;
-            s->queued -= 1;
         }
+        const int64_t m = static_cast<int64_t>(b->reqs.size());
+        s->stats.completed += m;
+        s->stats.samples_done += samples;
+        s->queued -= m;
         s->inflight_bytes -= b->bytes;
         s->inflight_batches -= 1;
     }
@@ -110,13 +126,10 @@ void CUDART_CB batch_done(void *arg) {
     delete b;
 }
 
+// Admission: the oldest ready chunks while the budget allows, with each chunk's filter and state
+// copies fixed here (a stream's current copy flips per admitted chunk); the batch then goes to the
+// launcher thread, so that admitting the next batch overlaps with issuing this one.
 void scheduler(sos_server *s) {
-    if (cudaSetDevice(s->device) != cudaSuccess) return;
-    std::vector<sos_filter *> fs;
-    std::vector<const float *> xs, zis;
-    std::vector<float *> ys, zfs;
-    std::vector<int64_t> ns;
-    std::vector<int> sids;  // the batch's streams (the batch itself may be gone once it completes)
     std::unique_lock<std::mutex> lk(s->mu);
     for (;;) {
         if (s->stop && s->queued == 0) break;
@@ -125,17 +138,22 @@ void scheduler(sos_server *s) {
             b = new (std::nothrow) Batch();
             if (b) {
                 b->srv = s;
+                b->reqs.reserve(std::min<size_t>(s->ready.size(), static_cast<size_t>(s->cfg.max_batch)));
                 const double t = now_s();
                 while (!s->ready.empty() && static_cast<int>(b->reqs.size()) < s->cfg.max_batch) {
                     Stream &st = s->streams[s->ready.front()];
                     const int64_t need = req_bytes(st.q.front());
                     if (s->inflight_bytes + b->bytes + need > s->cfg.budget_bytes) break;  // oldest first
-                    Req r = st.q.front();
+                    b->reqs.push_back(st.q.front());
+                    Req &r = b->reqs.back();
                     st.q.pop_front();
                     st.busy = true;
                     r.t_start = t;
+                    r.f = st.f;
+                    r.zi = st.d_state[st.cur];
+                    r.zf = st.d_state[st.cur ^ 1];
+                    st.cur ^= 1;
                     b->bytes += need;
-                    b->reqs.push_back(r);
                     s->ready.pop_front();
                 }
                 if (b->reqs.empty()) {
@@ -153,8 +171,31 @@ void scheduler(sos_server *s) {
             s->cv.wait_for(lk, std::chrono::milliseconds(2));
             continue;
         }
-        // issue the batch outside the lock; the streams of its requests are busy, so nobody else
-        // touches their state copies meanwhile
+        s->to_launch.push_back(b);
+        s->cv_launch.notify_one();
+    }
+    s->sched_done = true;
+    s->cv_launch.notify_one();
+}
+
+// Issue: one batched run per admitted batch, in admission order, on the next of the server's CUDA
+// streams, with a host function behind it for the completions.  The streams of a batch's requests
+// are busy, so nobody else touches their state copies meanwhile.
+void launcher(sos_server *s) {
+    if (cudaSetDevice(s->device) != cudaSuccess) return;
+    std::vector<sos_filter *> fs;
+    std::vector<const float *> xs, zis;
+    std::vector<float *> ys, zfs;
+    std::vector<int64_t> ns;
+    std::unique_lock<std::mutex> lk(s->mu);
+    for (;;) {
+        s->cv_launch.wait(lk, [&] { return !s->to_launch.empty() || s->sched_done; });
+        if (s->to_launch.empty()) break;  // the scheduler has exited and nothing is left
+        Batch *b = s->to_launch.front();
+        s->to_launch.pop_front();
+        cudaStream_t cs = s->cstreams[s->next_cs];
+        s->next_cs = (s->next_cs + 1) % static_cast<int>(s->cstreams.size());
+        lk.unlock();
         const size_t m = b->reqs.size();
         fs.resize(m);
         xs.resize(m);
@@ -162,34 +203,29 @@ void scheduler(sos_server *s) {
         ns.resize(m);
         zis.resize(m);
         zfs.resize(m);
-        sids.resize(m);
         for (size_t i = 0; i < m; ++i) {
-            Req &r = b->reqs[i];
-            Stream &st = s->streams[r.sid];
-            sids[i] = r.sid;
-            fs[i] = st.f;
+            const Req &r = b->reqs[i];
+            fs[i] = r.f;
             xs[i] = r.x;
             ys[i] = r.y;
             ns[i] = r.n;
-            zis[i] = st.d_state[st.cur];
-            zfs[i] = st.d_state[st.cur ^ 1];
-            st.cur ^= 1;
+            zis[i] = r.zi;
+            zfs[i] = r.zf;
         }
-        cudaStream_t cs = s->cstreams[s->next_cs];
-        s->next_cs = (s->next_cs + 1) % static_cast<int>(s->cstreams.size());
-        lk.unlock();
         sos_status st = sos_filter_run_batch_ex(static_cast<int>(m), fs.data(), xs.data(), ys.data(), ns.data(),
                                                 zis.data(), zfs.data(), cs);
-        if (st != SOS_OK)
+        if (st != SOS_OK) {
             for (Req &r : b->reqs) r.status = st;
+            // the batch did not run: its streams keep the state they had before it.  This happens
+            // before the batch can complete, while its streams are still busy, so none of them can
+            // have been admitted again meanwhile.
+            lk.lock();
+            if (s->sticky == SOS_OK) s->sticky = st;
+            for (const Req &r : b->reqs) s->streams[r.sid].cur ^= 1;
+            lk.unlock();
+        }
         const bool queued_ok = cudaLaunchHostFunc(cs, batch_done, b) == cudaSuccess;
         lk.lock();
-        if (st != SOS_OK) {
-            if (s->sticky == SOS_OK) s->sticky = st;
-            // the batch did not run: its streams keep the state they had before it (only this
-            // thread admits chunks, so none of them is in another batch meanwhile)
-            for (int sid : sids) s->streams[sid].cur ^= 1;
-        }
         if (!queued_ok) {  // complete it here so that pollers and the budget are not stuck
             if (s->sticky == SOS_OK) s->sticky = SOS_ECUDA;
             for (Req &r : b->reqs) r.status = SOS_ECUDA;
@@ -225,8 +261,20 @@ sos_status sos_server_create(const sos_server_config *cfg, sos_server **out) {
             return SOS_ECUDA;
         }
     try {
+        s->launcher = std::thread(launcher, s);
+    } catch (...) {
+        delete s;
+        return SOS_ENOMEM;
+    }
+    try {
         s->sched = std::thread(scheduler, s);
     } catch (...) {
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->sched_done = true;
+        }
+        s->cv_launch.notify_one();
+        s->launcher.join();
         delete s;
         return SOS_ENOMEM;
     }
@@ -242,6 +290,7 @@ sos_status sos_server_destroy(sos_server *s) {
     }
     s->cv.notify_all();
     if (s->sched.joinable()) s->sched.join();
+    if (s->launcher.joinable()) s->launcher.join();
     cudaSetDevice(s->device);
     for (auto &c : s->cstreams) cudaStreamSynchronize(c);
     // the filters before the CUDA streams their last batches ran on
