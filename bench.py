@@ -41,17 +41,21 @@ CPU_SAMPLE = 1 << 24  # oracle sample per step of the reference arm
 # an ncu capture of the same kernel on 2^26 samples scaled by 4.  An entry must be re-captured (or
 # removed) whenever its kernel changes.
 TRAFFIC_BYTES_2P28 = {}
-SOLVER_CR, SOLVER_PH = 1, 2
+SOLVER_CR, SOLVER_PH, SOLVER_DTCR = 1, 2, 3
 PH_GROUPS_PER_BLOCK = 7
 CR_GROUPS_PER_BLOCK = {32: 8, 64: 4}
 
 
-def kernel_name(solver: int, N: int, K: int) -> str:
-    """The kernel a run launches, by solver, samples per lane and sections per pass."""
+def kernel_name(solver: int, N: int, K: int, W: int = 0) -> str:
+    """The kernel a run launches, by solver, samples per lane, sections per pass and groups per tile."""
     k = min(K, 8)
     if solver == SOLVER_PH:
-        return (f"sos_lane_kernel<{k}, {N}> (PH factorization, {k} sections, N = {N} samples per lane, "
-                f"{PH_GROUPS_PER_BLOCK} groups per block)")
+        w = W or PH_GROUPS_PER_BLOCK
+        return (f"sos_lane_kernel<{k}, {N}, {w}> (PH factorization, {k} sections, N = {N} samples per lane, "
+                f"{w} groups per block)")
+    if solver == SOLVER_DTCR:
+        return (f"sos_dtcr_kernel<{k}, 64> (double-thread-group cyclic reduction, {k} sections, N = 64 samples per "
+                "lane, 4 groups of two warps per block)")
     return (f"sos_cascade_kernel<{k}, {N}> (cyclic reduction, {k} sections, N = {N} samples per lane, "
             f"{CR_GROUPS_PER_BLOCK.get(N, '?')} groups per block)")
 
@@ -268,11 +272,11 @@ def fp32_fma_roof(torch, dev, sm_max_mhz):
 
 
 def chosen_kernel(K: int, n: int):
-    """(solver, N) that a default-tuned filter of K sections runs on n samples: the autotuner's choice
-    when it has run in this process, else the library default (PH at N = 64)."""
+    """(solver, N, groups per tile) that a default-tuned filter of K sections runs on n samples: the
+    autotuner's choice when it has run in this process, else the library default (PH at N = 64, 7)."""
     from paper_2607_23763_gb300 import autotune_choice
-    c = autotune_choice(K, n)
-    return tuple(c) if c != (0, 0) else (SOLVER_PH, 64)
+    c = autotune_choice(K, n, with_groups=True)
+    return tuple(c) if c[:2] != (0, 0) else (SOLVER_PH, 64, PH_GROUPS_PER_BLOCK)
 
 
 def plain_rate(torch, sos, x, y, steps: int, warmup: int, tuning=None) -> float:
@@ -304,7 +308,8 @@ def order2_plateau_leg(torch, dev, steps: int, warmup: int):
     del x, y
     ms_mean = 0.5 * (pts["2^29"]["ms_per_launch"] / 2 + pts["2^30"]["ms_per_launch"] / 4)  # per 2^28 samples
     value = 0.5 * (pts["2^29"]["value"] + pts["2^30"]["value"])
-    roof = hbm_roofline(1 << 28, ms_mean, kernel_name(*chosen_kernel(1, 1 << 30), 1))
+    sv, nv, wv = chosen_kernel(1, 1 << 30)
+    roof = hbm_roofline(1 << 28, ms_mean, kernel_name(sv, nv, 1, wv))
     roof["achieved"] = value * BYTES_PER_SAMPLE  # mean of the two points' GB/s
     roof["frac"] = roof["achieved"] / roof["peak"]
     return {"workload": "order-2 Butterworth lowpass (1 SOS) at 0.2 Nyquist, 1 float32 signal of N(0,1) samples, "
@@ -336,13 +341,14 @@ def config1_leg(torch, dev, launches: int = 256, pool: int = 64):
                         "samples, seed 0, zero state",
             "value": n / ms / 1e6, "unit": "GS/s", "ms_per_launch": ms,
             "l2": f"{pool} input/output pairs of 2^20 samples cycled ({pool * 8} MiB, more than 4x L2)",
-            "launches": launches, "roofline": hbm_roofline(n, ms, kernel_name(*chosen_kernel(1, n), 1)),
+            "launches": launches, "roofline": hbm_roofline(n, ms, kernel_name(chosen_kernel(1, n)[0], chosen_kernel(1, n)[1], 1, chosen_kernel(1, n)[2])),
             "accuracy": {"max_rel_error": err, "bound": designs.tolerance_for(sos)}}
 
 
 def cr_solver_leg(torch, dev, x16, y16, steps: int, warmup: int, fma_peak):
     """The divide-and-conquer cyclic-reduction solver (Sec. II-D/E) on the order-16 workload and on
-    the order-2 filter, 2^28 samples each, at its default N."""
+    the order-2 filter, 2^28 samples each, at its default N, single-warp (STCR) and double-thread-group
+    (DTCR, Sec. IV-E)."""
     import workloads
     from workloads import designs
     out = {}
@@ -353,15 +359,16 @@ def cr_solver_leg(torch, dev, x16, y16, steps: int, warmup: int, fma_peak):
             y = torch.empty_like(x)
         K = order // 2
         N = 64 if K == 1 else 32  # the library's default N of cyclic reduction
-        ms = plain_rate(torch, sos, x, y, steps, warmup, tuning={"solver": SOLVER_CR})
         n = x.numel()
         fma = 10 * K
-        out[f"order{order}"] = {"value": n / ms / 1e6, "unit": "GS/s", "ms_per_launch": ms, "N": N,
-                                "roofline": hbm_roofline(n, ms, kernel_name(SOLVER_CR, N, K)),
-                                "roofline_alu": {"bound": "alu", "achieved": fma * n / (ms * 1e-3) / 1e12,
-                                                 "peak": fma_peak, "unit": "TFMA/s",
-                                                 "frac": fma * n / (ms * 1e-3) / 1e12 / fma_peak,
-                                                 "fma_per_sample": fma}}
+        for solver, tag, NN in ((SOLVER_CR, "", N), (SOLVER_DTCR, "dtcr_", 64)):
+            ms = plain_rate(torch, sos, x, y, steps, warmup, tuning={"solver": solver})
+            out[f"{tag}order{order}"] = {
+                "value": n / ms / 1e6, "unit": "GS/s", "ms_per_launch": ms, "N": NN,
+                "roofline": hbm_roofline(n, ms, kernel_name(solver, NN, K)),
+                "roofline_alu": {"bound": "alu", "achieved": fma * n / (ms * 1e-3) / 1e12, "peak": fma_peak,
+                                 "unit": "TFMA/s", "frac": fma * n / (ms * 1e-3) / 1e12 / fma_peak,
+                                 "fma_per_sample": fma}}
     return out
 
 
@@ -394,13 +401,14 @@ def bench_ours(args):
     sos = designs.butter_lowpass(ORDER, WN)
     x_host = workloads.normal_f32(SEED, N_SAMPLES)
     choice = None
-    if not args.no_autotune and not (args.N or args.carry or args.solver or args.lbw or args.deterministic):
+    if not args.no_autotune and not (args.N or args.carry or args.solver or args.lbw or args.deterministic or
+                                     args.groups):
         # the library's autotuner picks the launch configuration per order and length (outside the
         # timed region); the filter below, with default tuning, then runs its choice
         from paper_2607_23763_gb300 import autotune, autotune_choice
         autotune()
-        choice = autotune_choice(ORDER // 2, N_SAMPLES)
-        if choice == (0, 0):
+        choice = autotune_choice(ORDER // 2, N_SAMPLES, with_groups=True)
+        if choice[:2] == (0, 0):
             choice = None
     tuning = {}
     if args.N:
@@ -413,6 +421,8 @@ def bench_ours(args):
         tuning["solver"] = args.solver
     if args.deterministic:
         tuning["deterministic"] = 1
+    if args.groups:
+        tuning["groups_per_cta"] = args.groups
     tuning = tuning or None
     f = SosFilter(sos, tuning=tuning)
     x = torch.from_numpy(x_host).to(dev)
@@ -484,11 +494,11 @@ def bench_ours(args):
     if choice:
         kid = tuple(choice)
     elif args.solver:
-        kid = (args.solver, args.N or (64 if args.solver == SOLVER_PH else 32))
+        kid = (args.solver, args.N or (64 if args.solver in (SOLVER_PH, SOLVER_DTCR) else 32), args.groups)
     elif args.carry or args.lbw:
-        kid = (SOLVER_CR, args.N or 32)
+        kid = (SOLVER_CR, args.N or 32, 0)
     else:
-        kid = (SOLVER_PH, args.N or 64)
+        kid = (SOLVER_PH, args.N or 64, args.groups)
     K = ORDER // 2
     clocks = clk.summary()
     # the FP32 roof the method meets first at high order: its FMAs per sample (PH: 4K for the
@@ -496,19 +506,20 @@ def bench_ours(args):
     fma_per_sample = 6 * K if kid[0] == SOLVER_PH else 10 * K
     fma_peak, fma_kind = fp32_fma_roof(torch, dev, clocks.get("sm_max_mhz"))
     alu_achieved = fma_per_sample * N_SAMPLES / (ms_step * 1e-3) / 1e12
-    traffic = (TRAFFIC_BYTES_2P28.get(kid) if (N_SAMPLES == 1 << 28 and ORDER == 16 and not args.lbw
+    traffic = (TRAFFIC_BYTES_2P28.get(kid[:2]) if (N_SAMPLES == 1 << 28 and ORDER == 16 and not args.lbw
                                                and args.carry != 2) else None)
     line = {
         "metric": "GS/s", "value": gss, "unit": "GS/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "samples": N_SAMPLES, "sections": K,
-                   "N": kid[1], "L": 32, "solver": "PH" if kid[0] == SOLVER_PH else "CR",
+                   "N": kid[1], "L": 32, "groups_per_cta": kid[2] or None,
+                   "solver": {SOLVER_PH: "PH", SOLVER_CR: "CR", SOLVER_DTCR: "DTCR"}[kid[0]],
                    "deterministic": bool(args.deterministic),
                    "autotuned": choice is not None,
                    "l2": "inputs and outputs larger than L2 (1 GiB each)",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
-        "roofline": hbm_roofline(N_SAMPLES, ms_step, kernel_name(kid[0], kid[1], K), traffic),
+        "roofline": hbm_roofline(N_SAMPLES, ms_step, kernel_name(kid[0], kid[1], K, kid[2]), traffic),
         "roofline_alu": {"bound": "alu", "achieved": alu_achieved, "peak": fma_peak, "unit": "TFMA/s",
                          "frac": alu_achieved / fma_peak, "fma_per_sample": fma_per_sample, "peak_kind": fma_kind},
         "e2e": {"value": e_direct["value"] if use_direct else e_gss, "unit": "GS/s",
@@ -834,6 +845,7 @@ def main():
     ap.add_argument("--deterministic", action="store_true",
                     help="fixed lookback composition (bit-reproducible outputs; PH solver)")
     ap.add_argument("--lbw", type=int, default=0, help="lookback width (predecessor blocks per round / 32); 0 = default")
+    ap.add_argument("--groups", type=int, default=0, help="PH groups per tile (7, or 10 at N = 64); 0 = default")
     ap.add_argument("--order", type=int, default=16, help="filter order (16 = the workload; others for sweeps)")
     ap.add_argument("--log2n", type=int, default=28,
                     help="signal length 2^log2n (28 = the workload; smaller only for profiling captures)")

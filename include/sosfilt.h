@@ -73,11 +73,15 @@ enum {
                                tuning sets a carry scheme, a lookback width or N = 128 */
     SOS_SOLVER_CR = 1,      /* divide-and-conquer cyclic reduction per section (Sec. II-D, II-E,
                                Eqs. 14-23); both carry schemes */
-    SOS_SOLVER_PH = 2       /* PH factorization (Sec. II-C): per-lane particular solutions from zero
+    SOS_SOLVER_PH = 2,      /* PH factorization (Sec. II-C): per-lane particular solutions from zero
                                state (the sections skewed one sample apart so that their updates
                                are independent), a lane scan of the whole cascade state and one
                                homogeneous correction for lane and group states; cascade carry
                                only, N = 32 or 64 (default 64) */
+    SOS_SOLVER_DTCR = 3     /* double-thread-group cyclic reduction (Sec. IV-E): cyclic reduction
+                               with the even- and odd-parity chains of every group on two warps,
+                               exchanging through shared memory at each section (two barriers per
+                               section); cascade carry only, N = 64 (tiles of four groups) */
 };
 
 /*
@@ -86,8 +90,12 @@ enum {
  *   N                  samples per thread (block count of Eq. 2): 32 or 64 for
  *                      the cascade carry; 32, 64 or 128 for per-section carries
  *   L                  threads per group (block length of Eq. 2): 32
- *   groups_per_cta     reserved, must be 0 (the library picks the groups per thread
- *                      block from N and the carry scheme)
+ *   groups_per_cta     groups (compute warps, one per group) per thread block and tile:
+ *                      0 = the library's choice (the autotuner's, else 7 for PH and the
+ *                      carry scheme's fixed count for cyclic reduction); the PH solver
+ *                      also takes 7, or 10 at N = 64 (11 warps per block: three warps on
+ *                      most SM schedulers instead of two, a two-sample-wide correction
+ *                      to stay within 168 registers); any other solver: 0
  *   threads_per_group  L (one thread group per signal block group, Sec. IV-D)
  *   fp64_carry         reserved: must be 0 (carries are float32)
  *   spin_budget_cycles upper bound, in SM clock cycles, on one lookback wait;
@@ -96,17 +104,18 @@ enum {
  *                      round, in units of 32: 1, 2, 4, 8 or 16 (values other than
  *                      the default for N exist for 8-section passes with b0 != 0)
  *   carry              SOS_CARRY_DEFAULT, SOS_CARRY_CASCADE or SOS_CARRY_SECTION
- *   solver             SOS_SOLVER_DEFAULT, SOS_SOLVER_CR or SOS_SOLVER_PH (see SOS_SOLVER_*);
- *                      SOS_SOLVER_PH takes N = 0, 32 or 64, carry SOS_CARRY_DEFAULT or
- *                      SOS_CARRY_CASCADE and lookback_width 0
+ *   solver             SOS_SOLVER_DEFAULT, SOS_SOLVER_CR, SOS_SOLVER_PH or SOS_SOLVER_DTCR (see
+ *                      SOS_SOLVER_*); SOS_SOLVER_PH takes N = 0, 32 or 64, SOS_SOLVER_DTCR N = 0 or 64,
+ *                      both carry SOS_CARRY_DEFAULT or SOS_CARRY_CASCADE and lookback_width 0
  *   deterministic      0 or 1.  The PH solver (and batched runs) always compose a tile's
  *                      incoming state the same way -- the resolved carry of a fixed anchor tile
  *                      (the last multiple of 32 before it) and the local carries after it -- so
  *                      their outputs are bit-identical from run to run.  Cyclic reduction composes
  *                      from whichever predecessor's resolved carry its lookback meets first (Sec.
  *                      IV-B) and may differ in the last ulps; 1 requests reproducible results and
- *                      is rejected with SOS_EINVAL together with solver SOS_SOLVER_CR, a carry
- *                      other than SOS_CARRY_DEFAULT, a lookback width or N = 128.
+ *                      is rejected with SOS_EINVAL together with solver SOS_SOLVER_CR or
+ *                      SOS_SOLVER_DTCR, a carry other than SOS_CARRY_DEFAULT, a lookback width or
+ *                      N = 128.
  */
 typedef struct {
     int N, L, groups_per_cta, threads_per_group, fp64_carry;
@@ -386,21 +395,27 @@ sos_status sos_server_replay(sos_server *s, int64_t n_req, const int32_t *stream
 /*
  * Autotuner: on the current device, time each candidate launch configuration
  * -- divide-and-conquer cyclic reduction with the cascade carry at N = 32 (8
- * groups per tile) or N = 64 (4 groups per tile), and PH factorization at
- * N = 64 (7 groups per tile); L = 32 threads per group throughout -- for 1 to
- * 8 sections and lengths 2^16, 2^20, 2^24 and 2^28 (up to 2^max_log2n,
- * 0 = 28), and keep the fastest per (section count, length).  Afterwards every
- * run of a filter created with default tuning (all fields 0) uses the choice
- * for its section count and the nearest length.  Synchronous; allocates and
- * frees 2^(max_log2n + 3) bytes of device memory; about a second.
- *   report  NULL, or host float[8][4][3] receiving the measured GS/s
- *           (sections, length 2^16..2^28, candidate CR32/CR64/PH)
+ * groups per tile) or N = 64 (4 groups per tile), PH factorization at N = 64
+ * with 7 or 10 groups per tile, and double-thread-group cyclic reduction at N = 64
+ * (4 groups of two warps per tile); L = 32 threads per group (thread group)
+ * throughout -- for 1 to 8 sections and lengths 2^16, 2^20, 2^24 and 2^28 (up to
+ * 2^max_log2n, 0 = 28), and keep the fastest per (section count, length).
+ * Afterwards every run of a filter created with default tuning (all fields 0)
+ * uses the choice for its section count and the nearest length.  Synchronous;
+ * allocates and frees 2^(max_log2n + 3) bytes of device memory; a second or two.
+ *   report  NULL, or host float[8][4][5] receiving the measured GS/s
+ *           (sections, length 2^16..2^28, candidate CR32/CR64/PH/DTCR/PH with
+ *           10 groups per tile)
  */
 sos_status sos_autotune(int max_log2n, float *report);
 
 /* The autotuned choice for K sections and n samples on the current device:
- * solver (SOS_SOLVER_CR / SOS_SOLVER_PH) and N; both 0 if no autotuning ran. */
+ * solver (SOS_SOLVER_CR / SOS_SOLVER_PH / SOS_SOLVER_DTCR) and N; both 0 if no
+ * autotuning ran. */
 sos_status sos_autotune_choice(int n_sections, int64_t n, int *solver, int *N);
+/* The same with the groups per tile of a PH choice (7 or 10; 0 for the other solvers) in
+ * *groups_per_cta (may be NULL). */
+sos_status sos_autotune_choice_ex(int n_sections, int64_t n, int *solver, int *N, int *groups_per_cta);
 
 /* Human-readable name of a status code (static storage). */
 const char *sos_status_string(sos_status s);

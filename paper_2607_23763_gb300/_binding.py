@@ -27,7 +27,7 @@ EXPORTED = (
     "sos_filter_run_host", "sos_filter_run_noalloc", "sos_filter_run_batch_ex", "sos_batch_sync_status",
     "sos_server_create", "sos_server_destroy", "sos_server_add_stream", "sos_server_submit", "sos_server_poll",
     "sos_server_drain", "sos_server_stream_state", "sos_server_get_stats", "sos_server_replay",
-    "sos_autotune", "sos_autotune_choice", "sos_batch_plan_create", "sos_batch_plan_launch",
+    "sos_autotune", "sos_autotune_choice", "sos_autotune_choice_ex", "sos_batch_plan_create", "sos_batch_plan_launch",
     "sos_batch_plan_status", "sos_batch_plan_destroy", "sos_status_string",
 )
 
@@ -47,7 +47,7 @@ class Tuning(ctypes.Structure):
 
 CARRY_DEFAULT, CARRY_CASCADE, CARRY_SECTION = 0, 1, 2
 HOST_DIRECT = -1  # sos_filter_run_host: the kernels read and write the pinned host buffers in place
-SOLVER_DEFAULT, SOLVER_CR, SOLVER_PH = 0, 1, 2
+SOLVER_DEFAULT, SOLVER_CR, SOLVER_PH, SOLVER_DTCR = 0, 1, 2, 3
 
 
 _lib = None
@@ -86,6 +86,8 @@ def load_library(path: str | None = None):
         lib.sos_batch_plan_status.argtypes = [vp]
         lib.sos_batch_plan_destroy.argtypes = [vp]
         lib.sos_autotune_choice.argtypes = [c_int, i64, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]
+        lib.sos_autotune_choice_ex.argtypes = [c_int, i64, ctypes.POINTER(c_int), ctypes.POINTER(c_int),
+                                               ctypes.POINTER(c_int)]
         lib.sos_filter_stream_push.argtypes = [vp, vp, vp, i64, vp]
         lib.sos_filter_stream_state.argtypes = [vp, vp, vp, c_int]
         lib.sos_filter_sync_status.argtypes = [vp]
@@ -379,18 +381,20 @@ class SosServer:
 
 def autotune(max_log2n: int = 0) -> np.ndarray:
     """Time the candidate launch configurations on the current device and keep the fastest per
-    (section count, length); returns the measured GS/s as [8 sections][4 lengths][CR32, CR64, PH]."""
-    rep = np.zeros((8, 4, 3), dtype=np.float32)
+    (section count, length); returns the measured GS/s as [8 sections][4 lengths][CR32, CR64, PH, DTCR,
+    PH with 10 groups per tile]."""
+    rep = np.zeros((8, 4, 5), dtype=np.float32)
     _check(load_library().sos_autotune(int(max_log2n), rep.ctypes.data), "sos_autotune")
     return rep
 
 
-def autotune_choice(n_sections: int, n: int):
-    """(solver, N) the autotuner picked for this section count and length; (0, 0) if none."""
-    s, N = ctypes.c_int(), ctypes.c_int()
-    _check(load_library().sos_autotune_choice(int(n_sections), int(n), ctypes.byref(s), ctypes.byref(N)),
-           "sos_autotune_choice")
-    return s.value, N.value
+def autotune_choice(n_sections: int, n: int, with_groups: bool = False):
+    """(solver, N) the autotuner picked for this section count and length; (0, 0) if none.  With
+    with_groups, (solver, N, groups per tile)."""
+    s, N, W = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load_library().sos_autotune_choice_ex(int(n_sections), int(n), ctypes.byref(s), ctypes.byref(N),
+                                                 ctypes.byref(W)), "sos_autotune_choice_ex")
+    return (s.value, N.value, W.value) if with_groups else (s.value, N.value)
 
 
 class BatchPlan:

@@ -30,8 +30,11 @@ int lane_blocks_per_sm_n32a(int K, bool norm);
 int lane_blocks_per_sm_n32b(int K, bool norm);
 int lane_blocks_per_sm_n64a(int K, bool norm);
 int lane_blocks_per_sm_n64b(int K, bool norm);
-int lane_blocks_per_sm(int K, int N, bool norm) {
+int lane_blocks_per_sm_n64w10a(int K, bool norm);
+int lane_blocks_per_sm_n64w10b(int K, bool norm);
+int lane_blocks_per_sm(int K, int N, int W, bool norm) {
     if (N == 32) return K <= 4 ? lane_blocks_per_sm_n32a(K, norm) : lane_blocks_per_sm_n32b(K, norm);
+    if (W == kLaneWide) return K <= 4 ? lane_blocks_per_sm_n64w10a(K, norm) : lane_blocks_per_sm_n64w10b(K, norm);
     return K <= 4 ? lane_blocks_per_sm_n64a(K, norm) : lane_blocks_per_sm_n64b(K, norm);
 }
 }  // namespace sosk
@@ -135,7 +138,7 @@ struct CasTables {
 
 // One pass (<= 8 sections) of the skewed-pass PH kernel (sosfilt_lane.cuh) for one N.
 struct LanePass {
-    int k0 = 0, kp = 0, N = 0;
+    int k0 = 0, kp = 0, N = 0, W = 0;  // sections k0 .. k0 + kp - 1; N samples per lane, W groups per tile
     std::vector<double> coef;        // [kp][5] as the kernel applies them
     DMat M1;                         // one-sample zero-input transition of the pass's cascade state
     std::vector<sosk::LaneSec> sec;  // [kp]
@@ -175,7 +178,7 @@ struct sos_filter {
     sos_tuning tuning{};
     NTables tables[kNumN];
     CasTables cas[2];  // N = 32, 64
-    std::vector<LanePass> lane[2];  // skewed-pass PH kernel, N = 32 and N = 64
+    std::vector<LanePass> lane[3];  // skewed-pass PH kernel: (N, W) = (32, 7), (64, 7), (64, 10)
     // workspace
     unsigned long long *d_desc = nullptr;
     size_t desc_groups = 0;  // capacity in groups (per section slot)
@@ -443,13 +446,13 @@ sos_status build_cascade(sos_filter *f, int N, CasTables &ct) {
 // Tables of the skewed-pass PH kernel for one N (32 or 64), in float64, uploaded once.  Layout of
 // the device block as LaneDims<kp, N>: (M_N)^lane [32][stride], (A_T)^lane [32][stride] (packed),
 // A_C dense column-major, the output basis [2 kp][N], A_T dense.
-sos_status build_lane(sos_filter *f, int N, std::vector<LanePass> &out) {
-    constexpr int W = sosk::kLaneW;
+sos_status build_lane(sos_filter *f, int N, int W, std::vector<LanePass> &out) {
     out.clear();
     for (int k0 = 0; k0 < f->K; k0 += sosk::kMaxPass) {
         LanePass ps;
         ps.k0 = k0;
         ps.N = N;
+        ps.W = W;
         ps.kp = (f->K - k0) < sosk::kMaxPass ? (f->K - k0) : sosk::kMaxPass;
         const int kp = ps.kp, S = 2 * kp;
         ps.coef.resize(5 * kp);
@@ -531,7 +534,7 @@ sos_status build_lane(sos_filter *f, int N, std::vector<LanePass> &out) {
             pack_into(Pm, kp, &ps.Mm[static_cast<size_t>(m) * nf]);
             Pm = dmul(Pm, ps.M1);
         }
-        if (N == sosk::kBatchN) {
+        if (N == sosk::kBatchN && W == sosk::kBatchW) {
             const std::vector<float> &mm = ps.Mm;
             if (cudaMalloc(&ps.d_sec, sizeof(sosk::LaneSec) * kp) != cudaSuccess ||
                 cudaMalloc(&ps.d_MX, sizeof(float) * ps.MX.size()) != cudaSuccess ||
@@ -658,7 +661,7 @@ int sm_count(int device) {
 template <int K, int N>
 sos_status launch_cascade_pass(sos_filter *f, CasPass &ps, const sosk::SecCoef *sec, const float *x, float *y,
                                long long n, long long G, long long n_tiles, long long grid, const float *zi,
-                               float *zf, bool first, bool aligned, cudaStream_t s) {
+                               float *zf, bool first, bool aligned, cudaStream_t s, bool dtcr = false) {
     static_assert(K >= 1 && K <= sosk::kMaxPass, "pass size");
     auto p = std::make_unique<sosk::CasParams<K, N>>();
     std::memset(p.get(), 0, sizeof(*p));
@@ -693,7 +696,11 @@ sos_status launch_cascade_pass(sos_filter *f, CasPass &ps, const sosk::SecCoef *
         }
         std::memcpy(p->A_tail, ps.A_tail.data(), sizeof(float) * packed_floats(K));
     }
-    cudaError_t e = sosk::launch_cascade<K, N>(f->norm, *p, grid, s);
+    cudaError_t e;
+    if constexpr (N == 64)
+        e = dtcr ? sosk::launch_dtcr<K>(f->norm, *p, grid, s) : sosk::launch_cascade<K, N>(f->norm, *p, grid, s);
+    else
+        e = sosk::launch_cascade<K, N>(f->norm, *p, grid, s);
     if (e != cudaSuccess) return SOS_ECUDA;
     f->ticket_base += static_cast<unsigned long long>(n_tiles + grid);
     return SOS_OK;
@@ -702,10 +709,10 @@ sos_status launch_cascade_pass(sos_filter *f, CasPass &ps, const sosk::SecCoef *
 template <int N>
 sos_status launch_cascade_any(int K, sos_filter *f, CasPass &ps, const sosk::SecCoef *sec, const float *x, float *y,
                               long long n, long long G, long long n_tiles, long long grid, const float *zi, float *zf,
-                              bool first, bool aligned, cudaStream_t s) {
+                              bool first, bool aligned, cudaStream_t s, bool dtcr = false) {
     switch (K) {
 #define SOSK_CASE(k) \
-    case k: return launch_cascade_pass<k, N>(f, ps, sec, x, y, n, G, n_tiles, grid, zi, zf, first, aligned, s);
+    case k: return launch_cascade_pass<k, N>(f, ps, sec, x, y, n, G, n_tiles, grid, zi, zf, first, aligned, s, dtcr);
         SOSK_CASE(1) SOSK_CASE(2) SOSK_CASE(3) SOSK_CASE(4) SOSK_CASE(5) SOSK_CASE(6) SOSK_CASE(7) SOSK_CASE(8)
 #undef SOSK_CASE
         default: return SOS_EINVAL;
@@ -748,8 +755,35 @@ sos_status run_cascade(sos_filter *f, const float *x, float *y, int64_t n, const
     return SOS_OK;
 }
 
+// Double-thread-group cyclic reduction (sosfilt_dtcr.cuh): the cascade carry on the N = 64
+// cyclic-reduction tables, two warps (one per parity) per group.
+sos_status run_dtcr(sos_filter *f, const float *x, float *y, int64_t n, const float *zi, float *zf, cudaStream_t s) {
+    constexpr int N = 64;
+    const int ti = table_index(N);
+    const long long C = 32LL * N;
+    const long long W = sosk::cascade_warps(N);
+    const long long G = (n + C - 1) / C;
+    const long long n_tiles = (G + W - 1) / W;
+    sos_status st = ensure_desc(f, G, s);
+    if (st != SOS_OK) return st;
+    const bool aligned = (reinterpret_cast<uintptr_t>(x) % 16 == 0) && (reinterpret_cast<uintptr_t>(y) % 16 == 0);
+    const float *src = x;
+    for (auto &ps : f->cas[1].passes) {
+        const int bps = sosk::dtcr_blocks_per_sm(ps.kp, f->norm);
+        if (bps <= 0) return SOS_ECUDA;
+        long long grid = static_cast<long long>(bps) * sm_count(f->device);
+        if (grid > n_tiles) grid = n_tiles;
+        st = launch_cascade_any<64>(ps.kp, f, ps, &f->tables[ti].sec[ps.k0], src, y, n, G, n_tiles, grid,
+                                    zi ? zi + 2 * ps.k0 : nullptr, zf ? zf + 2 * ps.k0 : nullptr, ps.k0 == 0, aligned, s,
+                                    true);
+        if (st != SOS_OK) return st;
+        src = y;
+    }
+    return SOS_OK;
+}
+
 // ---- skewed-pass PH kernel (sosfilt_lane.cuh)
-template <int K, int N>
+template <int K, int N, int W>
 sos_status launch_lane_pass(sos_filter *f, LanePass &ps, const float *x, float *y, long long n, long long G,
                             long long n_tiles, long long grid, const float *zi, float *zf, bool first, bool aligned,
                             cudaStream_t s, const sosk::Scratch *sc = nullptr, unsigned sc_epoch = 0) {
@@ -796,19 +830,19 @@ sos_status launch_lane_pass(sos_filter *f, LanePass &ps, const float *x, float *
     const int m_last = static_cast<int>((n - 1 - (G - 1) * C) % N);
     p->m_last = m_last;
     if (zf) std::memcpy(p->A_tail, &ps.Mm[static_cast<size_t>(m_last) * packed_floats(K)], sizeof(float) * packed_floats(K));
-    cudaError_t e = sosk::launch_lane<K, N>(f->norm, *p, grid, s);
+    cudaError_t e = sosk::launch_lane<K, N, W>(f->norm, *p, grid, s);
     if (e != cudaSuccess) return SOS_ECUDA;
     if (!sc) f->ticket_base += static_cast<unsigned long long>(n_tiles + grid);
     return SOS_OK;
 }
 
-template <int N>
+template <int N, int W>
 sos_status launch_lane_any(int K, sos_filter *f, LanePass &ps, const float *x, float *y, long long n, long long G,
                            long long n_tiles, long long grid, const float *zi, float *zf, bool first, bool aligned,
                            cudaStream_t s, const sosk::Scratch *sc = nullptr, unsigned sc_epoch = 0) {
     switch (K) {
 #define SOSK_CASE(k) \
-    case k: return launch_lane_pass<k, N>(f, ps, x, y, n, G, n_tiles, grid, zi, zf, first, aligned, s, sc, sc_epoch);
+    case k: return launch_lane_pass<k, N, W>(f, ps, x, y, n, G, n_tiles, grid, zi, zf, first, aligned, s, sc, sc_epoch);
         SOSK_CASE(1) SOSK_CASE(2) SOSK_CASE(3) SOSK_CASE(4) SOSK_CASE(5) SOSK_CASE(6) SOSK_CASE(7) SOSK_CASE(8)
 #undef SOSK_CASE
         default: return SOS_EINVAL;
@@ -818,12 +852,15 @@ sos_status launch_lane_any(int K, sos_filter *f, LanePass &ps, const float *x, f
 // PH factorization with the skewed particular pass, one carry per tile for the whole cascade,
 // persistent grid.
 sos_status run_lane(sos_filter *f, const float *x, float *y, int64_t n, const float *zi, float *zf, cudaStream_t s,
-                    int N_choice = 0) {
+                    int N_choice = 0, int W_choice = 0) {
     const int N = f->tuning.N ? f->tuning.N : N_choice ? N_choice : 64;
     if (N != 32 && N != 64) return SOS_EINVAL;
-    auto &passes = f->lane[N == 32 ? 0 : 1];
+    const int Wv = N == 32 ? sosk::kLaneW
+                           : f->tuning.groups_per_cta ? f->tuning.groups_per_cta : W_choice ? W_choice : sosk::kLaneW;
+    if (Wv != sosk::kLaneW && Wv != sosk::kLaneWide) return SOS_EINVAL;
+    auto &passes = f->lane[N == 32 ? 0 : Wv == sosk::kLaneWide ? 2 : 1];
     const long long C = 32LL * N;
-    const long long W = sosk::kLaneW;
+    const long long W = Wv;
     const long long G = (n + C - 1) / C;
     const long long n_tiles = (G + W - 1) / W;
     sos_status st = ensure_desc(f, G, s);
@@ -831,16 +868,21 @@ sos_status run_lane(sos_filter *f, const float *x, float *y, int64_t n, const fl
     const bool aligned = (reinterpret_cast<uintptr_t>(x) % 16 == 0) && (reinterpret_cast<uintptr_t>(y) % 16 == 0);
     const float *src = x;
     for (auto &ps : passes) {
-        const int bps = sosk::lane_blocks_per_sm(ps.kp, N, f->norm);
+        const int bps = sosk::lane_blocks_per_sm(ps.kp, N, Wv, f->norm);
         if (bps <= 0) return SOS_ECUDA;
         long long grid = static_cast<long long>(bps) * sm_count(f->device);
         if (grid > n_tiles) grid = n_tiles;
+        const float *zp = zi ? zi + 2 * ps.k0 : nullptr;
+        float *zq = zf ? zf + 2 * ps.k0 : nullptr;
         if (N == 32)
-            st = launch_lane_any<32>(ps.kp, f, ps, src, y, n, G, n_tiles, grid, zi ? zi + 2 * ps.k0 : nullptr,
-                                     zf ? zf + 2 * ps.k0 : nullptr, ps.k0 == 0, aligned, s);
+            st = launch_lane_any<32, sosk::kLaneW>(ps.kp, f, ps, src, y, n, G, n_tiles, grid, zp, zq, ps.k0 == 0,
+                                                   aligned, s);
+        else if (Wv == sosk::kLaneWide)
+            st = launch_lane_any<64, sosk::kLaneWide>(ps.kp, f, ps, src, y, n, G, n_tiles, grid, zp, zq, ps.k0 == 0,
+                                                      aligned, s);
         else
-            st = launch_lane_any<64>(ps.kp, f, ps, src, y, n, G, n_tiles, grid, zi ? zi + 2 * ps.k0 : nullptr,
-                                     zf ? zf + 2 * ps.k0 : nullptr, ps.k0 == 0, aligned, s);
+            st = launch_lane_any<64, sosk::kLaneW>(ps.kp, f, ps, src, y, n, G, n_tiles, grid, zp, zq, ps.k0 == 0,
+                                                   aligned, s);
         if (st != SOS_OK) return st;
         src = y;
     }
@@ -861,7 +903,7 @@ int solver_of(const sos_filter *f) {
 // ---- autotuned launch choice (sos_autotune): per device, section count (1..8) and length bucket
 constexpr int kTuneBuckets = 4;                       // n around 2^16, 2^20, 2^24, 2^28
 constexpr int kTuneLog2[kTuneBuckets] = {16, 20, 24, 28};
-constexpr int kTuneCand = 3;                          // candidates: CR N = 32, CR N = 64, PH
+constexpr int kTuneCand = 5;  // candidates: CR N = 32, CR N = 64, PH (7 groups), DTCR, PH (10 groups)
 struct TuneTable {
     bool valid = false;
     unsigned char best[8][kTuneBuckets] = {};         // candidate index
@@ -870,9 +912,10 @@ struct TuneTable {
 std::mutex g_tune_mu;
 TuneTable g_tune[64];
 
-void candidate(int c, int *solver, int *N) {
-    *solver = c == 2 ? SOS_SOLVER_PH : SOS_SOLVER_CR;
+void candidate(int c, int *solver, int *N, int *W) {
+    *solver = (c == 2 || c == 4) ? SOS_SOLVER_PH : c == 3 ? SOS_SOLVER_DTCR : SOS_SOLVER_CR;
     *N = c == 0 ? 32 : 64;
+    *W = c == 4 ? sosk::kLaneWide : c == 2 ? sosk::kLaneW : 0;
 }
 
 int tune_bucket(int64_t n) {
@@ -882,12 +925,12 @@ int tune_bucket(int64_t n) {
     return b;
 }
 
-bool tuned_choice(int device, int K, int64_t n, int *solver, int *N) {
+bool tuned_choice(int device, int K, int64_t n, int *solver, int *N, int *W) {
     if (device < 0 || device >= 64) return false;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     if (!g_tune[device].valid) return false;
     const int k = (K > sosk::kMaxPass ? sosk::kMaxPass : K) - 1;
-    candidate(g_tune[device].best[k][tune_bucket(n)], solver, N);
+    candidate(g_tune[device].best[k][tune_bucket(n)], solver, N, W);
     return true;
 }
 
@@ -905,15 +948,17 @@ sos_status run_impl(sos_filter *f, const float *x, float *y, int64_t n, const fl
         return SOS_OK;
     }
     const sos_tuning &t = f->tuning;
-    if (!t.N && !t.carry && !t.solver && !t.lookback_width) {
+    if (!t.N && !t.carry && !t.solver && !t.lookback_width && !t.groups_per_cta) {
         // all defaults: the autotuned choice for this section count and length, if there is one
-        int solver = 0, N = 0;
-        if (tuned_choice(f->device, f->K, n, &solver, &N)) {
-            if (solver == SOS_SOLVER_PH) return run_lane(f, x, y, n, zi, zf, s, N);
+        int solver = 0, N = 0, W = 0;
+        if (tuned_choice(f->device, f->K, n, &solver, &N, &W)) {
+            if (solver == SOS_SOLVER_PH) return run_lane(f, x, y, n, zi, zf, s, N, W);
+            if (solver == SOS_SOLVER_DTCR) return run_dtcr(f, x, y, n, zi, zf, s);
             return run_cascade(f, x, y, n, zi, zf, s, N);
         }
     }
     if (solver_of(f) == SOS_SOLVER_PH) return run_lane(f, x, y, n, zi, zf, s);
+    if (solver_of(f) == SOS_SOLVER_DTCR) return run_dtcr(f, x, y, n, zi, zf, s);
     if (t.carry == SOS_CARRY_SECTION) return run_sections(f, x, y, n, zi, zf, s);
     return run_cascade(f, x, y, n, zi, zf, s);
 }
@@ -1352,12 +1397,12 @@ sos_status run_lane_scratch(sos_filter *f, const float *x, float *y, int64_t n, 
     const bool aligned = (reinterpret_cast<uintptr_t>(x) % 16 == 0) && (reinterpret_cast<uintptr_t>(y) % 16 == 0);
     const float *src = x;
     for (auto &ps : f->lane[1]) {
-        const int bps = lane_blocks_per_sm(ps.kp, N, f->norm);
+        const int bps = lane_blocks_per_sm(ps.kp, N, kLaneW, f->norm);
         if (bps <= 0) return SOS_ECUDA;
         long long grid = static_cast<long long>(bps) * sm_count(f->device);
         if (grid > n_tiles) grid = n_tiles;
         const unsigned epoch = next_epoch(f->device, s);
-        const sos_status st = launch_lane_any<64>(ps.kp, f, ps, src, y, n, G, n_tiles, grid,
+        const sos_status st = launch_lane_any<64, kLaneW>(ps.kp, f, ps, src, y, n, G, n_tiles, grid,
                                                   zi ? zi + 2 * ps.k0 : nullptr, zf ? zf + 2 * ps.k0 : nullptr,
                                                   ps.k0 == 0, aligned, s, &sc, epoch);
         if (st != SOS_OK) return st;
@@ -1391,7 +1436,14 @@ sos_status sos_filter_create(int n_sections, const double *sos, const float *zi,
         if (t->N && t->N != 32 && t->N != 64 && t->N != 128) return SOS_EINVAL;
         if (t->L && t->L != sosk::kL) return SOS_EINVAL;
         if (t->threads_per_group && t->threads_per_group != sosk::kL) return SOS_EINVAL;
-        if (t->groups_per_cta) return SOS_EINVAL;  // chosen by the library from N and the carry scheme
+        // groups per tile: chosen by the library (0), or for the PH solver 7, or 10 at N = 64
+        if (t->groups_per_cta && t->groups_per_cta != sosk::kLaneW && t->groups_per_cta != sosk::kLaneWide)
+            return SOS_EINVAL;
+        if (t->groups_per_cta) {
+            const bool ph = t->solver == SOS_SOLVER_PH ||
+                            (t->solver == SOS_SOLVER_DEFAULT && !t->carry && !t->lookback_width && t->N != 128);
+            if (!ph || (t->groups_per_cta == sosk::kLaneWide && t->N == 32)) return SOS_EINVAL;
+        }
         if (t->fp64_carry) return SOS_EINVAL;
         if (t->spin_budget_cycles < 0) return SOS_EINVAL;
         if (t->carry != SOS_CARRY_DEFAULT && t->carry != SOS_CARRY_CASCADE && t->carry != SOS_CARRY_SECTION)
@@ -1400,13 +1452,18 @@ sos_status sos_filter_create(int n_sections, const double *sos, const float *zi,
             return SOS_EINVAL;
         const int lw = t->lookback_width;
         if (lw != 0 && lw != 1 && lw != 2 && lw != 4 && lw != 8 && lw != 16) return SOS_EINVAL;
-        if (t->solver != SOS_SOLVER_DEFAULT && t->solver != SOS_SOLVER_CR && t->solver != SOS_SOLVER_PH)
+        if (t->solver != SOS_SOLVER_DEFAULT && t->solver != SOS_SOLVER_CR && t->solver != SOS_SOLVER_PH &&
+            t->solver != SOS_SOLVER_DTCR)
+            return SOS_EINVAL;
+        if (t->solver == SOS_SOLVER_DTCR &&
+            ((t->N && t->N != 64) || t->carry == SOS_CARRY_SECTION || t->lookback_width))
             return SOS_EINVAL;
         if (t->solver == SOS_SOLVER_PH &&
             ((t->N && t->N != 32 && t->N != 64) || t->carry == SOS_CARRY_SECTION || t->lookback_width))
             return SOS_EINVAL;
         if (t->deterministic != 0 && t->deterministic != 1) return SOS_EINVAL;
-        if (t->deterministic && (t->solver == SOS_SOLVER_CR || t->carry || t->lookback_width || t->N == 128))
+        if (t->deterministic && (t->solver == SOS_SOLVER_CR || t->solver == SOS_SOLVER_DTCR || t->carry ||
+                                 t->lookback_width || t->N == 128))
             return SOS_EINVAL;
     }
     for (int k = 0; k < n_sections; ++k) {
@@ -1464,7 +1521,8 @@ sos_status sos_filter_create(int n_sections, const double *sos, const float *zi,
             st = SOS_ECUDA;
     }
     for (int i = 0; i < 2 && st == SOS_OK; ++i) st = build_cascade(f, i == 0 ? 32 : 64, f->cas[i]);
-    for (int i = 0; i < 2 && st == SOS_OK; ++i) st = build_lane(f, i == 0 ? 32 : 64, f->lane[i]);
+    for (int i = 0; i < 3 && st == SOS_OK; ++i)
+        st = build_lane(f, i == 0 ? 32 : 64, i == 2 ? sosk::kLaneWide : sosk::kLaneW, f->lane[i]);
     if (st == SOS_OK) {
         const LanePass &ps = f->lane[1][0];
         f->bt.sec = ps.d_sec;
@@ -1731,10 +1789,11 @@ sos_status sos_autotune(int max_log2n, float *report) {
         }
         for (int c = 0; c < kTuneCand && rc == SOS_OK; ++c) {
             sos_tuning t{};
-            int solver = 0, N = 0;
-            candidate(c, &solver, &N);
+            int solver = 0, N = 0, W = 0;
+            candidate(c, &solver, &N, &W);
             t.solver = solver;
             t.N = N;
+            t.groups_per_cta = W;
             if (solver == SOS_SOLVER_CR) t.carry = SOS_CARRY_CASCADE;
             sos_filter *f = nullptr;
             rc = sos_filter_create(K, sos.data(), nullptr, &t, &f);
@@ -1782,15 +1841,22 @@ sos_status sos_autotune(int max_log2n, float *report) {
     return SOS_OK;
 }
 
-sos_status sos_autotune_choice(int n_sections, int64_t n, int *solver, int *N) {
+sos_status sos_autotune_choice_ex(int n_sections, int64_t n, int *solver, int *N, int *groups_per_cta) {
     if (n_sections < 1 || !solver || !N) return SOS_EINVAL;
     int device = 0;
     if (cudaGetDevice(&device) != cudaSuccess) return SOS_ECUDA;
-    if (!tuned_choice(device, n_sections, n, solver, N)) {
+    int W = 0;
+    if (!tuned_choice(device, n_sections, n, solver, N, &W)) {
         *solver = 0;
         *N = 0;
+        W = 0;
     }
+    if (groups_per_cta) *groups_per_cta = W;
     return SOS_OK;
+}
+
+sos_status sos_autotune_choice(int n_sections, int64_t n, int *solver, int *N) {
+    return sos_autotune_choice_ex(n_sections, n, solver, N, nullptr);
 }
 
 sos_status sos_filter_stream_push(sos_filter *f, const float *x_dev, float *y_dev, int64_t n, void *stream) {

@@ -190,6 +190,146 @@ __device__ __forceinline__ void cascade_zero_state(float2 (&P)[N / 2], const Sec
     }
 }
 
+// The coordinator warp of the cascade-carry kernels (one per block, warp 0: warp schedulers favour
+// lower, older warps, and its carry work is on every tile's critical path): for each tile of the
+// block it waits for the tile's fold, resolves the tile's incoming 2K-word state by decoupled
+// lookback over tiles (Sec. IV-B, Eq. 25 on the cascade state; 32 predecessors per round, the
+// first resolved one ends it), posts the tile's resolved carry, and derives the incoming state of
+// each of the tile's W groups.  Shared by the single- and double-thread-group kernels.
+template <int K, int N, int W>
+__device__ __forceinline__ void cascade_coordinator(const CasParams<K, N> &p, int lane, long long budget,
+                                                    unsigned long long *bar_local, unsigned long long *bar_zready,
+                                                    unsigned long long *bar_ticket, const long long *ring,
+                                                    const float *a_buf, float *z_buf, const float *agg,
+                                                    const float *sATl, const float *sACd, const float *gATd) {
+    using Dm = CasDims<K>;
+    constexpr int S = Dm::S, MS = Dm::MS;
+    // ------------------------------------------------------------------ coordinator warp
+    const unsigned tagL = (p.epoch << 2) | 1u, tagG = (p.epoch << 2) | 2u;
+    // initial state of the signal (scaled domain), word i
+    auto zinit = [&](int i) -> float { return p.zi ? p.zi[i] * p.sec[i >> 1].zscale : 0.f; };
+    unsigned it = 0;
+    for (;;) {
+        if (!mbar_wait(&bar_ticket[it & 3], (it >> 2) & 1, budget, p.status)) break;
+        const long long cur = ring[it & 3];
+        if (cur < 0) break;
+
+        if (!mbar_wait(&bar_local[it & 1], (it >> 1) & 1, budget, p.status)) break;
+
+        unsigned long long *tr = (p.trace && lane == 0 && cur < p.trace_tiles)
+                                     ? p.trace + static_cast<size_t>(cur) * kTraceSlots
+                                     : nullptr;
+        if (tr) {
+            unsigned smid;
+            asm volatile("mov.u32 %0, %smid;" : "=r"(smid));
+            tr[0] = static_cast<unsigned long long>(cur) + 1;
+            tr[1] = global_ns();
+            tr[11] = smid;
+        }
+        const float *abuf = a_buf + (it & 1) * W * S;
+        const float acc_i = agg[(it & 1) * S + (lane < S ? lane : 0)];  // this lane's word of the tile carry
+        float tmp[S];
+        if (tr) tr[2] = global_ns();
+        unsigned long long *dcur = p.desc + static_cast<size_t>(cur) * S;
+        float zi_lane = 0.f;  // word `lane` of the tile's incoming state (lanes < S)
+        unsigned n_win = 0, n_wait = 0;
+        if (cur == 0) {
+            zi_lane = zinit(lane < S ? lane : 0);
+        } else {
+            // ---- decoupled lookback over tiles, 32 predecessors per round (local carry posted
+            // by the folding compute warp)
+            const long long t_start = clock64();
+            int win = 0;
+            for (;;) {
+                const long long pred = cur - 1 - 32LL * win - lane;
+                float v[S];
+                int st;
+                if (pred >= 0) {
+                    const unsigned long long *dp = p.desc + static_cast<size_t>(pred) * S;
+                    bool allG = true, allL = true;
+#pragma unroll
+                    for (int i = 0; i < S; ++i) {
+                        const unsigned long long wd = ld_relaxed_b64(dp + i);
+                        const unsigned tg = static_cast<unsigned>(wd >> 32);
+                        allG = allG && (tg == tagG);
+                        allL = allL && (tg == tagL);
+                        v[i] = __uint_as_float(static_cast<unsigned>(wd));
+                    }
+                    st = allG ? 2 : (allL ? 1 : 0);
+                } else {
+                    st = 2;  // the signal's initial state is the resolved carry of tile -1
+#pragma unroll
+                    for (int i = 0; i < S; ++i) v[i] = (pred == -1) ? zinit(i) : 0.f;
+                }
+                const unsigned glob = __ballot_sync(0xffffffffu, st == 2);
+                const unsigned inv = __ballot_sync(0xffffffffu, st == 0);
+                const int j = glob ? __ffs(glob) - 1 : 32;
+                const unsigned need = (j >= 31) ? 0xffffffffu : ((2u << j) - 1u);
+                if (inv & need) {
+                    ++n_wait;
+                    if (__any_sync(0xffffffffu, (clock64() - t_start) > budget)) {
+                        if (lane == 0) atomicOr(p.status, kDevErrTimeout);
+                        break;
+                    }
+                    __nanosleep(64);  // leave the issue slots to the computing warps meanwhile
+                    continue;
+                }
+                ++n_win;
+                if (lane > j) {
+#pragma unroll
+                    for (int i = 0; i < S; ++i) v[i] = 0.f;
+                }
+                // sum over the window of (A_T)^k v_k: each lane applies its own power, then a
+                // reduce-scatter leaves word i of the sum in lane i
+                packed_mv<K>(sATl + lane * MS, v, tmp);
+                float part = reduce_scatter<S, Dm::P2, Dm::SH>(tmp, lane);
+                part = __shfl_sync(0xffffffffu, part, (lane < S ? lane : 0) << Dm::SH);
+                if (win == 0) {
+                    zi_lane += part;
+                } else {
+                    // (A_T)^(32 win) from the global table (rarely needed)
+                    const float *Aw = p.tab + Dm::TAB + win * Dm::FULL;
+                    float y = 0.f;
+                    const int row = lane < S ? lane : 0;
+#pragma unroll
+                    for (int jj = 0; jj < S; ++jj) y = fmaf(__ldg(Aw + jj * S + row), __shfl_sync(0xffffffffu, part, jj), y);
+                    zi_lane += y;
+                }
+                if (j < 32) break;
+                if (++win > kMaxWin) {  // predecessors too far behind: report and give up
+                    if (lane == 0) atomicOr(p.status, kDevErrTimeout);
+                    break;
+                }
+            }
+        }
+        if (tr) {
+            tr[3] = global_ns();
+            tr[5] = (static_cast<unsigned long long>(n_wait) << 32) | n_win;
+        }
+        if (cur + 1 < p.n_tiles) {
+            float gl = acc_i;  // A_T Z + tile carry
+            {
+                const int row = lane < S ? lane : 0;
+#pragma unroll
+                for (int jj = 0; jj < S; ++jj)
+                    gl = fmaf(__ldg(gATd + jj * S + row), __shfl_sync(0xffffffffu, zi_lane, jj), gl);
+            }
+            if (lane < S) st_relaxed_b64(dcur + lane, pack_word(tagG, gl));
+        }
+        // incoming state of each group of the tile: Z_0 = Z, Z_{w+1} = A_C Z_w + a_w
+        float *zb = z_buf + (it & 1) * W * S;
+#pragma unroll 1
+        for (int w = 0; w < W; ++w) {
+            if (lane < S) zb[w * S + lane] = zi_lane;
+            if (w + 1 < W) zi_lane = lane_mv<S>(sACd, zi_lane, lane) + abuf[w * S + (lane < S ? lane : 0)];
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bar_zready[it & 1]);  // one barrier per tile parity
+        if (tr) tr[4] = global_ns();
+        ++it;
+    }
+}
+
 template <int K, int N, bool NORM, int W>
 __global__ void __launch_bounds__((W + 1) * 32) __maxnreg__(N <= 32 ? 96 : 168) sos_cascade_kernel(const __grid_constant__ CasParams<K, N> p) {
     using Dm = CasDims<K>;
@@ -249,133 +389,10 @@ __global__ void __launch_bounds__((W + 1) * 32) __maxnreg__(N <= 32 ? 96 : 168) 
     }
     __syncthreads();
 
-    // Warp 0 coordinates: warp schedulers favour lower (older) warps, and its carry work is on
-    // every tile's critical path.  Warps 1..W compute groups 0..W-1 of the tile.
+    // Warp 0 coordinates; warps 1..W compute groups 0..W-1 of the tile.
     if (warp == 0) {
-        // ------------------------------------------------------------------ coordinator warp
-        const unsigned tagL = (p.epoch << 2) | 1u, tagG = (p.epoch << 2) | 2u;
-        // initial state of the signal (scaled domain), word i
-        auto zinit = [&](int i) -> float { return p.zi ? p.zi[i] * p.sec[i >> 1].zscale : 0.f; };
-        unsigned it = 0;
-        for (;;) {
-            if (!mbar_wait(&bar_ticket[it & 3], (it >> 2) & 1, budget, p.status)) break;
-            const long long cur = ring[it & 3];
-            if (cur < 0) break;
-
-            if (!mbar_wait(&bar_local[it & 1], (it >> 1) & 1, budget, p.status)) break;
-
-            unsigned long long *tr = (p.trace && lane == 0 && cur < p.trace_tiles)
-                                         ? p.trace + static_cast<size_t>(cur) * kTraceSlots
-                                         : nullptr;
-            if (tr) {
-                unsigned smid;
-                asm volatile("mov.u32 %0, %smid;" : "=r"(smid));
-                tr[0] = static_cast<unsigned long long>(cur) + 1;
-                tr[1] = global_ns();
-                tr[11] = smid;
-            }
-            const float *abuf = a_buf + (it & 1) * W * S;
-            const float acc_i = agg[(it & 1) * S + (lane < S ? lane : 0)];  // this lane's word of the tile carry
-            float tmp[S];
-            if (tr) tr[2] = global_ns();
-            unsigned long long *dcur = p.desc + static_cast<size_t>(cur) * S;
-            float zi_lane = 0.f;  // word `lane` of the tile's incoming state (lanes < S)
-            unsigned n_win = 0, n_wait = 0;
-            if (cur == 0) {
-                zi_lane = zinit(lane < S ? lane : 0);
-            } else {
-                // ---- decoupled lookback over tiles, 32 predecessors per round (local carry posted
-                // by the folding compute warp)
-                const long long t_start = clock64();
-                int win = 0;
-                for (;;) {
-                    const long long pred = cur - 1 - 32LL * win - lane;
-                    float v[S];
-                    int st;
-                    if (pred >= 0) {
-                        const unsigned long long *dp = p.desc + static_cast<size_t>(pred) * S;
-                        bool allG = true, allL = true;
-#pragma unroll
-                        for (int i = 0; i < S; ++i) {
-                            const unsigned long long wd = ld_relaxed_b64(dp + i);
-                            const unsigned tg = static_cast<unsigned>(wd >> 32);
-                            allG = allG && (tg == tagG);
-                            allL = allL && (tg == tagL);
-                            v[i] = __uint_as_float(static_cast<unsigned>(wd));
-                        }
-                        st = allG ? 2 : (allL ? 1 : 0);
-                    } else {
-                        st = 2;  // the signal's initial state is the resolved carry of tile -1
-#pragma unroll
-                        for (int i = 0; i < S; ++i) v[i] = (pred == -1) ? zinit(i) : 0.f;
-                    }
-                    const unsigned glob = __ballot_sync(0xffffffffu, st == 2);
-                    const unsigned inv = __ballot_sync(0xffffffffu, st == 0);
-                    const int j = glob ? __ffs(glob) - 1 : 32;
-                    const unsigned need = (j >= 31) ? 0xffffffffu : ((2u << j) - 1u);
-                    if (inv & need) {
-                        ++n_wait;
-                        if (__any_sync(0xffffffffu, (clock64() - t_start) > budget)) {
-                            if (lane == 0) atomicOr(p.status, kDevErrTimeout);
-                            break;
-                        }
-                        __nanosleep(64);  // leave the issue slots to the computing warps meanwhile
-                        continue;
-                    }
-                    ++n_win;
-                    if (lane > j) {
-#pragma unroll
-                        for (int i = 0; i < S; ++i) v[i] = 0.f;
-                    }
-                    // sum over the window of (A_T)^k v_k: each lane applies its own power, then a
-                    // reduce-scatter leaves word i of the sum in lane i
-                    packed_mv<K>(sATl + lane * MS, v, tmp);
-                    float part = reduce_scatter<S, Dm::P2, Dm::SH>(tmp, lane);
-                    part = __shfl_sync(0xffffffffu, part, (lane < S ? lane : 0) << Dm::SH);
-                    if (win == 0) {
-                        zi_lane += part;
-                    } else {
-                        // (A_T)^(32 win) from the global table (rarely needed)
-                        const float *Aw = p.tab + Dm::TAB + win * Dm::FULL;
-                        float y = 0.f;
-                        const int row = lane < S ? lane : 0;
-#pragma unroll
-                        for (int jj = 0; jj < S; ++jj) y = fmaf(__ldg(Aw + jj * S + row), __shfl_sync(0xffffffffu, part, jj), y);
-                        zi_lane += y;
-                    }
-                    if (j < 32) break;
-                    if (++win > kMaxWin) {  // predecessors too far behind: report and give up
-                        if (lane == 0) atomicOr(p.status, kDevErrTimeout);
-                        break;
-                    }
-                }
-            }
-            if (tr) {
-                tr[3] = global_ns();
-                tr[5] = (static_cast<unsigned long long>(n_wait) << 32) | n_win;
-            }
-            if (cur + 1 < p.n_tiles) {
-                float gl = acc_i;  // A_T Z + tile carry
-                {
-                    const int row = lane < S ? lane : 0;
-#pragma unroll
-                    for (int jj = 0; jj < S; ++jj)
-                        gl = fmaf(__ldg(gATd + jj * S + row), __shfl_sync(0xffffffffu, zi_lane, jj), gl);
-                }
-                if (lane < S) st_relaxed_b64(dcur + lane, pack_word(tagG, gl));
-            }
-            // incoming state of each group of the tile: Z_0 = Z, Z_{w+1} = A_C Z_w + a_w
-            float *zb = z_buf + (it & 1) * W * S;
-#pragma unroll 1
-            for (int w = 0; w < W; ++w) {
-                if (lane < S) zb[w * S + lane] = zi_lane;
-                if (w + 1 < W) zi_lane = lane_mv<S>(sACd, zi_lane, lane) + abuf[w * S + (lane < S ? lane : 0)];
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&bar_zready[it & 1]);  // one barrier per tile parity
-            if (tr) tr[4] = global_ns();
-            ++it;
-        }
+        cascade_coordinator<K, N, W>(p, lane, budget, bar_local, bar_zready, bar_ticket, ring, a_buf, z_buf, agg,
+                                     sATl, sACd, gATd);
         return;
     }
 

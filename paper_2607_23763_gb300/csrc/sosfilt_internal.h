@@ -117,11 +117,23 @@ SOSK_DECLARE_CASCADE_N(32)
 SOSK_DECLARE_CASCADE_N(64)
 // Thread blocks of the cascade kernel that fit on one SM (0 if unavailable).
 int cascade_blocks_per_sm(int K, int N, bool norm);
+
+// ---- double-thread-group cyclic reduction (sosfilt_dtcr.cuh): the cascade-carry kernel with two
+// warps per group (one per parity), on the N = 64 cyclic-reduction tables (tiles of 4 groups)
+template <int K>
+cudaError_t launch_dtcr(bool norm, const CasParams<K, 64> &p, long long grid, cudaStream_t s);
+#define SOSK_DECLARE_DTCR(K) \
+    template <>              \
+    cudaError_t launch_dtcr<K>(bool norm, const CasParams<K, 64> &p, long long grid, cudaStream_t s);
+SOSK_DECLARE_DTCR(1) SOSK_DECLARE_DTCR(2) SOSK_DECLARE_DTCR(3) SOSK_DECLARE_DTCR(4)
+SOSK_DECLARE_DTCR(5) SOSK_DECLARE_DTCR(6) SOSK_DECLARE_DTCR(7) SOSK_DECLARE_DTCR(8)
+int dtcr_blocks_per_sm(int K, bool norm);
 int cascade_warps(int N);       // compute warps (groups) per block
 size_t cascade_smem(int K, int N);
 
 // ---- PH-factorization kernel with a skewed direct-form-II particular pass (sosfilt_lane.cuh)
-constexpr int kLaneW = 7;  // compute warps per block, one group each; a tile is kLaneW groups
+constexpr int kLaneW = 7;    // compute warps per block, one group each; a tile is kLaneW groups
+constexpr int kLaneWide = 10;  // the wide variant at N = 64: 10 groups per tile (sos_tuning.groups_per_cta)
 
 // Per-section constants of the skewed-pass kernel, in the kernel's domain (b / b0 and b0 = 1 when
 // normalized; carried state = zscale * true state).
@@ -161,18 +173,20 @@ struct LaneParams {
 // [4] iteration start, [5] next ticket known, [6] particular pass done, [7] lane scan done, [8] fold
 // done; correction of the tile: [9] start, [10] group state observed, [11] row states stored,
 // [12] stored; [13] SM id; [14] stash start, [15] input stashed.
-template <int K, int N>
+template <int K, int N, int W>
 cudaError_t launch_lane(bool norm, const LaneParams<K> &p, long long grid, cudaStream_t s);
-#define SOSK_DECLARE_LANE(K, N) \
-    template <>                 \
-    cudaError_t launch_lane<K, N>(bool norm, const LaneParams<K> &p, long long grid, cudaStream_t s);
-#define SOSK_DECLARE_LANE_N(N)                                                                       \
-    SOSK_DECLARE_LANE(1, N) SOSK_DECLARE_LANE(2, N) SOSK_DECLARE_LANE(3, N) SOSK_DECLARE_LANE(4, N) \
-    SOSK_DECLARE_LANE(5, N) SOSK_DECLARE_LANE(6, N) SOSK_DECLARE_LANE(7, N) SOSK_DECLARE_LANE(8, N)
-SOSK_DECLARE_LANE_N(32)
-SOSK_DECLARE_LANE_N(64)
-// Thread blocks of the skewed-pass kernel that fit on one SM (0 if unavailable).
-int lane_blocks_per_sm(int K, int N, bool norm);
+#define SOSK_DECLARE_LANE(K, N, W) \
+    template <>                    \
+    cudaError_t launch_lane<K, N, W>(bool norm, const LaneParams<K> &p, long long grid, cudaStream_t s);
+#define SOSK_DECLARE_LANE_NW(N, W)                                                                          \
+    SOSK_DECLARE_LANE(1, N, W) SOSK_DECLARE_LANE(2, N, W) SOSK_DECLARE_LANE(3, N, W) SOSK_DECLARE_LANE(4, N, W) \
+    SOSK_DECLARE_LANE(5, N, W) SOSK_DECLARE_LANE(6, N, W) SOSK_DECLARE_LANE(7, N, W) SOSK_DECLARE_LANE(8, N, W)
+SOSK_DECLARE_LANE_NW(32, 7)
+SOSK_DECLARE_LANE_NW(64, 7)
+SOSK_DECLARE_LANE_NW(64, 10)
+// Thread blocks of the skewed-pass kernel (N samples per lane, W groups per tile) that fit on one SM
+// (0 if unavailable).
+int lane_blocks_per_sm(int K, int N, int W, bool norm);
 
 // ---- multi-signal persistent kernel (sosfilt_batch.cuh): the PH kernel with a skewed particular
 // pass over a global queue of (signal, tile) work items

@@ -39,7 +39,12 @@
 
 namespace sosk {
 
-template <int K, int N>
+// Geometry of the PH kernel for K sections, N samples per lane and W groups (compute warps) per
+// tile: W = 7 with N = 64 (one block per SM, 223 registers with the register prefetch) or N = 32 (two
+// blocks per SM, 128 registers); W = 10 with N = 64 (one block of 11 warps per SM: three warps on
+// most schedulers, at most 168 registers, so the correction takes two samples per lane and step and
+// (A_T)^lane stays in global memory, read through L1).
+template <int K, int N, int W = kLaneW>
 struct LaneDims {
     static constexpr int S = 2 * K;
     static constexpr int NB = K * (K + 1) / 2;
@@ -51,10 +56,11 @@ struct LaneDims {
     static constexpr int SH = 5 - (P2 == 2 ? 1 : P2 == 4 ? 2 : P2 == 8 ? 3 : 4);
     static constexpr int LQ = N / 4;             // 128-bit loads per lane per group
     static constexpr int BPS = N == 32 ? 2 : 1;  // thread blocks per SM (N = 32: 4 warps per scheduler)
-    static constexpr int V = N == 32 ? 2 : 4;    // samples per lane and step of the column-wise correction
+    static constexpr int MAXREG = N == 32 ? 128 : W > 7 ? 168 : 255;  // registers per thread
+    static constexpr int V = (N == 32 || W > 7) ? 2 : 4;  // samples per lane and step of the correction
     static constexpr int CC = N / V;             // correction chunks per row
     static constexpr int RPS = 32 / CC;          // rows per step of the column-wise correction
-    static constexpr bool ATL_SHARED = BPS == 1;  // (A_T)^lane in shared memory (else read from L1/L2)
+    static constexpr bool ATL_SHARED = BPS == 1 && W <= 7;  // (A_T)^lane in shared memory (else from L1/L2)
     // row-state pitch: S rounded up to whole 16-byte words, an odd number of them
     static constexpr int S4 = (S + 3) / 4;
     static constexpr int RSP = 4 * ((S4 & 1) ? S4 : S4 + 1);
@@ -308,11 +314,10 @@ __device__ __forceinline__ void lane_state_mv(const float *__restrict__ A, const
     }
 }
 
-template <int K, int N, bool NORM>
-__global__ void __launch_bounds__((kLaneW + 1) * 32, LaneDims<K, N>::BPS)
-    sos_lane_kernel(const __grid_constant__ LaneParams<K> p) {
-    using Dm = LaneDims<K, N>;
-    constexpr int S = Dm::S, MS = Dm::MS, W = kLaneW, LQ = Dm::LQ, V = Dm::V, CC = Dm::CC, RPS = Dm::RPS,
+template <int K, int N, bool NORM, int W>
+__global__ void __maxnreg__((LaneDims<K, N, W>::MAXREG)) sos_lane_kernel(const __grid_constant__ LaneParams<K> p) {
+    using Dm = LaneDims<K, N, W>;
+    constexpr int S = Dm::S, MS = Dm::MS, LQ = Dm::LQ, V = Dm::V, CC = Dm::CC, RPS = Dm::RPS,
                   RSP = Dm::RSP;
     constexpr int P = N + 4;  // padded row pitch (floats): conflict-free 128-bit row access
     constexpr int C = N * kL;
@@ -676,10 +681,9 @@ __global__ void __launch_bounds__((kLaneW + 1) * 32, LaneDims<K, N>::BPS)
     if (ok) correct_and_store(prev, it, B0 + (it & 1) * kL * P, Sprev);
 }
 
-template <int K, int N>
+template <int K, int N, int W>
 constexpr size_t lane_smem_bytes() {
-    using Dm = LaneDims<K, N>;
-    constexpr int W = kLaneW;
+    using Dm = LaneDims<K, N, W>;
     return sizeof(float) * (static_cast<size_t>(W) * 2 * kL * (N + 4) + Dm::SM_TAB + W * kL * Dm::RSP +
                             4 * W * Dm::S + 2 * Dm::S + ((Dm::S + 3) / 4) * 4);
 }

@@ -36,7 +36,7 @@ struct Launch {
 };
 std::vector<Launch> g_launches;
 bool g_light = false;          // record no parameter blocks and skip the marker (timing runs)
-float g_cost[5][3][9] = {};    // simulated time of a launch, ms, by kind, N (32, 64, 128) and K
+float g_cost[6][3][9] = {};    // simulated time of a launch, ms, by kind, N (32, 64, 128) and K
 
 int n_index(int N) { return N == 32 ? 0 : N == 64 ? 1 : 2; }
 
@@ -157,7 +157,10 @@ int lane_blocks_per_sm_n32a(int, bool) { return 2; }
 int lane_blocks_per_sm_n32b(int, bool) { return 2; }
 int lane_blocks_per_sm_n64a(int, bool) { return 1; }
 int lane_blocks_per_sm_n64b(int, bool) { return 1; }
+int lane_blocks_per_sm_n64w10a(int, bool) { return 1; }
+int lane_blocks_per_sm_n64w10b(int, bool) { return 1; }
 int batch_blocks_per_sm(int, bool) { return 1; }
+int dtcr_blocks_per_sm(int, bool) { return 1; }
 int default_lbm(int N) { return N <= 32 ? 4 : N == 64 ? 2 : 1; }
 
 cudaError_t launch_dccr(int K, int N, bool norm, int, const PassParams &p, long long grid, cudaStream_t) {
@@ -166,12 +169,12 @@ cudaError_t launch_dccr(int K, int N, bool norm, int, const PassParams &p, long 
     return cudaSuccess;
 }
 
-#define HOST_LANE(K, N)                                                                             \
-    template <>                                                                                     \
-    cudaError_t launch_lane<K, N>(bool norm, const LaneParams<K> &p, long long grid, cudaStream_t) { \
-        record(1, K, N, norm, grid, p);                                                             \
-        mark(p.x, p.y, p.n, p.zi, p.zf, K);                                                         \
-        return cudaSuccess;                                                                         \
+#define HOST_LANE(K, N, W)                                                                             \
+    template <>                                                                                        \
+    cudaError_t launch_lane<K, N, W>(bool norm, const LaneParams<K> &p, long long grid, cudaStream_t) {  \
+        record(1, K, N, norm, grid, p);                                                                \
+        mark(p.x, p.y, p.n, p.zi, p.zf, K);                                                            \
+        return cudaSuccess;                                                                            \
     }
 #define HOST_CAS(K, N)                                                                                \
     template <>                                                                                       \
@@ -192,7 +195,15 @@ cudaError_t launch_dccr(int K, int N, bool norm, int, const PassParams &p, long 
         }                                                                                            \
         return cudaSuccess;                                                                          \
     }
-#define HOST_ALL(K) HOST_LANE(K, 32) HOST_LANE(K, 64) HOST_CAS(K, 32) HOST_CAS(K, 64) HOST_BATCH(K)
+#define HOST_DTCR(K)                                                                                \
+    template <>                                                                                     \
+    cudaError_t launch_dtcr<K>(bool norm, const CasParams<K, 64> &p, long long grid, cudaStream_t) { \
+        record(5, K, 64, norm, grid, p);                                                            \
+        mark(p.x, p.y, p.n, p.zi, p.zf, K);                                                         \
+        return cudaSuccess;                                                                         \
+    }
+#define HOST_ALL(K) HOST_LANE(K, 32, 7) HOST_LANE(K, 64, 7) HOST_LANE(K, 64, 10) HOST_CAS(K, 32) HOST_CAS(K, 64) \
+    HOST_BATCH(K) HOST_DTCR(K)
 HOST_ALL(1) HOST_ALL(2) HOST_ALL(3) HOST_ALL(4) HOST_ALL(5) HOST_ALL(6) HOST_ALL(7) HOST_ALL(8)
 
 }  // namespace sosk
@@ -241,7 +252,8 @@ void host_reset(void) { g_launches.clear(); }
 void host_set_light(int on) { g_light = on != 0; }
 void host_set_cost(int kind, int N, int K, float ms) { g_cost[kind][n_index(N)][K] = ms; }
 int host_launches(void) { return static_cast<int>(g_launches.size()); }
-// kind (1 PH lane, 2 cyclic-reduction cascade, 3 batch, 4 per-section cyclic reduction), K, N,
+// kind (1 PH lane, 2 cyclic-reduction cascade, 3 batch, 4 per-section cyclic reduction, 5 double-
+// thread-group cyclic reduction), K, N,
 // b0 normalization, grid; returns the parameter block's size and copies up to cap bytes of it
 long long host_launch(int i, int *info, long long *grid, void *params, long long cap) {
     const Launch &l = g_launches.at(static_cast<size_t>(i));

@@ -33,7 +33,8 @@ def test_header_declares_the_abi():
         "sos_filter_run_host", "sos_filter_run_noalloc", "sos_filter_run_batch_ex", "sos_batch_sync_status",
         "sos_server_create", "sos_server_destroy", "sos_server_add_stream", "sos_server_submit", "sos_server_poll",
         "sos_server_drain", "sos_server_stream_state", "sos_server_get_stats", "sos_server_replay",
-        "sos_autotune", "sos_autotune_choice", "sos_batch_plan_create", "sos_batch_plan_launch",
+        "sos_autotune", "sos_autotune_choice", "sos_autotune_choice_ex", "sos_batch_plan_create",
+        "sos_batch_plan_launch",
         "sos_batch_plan_status", "sos_batch_plan_destroy", "sos_status_string"])
 
 
@@ -111,7 +112,7 @@ def test_ctypes_structures_match_the_header_layout():
 def _tuning_valid(N, carry, solver, lw, det):
     """sos_filter_create's verdict on a tuning, written from the sos_tuning documentation in
     include/sosfilt.h (not from the implementation)."""
-    if N not in (0, 32, 64, 128) or carry not in (0, 1, 2) or solver not in (0, 1, 2):
+    if N not in (0, 32, 64, 128) or carry not in (0, 1, 2) or solver not in (0, 1, 2, 3):
         return False
     if lw not in (0, 1, 2, 4, 8, 16) or det not in (0, 1):
         return False
@@ -119,7 +120,9 @@ def _tuning_valid(N, carry, solver, lw, det):
         return False
     if solver == 2 and (N == 128 or carry == 2 or lw):
         return False
-    if det and (solver == 1 or carry or lw or N == 128):
+    if solver == 3 and (N not in (0, 64) or carry == 2 or lw):  # double-thread-group: N = 64, cascade carry
+        return False
+    if det and (solver in (1, 3) or carry or lw or N == 128):
         return False
     return True
 
@@ -143,7 +146,7 @@ def test_tuning_validation_matches_the_header(lib):
     seen = {True: 0, False: 0}
     for N in (0, 24, 32, 64, 128):
         for carry in (0, 1, 2, 3):
-            for solver in (0, 1, 2, 3):
+            for solver in (0, 1, 2, 3, 4):
                 for lw in (0, 1, 3, 16):
                     for det in (0, 1, 2):
                         t = Tuning(N=N, carry=carry, solver=solver, lookback_width=lw, deterministic=det)
@@ -155,8 +158,13 @@ def test_tuning_validation_matches_the_header(lib):
     assert seen[True] > 50 and seen[False] > 500
     # the reserved and fixed fields
     for t in (Tuning(L=16), Tuning(threads_per_group=64), Tuning(groups_per_cta=2), Tuning(fp64_carry=1),
-              Tuning(spin_budget_cycles=-1)):
+              Tuning(spin_budget_cycles=-1), Tuning(groups_per_cta=10, N=32), Tuning(groups_per_cta=7, solver=1),
+              Tuning(groups_per_cta=10, solver=3), Tuning(groups_per_cta=7, carry=2)):
         assert _create_verdict(lib, sos, t) == -1
+    # groups per tile of the PH solver: 7, or 10 at N = 64 (the default solver is PH)
+    for t in (Tuning(groups_per_cta=7), Tuning(groups_per_cta=10), Tuning(groups_per_cta=10, solver=2, N=64),
+              Tuning(groups_per_cta=7, solver=2, N=32)):
+        assert _create_verdict(lib, sos, t) != -1
     for t in (Tuning(L=32), Tuning(threads_per_group=32), Tuning(spin_budget_cycles=1 << 20)):
         assert _create_verdict(lib, sos, t) != -1
 

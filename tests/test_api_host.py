@@ -33,7 +33,7 @@ _DEPS = _SRCS + [os.path.join(_HERE, "api_host", "cuda_runtime.h"), os.path.join
                  os.path.join(_CSRC, "sosfilt_internal.h")]
 _LIB = os.path.join(_HERE, "_build", "libapi_host.so")
 N64, W, C64 = 64, 7, 32 * 64
-KIND_LANE, KIND_CASCADE, KIND_BATCH, KIND_SECTION = 1, 2, 3, 4
+KIND_LANE, KIND_CASCADE, KIND_BATCH, KIND_SECTION, KIND_DTCR = 1, 2, 3, 4, 5
 
 
 @pytest.fixture(scope="module")
@@ -230,7 +230,8 @@ def test_ph_tables_match_a_float64_derivation(lib, name):
 
 @pytest.mark.parametrize("tuning,kind,N", [
     (None, KIND_LANE, 64), ({"N": 32}, KIND_LANE, 32), ({"deterministic": 1}, KIND_LANE, 64),
-    ({"solver": 1}, KIND_CASCADE, 32), ({"solver": 1, "N": 64}, KIND_CASCADE, 64),
+    ({"solver": 1}, KIND_CASCADE, 32), ({"solver": 1, "N": 64}, KIND_CASCADE, 64), ({"solver": 3}, KIND_DTCR, 64),
+    ({"groups_per_cta": 10}, KIND_LANE, 64),
     ({"carry": 2, "N": 32}, KIND_SECTION, 32), ({"carry": 2, "N": 128}, KIND_SECTION, 128),
 ])
 def test_a_tuning_selects_its_kernel(lib, tuning, kind, N):
@@ -731,7 +732,9 @@ def test_launch_parameters_follow_the_filter_settings(lib):
 
 def _tune_costs(lib, fastest):
     """Simulated launch times: the candidate fastest(K) takes 1 ms per launch, the others 2 and 3."""
-    cands = [(KIND_CASCADE, 32), (KIND_CASCADE, 64), (KIND_LANE, 64)]  # the autotuner's candidates
+    cands = [(KIND_CASCADE, 32), (KIND_CASCADE, 64), (KIND_LANE, 64), (KIND_DTCR, 64)]  # the autotuner's candidates
+    # (the PH candidates with 7 and 10 groups per tile are both (KIND_LANE, 64) here: equal simulated times,
+    # and the first measured of them, 7 groups, is kept)
     for K in range(1, 9):
         best = fastest(K)
         slow = 2.0
@@ -741,7 +744,7 @@ def _tune_costs(lib, fastest):
 
 
 def test_autotuner_choices_drive_the_default_launch(lib):
-    """The autotuner times its three candidates per section count and length bucket and keeps the
+    """The autotuner times its four candidates per section count and length bucket and keeps the
     fastest; default-tuned runs then launch that choice, an explicit tuning still wins."""
     lib.sos_autotune.argtypes = [ctypes.c_int, ctypes.c_void_p]
     lib.sos_autotune_choice.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_int),
@@ -754,25 +757,25 @@ def test_autotuner_choices_drive_the_default_launch(lib):
         return solver.value, N.value
 
     assert choice(4, 1 << 20) == (0, 0)  # nothing tuned yet: the library's defaults
-    report = np.zeros((8, 4, 3), dtype=np.float32)
-    _tune_costs(lib, lambda K: (KIND_CASCADE, 32) if K <= 3 else (KIND_LANE, 64))
+    report = np.zeros((8, 4, 5), dtype=np.float32)
+    _tune_costs(lib, lambda K: (KIND_CASCADE, 32) if K <= 3 else (KIND_DTCR, 64) if K == 5 else (KIND_LANE, 64))
     lib.host_set_light(1)
     try:
         assert lib.sos_autotune(16, report.ctypes.data) == 0
     finally:
         lib.host_set_light(0)
     for K in range(1, 9):
-        want = (1, 32) if K <= 3 else (2, 64)
+        want = (1, 32) if K <= 3 else (3, 64) if K == 5 else (2, 64)
         for n in (1000, 1 << 16, 1 << 22, 1 << 30):  # buckets above 2^16 repeat the measured one
             assert choice(K, n) == want, (K, n)
-        assert np.argmax(report[K - 1, 0]) == (0 if K <= 3 else 2)
+        assert np.argmax(report[K - 1, 0]) == (0 if K <= 3 else 3 if K == 5 else 2)
         np.testing.assert_array_equal(report[K - 1, 1:], np.repeat(report[K - 1, :1], 3, axis=0))
     assert choice(12, 1 << 20) == (2, 64)  # more than eight sections: the eight-section choice
 
     x = workloads.normal_f32(13, 40000)
     y = np.empty_like(x)
-    for K, tuning, want in [(2, None, (KIND_CASCADE, 32)), (6, None, (KIND_LANE, 64)),
-                            (2, {"solver": 2}, (KIND_LANE, 64))]:
+    for K, tuning, want in [(2, None, (KIND_CASCADE, 32)), (6, None, (KIND_LANE, 64)), (5, None, (KIND_DTCR, 64)),
+                            (2, {"solver": 2}, (KIND_LANE, 64)), (2, {"solver": 3}, (KIND_DTCR, 64))]:
         f = _create(lib, designs.butter_lowpass(2 * K, 0.2), tuning)
         lib.host_reset()
         assert lib.sos_filter_run(f, x.ctypes.data, y.ctypes.data, x.size, None, None, None) == 0

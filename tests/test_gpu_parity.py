@@ -71,19 +71,30 @@ SIZES = [1, 2, 3, 5, 31, 32, 33, 127, 511, 512, 513, 1023, 1024, 1025, 2047, 204
 
 
 CARRY_CASCADE, CARRY_SECTION = 1, 2
-SOLVER_CR, SOLVER_PH = 1, 2
+SOLVER_CR, SOLVER_PH, SOLVER_DTCR = 1, 2, 3
 # solver and launch configuration: PH factorization (skewed particular pass) at N = 64 and 32;
 # cyclic reduction with the cascade carry at N = 32 and 64, and with per-section carries at N = 32,
 # 64 and 128
 SCHEMES = [{"solver": SOLVER_PH}, {"solver": SOLVER_PH, "N": 32}, {"carry": CARRY_CASCADE, "N": 32},
            {"carry": CARRY_CASCADE, "N": 64}, {"carry": CARRY_SECTION, "N": 32}, {"carry": CARRY_SECTION, "N": 64},
-           {"carry": CARRY_SECTION, "N": 128}]
+           {"carry": CARRY_SECTION, "N": 128}, {"solver": SOLVER_DTCR}, {"solver": SOLVER_PH, "groups_per_cta": 10}]
 SCHEME_IDS = ["ph-64", "ph-32", "cr-cascade-32", "cr-cascade-64", "cr-section-32", "cr-section-64",
-              "cr-section-128"]
+              "cr-section-128", "dtcr-64", "ph-64-w10"]
 PH_W = 7  # groups per PH tile
+DTCR_W = 4  # groups per double-thread-group tile
+
+
+def _several_tiles(tuning):
+    """A length spanning three or more tiles of the scheme, with a ragged tail."""
+    if tuning.get("solver") == SOLVER_PH:
+        return 3 * tuning.get("groups_per_cta", PH_W) * 32 * tuning.get("N", 64) + 123
+    if tuning.get("solver") == SOLVER_DTCR:
+        return 3 * DTCR_W * 32 * 64 + 123
+    return 5 * 32 * tuning.get("N", 32) + 123
 # one setting per kernel: PH, cyclic reduction with the cascade carry, with per-section carries
-KERNELS = [{"solver": SOLVER_PH}, {"carry": CARRY_CASCADE}, {"carry": CARRY_SECTION}]
-KERNEL_IDS = ["ph", "cr-cascade", "cr-section"]
+KERNELS = [{"solver": SOLVER_PH}, {"carry": CARRY_CASCADE}, {"carry": CARRY_SECTION}, {"solver": SOLVER_DTCR},
+           {"solver": SOLVER_PH, "groups_per_cta": 10}]
+KERNEL_IDS = ["ph", "cr-cascade", "cr-section", "dtcr", "ph-w10"]
 
 
 @pytest.mark.parametrize("tuning", SCHEMES, ids=SCHEME_IDS)
@@ -101,10 +112,7 @@ def test_every_section_count(dev, K, tuning):
     u = workloads.uniform_f64(100 + K, 3 * K, stream=1).reshape(K, 3)
     sos = designs.random_sections(u)
     # several tiles and a ragged tail
-    if tuning.get("solver") == SOLVER_PH:
-        n = 3 * PH_W * 32 * tuning.get("N", 64) + 123
-    else:
-        n = 5 * 32 * tuning.get("N", 32) + 123
+    n = _several_tiles(tuning)
     x = workloads.normal_f32(200 + K, n)
     zi = np.random.default_rng(K).standard_normal((K, 2)) * 0.1
     _run_check(sos, x, dev, zi=zi, tuning=tuning, random_mix=True)
@@ -124,10 +132,7 @@ def test_every_section_count_designed_stated_bound(dev, K, tuning):
     """Butterworth and resonator cascades at every section count, every scheme, a nonzero initial
     state, several tiles and a ragged tail: the stated bound, no widening."""
     sos = _designed(K)
-    if tuning.get("solver") == SOLVER_PH:
-        n = 3 * PH_W * 32 * tuning.get("N", 64) + 123
-    else:
-        n = 5 * 32 * tuning.get("N", 32) + 123
+    n = _several_tiles(tuning)
     x = workloads.normal_f32(300 + K, n)
     zi = np.random.default_rng(30 + K).standard_normal((K, 2)) * 0.1
     _run_check(sos, x, dev, zi=zi, tuning=tuning, tol=designs.tolerance_for(sos))
@@ -450,3 +455,5 @@ def test_deterministic_mode_is_bit_reproducible(dev):
     assert _zerr(states[0], zf_ref) < 1e-4
     with pytest.raises(SosError):
         SosFilter(sos, tuning={"deterministic": 1, "solver": SOLVER_CR})
+    with pytest.raises(SosError):
+        SosFilter(sos, tuning={"deterministic": 1, "solver": SOLVER_DTCR})
