@@ -188,13 +188,14 @@ sos_status sos_filter_run_host(sos_filter *f, const float *x_host, float *y_host
                                float *zf_host, int64_t chunk_samples);
 
 /*
- * Filter many independent signals of uneven length and order: the signals with
- * the same section count (and the same b0 handling) share one persistent
- * launch over a global queue of (signal, tile) work items, tiles of 8 groups
- * of 1024 samples, with the lookback chains of Sec. IV-B kept per signal (a
- * chain ends at its signal's first tile).  The launches of the different
- * section counts run concurrently on library streams forked from and joined
- * back into `stream`.  Zero initial state for every signal.
+ * Filter many independent signals of uneven length and order in one persistent
+ * kernel launch on `stream`: the signals with the same section count (and the
+ * same b0 handling) form a class with its own global queue of (signal, tile)
+ * work items, tiles of 7 groups of 2048 samples, with the lookback chains of
+ * Sec. IV-B kept per signal (a chain ends at its signal's first tile); each
+ * thread block starts on a class in proportion to the classes' work and then
+ * takes every other class that still has tiles.  Zero initial state for every
+ * signal.
  *   n_signals  >= 0
  *   filters    host array [n_signals] of filter objects (may repeat), all on one device
  *   x_dev      host array [n_signals] of device input pointers
@@ -228,9 +229,8 @@ sos_status sos_filter_run_batch_ex(int n_signals, sos_filter *const *filters, co
  * sos_filter_run_batch_ex; every n > 0, at most 8 sections per filter) are
  * uploaded once.  sos_batch_plan_launch enqueues the batch on `stream` with no
  * host synchronization and no host-side work per signal (a reset of the
- * plan's descriptors and tickets, then one persistent launch per class on the
- * plan's own streams, forked from and joined back into `stream`), so it may be
- * captured into a CUDA graph and the graph replayed.  Launches of one plan
+ * plan's descriptors and tickets, then the one persistent launch over every
+ * class), so it may be captured into a CUDA graph and the graph replayed.  Launches of one plan
  * must not overlap on the device (they share its workspace).  The buffers and
  * filters named at creation must outlive the plan.
  */

@@ -562,6 +562,7 @@ int default_N(const sos_filter *, int64_t) { return 64; }
 
 sos_status ensure_desc(sos_filter *f, long long G, cudaStream_t s) {
     if (static_cast<size_t>(G) <= f->desc_groups && f->d_desc) return SOS_OK;
+    if (stream_capturing(s)) return SOS_EINVAL;  // no allocation inside a capture: run it once eagerly first
     size_t want = static_cast<size_t>(G);
     if (want < 1024) want = 1024;
     if (f->d_desc) {
@@ -581,13 +582,41 @@ sos_status ensure_desc(sos_filter *f, long long G, cudaStream_t s) {
     return SOS_OK;
 }
 
+// The tag of every launch captured into a CUDA graph; eager launches never use it.
+constexpr unsigned kCaptureEpoch = 0x3fffffffu;
+
 unsigned next_epoch(sos_filter *f, cudaStream_t s) {
-    f->epoch = (f->epoch + 1) & 0x3fffffffu;
-    if (f->epoch == 0) {  // wrapped: clear stale tags so no old descriptor matches
+    f->epoch = f->epoch + 1;
+    if (f->epoch >= kCaptureEpoch) {  // wrapped: clear stale tags so no old descriptor matches
         cudaMemsetAsync(f->d_desc, 0, f->desc_groups * sosk::kMaxPass * 2 * sizeof(unsigned long long), s);
         f->epoch = 1;
     }
     return f->epoch;
+}
+
+bool stream_capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &st) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return st == cudaStreamCaptureStatusActive;
+}
+
+// A launch being captured into a CUDA graph takes the filter's second ticket counter and the capture
+// tag, and the graph resets both the counter and the launch's descriptors before the kernel, so that
+// every replay starts afresh whatever ran before it; the eager launches' counter and tags are left
+// as they are.  The workspace must already be large enough (no allocation while capturing).
+sos_status capture_setup(sos_filter *f, cudaStream_t s, size_t desc_words, unsigned long long **ticket,
+                         unsigned long long *base, unsigned *epoch) {
+    if (!f->d_desc || desc_words > f->desc_groups * sosk::kMaxPass * 2) return SOS_EINVAL;
+    if (cudaMemsetAsync(f->d_ticket + 1, 0, sizeof(unsigned long long), s) != cudaSuccess ||
+        cudaMemsetAsync(f->d_desc, 0, desc_words * sizeof(unsigned long long), s) != cudaSuccess)
+        return SOS_ECUDA;
+    *ticket = f->d_ticket + 1;
+    *base = 0;
+    *epoch = kCaptureEpoch;
+    return SOS_OK;
 }
 
 bool ranges_overlap(const void *a, const void *b, int64_t n) {
@@ -1043,6 +1072,49 @@ sos_status launch_batch_any(int K, bool norm, const sosk::BatchSig *sigs, const 
 
 // All signals of a batch in one persistent launch per (K, normalized) class; the class launches run
 // on forked streams, joined back into `s`.  Filters of more than eight sections run one by one.
+// The single batch kernel's parameters: one queue per class present (its signal descriptors, tile ->
+// signal map, lookback descriptors and ticket counter), the grid, and each class's share of the
+// grid to start on, in proportion to its work (tiles x (2 + K), the particular pass and correction
+// growing with K).
+sos_status batch_all_params(const long long *cls_sigs, const long long *cls_tiles, const long long *sig_off,
+                            const long long *tile_off, const long long *desc_off, const sosk::BatchSig *d_sigs,
+                            const int *d_tile_sig, unsigned long long *d_desc, unsigned long long *d_ticket,
+                            unsigned epoch, int *d_status, int device, sosk::BatchAllParams &ap, long long &grid) {
+    std::memset(&ap, 0, sizeof ap);
+    double work[kBatchClasses] = {0.0}, total = 0.0;
+    long long tiles = 0;
+    int nc = 0;
+    for (int c = 0; c < kBatchClasses; ++c) {
+        if (cls_sigs[c] == 0) continue;
+        ap.code[nc] = c;
+        ap.q[nc] = sosk::BatchQueue{d_sigs + sig_off[c], d_tile_sig + tile_off[c], cls_tiles[c], d_desc + desc_off[c],
+                                    d_ticket + c, 0ULL, epoch};
+        work[nc] = static_cast<double>(cls_tiles[c]) * (2 + c / 2 + 1);
+        total += work[nc];
+        tiles += cls_tiles[c];
+        ++nc;
+    }
+    ap.n_classes = nc;
+    ap.status = d_status;
+    ap.spin_budget = kDefaultSpinBudget;
+    const int bps = sosk::batch_all_blocks_per_sm();
+    if (bps <= 0) return SOS_ECUDA;
+    grid = static_cast<long long>(bps) * sm_count(device);
+    if (grid > tiles) grid = tiles;
+    // shares: at least one block per class while blocks last, the rest by work
+    double acc = 0.0;
+    ap.blk_off[0] = 0;
+    for (int i = 0; i < nc; ++i) {
+        acc += work[i];
+        long long end = static_cast<long long>(acc / total * static_cast<double>(grid) + 0.5);
+        if (end <= ap.blk_off[i]) end = ap.blk_off[i] + 1;
+        if (end > grid) end = grid;
+        ap.blk_off[i + 1] = static_cast<int>(end);
+    }
+    ap.blk_off[nc] = static_cast<int>(grid);
+    return SOS_OK;
+}
+
 sos_status run_batch_impl(int n_signals, sos_filter *const *filters, const float *const *x, float *const *y,
                           const int64_t *n, const float *const *zi, float *const *zf, cudaStream_t s) {
     if (n_signals < 0) return SOS_EINVAL;
@@ -1176,33 +1248,19 @@ sos_status run_batch_impl(int n_signals, sos_filter *const *filters, const float
 
     // one persistent launch per class, each on its own stream forked from and joined into s (a
     // single class runs on s itself)
-    const bool fork = n_cls > 1;
-    if (fork && cudaEventRecord(sl.fork, s) != cudaSuccess) return SOS_ECUDA;
-    const long long budget = kDefaultSpinBudget;
-    for (int c = 0; c < kBatchClasses; ++c) {
-        if (cls_sigs[c] == 0) continue;
-        const int K = c / 2 + 1;
-        const bool norm = (c & 1) != 0;
-        cudaStream_t cs = fork ? sl.side[c] : s;
-        if (fork && cudaStreamWaitEvent(cs, sl.fork, 0) != cudaSuccess) return SOS_ECUDA;
-        ctx->epoch = (ctx->epoch + 1) & 0x3fffffffu;
-        if (ctx->epoch == 0) {  // wrapped: clear stale tags of every slot's descriptors
-            for (auto &o : ctx->slot)
-                if (o.d_desc) cudaMemsetAsync(o.d_desc, 0, o.desc_cap * sizeof(unsigned long long), cs);
-            ctx->epoch = 1;
-        }
-        const int bps = sosk::batch_blocks_per_sm(K, norm);
-        if (bps <= 0) return SOS_ECUDA;
-        long long grid = static_cast<long long>(bps) * sm_count(device);
-        if (grid > cls_tiles[c]) grid = cls_tiles[c];
-        sos_status st = launch_batch_any(K, norm, d_sigs + sig_off[c], d_tile_sig + tile_off[c], cls_tiles[c],
-                                         sl.d_desc + desc_off[c], sl.d_ticket + c, ctx->epoch, ctx->d_status, budget,
-                                         grid, cs);
-        if (st != SOS_OK) return st;
-        if (fork && (cudaEventRecord(sl.join[c], cs) != cudaSuccess ||
-                     cudaStreamWaitEvent(s, sl.join[c], 0) != cudaSuccess))
-            return SOS_ECUDA;
+    // one persistent launch over every class (sos_batch_all_kernel)
+    ctx->epoch = (ctx->epoch + 1) & 0x3fffffffu;
+    if (ctx->epoch == 0) {  // wrapped: clear stale tags of every slot's descriptors
+        for (auto &o : ctx->slot)
+            if (o.d_desc) cudaMemsetAsync(o.d_desc, 0, o.desc_cap * sizeof(unsigned long long), s);
+        ctx->epoch = 1;
     }
+    sosk::BatchAllParams ap;
+    long long grid = 0;
+    sos_status pst = batch_all_params(cls_sigs, cls_tiles, sig_off, tile_off, desc_off, d_sigs, d_tile_sig, sl.d_desc,
+                                      sl.d_ticket, ctx->epoch, ctx->d_status, device, ap, grid);
+    if (pst != SOS_OK) return pst;
+    if (sosk::launch_batch_all(ap, grid, s) != cudaSuccess) return SOS_ECUDA;
     if (cudaEventRecord(sl.done, s) != cudaSuccess) return SOS_ECUDA;
     sl.pending = true;
     return SOS_OK;
@@ -1722,19 +1780,27 @@ sos_status sos_batch_plan_launch(sos_batch_plan *p, void *stream) {
     // fresh descriptors (tag 0 never matches) and tickets each launch: a launch enqueues no host work
     // and may be captured into a CUDA graph and replayed
     if (cudaMemsetAsync(p->d_desc, 0, sizeof(unsigned long long) * p->desc_words, s) != cudaSuccess ||
-        cudaMemsetAsync(p->d_ticket, 0, sizeof(unsigned long long) * kBatchClasses, s) != cudaSuccess ||
-        cudaEventRecord(p->fork, s) != cudaSuccess)
+        cudaMemsetAsync(p->d_ticket, 0, sizeof(unsigned long long) * kBatchClasses, s) != cudaSuccess)
         return SOS_ECUDA;
+    // one persistent launch over every class: the plan's queues, each class at offset 0 of its own
+    // signal and tile arrays
+    long long cls_sigs[kBatchClasses], cls_tiles[kBatchClasses], zero[kBatchClasses + 1] = {0};
+    long long desc_off[kBatchClasses + 1] = {0};
     for (int c = 0; c < kBatchClasses; ++c) {
-        if (!p->tiles[c]) continue;
-        cudaStream_t cs = p->side[c];
-        if (cudaStreamWaitEvent(cs, p->fork, 0) != cudaSuccess) return SOS_ECUDA;
-        sos_status st = launch_batch_any(p->K[c], p->norm[c], p->sigs[c], p->tile_sig[c], p->tiles[c], p->desc[c],
-                                         p->d_ticket + c, 1u, p->d_status, kDefaultSpinBudget, p->grid[c], cs);
-        if (st != SOS_OK) return st;
-        if (cudaEventRecord(p->join[c], cs) != cudaSuccess || cudaStreamWaitEvent(s, p->join[c], 0) != cudaSuccess)
-            return SOS_ECUDA;
+        cls_sigs[c] = p->tiles[c] ? 1 : 0;
+        cls_tiles[c] = p->tiles[c];
+        desc_off[c] = p->desc[c] ? p->desc[c] - p->d_desc : 0;
     }
+    sosk::BatchAllParams ap;
+    long long grid = 0;
+    sos_status st = batch_all_params(cls_sigs, cls_tiles, zero, zero, desc_off, nullptr, nullptr, p->d_desc,
+                                     p->d_ticket, 1u, p->d_status, p->device, ap, grid);
+    if (st != SOS_OK) return st;
+    for (int i = 0; i < ap.n_classes; ++i) {  // the plan keeps each class's arrays apart
+        ap.q[i].sigs = p->sigs[ap.code[i]];
+        ap.q[i].tile_sig = p->tile_sig[ap.code[i]];
+    }
+    if (sosk::launch_batch_all(ap, grid, s) != cudaSuccess) return SOS_ECUDA;
     return SOS_OK;
 }
 

@@ -7,6 +7,13 @@ namespace {
 template <int K, bool NORM>
 KernelOnce g_once;
 
+// One class per launch (the prepared plans' per-class form and the reference for the single kernel).
+template <int K, bool NORM>
+__global__ void __launch_bounds__((kBatchW + 1) * 32, 1) sos_batch_kernel(const __grid_constant__ BatchParams<K> p) {
+    extern __shared__ float4 smem4[];
+    batch_body<K, NORM>(p, smem4);
+}
+
 template <int K, bool NORM>
 cudaError_t launch_k(const BatchParams<K> &p, long long grid, cudaStream_t s) {
     auto kern = sos_batch_kernel<K, NORM>;

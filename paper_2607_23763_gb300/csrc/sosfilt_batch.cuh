@@ -74,15 +74,16 @@ __device__ __forceinline__ float lane_mv_rows(const float (&r)[S], float xi) {
     return y;
 }
 
+// One block's share of a class of the batch (signals of K sections with the same b0 handling): the
+// block draws tiles from the class's ticket counter until the class is exhausted, then returns.
 template <int K, bool NORM>
-__global__ void __launch_bounds__((kBatchW + 1) * 32, 1) sos_batch_kernel(const __grid_constant__ BatchParams<K> p) {
+__device__ __forceinline__ void batch_body(const BatchParams<K> &p, float4 *smem4) {
     using Dm = LaneDims<K, kBatchN>;
     constexpr int S = Dm::S, MS = Dm::MS, N = kBatchN, W = kBatchW, CH = Dm::LQ, RPS = Dm::RPS, RSP = Dm::RSP;
     static_assert(Dm::V == 4 && Dm::CC == CH, "the batch kernel corrects four samples per lane and step");
     constexpr int P = N + 4;  // padded row pitch (floats): conflict-free 128-bit row access
     constexpr int C = N * kL;
     constexpr int SZ = ((S + 3) / 4) * 4;
-    extern __shared__ float4 smem4[];
     float *rows = reinterpret_cast<float *>(smem4);  // [W][3][32][P]: three row buffers per warp
     float *rowst = rows + W * 3 * kL * P;            // [W][32][RSP] rows' true incoming states
     float *a_buf = rowst + W * kL * RSP;             // [2][W][S] local carries of the groups

@@ -222,6 +222,32 @@ struct BatchParams {
     long long spin_budget;
 };
 
+// One class's queue in the single-kernel batch (the fields of BatchParams that do not depend on K).
+struct BatchQueue {
+    const BatchSig *sigs;
+    const int *tile_sig;
+    long long n_tiles;
+    unsigned long long *desc;
+    unsigned long long *ticket;
+    unsigned long long ticket_base;
+    unsigned int epoch;
+};
+
+constexpr int kBatchClassesMax = 16;  // (K, b0-normalized) classes: K = 1..8, normalized or not
+
+struct BatchAllParams {
+    int n_classes;
+    int code[kBatchClassesMax];         // class code: 2 (K - 1) + b0-normalized
+    int blk_off[kBatchClassesMax + 1];  // blocks [blk_off[c], blk_off[c + 1]) start on class c
+    BatchQueue q[kBatchClassesMax];
+    int *status;
+    long long spin_budget;
+};
+
+// Launch the single persistent kernel over every class of a batch (sosfilt_batch.cu).
+cudaError_t launch_batch_all(const BatchAllParams &p, long long grid, cudaStream_t s);
+int batch_all_blocks_per_sm();
+
 template <int K>
 cudaError_t launch_batch(bool norm, const BatchParams<K> &p, long long grid, cudaStream_t s);
 #define SOSK_DECLARE_BATCH(K) \

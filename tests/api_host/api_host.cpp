@@ -160,6 +160,7 @@ int lane_blocks_per_sm_n64b(int, bool) { return 1; }
 int lane_blocks_per_sm_n64w10a(int, bool) { return 1; }
 int lane_blocks_per_sm_n64w10b(int, bool) { return 1; }
 int batch_blocks_per_sm(int, bool) { return 1; }
+int batch_all_blocks_per_sm() { return 1; }
 int dtcr_blocks_per_sm(int, bool) { return 1; }
 int default_lbm(int N) { return N <= 32 ? 4 : N == 64 ? 2 : 1; }
 
@@ -195,6 +196,27 @@ cudaError_t launch_dccr(int K, int N, bool norm, int, const PassParams &p, long 
         }                                                                                            \
         return cudaSuccess;                                                                          \
     }
+// The single batch kernel: counted, and recorded as one launch record per class it covers (the
+// class's queue in the layout of BatchParams, so the tests read every class alike).
+long long g_batch_all_launches = 0;
+cudaError_t launch_batch_all(const BatchAllParams &p, long long grid, cudaStream_t) {
+    ++g_batch_all_launches;
+    for (int i = 0; i < p.n_classes; ++i) {
+        const BatchQueue &q = p.q[i];
+        const BatchParams<1> bp{q.sigs, q.tile_sig, q.n_tiles, q.desc, q.ticket, q.ticket_base, q.epoch, p.status,
+                                p.spin_budget};
+        const int K = p.code[i] / 2 + 1;
+        record(3, K, 64, (p.code[i] & 1) != 0, grid, bp);
+        if (g_light) continue;
+        std::set<int> sigs(q.tile_sig, q.tile_sig + q.n_tiles);
+        for (int j : sigs) {
+            const BatchSig &g = q.sigs[j];
+            mark(g.x, g.y, g.n, g.zi, g.zf, K);
+        }
+    }
+    return cudaSuccess;
+}
+
 #define HOST_DTCR(K)                                                                                \
     template <>                                                                                     \
     cudaError_t launch_dtcr<K>(bool norm, const CasParams<K, 64> &p, long long grid, cudaStream_t) { \
@@ -252,6 +274,8 @@ void host_reset(void) { g_launches.clear(); }
 void host_set_light(int on) { g_light = on != 0; }
 void host_set_cost(int kind, int N, int K, float ms) { g_cost[kind][n_index(N)][K] = ms; }
 int host_launches(void) { return static_cast<int>(g_launches.size()); }
+// single-kernel batch launches so far
+long long host_batch_all_launches(void) { return sosk::g_batch_all_launches; }
 // kind (1 PH lane, 2 cyclic-reduction cascade, 3 batch, 4 per-section cyclic reduction, 5 double-
 // thread-group cyclic reduction), K, N,
 // b0 normalization, grid; returns the parameter block's size and copies up to cap bytes of it

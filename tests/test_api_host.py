@@ -341,6 +341,8 @@ def test_batched_plan_groups_signals_by_class_with_consecutive_tiles(lib):
     arr = lambda vals: (ctypes.c_void_p * m)(*vals)
     lens = (ctypes.c_int64 * m)(*[n for _, n in specs])
     lib.host_reset()
+    lib.host_batch_all_launches.restype = ctypes.c_longlong
+    all_before = lib.host_batch_all_launches()
     rc = lib.sos_filter_run_batch_ex(m, arr([h.value for h in fs]), arr([x.ctypes.data for x in xs]),
                                      arr([y.ctypes.data for y in ys]), lens, arr([z.ctypes.data for z in zis]),
                                      arr([z.ctypes.data for z in zfs]), None)
@@ -349,7 +351,9 @@ def test_batched_plan_groups_signals_by_class_with_consecutive_tiles(lib):
     lib.host_batch_layout(lay)
     _, sig_size, ox, oy, on, oG, ot0, ozi, ozf, otab, ogain, p_sigs, p_tile_sig, p_ntiles, _, _, _ = lay
     launches = _launches(lib)
-    assert all(l["kind"] == KIND_BATCH for l in launches)
+    # one persistent launch covers every class (recorded once per class)
+    assert lib.host_batch_all_launches() - all_before == 1
+    assert all(l["kind"] == KIND_BATCH for l in launches) and len({l["grid"] for l in launches}) == 1
     seen = []
     for l in launches:
         raw = l["raw"]
@@ -373,7 +377,7 @@ def test_batched_plan_groups_signals_by_class_with_consecutive_tiles(lib):
             tiles += nt
             seen.append(i)
         assert tiles == n_tiles  # the map holds exactly the class's signals' tiles
-    # every signal with samples is in exactly one class launch; the empty ones copy their state
+    # every signal with samples is in exactly one class; the empty ones copy their state
     assert sorted(seen) == [i for i, (_, n) in enumerate(specs) if n > 0]  # once each
     for i, (sos, n) in enumerate(specs):
         if n:
@@ -623,8 +627,8 @@ def test_batch_tables_match_a_float64_derivation(lib):
 
 
 def test_batch_plan_launches_reuse_the_uploaded_plan(lib):
-    """A prepared plan uploads its signals once; every launch then runs one class launch per
-    (section count, b0 handling) over the same descriptors."""
+    """A prepared plan uploads its signals once; every launch then runs one persistent launch over
+    every (section count, b0 handling) class, on the same descriptors."""
     vp = ctypes.c_void_p
     lib.sos_batch_plan_create.argtypes = [ctypes.c_int, vp, vp, vp, vp, vp, vp, ctypes.POINTER(vp)]
     lib.sos_batch_plan_launch.argtypes = [vp, vp]
@@ -647,6 +651,7 @@ def test_batch_plan_launches_reuse_the_uploaded_plan(lib):
         assert lib.sos_batch_plan_launch(plan, None) == 0
         ls = _launches(lib)
         assert sorted((l["kind"], l["K"]) for l in ls) == [(KIND_BATCH, 1), (KIND_BATCH, 4), (KIND_BATCH, 8)]
+        assert len({l["grid"] for l in ls}) == 1  # the classes of one launch
         for x, y in zip(xs, ys):
             np.testing.assert_array_equal(y, 2 * x)
     assert lib.sos_batch_plan_status(plan) == 0
