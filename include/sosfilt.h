@@ -156,6 +156,12 @@ sos_status sos_filter_destroy(sos_filter *f);
  *   stream  cudaStream_t as void*
  * Ownership: the caller owns x, y, zi, zf; the library owns its workspace
  * (lookback descriptors, ticket counter, status word), grown on demand.
+ * CUDA graphs: a run may be captured into a graph on `stream` (solvers PH, DTCR and
+ * cyclic reduction with the cascade carry; per-section carries give SOS_EINVAL).
+ * A captured run resets its own ticket counter and lookback descriptors inside the
+ * graph, so every replay starts afresh; it allocates nothing, so the filter must
+ * have run once outside the capture on a signal at least as long (else SOS_EINVAL).
+ * Replays must not overlap each other or other runs of the same filter.
  */
 sos_status sos_filter_run(sos_filter *f, const float *x_dev, float *y_dev, int64_t n, const float *zi_dev,
                           float *zf_dev, void *stream);

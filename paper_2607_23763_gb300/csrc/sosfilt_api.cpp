@@ -182,7 +182,7 @@ struct sos_filter {
     // workspace
     unsigned long long *d_desc = nullptr;
     size_t desc_groups = 0;  // capacity in groups (per section slot)
-    unsigned long long *d_ticket = nullptr;
+    unsigned long long *d_ticket = nullptr;  // [2]: eager launches' counter, captured launches' counter
     unsigned long long ticket_base = 0;
     unsigned int epoch = 0;
     int *d_status = nullptr;
@@ -560,39 +560,8 @@ int table_index(int N) {
 // (N = 128 is built for b0-normalized filters only and is never the default).
 int default_N(const sos_filter *, int64_t) { return 64; }
 
-sos_status ensure_desc(sos_filter *f, long long G, cudaStream_t s) {
-    if (static_cast<size_t>(G) <= f->desc_groups && f->d_desc) return SOS_OK;
-    if (stream_capturing(s)) return SOS_EINVAL;  // no allocation inside a capture: run it once eagerly first
-    size_t want = static_cast<size_t>(G);
-    if (want < 1024) want = 1024;
-    if (f->d_desc) {
-        cudaStreamSynchronize(s);
-        cudaFree(f->d_desc);
-        f->d_desc = nullptr;
-        f->desc_groups = 0;
-    }
-    const size_t bytes = want * sosk::kMaxPass * 2 * sizeof(unsigned long long);
-    if (cudaMalloc(&f->d_desc, bytes) != cudaSuccess) {
-        cudaGetLastError();
-        return SOS_ENOMEM;
-    }
-    if (cudaMemsetAsync(f->d_desc, 0, bytes, s) != cudaSuccess) return cuda_fail();
-    f->desc_groups = want;
-    f->epoch = 0;
-    return SOS_OK;
-}
-
 // The tag of every launch captured into a CUDA graph; eager launches never use it.
 constexpr unsigned kCaptureEpoch = 0x3fffffffu;
-
-unsigned next_epoch(sos_filter *f, cudaStream_t s) {
-    f->epoch = f->epoch + 1;
-    if (f->epoch >= kCaptureEpoch) {  // wrapped: clear stale tags so no old descriptor matches
-        cudaMemsetAsync(f->d_desc, 0, f->desc_groups * sosk::kMaxPass * 2 * sizeof(unsigned long long), s);
-        f->epoch = 1;
-    }
-    return f->epoch;
-}
 
 bool stream_capturing(cudaStream_t s) {
     cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
@@ -619,6 +588,39 @@ sos_status capture_setup(sos_filter *f, cudaStream_t s, size_t desc_words, unsig
     return SOS_OK;
 }
 
+sos_status ensure_desc(sos_filter *f, long long G, cudaStream_t s) {
+    if (static_cast<size_t>(G) <= f->desc_groups && f->d_desc) return SOS_OK;
+    if (stream_capturing(s)) return SOS_EINVAL;  // no allocation inside a capture: run it once eagerly first
+    size_t want = static_cast<size_t>(G);
+    if (want < 1024) want = 1024;
+    if (f->d_desc) {
+        cudaStreamSynchronize(s);
+        cudaFree(f->d_desc);
+        f->d_desc = nullptr;
+        f->desc_groups = 0;
+    }
+    const size_t bytes = want * sosk::kMaxPass * 2 * sizeof(unsigned long long);
+    if (cudaMalloc(&f->d_desc, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return SOS_ENOMEM;
+    }
+    if (cudaMemsetAsync(f->d_desc, 0, bytes, s) != cudaSuccess) return cuda_fail();
+    f->desc_groups = want;
+    f->epoch = 0;
+    return SOS_OK;
+}
+
+unsigned next_epoch(sos_filter *f, cudaStream_t s) {
+    f->epoch = f->epoch + 1;
+    if (f->epoch >= kCaptureEpoch) {  // wrapped: clear stale tags so no old descriptor matches
+        cudaMemsetAsync(f->d_desc, 0, f->desc_groups * sosk::kMaxPass * 2 * sizeof(unsigned long long), s);
+        f->epoch = 1;
+    }
+    return f->epoch;
+}
+
+
+
 bool ranges_overlap(const void *a, const void *b, int64_t n) {
     const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
     const uintptr_t bytes = static_cast<uintptr_t>(n) * sizeof(float);
@@ -628,6 +630,7 @@ bool ranges_overlap(const void *a, const void *b, int64_t n) {
 // Per-section carries: one decoupled lookback per section and thread block (sosfilt_dccr.cuh).
 sos_status run_sections(sos_filter *f, const float *x, float *y, int64_t n, const float *zi, float *zf,
                         cudaStream_t s) {
+    if (stream_capturing(s)) return SOS_EINVAL;  // per-section carries are not captured into graphs
     int N = f->tuning.N ? f->tuning.N : default_N(f, n);
     if (N == 128 && !f->norm) N = 64;
     const int ti = table_index(N);
@@ -703,9 +706,16 @@ sos_status launch_cascade_pass(sos_filter *f, CasPass &ps, const sosk::SecCoef *
     p->zf = zf;
     p->gain = first ? static_cast<float>(f->gain) : 1.0f;
     p->desc = f->d_desc;
-    p->ticket = f->d_ticket;
-    p->ticket_base = f->ticket_base;
-    p->epoch = next_epoch(f, s);
+    const bool eager = !stream_capturing(s);
+    if (eager) {
+        p->ticket = f->d_ticket;
+        p->ticket_base = f->ticket_base;
+        p->epoch = next_epoch(f, s);
+    } else {
+        const sos_status cst = capture_setup(f, s, static_cast<size_t>(n_tiles) * 2 * K, &p->ticket,
+                                             &p->ticket_base, &p->epoch);
+        if (cst != SOS_OK) return cst;
+    }
     p->status = f->d_status;
     p->spin_budget = f->tuning.spin_budget_cycles ? f->tuning.spin_budget_cycles : kDefaultSpinBudget;
     p->aligned = aligned ? 1 : 0;
@@ -731,7 +741,7 @@ sos_status launch_cascade_pass(sos_filter *f, CasPass &ps, const sosk::SecCoef *
     else
         e = sosk::launch_cascade<K, N>(f->norm, *p, grid, s);
     if (e != cudaSuccess) return SOS_ECUDA;
-    f->ticket_base += static_cast<unsigned long long>(n_tiles + grid);
+    if (eager) f->ticket_base += static_cast<unsigned long long>(n_tiles + grid);
     return SOS_OK;
 }
 
@@ -841,12 +851,18 @@ sos_status launch_lane_pass(sos_filter *f, LanePass &ps, const float *x, float *
         p->ticket = sc->ticket;
         p->ticket_base = 0;
         p->epoch = sc_epoch;
+    } else if (stream_capturing(s)) {
+        p->desc = f->d_desc;
+        const sos_status cst = capture_setup(f, s, static_cast<size_t>(n_tiles) * 2 * 2 * K, &p->ticket,
+                                             &p->ticket_base, &p->epoch);
+        if (cst != SOS_OK) return cst;
     } else {
         p->desc = f->d_desc;
         p->ticket = f->d_ticket;
         p->ticket_base = f->ticket_base;
         p->epoch = next_epoch(f, s);
     }
+    const bool eager = !sc && p->ticket == f->d_ticket;
     p->status = f->d_status;
     p->spin_budget = f->tuning.spin_budget_cycles ? f->tuning.spin_budget_cycles : kDefaultSpinBudget;
     p->aligned = aligned ? 1 : 0;
@@ -861,7 +877,7 @@ sos_status launch_lane_pass(sos_filter *f, LanePass &ps, const float *x, float *
     if (zf) std::memcpy(p->A_tail, &ps.Mm[static_cast<size_t>(m_last) * packed_floats(K)], sizeof(float) * packed_floats(K));
     cudaError_t e = sosk::launch_lane<K, N, W>(f->norm, *p, grid, s);
     if (e != cudaSuccess) return SOS_ECUDA;
-    if (!sc) f->ticket_base += static_cast<unsigned long long>(n_tiles + grid);
+    if (eager) f->ticket_base += static_cast<unsigned long long>(n_tiles + grid);
     return SOS_OK;
 }
 
@@ -1591,13 +1607,13 @@ sos_status sos_filter_create(int n_sections, const double *sos, const float *zi,
         f->bt.cls = f->K > sosk::kMaxPass ? -1 : (f->K - 1) * 2 + (f->norm ? 1 : 0);
     }
     if (st == SOS_OK) {
-        if (cudaMalloc(&f->d_ticket, sizeof(unsigned long long)) != cudaSuccess ||
+        if (cudaMalloc(&f->d_ticket, 2 * sizeof(unsigned long long)) != cudaSuccess ||  // eager, captured
             cudaMalloc(&f->d_status, sizeof(int)) != cudaSuccess ||
             cudaMalloc(&f->d_state, sizeof(float) * 2 * n_sections) != cudaSuccess)
             st = SOS_ENOMEM;
     }
     if (st == SOS_OK) {
-        if (cudaMemset(f->d_ticket, 0, sizeof(unsigned long long)) != cudaSuccess ||
+        if (cudaMemset(f->d_ticket, 0, 2 * sizeof(unsigned long long)) != cudaSuccess ||
             cudaMemset(f->d_status, 0, sizeof(int)) != cudaSuccess)
             st = SOS_ECUDA;
         std::vector<float> z(2 * n_sections, 0.f);

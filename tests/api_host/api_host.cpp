@@ -112,6 +112,11 @@ cudaError_t cudaStreamCreateWithFlags(cudaStream_t *s, unsigned) {
     return cudaSuccess;
 }
 cudaError_t cudaStreamSynchronize(cudaStream_t) { return cudaSuccess; }
+bool g_capturing = false;  // host_set_capturing: every stream reports an active capture
+cudaError_t cudaStreamIsCapturing(cudaStream_t, cudaStreamCaptureStatus *st) {
+    *st = g_capturing ? cudaStreamCaptureStatusActive : cudaStreamCaptureStatusNone;
+    return cudaSuccess;
+}
 cudaError_t cudaStreamDestroy(cudaStream_t s) {
     delete s;
     return cudaSuccess;
@@ -272,6 +277,7 @@ int host_run_scratch(sos_filter *f, const float *x, float *y, long long n, const
 }
 void host_reset(void) { g_launches.clear(); }
 void host_set_light(int on) { g_light = on != 0; }
+void host_set_capturing(int on) { g_capturing = on != 0; }
 void host_set_cost(int kind, int N, int K, float ms) { g_cost[kind][n_index(N)][K] = ms; }
 int host_launches(void) { return static_cast<int>(g_launches.size()); }
 // single-kernel batch launches so far

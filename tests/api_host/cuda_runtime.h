@@ -20,6 +20,7 @@ typedef struct host_stream *cudaStream_t;
 typedef struct host_event *cudaEvent_t;
 enum cudaMemcpyKind { cudaMemcpyHostToDevice = 1, cudaMemcpyDeviceToHost = 2, cudaMemcpyDeviceToDevice = 3 };
 enum cudaDeviceAttr { cudaDevAttrMultiProcessorCount = 16 };
+enum cudaStreamCaptureStatus { cudaStreamCaptureStatusNone = 0, cudaStreamCaptureStatusActive = 1 };
 #define cudaStreamNonBlocking 1
 #define cudaEventDisableTiming 2
 
@@ -39,6 +40,7 @@ cudaError_t cudaMemset(void *dst, int value, size_t bytes);
 cudaError_t cudaMemsetAsync(void *dst, int value, size_t bytes, cudaStream_t s = nullptr);
 cudaError_t cudaStreamCreateWithFlags(cudaStream_t *stream, unsigned flags);
 cudaError_t cudaStreamSynchronize(cudaStream_t stream);
+cudaError_t cudaStreamIsCapturing(cudaStream_t stream, cudaStreamCaptureStatus *status);
 cudaError_t cudaStreamDestroy(cudaStream_t stream);
 cudaError_t cudaStreamWaitEvent(cudaStream_t stream, cudaEvent_t event, unsigned flags = 0);
 cudaError_t cudaEventCreate(cudaEvent_t *event);

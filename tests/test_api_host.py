@@ -735,6 +735,63 @@ def test_launch_parameters_follow_the_filter_settings(lib):
     lib.sos_filter_destroy(f)
 
 
+@pytest.mark.parametrize("tuning,kind,words_per_tile,W_tile", [(None, KIND_LANE, 4, 7), ({"solver": 1, "N": 64}, KIND_CASCADE, 2, 4),
+                                                      ({"solver": 3}, KIND_DTCR, 2, 4)])
+def test_a_captured_run_resets_its_own_counter_and_descriptors(lib, tuning, kind, words_per_tile, W_tile):
+    """A run on a stream that is being captured into a CUDA graph takes the filter's second ticket
+    counter, base 0 and the capture tag, and clears that counter and its descriptors first (inside the
+    graph), leaving the eager launches' counter and ticket base as they were; it allocates nothing,
+    so a run whose workspace would have to grow is refused during capture."""
+    lib.host_set_capturing.argtypes = [ctypes.c_int]
+    K = 4
+    f = _create(lib, designs.butter_lowpass(2 * K, 0.2), tuning)
+    N = 64
+    n = 3 * W_tile * 32 * N + 5
+    x = workloads.normal_f32(16, n)
+    y = np.empty_like(x)
+    offs = (ctypes.c_longlong * 21)()
+    lib.host_lane_layout(K, offs)
+    lib.host_reset()
+    assert lib.sos_filter_run(f, x.ctypes.data, y.ctypes.data, n, None, None, None) == 0  # eager: workspace
+    (eager,) = _launches(lib)
+    if kind == KIND_LANE:
+        o_desc, o_ticket, o_base, o_epoch = offs[13], offs[14], offs[15], offs[16]
+    else:
+        c_offs = (ctypes.c_longlong * 8)()
+        lib.host_cas_layout.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+        lib.host_cas_layout(K, N, c_offs)
+        # CasParams: x, y, n, G, n_tiles, zi, zf, gain, desc, ticket, ticket_base, epoch
+        o_desc = 8 * 7 + 8
+        o_ticket, o_base, o_epoch = o_desc + 8, o_desc + 16, o_desc + 24
+    t_eager = int(_at(eager["raw"], o_ticket, np.uint64)[0])
+    base_eager = int(_at(eager["raw"], o_base, np.uint64)[0])
+    desc = int(_at(eager["raw"], o_desc, np.uint64)[0])
+    n_tiles = -(-(-(-n // (32 * N))) // W_tile)
+    used = _mem(desc, np.uint64, n_tiles * words_per_tile * K)
+    used[:] = 0xabab  # stale words left by earlier launches
+    _mem(t_eager + 8, np.uint64, 1)[:] = 777  # the captured counter's stale value
+    lib.host_set_capturing(1)
+    try:
+        lib.host_reset()
+        assert lib.sos_filter_run(f, x.ctypes.data, y.ctypes.data, n, None, None, None) == 0
+        (cap,) = _launches(lib)
+        assert int(_at(cap["raw"], o_ticket, np.uint64)[0]) == t_eager + 8
+        assert int(_at(cap["raw"], o_base, np.uint64)[0]) == 0
+        assert int(_at(cap["raw"], o_epoch, np.uint32)[0]) == 0x3fffffff
+        assert np.all(used == 0) and _mem(t_eager + 8, np.uint64, 1)[0] == 0
+        # no allocation while capturing: a longer signal than the workspace holds is refused
+        big = np.zeros(2048 * 32 * N, np.float32)  # 2048 groups: more than the workspace holds
+        assert lib.sos_filter_run(f, big.ctypes.data, big.ctypes.data, big.size, None, None, None) == -1
+    finally:
+        lib.host_set_capturing(0)
+    lib.host_reset()
+    assert lib.sos_filter_run(f, x.ctypes.data, y.ctypes.data, n, None, None, None) == 0  # eager again
+    (again,) = _launches(lib)
+    assert int(_at(again["raw"], o_ticket, np.uint64)[0]) == t_eager
+    assert int(_at(again["raw"], o_base, np.uint64)[0]) == base_eager + n_tiles + eager["grid"]
+    lib.sos_filter_destroy(f)
+
+
 def _tune_costs(lib, fastest):
     """Simulated launch times: the candidate fastest(K) takes 1 ms per launch, the others 2 and 3."""
     cands = [(KIND_CASCADE, 32), (KIND_CASCADE, 64), (KIND_LANE, 64), (KIND_DTCR, 64)]  # the autotuner's candidates

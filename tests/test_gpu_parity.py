@@ -309,6 +309,48 @@ def test_run_host_direct_on_pinned_buffers(dev):
     f.close()
 
 
+@pytest.mark.parametrize("tuning,order", [({"solver": SOLVER_PH}, 16), ({"solver": SOLVER_CR, "N": 64}, 16),
+                                          ({"solver": SOLVER_DTCR}, 16), ({"solver": SOLVER_PH}, 24)],
+                         ids=["ph", "cr-64", "dtcr", "ph-two-pass"])
+def test_run_captured_in_a_cuda_graph_and_replayed(dev, tuning, order):
+    """sos_filter_run captured into a CUDA graph: every replay resets the run's own ticket counter and
+    lookback descriptors inside the graph, so replays with new input each match the oracle, and eager
+    runs of the same filter before and after stay correct.  Twelve sections run as two passes of the
+    kernel, both in the graph, in stream order."""
+    from paper_2607_23763_gb300 import SosFilter
+    sos = designs.butter_lowpass(order, 0.1)
+    tol = designs.tolerance_for(sos)
+    n = 5 * 14336 + 333
+    f = SosFilter(sos, tuning=tuning)
+    x = torch.empty(n, device=dev)
+    y = torch.empty(n, device=dev)
+    x0 = workloads.normal_f32(40, n)
+    x.copy_(torch.from_numpy(x0))
+    f.run(x, y)  # eager: allocates the workspace
+    torch.cuda.synchronize()
+    assert _rel(y.cpu().numpy(), oracle.sosfilt(sos, x0)) < tol
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side):
+            f.run(x, y, stream=side)
+    torch.cuda.synchronize()
+    for rep in range(3):
+        xr = workloads.normal_f32(41 + rep, n)
+        x.copy_(torch.from_numpy(xr))
+        y.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        assert f.sync_status() == 0
+        err = _rel(y.cpu().numpy(), oracle.sosfilt(sos, xr))
+        assert err < tol, (rep, err)
+    y2 = f.run(x)  # eager again after the replays
+    torch.cuda.synchronize()
+    assert _rel(y2.cpu().numpy(), oracle.sosfilt(sos, xr)) < tol
+    f.close()
+
+
 def test_overlap_rejected(dev):
     from paper_2607_23763_gb300 import SosError
     f = _filt(designs.butter_lowpass(2, 0.2))
