@@ -40,7 +40,7 @@ CPU_SAMPLE = 1 << 24  # oracle sample per step of the reference arm
 # DRAM bytes (read + write) of one launch of the timed kernel on the 2^28 workload, per (solver, N):
 # an ncu capture of the same kernel on 2^26 samples scaled by 4.  An entry must be re-captured (or
 # removed) whenever its kernel changes.
-SOLVER_CR, SOLVER_PH, SOLVER_DTCR = 1, 2, 3
+SOLVER_CR, SOLVER_PH, SOLVER_DTCR, SOLVER_TC = 1, 2, 3, 4
 TRAFFIC_BYTES_2P28 = {
     # sos_lane_kernel<8, 64, 1, 7> at 2^26 samples: 268,859,904 B read + 211,708,672 B written
     (SOLVER_PH, 64): 4 * (268859904 + 211708672),
@@ -59,6 +59,9 @@ def kernel_name(solver: int, N: int, K: int, W: int = 0) -> str:
     if solver == SOLVER_DTCR:
         return (f"sos_dtcr_kernel<{k}, 64> (double-thread-group cyclic reduction, {k} sections, N = 64 samples per "
                 "lane, 4 groups of two warps per block)")
+    if solver == SOLVER_TC:
+        return (f"sos_tc_kernel<{k}> (PH factorization on the tensor cores: tcgen05 TF32 products split three "
+                f"ways, TMA staging; {k} sections, N = 64 samples per lane, 8 groups per block)")
     return (f"sos_cascade_kernel<{k}, {N}> (cyclic reduction, {k} sections, N = {N} samples per lane, "
             f"{CR_GROUPS_PER_BLOCK.get(N, '?')} groups per block)")
 
@@ -272,6 +275,25 @@ def fp32_fma_roof(torch, dev, sm_max_mhz):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     mhz = float(sm_max_mhz) if sm_max_mhz else 2070.0
     return sms * 128 * mhz * 1e6 / 1e12, f"derived: {sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz (max SM clock)"
+
+
+def tc_tensor_roofline(K: int, n: int, ms: float) -> dict:
+    """Tensor-core roofline of the PH kernel on the tensor cores.  Per 128-row unit (8192 samples) it
+    issues 24 TF32 MMAs of 128 x 80 x 8 (the Toeplitz and state-response products, three ways) and 6
+    (2K <= 8: 3) of 128 x 64 x 8 (the correction), i.e. 576 (528) flops per sample; the peak is the
+    measured bf16 burst rate times the nominal TF32 / bf16 ratio 1.1 / 2.25."""
+    corr = 6 if K > 4 else 3
+    flops_per_sample = (24 * 2 * 128 * 80 * 8 + corr * 2 * 128 * 64 * 8) / 8192
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            bf16, kind = float(json.load(fh)["bf16_tflops"]), "measured"
+    except Exception:
+        bf16, kind = 1900.0, "fallback"
+    peak = bf16 * 1.1 / 2.25
+    achieved = flops_per_sample * n / (ms * 1e-3) / 1e12
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "flops_per_sample": flops_per_sample, "peak_kind": kind,
+            "peak_how": "bf16 dense burst (MEASURED_PEAKS.json) x nominal TF32/bf16 ratio 1.1/2.25"}
 
 
 def chosen_kernel(K: int, n: int):
@@ -515,7 +537,7 @@ def bench_ours(args):
     if choice:
         kid = tuple(choice)
     elif args.solver:
-        kid = (args.solver, args.N or (64 if args.solver in (SOLVER_PH, SOLVER_DTCR) else 32), args.groups)
+        kid = (args.solver, args.N or (64 if args.solver in (SOLVER_PH, SOLVER_DTCR, SOLVER_TC) else 32), args.groups)
     elif args.carry or args.lbw:
         kid = (SOLVER_CR, args.N or 32, 0)
     else:
@@ -535,7 +557,7 @@ def bench_ours(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "samples": N_SAMPLES, "sections": K,
                    "N": kid[1], "L": 32, "groups_per_cta": kid[2] or None,
-                   "solver": {SOLVER_PH: "PH", SOLVER_CR: "CR", SOLVER_DTCR: "DTCR"}[kid[0]],
+                   "solver": {SOLVER_PH: "PH", SOLVER_CR: "CR", SOLVER_DTCR: "DTCR", SOLVER_TC: "PH-TC"}[kid[0]],
                    "deterministic": bool(args.deterministic),
                    "autotuned": choice is not None,
                    "l2": "inputs and outputs larger than L2 (1 GiB each)",
@@ -549,6 +571,10 @@ def bench_ours(args):
         "gpu_launches": args.steps,
         "clocks": clocks,
     }
+    if kid[0] == SOLVER_TC:
+        # the products run on the tensor cores, not the FP32 pipe: their TF32 rate instead
+        line.pop("roofline_alu")
+        line["roofline_tensor"] = tc_tensor_roofline(K, N_SAMPLES, ms_step)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"], line["accuracy"] = cpu_baseline_leg(sos, x_host, y)
         line["cpu_wavefront"] = cpu_wavefront_leg(x_host)
@@ -862,7 +888,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the autotuner (profiling runs: a fixed sequence of launches)")
     ap.add_argument("--carry", type=int, default=0, help="1 = one carry per tile for the cascade, 2 = per section")
-    ap.add_argument("--solver", type=int, default=0, help="1 = cyclic reduction, 2 = PH factorization; 0 = default")
+    ap.add_argument("--solver", type=int, default=0,
+                    help="1 = cyclic reduction, 2 = PH factorization, 3 = DTCR, 4 = PH on the tensor cores; 0 = default")
     ap.add_argument("--deterministic", action="store_true",
                     help="fixed lookback composition (bit-reproducible outputs; PH solver)")
     ap.add_argument("--lbw", type=int, default=0, help="lookback width (predecessor blocks per round / 32); 0 = default")

@@ -78,10 +78,19 @@ enum {
                                are independent), a lane scan of the whole cascade state and one
                                homogeneous correction for lane and group states; cascade carry
                                only, N = 32 or 64 (default 64) */
-    SOS_SOLVER_DTCR = 3     /* double-thread-group cyclic reduction (Sec. IV-E): cyclic reduction
+    SOS_SOLVER_DTCR = 3,    /* double-thread-group cyclic reduction (Sec. IV-E): cyclic reduction
                                with the even- and odd-parity chains of every group on two warps,
                                exchanging through shared memory at each section (two barriers per
                                section); cascade carry only, N = 64 (tiles of four groups) */
+    SOS_SOLVER_TC = 4       /* PH factorization (Sec. II-C) on the tensor cores: a lane's particular
+                               solution is its 64 samples times the lower-triangular Toeplitz matrix
+                               of the cascade's first 64 impulse-response taps (the inverse of the
+                               lane's band matrix), its terminal state the product with the 64 state
+                               responses, and the homogeneous correction (Eq. 24) the product of the
+                               lanes' true states with the output basis; TF32 products with every
+                               float32 operand split into head and remainder (float32 accuracy).
+                               Cascade carry only, N = 64, tiles of 8 groups.  Needs x and y
+                               16-byte aligned and n >= 64; other runs use SOS_SOLVER_PH */
 };
 
 /*
@@ -104,10 +113,11 @@ enum {
  *                      round, in units of 32: 1, 2, 4, 8 or 16 (values other than
  *                      the default for N exist for 8-section passes with b0 != 0)
  *   carry              SOS_CARRY_DEFAULT, SOS_CARRY_CASCADE or SOS_CARRY_SECTION
- *   solver             SOS_SOLVER_DEFAULT, SOS_SOLVER_CR, SOS_SOLVER_PH or SOS_SOLVER_DTCR (see
- *                      SOS_SOLVER_*); SOS_SOLVER_PH takes N = 0, 32 or 64, SOS_SOLVER_DTCR N = 0 or 64,
- *                      both carry SOS_CARRY_DEFAULT or SOS_CARRY_CASCADE and lookback_width 0
- *   deterministic      0 or 1.  The PH solver (and batched runs) always compose a tile's
+ *   solver             SOS_SOLVER_DEFAULT, SOS_SOLVER_CR, SOS_SOLVER_PH, SOS_SOLVER_DTCR or
+ *                      SOS_SOLVER_TC (see SOS_SOLVER_*); SOS_SOLVER_PH takes N = 0, 32 or 64,
+ *                      SOS_SOLVER_DTCR and SOS_SOLVER_TC N = 0 or 64, all three carry
+ *                      SOS_CARRY_DEFAULT or SOS_CARRY_CASCADE and lookback_width 0
+ *   deterministic      0 or 1.  The PH solvers (and batched runs) always compose a tile's
  *                      incoming state the same way -- the resolved carry of a fixed anchor tile
  *                      (the last multiple of 32 before it) and the local carries after it -- so
  *                      their outputs are bit-identical from run to run.  Cyclic reduction composes
@@ -402,25 +412,26 @@ sos_status sos_server_replay(sos_server *s, int64_t n_req, const int32_t *stream
  * Autotuner: on the current device, time each candidate launch configuration
  * -- divide-and-conquer cyclic reduction with the cascade carry at N = 32 (8
  * groups per tile) or N = 64 (4 groups per tile), PH factorization at N = 64
- * with 7 or 10 groups per tile, and double-thread-group cyclic reduction at N = 64
- * (4 groups of two warps per tile); L = 32 threads per group (thread group)
+ * with 7 or 10 groups per tile, double-thread-group cyclic reduction at N = 64
+ * (4 groups of two warps per tile) and PH factorization on the tensor cores (8
+ * groups per tile); L = 32 threads per group (thread group)
  * throughout -- for 1 to 8 sections and lengths 2^16, 2^20, 2^24 and 2^28 (up to
  * 2^max_log2n, 0 = 28), and keep the fastest per (section count, length).
  * Afterwards every run of a filter created with default tuning (all fields 0)
  * uses the choice for its section count and the nearest length.  Synchronous;
  * allocates and frees 2^(max_log2n + 3) bytes of device memory; a second or two.
- *   report  NULL, or host float[8][4][5] receiving the measured GS/s
+ *   report  NULL, or host float[8][4][6] receiving the measured GS/s
  *           (sections, length 2^16..2^28, candidate CR32/CR64/PH/DTCR/PH with
- *           10 groups per tile)
+ *           10 groups per tile/PH on the tensor cores)
  */
 sos_status sos_autotune(int max_log2n, float *report);
 
 /* The autotuned choice for K sections and n samples on the current device:
- * solver (SOS_SOLVER_CR / SOS_SOLVER_PH / SOS_SOLVER_DTCR) and N; both 0 if no
- * autotuning ran. */
+ * solver (SOS_SOLVER_CR / SOS_SOLVER_PH / SOS_SOLVER_DTCR / SOS_SOLVER_TC) and N; both
+ * 0 if no autotuning ran. */
 sos_status sos_autotune_choice(int n_sections, int64_t n, int *solver, int *N);
-/* The same with the groups per tile of a PH choice (7 or 10; 0 for the other solvers) in
- * *groups_per_cta (may be NULL). */
+/* The same with the groups per tile of a PH choice (7 or 10; 8 for SOS_SOLVER_TC; 0 for the
+ * other solvers) in *groups_per_cta (may be NULL). */
 sos_status sos_autotune_choice_ex(int n_sections, int64_t n, int *solver, int *N, int *groups_per_cta);
 
 /* Human-readable name of a status code (static storage). */

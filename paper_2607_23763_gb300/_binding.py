@@ -47,7 +47,7 @@ class Tuning(ctypes.Structure):
 
 CARRY_DEFAULT, CARRY_CASCADE, CARRY_SECTION = 0, 1, 2
 HOST_DIRECT = -1  # sos_filter_run_host: the kernels read and write the pinned host buffers in place
-SOLVER_DEFAULT, SOLVER_CR, SOLVER_PH, SOLVER_DTCR = 0, 1, 2, 3
+SOLVER_DEFAULT, SOLVER_CR, SOLVER_PH, SOLVER_DTCR, SOLVER_TC = 0, 1, 2, 3, 4
 
 
 _lib = None
@@ -383,7 +383,7 @@ def autotune(max_log2n: int = 0) -> np.ndarray:
     """Time the candidate launch configurations on the current device and keep the fastest per
     (section count, length); returns the measured GS/s as [8 sections][4 lengths][CR32, CR64, PH, DTCR,
     PH with 10 groups per tile]."""
-    rep = np.zeros((8, 4, 5), dtype=np.float32)
+    rep = np.zeros((8, 4, 6), dtype=np.float32)
     _check(load_library().sos_autotune(int(max_log2n), rep.ctypes.data), "sos_autotune")
     return rep
 

@@ -152,6 +152,9 @@ struct LanePass {
     sosk::LaneSec *d_sec = nullptr;  // [kp] section constants
     float4 *d_MX = nullptr;          // coupling blocks of M_N
     float *d_Mm = nullptr;           // device copy of Mm
+    // tensor-core kernel only (N = 64, W = kTcGroups): its constant operands and final-state table
+    float *d_tcimg = nullptr;        // shared-memory image of the MMA B operands (kTcImageBytes)
+    float *d_gtail = nullptr;        // [2 kp][64] state responses G, float32
 };
 
 }  // namespace
@@ -178,7 +181,8 @@ struct sos_filter {
     sos_tuning tuning{};
     NTables tables[kNumN];
     CasTables cas[2];  // N = 32, 64
-    std::vector<LanePass> lane[3];  // skewed-pass PH kernel: (N, W) = (32, 7), (64, 7), (64, 10)
+    // PH kernels: skewed pass at (N, W) = (32, 7), (64, 7), (64, 10); tensor cores at (64, 8)
+    std::vector<LanePass> lane[4];
     // workspace
     unsigned long long *d_desc = nullptr;
     size_t desc_groups = 0;  // capacity in groups (per section slot)
@@ -512,7 +516,9 @@ sos_status build_lane(sos_filter *f, int N, int W, std::vector<LanePass> &out) {
             }
         const int ms = lane_stride(kp), full = S * S;
         const size_t off_ac = 64 * static_cast<size_t>(ms), off_h = off_ac + full, off_at = off_h + N * S;
-        std::vector<float> tab(off_at + full, 0.f);
+        const size_t off_at32 = off_at + full, off_ats = off_at32 + full, off_ats1 = off_ats + full;
+        std::vector<float> tab(off_ats1 + full, 0.f);
+        const int span = 32 * (W == sosk::kTcGroups ? sosk::kTcSpan : sosk::kLaneSpan);  // anchor spacing in tiles
         DMat L = deye(S), LT = deye(S);
         for (int l = 0; l < 32; ++l) {
             pack_into(L, kp, &tab[static_cast<size_t>(l) * ms]);
@@ -524,6 +530,9 @@ sos_status build_lane(sos_filter *f, int N, int W, std::vector<LanePass> &out) {
         for (int j = 0; j < S; ++j)
             for (int m = 0; m < N; ++m) tab[off_h + static_cast<size_t>(j) * N + m] = ps.H[static_cast<size_t>(j) * N + m];
         dense_colmajor_into(AT, &tab[off_at]);
+        dense_colmajor_into(dpow(AT, 32), &tab[off_at32]);
+        dense_colmajor_into(dpow(AT, span), &tab[off_ats]);
+        dense_colmajor_into(dpow(AT, span - 1), &tab[off_ats1]);
         if (cudaMalloc(&ps.d_tab, tab.size() * sizeof(float)) != cudaSuccess) return SOS_ENOMEM;
         if (cudaMemcpy(ps.d_tab, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
             return SOS_ECUDA;
@@ -547,6 +556,77 @@ sos_status build_lane(sos_filter *f, int N, int W, std::vector<LanePass> &out) {
         }
         out.push_back(std::move(ps));
     }
+    return SOS_OK;
+}
+
+// Operands of the tensor-core kernel for one pass (Sec. II-C with the particular solution as a
+// product): the pass's cascade, as the tables model it (b0-normalized sections, the input gain in the
+// first pass), driven by an impulse gives the impulse response h and the state responses; the
+// particular solution of a 64-sample row is T x with T[m][j] = h[m - j] (m >= j), the row's terminal
+// state G x with G[s][j] the state s after sample 63 of an impulse at j.  B1 stacks T (rows 0..63)
+// and G (rows 64..64 + 2 kp - 1) as 80 rows over the 64 input samples; B2 holds the zero-input output
+// basis H[m][s].  Each value is split into its TF32 head (upper 19 bits of the float32) and the
+// float32 remainder, laid out as the kernel's shared memory holds them: K-major rows of 128 bytes
+// whose 16-byte chunk j sits at chunk j ^ (row mod 8).
+sos_status build_tc(sos_filter *f, LanePass &ps) {
+    constexpr int N = 64, R1 = 80, HB = 2 * R1 * 128;  // samples per row, B1 rows, bytes of one B1 image
+    const int kp = ps.kp, S = 2 * kp;
+    const double gain = ps.k0 == 0 ? f->gain : 1.0;
+    std::vector<double> h(N), g(static_cast<size_t>(N) * S);
+    {
+        std::vector<double> z(S, 0.0);
+        for (int m = 0; m < N; ++m) {
+            h[m] = cascade_step(ps.coef, kp, z, m == 0 ? gain : 0.0);
+            for (int k = 0; k < S; ++k) g[static_cast<size_t>(m) * S + k] = z[k];
+        }
+    }
+    std::vector<double> H(static_cast<size_t>(S) * N);
+    for (int k = 0; k < S; ++k) {
+        std::vector<double> z(S, 0.0);
+        z[k] = 1.0;
+        for (int m = 0; m < N; ++m) H[static_cast<size_t>(k) * N + m] = cascade_step(ps.coef, kp, z, 0.0);
+    }
+    std::vector<unsigned char> img(sosk::kTcImageBytes, 0);
+    auto put = [&](size_t base, int r, int c, float v) {
+        const size_t off = base + static_cast<size_t>(r) * 128 + ((((c >> 2) ^ (r & 7)) << 4) | ((c & 3) << 2));
+        std::memcpy(&img[off], &v, sizeof v);
+    };
+    auto head = [](double v) {
+        float x = static_cast<float>(v);
+        uint32_t u;
+        std::memcpy(&u, &x, sizeof u);
+        u &= 0xffffe000u;
+        std::memcpy(&x, &u, sizeof x);
+        return x;
+    };
+    for (int n = 0; n < R1; ++n)
+        for (int j = 0; j < N; ++j) {
+            double v = 0.0;
+            if (n < N)
+                v = n >= j ? h[n - j] : 0.0;
+            else if (n - N < S)
+                v = g[static_cast<size_t>(N - 1 - j) * S + (n - N)];
+            const float hi = head(v), lo = static_cast<float>(v - static_cast<double>(hi));
+            const size_t half = static_cast<size_t>(j >> 5) * (HB / 2);
+            put(half, n, j & 31, hi);
+            put(HB + half, n, j & 31, lo);
+        }
+    for (int m = 0; m < N; ++m)
+        for (int k = 0; k < S; ++k) {
+            const double v = H[static_cast<size_t>(k) * N + m];
+            const float hi = head(v), lo = static_cast<float>(v - static_cast<double>(hi));
+            put(2 * HB, m, k, hi);
+            put(2 * HB, m, 16 + k, lo);
+        }
+    std::vector<float> gt(static_cast<size_t>(S) * N);
+    for (int k = 0; k < S; ++k)
+        for (int j = 0; j < N; ++j) gt[static_cast<size_t>(k) * N + j] = static_cast<float>(g[static_cast<size_t>(N - 1 - j) * S + k]);
+    if (cudaMalloc(&ps.d_tcimg, img.size()) != cudaSuccess ||
+        cudaMalloc(&ps.d_gtail, gt.size() * sizeof(float)) != cudaSuccess)
+        return SOS_ENOMEM;
+    if (cudaMemcpy(ps.d_tcimg, img.data(), img.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(ps.d_gtail, gt.data(), gt.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+        return SOS_ECUDA;
     return SOS_OK;
 }
 
@@ -822,7 +902,7 @@ sos_status run_dtcr(sos_filter *f, const float *x, float *y, int64_t n, const fl
 }
 
 // ---- skewed-pass PH kernel (sosfilt_lane.cuh)
-template <int K, int N, int W>
+template <int K, int N, int W, bool TC = false>
 sos_status launch_lane_pass(sos_filter *f, LanePass &ps, const float *x, float *y, long long n, long long G,
                             long long n_tiles, long long grid, const float *zi, float *zf, bool first, bool aligned,
                             cudaStream_t s, const sosk::Scratch *sc = nullptr, unsigned sc_epoch = 0) {
@@ -875,19 +955,24 @@ sos_status launch_lane_pass(sos_filter *f, LanePass &ps, const float *x, float *
     const int m_last = static_cast<int>((n - 1 - (G - 1) * C) % N);
     p->m_last = m_last;
     if (zf) std::memcpy(p->A_tail, &ps.Mm[static_cast<size_t>(m_last) * packed_floats(K)], sizeof(float) * packed_floats(K));
-    cudaError_t e = sosk::launch_lane<K, N, W>(f->norm, *p, grid, s);
+    cudaError_t e;
+    if constexpr (TC)
+        e = sosk::launch_tc<K>(*p, ps.d_tcimg, ps.d_gtail, grid, s);
+    else
+        e = sosk::launch_lane<K, N, W>(f->norm, *p, grid, s);
     if (e != cudaSuccess) return SOS_ECUDA;
     if (eager) f->ticket_base += static_cast<unsigned long long>(n_tiles + grid);
     return SOS_OK;
 }
 
-template <int N, int W>
+template <int N, int W, bool TC = false>
 sos_status launch_lane_any(int K, sos_filter *f, LanePass &ps, const float *x, float *y, long long n, long long G,
                            long long n_tiles, long long grid, const float *zi, float *zf, bool first, bool aligned,
                            cudaStream_t s, const sosk::Scratch *sc = nullptr, unsigned sc_epoch = 0) {
     switch (K) {
 #define SOSK_CASE(k) \
-    case k: return launch_lane_pass<k, N, W>(f, ps, x, y, n, G, n_tiles, grid, zi, zf, first, aligned, s, sc, sc_epoch);
+    case k:          \
+        return launch_lane_pass<k, N, W, TC>(f, ps, x, y, n, G, n_tiles, grid, zi, zf, first, aligned, s, sc, sc_epoch);
         SOSK_CASE(1) SOSK_CASE(2) SOSK_CASE(3) SOSK_CASE(4) SOSK_CASE(5) SOSK_CASE(6) SOSK_CASE(7) SOSK_CASE(8)
 #undef SOSK_CASE
         default: return SOS_EINVAL;
@@ -934,6 +1019,33 @@ sos_status run_lane(sos_filter *f, const float *x, float *y, int64_t n, const fl
     return SOS_OK;
 }
 
+// PH factorization on the tensor cores (sosfilt_tc.cuh): tiles of kTcGroups groups of 32 rows of 64
+// samples.  Its TMA copies need 16-byte aligned signals of at least one full row; other signals run
+// the skewed-pass PH kernel.
+sos_status run_tc(sos_filter *f, const float *x, float *y, int64_t n, const float *zi, float *zf, cudaStream_t s) {
+    const bool aligned = (reinterpret_cast<uintptr_t>(x) % 16 == 0) && (reinterpret_cast<uintptr_t>(y) % 16 == 0);
+    if (!aligned || n < 64) return run_lane(f, x, y, n, zi, zf, s, 64, sosk::kLaneW);
+    constexpr long long C = 32LL * 64, W = sosk::kTcGroups;
+    const long long G = (n + C - 1) / C;
+    const long long n_tiles = (G + W - 1) / W;
+    sos_status st = ensure_desc(f, G, s);
+    if (st != SOS_OK) return st;
+    const float *src = x;
+    for (auto &ps : f->lane[3]) {
+        const int bps = sosk::tc_blocks_per_sm(ps.kp);
+        if (bps <= 0) return SOS_ECUDA;
+        long long grid = static_cast<long long>(bps) * sm_count(f->device);
+        if (grid > n_tiles) grid = n_tiles;
+        const float *zp = zi ? zi + 2 * ps.k0 : nullptr;
+        float *zq = zf ? zf + 2 * ps.k0 : nullptr;
+        st = launch_lane_any<64, sosk::kTcGroups, true>(ps.kp, f, ps, src, y, n, G, n_tiles, grid, zp, zq,
+                                                        ps.k0 == 0, true, s);
+        if (st != SOS_OK) return st;
+        src = y;
+    }
+    return SOS_OK;
+}
+
 // Solver of a run: the tuning's choice; by default PH factorization with the skewed particular
 // pass (faster than cyclic reduction at every order on GB300 at 2^28 samples: 227 vs 154 GS/s at
 // order 16, 606 vs 540 at order 2), unless the tuning asks for what only cyclic reduction has (a
@@ -948,7 +1060,7 @@ int solver_of(const sos_filter *f) {
 // ---- autotuned launch choice (sos_autotune): per device, section count (1..8) and length bucket
 constexpr int kTuneBuckets = 4;                       // n around 2^16, 2^20, 2^24, 2^28
 constexpr int kTuneLog2[kTuneBuckets] = {16, 20, 24, 28};
-constexpr int kTuneCand = 5;  // candidates: CR N = 32, CR N = 64, PH (7 groups), DTCR, PH (10 groups)
+constexpr int kTuneCand = 6;  // candidates: CR N = 32, CR N = 64, PH (7 groups), DTCR, PH (10 groups), TC
 struct TuneTable {
     bool valid = false;
     unsigned char best[8][kTuneBuckets] = {};         // candidate index
@@ -958,9 +1070,9 @@ std::mutex g_tune_mu;
 TuneTable g_tune[64];
 
 void candidate(int c, int *solver, int *N, int *W) {
-    *solver = (c == 2 || c == 4) ? SOS_SOLVER_PH : c == 3 ? SOS_SOLVER_DTCR : SOS_SOLVER_CR;
+    *solver = (c == 2 || c == 4) ? SOS_SOLVER_PH : c == 3 ? SOS_SOLVER_DTCR : c == 5 ? SOS_SOLVER_TC : SOS_SOLVER_CR;
     *N = c == 0 ? 32 : 64;
-    *W = c == 4 ? sosk::kLaneWide : c == 2 ? sosk::kLaneW : 0;
+    *W = c == 4 ? sosk::kLaneWide : c == 2 ? sosk::kLaneW : c == 5 ? sosk::kTcGroups : 0;
 }
 
 int tune_bucket(int64_t n) {
@@ -999,11 +1111,13 @@ sos_status run_impl(sos_filter *f, const float *x, float *y, int64_t n, const fl
         if (tuned_choice(f->device, f->K, n, &solver, &N, &W)) {
             if (solver == SOS_SOLVER_PH) return run_lane(f, x, y, n, zi, zf, s, N, W);
             if (solver == SOS_SOLVER_DTCR) return run_dtcr(f, x, y, n, zi, zf, s);
+            if (solver == SOS_SOLVER_TC) return run_tc(f, x, y, n, zi, zf, s);
             return run_cascade(f, x, y, n, zi, zf, s, N);
         }
     }
     if (solver_of(f) == SOS_SOLVER_PH) return run_lane(f, x, y, n, zi, zf, s);
     if (solver_of(f) == SOS_SOLVER_DTCR) return run_dtcr(f, x, y, n, zi, zf, s);
+    if (solver_of(f) == SOS_SOLVER_TC) return run_tc(f, x, y, n, zi, zf, s);
     if (t.carry == SOS_CARRY_SECTION) return run_sections(f, x, y, n, zi, zf, s);
     return run_cascade(f, x, y, n, zi, zf, s);
 }
@@ -1527,7 +1641,10 @@ sos_status sos_filter_create(int n_sections, const double *sos, const float *zi,
         const int lw = t->lookback_width;
         if (lw != 0 && lw != 1 && lw != 2 && lw != 4 && lw != 8 && lw != 16) return SOS_EINVAL;
         if (t->solver != SOS_SOLVER_DEFAULT && t->solver != SOS_SOLVER_CR && t->solver != SOS_SOLVER_PH &&
-            t->solver != SOS_SOLVER_DTCR)
+            t->solver != SOS_SOLVER_DTCR && t->solver != SOS_SOLVER_TC)
+            return SOS_EINVAL;
+        if (t->solver == SOS_SOLVER_TC &&
+            ((t->N && t->N != 64) || t->carry == SOS_CARRY_SECTION || t->lookback_width || t->groups_per_cta))
             return SOS_EINVAL;
         if (t->solver == SOS_SOLVER_DTCR &&
             ((t->N && t->N != 64) || t->carry == SOS_CARRY_SECTION || t->lookback_width))
@@ -1595,8 +1712,10 @@ sos_status sos_filter_create(int n_sections, const double *sos, const float *zi,
             st = SOS_ECUDA;
     }
     for (int i = 0; i < 2 && st == SOS_OK; ++i) st = build_cascade(f, i == 0 ? 32 : 64, f->cas[i]);
-    for (int i = 0; i < 3 && st == SOS_OK; ++i)
-        st = build_lane(f, i == 0 ? 32 : 64, i == 2 ? sosk::kLaneWide : sosk::kLaneW, f->lane[i]);
+    for (int i = 0; i < 4 && st == SOS_OK; ++i)
+        st = build_lane(f, i == 0 ? 32 : 64, i == 2 ? sosk::kLaneWide : i == 3 ? sosk::kTcGroups : sosk::kLaneW,
+                        f->lane[i]);
+    for (size_t i = 0; i < f->lane[3].size() && st == SOS_OK; ++i) st = build_tc(f, f->lane[3][i]);
     if (st == SOS_OK) {
         const LanePass &ps = f->lane[1][0];
         f->bt.sec = ps.d_sec;
@@ -1652,6 +1771,8 @@ sos_status sos_filter_destroy(sos_filter *f) {
             if (ps.d_sec) cudaFree(ps.d_sec);
             if (ps.d_MX) cudaFree(ps.d_MX);
             if (ps.d_Mm) cudaFree(ps.d_Mm);
+            if (ps.d_tcimg) cudaFree(ps.d_tcimg);
+            if (ps.d_gtail) cudaFree(ps.d_gtail);
         }
     if (f->d_desc) cudaFree(f->d_desc);
     if (f->d_ticket) cudaFree(f->d_ticket);
@@ -1875,7 +1996,7 @@ sos_status sos_autotune(int max_log2n, float *report) {
             candidate(c, &solver, &N, &W);
             t.solver = solver;
             t.N = N;
-            t.groups_per_cta = W;
+            t.groups_per_cta = solver == SOS_SOLVER_TC ? 0 : W;  // the tensor-core tile is fixed
             if (solver == SOS_SOLVER_CR) t.carry = SOS_CARRY_CASCADE;
             sos_filter *f = nullptr;
             rc = sos_filter_create(K, sos.data(), nullptr, &t, &f);

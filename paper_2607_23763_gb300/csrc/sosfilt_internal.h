@@ -134,6 +134,8 @@ size_t cascade_smem(int K, int N);
 // ---- PH-factorization kernel with a skewed direct-form-II particular pass (sosfilt_lane.cuh)
 constexpr int kLaneW = 7;    // compute warps per block, one group each; a tile is kLaneW groups
 constexpr int kLaneWide = 10;  // the wide variant at N = 64: 10 groups per tile (sos_tuning.groups_per_cta)
+constexpr int kLaneSpan = 1;   // PH kernels: lookback anchors every 32 kLaneSpan tiles
+constexpr int kTcSpan = 1;     // the tensor-core kernel: anchors every 32 kTcSpan tiles
 
 // Per-section constants of the skewed-pass kernel, in the kernel's domain (b / b0 and b0 = 1 when
 // normalized; carried state = zscale * true state).
@@ -173,6 +175,14 @@ struct LaneParams {
 // [4] iteration start, [5] next ticket known, [6] particular pass done, [7] lane scan done, [8] fold
 // done; correction of the tile: [9] start, [10] group state observed, [11] row states stored,
 // [12] stored; [13] SM id; [14] stash start, [15] input stashed.
+// Phase trace of the tensor-core kernel, per tile (global timer, ns): [0] tile + 1, [13] SM id;
+// coordinator: [1] tile folded, [2] incoming state resolved, [3] group states posted; producer:
+// [16] ticket drawn, [17] unit 0 loads issued; MMA issuer: [18] unit 0 first products issued,
+// [19] unit 0 remainder products issued, [20] unit 0 correction issued; [21] unit 0 remainder formed;
+// epilogue warp of group 0: [4] accumulator observed, [7] lane scan done, [8] fold done, [9]
+// correction start, [10] group state observed, [11] state operand posted, [12] correction observed,
+// [14] outputs stored; epilogue warp of group 4: [22] accumulator observed, [23] lane scan done,
+// [24] correction observed, [25] outputs stored.
 template <int K, int N, int W>
 cudaError_t launch_lane(bool norm, const LaneParams<K> &p, long long grid, cudaStream_t s);
 #define SOSK_DECLARE_LANE(K, N, W) \
@@ -187,6 +197,21 @@ SOSK_DECLARE_LANE_NW(64, 10)
 // Thread blocks of the skewed-pass kernel (N samples per lane, W groups per tile) that fit on one SM
 // (0 if unavailable).
 int lane_blocks_per_sm(int K, int N, int W, bool norm);
+
+// ---- PH kernel on the tensor cores (sosfilt_tc.cuh): N = 64 samples per lane, tiles of kTcGroups
+// groups; x and y 16-byte aligned and n >= 64.  img: the constant operands' shared-memory image
+// (tc_image_bytes), gtail: [2K][64] state responses in float32.
+constexpr int kTcGroups = 8;
+constexpr int kTcImageBytes = 49152;
+template <int K>
+cudaError_t launch_tc(const LaneParams<K> &p, const float *img, const float *gtail, long long grid, cudaStream_t s);
+#define SOSK_DECLARE_TC(K) \
+    template <>            \
+    cudaError_t launch_tc<K>(const LaneParams<K> &p, const float *img, const float *gtail, long long grid, cudaStream_t s);
+SOSK_DECLARE_TC(1) SOSK_DECLARE_TC(2) SOSK_DECLARE_TC(3) SOSK_DECLARE_TC(4)
+SOSK_DECLARE_TC(5) SOSK_DECLARE_TC(6) SOSK_DECLARE_TC(7) SOSK_DECLARE_TC(8)
+#undef SOSK_DECLARE_TC
+int tc_blocks_per_sm(int K);
 
 // ---- multi-signal persistent kernel (sosfilt_batch.cuh): the PH kernel with a skewed particular
 // pass over a global queue of (signal, tile) work items

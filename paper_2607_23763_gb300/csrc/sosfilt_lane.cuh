@@ -65,12 +65,17 @@ struct LaneDims {
     static constexpr int S4 = (S + 3) / 4;
     static constexpr int RSP = 4 * ((S4 & 1) ? S4 : S4 + 1);
     // table block: (M_N)^lane [32][MS], (A_T)^lane [32][MS], A_C dense column-major, the basis
-    // [S][N] (read in chunks of V samples), A_T dense
+    // [S][N] (read in chunks of V samples), A_T dense, (A_T)^32, (A_T)^SPAN, (A_T)^(SPAN - 1) dense
     static constexpr int OFF_ATL = 32 * MS;
     static constexpr int OFF_AC = 64 * MS;
     static constexpr int OFF_H = OFF_AC + FULL;
     static constexpr int OFF_AT = OFF_H + N * S;
-    static constexpr int TAB = OFF_AT + FULL;
+    static constexpr int OFF_AT32 = OFF_AT + FULL;  // (A_T)^32 dense: combines lookback blocks of 32 tiles
+    // (A_T)^SPAN and (A_T)^(SPAN - 1) dense, SPAN the anchor spacing in tiles: an anchor's resolved
+    // carry from the previous anchor's, and its incoming state
+    static constexpr int OFF_ATS = OFF_AT32 + FULL;
+    static constexpr int OFF_ATS1 = OFF_ATS + FULL;
+    static constexpr int TAB = OFF_ATS1 + FULL;
     static constexpr int TAB_GLOBAL = TAB;
     // the shared-memory copy: (M_N)^lane, (A_T)^lane when ATL_SHARED, then A_C .. A_T
     static constexpr int SM_AC = ATL_SHARED ? OFF_AC : OFF_ATL;
@@ -314,6 +319,133 @@ __device__ __forceinline__ void lane_state_mv(const float *__restrict__ A, const
     }
 }
 
+// Dense matrices the coordinator applies (column-major S x S): A_T, (A_T)^32, (A_T)^SPAN and
+// (A_T)^(SPAN - 1), SPAN the anchor spacing in tiles.
+struct CoordMats {
+    const float *AT, *AT32, *ATS, *ATS1;
+};
+
+// One tile's work of the coordinator warp: decoupled lookback over tiles (Sec. IV-B, Eq. 25 on the
+// cascade state) for tile cur's incoming 2K-word state, its resolved carry when cur is an anchor
+// tile, and the incoming state of each of its W groups in z_buf[slot] (Z_0 = Z, Z_{v+1} = A_C Z_v +
+// a_v).  The composition is fixed: the resolved carry of the last anchor before cur (the tiles at
+// multiples of SPAN = 32 M) and the local carries after it, so that outputs are reproducible bit for
+// bit.  Each lane reads M predecessors, 32 apart, and the M partial sums combine by Horner's rule
+// with (A_T)^32.
+// The anchors' resolved carries form a chain, one hop per SPAN tiles, that bounds the kernel's rate;
+// an anchor therefore sums its local carries first, before the previous anchor's carry G can have
+// arrived, and the hop itself is one product: G(cur) = (A_T)^SPAN G + [A_T P + carry(cur)], with P
+// the local carries' part of the incoming state Z = (A_T)^(SPAN - 1) G + P.
+template <int K, int W, int MS, int P2, int SH, int M = 1>
+__device__ __forceinline__ void coordinate_tile(const LaneParams<K> &p, int lane, long long cur, unsigned slot,
+                                                long long budget, const float *sATl, const CoordMats &mats,
+                                                const float *sACd, const float *a_buf, float *z_buf, const float *agg,
+                                                unsigned long long *tr) {
+    constexpr int S = 2 * K;
+    constexpr long long SPAN = 32LL * M;
+    const unsigned tagL = (p.epoch << 2) | 1u, tagG = (p.epoch << 2) | 2u;
+    auto zinit = [&](int i) -> float { return p.zi ? p.zi[i] * p.sec[i >> 1].zscale : 0.f; };
+    const float *abuf = a_buf + slot * W * S;
+    const float acc_i = agg[slot * S + (lane < S ? lane : 0)];
+    // descriptor of a tile: two slots of 2K tagged words, its local carry (posted by the fold)
+    // and its resolved carry (posted below)
+    unsigned long long *dcur = p.desc + static_cast<size_t>(cur) * 2 * S + S;
+    const bool anchor = (cur % SPAN) == 0 && cur + 1 < p.n_tiles;  // only anchors' carries are read
+    float zi_lane = 0.f;
+    if (cur == 0) {
+        zi_lane = zinit(lane < S ? lane : 0);
+        if (anchor) {
+            const float gl = lane_mv<S>(mats.AT, zi_lane, lane) + acc_i;
+            if (lane < S) st_relaxed_b64(dcur + lane, pack_word(tagG, gl));
+        }
+    } else {
+        const long long a = ((cur - 1) / SPAN) * SPAN;
+        float v[M][S];
+        // wait for the predecessors' carries: the local carries of tiles a + 1 .. cur - 1 and, with
+        // with_g, the resolved carry of the anchor a (else its slot stays zero); false on timeout
+        auto poll = [&](bool with_g) -> bool {
+            const long long t_start = clock64();
+            for (;;) {
+                bool ok = true;
+#pragma unroll
+                for (int j = 0; j < M; ++j) {
+                    const long long pred = cur - 1 - lane - 32LL * j;
+                    if (pred > a || (with_g && pred == a)) {
+                        const bool g = pred == a;
+                        const unsigned want = g ? tagG : tagL;
+                        const unsigned long long *dp = p.desc + static_cast<size_t>(pred) * 2 * S + (g ? S : 0);
+#pragma unroll
+                        for (int q = 0; q < S; q += 2) {
+                            unsigned long long x0, x1;
+                            ld_relaxed_v2(dp + q, x0, x1);
+                            ok = ok && static_cast<unsigned>(x0 >> 32) == want &&
+                                 static_cast<unsigned>(x1 >> 32) == want;
+                            v[j][q] = __uint_as_float(static_cast<unsigned>(x0));
+                            v[j][q + 1] = __uint_as_float(static_cast<unsigned>(x1));
+                        }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < S; ++q) v[j][q] = 0.f;
+                    }
+                }
+                if (__all_sync(0xffffffffu, ok)) return true;
+                if (__any_sync(0xffffffffu, (clock64() - t_start) > budget)) {
+                    if (lane == 0) atomicOr(p.status, kDevErrTimeout);
+                    return false;
+                }
+                __nanosleep(64);  // a short nap: the successors' lookbacks wait on this tile
+            }
+        };
+        // sum_k (A_T)^k v_k over the predecessors read: block j of 32 by each lane's own power
+        // (A_T)^lane and a reduce-scatter (word i of the block's sum in lane i), the blocks by
+        // Horner's rule with (A_T)^32
+        auto combine = [&]() -> float {
+            float z = 0.f, tmp[S];
+#pragma unroll
+            for (int j = M - 1; j >= 0; --j) {
+                packed_mv<K>(sATl + lane * MS, v[j], tmp);
+                const float part = reduce_scatter<S, P2, SH>(tmp, lane);
+                const float pj = __shfl_sync(0xffffffffu, part, (lane < S ? lane : 0) << SH);
+                z = (j == M - 1) ? pj : lane_mv<S>(mats.AT32, z, lane) + pj;
+            }
+            return z;
+        };
+        if (!anchor) {
+            poll(true);
+            zi_lane = combine();
+        } else {
+            poll(false);
+            const float pl = combine();                              // P, word lane
+            const float wl = lane_mv<S>(mats.AT, pl, lane) + acc_i;  // A_T P + carry(cur)
+            // the previous anchor's resolved carry, word lane (lanes >= S read word 0)
+            const unsigned long long *dg = p.desc + static_cast<size_t>(a) * 2 * S + S + (lane < S ? lane : 0);
+            const long long t_start = clock64();
+            unsigned long long gw = 0;
+            for (;;) {
+                gw = ld_relaxed_b64(dg);
+                if (__all_sync(0xffffffffu, static_cast<unsigned>(gw >> 32) == tagG)) break;
+                if (__any_sync(0xffffffffu, (clock64() - t_start) > budget)) {
+                    if (lane == 0) atomicOr(p.status, kDevErrTimeout);
+                    break;
+                }
+                __nanosleep(32);
+            }
+            const float gi = lane < S ? __uint_as_float(static_cast<unsigned>(gw)) : 0.f;
+            const float gl = lane_mv<S>(mats.ATS, gi, lane) + wl;
+            if (lane < S) st_relaxed_b64(dcur + lane, pack_word(tagG, gl));
+            zi_lane = lane_mv<S>(mats.ATS1, gi, lane) + pl;
+        }
+    }
+    if (tr) tr[2] = global_ns();
+    // incoming state of each group of the tile: Z_0 = Z, Z_{v+1} = A_C Z_v + a_v
+    float *zb = z_buf + slot * W * S;
+#pragma unroll 1
+    for (int v = 0; v < W; ++v) {
+        if (lane < S) zb[v * S + lane] = zi_lane;
+        if (v + 1 < W) zi_lane = lane_mv<S>(sACd, zi_lane, lane) + abuf[v * S + (lane < S ? lane : 0)];
+    }
+}
+
 template <int K, int N, bool NORM, int W>
 __global__ void __maxnreg__((LaneDims<K, N, W>::MAXREG)) sos_lane_kernel(const __grid_constant__ LaneParams<K> p) {
     using Dm = LaneDims<K, N, W>;
@@ -334,6 +466,8 @@ __global__ void __maxnreg__((LaneDims<K, N, W>::MAXREG)) sos_lane_kernel(const _
     float *agg = z_buf + 2 * W * S;                  // [2][S] tile carry under zero incoming state
     float *zs_tail = agg + 2 * S;                    // [S] lane-local state after the last sample
     const float *sATd = tab + Dm::SM_AC + (Dm::OFF_AT - Dm::OFF_AC);    // A_T dense column-major
+    const CoordMats mats{sATd, tab + Dm::SM_AC + (Dm::OFF_AT32 - Dm::OFF_AC), tab + Dm::SM_AC + (Dm::OFF_ATS - Dm::OFF_AC),
+                         tab + Dm::SM_AC + (Dm::OFF_ATS1 - Dm::OFF_AC)};  // dense powers of A_T
     // tiles alternate between two slots; the incoming-state barrier has one per slot, so that it
     // never runs two phases ahead of a waiter
     __shared__ unsigned long long bar_local[2], bar_zready[2], bar_ticket[8];
@@ -382,8 +516,6 @@ __global__ void __maxnreg__((LaneDims<K, N, W>::MAXREG)) sos_lane_kernel(const _
 
     if (warp == 0) {
         // ------------------------------------------------------------------ coordinator warp
-        const unsigned tagL = (p.epoch << 2) | 1u, tagG = (p.epoch << 2) | 2u;
-        auto zinit = [&](int i) -> float { return p.zi ? p.zi[i] * p.sec[i >> 1].zscale : 0.f; };
         unsigned it = 0;
         for (;;) {
             const unsigned slot = it & 1;
@@ -400,69 +532,8 @@ __global__ void __maxnreg__((LaneDims<K, N, W>::MAXREG)) sos_lane_kernel(const _
                 tr[1] = global_ns();
                 tr[13] = smid;
             }
-            const float *abuf = a_buf + slot * W * S;
-            const float acc_i = agg[slot * S + (lane < S ? lane : 0)];
-            float tmp[S];
-            // descriptor of a tile: two slots of 2K tagged words, its local carry (posted by the fold)
-            // and its resolved carry (posted below)
-            unsigned long long *dcur = p.desc + static_cast<size_t>(cur) * 2 * S + S;
-            float zi_lane = 0.f;
-            if (cur == 0) {
-                zi_lane = zinit(lane < S ? lane : 0);
-            } else {
-                // decoupled lookback with a fixed composition: the resolved carry of the anchor tile a
-                // (the last multiple of 32 before cur) and the local carries of tiles a + 1 .. cur - 1,
-                // whichever of them have resolved meanwhile, so that the sum does not depend on timing
-                // and outputs are reproducible bit for bit; the anchors form a chain of one hop per 32
-                // tiles
-                const long long a = ((cur - 1) / 32) * 32;
-                const int ja = static_cast<int>(cur - 1 - a);  // the anchor's lane
-                const long long pred = cur - 1 - lane;
-                const long long t_start = clock64();
-                float v[S];
-                for (;;) {
-                    bool ok = true;
-                    if (lane <= ja) {
-                        const unsigned want = lane == ja ? tagG : tagL;
-                        const unsigned long long *dp = p.desc + static_cast<size_t>(pred) * 2 * S + (lane == ja ? S : 0);
-#pragma unroll
-                        for (int q = 0; q < S; q += 2) {
-                            unsigned long long x0, x1;
-                            ld_relaxed_v2(dp + q, x0, x1);
-                            ok = ok && static_cast<unsigned>(x0 >> 32) == want && static_cast<unsigned>(x1 >> 32) == want;
-                            v[q] = __uint_as_float(static_cast<unsigned>(x0));
-                            v[q + 1] = __uint_as_float(static_cast<unsigned>(x1));
-                        }
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < S; ++q) v[q] = 0.f;
-                    }
-                    if (__all_sync(0xffffffffu, ok)) break;
-                    if (__any_sync(0xffffffffu, (clock64() - t_start) > budget)) {
-                        if (lane == 0) atomicOr(p.status, kDevErrTimeout);
-                        break;
-                    }
-                    __nanosleep(64);  // a short nap: the successors' lookbacks wait on this tile
-                }
-                // sum over the predecessors of (A_T)^k v_k: each lane applies its own power, then a
-                // reduce-scatter leaves word i of the sum in lane i
-                packed_mv<K>(sATl + lane * MS, v, tmp);
-                const float part = reduce_scatter<S, Dm::P2, Dm::SH>(tmp, lane);
-                zi_lane = __shfl_sync(0xffffffffu, part, (lane < S ? lane : 0) << Dm::SH);
-            }
-            if (tr) tr[2] = global_ns();
-            if ((cur & 31) == 0 && cur + 1 < p.n_tiles) {
-                // only anchor tiles' resolved carries are read: A_T Z + tile carry
-                const float gl = lane_mv<S>(sATd, zi_lane, lane) + acc_i;
-                if (lane < S) st_relaxed_b64(dcur + lane, pack_word(tagG, gl));
-            }
-            // incoming state of each group of the tile: Z_0 = Z, Z_{v+1} = A_C Z_v + a_v
-            float *zb = z_buf + slot * W * S;
-#pragma unroll 1
-            for (int v = 0; v < W; ++v) {
-                if (lane < S) zb[v * S + lane] = zi_lane;
-                if (v + 1 < W) zi_lane = lane_mv<S>(sACd, zi_lane, lane) + abuf[v * S + (lane < S ? lane : 0)];
-            }
+            coordinate_tile<K, W, MS, Dm::P2, Dm::SH, kLaneSpan>(p, lane, cur, slot, budget, sATl, mats, sACd, a_buf,
+                                                                 z_buf, agg, tr);
             __syncwarp();
             if (lane == 0) mbar_arrive(&bar_zready[slot]);
             if (tr) tr[3] = global_ns();

@@ -36,7 +36,7 @@ struct Launch {
 };
 std::vector<Launch> g_launches;
 bool g_light = false;          // record no parameter blocks and skip the marker (timing runs)
-float g_cost[6][3][9] = {};    // simulated time of a launch, ms, by kind, N (32, 64, 128) and K
+float g_cost[7][3][9] = {};    // simulated time of a launch, ms, by kind, N (32, 64, 128) and K
 
 int n_index(int N) { return N == 32 ? 0 : N == 64 ? 1 : 2; }
 
@@ -167,6 +167,7 @@ int lane_blocks_per_sm_n64w10b(int, bool) { return 1; }
 int batch_blocks_per_sm(int, bool) { return 1; }
 int batch_all_blocks_per_sm() { return 1; }
 int dtcr_blocks_per_sm(int, bool) { return 1; }
+int tc_blocks_per_sm(int) { return 1; }
 int default_lbm(int N) { return N <= 32 ? 4 : N == 64 ? 2 : 1; }
 
 cudaError_t launch_dccr(int K, int N, bool norm, int, const PassParams &p, long long grid, cudaStream_t) {
@@ -229,8 +230,18 @@ cudaError_t launch_batch_all(const BatchAllParams &p, long long grid, cudaStream
         mark(p.x, p.y, p.n, p.zi, p.zf, K);                                                         \
         return cudaSuccess;                                                                         \
     }
+// the tensor-core kernel: recorded as kind 6; its operand image and final-state table must exist
+#define HOST_TC(K)                                                                                           \
+    template <>                                                                                              \
+    cudaError_t launch_tc<K>(const LaneParams<K> &p, const float *img, const float *gtail, long long grid, \
+                             cudaStream_t) {                                                                 \
+        if (!img || !gtail) return cudaErrorInvalidValue;                                                    \
+        record(6, K, 64, false, grid, p);                                                                    \
+        mark(p.x, p.y, p.n, p.zi, p.zf, K);                                                                  \
+        return cudaSuccess;                                                                                  \
+    }
 #define HOST_ALL(K) HOST_LANE(K, 32, 7) HOST_LANE(K, 64, 7) HOST_LANE(K, 64, 10) HOST_CAS(K, 32) HOST_CAS(K, 64) \
-    HOST_BATCH(K) HOST_DTCR(K)
+    HOST_BATCH(K) HOST_DTCR(K) HOST_TC(K)
 HOST_ALL(1) HOST_ALL(2) HOST_ALL(3) HOST_ALL(4) HOST_ALL(5) HOST_ALL(6) HOST_ALL(7) HOST_ALL(8)
 
 }  // namespace sosk

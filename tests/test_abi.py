@@ -112,7 +112,7 @@ def test_ctypes_structures_match_the_header_layout():
 def _tuning_valid(N, carry, solver, lw, det):
     """sos_filter_create's verdict on a tuning, written from the sos_tuning documentation in
     include/sosfilt.h (not from the implementation)."""
-    if N not in (0, 32, 64, 128) or carry not in (0, 1, 2) or solver not in (0, 1, 2, 3):
+    if N not in (0, 32, 64, 128) or carry not in (0, 1, 2) or solver not in (0, 1, 2, 3, 4):
         return False
     if lw not in (0, 1, 2, 4, 8, 16) or det not in (0, 1):
         return False
@@ -121,6 +121,8 @@ def _tuning_valid(N, carry, solver, lw, det):
     if solver == 2 and (N == 128 or carry == 2 or lw):
         return False
     if solver == 3 and (N not in (0, 64) or carry == 2 or lw):  # double-thread-group: N = 64, cascade carry
+        return False
+    if solver == 4 and (N not in (0, 64) or carry == 2 or lw):  # tensor cores: N = 64, cascade carry
         return False
     if det and (solver in (1, 3) or carry or lw or N == 128):
         return False
@@ -159,7 +161,8 @@ def test_tuning_validation_matches_the_header(lib):
     # the reserved and fixed fields
     for t in (Tuning(L=16), Tuning(threads_per_group=64), Tuning(groups_per_cta=2), Tuning(fp64_carry=1),
               Tuning(spin_budget_cycles=-1), Tuning(groups_per_cta=10, N=32), Tuning(groups_per_cta=7, solver=1),
-              Tuning(groups_per_cta=10, solver=3), Tuning(groups_per_cta=7, carry=2)):
+              Tuning(groups_per_cta=10, solver=3), Tuning(groups_per_cta=7, carry=2), Tuning(groups_per_cta=8, solver=4),
+              Tuning(groups_per_cta=7, solver=4)):
         assert _create_verdict(lib, sos, t) == -1
     # groups per tile of the PH solver: 7, or 10 at N = 64 (the default solver is PH)
     for t in (Tuning(groups_per_cta=7), Tuning(groups_per_cta=10), Tuning(groups_per_cta=10, solver=2, N=64),

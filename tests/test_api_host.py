@@ -33,7 +33,7 @@ _DEPS = _SRCS + [os.path.join(_HERE, "api_host", "cuda_runtime.h"), os.path.join
                  os.path.join(_CSRC, "sosfilt_internal.h")]
 _LIB = os.path.join(_HERE, "_build", "libapi_host.so")
 N64, W, C64 = 64, 7, 32 * 64
-KIND_LANE, KIND_CASCADE, KIND_BATCH, KIND_SECTION, KIND_DTCR = 1, 2, 3, 4, 5
+KIND_LANE, KIND_CASCADE, KIND_BATCH, KIND_SECTION, KIND_DTCR, KIND_TC = 1, 2, 3, 4, 5, 6
 
 
 @pytest.fixture(scope="module")
@@ -794,7 +794,7 @@ def test_a_captured_run_resets_its_own_counter_and_descriptors(lib, tuning, kind
 
 def _tune_costs(lib, fastest):
     """Simulated launch times: the candidate fastest(K) takes 1 ms per launch, the others 2 and 3."""
-    cands = [(KIND_CASCADE, 32), (KIND_CASCADE, 64), (KIND_LANE, 64), (KIND_DTCR, 64)]  # the autotuner's candidates
+    cands = [(KIND_CASCADE, 32), (KIND_CASCADE, 64), (KIND_LANE, 64), (KIND_DTCR, 64), (KIND_TC, 64)]  # the autotuner's candidates
     # (the PH candidates with 7 and 10 groups per tile are both (KIND_LANE, 64) here: equal simulated times,
     # and the first measured of them, 7 groups, is kept)
     for K in range(1, 9):
@@ -806,8 +806,8 @@ def _tune_costs(lib, fastest):
 
 
 def test_autotuner_choices_drive_the_default_launch(lib):
-    """The autotuner times its four candidates per section count and length bucket and keeps the
-    fastest; default-tuned runs then launch that choice, an explicit tuning still wins."""
+    """The autotuner times its candidates per section count and length bucket and keeps the fastest;
+    default-tuned runs then launch that choice, an explicit tuning still wins."""
     lib.sos_autotune.argtypes = [ctypes.c_int, ctypes.c_void_p]
     lib.sos_autotune_choice.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_int)]
@@ -819,25 +819,27 @@ def test_autotuner_choices_drive_the_default_launch(lib):
         return solver.value, N.value
 
     assert choice(4, 1 << 20) == (0, 0)  # nothing tuned yet: the library's defaults
-    report = np.zeros((8, 4, 5), dtype=np.float32)
-    _tune_costs(lib, lambda K: (KIND_CASCADE, 32) if K <= 3 else (KIND_DTCR, 64) if K == 5 else (KIND_LANE, 64))
+    report = np.zeros((8, 4, 6), dtype=np.float32)
+    fastest = {5: (KIND_DTCR, 64), 7: (KIND_TC, 64)}
+    _tune_costs(lib, lambda K: (KIND_CASCADE, 32) if K <= 3 else fastest.get(K, (KIND_LANE, 64)))
     lib.host_set_light(1)
     try:
         assert lib.sos_autotune(16, report.ctypes.data) == 0
     finally:
         lib.host_set_light(0)
     for K in range(1, 9):
-        want = (1, 32) if K <= 3 else (3, 64) if K == 5 else (2, 64)
+        want = (1, 32) if K <= 3 else (3, 64) if K == 5 else (4, 64) if K == 7 else (2, 64)
         for n in (1000, 1 << 16, 1 << 22, 1 << 30):  # buckets above 2^16 repeat the measured one
             assert choice(K, n) == want, (K, n)
-        assert np.argmax(report[K - 1, 0]) == (0 if K <= 3 else 3 if K == 5 else 2)
+        assert np.argmax(report[K - 1, 0]) == (0 if K <= 3 else 3 if K == 5 else 5 if K == 7 else 2)
         np.testing.assert_array_equal(report[K - 1, 1:], np.repeat(report[K - 1, :1], 3, axis=0))
     assert choice(12, 1 << 20) == (2, 64)  # more than eight sections: the eight-section choice
 
     x = workloads.normal_f32(13, 40000)
     y = np.empty_like(x)
     for K, tuning, want in [(2, None, (KIND_CASCADE, 32)), (6, None, (KIND_LANE, 64)), (5, None, (KIND_DTCR, 64)),
-                            (2, {"solver": 2}, (KIND_LANE, 64)), (2, {"solver": 3}, (KIND_DTCR, 64))]:
+                            (7, None, (KIND_TC, 64)), (2, {"solver": 2}, (KIND_LANE, 64)),
+                            (2, {"solver": 3}, (KIND_DTCR, 64)), (2, {"solver": 4}, (KIND_TC, 64))]:
         f = _create(lib, designs.butter_lowpass(2 * K, 0.2), tuning)
         lib.host_reset()
         assert lib.sos_filter_run(f, x.ctypes.data, y.ctypes.data, x.size, None, None, None) == 0

@@ -18,12 +18,13 @@ def test_autotune_choices_and_parity():
     from paper_2607_23763_gb300 import SosFilter, autotune, autotune_choice
     dev = torch.device("cuda:0")
     rep = autotune(max_log2n=22)
-    assert rep.shape == (8, 4, 5)
+    assert rep.shape == (8, 4, 6)
     assert np.all(rep[:, :3, :] > 0)  # lengths up to 2^24 (2^22 cap: the last bucket repeats the third)
     for K in (1, 2, 4, 8):
         for n in (1000, 1 << 16, 3 << 20, 1 << 27):
             solver, N, W = autotune_choice(K, n, with_groups=True)
-            assert (solver, N, W) in ((1, 32, 0), (1, 64, 0), (2, 64, 7), (3, 64, 0), (2, 64, 10)), (K, n, solver, N, W)
+            assert (solver, N, W) in ((1, 32, 0), (1, 64, 0), (2, 64, 7), (3, 64, 0), (2, 64, 10), (4, 64, 8)), \
+                (K, n, solver, N, W)
     for K, n in ((1, 70001), (2, 1 << 16), (4, 300000), (8, 1 << 20)):
         sos = designs.butter_lowpass(2 * K, 0.05 if K > 1 else 0.2)
         x = workloads.normal_f32(K, n)

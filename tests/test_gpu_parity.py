@@ -71,17 +71,19 @@ SIZES = [1, 2, 3, 5, 31, 32, 33, 127, 511, 512, 513, 1023, 1024, 1025, 2047, 204
 
 
 CARRY_CASCADE, CARRY_SECTION = 1, 2
-SOLVER_CR, SOLVER_PH, SOLVER_DTCR = 1, 2, 3
+SOLVER_CR, SOLVER_PH, SOLVER_DTCR, SOLVER_TC = 1, 2, 3, 4
 # solver and launch configuration: PH factorization (skewed particular pass) at N = 64 and 32;
 # cyclic reduction with the cascade carry at N = 32 and 64, and with per-section carries at N = 32,
 # 64 and 128
 SCHEMES = [{"solver": SOLVER_PH}, {"solver": SOLVER_PH, "N": 32}, {"carry": CARRY_CASCADE, "N": 32},
            {"carry": CARRY_CASCADE, "N": 64}, {"carry": CARRY_SECTION, "N": 32}, {"carry": CARRY_SECTION, "N": 64},
-           {"carry": CARRY_SECTION, "N": 128}, {"solver": SOLVER_DTCR}, {"solver": SOLVER_PH, "groups_per_cta": 10}]
+           {"carry": CARRY_SECTION, "N": 128}, {"solver": SOLVER_DTCR}, {"solver": SOLVER_PH, "groups_per_cta": 10},
+           {"solver": SOLVER_TC}]
 SCHEME_IDS = ["ph-64", "ph-32", "cr-cascade-32", "cr-cascade-64", "cr-section-32", "cr-section-64",
-              "cr-section-128", "dtcr-64", "ph-64-w10"]
+              "cr-section-128", "dtcr-64", "ph-64-w10", "tc-64"]
 PH_W = 7  # groups per PH tile
 DTCR_W = 4  # groups per double-thread-group tile
+TC_W = 8  # groups per tensor-core tile
 
 
 def _several_tiles(tuning):
@@ -90,11 +92,13 @@ def _several_tiles(tuning):
         return 3 * tuning.get("groups_per_cta", PH_W) * 32 * tuning.get("N", 64) + 123
     if tuning.get("solver") == SOLVER_DTCR:
         return 3 * DTCR_W * 32 * 64 + 123
+    if tuning.get("solver") == SOLVER_TC:
+        return 3 * TC_W * 32 * 64 + 123
     return 5 * 32 * tuning.get("N", 32) + 123
 # one setting per kernel: PH, cyclic reduction with the cascade carry, with per-section carries
 KERNELS = [{"solver": SOLVER_PH}, {"carry": CARRY_CASCADE}, {"carry": CARRY_SECTION}, {"solver": SOLVER_DTCR},
-           {"solver": SOLVER_PH, "groups_per_cta": 10}]
-KERNEL_IDS = ["ph", "cr-cascade", "cr-section", "dtcr", "ph-w10"]
+           {"solver": SOLVER_PH, "groups_per_cta": 10}, {"solver": SOLVER_TC}]
+KERNEL_IDS = ["ph", "cr-cascade", "cr-section", "dtcr", "ph-w10", "tc"]
 
 
 @pytest.mark.parametrize("tuning", SCHEMES, ids=SCHEME_IDS)
@@ -310,8 +314,9 @@ def test_run_host_direct_on_pinned_buffers(dev):
 
 
 @pytest.mark.parametrize("tuning,order", [({"solver": SOLVER_PH}, 16), ({"solver": SOLVER_CR, "N": 64}, 16),
-                                          ({"solver": SOLVER_DTCR}, 16), ({"solver": SOLVER_PH}, 24)],
-                         ids=["ph", "cr-64", "dtcr", "ph-two-pass"])
+                                          ({"solver": SOLVER_DTCR}, 16), ({"solver": SOLVER_PH}, 24),
+                                          ({"solver": SOLVER_TC}, 16), ({"solver": SOLVER_TC}, 24)],
+                         ids=["ph", "cr-64", "dtcr", "ph-two-pass", "tc", "tc-two-pass"])
 def test_run_captured_in_a_cuda_graph_and_replayed(dev, tuning, order):
     """sos_filter_run captured into a CUDA graph: every replay resets the run's own ticket counter and
     lookback descriptors inside the graph, so replays with new input each match the oracle, and eager
@@ -391,12 +396,14 @@ def _window_check(sos, x_host, y_dev, starts, width, settle):
     return worst
 
 
-def test_config2_full_size_sampled(dev):
-    """Order-16 Butterworth at 0.05 Nyquist, 2^28 samples, seed 1, in the bench's launch configuration."""
+@pytest.mark.parametrize("tuning", [None, {"solver": SOLVER_TC}], ids=["default", "tc"])
+def test_config2_full_size_sampled(dev, tuning):
+    """Order-16 Butterworth at 0.05 Nyquist, 2^28 samples, seed 1, in the bench's launch configuration
+    (and on the tensor-core kernel)."""
     sos = designs.butter_lowpass(16, 0.05)
     n = 1 << 28
     x = workloads.normal_f32(1, n)
-    f = _filt(sos)
+    f = _filt(sos, tuning=tuning)
     xd = torch.from_numpy(x).to(dev)
     y = f.run(xd)
     torch.cuda.synchronize()
@@ -409,6 +416,19 @@ def test_config2_full_size_sampled(dev):
     # a property at full size: the tail matches a one-shot oracle run on the last 2^20 samples
     assert np.all(np.isfinite(y[-(1 << 20):].cpu().numpy()))
     f.close()
+
+
+@pytest.mark.parametrize("order", [2, 16, 24])
+def test_tc_many_tiles_per_block(dev, order):
+    """The tensor-core kernel with many tiles per thread block (2^24 + 333 samples: about seven tiles of
+    16384 samples per SM, so every input stage, accumulator slot and carry slot is reused many times),
+    a ragged last row, an initial state and the final state, against the oracle on every sample."""
+    sos = designs.butter_lowpass(order, 0.05 if order > 2 else 0.2)
+    K = sos.shape[0]
+    n = (1 << 24) + 333
+    x = workloads.normal_f32(90 + order, n)
+    zi = np.random.default_rng(order).standard_normal((K, 2)) * 0.01
+    _run_check(sos, x, dev, zi=zi, tuning={"solver": SOLVER_TC}, tol=designs.tolerance_for(sos))
 
 
 def _full_error_chunked(sos, x_host, y_dev, chunk=1 << 24):
@@ -467,7 +487,8 @@ def test_wait_budget_expiry_reports_timeout_and_recovers(dev, tuning):
     g.close()
 
 
-def test_deterministic_mode_is_bit_reproducible(dev):
+@pytest.mark.parametrize("solver", [0, SOLVER_TC], ids=["ph", "tc"])
+def test_deterministic_mode_is_bit_reproducible(dev, solver):
     """With deterministic = 1 every tile composes its incoming state from a fixed anchor, so repeated
     runs (and a second filter object) give bit-identical outputs and final states; the result still
     matches the oracle."""
@@ -479,7 +500,7 @@ def test_deterministic_mode_is_bit_reproducible(dev):
     zid = torch.from_numpy(zi).to(dev)
     outs, states = [], []
     for rep in range(3):
-        f = SosFilter(sos, tuning={"deterministic": 1})
+        f = SosFilter(sos, tuning={"deterministic": 1, "solver": solver})
         zf = torch.zeros(8, 2, device=dev)
         y = f.run(xd, zi=zid, zf=zf)
         assert f.sync_status() == 0
