@@ -516,9 +516,8 @@ sos_status build_lane(sos_filter *f, int N, int W, std::vector<LanePass> &out) {
             }
         const int ms = lane_stride(kp), full = S * S;
         const size_t off_ac = 64 * static_cast<size_t>(ms), off_h = off_ac + full, off_at = off_h + N * S;
-        const size_t off_at32 = off_at + full, off_ats = off_at32 + full, off_ats1 = off_ats + full;
-        std::vector<float> tab(off_ats1 + full, 0.f);
-        const int span = 32 * (W == sosk::kTcGroups ? sosk::kTcSpan : sosk::kLaneSpan);  // anchor spacing in tiles
+        const size_t off_at32 = off_at + full, off_at31 = off_at32 + full, off_acp = off_at31 + full;
+        std::vector<float> tab(off_acp + static_cast<size_t>(W - 1) * full, 0.f);
         DMat L = deye(S), LT = deye(S);
         for (int l = 0; l < 32; ++l) {
             pack_into(L, kp, &tab[static_cast<size_t>(l) * ms]);
@@ -531,8 +530,14 @@ sos_status build_lane(sos_filter *f, int N, int W, std::vector<LanePass> &out) {
             for (int m = 0; m < N; ++m) tab[off_h + static_cast<size_t>(j) * N + m] = ps.H[static_cast<size_t>(j) * N + m];
         dense_colmajor_into(AT, &tab[off_at]);
         dense_colmajor_into(dpow(AT, 32), &tab[off_at32]);
-        dense_colmajor_into(dpow(AT, span), &tab[off_ats]);
-        dense_colmajor_into(dpow(AT, span - 1), &tab[off_ats1]);
+        dense_colmajor_into(dpow(AT, 31), &tab[off_at31]);
+        {
+            DMat P = AC;
+            for (int v = 1; v < W; ++v) {
+                dense_colmajor_into(P, &tab[off_acp + static_cast<size_t>(v - 1) * full]);
+                P = dmul(P, AC);
+            }
+        }
         if (cudaMalloc(&ps.d_tab, tab.size() * sizeof(float)) != cudaSuccess) return SOS_ENOMEM;
         if (cudaMemcpy(ps.d_tab, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
             return SOS_ECUDA;

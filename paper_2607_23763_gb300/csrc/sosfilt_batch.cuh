@@ -89,7 +89,10 @@ __device__ __forceinline__ void batch_body(const BatchParams<K> &p, float4 *smem
     float *a_buf = rowst + W * kL * RSP;             // [2][W][S] local carries of the groups
     float *z_buf = a_buf + 2 * W * S;                // [2][W][S] incoming states of the groups
     float *agg = z_buf + 2 * W * S;                  // [2][S] tile carry under zero incoming state
-    float *zs_tail = agg + 2 * S;                    // [2][SZ] lane-local state after a signal's last sample
+    // [2][W][SZ] lane-local state after a signal's last sample, per slot and warp: a warp overwrites
+    // only its own capture, after its own correction has read it (another warp may run two tiles
+    // ahead, into the same slot, before this one corrects)
+    float *zs_tail = agg + 2 * S;
     __shared__ unsigned long long bar_local[2], bar_zready[2], bar_ticket[8];
     __shared__ long long ring[8];
     __shared__ int ring_sig[8];
@@ -277,7 +280,7 @@ __device__ __forceinline__ void batch_body(const BatchParams<K> &p, float4 *smem
                 // lane's incoming state over the samples up to it, M1^(m_last + 1) st
                 float zt[S];
                 packed_mv_gr<K>(sg->Mm + static_cast<int>(p_last % N) * Dm::NF, st, zt);
-                const float *zs = zs_tail + slot * SZ;
+                const float *zs = zs_tail + (slot * W + w) * SZ;
                 float *zf = sg->zf;
 #pragma unroll
                 for (int s = 0; s < K; ++s) {
@@ -366,7 +369,7 @@ __device__ __forceinline__ void batch_body(const BatchParams<K> &p, float4 *smem
             const long long p_last = sg->n - 1 - (G - 1) * C;
             if (g == G - 1 && sg->zf)
                 lane_particular<K, N, NORM, true>(cs, X + lane * P, sg->gain, t, static_cast<int>(p_last % N),
-                                                  lane == static_cast<int>(p_last / N), zs_tail + slot * SZ);
+                                                  lane == static_cast<int>(p_last / N), zs_tail + (slot * W + w) * SZ);
             else
                 lane_particular<K, N, NORM, false>(cs, X + lane * P, sg->gain, t, 0, false, nullptr);
             lane_scan<K>(cs, t, Sl, a_buf + (slot * W + w) * S, lane);
@@ -430,7 +433,7 @@ template <int K>
 constexpr size_t batch_smem_bytes() {
     using Dm = LaneDims<K, kBatchN>;
     return sizeof(float) * (static_cast<size_t>(kBatchW) * 3 * kL * (kBatchN + 4) + kBatchW * kL * Dm::RSP +
-                            4 * kBatchW * Dm::S + 2 * Dm::S + 2 * ((Dm::S + 3) / 4) * 4);
+                            4 * kBatchW * Dm::S + 2 * Dm::S + 2 * kBatchW * ((Dm::S + 3) / 4) * 4);
 }
 
 }  // namespace sosk

@@ -134,8 +134,6 @@ size_t cascade_smem(int K, int N);
 // ---- PH-factorization kernel with a skewed direct-form-II particular pass (sosfilt_lane.cuh)
 constexpr int kLaneW = 7;    // compute warps per block, one group each; a tile is kLaneW groups
 constexpr int kLaneWide = 10;  // the wide variant at N = 64: 10 groups per tile (sos_tuning.groups_per_cta)
-constexpr int kLaneSpan = 1;   // PH kernels: lookback anchors every 32 kLaneSpan tiles
-constexpr int kTcSpan = 1;     // the tensor-core kernel: anchors every 32 kTcSpan tiles
 
 // Per-section constants of the skewed-pass kernel, in the kernel's domain (b / b0 and b0 = 1 when
 // normalized; carried state = zscale * true state).

@@ -65,18 +65,20 @@ struct LaneDims {
     static constexpr int S4 = (S + 3) / 4;
     static constexpr int RSP = 4 * ((S4 & 1) ? S4 : S4 + 1);
     // table block: (M_N)^lane [32][MS], (A_T)^lane [32][MS], A_C dense column-major, the basis
-    // [S][N] (read in chunks of V samples), A_T dense, (A_T)^32, (A_T)^SPAN, (A_T)^(SPAN - 1) dense
+    // [S][N] (read in chunks of V samples), A_T, (A_T)^32 and (A_T)^31 dense
     static constexpr int OFF_ATL = 32 * MS;
     static constexpr int OFF_AC = 64 * MS;
     static constexpr int OFF_H = OFF_AC + FULL;
     static constexpr int OFF_AT = OFF_H + N * S;
-    static constexpr int OFF_AT32 = OFF_AT + FULL;  // (A_T)^32 dense: combines lookback blocks of 32 tiles
-    // (A_T)^SPAN and (A_T)^(SPAN - 1) dense, SPAN the anchor spacing in tiles: an anchor's resolved
-    // carry from the previous anchor's, and its incoming state
-    static constexpr int OFF_ATS = OFF_AT32 + FULL;
-    static constexpr int OFF_ATS1 = OFF_ATS + FULL;
-    static constexpr int TAB = OFF_ATS1 + FULL;
-    static constexpr int TAB_GLOBAL = TAB;
+    // (A_T)^32 and (A_T)^31 dense: an anchor's resolved carry from the previous anchor's, and its
+    // incoming state
+    static constexpr int OFF_AT32 = OFF_AT + FULL;
+    static constexpr int OFF_AT31 = OFF_AT32 + FULL;
+    static constexpr int TAB = OFF_AT31 + FULL;
+    // global only: (A_C)^v dense, v = 1 .. W - 1, the transitions from a tile's incoming state to its
+    // groups' (read through L1, or copied by kernels with room for them)
+    static constexpr int OFF_ACP = TAB;
+    static constexpr int TAB_GLOBAL = OFF_ACP + (W - 1) * FULL;
     // the shared-memory copy: (M_N)^lane, (A_T)^lane when ATL_SHARED, then A_C .. A_T
     static constexpr int SM_AC = ATL_SHARED ? OFF_AC : OFF_ATL;
     static constexpr int SM_TAB = SM_AC + (TAB - OFF_AC);
@@ -319,130 +321,179 @@ __device__ __forceinline__ void lane_state_mv(const float *__restrict__ A, const
     }
 }
 
-// Dense matrices the coordinator applies (column-major S x S): A_T, (A_T)^32, (A_T)^SPAN and
-// (A_T)^(SPAN - 1), SPAN the anchor spacing in tiles.
+// Dense matrices the coordinator applies (column-major S x S): A_T, (A_T)^32, (A_T)^31, and
+// (A_C)^v for v = 1 .. W - 1 (consecutive).
 struct CoordMats {
-    const float *AT, *AT32, *ATS, *ATS1;
+    const float *AT, *AT32, *AT31, *ACp;
 };
 
+constexpr long long kAnchor = 32;      // tiles between anchors
+constexpr long long kSuperAnchor = 4;  // anchors between super-anchors
+
+// Row `lane` (< 2K) of a packed lower block-triangular matrix times a vector held by every lane;
+// lanes >= 2K give 0.
+template <int K>
+__device__ __forceinline__ float packed_row(const float *__restrict__ A, const float (&x)[2 * K], int lane) {
+    float y = 0.f;
+    const int sb = lane >> 1, r = lane & 1;
+#pragma unroll
+    for (int s = 0; s < K; ++s) {
+        if (s == sb) {
+#pragma unroll
+            for (int t = 0; t <= s; ++t) {
+                const float4 B = *reinterpret_cast<const float4 *>(A + 4 * (s * (s + 1) / 2 + t));
+                y = fmaf(r ? B.z : B.x, x[2 * t], fmaf(r ? B.w : B.y, x[2 * t + 1], y));
+            }
+        }
+    }
+    return y;
+}
+
 // One tile's work of the coordinator warp: decoupled lookback over tiles (Sec. IV-B, Eq. 25 on the
-// cascade state) for tile cur's incoming 2K-word state, its resolved carry when cur is an anchor
-// tile, and the incoming state of each of its W groups in z_buf[slot] (Z_0 = Z, Z_{v+1} = A_C Z_v +
-// a_v).  The composition is fixed: the resolved carry of the last anchor before cur (the tiles at
-// multiples of SPAN = 32 M) and the local carries after it, so that outputs are reproducible bit for
-// bit.  Each lane reads M predecessors, 32 apart, and the M partial sums combine by Horner's rule
-// with (A_T)^32.
-// The anchors' resolved carries form a chain, one hop per SPAN tiles, that bounds the kernel's rate;
-// an anchor therefore sums its local carries first, before the previous anchor's carry G can have
-// arrived, and the hop itself is one product: G(cur) = (A_T)^SPAN G + [A_T P + carry(cur)], with P
-// the local carries' part of the incoming state Z = (A_T)^(SPAN - 1) G + P.
-template <int K, int W, int MS, int P2, int SH, int M = 1>
+// cascade state) for tile cur's incoming 2K-word state Z, its resolved carry G when cur is an anchor,
+// and the incoming state of each of its W groups in z_buf[slot]: Z_0 = Z, Z_v = (A_C)^v Z + c_{v-1}
+// with c_v the fold's carry of groups 0 .. v under zero input (pref), all independent products.
+// The composition is fixed, so that outputs are reproducible bit for bit:
+//   * every tile first sums the local carries L of the tiles after the anchor a below it (a multiple
+//     of 32): P = sum_{k=1}^{cur-1-a} (A_T)^(k-1) L(cur - k);
+//   * a tile between anchors then adds (A_T)^(cur-1-a) G(a), one packed row per lane, once G(a) is
+//     visible;
+//   * an anchor posts W(cur) = A_T P + carry(cur) in its local-carry slot (an anchor's local carry is
+//     never read); from the super-anchor A below it (multiples of 128), i = (cur - A) / 32 <= 4,
+//     G(cur) = (A_T)^32 (... ((A_T)^32 G(A) + W(A + 32)) ...) + W(cur) by Horner's rule, and
+//     Z = (A_T)^31 G(cur - 32) + P.
+// So the resolved carries form a chain of one hop per 128 tiles, every anchor resolves one hop after
+// the super-anchor below it, and what waits on a carry is a few 2K x 2K products: the local carries
+// are summed before it can have arrived.
+template <int K, int W, int MS, int P2, int SH>
 __device__ __forceinline__ void coordinate_tile(const LaneParams<K> &p, int lane, long long cur, unsigned slot,
                                                 long long budget, const float *sATl, const CoordMats &mats,
-                                                const float *sACd, const float *a_buf, float *z_buf, const float *agg,
+                                                const float *pref, float *z_buf, const float *agg,
                                                 unsigned long long *tr) {
     constexpr int S = 2 * K;
-    constexpr long long SPAN = 32LL * M;
-    const unsigned tagL = (p.epoch << 2) | 1u, tagG = (p.epoch << 2) | 2u;
+    const unsigned tagL = (p.epoch << 2) | 1u, tagG = (p.epoch << 2) | 2u, tagW = (p.epoch << 2) | 3u;
     auto zinit = [&](int i) -> float { return p.zi ? p.zi[i] * p.sec[i >> 1].zscale : 0.f; };
-    const float *abuf = a_buf + slot * W * S;
     const float acc_i = agg[slot * S + (lane < S ? lane : 0)];
-    // descriptor of a tile: two slots of 2K tagged words, its local carry (posted by the fold)
-    // and its resolved carry (posted below)
-    unsigned long long *dcur = p.desc + static_cast<size_t>(cur) * 2 * S + S;
-    const bool anchor = (cur % SPAN) == 0 && cur + 1 < p.n_tiles;  // only anchors' carries are read
+    const int li = lane < S ? lane : 0;
+    // descriptor of a tile: two slots of 2K tagged words, [0] its local carry (posted by the fold;
+    // an anchor's local part W), [1] its resolved carry (anchors only)
+    auto desc = [&](long long t, int k) { return p.desc + static_cast<size_t>(t) * 2 * S + k * S; };
+    auto timed_out = [&](long long t_start) {
+        if (__any_sync(0xffffffffu, (clock64() - t_start) > budget)) {
+            if (lane == 0) atomicOr(p.status, kDevErrTimeout);
+            return true;
+        }
+        return false;
+    };
+    const bool anchor = cur % kAnchor == 0 && cur + 1 < p.n_tiles;  // its carries are read
     float zi_lane = 0.f;
     if (cur == 0) {
-        zi_lane = zinit(lane < S ? lane : 0);
+        zi_lane = zinit(li);
         if (anchor) {
             const float gl = lane_mv<S>(mats.AT, zi_lane, lane) + acc_i;
-            if (lane < S) st_relaxed_b64(dcur + lane, pack_word(tagG, gl));
+            if (lane < S) st_relaxed_b64(desc(0, 1) + lane, pack_word(tagG, gl));
         }
     } else {
-        const long long a = ((cur - 1) / SPAN) * SPAN;
-        float v[M][S];
-        // wait for the predecessors' carries: the local carries of tiles a + 1 .. cur - 1 and, with
-        // with_g, the resolved carry of the anchor a (else its slot stays zero); false on timeout
-        auto poll = [&](bool with_g) -> bool {
+        const long long a = ((cur - 1) / kAnchor) * kAnchor;
+        const int ja = static_cast<int>(cur - 1 - a);  // lane of the anchor a
+        // the local carries of tiles a + 1 .. cur - 1, lane l holding tile cur - 1 - l's
+        float v[S];
+        {
+            const long long pred = cur - 1 - lane;
             const long long t_start = clock64();
             for (;;) {
                 bool ok = true;
+                if (pred > a) {
+                    const unsigned long long *dp = desc(pred, 0);
 #pragma unroll
-                for (int j = 0; j < M; ++j) {
-                    const long long pred = cur - 1 - lane - 32LL * j;
-                    if (pred > a || (with_g && pred == a)) {
-                        const bool g = pred == a;
-                        const unsigned want = g ? tagG : tagL;
-                        const unsigned long long *dp = p.desc + static_cast<size_t>(pred) * 2 * S + (g ? S : 0);
-#pragma unroll
-                        for (int q = 0; q < S; q += 2) {
-                            unsigned long long x0, x1;
-                            ld_relaxed_v2(dp + q, x0, x1);
-                            ok = ok && static_cast<unsigned>(x0 >> 32) == want &&
-                                 static_cast<unsigned>(x1 >> 32) == want;
-                            v[j][q] = __uint_as_float(static_cast<unsigned>(x0));
-                            v[j][q + 1] = __uint_as_float(static_cast<unsigned>(x1));
-                        }
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < S; ++q) v[j][q] = 0.f;
+                    for (int q = 0; q < S; q += 2) {
+                        unsigned long long x0, x1;
+                        ld_relaxed_v2(dp + q, x0, x1);
+                        ok = ok && static_cast<unsigned>(x0 >> 32) == tagL && static_cast<unsigned>(x1 >> 32) == tagL;
+                        v[q] = __uint_as_float(static_cast<unsigned>(x0));
+                        v[q + 1] = __uint_as_float(static_cast<unsigned>(x1));
                     }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < S; ++q) v[q] = 0.f;
                 }
-                if (__all_sync(0xffffffffu, ok)) return true;
-                if (__any_sync(0xffffffffu, (clock64() - t_start) > budget)) {
-                    if (lane == 0) atomicOr(p.status, kDevErrTimeout);
-                    return false;
-                }
+                if (__all_sync(0xffffffffu, ok) || timed_out(t_start)) break;
                 __nanosleep(64);  // a short nap: the successors' lookbacks wait on this tile
             }
-        };
-        // sum_k (A_T)^k v_k over the predecessors read: block j of 32 by each lane's own power
-        // (A_T)^lane and a reduce-scatter (word i of the block's sum in lane i), the blocks by
-        // Horner's rule with (A_T)^32
-        auto combine = [&]() -> float {
-            float z = 0.f, tmp[S];
+        }
+        // the anchor's carries are read before the local sum is formed, so that their latency overlaps
+        // it: G(a) whole in every lane (a tile between anchors), or word li of G(A) and of the local
+        // parts W(A + 32 j), j < ni (an anchor)
+        float g[S], h[kSuperAnchor];
+        const long long A = ((cur - 1) / (kAnchor * kSuperAnchor)) * (kAnchor * kSuperAnchor);
+        const int ni = static_cast<int>((cur - A) / kAnchor);  // 1 .. kSuperAnchor (anchors)
+        auto load_g = [&]() -> bool {
+            bool ok = true;
+            const unsigned long long *dp = desc(a, 1);
 #pragma unroll
-            for (int j = M - 1; j >= 0; --j) {
-                packed_mv<K>(sATl + lane * MS, v[j], tmp);
-                const float part = reduce_scatter<S, P2, SH>(tmp, lane);
-                const float pj = __shfl_sync(0xffffffffu, part, (lane < S ? lane : 0) << SH);
-                z = (j == M - 1) ? pj : lane_mv<S>(mats.AT32, z, lane) + pj;
+            for (int q = 0; q < S; q += 2) {
+                unsigned long long x0, x1;
+                ld_relaxed_v2(dp + q, x0, x1);
+                ok = ok && static_cast<unsigned>(x0 >> 32) == tagG && static_cast<unsigned>(x1 >> 32) == tagG;
+                g[q] = __uint_as_float(static_cast<unsigned>(x0));
+                g[q + 1] = __uint_as_float(static_cast<unsigned>(x1));
             }
-            return z;
+            return ok;
         };
-        if (!anchor) {
-            poll(true);
-            zi_lane = combine();
-        } else {
-            poll(false);
-            const float pl = combine();                              // P, word lane
-            const float wl = lane_mv<S>(mats.AT, pl, lane) + acc_i;  // A_T P + carry(cur)
-            // the previous anchor's resolved carry, word lane (lanes >= S read word 0)
-            const unsigned long long *dg = p.desc + static_cast<size_t>(a) * 2 * S + S + (lane < S ? lane : 0);
-            const long long t_start = clock64();
-            unsigned long long gw = 0;
-            for (;;) {
-                gw = ld_relaxed_b64(dg);
-                if (__all_sync(0xffffffffu, static_cast<unsigned>(gw >> 32) == tagG)) break;
-                if (__any_sync(0xffffffffu, (clock64() - t_start) > budget)) {
-                    if (lane == 0) atomicOr(p.status, kDevErrTimeout);
-                    break;
+        auto load_h = [&]() -> bool {
+            bool ok = true;
+#pragma unroll
+            for (int j = 0; j < kSuperAnchor; ++j) {
+                h[j] = 0.f;
+                if (j < ni) {
+                    const unsigned long long w = ld_relaxed_b64(desc(A + kAnchor * j, j == 0 ? 1 : 0) + li);
+                    ok = ok && static_cast<unsigned>(w >> 32) == (j == 0 ? tagG : tagW);
+                    h[j] = __uint_as_float(static_cast<unsigned>(w));
                 }
-                __nanosleep(32);
             }
-            const float gi = lane < S ? __uint_as_float(static_cast<unsigned>(gw)) : 0.f;
-            const float gl = lane_mv<S>(mats.ATS, gi, lane) + wl;
-            if (lane < S) st_relaxed_b64(dcur + lane, pack_word(tagG, gl));
-            zi_lane = lane_mv<S>(mats.ATS1, gi, lane) + pl;
+            return ok;
+        };
+        bool ready = anchor ? load_h() : load_g();
+        // P: each lane applies its own power (A_T)^lane, a reduce-scatter leaves word i in lane i
+        float pl;
+        {
+            float tmp[S];
+            packed_mv<K>(sATl + lane * MS, v, tmp);
+            const float part = reduce_scatter<S, P2, SH>(tmp, lane);
+            pl = __shfl_sync(0xffffffffu, part, li << SH);
+        }
+        if (!anchor) {
+            const long long t_start = clock64();
+            while (!__all_sync(0xffffffffu, ready) && !timed_out(t_start)) {
+                __nanosleep(32);
+                ready = load_g();
+            }
+            zi_lane = pl + packed_row<K>(sATl + ja * MS, g, lane);
+        } else {
+            const float wl = lane_mv<S>(mats.AT, pl, lane) + acc_i;  // W(cur) = A_T P + carry(cur)
+            if (lane < S) st_relaxed_b64(desc(cur, 0) + lane, pack_word(tagW, wl));
+            const long long t_start = clock64();
+            while (!__all_sync(0xffffffffu, ready) && !timed_out(t_start)) {
+                __nanosleep(32);
+                ready = load_h();
+            }
+            float gprev = h[0];  // G(A), then the resolved carries of the anchors after it
+#pragma unroll
+            for (int j = 1; j < kSuperAnchor; ++j)
+                if (j < ni) gprev = lane_mv<S>(mats.AT32, gprev, lane) + h[j];
+            const float gl = lane_mv<S>(mats.AT32, gprev, lane) + wl;
+            if (lane < S) st_relaxed_b64(desc(cur, 1) + lane, pack_word(tagG, gl));
+            zi_lane = lane_mv<S>(mats.AT31, gprev, lane) + pl;
         }
     }
     if (tr) tr[2] = global_ns();
-    // incoming state of each group of the tile: Z_0 = Z, Z_{v+1} = A_C Z_v + a_v
     float *zb = z_buf + slot * W * S;
-#pragma unroll 1
-    for (int v = 0; v < W; ++v) {
-        if (lane < S) zb[v * S + lane] = zi_lane;
-        if (v + 1 < W) zi_lane = lane_mv<S>(sACd, zi_lane, lane) + abuf[v * S + (lane < S ? lane : 0)];
+    const float *pb = pref + slot * W * S;
+    if (lane < S) zb[lane] = zi_lane;
+#pragma unroll
+    for (int w = 1; w < W; ++w) {
+        const float zw = lane_mv<S>(mats.ACp + (w - 1) * S * S, zi_lane, lane) + pb[(w - 1) * S + li];
+        if (lane < S) zb[w * S + lane] = zw;
     }
 }
 
@@ -465,9 +516,11 @@ __global__ void __maxnreg__((LaneDims<K, N, W>::MAXREG)) sos_lane_kernel(const _
     float *z_buf = a_buf + 2 * W * S;                // [2][W][S] incoming states
     float *agg = z_buf + 2 * W * S;                  // [2][S] tile carry under zero incoming state
     float *zs_tail = agg + 2 * S;                    // [S] lane-local state after the last sample
+    float *pref = zs_tail + ((S + 3) / 4) * 4;       // [2][W][S] fold prefixes: carries of groups 0 .. v
     const float *sATd = tab + Dm::SM_AC + (Dm::OFF_AT - Dm::OFF_AC);    // A_T dense column-major
-    const CoordMats mats{sATd, tab + Dm::SM_AC + (Dm::OFF_AT32 - Dm::OFF_AC), tab + Dm::SM_AC + (Dm::OFF_ATS - Dm::OFF_AC),
-                         tab + Dm::SM_AC + (Dm::OFF_ATS1 - Dm::OFF_AC)};  // dense powers of A_T
+    const CoordMats mats{sATd, tab + Dm::SM_AC + (Dm::OFF_AT32 - Dm::OFF_AC),
+                         tab + Dm::SM_AC + (Dm::OFF_AT31 - Dm::OFF_AC),
+                         p.tab + Dm::OFF_ACP};  // dense powers of A_T (shared) and of A_C (global)
     // tiles alternate between two slots; the incoming-state barrier has one per slot, so that it
     // never runs two phases ahead of a waiter
     __shared__ unsigned long long bar_local[2], bar_zready[2], bar_ticket[8];
@@ -532,8 +585,7 @@ __global__ void __maxnreg__((LaneDims<K, N, W>::MAXREG)) sos_lane_kernel(const _
                 tr[1] = global_ns();
                 tr[13] = smid;
             }
-            coordinate_tile<K, W, MS, Dm::P2, Dm::SH, kLaneSpan>(p, lane, cur, slot, budget, sATl, mats, sACd, a_buf,
-                                                                 z_buf, agg, tr);
+            coordinate_tile<K, W, MS, Dm::P2, Dm::SH>(p, lane, cur, slot, budget, sATl, mats, pref, z_buf, agg, tr);
             __syncwarp();
             if (lane == 0) mbar_arrive(&bar_zready[slot]);
             if (tr) tr[3] = global_ns();
@@ -724,8 +776,11 @@ __global__ void __maxnreg__((LaneDims<K, N, W>::MAXREG)) sos_lane_kernel(const _
                 const int li = lane < S ? lane : 0;
                 float c = abt[li];
 #pragma unroll 1
-                for (int v = 1; v < W; ++v) c = lane_mv<S>(sACd, c, lane) + abt[v * S + li];
-                if (tile > 0 && lane < S)
+                for (int v = 1; v < W; ++v) {
+                    if (lane < S) pref[(slot * W + v - 1) * S + lane] = c;
+                    c = lane_mv<S>(sACd, c, lane) + abt[v * S + li];
+                }
+                if (tile % kAnchor != 0 && lane < S)  // an anchor's local carry is never read
                     st_relaxed_b64(p.desc + static_cast<size_t>(tile) * 2 * S + lane, pack_word((p.epoch << 2) | 1u, c));
                 if (lane < S) agg[slot * S + lane] = c;
                 if (lane == 0) {
@@ -756,7 +811,7 @@ template <int K, int N, int W>
 constexpr size_t lane_smem_bytes() {
     using Dm = LaneDims<K, N, W>;
     return sizeof(float) * (static_cast<size_t>(W) * 2 * kL * (N + 4) + Dm::SM_TAB + W * kL * Dm::RSP +
-                            4 * W * Dm::S + 2 * Dm::S + ((Dm::S + 3) / 4) * 4);
+                            6 * W * Dm::S + 2 * Dm::S + ((Dm::S + 3) / 4) * 4);
 }
 
 }  // namespace sosk

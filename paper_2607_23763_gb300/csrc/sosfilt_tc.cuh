@@ -27,7 +27,7 @@
 //   warps 4-11  epilogue: warpgroup u (warps 4 + 4u .. 7 + 4u) takes unit u of every tile, warp
 //               q of it group 4u + q, reading accumulator lanes 32q..32q+31: terminal states,
 //               lane scan, fold, true row states, outputs staged for TMA stores
-// Pipelines: 3 input stages, 6 accumulator slots of 80 columns (tensor memory, 512 columns), one
+// Pipelines: 2 input stages, 6 accumulator slots of 80 columns (tensor memory, 512 columns), one
 // state-and-output buffer per epilogue warpgroup.  Every wait is bounded by the spin budget.
 #pragma once
 #include <cuda.h>
@@ -43,7 +43,6 @@ constexpr int kTcRows = 128;                      // rows of one MMA unit (four 
 constexpr int kTcUnits = 2;                       // units per tile
 constexpr int kTcW = 4 * kTcUnits;                // groups per tile
 static_assert(kTcW == kTcGroups, "tile geometry");
-constexpr int kTcXS = 3;                          // input stages
 constexpr int kTcDS = 6;                          // accumulator slots
 constexpr int kTcCols = 80;                       // accumulator columns: 64 outputs, 16 state words
 constexpr int kTcTmemCols = 512;                  // tensor memory allocated (kTcDS * kTcCols rounded up)
@@ -54,10 +53,6 @@ constexpr int kTcImg = 2 * kTcB1 + kTcN * 128;    // B1 head, B1 remainder, B2 (
 static_assert(kTcImg == kTcImageBytes, "operand image size");
 constexpr int kTcXBytes = kTcRows * kTcN * 4;     // one unit of rows (two K halves of 16 KB)
 constexpr int kTcOffX = kTcImg;                   // input stages
-// one buffer per epilogue warpgroup: the correction's A operand [128 rows][128 B], then the unit's
-// outputs staged for the TMA stores (two K halves of 16 KB)
-constexpr int kTcOffY = kTcOffX + kTcXS * kTcXBytes;
-constexpr int kTcOffTab = kTcOffY + kTcUnits * kTcXBytes;
 
 template <int K>
 struct TcParams {
@@ -74,23 +69,30 @@ template <int K>
 struct TcDims {
     using Dm = LaneDims<K, kTcN, kTcW>;
     static constexpr int S = 2 * K;
-    // tables after the staging buffers: A_C, A_T, (A_T)^32, (A_T)^SPAN, (A_T)^(SPAN - 1), local
-    // carries, incoming states, tile
-    // carries (floats); (M_N)^lane and (A_T)^lane are read through L1
-    static constexpr int T_AC = 0;
+    static constexpr int XS = K <= 5 ? 3 : 2;  // input stages: three where the tables leave room
+    // one buffer per epilogue warpgroup: the correction's A operand [128 rows][128 B], then the
+    // unit's outputs staged for the TMA stores (two K halves of 16 KB)
+    static constexpr int OFF_Y = kTcOffX + XS * kTcXBytes;
+    static constexpr int OFF_TAB = OFF_Y + kTcUnits * kTcXBytes;
+    // tables after the staging buffers (floats): (M_N)^lane, A_C, A_T, (A_T)^32, (A_T)^31, (A_C)^v for
+    // v = 1 .. W - 1, local carries, incoming states, fold prefixes, tile carries; (A_T)^lane is read
+    // through L1
+    static constexpr int T_ML = 0;
+    static constexpr int T_AC = T_ML + 32 * Dm::MS;
     static constexpr int T_AT = T_AC + S * S;
     static constexpr int T_AT32 = T_AT + S * S;
-    static constexpr int T_ATS = T_AT32 + S * S;
-    static constexpr int T_ATS1 = T_ATS + S * S;
-    static constexpr int T_A = T_ATS1 + S * S;
+    static constexpr int T_AT31 = T_AT32 + S * S;
+    static constexpr int T_ACP = T_AT31 + S * S;
+    static constexpr int T_A = T_ACP + (kTcW - 1) * S * S;
     static constexpr int T_Z = T_A + 2 * kTcW * S;
-    static constexpr int T_AGG = T_Z + 2 * kTcW * S;
+    static constexpr int T_PREF = T_Z + 2 * kTcW * S;
+    static constexpr int T_AGG = T_PREF + 2 * kTcW * S;
     static constexpr int T_END = T_AGG + 2 * S;
 };
 
 template <int K>
 constexpr size_t tc_smem_bytes() {
-    return 1024 + kTcOffTab + sizeof(float) * TcDims<K>::T_END;  // 1024: alignment of the base
+    return 1024 + TcDims<K>::OFF_TAB + sizeof(float) * TcDims<K>::T_END;  // 1024: alignment of the base
 }
 
 // ---- tcgen05, TMA and synchronisation primitives
@@ -171,29 +173,30 @@ template <int K>
 __global__ void __launch_bounds__(kTcThreads, 1) sos_tc_kernel(const __grid_constant__ TcParams<K> P) {
     using Td = TcDims<K>;
     using Dm = typename Td::Dm;
-    constexpr int S = Td::S, MS = Dm::MS;
+    constexpr int S = Td::S, MS = Dm::MS, XS = Td::XS;
     const LaneParams<K> &p = P.p;
     extern __shared__ unsigned char smraw[];
     unsigned char *sm =
         reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~static_cast<uintptr_t>(1023));
-    float *tabs = reinterpret_cast<float *>(sm + kTcOffTab);
-    const float *gML = p.tab;  // (M_N)^lane [32][MS] (global, L1-resident)
+    float *tabs = reinterpret_cast<float *>(sm + Td::OFF_TAB);
+    float *sML = tabs + Td::T_ML;
     float *sACd = tabs + Td::T_AC;
     float *sATd = tabs + Td::T_AT;
     float *sAT32d = tabs + Td::T_AT32;
-    float *sATSd = tabs + Td::T_ATS;
-    float *sATS1d = tabs + Td::T_ATS1;
-    const CoordMats mats{sATd, sAT32d, sATSd, sATS1d};
+    float *sAT31d = tabs + Td::T_AT31;
+    float *sACp = tabs + Td::T_ACP;
+    float *pref = tabs + Td::T_PREF;
+    const CoordMats mats{sATd, sAT32d, sAT31d, sACp};
     float *a_buf = tabs + Td::T_A;
     float *z_buf = tabs + Td::T_Z;
     float *agg = tabs + Td::T_AGG;
     const float *sATl = p.tab + Dm::OFF_ATL;  // (A_T)^lane, read by the coordinator through L1
 
-    __shared__ unsigned long long full[kTcXS], mma_a[kTcXS], conv[kTcXS], xfree[kTcXS];
+    __shared__ unsigned long long full[XS], mma_a[XS], conv[XS], xfree[XS];
     __shared__ unsigned long long dfull[kTcDS], dfree[kTcDS];
     __shared__ unsigned long long st_ready[kTcUnits], corr_done[kTcUnits], patch_bar, mma_fin;
     __shared__ unsigned long long bar_local[2], bar_zready[2];
-    __shared__ long long xs_tile[kTcXS];  // tile of the unit in each input stage, -1: no more tiles
+    __shared__ long long xs_tile[XS];  // tile of the unit in each input stage, -1: no more tiles
     __shared__ long long d_tile[kTcDS];   // tile of the unit in each accumulator slot, -1: no more
     __shared__ long long coord_tile[2];
     __shared__ int fold_count[2];
@@ -214,12 +217,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) sos_tc_kernel(const __grid_cons
             sACd[i] = __ldg(p.tab + Dm::OFF_AC + i);
             sATd[i] = __ldg(p.tab + Dm::OFF_AT + i);
             sAT32d[i] = __ldg(p.tab + Dm::OFF_AT32 + i);
-            sATSd[i] = __ldg(p.tab + Dm::OFF_ATS + i);
-            sATS1d[i] = __ldg(p.tab + Dm::OFF_ATS1 + i);
+            sAT31d[i] = __ldg(p.tab + Dm::OFF_AT31 + i);
         }
+        for (int i = tid; i < 32 * MS; i += kTcThreads) sML[i] = __ldg(p.tab + i);
+        for (int i = tid; i < (kTcW - 1) * S * S; i += kTcThreads) sACp[i] = __ldg(p.tab + Dm::OFF_ACP + i);
     }
     if (tid == 0) {
-        for (int i = 0; i < kTcXS; ++i) {
+        for (int i = 0; i < XS; ++i) {
             mbar_init(&full[i], 1);
             mbar_init(&mma_a[i], 1);
             mbar_init(&conv[i], 1);
@@ -271,8 +275,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sos_tc_kernel(const __grid_cons
                 tr[1] = global_ns();
                 tr[13] = smid;
             }
-            coordinate_tile<K, kTcW, MS, Dm::P2, Dm::SH, kTcSpan>(p, lane, cur, slot, budget, sATl, mats, sACd, a_buf,
-                                                                  z_buf, agg, tr);
+            coordinate_tile<K, kTcW, MS, Dm::P2, Dm::SH>(p, lane, cur, slot, budget, sATl, mats, pref, z_buf, agg, tr);
             __syncwarp();
             if (lane == 0) mbar_arrive(&bar_zready[slot]);
             if (tr) tr[3] = global_ns();
@@ -287,8 +290,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) sos_tc_kernel(const __grid_cons
                 if (tile >= p.n_tiles) tile = -1;
                 trace(tile, 16);
                 for (int u = 0; u < kTcUnits && !stop; ++u) {
-                    const int xs = static_cast<int>(i % kTcXS);
-                    if (i >= kTcXS && !mbar_wait(&xfree[xs], ((i / kTcXS) - 1) & 1, budget, p.status)) {
+                    const int xs = static_cast<int>(i % XS);
+                    if (i >= XS && !mbar_wait(&xfree[xs], ((i / XS) - 1) & 1, budget, p.status)) {
                         stop = gave_up = true;
                         break;
                     }
@@ -325,12 +328,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) sos_tc_kernel(const __grid_cons
                 }
             }
             // when a wait gave up, the loads still in flight complete before the block exits (the last
-            // kTcXS units sit in distinct stages with no arrival after theirs, so their phases are the
+            // XS units sit in distinct stages with no arrival after theirs, so their phases are the
             // current ones); after the end of the tiles the consumers take every unit issued
             if (gave_up)
-                for (unsigned k = 0; k < kTcXS && k < i; ++k) {
+                for (unsigned k = 0; k < XS && k < i; ++k) {
                     const unsigned u = i - 1 - k;
-                    mbar_wait(&full[u % kTcXS], (u / kTcXS) & 1, budget, p.status);
+                    mbar_wait(&full[u % XS], (u / XS) & 1, budget, p.status);
                 }
         }
     } else if (warp == 2) {
@@ -338,7 +341,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sos_tc_kernel(const __grid_cons
         if (lane == 0) {
             constexpr unsigned i80 = tc_idesc(kTcCols), i64 = tc_idesc(kTcN);
             const unsigned b1h = smem_u32(sm), b1l = b1h + kTcB1, b2 = b1h + 2 * kTcB1;
-            const unsigned yb = smem_u32(sm + kTcOffY), xb = smem_u32(sm + kTcOffX);
+            const unsigned yb = smem_u32(sm + Td::OFF_Y), xb = smem_u32(sm + kTcOffX);
             // units through the first products (ia), through the remainder (ib); corrections issued per
             // epilogue warpgroup (ic[u]: units 2 ic[u] + u)
             unsigned ia = 0, ib = 0, ic[kTcUnits] = {};
@@ -376,26 +379,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) sos_tc_kernel(const __grid_cons
                         prog = true;
                     }
                 }
-                if (ib < ia && mbar_try_wait(&conv[ib % kTcXS], (ib / kTcXS) & 1)) {
+                if (ib < ia && mbar_try_wait(&conv[ib % XS], (ib / XS) & 1)) {
                     tc_fence_after();
-                    chain(tmem + (ib % kTcDS) * kTcCols, xb + (ib % kTcXS) * kTcXBytes, b1h, false);  // X_lo B_hi
-                    tc_commit(&xfree[ib % kTcXS]);
+                    chain(tmem + (ib % kTcDS) * kTcCols, xb + (ib % XS) * kTcXBytes, b1h, false);  // X_lo B_hi
+                    tc_commit(&xfree[ib % XS]);
                     tc_commit(&dfull[ib % kTcDS]);
                     if (ib % kTcUnits == 0) trace(d_tile[ib % kTcDS], 19);
                     ++ib;
                     prog = true;
                 }
-                if (!no_more && mbar_try_wait(&full[ia % kTcXS], (ia / kTcXS) & 1)) {
-                    const long long tile = xs_tile[ia % kTcXS];
+                if (!no_more && mbar_try_wait(&full[ia % XS], (ia / XS) & 1)) {
+                    const long long tile = xs_tile[ia % XS];
                     if (tile < 0) {
                         no_more = true;
                         prog = true;
                     } else if (slot_free(ia)) {
                         tc_fence_after();
-                        const unsigned d = tmem + (ia % kTcDS) * kTcCols, a = xb + (ia % kTcXS) * kTcXBytes;
+                        const unsigned d = tmem + (ia % kTcDS) * kTcCols, a = xb + (ia % XS) * kTcXBytes;
                         chain(d, a, b1h, true);   // X B_hi
                         chain(d, a, b1l, false);  // X B_lo
-                        tc_commit(&mma_a[ia % kTcXS]);
+                        tc_commit(&mma_a[ia % XS]);
                         if (ia % kTcUnits == 0) trace(tile, 18);
                         d_tile[ia % kTcDS] = tile;
                         mbar_arrive(&dfull[ia % kTcDS]);
@@ -435,7 +438,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sos_tc_kernel(const __grid_cons
         const int r = 32 * q + lane;  // row within the unit
         const bool lead = q == 0 && lane == 0;  // issues the warpgroup's stores
         const unsigned tl = tmem + (static_cast<unsigned>(32 * q) << 16);
-        unsigned char *buf = sm + kTcOffY + u * kTcXBytes;  // state operand, then the staged outputs
+        unsigned char *buf = sm + Td::OFF_Y + u * kTcXBytes;  // state operand, then the staged outputs
         const ParamSecs<K> cs{p};
         const bool want_zf = p.zf != nullptr;
         const long long g_last = p.G - 1;
@@ -476,8 +479,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) sos_tc_kernel(const __grid_cons
                     const int li = lane < S ? lane : 0;
                     float cc = abt[li];
 #pragma unroll 1
-                    for (int w = 1; w < kTcW; ++w) cc = lane_mv<S>(sACd, cc, lane) + abt[w * S + li];
-                    if (tile > 0 && lane < S)
+                    for (int w = 1; w < kTcW; ++w) {
+                        if (lane < S) pref[(slot * kTcW + w - 1) * S + lane] = cc;
+                        cc = lane_mv<S>(sACd, cc, lane) + abt[w * S + li];
+                    }
+                    if (tile % kAnchor != 0 && lane < S)  // an anchor's local carry is never read
                         st_relaxed_b64(p.desc + static_cast<size_t>(tile) * 2 * S + lane,
                                        pack_word((p.epoch << 2) | 1u, cc));
                     if (lane < S) agg[slot * S + lane] = cc;
@@ -502,7 +508,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sos_tc_kernel(const __grid_cons
                 float st[S];
 #pragma unroll
                 for (int j = 0; j < S; ++j) st[j] = Sp[j];
-                lane_state_mv<K>(gML + lane * MS, z_buf + (ps * kTcW + v) * S, st);
+                lane_state_mv<K>(sML + lane * MS, z_buf + (ps * kTcW + v) * S, st);
                 const long long g = prev * kTcW + v;
                 if (want_zf && g == g_last && lane == lane_last) {
                     // final state: the lane's zero-state state after its last sample (G restricted to
@@ -593,8 +599,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) sos_tc_kernel(const __grid_cons
     } else if (warp == 3) {
         // ------------------------------------------------------------------ TF32 remainder of the input
         for (unsigned i = 0;; ++i) {
-            const int xs = static_cast<int>(i % kTcXS);
-            const unsigned ph = (i / kTcXS) & 1;
+            const int xs = static_cast<int>(i % XS);
+            const unsigned ph = (i / XS) & 1;
             if (!mbar_wait(&full[xs], ph, budget, p.status)) break;
             if (xs_tile[xs] < 0) break;
             if (!mbar_wait(&mma_a[xs], ph, budget, p.status)) break;

@@ -12,6 +12,14 @@
  * the same order as emu_reference(), so a correct protocol gives bit-identical results whatever
  * the interleaving of the threads.
  *
+ * The single-signal form (emu_run_hier) is the single-signal kernels': every tile first sums the
+ * local carries after its anchor, P = sum_k A^(k-1) L(t - k) (Horner from zero); a tile between
+ * anchors then waits for G(a) and takes Z = A^(t-1-a) G(a) + P; an anchor t publishes its local part
+ * W = A P + L(t) in its slot 0 (tag epoch << 2 | 3), waits for the resolved carry of the
+ * super-anchor s below it (multiples of 128) and the local parts of the anchors between, composes
+ * G(t) = A^32 (... (A^32 G(s) + W(s + 32)) ...) + W(t) by Horner's rule, publishes it and takes
+ * Z = A^31 G(t - 32) + P.  The powers A^k are passed in (float32).
+ *
  * The batched form (emu_run_batch) is the batch kernel's: the tiles of several signals share one
  * ticket queue (a tile -> signal map, each signal's tiles consecutive from its first tile t0), and
  * each signal keeps its own chain -- its first tile starts from the signal's initial state, the
@@ -32,6 +40,7 @@ typedef struct {
     _Atomic uint64_t *desc;  /* [n_tiles][2][S] */
     const float *local;      /* [n_tiles][S] local carries */
     const float *AT;         /* [signals][S][S] row-major tile transition of each signal */
+    const float *APow;       /* hierarchical protocol: [33][S][S] A^k, k = 0 .. 32; else NULL */
     const float *z0;         /* [signals][S] initial state of each signal */
     const int *tile_sig;     /* [n_tiles] signal of each tile */
     const int64_t *tile0;    /* [signals] first tile of each signal */
@@ -88,6 +97,51 @@ static void publish(emu_ctx *c, int64_t tile, int slot, unsigned tag, const floa
     for (int i = 0; i < c->S; ++i) atomic_store_explicit(&w[i], pack(tag, v[i]), memory_order_release);
 }
 
+/* The hierarchical composition of tile t (single signal); 0 when a wait ran out. */
+static int hier_tile(emu_ctx *c, int64_t t) {
+    const int S = c->S;
+    const unsigned tagL = (c->epoch << 2) | 1u, tagG = (c->epoch << 2) | 2u, tagW = (c->epoch << 2) | 3u;
+    const float *A = c->AT, *AP = c->APow;
+    const float *loc = c->local + (size_t)t * S;
+    const int anchor = t % 32 == 0 && t + 1 < c->n_tiles;
+    float P[64], v[64], tmp[64], h[64], g[64];
+    if (!anchor && t > 0) publish(c, t, 0, tagL, loc);
+    if (t == 0) {
+        memcpy(c->Z, c->z0, sizeof(float) * (size_t)S);
+        if (anchor) {
+            mv_add(S, A, c->z0, loc, tmp);
+            publish(c, 0, 1, tagG, tmp);
+        }
+        return 1;
+    }
+    const int64_t a = ((t - 1) / 32) * 32;
+    memset(P, 0, sizeof(float) * (size_t)S);
+    for (int64_t p = a + 1; p < t; ++p) {
+        if (!wait_slot(c, p, 0, tagL, v)) return 0;
+        mv_add(S, A, P, v, tmp);
+        memcpy(P, tmp, sizeof(float) * (size_t)S);
+    }
+    if (!anchor) {
+        if (!wait_slot(c, a, 1, tagG, g)) return 0;
+        mv_add(S, AP + (size_t)(t - 1 - a) * S * S, g, P, c->Z + (size_t)t * S);
+        return 1;
+    }
+    float W[64];
+    mv_add(S, A, P, loc, W);
+    publish(c, t, 0, tagW, W);
+    const int64_t s0 = ((t - 1) / 128) * 128;
+    if (!wait_slot(c, s0, 1, tagG, h)) return 0;
+    for (int64_t b = s0 + 32; b < t; b += 32) {
+        if (!wait_slot(c, b, 0, tagW, v)) return 0;
+        mv_add(S, AP + (size_t)32 * S * S, h, v, tmp);
+        memcpy(h, tmp, sizeof(float) * (size_t)S);
+    }
+    mv_add(S, AP + (size_t)32 * S * S, h, W, tmp);
+    publish(c, t, 1, tagG, tmp);
+    mv_add(S, AP + (size_t)31 * S * S, h, P, c->Z + (size_t)t * S);
+    return 1;
+}
+
 static void *emu_worker(void *arg) {
     emu_ctx *c = (emu_ctx *)arg;
     const int S = c->S;
@@ -97,6 +151,13 @@ static void *emu_worker(void *arg) {
         const int64_t t = atomic_fetch_add(&c->ticket, 1);
         if (t >= c->n_tiles || atomic_load(&c->status)) break;
         if (t == c->silent) continue;  /* this tile's worker "dies" before publishing anything */
+        if (c->APow) {
+            if (!hier_tile(c, t)) {
+                atomic_store(&c->status, 1);
+                break;
+            }
+            continue;
+        }
         const int sig = c->tile_sig[t];
         const int64_t t0 = c->tile0[sig];
         const float *A = c->AT + (size_t)sig * S * S;
@@ -130,9 +191,9 @@ static void *emu_worker(void *arg) {
 
 /* One launch of the batched protocol over `desc` (kept by the caller between launches: its old
  * tags must not be mistaken for this epoch's).  Returns 0, or 1 when some wait ran out. */
-int emu_run_batch(int S, int64_t n_tiles, unsigned epoch, uint64_t *desc, const float *local, const float *AT,
-                  const float *z0, const int *tile_sig, const int64_t *tile0, float *Z, int threads,
-                  int64_t spin_limit, int64_t silent) {
+static int emu_launch(int S, int64_t n_tiles, unsigned epoch, uint64_t *desc, const float *local, const float *AT,
+                      const float *APow, const float *z0, const int *tile_sig, const int64_t *tile0, float *Z,
+                      int threads, int64_t spin_limit, int64_t silent) {
     if (S < 1 || S > 64 || n_tiles < 0 || threads < 1 || threads > 64) return -1;
     emu_ctx c;
     memset(&c, 0, sizeof c);
@@ -142,6 +203,7 @@ int emu_run_batch(int S, int64_t n_tiles, unsigned epoch, uint64_t *desc, const 
     c.desc = (_Atomic uint64_t *)desc;
     c.local = local;
     c.AT = AT;
+    c.APow = APow;
     c.z0 = z0;
     c.tile_sig = tile_sig;
     c.tile0 = tile0;
@@ -157,6 +219,64 @@ int emu_run_batch(int S, int64_t n_tiles, unsigned epoch, uint64_t *desc, const 
     emu_worker(&c);
     for (int i = 0; i < made; ++i) pthread_join(tid[i], NULL);
     return atomic_load(&c.status);
+}
+
+int emu_run_batch(int S, int64_t n_tiles, unsigned epoch, uint64_t *desc, const float *local, const float *AT,
+                  const float *z0, const int *tile_sig, const int64_t *tile0, float *Z, int threads,
+                  int64_t spin_limit, int64_t silent) {
+    return emu_launch(S, n_tiles, epoch, desc, local, AT, NULL, z0, tile_sig, tile0, Z, threads, spin_limit, silent);
+}
+
+/* One signal, hierarchical protocol (APow: A^k, k = 0 .. 32). */
+int emu_run_hier(int S, int64_t n_tiles, unsigned epoch, uint64_t *desc, const float *local, const float *AT,
+                 const float *APow, const float *z0, float *Z, int threads, int64_t spin_limit, int64_t silent) {
+    if (n_tiles < 0 || !APow) return -1;
+    int *ts = (int *)calloc((size_t)(n_tiles > 0 ? n_tiles : 1), sizeof(int));
+    if (!ts) return -1;
+    const int64_t t0 = 0;
+    const int rc = emu_launch(S, n_tiles, epoch, desc, local, AT, APow, z0, ts, &t0, Z, threads, spin_limit, silent);
+    free(ts);
+    return rc;
+}
+
+/* The hierarchical composition, tile after tile on one thread (the same operations in the same
+ * order as hier_tile). */
+void emu_reference_hier(int S, int64_t n_tiles, const float *local, const float *A, const float *AP, const float *z0,
+                        float *Z) {
+    float *Wv = (float *)calloc((size_t)S * (size_t)(n_tiles > 0 ? n_tiles : 1), sizeof(float));
+    float *Gv = (float *)calloc((size_t)S * (size_t)(n_tiles > 0 ? n_tiles : 1), sizeof(float));
+    float P[64], tmp[64], h[64];
+    for (int64_t t = 0; t < n_tiles; ++t) {
+        const float *loc = local + (size_t)t * S;
+        const int anchor = t % 32 == 0 && t + 1 < n_tiles;
+        if (t == 0) {
+            memcpy(Z, z0, sizeof(float) * (size_t)S);
+            if (anchor) mv_add(S, A, z0, loc, Gv);
+            continue;
+        }
+        const int64_t a = ((t - 1) / 32) * 32;
+        memset(P, 0, sizeof(float) * (size_t)S);
+        for (int64_t p = a + 1; p < t; ++p) {
+            mv_add(S, A, P, local + (size_t)p * S, tmp);
+            memcpy(P, tmp, sizeof(float) * (size_t)S);
+        }
+        if (!anchor) {
+            mv_add(S, AP + (size_t)(t - 1 - a) * S * S, Gv + (size_t)a * S, P, Z + (size_t)t * S);
+            continue;
+        }
+        float *W = Wv + (size_t)t * S;
+        mv_add(S, A, P, loc, W);
+        const int64_t s0 = ((t - 1) / 128) * 128;
+        memcpy(h, Gv + (size_t)s0 * S, sizeof(float) * (size_t)S);
+        for (int64_t b = s0 + 32; b < t; b += 32) {
+            mv_add(S, AP + (size_t)32 * S * S, h, Wv + (size_t)b * S, tmp);
+            memcpy(h, tmp, sizeof(float) * (size_t)S);
+        }
+        mv_add(S, AP + (size_t)32 * S * S, h, W, Gv + (size_t)t * S);
+        mv_add(S, AP + (size_t)31 * S * S, h, P, Z + (size_t)t * S);
+    }
+    free(Wv);
+    free(Gv);
 }
 
 /* One signal: every tile maps to signal 0, whose first tile is 0. */

@@ -85,6 +85,35 @@ def test_batch_mixed_orders_lengths_states(dev):
         f.close()
 
 
+def test_batch_final_states_of_many_short_signals(dev):
+    """Hundreds of signals of one to seven groups: almost every tile holds some signal's last group,
+    owned by varying warps, so consecutive tiles of the same slot capture final states in different
+    warps; each signal's final state must match the oracle (repeated launches)."""
+    from paper_2607_23763_gb300 import SosFilter, run_batch, batch_sync_status
+    rng = np.random.default_rng(31)
+    sos = designs.butter_lowpass(4, 0.1)
+    K = sos.shape[0]
+    f = SosFilter(sos)
+    n_sig = 600
+    lengths = rng.integers(1, 7 * 2048 + 1, n_sig)
+    xs = [workloads.normal_f32(5000 + i, int(n)) for i, n in enumerate(lengths)]
+    zis = [rng.standard_normal((K, 2)) * 0.1 for _ in range(n_sig)]
+    xd = [torch.from_numpy(x).to(dev) for x in xs]
+    zid = [torch.from_numpy(z.astype(np.float32)).to(dev) for z in zis]
+    refs = [oracle.sosfilt(sos, x, zi=z.astype(np.float32).astype(np.float64), return_state=True)
+            for x, z in zip(xs, zis)]
+    for rep in range(3):
+        ys = [torch.empty_like(x) for x in xd]
+        zfs = [torch.full((K, 2), float("nan"), device=dev) for _ in range(n_sig)]
+        run_batch([f] * n_sig, xd, ys, zis=zid, zfs=zfs)
+        torch.cuda.synchronize()
+        assert batch_sync_status(0) == 0
+        for i, ((y_ref, zf_ref), y, zf) in enumerate(zip(refs, ys, zfs)):
+            assert _rel(y.cpu().numpy(), y_ref) < 1e-4, (rep, i)
+            assert _zerr(zf.cpu().numpy(), zf_ref) < 1e-4, (rep, i, int(lengths[i]))
+    f.close()
+
+
 def test_batch_alone_equals_mix(dev):
     """Each signal filtered alone in a batch of its own and inside the mix gives the same output and
     final state bit for bit: the batch kernel composes every tile's incoming state from anchors

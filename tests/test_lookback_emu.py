@@ -5,7 +5,9 @@ each tile's incoming state from its anchor's resolved carry and the local carrie
 bounded spins, and publish resolved carries at anchors.  The tests check that any interleaving
 gives the single-thread result bit for bit, that stale tags of an earlier launch over the same
 descriptor memory are never taken, and that a tile which never publishes makes its successors'
-waits run out and return (no hang) with the status set.  The batched form shares one ticket queue
+waits run out and return (no hang) with the status set.  The single-signal kernels' hierarchical
+form (anchors every 32 tiles post their local part early, super-anchors every 128 tiles chain the
+resolved carries) is checked the same way, and against the plain composition in float64.  The batched form shares one ticket queue
 among the tiles of several signals, each signal with its own chain, anchors and transition, as the
 batch kernel does.
 """
@@ -36,6 +38,9 @@ def emu():
     lib.emu_run_batch.argtypes = [ctypes.c_int, i64, ctypes.c_uint, vp, vp, vp, vp, vp, vp, vp, ctypes.c_int, i64, i64]
     lib.emu_run_batch.restype = ctypes.c_int
     lib.emu_reference_batch.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp, vp]
+    lib.emu_run_hier.argtypes = [ctypes.c_int, i64, ctypes.c_uint, vp, vp, vp, vp, vp, vp, ctypes.c_int, i64, i64]
+    lib.emu_run_hier.restype = ctypes.c_int
+    lib.emu_reference_hier.argtypes = [ctypes.c_int, i64, vp, vp, vp, vp, vp]
     return lib
 
 
@@ -168,3 +173,66 @@ def test_batched_silent_tile_times_out_only_later_work(emu):
                            4, 2000, silent)
     assert rc == 1
     assert np.array_equal(Z[:silent], ref[:silent])  # the first signal and the silent tile's predecessors
+
+
+def _powers(A):
+    """A^k, k = 0 .. 32, float32 (from float64 products)."""
+    S = A.shape[0]
+    P = np.empty((33, S, S), dtype=np.float32)
+    M = np.eye(S)
+    for k in range(33):
+        P[k] = M
+        M = M @ A.astype(np.float64)
+    return np.ascontiguousarray(P)
+
+
+@pytest.mark.parametrize("S,n_tiles,threads", [(2, 1, 4), (4, 33, 3), (16, 300, 8), (6, 129, 1), (8, 520, 16),
+                                               (4, 128, 5), (4, 161, 6)])
+def test_hierarchical_any_interleaving_gives_the_serial_result(emu, S, n_tiles, threads):
+    A, local, z0 = _case(S, n_tiles, S * 100 + n_tiles)
+    AP = _powers(A)
+    ref = np.zeros((n_tiles, S), dtype=np.float32)
+    emu.emu_reference_hier(S, n_tiles, _p(local), _p(A), _p(AP), _p(z0), _p(ref))
+    desc = np.zeros(n_tiles * 2 * S, dtype=np.uint64)
+    for epoch in (1, 2, 3):
+        Z = np.full((n_tiles, S), np.nan, dtype=np.float32)
+        rc = emu.emu_run_hier(S, n_tiles, epoch, _p(desc), _p(local), _p(A), _p(AP), _p(z0), _p(Z), threads,
+                              1 << 22, -1)
+        assert rc == 0
+        assert np.array_equal(Z, ref)
+    # the composition is the recurrence Z(t + 1) = A Z(t) + L(t), up to float32 rounding
+    z = z0.astype(np.float64)
+    want = np.empty((n_tiles, S))
+    for t in range(n_tiles):
+        want[t] = z
+        z = A.astype(np.float64) @ z + local[t]
+    assert np.allclose(ref, want, rtol=1e-4, atol=1e-4 * np.abs(want).max())
+
+
+def test_hierarchical_stale_tags_are_not_taken(emu):
+    S, n_tiles = 8, 300
+    A, local, z0 = _case(S, n_tiles, 17)
+    AP = _powers(A)
+    desc = np.zeros(n_tiles * 2 * S, dtype=np.uint64)
+    other = (local * 3 + 1).astype(np.float32)
+    Z = np.zeros((n_tiles, S), dtype=np.float32)
+    assert emu.emu_run_hier(S, n_tiles, 5, _p(desc), _p(other), _p(A), _p(AP), _p(z0), _p(Z), 6, 1 << 22, -1) == 0
+    ref = np.zeros((n_tiles, S), dtype=np.float32)
+    emu.emu_reference_hier(S, n_tiles, _p(local), _p(A), _p(AP), _p(z0), _p(ref))
+    Z2 = np.zeros((n_tiles, S), dtype=np.float32)
+    assert emu.emu_run_hier(S, n_tiles, 6, _p(desc), _p(local), _p(A), _p(AP), _p(z0), _p(Z2), 6, 1 << 22, -1) == 0
+    assert np.array_equal(Z2, ref)
+
+
+@pytest.mark.parametrize("silent", [0, 5, 32, 128, 140])
+def test_hierarchical_silent_tile_times_out_its_successors(emu, silent):
+    S, n_tiles = 4, 300
+    A, local, z0 = _case(S, n_tiles, 19)
+    AP = _powers(A)
+    ref = np.zeros((n_tiles, S), dtype=np.float32)
+    emu.emu_reference_hier(S, n_tiles, _p(local), _p(A), _p(AP), _p(z0), _p(ref))
+    desc = np.zeros(n_tiles * 2 * S, dtype=np.uint64)
+    Z = np.full((n_tiles, S), np.nan, dtype=np.float32)
+    rc = emu.emu_run_hier(S, n_tiles, 1, _p(desc), _p(local), _p(A), _p(AP), _p(z0), _p(Z), 4, 2000, silent)
+    assert rc == 1
+    assert np.array_equal(Z[:silent], ref[:silent])
