@@ -42,8 +42,10 @@ CPU_SAMPLE = 1 << 24  # oracle sample per step of the reference arm
 # removed) whenever its kernel changes.
 SOLVER_CR, SOLVER_PH, SOLVER_DTCR, SOLVER_TC = 1, 2, 3, 4
 TRAFFIC_BYTES_2P28 = {
-    # sos_lane_kernel<8, 64, 1, 7> at 2^26 samples: 268,859,904 B read + 211,708,672 B written
+    # sos_lane_kernel<8, 64, 7> at 2^26 samples: 268,859,904 B read + 211,708,672 B written
     (SOLVER_PH, 64): 4 * (268859904 + 211708672),
+    # sos_tc_kernel<8> at 2^26 samples: 269,093,888 B read + 211,570,944 B written
+    (SOLVER_TC, 64): 4 * (269093888 + 211570944),
 }
 PH_GROUPS_PER_BLOCK = 7
 CR_GROUPS_PER_BLOCK = {32: 8, 64: 4}

@@ -330,6 +330,78 @@ struct CoordMats {
 constexpr long long kAnchor = 32;      // tiles between anchors
 constexpr long long kSuperAnchor = 4;  // anchors between super-anchors
 
+// The skewed-pass PH kernel's composition: decoupled lookback over tiles (Sec. IV-B, Eq. 25 on
+// the cascade state) for tile cur's incoming 2K-word state, its resolved carry when cur is an anchor
+// (the tiles at multiples of 32), and the incoming state of each of its W groups in z_buf[slot]
+// (Z_0 = Z, Z_{v+1} = A_C Z_v + a_v).  Fixed composition: the resolved carry of the last anchor before
+// cur and the local carries after it, so that outputs are reproducible bit for bit; the anchors form
+// a chain of one hop per 32 tiles.  (The tensor-core kernel, whose tiles are resolved with less work
+// around them, takes the hierarchical composition of coordinate_tile below.)
+template <int K, int W, int MS, int P2, int SH>
+__device__ __forceinline__ void coordinate_tile_plain(const LaneParams<K> &p, int lane, long long cur, unsigned slot,
+                                                      long long budget, const float *sATl, const float *sATd,
+                                                      const float *sACd, const float *a_buf, float *z_buf,
+                                                      const float *agg, unsigned long long *tr) {
+    constexpr int S = 2 * K;
+    const unsigned tagL = (p.epoch << 2) | 1u, tagG = (p.epoch << 2) | 2u;
+    auto zinit = [&](int i) -> float { return p.zi ? p.zi[i] * p.sec[i >> 1].zscale : 0.f; };
+    const float *abuf = a_buf + slot * W * S;
+    const float acc_i = agg[slot * S + (lane < S ? lane : 0)];
+    float tmp[S];
+    unsigned long long *dcur = p.desc + static_cast<size_t>(cur) * 2 * S + S;
+    float zi_lane = 0.f;
+    if (cur == 0) {
+        zi_lane = zinit(lane < S ? lane : 0);
+    } else {
+        const long long a = ((cur - 1) / 32) * 32;
+        const int ja = static_cast<int>(cur - 1 - a);  // the anchor's lane
+        const long long pred = cur - 1 - lane;
+        const long long t_start = clock64();
+        float v[S];
+        for (;;) {
+            bool ok = true;
+            if (lane <= ja) {
+                const unsigned want = lane == ja ? tagG : tagL;
+                const unsigned long long *dp = p.desc + static_cast<size_t>(pred) * 2 * S + (lane == ja ? S : 0);
+#pragma unroll
+                for (int q = 0; q < S; q += 2) {
+                    unsigned long long x0, x1;
+                    ld_relaxed_v2(dp + q, x0, x1);
+                    ok = ok && static_cast<unsigned>(x0 >> 32) == want && static_cast<unsigned>(x1 >> 32) == want;
+                    v[q] = __uint_as_float(static_cast<unsigned>(x0));
+                    v[q + 1] = __uint_as_float(static_cast<unsigned>(x1));
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < S; ++q) v[q] = 0.f;
+            }
+            if (__all_sync(0xffffffffu, ok)) break;
+            if (__any_sync(0xffffffffu, (clock64() - t_start) > budget)) {
+                if (lane == 0) atomicOr(p.status, kDevErrTimeout);
+                break;
+            }
+            __nanosleep(64);  // a short nap: the successors' lookbacks wait on this tile
+        }
+        // sum over the predecessors of (A_T)^k v_k: each lane applies its own power, then a
+        // reduce-scatter leaves word i of the sum in lane i
+        packed_mv<K>(sATl + lane * MS, v, tmp);
+        const float part = reduce_scatter<S, P2, SH>(tmp, lane);
+        zi_lane = __shfl_sync(0xffffffffu, part, (lane < S ? lane : 0) << SH);
+    }
+    if (tr) tr[2] = global_ns();
+    if ((cur & 31) == 0 && cur + 1 < p.n_tiles) {
+        // only anchor tiles' resolved carries are read: A_T Z + tile carry
+        const float gl = lane_mv<S>(sATd, zi_lane, lane) + acc_i;
+        if (lane < S) st_relaxed_b64(dcur + lane, pack_word(tagG, gl));
+    }
+    float *zb = z_buf + slot * W * S;
+#pragma unroll 1
+    for (int v = 0; v < W; ++v) {
+        if (lane < S) zb[v * S + lane] = zi_lane;
+        if (v + 1 < W) zi_lane = lane_mv<S>(sACd, zi_lane, lane) + abuf[v * S + (lane < S ? lane : 0)];
+    }
+}
+
 // Row `lane` (< 2K) of a packed lower block-triangular matrix times a vector held by every lane;
 // lanes >= 2K give 0.
 template <int K>
@@ -516,11 +588,7 @@ __global__ void __maxnreg__((LaneDims<K, N, W>::MAXREG)) sos_lane_kernel(const _
     float *z_buf = a_buf + 2 * W * S;                // [2][W][S] incoming states
     float *agg = z_buf + 2 * W * S;                  // [2][S] tile carry under zero incoming state
     float *zs_tail = agg + 2 * S;                    // [S] lane-local state after the last sample
-    float *pref = zs_tail + ((S + 3) / 4) * 4;       // [2][W][S] fold prefixes: carries of groups 0 .. v
     const float *sATd = tab + Dm::SM_AC + (Dm::OFF_AT - Dm::OFF_AC);    // A_T dense column-major
-    const CoordMats mats{sATd, tab + Dm::SM_AC + (Dm::OFF_AT32 - Dm::OFF_AC),
-                         tab + Dm::SM_AC + (Dm::OFF_AT31 - Dm::OFF_AC),
-                         p.tab + Dm::OFF_ACP};  // dense powers of A_T (shared) and of A_C (global)
     // tiles alternate between two slots; the incoming-state barrier has one per slot, so that it
     // never runs two phases ahead of a waiter
     __shared__ unsigned long long bar_local[2], bar_zready[2], bar_ticket[8];
@@ -585,7 +653,8 @@ __global__ void __maxnreg__((LaneDims<K, N, W>::MAXREG)) sos_lane_kernel(const _
                 tr[1] = global_ns();
                 tr[13] = smid;
             }
-            coordinate_tile<K, W, MS, Dm::P2, Dm::SH>(p, lane, cur, slot, budget, sATl, mats, pref, z_buf, agg, tr);
+            coordinate_tile_plain<K, W, MS, Dm::P2, Dm::SH>(p, lane, cur, slot, budget, sATl, sATd, sACd, a_buf, z_buf,
+                                                            agg, tr);
             __syncwarp();
             if (lane == 0) mbar_arrive(&bar_zready[slot]);
             if (tr) tr[3] = global_ns();
@@ -776,10 +845,7 @@ __global__ void __maxnreg__((LaneDims<K, N, W>::MAXREG)) sos_lane_kernel(const _
                 const int li = lane < S ? lane : 0;
                 float c = abt[li];
 #pragma unroll 1
-                for (int v = 1; v < W; ++v) {
-                    if (lane < S) pref[(slot * W + v - 1) * S + lane] = c;
-                    c = lane_mv<S>(sACd, c, lane) + abt[v * S + li];
-                }
+                for (int v = 1; v < W; ++v) c = lane_mv<S>(sACd, c, lane) + abt[v * S + li];
                 if (tile % kAnchor != 0 && lane < S)  // an anchor's local carry is never read
                     st_relaxed_b64(p.desc + static_cast<size_t>(tile) * 2 * S + lane, pack_word((p.epoch << 2) | 1u, c));
                 if (lane < S) agg[slot * S + lane] = c;
@@ -811,7 +877,7 @@ template <int K, int N, int W>
 constexpr size_t lane_smem_bytes() {
     using Dm = LaneDims<K, N, W>;
     return sizeof(float) * (static_cast<size_t>(W) * 2 * kL * (N + 4) + Dm::SM_TAB + W * kL * Dm::RSP +
-                            6 * W * Dm::S + 2 * Dm::S + ((Dm::S + 3) / 4) * 4);
+                            4 * W * Dm::S + 2 * Dm::S + ((Dm::S + 3) / 4) * 4);
 }
 
 }  // namespace sosk

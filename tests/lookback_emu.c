@@ -1,5 +1,5 @@
 /*
- * Host-thread emulation of the lookback protocol of the PH kernels (a test aid; it shares no code
+ * Host-thread emulation of the lookback protocols of the PH kernels (a test aid; it shares no code
  * with the CUDA library).  Tiles are drawn from an ascending ticket counter by T worker threads
  * (Sec. IV-A).  Tile t publishes its local carry in slot 0 of its descriptor, tagged words of
  * (epoch << 2 | 1, float bits); it then composes its incoming state from the resolved carry of its
@@ -12,7 +12,8 @@
  * the same order as emu_reference(), so a correct protocol gives bit-identical results whatever
  * the interleaving of the threads.
  *
- * The single-signal form (emu_run_hier) is the single-signal kernels': every tile first sums the
+ * emu_run is the skewed-pass PH kernel's protocol.  The hierarchical form (emu_run_hier) is the
+ * tensor-core kernel's: every tile first sums the
  * local carries after its anchor, P = sum_k A^(k-1) L(t - k) (Horner from zero); a tile between
  * anchors then waits for G(a) and takes Z = A^(t-1-a) G(a) + P; an anchor t publishes its local part
  * W = A P + L(t) in its slot 0 (tag epoch << 2 | 3), waits for the resolved carry of the

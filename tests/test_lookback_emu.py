@@ -5,9 +5,9 @@ each tile's incoming state from its anchor's resolved carry and the local carrie
 bounded spins, and publish resolved carries at anchors.  The tests check that any interleaving
 gives the single-thread result bit for bit, that stale tags of an earlier launch over the same
 descriptor memory are never taken, and that a tile which never publishes makes its successors'
-waits run out and return (no hang) with the status set.  The single-signal kernels' hierarchical
+waits run out and return (no hang) with the status set.  The tensor-core kernel's hierarchical
 form (anchors every 32 tiles post their local part early, super-anchors every 128 tiles chain the
-resolved carries) is checked the same way, and against the plain composition in float64.  The batched form shares one ticket queue
+resolved carries) is checked the same way, and against the recurrence in float64.  The batched form shares one ticket queue
 among the tiles of several signals, each signal with its own chain, anchors and transition, as the
 batch kernel does.
 """
