@@ -1134,6 +1134,7 @@ constexpr int kBatchClasses = 16;  // (K, normalized) classes: K = 1..8, b0-norm
 // Scratch of one batch in flight: signal descriptors and the tile -> signal map (one upload from
 // pinned staging), lookback descriptors and ticket counters of its class launches.
 struct BatchSlot {
+    std::mutex mu;  // held by the call using the slot: its staging, capacities and event
     unsigned char *d_up = nullptr, *h_up = nullptr;  // [descriptors][tile -> signal map]
     size_t up_cap = 0;
     unsigned long long *d_desc = nullptr;
@@ -1278,7 +1279,6 @@ sos_status run_batch_impl(int n_signals, sos_filter *const *filters, const float
     if (cudaSetDevice(device) != cudaSuccess) return SOS_ECUDA;
     BatchCtx *ctx = batch_ctx(device);
     if (!ctx) return SOS_ENOMEM;
-    std::lock_guard<std::mutex> lk(ctx->mu);
 
     for (int i = 0; any_other && i < n_signals; ++i) {
         sos_filter *f = filters[i];
@@ -1306,9 +1306,31 @@ sos_status run_batch_impl(int n_signals, sos_filter *const *filters, const float
     }
     if (sig_off[kBatchClasses] == 0) return SOS_OK;
 
-    // a free scratch slot (its previous batch has completed on the device)
-    BatchSlot &sl = ctx->slot[ctx->next];
-    ctx->next = (ctx->next + 1) % kBatchSlots;
+    // a scratch slot and the launch's epoch under the context's lock; the slot's own lock then covers
+    // its use, so that calls from several threads plan and launch on different slots at once
+    BatchSlot *slp = nullptr;
+    unsigned epoch = 0;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        slp = &ctx->slot[ctx->next];
+        ctx->next = (ctx->next + 1) % kBatchSlots;
+        ctx->epoch = (ctx->epoch + 1) & 0x3fffffffu;
+        if (ctx->epoch == 0) {
+            // wrapped (once in 2^30 calls): clear stale tags of every slot's descriptors, with every
+            // slot held and the device idle
+            std::unique_lock<std::mutex> held[kBatchSlots];
+            for (int k = 0; k < kBatchSlots; ++k) held[k] = std::unique_lock<std::mutex>(ctx->slot[k].mu);
+            if (cudaDeviceSynchronize() != cudaSuccess) return SOS_ECUDA;
+            for (auto &o : ctx->slot)
+                if (o.d_desc && cudaMemset(o.d_desc, 0, o.desc_cap * sizeof(unsigned long long)) != cudaSuccess)
+                    return SOS_ECUDA;
+            ctx->epoch = 1;
+        }
+        epoch = ctx->epoch;
+    }
+    BatchSlot &sl = *slp;
+    std::lock_guard<std::mutex> slk(sl.mu);
+    // the slot is free once its previous batch has completed on the device
     if (sl.pending && cudaEventSynchronize(sl.done) != cudaSuccess) return SOS_ECUDA;
     sl.pending = false;
     const size_t sig_bytes = sizeof(sosk::BatchSig) * sig_off[kBatchClasses];
@@ -1381,19 +1403,11 @@ sos_status run_batch_impl(int n_signals, sos_filter *const *filters, const float
         cudaMemsetAsync(sl.d_ticket, 0, sizeof(unsigned long long) * kBatchClasses, s) != cudaSuccess)
         return SOS_ECUDA;
 
-    // one persistent launch per class, each on its own stream forked from and joined into s (a
-    // single class runs on s itself)
     // one persistent launch over every class (sos_batch_all_kernel)
-    ctx->epoch = (ctx->epoch + 1) & 0x3fffffffu;
-    if (ctx->epoch == 0) {  // wrapped: clear stale tags of every slot's descriptors
-        for (auto &o : ctx->slot)
-            if (o.d_desc) cudaMemsetAsync(o.d_desc, 0, o.desc_cap * sizeof(unsigned long long), s);
-        ctx->epoch = 1;
-    }
     sosk::BatchAllParams ap;
     long long grid = 0;
     sos_status pst = batch_all_params(cls_sigs, cls_tiles, sig_off, tile_off, desc_off, d_sigs, d_tile_sig, sl.d_desc,
-                                      sl.d_ticket, ctx->epoch, ctx->d_status, device, ap, grid);
+                                      sl.d_ticket, epoch, ctx->d_status, device, ap, grid);
     if (pst != SOS_OK) return pst;
     if (sosk::launch_batch_all(ap, grid, s) != cudaSuccess) return SOS_ECUDA;
     if (cudaEventRecord(sl.done, s) != cudaSuccess) return SOS_ECUDA;

@@ -6,9 +6,11 @@
 // admitted, so chunk i + 1 continues from chunk i's final state without a host round trip.
 // Requests name caller-owned device buffers.  A scheduler thread admits the oldest ready chunks
 // (streams with a queued chunk and none in flight) while the bytes in flight stay inside the
-// memory budget; a launcher thread issues each admitted batch through sos_filter_run_batch_ex on
-// one of a few CUDA streams, so that several batches overlap on the device and admission overlaps
-// with issuing; completions come from a host function enqueued behind every batch.  New requests are admitted as soon as budget and batch slots free up.
+// memory budget; two launcher threads issue the admitted batches through sos_filter_run_batch_ex on
+// a few CUDA streams, so that several batches overlap on the device and admission, planning and
+// issuing overlap; a host function behind every batch hands it to a completion thread, which
+// releases its streams and budget.  New requests are admitted as soon as budget and batch slots
+// free up.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -76,10 +78,16 @@ struct sos_server {
     int next_cs = 0;
     bool stop = false;
     int sticky = SOS_OK;            // first error of a batch launch
-    std::deque<Batch *> to_launch;  // admitted batches, in admission order, for the launcher thread
+    std::deque<Batch *> to_launch;  // admitted batches, in admission order, for the launcher threads
     std::condition_variable cv_launch;
-    bool sched_done = false;        // the scheduler has exited; the launcher drains and exits
-    std::thread sched, launcher;
+    bool sched_done = false;        // the scheduler has exited; the launchers drain and exit
+    // batches whose device work has finished, for the completion thread (their own lock: the CUDA
+    // host function behind a batch only hands it over)
+    std::mutex mu_fin;
+    std::condition_variable cv_fin;
+    std::deque<Batch *> finished;
+    bool fin_stop = false;
+    std::thread sched, launchers[2], completer;
 };
 
 namespace {
@@ -88,15 +96,16 @@ struct Batch {
     sos_server *srv = nullptr;
     std::vector<Req> reqs;
     int64_t bytes = 0;
+    double t_done = 0;  // when its device work finished
 };
 
 int64_t req_bytes(const Req &r) { return (r.x == r.y ? 4 : 8) * r.n; }
 
-// Host function behind a batch on its CUDA stream: completion bookkeeping only (no CUDA calls).
-void CUDART_CB batch_done(void *arg) {
-    Batch *b = static_cast<Batch *>(arg);
+// Completion bookkeeping of a batch whose device work has finished (no CUDA calls): records for the
+// pollers, the streams' next chunks made ready, the budget released.
+void complete_batch(Batch *b) {
     sos_server *s = b->srv;
-    const double t = now_s();
+    const double t = b->t_done;
     // the completion records are built before the lock is taken; under it, one append and the
     // streams' bookkeeping
     std::vector<sos_completion> recs(b->reqs.size());
@@ -124,6 +133,33 @@ void CUDART_CB batch_done(void *arg) {
     s->cv.notify_all();
     s->cv_done.notify_all();
     delete b;
+}
+
+// Host function behind a batch on its CUDA stream: it stamps the completion time and hands the
+// batch to the completion thread, so that the CUDA stream's next batch does not wait on the
+// bookkeeping.
+void CUDART_CB batch_done(void *arg) {
+    Batch *b = static_cast<Batch *>(arg);
+    sos_server *s = b->srv;
+    b->t_done = now_s();
+    {
+        std::lock_guard<std::mutex> lk(s->mu_fin);
+        s->finished.push_back(b);
+    }
+    s->cv_fin.notify_one();
+}
+
+void completer(sos_server *s) {
+    std::unique_lock<std::mutex> lk(s->mu_fin);
+    for (;;) {
+        s->cv_fin.wait(lk, [&] { return !s->finished.empty() || s->fin_stop; });
+        if (s->finished.empty()) break;  // stopping, and every batch has been completed
+        Batch *b = s->finished.front();
+        s->finished.pop_front();
+        lk.unlock();
+        complete_batch(b);
+        lk.lock();
+    }
 }
 
 // Admission: the oldest ready chunks while the budget allows, with each chunk's filter and state
@@ -175,12 +211,13 @@ void scheduler(sos_server *s) {
         s->cv_launch.notify_one();
     }
     s->sched_done = true;
-    s->cv_launch.notify_one();
+    s->cv_launch.notify_all();
 }
 
-// Issue: one batched run per admitted batch, in admission order, on the next of the server's CUDA
-// streams, with a host function behind it for the completions.  The streams of a batch's requests
-// are busy, so nobody else touches their state copies meanwhile.
+// Issue: one batched run per admitted batch, on the next of the server's CUDA streams, with a host
+// function behind it for the completions.  Two launcher threads take batches in admission order and
+// plan them at the same time (the library's batched runs plan concurrently on separate scratch);
+// the streams of a batch's requests are busy, so nobody else touches their state copies meanwhile.
 void launcher(sos_server *s) {
     if (cudaSetDevice(s->device) != cudaSuccess) return;
     std::vector<sos_filter *> fs;
@@ -260,21 +297,33 @@ sos_status sos_server_create(const sos_server_config *cfg, sos_server **out) {
             delete s;
             return SOS_ECUDA;
         }
+    auto stop_threads = [s] {
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->sched_done = true;
+        }
+        s->cv_launch.notify_all();
+        for (auto &l : s->launchers)
+            if (l.joinable()) l.join();
+        {
+            std::lock_guard<std::mutex> lk(s->mu_fin);
+            s->fin_stop = true;
+        }
+        s->cv_fin.notify_all();
+        if (s->completer.joinable()) s->completer.join();
+    };
     try {
-        s->launcher = std::thread(launcher, s);
+        s->completer = std::thread(completer, s);
+        for (auto &l : s->launchers) l = std::thread(launcher, s);
     } catch (...) {
+        stop_threads();
         delete s;
         return SOS_ENOMEM;
     }
     try {
         s->sched = std::thread(scheduler, s);
     } catch (...) {
-        {
-            std::lock_guard<std::mutex> lk(s->mu);
-            s->sched_done = true;
-        }
-        s->cv_launch.notify_one();
-        s->launcher.join();
+        stop_threads();
         delete s;
         return SOS_ENOMEM;
     }
@@ -289,8 +338,15 @@ sos_status sos_server_destroy(sos_server *s) {
         s->stop = true;
     }
     s->cv.notify_all();
-    if (s->sched.joinable()) s->sched.join();
-    if (s->launcher.joinable()) s->launcher.join();
+    if (s->sched.joinable()) s->sched.join();  // after every queued request has completed
+    for (auto &l : s->launchers)
+        if (l.joinable()) l.join();
+    {
+        std::lock_guard<std::mutex> lk(s->mu_fin);
+        s->fin_stop = true;
+    }
+    s->cv_fin.notify_all();
+    if (s->completer.joinable()) s->completer.join();
     cudaSetDevice(s->device);
     for (auto &c : s->cstreams) cudaStreamSynchronize(c);
     // the filters before the CUDA streams their last batches ran on
