@@ -367,7 +367,7 @@ typedef struct sos_server sos_server;
 typedef struct {
     int64_t budget_bytes; /* device bytes of chunks in flight; 0 = 16 GiB */
     int max_batch;        /* chunks per batch; 0 = 4096 */
-    int max_inflight;     /* batches in flight on the device (1..4); 0 = 3 */
+    int max_inflight;     /* batches in flight on the device (1..8); 0 = 4 */
 } sos_server_config;
 
 typedef struct {

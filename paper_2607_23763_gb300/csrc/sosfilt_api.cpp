@@ -1128,7 +1128,7 @@ sos_status run_impl(sos_filter *f, const float *x, float *y, int64_t n, const fl
 }
 
 // ---- multi-signal runs (sosfilt_batch.cuh)
-constexpr int kBatchSlots = 4;     // batches whose scratch may be in use on the device at once
+constexpr int kBatchSlots = 8;     // batches whose scratch may be in use on the device at once
 constexpr int kBatchClasses = 16;  // (K, normalized) classes: K = 1..8, b0-normalized or not
 
 // Scratch of one batch in flight: signal descriptors and the tile -> signal map (one upload from

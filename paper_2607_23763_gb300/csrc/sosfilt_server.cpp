@@ -101,6 +101,8 @@ struct Batch {
 
 int64_t req_bytes(const Req &r) { return (r.x == r.y ? 4 : 8) * r.n; }
 
+constexpr double kFillWait = 200e-6;  // seconds a small batch may wait to fill while the device is busy
+
 // Completion bookkeeping of a batch whose device work has finished (no CUDA calls): records for the
 // pollers, the streams' next chunks made ready, the budget released.
 void complete_batch(Batch *b) {
@@ -167,10 +169,20 @@ void completer(sos_server *s) {
 // launcher thread, so that admitting the next batch overlaps with issuing this one.
 void scheduler(sos_server *s) {
     std::unique_lock<std::mutex> lk(s->mu);
+    double fill_since = 0;  // when a small batch started waiting to fill
     for (;;) {
         if (s->stop && s->queued == 0) break;
         Batch *b = nullptr;
-        if (s->inflight_batches < s->cfg.max_inflight && !s->ready.empty()) {
+        // while two or more batches keep the device busy, a batch waits up to kFillWait to gather a
+        // quarter of the largest batch: fewer, larger batches cost less per chunk on the host
+        bool fill = false;
+        if (s->inflight_batches >= 2 && static_cast<int64_t>(s->ready.size()) < s->cfg.max_batch / 4 && !s->stop) {
+            const double t = now_s();
+            if (fill_since == 0) fill_since = t;
+            fill = t - fill_since < kFillWait;
+        }
+        if (!fill && s->inflight_batches < s->cfg.max_inflight && !s->ready.empty()) {
+            fill_since = 0;
             b = new (std::nothrow) Batch();
             if (b) {
                 b->srv = s;
@@ -204,7 +216,10 @@ void scheduler(sos_server *s) {
             }
         }
         if (!b) {
-            s->cv.wait_for(lk, std::chrono::milliseconds(2));
+            if (fill)
+                s->cv.wait_for(lk, std::chrono::microseconds(50));
+            else
+                s->cv.wait_for(lk, std::chrono::milliseconds(2));
             continue;
         }
         s->to_launch.push_back(b);
@@ -285,8 +300,8 @@ sos_status sos_server_create(const sos_server_config *cfg, sos_server **out) {
     if (cfg) s->cfg = *cfg;
     if (s->cfg.budget_bytes <= 0) s->cfg.budget_bytes = 16LL << 30;
     if (s->cfg.max_batch <= 0) s->cfg.max_batch = 4096;
-    if (s->cfg.max_inflight <= 0) s->cfg.max_inflight = 3;
-    if (s->cfg.max_inflight > 4) s->cfg.max_inflight = 4;  // the library keeps four batch scratch sets
+    if (s->cfg.max_inflight <= 0) s->cfg.max_inflight = 4;
+    if (s->cfg.max_inflight > 8) s->cfg.max_inflight = 8;  // the library keeps eight batch scratch sets
     if (cudaGetDevice(&s->device) != cudaSuccess) {
         delete s;
         return SOS_ECUDA;
