@@ -592,10 +592,11 @@ def bench_ours(args):
         _leg("config1_2p20", config1_leg, line, torch, dev)
         torch.cuda.empty_cache()
         plain = {}
-        _leg("batched", batched_leg, line, torch, dev, steps=5, warmup=3, no_cpu=args.no_cpu, plain=plain)
+        _leg("batched", batched_leg, line, torch, dev, steps=5, warmup=3, no_cpu=args.no_cpu, plain=plain,
+             autotune=not args.no_autotune)
         torch.cuda.empty_cache()
         _leg("serving", serving_leg, line, torch, dev, n_streams=args.streams, per_stream=2,
-             n_open=args.serving_open_requests, plain=plain)
+             n_open=args.serving_open_requests, plain=plain, autotune=not args.no_autotune)
     line["wall_s"] = round(time.perf_counter() - t_start, 1)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -642,15 +643,21 @@ def plain_rates_by_sections(torch, dev, plain: dict, steps: int = 5, warmup: int
     return plain
 
 
-def batched_leg(torch, dev, steps: int = 5, warmup: int = 3, no_cpu: bool = False, plain=None):
+def batched_leg(torch, dev, steps: int = 5, warmup: int = 3, no_cpu: bool = False, plain=None,
+                autotune: bool = True):
     """Batched mix: 4096 signals (orders 2/4/8/16, lengths 2^10..2^22) in one sos_filter_run_batch call
     per step; GS/s of the whole batch, the same batch as a prepared plan replayed from a CUDA graph,
-    and both as a fraction of the plain kernel's time for the same signals at each signal's order."""
+    and both as a fraction of the plain kernel's time for the same signals at each signal's order.
+    With `autotune`, the batch autotuner first picks each signal's tile geometry (N = 64 or 32 samples
+    per lane) by section count and length (outside the timed region)."""
     import workloads
-    from paper_2607_23763_gb300 import SosFilter, run_batch, batch_sync_status, BatchPlan
+    from paper_2607_23763_gb300 import (SosFilter, run_batch, batch_sync_status, BatchPlan, autotune_batch,
+                                        autotune_batch_choice)
 
     n_sig = 4096
     specs = [workloads.batched_signal(i) for i in range(n_sig)]
+    tune_gss = autotune_batch() if autotune else None
+    geom = [autotune_batch_choice(sos.shape[0], n) or 64 for sos, n, _ in specs]
     fs = [SosFilter(sos) for sos, _, _ in specs]
     xs, xs_host = [], []  # host copies kept only for the CPU leg's sample
     for i, (_, n, seed) in enumerate(specs):
@@ -695,7 +702,14 @@ def batched_leg(torch, dev, steps: int = 5, warmup: int = 3, no_cpu: bool = Fals
            "cuda_graph": {"value": total / graph_ms / 1e6, "ms_per_step": graph_ms,
                           "vs_plain_kernel": plain_ms / graph_ms},
            "plain_gss_by_order": {str(2 * k): v for k, v in rate.items()},
-           "target_vs_plain": 0.60, "clocks": clk.summary()}
+           "target_vs_plain": 0.60, "clocks": clk.summary(),
+           "tile_geometry": {
+               "autotuned": tune_gss is not None, "L": 32, "groups_per_tile": 7,
+               "signals_N32": sum(g == 32 for g in geom),
+               "samples_N32": sum(n for (_, n, _), g in zip(specs, geom) if g == 32),
+               "autotune_gss": None if tune_gss is None else {
+                   "layout": "[sections 1..8][signal length 2^12, 2^15, 2^18, 2^21][N = 64, N = 32]",
+                   "value": np.round(tune_gss, 1).tolist()}}}
     if not no_cpu:
         out["cpu_baseline"], out["accuracy"] = batch_sample_leg(specs, xs_host, ys)
     for f in fs:
@@ -706,25 +720,29 @@ def batched_leg(torch, dev, steps: int = 5, warmup: int = 3, no_cpu: bool = Fals
 def bench_batched(args):
     import torch
     torch.cuda.set_device(0)
-    leg = batched_leg(torch, torch.device("cuda", 0), args.steps, args.warmup, args.no_cpu)
+    leg = batched_leg(torch, torch.device("cuda", 0), args.steps, args.warmup, args.no_cpu,
+                      autotune=not args.no_autotune)
     line = {"metric": "GS/s", "value": leg["value"], "unit": "GS/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": leg["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": leg["workload"], "samples": leg["samples"], "l2": leg["l2"]},
-            "gpu_launches": 4 * args.steps}
+            "gpu_launches": args.steps}
     line.update({k: v for k, v in leg.items() if k not in line and k not in ("workload", "samples", "l2")})
     print(json.dumps(line), flush=True)
 
 
-def serving_leg(torch, dev, n_streams: int = 10000, per_stream: int = 10, n_open: int = 110000, plain=None):
+def serving_leg(torch, dev, n_streams: int = 10000, per_stream: int = 10, n_open: int = 110000, plain=None,
+                autotune: bool = True):
     """Serving mix: streams with orders 2/4/8/16 at 40/30/20/10 %, chunks of U[4096, 65536] samples.
     Capacity = closed loop (every chunk queued at t = 0); then Poisson arrivals at 80 % of capacity;
     latency = completion - scheduled arrival; p50/p99 over the requests after a 10 % warm-up.  The
     capacity is also given as a fraction of the plain kernel's rate for the same chunks (each chunk
     at the plain 2^28-sample rate of its order)."""
     import workloads
-    from paper_2607_23763_gb300 import SosServer
+    from paper_2607_23763_gb300 import SosServer, autotune_batch, autotune_batch_choice
 
+    if autotune and autotune_batch_choice(1, 1 << 15) == 0:
+        autotune_batch()  # each chunk's tile geometry by order and length (outside the timed region)
     srv = SosServer(budget_bytes=16 << 30)
     t0 = time.perf_counter()
     soss = [workloads.serving_stream(s) for s in range(n_streams)]
@@ -819,7 +837,8 @@ def serving_batch_probe(torch, dev, soss, pool, m: int = 4096, reps: int = 3):
 def bench_serving(args):
     import torch
     torch.cuda.set_device(0)
-    leg = serving_leg(torch, torch.device("cuda", 0), args.streams, args.chunks_per_stream, args.open_requests, {})
+    leg = serving_leg(torch, torch.device("cuda", 0), args.streams, args.chunks_per_stream, args.open_requests, {},
+                      autotune=not args.no_autotune)
     line = {"metric": "GS/s", "value": leg["value"], "unit": "GS/s", "n_gpus": 1, "steps": 1, "warmup": 0,
             "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",

@@ -205,12 +205,16 @@ sos_status sos_filter_run_host(sos_filter *f, const float *x_host, float *y_host
 
 /*
  * Filter many independent signals of uneven length and order in one persistent
- * kernel launch on `stream`: the signals with the same section count (and the
- * same b0 handling) form a class with its own global queue of (signal, tile)
- * work items, tiles of 7 groups of 2048 samples, with the lookback chains of
- * Sec. IV-B kept per signal (a chain ends at its signal's first tile); each
- * thread block starts on a class in proportion to the classes' work and then
- * takes every other class that still has tiles.  Zero initial state for every
+ * kernel launch on `stream`: the signals with the same section count, the same
+ * b0 handling and the same tile geometry form a class with its own global
+ * queue of (signal, tile) work items, with the lookback chains of Sec. IV-B
+ * kept per signal (a chain ends at its signal's first tile); each thread block
+ * starts on a class in proportion to the classes' work and then takes every
+ * other class that still has tiles.  Tile geometry per signal: 7 groups of
+ * 32 x 64 samples (N = 64) or of 32 x 32 samples (N = 32), L = 32 threads per
+ * group either way -- the filter's tuning N when it is 32 or 64, else the
+ * choice of sos_autotune_batch for the signal's section count and length when
+ * it has run on the device, else N = 64.  Zero initial state for every
  * signal.
  *   n_signals  >= 0
  *   filters    host array [n_signals] of filter objects (may repeat), all on one device
@@ -218,9 +222,9 @@ sos_status sos_filter_run_host(sos_filter *f, const float *x_host, float *y_host
  *   y_dev      host array [n_signals] of device output pointers (in place allowed)
  *   n          host array [n_signals] of lengths (>= 0)
  * Filters of more than 8 sections are filtered one by one (sos_filter_run).
- * The library keeps four scratch sets per device (signal descriptors, lookback
+ * The library keeps eight scratch sets per device (signal descriptors, lookback
  * descriptors); a call waits on the host until the device has finished the
- * batch that used its scratch set four calls earlier, so batch calls must not
+ * batch that used its scratch set eight calls earlier, so batch calls must not
  * be made while `stream` is being captured into a CUDA graph.  Calls on one
  * device are serialized on the host.  Device-side errors: sos_batch_sync_status.
  */
@@ -441,6 +445,24 @@ sos_status sos_autotune_choice(int n_sections, int64_t n, int *solver, int *N);
 /* The same with the groups per tile of a PH choice (7 or 10; 8 for SOS_SOLVER_TC; 0 for the
  * other solvers) in *groups_per_cta (may be NULL). */
 sos_status sos_autotune_choice_ex(int n_sections, int64_t n, int *solver, int *N, int *groups_per_cta);
+
+/*
+ * Autotuner of batched runs (Sec. IV-D configurations for many signals): on
+ * the current device, time the batch kernel's two tile geometries (N = 64 and
+ * N = 32 samples per thread, 7 groups of L = 32 threads per tile) for 1 to 8
+ * sections on batches of 2^24 samples in equal signals of 2^12, 2^15, 2^18 and
+ * 2^21 samples, and keep the faster per (section count, length).  Afterwards
+ * every batched run (sos_filter_run_batch[_ex], sos_batch_plan_create, the
+ * serving loop) takes the choice for each signal whose filter's tuning leaves
+ * N at 0.  Synchronous; allocates and frees 128 MiB of device memory.
+ *   report  NULL, or host float[8][4][2] receiving the measured GS/s
+ *           (sections, signal length 2^12..2^21, geometry N = 64 / N = 32)
+ */
+sos_status sos_autotune_batch(float *report);
+
+/* The batch autotuner's samples per thread for a signal of K sections and n
+ * samples on the current device (64 or 32); 0 if sos_autotune_batch has not run. */
+sos_status sos_autotune_batch_choice(int n_sections, int64_t n, int *N);
 
 /* Human-readable name of a status code (static storage). */
 const char *sos_status_string(sos_status s);

@@ -27,7 +27,8 @@ EXPORTED = (
     "sos_filter_run_host", "sos_filter_run_noalloc", "sos_filter_run_batch_ex", "sos_batch_sync_status",
     "sos_server_create", "sos_server_destroy", "sos_server_add_stream", "sos_server_submit", "sos_server_poll",
     "sos_server_drain", "sos_server_stream_state", "sos_server_get_stats", "sos_server_replay",
-    "sos_autotune", "sos_autotune_choice", "sos_autotune_choice_ex", "sos_batch_plan_create", "sos_batch_plan_launch",
+    "sos_autotune", "sos_autotune_choice", "sos_autotune_choice_ex", "sos_autotune_batch", "sos_autotune_batch_choice",
+    "sos_batch_plan_create", "sos_batch_plan_launch",
     "sos_batch_plan_status", "sos_batch_plan_destroy", "sos_status_string",
 )
 
@@ -81,6 +82,8 @@ def load_library(path: str | None = None):
         lib.sos_server_get_stats.argtypes = [vp, vp]
         lib.sos_server_replay.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
         lib.sos_autotune.argtypes = [c_int, vp]
+        lib.sos_autotune_batch.argtypes = [vp]
+        lib.sos_autotune_batch_choice.argtypes = [c_int, i64, ctypes.POINTER(c_int)]
         lib.sos_batch_plan_create.argtypes = [c_int, vp, vp, vp, vp, vp, vp, ctypes.POINTER(vp)]
         lib.sos_batch_plan_launch.argtypes = [vp, vp]
         lib.sos_batch_plan_status.argtypes = [vp]
@@ -382,7 +385,7 @@ class SosServer:
 def autotune(max_log2n: int = 0) -> np.ndarray:
     """Time the candidate launch configurations on the current device and keep the fastest per
     (section count, length); returns the measured GS/s as [8 sections][4 lengths][CR32, CR64, PH, DTCR,
-    PH with 10 groups per tile]."""
+    PH with 10 groups per tile, PH on the tensor cores]."""
     rep = np.zeros((8, 4, 6), dtype=np.float32)
     _check(load_library().sos_autotune(int(max_log2n), rep.ctypes.data), "sos_autotune")
     return rep
@@ -395,6 +398,24 @@ def autotune_choice(n_sections: int, n: int, with_groups: bool = False):
     _check(load_library().sos_autotune_choice_ex(int(n_sections), int(n), ctypes.byref(s), ctypes.byref(N),
                                                  ctypes.byref(W)), "sos_autotune_choice_ex")
     return (s.value, N.value, W.value) if with_groups else (s.value, N.value)
+
+
+def autotune_batch() -> np.ndarray:
+    """Time the batch kernel's tile geometries (N = 64, N = 32) on the current device and keep the
+    faster per (section count, signal length); returns the measured GS/s as [8 sections][signal
+    lengths 2^12, 2^15, 2^18, 2^21][N = 64, N = 32]."""
+    rep = np.zeros((8, 4, 2), dtype=np.float32)
+    _check(load_library().sos_autotune_batch(rep.ctypes.data), "sos_autotune_batch")
+    return rep
+
+
+def autotune_batch_choice(n_sections: int, n: int) -> int:
+    """Samples per thread the batch autotuner picked for this section count and signal length; 0 if
+    it has not run."""
+    N = ctypes.c_int()
+    _check(load_library().sos_autotune_batch_choice(int(n_sections), int(n), ctypes.byref(N)),
+           "sos_autotune_batch_choice")
+    return N.value
 
 
 class BatchPlan:

@@ -148,7 +148,8 @@ struct LanePass {
     // the cascade transition over the first m + 1 samples of a lane, M1^(m+1) packed, m < N: the
     // final state's tail transition, taken by every run without further host work
     std::vector<float> Mm;           // [N][packed_floats(kp)]
-    // N = kBatchN only: device copies for the multi-signal kernel
+    // the batch kernel's geometries (N = kBatchN or kBatchNs, W = kBatchW) only: device copies for
+    // the multi-signal kernel
     sosk::LaneSec *d_sec = nullptr;  // [kp] section constants
     float4 *d_MX = nullptr;          // coupling blocks of M_N
     float *d_Mm = nullptr;           // device copy of Mm
@@ -160,15 +161,18 @@ struct LanePass {
 }  // namespace
 
 // What a batched run reads of a filter, in one cache line at the front of the filter object: the
-// batch kernel's device tables (N = kBatchN, first pass) and the launch class.
+// batch kernel's device tables for each tile geometry (first pass; the transition powers M1^(m+1),
+// m < 64, serve both) and the launch class.
 struct BatchTmpl {
-    const sosk::LaneSec *sec = nullptr;
-    const float4 *MX = nullptr;
-    const float *tab = nullptr;
+    const sosk::LaneSec *sec[sosk::kBatchGeoms] = {};
+    const float4 *MX[sosk::kBatchGeoms] = {};
+    const float *tab[sosk::kBatchGeoms] = {};
     const float *Mm = nullptr;
     float gain = 1.f;
-    int cls = -1;  // (K - 1) * 2 + b0-normalized, or -1 for more than kMaxPass sections
+    short cls = -1;        // (K - 1) * 2 + b0-normalized (geometry 0), or -1 for more than kMaxPass sections
+    signed char geom = -1;  // tile geometry pinned by the filter's tuning (N = 64: 0, N = 32: 1), or -1
 };
+static_assert(sizeof(BatchTmpl) <= 64, "one cache line");
 
 struct sos_filter {
     int K = 0;
@@ -548,15 +552,16 @@ sos_status build_lane(sos_filter *f, int N, int W, std::vector<LanePass> &out) {
             pack_into(Pm, kp, &ps.Mm[static_cast<size_t>(m) * nf]);
             Pm = dmul(Pm, ps.M1);
         }
-        if (N == sosk::kBatchN && W == sosk::kBatchW) {
+        if ((N == sosk::kBatchN || N == sosk::kBatchNs) && W == sosk::kBatchW) {
             const std::vector<float> &mm = ps.Mm;
+            const bool with_mm = N == sosk::kBatchN;  // M1^(m+1) for m < 64 serves both geometries
             if (cudaMalloc(&ps.d_sec, sizeof(sosk::LaneSec) * kp) != cudaSuccess ||
                 cudaMalloc(&ps.d_MX, sizeof(float) * ps.MX.size()) != cudaSuccess ||
-                cudaMalloc(&ps.d_Mm, sizeof(float) * mm.size()) != cudaSuccess)
+                (with_mm && cudaMalloc(&ps.d_Mm, sizeof(float) * mm.size()) != cudaSuccess))
                 return SOS_ENOMEM;
             if (cudaMemcpy(ps.d_sec, ps.sec.data(), sizeof(sosk::LaneSec) * kp, cudaMemcpyHostToDevice) != cudaSuccess ||
                 cudaMemcpy(ps.d_MX, ps.MX.data(), sizeof(float) * ps.MX.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-                cudaMemcpy(ps.d_Mm, mm.data(), sizeof(float) * mm.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+                (with_mm && cudaMemcpy(ps.d_Mm, mm.data(), sizeof(float) * mm.size(), cudaMemcpyHostToDevice) != cudaSuccess))
                 return SOS_ECUDA;
         }
         out.push_back(std::move(ps));
@@ -1074,6 +1079,44 @@ struct TuneTable {
 std::mutex g_tune_mu;
 TuneTable g_tune[64];
 
+// Autotuned tile geometry of batched runs (sos_autotune_batch): per device, section count and
+// signal length bucket, geometry 0 (N = 64) or 1 (N = 32).
+constexpr int kBatchTuneBuckets = 4;  // signal lengths around 2^12, 2^15, 2^18, 2^21
+constexpr int kBatchTuneLog2[kBatchTuneBuckets] = {12, 15, 18, 21};
+struct BatchTune {
+    bool valid = false;
+    unsigned char geom[8][kBatchTuneBuckets] = {};
+    float gss[8][kBatchTuneBuckets][sosk::kBatchGeoms] = {};  // measured GS/s
+};
+BatchTune g_btune[64];
+
+int batch_tune_bucket(int64_t n) {
+    int b = 0;
+    for (int i = 1; i < kBatchTuneBuckets; ++i)
+        if (n >= (1LL << ((kBatchTuneLog2[i - 1] + kBatchTuneLog2[i]) / 2))) b = i;
+    return b;
+}
+
+// The tile geometry of one batched signal: the filter's pinned geometry, else the device's autotuned
+// choice for its section count and length (a copy taken once per call), else N = 64.
+struct BatchGeomChoice {
+    bool valid = false;
+    unsigned char geom[8][kBatchTuneBuckets] = {};
+};
+BatchGeomChoice batch_geom_choice(int device) {
+    BatchGeomChoice c;
+    if (device < 0 || device >= 64) return c;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    c.valid = g_btune[device].valid;
+    std::memcpy(c.geom, g_btune[device].geom, sizeof c.geom);
+    return c;
+}
+int batch_geom_of(const BatchTmpl &bt, int K, int64_t n, const BatchGeomChoice &gc) {
+    if (bt.geom >= 0) return bt.geom;
+    if (!gc.valid) return 0;
+    return gc.geom[(K > sosk::kMaxPass ? sosk::kMaxPass : K) - 1][batch_tune_bucket(n)];
+}
+
 void candidate(int c, int *solver, int *N, int *W) {
     *solver = (c == 2 || c == 4) ? SOS_SOLVER_PH : c == 3 ? SOS_SOLVER_DTCR : c == 5 ? SOS_SOLVER_TC : SOS_SOLVER_CR;
     *N = c == 0 ? 32 : 64;
@@ -1129,10 +1172,10 @@ sos_status run_impl(sos_filter *f, const float *x, float *y, int64_t n, const fl
 
 // ---- multi-signal runs (sosfilt_batch.cuh)
 constexpr int kBatchSlots = 8;     // batches whose scratch may be in use on the device at once
-constexpr int kBatchClasses = 16;  // (K, normalized) classes: K = 1..8, b0-normalized or not
+constexpr int kBatchClasses = sosk::kBatchClassesMax;  // (geometry, K, b0-normalized): sosk::batch_class
 
 // Scratch of one batch in flight: signal descriptors and the tile -> signal map (one upload from
-// pinned staging), lookback descriptors and ticket counters of its class launches.
+// pinned staging), lookback descriptors and the ticket counters of its classes.
 struct BatchSlot {
     std::mutex mu;  // held by the call using the slot: its staging, capacities and event
     unsigned char *d_up = nullptr, *h_up = nullptr;  // [descriptors][tile -> signal map]
@@ -1142,10 +1185,6 @@ struct BatchSlot {
     unsigned long long *d_ticket = nullptr;  // [kBatchClasses]
     cudaEvent_t done = nullptr;
     bool pending = false;
-    // class launches of this slot's batch run on their own streams, so that batches issued on
-    // different caller streams overlap on the device
-    cudaStream_t side[kBatchClasses] = {};
-    cudaEvent_t fork = nullptr, join[kBatchClasses] = {};
 };
 
 struct BatchCtx {
@@ -1171,11 +1210,7 @@ BatchCtx *batch_ctx(int device) {
         for (int i = 0; ok && i < kBatchSlots; ++i) {
             BatchSlot &sl = c->slot[i];
             ok = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) == cudaSuccess &&
-                 cudaEventCreateWithFlags(&sl.fork, cudaEventDisableTiming) == cudaSuccess &&
                  cudaMalloc(&sl.d_ticket, sizeof(unsigned long long) * kBatchClasses) == cudaSuccess;
-            for (int k = 0; ok && k < kBatchClasses; ++k)
-                ok = cudaStreamCreateWithFlags(&sl.side[k], cudaStreamNonBlocking) == cudaSuccess &&
-                     cudaEventCreateWithFlags(&sl.join[k], cudaEventDisableTiming) == cudaSuccess;
         }
         if (!ok) {
             cudaGetLastError();
@@ -1186,32 +1221,10 @@ BatchCtx *batch_ctx(int device) {
     return ctx[device];
 }
 
-template <int K>
-sos_status launch_batch_class(bool norm, const sosk::BatchParams<K> &bp, long long grid, cudaStream_t s) {
-    return sosk::launch_batch<K>(norm, bp, grid, s) == cudaSuccess ? SOS_OK : SOS_ECUDA;
-}
-
-sos_status launch_batch_any(int K, bool norm, const sosk::BatchSig *sigs, const int *tile_sig, long long n_tiles,
-                            unsigned long long *desc, unsigned long long *ticket, unsigned epoch, int *status,
-                            long long budget, long long grid, cudaStream_t s) {
-    switch (K) {
-#define SOSK_CASE(k)                                                                              \
-    case k: {                                                                                     \
-        sosk::BatchParams<k> bp{sigs, tile_sig, n_tiles, desc, ticket, 0ULL, epoch, status, budget}; \
-        return launch_batch_class<k>(norm, bp, grid, s);                                          \
-    }
-        SOSK_CASE(1) SOSK_CASE(2) SOSK_CASE(3) SOSK_CASE(4) SOSK_CASE(5) SOSK_CASE(6) SOSK_CASE(7) SOSK_CASE(8)
-#undef SOSK_CASE
-        default: return SOS_EINVAL;
-    }
-}
-
-// All signals of a batch in one persistent launch per (K, normalized) class; the class launches run
-// on forked streams, joined back into `s`.  Filters of more than eight sections run one by one.
 // The single batch kernel's parameters: one queue per class present (its signal descriptors, tile ->
 // signal map, lookback descriptors and ticket counter), the grid, and each class's share of the
-// grid to start on, in proportion to its work (tiles x (2 + K), the particular pass and correction
-// growing with K).
+// grid to start on, in proportion to its work (samples per tile x tiles x (2 + K), the particular
+// pass and correction growing with K).
 sos_status batch_all_params(const long long *cls_sigs, const long long *cls_tiles, const long long *sig_off,
                             const long long *tile_off, const long long *desc_off, const sosk::BatchSig *d_sigs,
                             const int *d_tile_sig, unsigned long long *d_desc, unsigned long long *d_ticket,
@@ -1225,7 +1238,8 @@ sos_status batch_all_params(const long long *cls_sigs, const long long *cls_tile
         ap.code[nc] = c;
         ap.q[nc] = sosk::BatchQueue{d_sigs + sig_off[c], d_tile_sig + tile_off[c], cls_tiles[c], d_desc + desc_off[c],
                                     d_ticket + c, 0ULL, epoch};
-        work[nc] = static_cast<double>(cls_tiles[c]) * (2 + c / 2 + 1);
+        work[nc] = static_cast<double>(cls_tiles[c]) * sosk::batch_geom_n(sosk::batch_class_geom(c)) *
+                   (2 + sosk::batch_class_k(c));
         total += work[nc];
         tiles += cls_tiles[c];
         ++nc;
@@ -1256,11 +1270,11 @@ sos_status run_batch_impl(int n_signals, sos_filter *const *filters, const float
     if (n_signals < 0) return SOS_EINVAL;
     if (n_signals == 0) return SOS_OK;
     if (!filters || !x || !y || !n) return SOS_EINVAL;
-    constexpr long long C = 32LL * sosk::kBatchN;
     constexpr long long W = sosk::kBatchW;
     // arguments, classes and sizes in one pass over the signals (the per-signal work of a call
     // reads only the front cache line of each filter)
     const int device = filters[0] ? filters[0]->device : -1;
+    const BatchGeomChoice gc = batch_geom_choice(device);
     long long cls_sigs[kBatchClasses] = {0}, cls_tiles[kBatchClasses] = {0};
     bool any_other = false;  // zero-length signals or filters of more than kMaxPass sections
     for (int i = 0; i < n_signals; ++i) {
@@ -1268,11 +1282,14 @@ sos_status run_batch_impl(int n_signals, sos_filter *const *filters, const float
         if (!f || n[i] < 0 || (n[i] > 0 && (!x[i] || !y[i]))) return SOS_EINVAL;
         if (x[i] != y[i] && n[i] > 0 && ranges_overlap(x[i], y[i], n[i])) return SOS_EINVAL;
         if (f->device != device) return SOS_EINVAL;
-        const int c = f->bt.cls;
-        if (n[i] == 0 || c < 0) {
+        const BatchTmpl &bt = f->bt;
+        if (n[i] == 0 || bt.cls < 0) {
             any_other = true;
             continue;
         }
+        const int g = batch_geom_of(bt, sosk::batch_class_k(bt.cls), n[i], gc);
+        const int c = bt.cls + 16 * g;
+        const long long C = 32LL * sosk::batch_geom_n(g);
         cls_sigs[c] += 1;
         cls_tiles[c] += ((n[i] + C - 1) / C + W - 1) / W;
     }
@@ -1301,7 +1318,7 @@ sos_status run_batch_impl(int n_signals, sos_filter *const *filters, const float
     for (int c = 0; c < kBatchClasses; ++c) {
         sig_off[c + 1] = sig_off[c] + cls_sigs[c];
         tile_off[c + 1] = tile_off[c] + cls_tiles[c];
-        desc_off[c + 1] = desc_off[c] + cls_tiles[c] * 4 * (c / 2 + 1);  // [tiles][2][2K]
+        desc_off[c + 1] = desc_off[c] + cls_tiles[c] * 4 * sosk::batch_class_k(c);  // [tiles][2][2K]
         if (cls_sigs[c]) ++n_cls;
     }
     if (sig_off[kBatchClasses] == 0) return SOS_OK;
@@ -1374,9 +1391,11 @@ sos_status run_batch_impl(int n_signals, sos_filter *const *filters, const float
         fill_tile[c] = tile_off[c];
     }
     for (int i = 0; i < n_signals; ++i) {
-        const BatchTmpl &bt = filters[i]->bt;  // the batch kernel's tables (N = kBatchN), read only
-        const int c = bt.cls;
-        if (c < 0 || n[i] == 0) continue;
+        const BatchTmpl &bt = filters[i]->bt;  // the batch kernel's tables, read only
+        if (bt.cls < 0 || n[i] == 0) continue;
+        const int g = batch_geom_of(bt, sosk::batch_class_k(bt.cls), n[i], gc);
+        const int c = bt.cls + 16 * g;
+        const long long C = 32LL * sosk::batch_geom_n(g);
         const long long G = (n[i] + C - 1) / C;
         const long long nt = (G + W - 1) / W;
         const long long si = fill_sig[c]++;
@@ -1388,9 +1407,9 @@ sos_status run_batch_impl(int n_signals, sos_filter *const *filters, const float
         b.tile0 = fill_tile[c] - tile_off[c];
         b.zi = zi ? zi[i] : nullptr;
         b.zf = zf ? zf[i] : nullptr;
-        b.sec = bt.sec;
-        b.MX = bt.MX;
-        b.tab = bt.tab;
+        b.sec = bt.sec[g];
+        b.MX = bt.MX[g];
+        b.tab = bt.tab[g];
         b.Mm = bt.Mm;
         b.gain = bt.gain;
         b.aligned = ((reinterpret_cast<uintptr_t>(x[i]) | reinterpret_cast<uintptr_t>(y[i])) % 16 == 0) ? 1 : 0;
@@ -1421,10 +1440,7 @@ sos_status run_batch_impl(int n_signals, sos_filter *const *filters, const float
 struct sos_batch_plan {
     int device = -1;
     int n_cls = 0;
-    int K[kBatchClasses] = {};
-    bool norm[kBatchClasses] = {};
     long long tiles[kBatchClasses] = {};
-    long long grid[kBatchClasses] = {};
     const sosk::BatchSig *sigs[kBatchClasses] = {};
     const int *tile_sig[kBatchClasses] = {};
     unsigned long long *desc[kBatchClasses] = {};
@@ -1433,8 +1449,6 @@ struct sos_batch_plan {
     size_t desc_words = 0;
     unsigned long long *d_ticket = nullptr;   // [kBatchClasses]
     int *d_status = nullptr;
-    cudaStream_t side[kBatchClasses] = {};
-    cudaEvent_t fork = nullptr, join[kBatchClasses] = {};
 };
 
 namespace {
@@ -1447,11 +1461,6 @@ void plan_free(sos_batch_plan *p) {
     if (p->d_desc) cudaFree(p->d_desc);
     if (p->d_ticket) cudaFree(p->d_ticket);
     if (p->d_status) cudaFree(p->d_status);
-    for (int c = 0; c < kBatchClasses; ++c) {
-        if (p->side[c]) cudaStreamDestroy(p->side[c]);
-        if (p->join[c]) cudaEventDestroy(p->join[c]);
-    }
-    if (p->fork) cudaEventDestroy(p->fork);
     delete p;
 }
 
@@ -1459,18 +1468,20 @@ sos_status plan_create(int n_signals, sos_filter *const *filters, const float *c
                        const int64_t *n, const float *const *zi, float *const *zf, sos_batch_plan **out) {
     if (!out || n_signals <= 0 || !filters || !x || !y || !n) return SOS_EINVAL;
     *out = nullptr;
-    constexpr long long C = 32LL * sosk::kBatchN;
     constexpr long long W = sosk::kBatchW;
     int device = filters[0] ? filters[0]->device : -1;
+    const BatchGeomChoice gc = batch_geom_choice(device);
     long long cls_sigs[kBatchClasses] = {0}, cls_tiles[kBatchClasses] = {0};
     std::vector<int> cls(n_signals);
     for (int i = 0; i < n_signals; ++i) {
         sos_filter *f = filters[i];
         if (!f || f->device != device || n[i] <= 0 || !x[i] || !y[i] || f->K > sosk::kMaxPass) return SOS_EINVAL;
         if (x[i] != y[i] && ranges_overlap(x[i], y[i], n[i])) return SOS_EINVAL;
-        const int c = (f->K - 1) * 2 + (f->norm ? 1 : 0);
+        const int g = batch_geom_of(f->bt, f->K, n[i], gc);
+        const int c = sosk::batch_class(g, f->K, f->norm);
         cls[i] = c;
         cls_sigs[c] += 1;
+        const long long C = 32LL * sosk::batch_geom_n(g);
         const long long G = (n[i] + C - 1) / C;
         cls_tiles[c] += (G + W - 1) / W;
     }
@@ -1479,7 +1490,7 @@ sos_status plan_create(int n_signals, sos_filter *const *filters, const float *c
     for (int c = 0; c < kBatchClasses; ++c) {
         sig_off[c + 1] = sig_off[c] + cls_sigs[c];
         tile_off[c + 1] = tile_off[c] + cls_tiles[c];
-        desc_off[c + 1] = desc_off[c] + cls_tiles[c] * 4 * (c / 2 + 1);  // [tiles][2][2K]
+        desc_off[c + 1] = desc_off[c] + cls_tiles[c] * 4 * sosk::batch_class_k(c);  // [tiles][2][2K]
     }
     const size_t sig_bytes = sizeof(sosk::BatchSig) * sig_off[kBatchClasses];
     const size_t up_bytes = sig_bytes + sizeof(int) * tile_off[kBatchClasses];
@@ -1493,8 +1504,10 @@ sos_status plan_create(int n_signals, sos_filter *const *filters, const float *c
     }
     for (int i = 0; i < n_signals; ++i) {
         const int c = cls[i];
+        const int g = sosk::batch_class_geom(c);
         sos_filter *f = filters[i];
-        const LanePass &ps = f->lane[1][0];  // N = kBatchN: the batch kernel's tables (read only)
+        const BatchTmpl &bt = f->bt;  // the batch kernel's tables for the signal's geometry (read only)
+        const long long C = 32LL * sosk::batch_geom_n(g);
         const long long G = (n[i] + C - 1) / C;
         const long long nt = (G + W - 1) / W;
         const long long si = fill_sig[c]++;
@@ -1506,11 +1519,11 @@ sos_status plan_create(int n_signals, sos_filter *const *filters, const float *c
         b.tile0 = fill_tile[c] - tile_off[c];
         b.zi = zi ? zi[i] : nullptr;
         b.zf = zf ? zf[i] : nullptr;
-        b.sec = ps.d_sec;
-        b.MX = ps.d_MX;
-        b.tab = ps.d_tab;
-        b.Mm = ps.d_Mm;
-        b.gain = static_cast<float>(f->gain);
+        b.sec = bt.sec[g];
+        b.MX = bt.MX[g];
+        b.tab = bt.tab[g];
+        b.Mm = bt.Mm;
+        b.gain = bt.gain;
         b.aligned = (reinterpret_cast<uintptr_t>(x[i]) % 16 == 0 && reinterpret_cast<uintptr_t>(y[i]) % 16 == 0) ? 1 : 0;
         const int local = static_cast<int>(si - sig_off[c]);
         for (long long t = 0; t < nt; ++t) h_tile_sig[fill_tile[c]++] = local;
@@ -1524,18 +1537,10 @@ sos_status plan_create(int n_signals, sos_filter *const *filters, const float *c
               cudaMalloc(&p->d_ticket, sizeof(unsigned long long) * kBatchClasses) == cudaSuccess &&
               cudaMalloc(&p->d_status, sizeof(int)) == cudaSuccess &&
               cudaMemcpy(p->d_up, up.data(), up_bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
-              cudaMemset(p->d_status, 0, sizeof(int)) == cudaSuccess &&
-              cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming) == cudaSuccess;
+              cudaMemset(p->d_status, 0, sizeof(int)) == cudaSuccess && sosk::batch_all_blocks_per_sm() > 0;
     for (int c = 0; ok && c < kBatchClasses; ++c) {
         if (!cls_sigs[c]) continue;
-        const int K = c / 2 + 1;
-        const int bps = sosk::batch_blocks_per_sm(K, (c & 1) != 0);
-        ok = bps > 0 && cudaStreamCreateWithFlags(&p->side[c], cudaStreamNonBlocking) == cudaSuccess &&
-             cudaEventCreateWithFlags(&p->join[c], cudaEventDisableTiming) == cudaSuccess;
-        p->K[c] = K;
-        p->norm[c] = (c & 1) != 0;
         p->tiles[c] = cls_tiles[c];
-        p->grid[c] = std::min<long long>(static_cast<long long>(bps) * sm_count(device), cls_tiles[c]);
         p->sigs[c] = reinterpret_cast<const sosk::BatchSig *>(p->d_up) + sig_off[c];
         p->tile_sig[c] = reinterpret_cast<const int *>(p->d_up + sig_bytes) + tile_off[c];
         p->desc[c] = p->d_desc + desc_off[c];
@@ -1736,13 +1741,16 @@ sos_status sos_filter_create(int n_sections, const double *sos, const float *zi,
                         f->lane[i]);
     for (size_t i = 0; i < f->lane[3].size() && st == SOS_OK; ++i) st = build_tc(f, f->lane[3][i]);
     if (st == SOS_OK) {
-        const LanePass &ps = f->lane[1][0];
-        f->bt.sec = ps.d_sec;
-        f->bt.MX = ps.d_MX;
-        f->bt.tab = ps.d_tab;
-        f->bt.Mm = ps.d_Mm;
+        for (int g = 0; g < sosk::kBatchGeoms; ++g) {
+            const LanePass &ps = f->lane[g == 0 ? 1 : 0][0];  // (64, kBatchW) and (32, kBatchW)
+            f->bt.sec[g] = ps.d_sec;
+            f->bt.MX[g] = ps.d_MX;
+            f->bt.tab[g] = ps.d_tab;
+        }
+        f->bt.Mm = f->lane[1][0].d_Mm;
         f->bt.gain = static_cast<float>(f->gain);
-        f->bt.cls = f->K > sosk::kMaxPass ? -1 : (f->K - 1) * 2 + (f->norm ? 1 : 0);
+        f->bt.cls = static_cast<short>(f->K > sosk::kMaxPass ? -1 : sosk::batch_class(0, f->K, f->norm));
+        f->bt.geom = static_cast<signed char>(f->tuning.N == sosk::kBatchNs ? 1 : f->tuning.N ? 0 : -1);
     }
     if (st == SOS_OK) {
         if (cudaMalloc(&f->d_ticket, 2 * sizeof(unsigned long long)) != cudaSuccess ||  // eager, captured
@@ -2079,6 +2087,99 @@ sos_status sos_autotune_choice_ex(int n_sections, int64_t n, int *solver, int *N
 
 sos_status sos_autotune_choice(int n_sections, int64_t n, int *solver, int *N) {
     return sos_autotune_choice_ex(n_sections, n, solver, N, nullptr);
+}
+
+sos_status sos_autotune_batch(float *report) {
+    int device = 0;
+    if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= 64) return SOS_ECUDA;
+    constexpr int64_t kTotal = 1LL << 24;  // samples per timed batch
+    float *x = nullptr, *y = nullptr;
+    if (cudaMalloc(&x, sizeof(float) * kTotal) != cudaSuccess || cudaMalloc(&y, sizeof(float) * kTotal) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(x);
+        return SOS_ENOMEM;
+    }
+    cudaMemset(x, 0, sizeof(float) * kTotal);
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaFree(x);
+        cudaFree(y);
+        return SOS_ECUDA;
+    }
+    BatchTune bt;
+    sos_status rc = SOS_OK;
+    for (int K = 1; K <= sosk::kMaxPass && rc == SOS_OK; ++K) {
+        std::vector<double> sos(5 * K);  // a stable cascade (the timing does not depend on the values)
+        for (int k = 0; k < K; ++k) {
+            const double r = 0.9 + 0.01 * k, th = 0.2 + 0.05 * k;
+            const double c[5] = {0.05, 0.1, 0.05, -2.0 * r * std::cos(th), r * r};
+            std::memcpy(&sos[5 * k], c, sizeof c);
+        }
+        for (int g = 0; g < sosk::kBatchGeoms && rc == SOS_OK; ++g) {
+            sos_tuning t{};
+            t.N = sosk::batch_geom_n(g);  // pins the batch geometry of the filter's signals
+            sos_filter *f = nullptr;
+            rc = sos_filter_create(K, sos.data(), nullptr, &t, &f);
+            if (rc != SOS_OK) break;
+            for (int b = 0; b < kBatchTuneBuckets && rc == SOS_OK; ++b) {
+                // equal signals filling kTotal samples, timed from a prepared plan (no host work
+                // between the launches)
+                const int64_t len = 1LL << kBatchTuneLog2[b];
+                const int m = static_cast<int>(kTotal / len);
+                std::vector<sos_filter *> fs(m, f);
+                std::vector<const float *> xs(m);
+                std::vector<float *> ys(m);
+                std::vector<int64_t> ns(m, len);
+                for (int i = 0; i < m; ++i) {
+                    xs[i] = x + static_cast<int64_t>(i) * len;
+                    ys[i] = y + static_cast<int64_t>(i) * len;
+                }
+                sos_batch_plan *plan = nullptr;
+                rc = plan_create(m, fs.data(), xs.data(), ys.data(), ns.data(), nullptr, nullptr, &plan);
+                if (rc != SOS_OK) break;
+                constexpr int kReps = 5;
+                for (int w = 0; w < 2 && rc == SOS_OK; ++w) rc = sos_batch_plan_launch(plan, st);
+                cudaEventRecord(e0, st);
+                for (int r = 0; r < kReps && rc == SOS_OK; ++r) rc = sos_batch_plan_launch(plan, st);
+                cudaEventRecord(e1, st);
+                float ms = 0.f;
+                if (rc == SOS_OK && (cudaEventSynchronize(e1) != cudaSuccess ||
+                                     cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                    rc = SOS_ECUDA;
+                if (rc == SOS_OK) rc = sos_batch_plan_status(plan);
+                plan_free(plan);
+                if (rc == SOS_OK) bt.gss[K - 1][b][g] = ms > 0.f ? static_cast<float>(kTotal) * kReps / ms / 1e6f : 0.f;
+            }
+            sos_filter_destroy(f);
+        }
+        for (int b = 0; b < kBatchTuneBuckets; ++b)
+            bt.geom[K - 1][b] = bt.gss[K - 1][b][1] > bt.gss[K - 1][b][0] ? 1 : 0;
+    }
+    cudaStreamSynchronize(st);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(st);
+    cudaFree(x);
+    cudaFree(y);
+    if (rc != SOS_OK) return rc;
+    bt.valid = true;
+    if (report) std::memcpy(report, bt.gss, sizeof bt.gss);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_btune[device] = bt;
+    return SOS_OK;
+}
+
+sos_status sos_autotune_batch_choice(int n_sections, int64_t n, int *N) {
+    if (n_sections < 1 || !N) return SOS_EINVAL;
+    int device = 0;
+    if (cudaGetDevice(&device) != cudaSuccess) return SOS_ECUDA;
+    const BatchGeomChoice gc = batch_geom_choice(device);
+    *N = gc.valid ? sosk::batch_geom_n(gc.geom[(n_sections > sosk::kMaxPass ? sosk::kMaxPass : n_sections) - 1]
+                                             [batch_tune_bucket(n)])
+                  : 0;
+    return SOS_OK;
 }
 
 sos_status sos_filter_stream_push(sos_filter *f, const float *x_dev, float *y_dev, int64_t n, void *stream) {

@@ -2,7 +2,7 @@
 // in one launch over a global queue of (signal, tile) work items.
 //
 // The work of every signal is cut into tiles of W = kBatchW groups of C = 32 N samples
-// (N = kBatchN); the tiles of all signals of the launch form one queue, drawn in ascending order
+// (N = 64, or N = 32 for the short geometry); the tiles of all signals of a class form one queue, drawn in ascending order
 // from a ticket counter (Sec. IV-A), so that tile t's predecessors within its signal are held by
 // running or finished blocks.  Each tile is filtered as by the single-signal PH kernel
 // (sosfilt_lane.cuh): a skewed particular pass per lane in direct-form-I order (Sec. II-C), the
@@ -74,13 +74,17 @@ __device__ __forceinline__ float lane_mv_rows(const float (&r)[S], float xi) {
     return y;
 }
 
-// One block's share of a class of the batch (signals of K sections with the same b0 handling): the
-// block draws tiles from the class's ticket counter until the class is exhausted, then returns.
-template <int K, bool NORM>
+// One block's share of a class of the batch (signals of K sections with the same b0 handling and
+// tile geometry, N samples per lane): the block draws tiles from the class's ticket counter until
+// the class is exhausted, then returns.
+template <int K, bool NORM, int N>
 __device__ __forceinline__ void batch_body(const BatchParams<K> &p, float4 *smem4) {
-    using Dm = LaneDims<K, kBatchN>;
-    constexpr int S = Dm::S, MS = Dm::MS, N = kBatchN, W = kBatchW, CH = Dm::LQ, RPS = Dm::RPS, RSP = Dm::RSP;
-    static_assert(Dm::V == 4 && Dm::CC == CH, "the batch kernel corrects four samples per lane and step");
+    using Dm = LaneDims<K, N, kBatchW>;
+    constexpr int S = Dm::S, MS = Dm::MS, W = kBatchW, RSP = Dm::RSP;
+    // the correction takes four consecutive samples of a row per lane and step: CH chunks per row,
+    // RPS rows per step
+    constexpr int CH = N / 4, RPS = 32 / CH;
+    static_assert(CH == Dm::LQ && CH * RPS == 32, "batch tile geometry");
     constexpr int P = N + 4;  // padded row pitch (floats): conflict-free 128-bit row access
     constexpr int C = N * kL;
     constexpr int SZ = ((S + 3) / 4) * 4;
@@ -429,10 +433,18 @@ __device__ __forceinline__ void batch_body(const BatchParams<K> &p, float4 *smem
     cp_async_wait_all();
 }
 
-template <int K>
+// The body of one class as a function of its own (not inlined): the single batch kernel calls it
+// per class, so that the register allocator treats each class's body apart (inlining all 32 into
+// one function costs spills and three times the build time).
+template <int K, bool NORM, int N>
+__device__ __noinline__ void batch_entry(BatchParams<K> p, float4 *smem4) {
+    batch_body<K, NORM, N>(p, smem4);
+}
+
+template <int K, int N>
 constexpr size_t batch_smem_bytes() {
-    using Dm = LaneDims<K, kBatchN>;
-    return sizeof(float) * (static_cast<size_t>(kBatchW) * 3 * kL * (kBatchN + 4) + kBatchW * kL * Dm::RSP +
+    using Dm = LaneDims<K, N, kBatchW>;
+    return sizeof(float) * (static_cast<size_t>(kBatchW) * 3 * kL * (N + 4) + kBatchW * kL * Dm::RSP +
                             4 * kBatchW * Dm::S + 2 * Dm::S + 2 * kBatchW * ((Dm::S + 3) / 4) * 4);
 }
 

@@ -212,21 +212,31 @@ SOSK_DECLARE_TC(5) SOSK_DECLARE_TC(6) SOSK_DECLARE_TC(7) SOSK_DECLARE_TC(8)
 int tc_blocks_per_sm(int K);
 
 // ---- multi-signal persistent kernel (sosfilt_batch.cuh): the PH kernel with a skewed particular
-// pass over a global queue of (signal, tile) work items
-constexpr int kBatchN = 64;      // samples per lane
-constexpr int kBatchW = kLaneW;  // groups (compute warps) per tile: the N = 64 tables of the PH kernel
+// pass over a global queue of (signal, tile) work items.  Two tile geometries, chosen per signal:
+// N = 64 or N = 32 samples per lane, kBatchW groups (compute warps) per tile either way, so that
+// both run in blocks of the same shape and one launch serves every class.
+constexpr int kBatchN = 64;      // samples per lane of the wide geometry
+constexpr int kBatchNs = 32;     // samples per lane of the short geometry (tiles of half the samples)
+constexpr int kBatchW = kLaneW;  // groups (compute warps) per tile: the tables of the PH kernel
+constexpr int kBatchGeoms = 2;   // geometry 0: N = kBatchN, geometry 1: N = kBatchNs
+#if defined(__CUDACC__)
+#define SOSK_HD __host__ __device__
+#else
+#define SOSK_HD
+#endif
+SOSK_HD constexpr int batch_geom_n(int geom) { return geom == 0 ? kBatchN : kBatchNs; }
 
 // One signal of a batch (device array, built by the host for each batched run).
 struct BatchSig {
     const float *x;
     float *y;
-    long long n, G;        // samples, groups of 32 kBatchN samples
+    long long n, G;        // samples, groups of 32 N samples (N of the signal's class)
     long long tile0;       // first global tile of the signal; its tiles are tile0 .. tile0 + ceil(G / W) - 1
     const float *zi;       // device [K][2] initial state (true domain) or nullptr
     float *zf;             // device [K][2] final state or nullptr
-    const LaneSec *sec;    // device [K] section constants for N = kBatchN
+    const LaneSec *sec;    // device [K] section constants for the class's N
     const float4 *MX;      // device coupling blocks of M_N (as LaneParams::MX)
-    const float *tab;      // device table block (LaneDims<K, kBatchN>::TAB_GLOBAL floats)
+    const float *tab;      // device table block (LaneDims<K, N>::TAB_GLOBAL floats)
     const float *Mm;       // device [kBatchN][2K(K+1)] packed one-sample transition powers M1^(m+1)
     float gain;            // input multiplier (product of the b0 when normalized)
     int aligned;           // x and y 16-byte aligned
@@ -256,29 +266,25 @@ struct BatchQueue {
     unsigned int epoch;
 };
 
-constexpr int kBatchClassesMax = 16;  // (K, b0-normalized) classes: K = 1..8, normalized or not
+// Class of a batched signal: geometry, section count K = 1..8 and b0 handling,
+// code = 16 geometry + 2 (K - 1) + b0-normalized.
+constexpr int kBatchClassesMax = 16 * kBatchGeoms;
+SOSK_HD constexpr int batch_class(int geom, int K, bool norm) { return 16 * geom + 2 * (K - 1) + (norm ? 1 : 0); }
+SOSK_HD constexpr int batch_class_k(int code) { return ((code & 15) >> 1) + 1; }
+SOSK_HD constexpr int batch_class_geom(int code) { return code >> 4; }
 
 struct BatchAllParams {
     int n_classes;
-    int code[kBatchClassesMax];         // class code: 2 (K - 1) + b0-normalized
+    int code[kBatchClassesMax];         // class code (batch_class)
     int blk_off[kBatchClassesMax + 1];  // blocks [blk_off[c], blk_off[c + 1]) start on class c
     BatchQueue q[kBatchClassesMax];
     int *status;
     long long spin_budget;
 };
 
-// Launch the single persistent kernel over every class of a batch (sosfilt_batch.cu).
+// Launch the single persistent kernel over every class of a batch (sosfilt_batch_all.cu).
 cudaError_t launch_batch_all(const BatchAllParams &p, long long grid, cudaStream_t s);
 int batch_all_blocks_per_sm();
-
-template <int K>
-cudaError_t launch_batch(bool norm, const BatchParams<K> &p, long long grid, cudaStream_t s);
-#define SOSK_DECLARE_BATCH(K) \
-    template <>               \
-    cudaError_t launch_batch<K>(bool norm, const BatchParams<K> &p, long long grid, cudaStream_t s);
-SOSK_DECLARE_BATCH(1) SOSK_DECLARE_BATCH(2) SOSK_DECLARE_BATCH(3) SOSK_DECLARE_BATCH(4)
-SOSK_DECLARE_BATCH(5) SOSK_DECLARE_BATCH(6) SOSK_DECLARE_BATCH(7) SOSK_DECLARE_BATCH(8)
-int batch_blocks_per_sm(int K, bool norm);
 
 // Device memory for the lookback descriptors and the ticket counter of one cascade run.
 struct Scratch {

@@ -164,7 +164,6 @@ int lane_blocks_per_sm_n64a(int, bool) { return 1; }
 int lane_blocks_per_sm_n64b(int, bool) { return 1; }
 int lane_blocks_per_sm_n64w10a(int, bool) { return 1; }
 int lane_blocks_per_sm_n64w10b(int, bool) { return 1; }
-int batch_blocks_per_sm(int, bool) { return 1; }
 int batch_all_blocks_per_sm() { return 1; }
 int dtcr_blocks_per_sm(int, bool) { return 1; }
 int tc_blocks_per_sm(int) { return 1; }
@@ -190,20 +189,9 @@ cudaError_t launch_dccr(int K, int N, bool norm, int, const PassParams &p, long 
         mark(p.x, p.y, p.n, p.zi, p.zf, K);                                                           \
         return cudaSuccess;                                                                           \
     }
-#define HOST_BATCH(K)                                                                                \
-    template <>                                                                                      \
-    cudaError_t launch_batch<K>(bool norm, const BatchParams<K> &p, long long grid, cudaStream_t) {   \
-        record(3, K, 64, norm, grid, p);                                                             \
-        if (g_light) return cudaSuccess;                                                             \
-        std::set<int> sigs(p.tile_sig, p.tile_sig + p.n_tiles);                                      \
-        for (int i : sigs) {                                                                         \
-            const BatchSig &g = p.sigs[i];                                                           \
-            mark(g.x, g.y, g.n, g.zi, g.zf, K);                                                      \
-        }                                                                                            \
-        return cudaSuccess;                                                                          \
-    }
 // The single batch kernel: counted, and recorded as one launch record per class it covers (the
-// class's queue in the layout of BatchParams, so the tests read every class alike).
+// class's queue in the layout of BatchParams, so the tests read every class alike; N = the class's
+// samples per lane).
 long long g_batch_all_launches = 0;
 cudaError_t launch_batch_all(const BatchAllParams &p, long long grid, cudaStream_t) {
     ++g_batch_all_launches;
@@ -211,8 +199,8 @@ cudaError_t launch_batch_all(const BatchAllParams &p, long long grid, cudaStream
         const BatchQueue &q = p.q[i];
         const BatchParams<1> bp{q.sigs, q.tile_sig, q.n_tiles, q.desc, q.ticket, q.ticket_base, q.epoch, p.status,
                                 p.spin_budget};
-        const int K = p.code[i] / 2 + 1;
-        record(3, K, 64, (p.code[i] & 1) != 0, grid, bp);
+        const int K = batch_class_k(p.code[i]);
+        record(3, K, batch_geom_n(batch_class_geom(p.code[i])), (p.code[i] & 1) != 0, grid, bp);
         if (g_light) continue;
         std::set<int> sigs(q.tile_sig, q.tile_sig + q.n_tiles);
         for (int j : sigs) {
@@ -241,7 +229,7 @@ cudaError_t launch_batch_all(const BatchAllParams &p, long long grid, cudaStream
         return cudaSuccess;                                                                                  \
     }
 #define HOST_ALL(K) HOST_LANE(K, 32, 7) HOST_LANE(K, 64, 7) HOST_LANE(K, 64, 10) HOST_CAS(K, 32) HOST_CAS(K, 64) \
-    HOST_BATCH(K) HOST_DTCR(K) HOST_TC(K)
+    HOST_DTCR(K) HOST_TC(K)
 HOST_ALL(1) HOST_ALL(2) HOST_ALL(3) HOST_ALL(4) HOST_ALL(5) HOST_ALL(6) HOST_ALL(7) HOST_ALL(8)
 
 }  // namespace sosk

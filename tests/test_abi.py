@@ -33,7 +33,8 @@ def test_header_declares_the_abi():
         "sos_filter_run_host", "sos_filter_run_noalloc", "sos_filter_run_batch_ex", "sos_batch_sync_status",
         "sos_server_create", "sos_server_destroy", "sos_server_add_stream", "sos_server_submit", "sos_server_poll",
         "sos_server_drain", "sos_server_stream_state", "sos_server_get_stats", "sos_server_replay",
-        "sos_autotune", "sos_autotune_choice", "sos_autotune_choice_ex", "sos_batch_plan_create",
+        "sos_autotune", "sos_autotune_choice", "sos_autotune_choice_ex", "sos_autotune_batch",
+        "sos_autotune_batch_choice", "sos_batch_plan_create",
         "sos_batch_plan_launch",
         "sos_batch_plan_status", "sos_batch_plan_destroy", "sos_status_string"])
 

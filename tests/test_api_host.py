@@ -575,14 +575,16 @@ def test_cascade_carry_tables_match_a_float64_derivation(lib, name, N):
     lib.sos_filter_destroy(f)
 
 
-def test_batch_tables_match_a_float64_derivation(lib):
-    """A signal of a batch carries its own tables: the PH section constants and coupling blocks, the
-    table block for tiles of seven groups, the gain, and the one-sample transition powers M1^(m+1),
-    m < 64, from which the kernel forms a signal's final state."""
+@pytest.mark.parametrize("N", [64, 32])
+def test_batch_tables_match_a_float64_derivation(lib, N):
+    """A signal of a batch carries its own tables for its tile geometry (N samples per lane, pinned
+    here by the filter's tuning): the PH section constants and coupling blocks, the table block for
+    tiles of seven groups, the gain, and the one-sample transition powers M1^(m+1), m < 64, from
+    which the kernel forms a signal's final state."""
     sos = DESIGNS["butter8"]
     K = sos.shape[0]
-    f = _create(lib, sos)
-    x = workloads.normal_f32(12, 3 * W * C64 + 11)
+    f = _create(lib, sos, {"N": N})
+    x = workloads.normal_f32(12, 3 * W * 32 * N + 11)
     y = np.empty_like(x)
     zf = np.zeros((K, 2), dtype=np.float32)
     one = lambda v: (ctypes.c_void_p * 1)(v)
@@ -590,15 +592,16 @@ def test_batch_tables_match_a_float64_derivation(lib):
     assert lib.sos_filter_run_batch_ex(1, one(f.value), one(x.ctypes.data), one(y.ctypes.data),
                                        (ctypes.c_int64 * 1)(x.size), None, one(zf.ctypes.data), None) == 0
     (l,) = _launches(lib)
-    assert (l["kind"], l["K"]) == (KIND_BATCH, K)
+    assert (l["kind"], l["K"], l["N"]) == (KIND_BATCH, K, N)
     lay = (ctypes.c_longlong * 17)()
     lib.host_batch_layout(lay)
     sec_size, sig_size = lay[0], lay[1]
-    otab, ogain, p_sigs, osec, oMX, oMm = lay[9], lay[10], lay[11], lay[14], lay[15], lay[16]
+    otab, ogain, p_sigs, osec, oMX, oMm, oG = lay[9], lay[10], lay[11], lay[14], lay[15], lay[16], lay[5]
     sig = bytes(_mem(int(_at(l["raw"], p_sigs, np.uint64)[0]), np.uint8, sig_size))
+    assert _at(sig, oG, np.int64)[0] == -(-x.size // (32 * N))  # groups of 32 N samples
     c, norm = _normalised(sos)
-    M1, H = _transition_and_basis(c, N64)
-    MN = np.linalg.matrix_power(M1, N64)
+    M1, H = _transition_and_basis(c, N)
+    MN = np.linalg.matrix_power(M1, N)
     AC = np.linalg.matrix_power(MN, 32)
     AT = np.linalg.matrix_power(AC, W)
     S, nf = 2 * K, 2 * K * (K + 1)
@@ -617,12 +620,14 @@ def test_batch_tables_match_a_float64_derivation(lib):
         P = P @ M1
     ms = nf if (nf // 4) % 2 else nf + 4
     full = S * S
-    tab = _mem(int(_at(sig, otab, np.uint64)[0]), np.float32, 64 * ms + 2 * full + N64 * S)
-    Tl = np.eye(S)
+    tab = _mem(int(_at(sig, otab, np.uint64)[0]), np.float32, 64 * ms + 2 * full + N * S)
+    Ml, Tl = np.eye(S), np.eye(S)
     for lane in range(32):
+        _close(tab[lane * ms:lane * ms + nf], _packed(Ml, K), f"batch (M_N)^{lane}")
         _close(tab[(32 + lane) * ms:(32 + lane) * ms + nf], _packed(Tl, K), f"batch (A_T)^{lane}")
-        Tl = Tl @ AT
-    _close(tab[64 * ms + full + S * N64:64 * ms + 2 * full + S * N64], AT.T.reshape(-1), "batch A_T")
+        Ml, Tl = Ml @ MN, Tl @ AT
+    _close(tab[64 * ms + full:64 * ms + full + S * N], H.reshape(-1), "batch basis")
+    _close(tab[64 * ms + full + S * N:64 * ms + 2 * full + S * N], AT.T.reshape(-1), "batch A_T")
     lib.sos_filter_destroy(f)
 
 
@@ -854,3 +859,79 @@ def test_autotuner_choices_drive_the_default_launch(lib):
     finally:
         lib.host_set_light(0)
         lib.host_reset()
+
+
+def test_batch_autotuner_picks_the_tile_geometry_per_section_count(lib):
+    """The batch autotuner times both tile geometries per section count and signal length from
+    prepared plans and keeps the faster; default-tuned batched runs then put each signal in the
+    class of its geometry (tiles of 32 N samples per group), a filter's tuning N still wins, and one
+    persistent launch covers the mix."""
+    vp = ctypes.c_void_p
+    lib.sos_autotune_batch.argtypes = [vp]
+    lib.sos_autotune_batch_choice.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_int)]
+    lib.host_set_cost.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float]
+    lib.host_batch_all_launches.restype = ctypes.c_longlong
+    N = ctypes.c_int()
+
+    def choice(K, n):
+        assert lib.sos_autotune_batch_choice(K, n, ctypes.byref(N)) == 0
+        return N.value
+
+    def tune(fast32):
+        for K in range(1, 9):
+            lib.host_set_cost(KIND_BATCH, 32, K, 1.0 if fast32(K) else 2.0)
+            lib.host_set_cost(KIND_BATCH, 64, K, 2.0 if fast32(K) else 1.0)
+        report = np.zeros((8, 4, 2), dtype=np.float32)
+        lib.host_set_light(1)
+        try:
+            assert lib.sos_autotune_batch(report.ctypes.data) == 0
+        finally:
+            lib.host_set_light(0)
+            lib.host_reset()
+        return report
+
+    report = tune(lambda K: K <= 4)
+    for K in range(1, 9):
+        assert np.all(report[K - 1, :, 1] > 0) and np.all(report[K - 1, :, 0] > 0)
+        assert np.all(np.argmax(report[K - 1], axis=1) == (1 if K <= 4 else 0)), K
+        for n in (1000, 1 << 15, 1 << 20, 1 << 30):
+            assert choice(K, n) == (32 if K <= 4 else 64), (K, n)
+    assert choice(12, 1 << 20) == 64  # more than eight sections: the eight-section choice
+    try:
+        specs = [(2, None, 32), (2, {"N": 64}, 64), (8, None, 64), (8, {"N": 32}, 32), (4, None, 32)]
+        fs = [_create(lib, designs.butter_lowpass(2 * K, 0.2), t) for K, t, _ in specs]
+        n = 3 * W * C64 + 5
+        xs = [workloads.normal_f32(40 + i, n) for i in range(len(specs))]
+        ys = [np.empty_like(x) for x in xs]
+        m = len(specs)
+        arr = lambda vals: (vp * m)(*vals)
+        lib.host_reset()
+        before = lib.host_batch_all_launches()
+        assert lib.sos_filter_run_batch_ex(m, arr([h.value for h in fs]), arr([x.ctypes.data for x in xs]),
+                                           arr([y.ctypes.data for y in ys]), (ctypes.c_int64 * m)(*[n] * m), None,
+                                           None, None) == 0
+        assert lib.host_batch_all_launches() - before == 1
+        lay = (ctypes.c_longlong * 17)()
+        lib.host_batch_layout(lay)
+        sig_size, ox, oG, p_sigs, p_ntiles = lay[1], lay[2], lay[5], lay[11], lay[13]
+        got = {}
+        for l in _launches(lib):
+            n_tiles = int(_at(l["raw"], p_ntiles, np.int64)[0])
+            tile_sig = _mem(int(_at(l["raw"], lay[12], np.uint64)[0]), np.int32, n_tiles)
+            n_sig = int(tile_sig.max()) + 1
+            sigs = bytes(_mem(int(_at(l["raw"], p_sigs, np.uint64)[0]), np.uint8, n_sig * sig_size))
+            for k in range(n_sig):
+                b = sigs[k * sig_size:(k + 1) * sig_size]
+                i = next(j for j, x in enumerate(xs) if x.ctypes.data == _at(b, ox, np.uint64)[0])
+                G = -(-n // (32 * l["N"]))
+                assert _at(b, oG, np.int64)[0] == G
+                got[i] = (l["K"], l["N"], n_tiles)
+        for i, (K, _, Nw) in enumerate(specs):
+            assert got[i][:2] == (K, Nw), i
+            np.testing.assert_array_equal(ys[i], 2 * xs[i])
+        # the two eight-section signals sit in different classes, each with its own tiles
+        assert got[2][2] == -(-(-(-n // C64)) // W) and got[3][2] == -(-(-(-n // (32 * 32))) // W)
+        for h in fs:
+            lib.sos_filter_destroy(h)
+    finally:
+        tune(lambda K: False)  # leave the library's batched runs at N = 64 for the other tests

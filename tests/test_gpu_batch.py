@@ -1,9 +1,11 @@
 """GPU parity of the batched runs (sos_filter_run_batch / _ex) against the float64 oracle.
 
-The multi-signal kernel keeps one lookback chain per signal inside one persistent launch per
-section count; these tests mix section counts, lengths (ragged tails, signals shorter than a tile,
-several tiles), b0 handling, in-place and unaligned buffers, initial and final states, and filters
-of more than eight sections (filtered one by one), and check every signal against the oracle.
+The multi-signal kernel keeps one lookback chain per signal inside one persistent launch over every
+class (section count, b0 handling, tile geometry); these tests mix section counts, lengths (ragged
+tails, signals shorter than a tile, several tiles), b0 handling, both tile geometries (N = 64 and
+N = 32 samples per lane, pinned per filter or picked by the batch autotuner), in-place and unaligned
+buffers, initial and final states, and filters of more than eight sections (filtered one by one),
+and check every signal against the oracle.
 """
 import numpy as np
 import pytest
@@ -36,6 +38,17 @@ def _zerr(zf, zf_ref):
 
 LENGTHS = [1, 2, 31, 32, 33, 1023, 1024, 1025, 8191, 8192, 8193, 3 * 8192 + 1, 50000, 123457]
 
+# tile geometry of the filters of a test: the library's choice, N = 32 pinned, or alternating
+GEOMETRIES = ["default", "n32", "mixed"]
+
+
+def _tuning(geometry, i):
+    if geometry == "n32" or (geometry == "mixed" and i % 2 == 1):
+        return {"N": 32}
+    if geometry == "mixed":
+        return {"N": 64}
+    return None
+
 
 def _mix(n_signals, seed):
     rng = np.random.default_rng(seed)
@@ -52,7 +65,8 @@ def _mix(n_signals, seed):
     return items
 
 
-def test_batch_mixed_orders_lengths_states(dev):
+@pytest.mark.parametrize("geometry", GEOMETRIES)
+def test_batch_mixed_orders_lengths_states(dev, geometry):
     from paper_2607_23763_gb300 import SosFilter, run_batch, batch_sync_status
     items = _mix(56, 3)
     # a 12-section filter in the mix (more than one pass: filtered on its own)
@@ -60,7 +74,7 @@ def test_batch_mixed_orders_lengths_states(dev):
     items.append((sos12, workloads.normal_f32(99, 20000), np.random.default_rng(9).standard_normal((12, 2)) * 0.1))
     fs, xs, ys, zis, zfs = [], [], [], [], []
     for i, (sos, x, zi) in enumerate(items):
-        fs.append(SosFilter(sos))
+        fs.append(SosFilter(sos, tuning=_tuning(geometry, i)))
         off = 1 if i % 11 == 5 else 0  # some unaligned buffers
         buf = torch.zeros(len(x) + off, device=dev)
         buf[off:] = torch.from_numpy(x).to(dev)
@@ -85,7 +99,8 @@ def test_batch_mixed_orders_lengths_states(dev):
         f.close()
 
 
-def test_batch_final_states_of_many_short_signals(dev):
+@pytest.mark.parametrize("N", [64, 32])
+def test_batch_final_states_of_many_short_signals(dev, N):
     """Hundreds of signals of one to seven groups: almost every tile holds some signal's last group,
     owned by varying warps, so consecutive tiles of the same slot capture final states in different
     warps; each signal's final state must match the oracle (repeated launches)."""
@@ -93,9 +108,9 @@ def test_batch_final_states_of_many_short_signals(dev):
     rng = np.random.default_rng(31)
     sos = designs.butter_lowpass(4, 0.1)
     K = sos.shape[0]
-    f = SosFilter(sos)
+    f = SosFilter(sos, tuning={"N": N})
     n_sig = 600
-    lengths = rng.integers(1, 7 * 2048 + 1, n_sig)
+    lengths = rng.integers(1, 7 * 32 * N + 1, n_sig)
     xs = [workloads.normal_f32(5000 + i, int(n)) for i, n in enumerate(lengths)]
     zis = [rng.standard_normal((K, 2)) * 0.1 for _ in range(n_sig)]
     xd = [torch.from_numpy(x).to(dev) for x in xs]
@@ -114,7 +129,8 @@ def test_batch_final_states_of_many_short_signals(dev):
     f.close()
 
 
-def test_batch_alone_equals_mix(dev):
+@pytest.mark.parametrize("geometry", GEOMETRIES)
+def test_batch_alone_equals_mix(dev, geometry):
     """Each signal filtered alone in a batch of its own and inside the mix gives the same output and
     final state bit for bit: the batch kernel composes every tile's incoming state from anchors
     counted from the signal's own first tile, so nothing depends on the other signals or on where
@@ -123,7 +139,7 @@ def test_batch_alone_equals_mix(dev):
     from paper_2607_23763_gb300 import SosFilter, run_batch
     items = _mix(24, 5)
     items = [it for it in items if it[0].shape[0] <= 8]
-    fs = [SosFilter(sos) for sos, _, _ in items]
+    fs = [SosFilter(sos, tuning=_tuning(geometry, i)) for i, (sos, _, _) in enumerate(items)]
     xs = [torch.from_numpy(x).to(dev) for _, x, _ in items]
     zis = [torch.from_numpy(zi.astype(np.float32)).to(dev) for _, _, zi in items]
     zf_mix = [torch.full((sos.shape[0], 2), float("nan"), device=dev) for sos, _, _ in items]
@@ -151,7 +167,7 @@ def test_batch_repeated_calls_reuse_scratch(dev):
     """More calls than scratch sets in flight, back to back on one stream."""
     from paper_2607_23763_gb300 import SosFilter, run_batch
     items = _mix(10, 8)
-    fs = [SosFilter(sos) for sos, _, _ in items]
+    fs = [SosFilter(sos, tuning=_tuning("mixed", i)) for i, (sos, _, _) in enumerate(items)]
     xs = [torch.from_numpy(x).to(dev) for _, x, _ in items]
     outs = [run_batch(fs, xs) for _ in range(9)]
     torch.cuda.synchronize()
@@ -168,6 +184,25 @@ def test_batched_mix_full_size_sampled(dev):
     """The batched mix at full size (4096 signals, lengths 2^10..2^22, orders 2..16, random
     sections) in one batched call, as the benchmark times it; every 16th signal checked against
     the oracle (whole signal up to 2^18 samples, else windows restarted early with zero state)."""
+    _full_size_mix(dev)
+
+
+def test_batch_autotuner_then_full_size_mix(dev):
+    """The batch autotuner times both tile geometries per section count and signal length; the
+    full-size mix then runs with its choices (one launch over the classes of both geometries) and
+    stays within the bound.  The tuned choice stays in force for the rest of the process."""
+    from paper_2607_23763_gb300 import autotune_batch, autotune_batch_choice
+    assert autotune_batch_choice(4, 1 << 16) == 0  # nothing tuned yet
+    rep = autotune_batch()
+    print("batch autotuner GS/s [sections][2^12, 2^15, 2^18, 2^21][N = 64, N = 32]:\n", np.round(rep, 1))
+    assert rep.shape == (8, 4, 2) and np.all(rep > 0)
+    for K in range(1, 9):
+        for b, n in enumerate([1 << 12, 1 << 15, 1 << 18, 1 << 21]):
+            assert autotune_batch_choice(K, n) == (32 if rep[K - 1, b, 1] > rep[K - 1, b, 0] else 64)
+    _full_size_mix(dev)
+
+
+def _full_size_mix(dev):
     from paper_2607_23763_gb300 import SosFilter, run_batch, batch_sync_status
     n_sig = 4096
     specs = [workloads.batched_signal(i) for i in range(n_sig)]
@@ -205,9 +240,8 @@ def test_batch_plan_launch_and_cuda_graph_replay(dev):
     """A prepared batch launched directly, then captured into a CUDA graph and replayed: every replay
     gives the oracle's output (descriptors and tickets are reset inside the captured work)."""
     from paper_2607_23763_gb300 import SosFilter, BatchPlan
-    items = [it for it in _mix(30, 11) if len(it[1]) > 0]
-    fs = [SosFilter(sos) for sos, _, _ in items if sos.shape[0] <= 8]
-    items = [it for it in items if it[0].shape[0] <= 8]
+    items = [it for it in _mix(30, 11) if len(it[1]) > 0 and it[0].shape[0] <= 8]
+    fs = [SosFilter(sos, tuning=_tuning("mixed", i)) for i, (sos, _, _) in enumerate(items)]
     xs = [torch.from_numpy(x).to(dev) for _, x, _ in items]
     plan = BatchPlan(fs, xs)
     refs = [oracle.sosfilt(sos, x) for sos, x, _ in items]
