@@ -309,11 +309,13 @@ sos_status sos_filter_sync_status(sos_filter *f);
  *     observed, [11] row states stored, [12] stored, [14]/[15] input stash;
  *     [13] SM id.
  *   PH on the tensor cores (per tile): [0] tile + 1, [13] SM id; coordinator: [1]
- *     start, [2] incoming state resolved, [3] group states posted; producer: [16]
+ *     start, [26] predecessors' local carries observed, [27] anchor carries
+ *     observed, [2] incoming state resolved, [3] group states posted; producer: [16]
  *     ticket drawn, [17] loads issued; MMA issuer: [18] first products issued,
  *     [19] remainder products issued, [20] correction issued; [21] input
  *     remainder formed; epilogue (first warp of each warpgroup): [4]/[22]
- *     accumulator observed, [7]/[23] lane scan done, [8] fold done, [9]
+ *     accumulator observed, [7]/[23] lane scan done, [8] fold start, [28] tile
+ *     carry folded (the folding warp), [9]
  *     correction start, [10] group state observed, [11] state operand posted,
  *     [12]/[24] correction observed, [14]/[25] outputs stored.
  *   cyclic reduction, cascade carry (per tile): see the kernel's source.

@@ -493,6 +493,7 @@ __device__ __forceinline__ void coordinate_tile(const LaneParams<K> &p, int lane
                 __nanosleep(64);  // a short nap: the successors' lookbacks wait on this tile
             }
         }
+        if (tr) tr[26] = global_ns();
         // the anchor's carries are read before the local sum is formed, so that their latency overlaps
         // it: G(a) whole in every lane (a tile between anchors), or word li of G(A) and of the local
         // parts W(A + 32 j), j < ni (an anchor)
@@ -540,6 +541,7 @@ __device__ __forceinline__ void coordinate_tile(const LaneParams<K> &p, int lane
                 __nanosleep(32);
                 ready = load_g();
             }
+            if (tr) tr[27] = global_ns();
             zi_lane = pl + packed_row<K>(sATl + ja * MS, g, lane);
         } else {
             const float wl = lane_mv<S>(mats.AT, pl, lane) + acc_i;  // W(cur) = A_T P + carry(cur)
@@ -549,6 +551,7 @@ __device__ __forceinline__ void coordinate_tile(const LaneParams<K> &p, int lane
                 __nanosleep(32);
                 ready = load_h();
             }
+            if (tr) tr[27] = global_ns();
             float gprev = h[0];  // G(A), then the resolved carries of the anchors after it
 #pragma unroll
             for (int j = 1; j < kSuperAnchor; ++j)

@@ -19,9 +19,10 @@
 // A tile is two units (256 rows, 8 groups of 32 lanes, 16384 samples); tiles come from an ascending
 // ticket counter (Sec. IV-A), and the carry between tiles is the PH kernels' decoupled lookback on
 // the cascade state (coordinate_tile).  Warp roles per block (one block per SM):
-//   warps 0, 12 coordinators, one per carry slot (tiles alternate): lookback and the groups'
-//               incoming states
-//   warp 1      producer: tickets, TMA loads of the units' rows (the ragged last row patched in)
+//   warps 0, 1  coordinators, one per carry slot (tiles alternate): lookback and the groups'
+//               incoming states (on two different SM schedulers: 3 % faster at orders 8 and 16
+//               than both on the first)
+//   warp 12     producer: tickets, TMA loads of the units' rows (the ragged last row patched in)
 //   warp 2      tensor-memory owner; lane 0 issues every tcgen05.mma and commit
 //   warp 3      split of the staged input into its TF32 remainder
 //   warps 4-11  epilogue: warpgroup u (warps 4 + 4u .. 7 + 4u) takes unit u of every tile, warp
@@ -47,12 +48,15 @@ constexpr int kTcDS = 6;                          // accumulator slots
 constexpr int kTcCols = 80;                       // accumulator columns: 64 outputs, 16 state words
 constexpr int kTcTmemCols = 512;                  // tensor memory allocated (kTcDS * kTcCols rounded up)
 constexpr int kTcThreads = 416;                   // 13 warps
-constexpr int kTcCoord1 = 12;                     // the second coordinator warp
+constexpr int kTcCoord1 = 1;                      // the second coordinator warp
 constexpr int kTcB1 = 2 * kTcCols * 128;          // one B1 image (two K halves of 80 rows x 128 B)
 constexpr int kTcImg = 2 * kTcB1 + kTcN * 128;    // B1 head, B1 remainder, B2 (H head | H remainder)
 static_assert(kTcImg == kTcImageBytes, "operand image size");
 constexpr int kTcXBytes = kTcRows * kTcN * 4;     // one unit of rows (two K halves of 16 KB)
 constexpr int kTcOffX = kTcImg;                   // input stages
+// from this many sections on, a tile's ticket waits for its accumulator slot (measured at 2^28
+// samples: order 16 +22 %; orders 8 and 2 lose 2 % and 10 %, where the loads in flight matter more)
+constexpr int kTcLateTicketK = 5;
 
 template <int K>
 struct TcParams {
@@ -280,12 +284,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) sos_tc_kernel(const __grid_cons
             if (lane == 0) mbar_arrive(&bar_zready[slot]);
             if (tr) tr[3] = global_ns();
         }
-    } else if (warp == 1) {
+    } else if (warp == 12) {
         // ------------------------------------------------------------------ producer
         if (lane == 0) {
             unsigned i = 0, patch_phase = 0;
             bool stop = false, gave_up = false;
             while (!stop) {
+                if constexpr (K >= kTcLateTicketK) {
+                    // the tile's ticket is drawn only once the accumulator slot of its first unit is
+                    // free, so that tiles are numbered in the order the blocks reach them and a
+                    // tile's predecessors fold close to it (a shorter wait in its lookback)
+                    const long long k = static_cast<long long>(i) - kTcDS;
+                    if (k >= 0 && !mbar_wait(&dfree[k % kTcDS], static_cast<unsigned>(k / kTcDS) & 1u, budget, p.status)) {
+                        stop = gave_up = true;
+                        break;
+                    }
+                }
                 long long tile = static_cast<long long>(atomicAdd(p.ticket, 1ULL) - p.ticket_base);
                 if (tile >= p.n_tiles) tile = -1;
                 trace(tile, 16);
@@ -483,6 +497,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sos_tc_kernel(const __grid_cons
                         if (lane < S) pref[(slot * kTcW + w - 1) * S + lane] = cc;
                         cc = lane_mv<S>(sACd, cc, lane) + abt[w * S + li];
                     }
+                    if (lane == 0) trace(tile, 28);
                     if (tile % kAnchor != 0 && lane < S)  // an anchor's local carry is never read
                         st_relaxed_b64(p.desc + static_cast<size_t>(tile) * 2 * S + lane,
                                        pack_word((p.epoch << 2) | 1u, cc));
