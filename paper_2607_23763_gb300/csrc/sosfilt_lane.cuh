@@ -494,25 +494,12 @@ __device__ __forceinline__ void coordinate_tile(const LaneParams<K> &p, int lane
             }
         }
         if (tr) tr[26] = global_ns();
-        // the anchor's carries are read before the local sum is formed, so that their latency overlaps
-        // it: G(a) whole in every lane (a tile between anchors), or word li of G(A) and of the local
-        // parts W(A + 32 j), j < ni (an anchor)
+        // the carries the composition starts from are read before the local sum is formed, so that
+        // their latency overlaps it: word li of G(A) and of the local parts W(A + 32 j) of the anchors
+        // after A -- up to cur for an anchor, up to a (whose G(a) the tile forms itself) otherwise
         float g[S], h[kSuperAnchor];
         const long long A = ((cur - 1) / (kAnchor * kSuperAnchor)) * (kAnchor * kSuperAnchor);
-        const int ni = static_cast<int>((cur - A) / kAnchor);  // 1 .. kSuperAnchor (anchors)
-        auto load_g = [&]() -> bool {
-            bool ok = true;
-            const unsigned long long *dp = desc(a, 1);
-#pragma unroll
-            for (int q = 0; q < S; q += 2) {
-                unsigned long long x0, x1;
-                ld_relaxed_v2(dp + q, x0, x1);
-                ok = ok && static_cast<unsigned>(x0 >> 32) == tagG && static_cast<unsigned>(x1 >> 32) == tagG;
-                g[q] = __uint_as_float(static_cast<unsigned>(x0));
-                g[q + 1] = __uint_as_float(static_cast<unsigned>(x1));
-            }
-            return ok;
-        };
+        const int ni = anchor ? static_cast<int>((cur - A) / kAnchor) : static_cast<int>((a - A) / kAnchor) + 1;
         auto load_h = [&]() -> bool {
             bool ok = true;
 #pragma unroll
@@ -526,7 +513,7 @@ __device__ __forceinline__ void coordinate_tile(const LaneParams<K> &p, int lane
             }
             return ok;
         };
-        bool ready = anchor ? load_h() : load_g();
+        bool ready = load_h();
         // P: each lane applies its own power (A_T)^lane, a reduce-scatter leaves word i in lane i
         float pl;
         {
@@ -539,9 +526,15 @@ __device__ __forceinline__ void coordinate_tile(const LaneParams<K> &p, int lane
             const long long t_start = clock64();
             while (!__all_sync(0xffffffffu, ready) && !timed_out(t_start)) {
                 __nanosleep(32);
-                ready = load_g();
+                ready = load_h();
             }
             if (tr) tr[27] = global_ns();
+            float ga = h[0];  // G(A), then the resolved carries of the anchors after it, up to G(a)
+#pragma unroll
+            for (int j = 1; j < kSuperAnchor; ++j)
+                if (j < ni) ga = lane_mv<S>(mats.AT32, ga, lane) + h[j];
+#pragma unroll
+            for (int q = 0; q < S; ++q) g[q] = __shfl_sync(0xffffffffu, ga, q);  // G(a) whole in every lane
             zi_lane = pl + packed_row<K>(sATl + ja * MS, g, lane);
         } else {
             const float wl = lane_mv<S>(mats.AT, pl, lane) + acc_i;  // W(cur) = A_T P + carry(cur)

@@ -15,7 +15,9 @@
  * emu_run is the skewed-pass PH kernel's protocol.  The hierarchical form (emu_run_hier) is the
  * tensor-core kernel's: every tile first sums the
  * local carries after its anchor, P = sum_k A^(k-1) L(t - k) (Horner from zero); a tile between
- * anchors then waits for G(a) and takes Z = A^(t-1-a) G(a) + P; an anchor t publishes its local part
+ * anchors then forms G(a) itself, from the resolved carry of the super-anchor s below it and the
+ * local parts of the anchors s + 32 .. a by the same Horner steps the anchor takes (so the bits
+ * agree), and takes Z = A^(t-1-a) G(a) + P; an anchor t publishes its local part
  * W = A P + L(t) in its slot 0 (tag epoch << 2 | 3), waits for the resolved carry of the
  * super-anchor s below it (multiples of 128) and the local parts of the anchors between, composes
  * G(t) = A^32 (... (A^32 G(s) + W(s + 32)) ...) + W(t) by Horner's rule, publishes it and takes
@@ -123,7 +125,14 @@ static int hier_tile(emu_ctx *c, int64_t t) {
         memcpy(P, tmp, sizeof(float) * (size_t)S);
     }
     if (!anchor) {
-        if (!wait_slot(c, a, 1, tagG, g)) return 0;
+        /* G(a) formed here from the super-anchor's resolved carry and the anchors' local parts */
+        const int64_t s0 = ((t - 1) / 128) * 128;
+        if (!wait_slot(c, s0, 1, tagG, g)) return 0;
+        for (int64_t b = s0 + 32; b <= a; b += 32) {
+            if (!wait_slot(c, b, 0, tagW, v)) return 0;
+            mv_add(S, AP + (size_t)32 * S * S, g, v, tmp);
+            memcpy(g, tmp, sizeof(float) * (size_t)S);
+        }
         mv_add(S, AP + (size_t)(t - 1 - a) * S * S, g, P, c->Z + (size_t)t * S);
         return 1;
     }
