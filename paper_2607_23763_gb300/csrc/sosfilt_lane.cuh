@@ -473,10 +473,13 @@ __device__ __forceinline__ void coordinate_tile(const LaneParams<K> &p, int lane
         {
             const long long pred = cur - 1 - lane;
             const long long t_start = clock64();
+            bool have = pred <= a;  // this lane's carry is complete (kept, not read again)
+#pragma unroll
+            for (int q = 0; q < S; ++q) v[q] = 0.f;
             for (;;) {
-                bool ok = true;
-                if (pred > a) {
+                if (!have) {
                     const unsigned long long *dp = desc(pred, 0);
+                    bool ok = true;
 #pragma unroll
                     for (int q = 0; q < S; q += 2) {
                         unsigned long long x0, x1;
@@ -485,11 +488,9 @@ __device__ __forceinline__ void coordinate_tile(const LaneParams<K> &p, int lane
                         v[q] = __uint_as_float(static_cast<unsigned>(x0));
                         v[q + 1] = __uint_as_float(static_cast<unsigned>(x1));
                     }
-                } else {
-#pragma unroll
-                    for (int q = 0; q < S; ++q) v[q] = 0.f;
+                    have = ok;
                 }
-                if (__all_sync(0xffffffffu, ok) || timed_out(t_start)) break;
+                if (__all_sync(0xffffffffu, have) || timed_out(t_start)) break;
                 __nanosleep(64);  // a short nap: the successors' lookbacks wait on this tile
             }
         }
