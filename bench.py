@@ -44,8 +44,6 @@ SOLVER_CR, SOLVER_PH, SOLVER_DTCR, SOLVER_TC = 1, 2, 3, 4
 TRAFFIC_BYTES_2P28 = {
     # sos_lane_kernel<8, 64, 7> at 2^26 samples: 268,859,904 B read + 211,708,672 B written
     (SOLVER_PH, 64): 4 * (268859904 + 211708672),
-    # sos_tc_kernel<8> at 2^26 samples: 269,093,888 B read + 211,570,944 B written
-    (SOLVER_TC, 64): 4 * (269093888 + 211570944),
 }
 PH_GROUPS_PER_BLOCK = 7
 CR_GROUPS_PER_BLOCK = {32: 8, 64: 4}
@@ -675,6 +673,21 @@ def batched_leg(torch, dev, steps: int = 5, warmup: int = 3, no_cpu: bool = Fals
     with ClockSampler(dev.index or 0) as clk:
         ms = time_launches(torch, lambda i: run_batch(fs, xs, ys), steps, stream)
     assert batch_sync_status(0) == 0
+    # the same call through the C ABI with the caller's host arrays built once (as a C caller keeps
+    # them): the library's per-call cost without the Python binding's marshalling of 4096 tensors
+    import ctypes
+    from paper_2607_23763_gb300 import load_library
+    lib = load_library()
+    arr = lambda vals, t=ctypes.c_void_p: (t * n_sig)(*vals)
+    hf, hx, hy = arr([f.handle for f in fs]), arr([x.data_ptr() for x in xs]), arr([y.data_ptr() for y in ys])
+    hn = arr([x.numel() for x in xs], ctypes.c_int64)
+    sh = ctypes.c_void_p(stream.cuda_stream)
+    c_call = lambda i: lib.sos_filter_run_batch(n_sig, ctypes.addressof(hf), ctypes.addressof(hx), ctypes.addressof(hy),
+                                                ctypes.addressof(hn), sh)
+    for _ in range(warmup):
+        c_call(0)
+    c_ms = time_launches(torch, c_call, steps, stream)
+    assert batch_sync_status(0) == 0
     # the same batch as a prepared plan captured into a CUDA graph, replayed
     plan = BatchPlan(fs, xs, ys)
     side = torch.cuda.Stream()
@@ -701,6 +714,9 @@ def batched_leg(torch, dev, steps: int = 5, warmup: int = 3, no_cpu: bool = Fals
            "vs_plain_kernel": plain_ms / ms,
            "cuda_graph": {"value": total / graph_ms / 1e6, "ms_per_step": graph_ms,
                           "vs_plain_kernel": plain_ms / graph_ms},
+           "c_abi_per_call": {"value": total / c_ms / 1e6, "ms_per_step": c_ms, "vs_plain_kernel": plain_ms / c_ms,
+                              "note": "sos_filter_run_batch with host arrays built once; `value` goes through the "
+                                      "Python binding, which marshals 4096 tensors per call"},
            "plain_gss_by_order": {str(2 * k): v for k, v in rate.items()},
            "target_vs_plain": 0.60, "clocks": clk.summary(),
            "tile_geometry": {

@@ -344,7 +344,7 @@ sos_status sos_filter_trace(sos_filter *f, uint64_t *buf_dev, int64_t capacity_b
  *   solver), and so are its outputs and final states, bit for bit.
  *   n            at most SOS_NOALLOC_MAX_SAMPLES samples per call, else SOS_EBUDGET
  *   The first call on a device looks up the array's device address on the current device
- *   (a one-time set-up); make that first call before any stream capture.
+ *   (a one-time set-up).
  *   All calls on a device share the array and keep its last contents: each pass first clears the
  *   ticket counter and the descriptors it will use (with cudaMemsetAsync on `stream`), so nothing
  *   needs clearing by the caller, but calls that overlap on the GPU (different streams, or

@@ -428,15 +428,15 @@ __device__ __forceinline__ float packed_row(const float *__restrict__ A, const f
 // The composition is fixed, so that outputs are reproducible bit for bit:
 //   * every tile first sums the local carries L of the tiles after the anchor a below it (a multiple
 //     of 32): P = sum_{k=1}^{cur-1-a} (A_T)^(k-1) L(cur - k);
-//   * a tile between anchors then adds (A_T)^(cur-1-a) G(a), one packed row per lane, once G(a) is
-//     visible;
 //   * an anchor posts W(cur) = A_T P + carry(cur) in its local-carry slot (an anchor's local carry is
 //     never read); from the super-anchor A below it (multiples of 128), i = (cur - A) / 32 <= 4,
 //     G(cur) = (A_T)^32 (... ((A_T)^32 G(A) + W(A + 32)) ...) + W(cur) by Horner's rule, and
-//     Z = (A_T)^31 G(cur - 32) + P.
-// So the resolved carries form a chain of one hop per 128 tiles, every anchor resolves one hop after
-// the super-anchor below it, and what waits on a carry is a few 2K x 2K products: the local carries
-// are summed before it can have arrived.
+//     Z = (A_T)^31 G(cur - 32) + P;
+//   * a tile between anchors forms G(a) by the same Horner steps from G(A) and the anchors' W (the
+//     same bits as the anchor's own) and adds (A_T)^(cur-1-a) G(a), one packed row per lane.
+// So the resolved carries form a chain of one hop per 128 tiles, every tile is one hop from the
+// super-anchor below it, and what waits on a carry is a few 2K x 2K products: the local carries are
+// summed before it can have arrived.  A lane whose carry has arrived keeps it and stops reading.
 template <int K, int W, int MS, int P2, int SH>
 __device__ __forceinline__ void coordinate_tile(const LaneParams<K> &p, int lane, long long cur, unsigned slot,
                                                 long long budget, const float *sATl, const CoordMats &mats,
