@@ -44,6 +44,8 @@ SOLVER_CR, SOLVER_PH, SOLVER_DTCR, SOLVER_TC = 1, 2, 3, 4
 TRAFFIC_BYTES_2P28 = {
     # sos_lane_kernel<8, 64, 7> at 2^26 samples: 268,859,904 B read + 211,708,672 B written
     (SOLVER_PH, 64): 4 * (268859904 + 211708672),
+    # sos_tc_kernel<8> at 2^26 samples: 269,067,008 B read + 213,834,496 B written
+    (SOLVER_TC, 64): 4 * (269067008 + 213834496),
 }
 PH_GROUPS_PER_BLOCK = 7
 CR_GROUPS_PER_BLOCK = {32: 8, 64: 4}
@@ -733,9 +735,18 @@ def batched_leg(torch, dev, steps: int = 5, warmup: int = 3, no_cpu: bool = Fals
     return out
 
 
+def _autotune_plain(args):
+    """The library's autotuner, so that the plain kernel the mixes are compared with is the fastest
+    configuration per order (as in the default run)."""
+    if not args.no_autotune:
+        from paper_2607_23763_gb300 import autotune
+        autotune()
+
+
 def bench_batched(args):
     import torch
     torch.cuda.set_device(0)
+    _autotune_plain(args)
     leg = batched_leg(torch, torch.device("cuda", 0), args.steps, args.warmup, args.no_cpu,
                       autotune=not args.no_autotune)
     line = {"metric": "GS/s", "value": leg["value"], "unit": "GS/s", "n_gpus": 1, "steps": args.steps,
@@ -853,6 +864,7 @@ def serving_batch_probe(torch, dev, soss, pool, m: int = 4096, reps: int = 3):
 def bench_serving(args):
     import torch
     torch.cuda.set_device(0)
+    _autotune_plain(args)
     leg = serving_leg(torch, torch.device("cuda", 0), args.streams, args.chunks_per_stream, args.open_requests, {},
                       autotune=not args.no_autotune)
     line = {"metric": "GS/s", "value": leg["value"], "unit": "GS/s", "n_gpus": 1, "steps": 1, "warmup": 0,
