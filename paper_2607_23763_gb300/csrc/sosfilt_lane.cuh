@@ -422,9 +422,10 @@ __device__ __forceinline__ float packed_row(const float *__restrict__ A, const f
 }
 
 // One tile's work of the coordinator warp: decoupled lookback over tiles (Sec. IV-B, Eq. 25 on the
-// cascade state) for tile cur's incoming 2K-word state Z, its resolved carry G when cur is an anchor,
-// and the incoming state of each of its W groups in z_buf[slot]: Z_0 = Z, Z_v = (A_C)^v Z + c_{v-1}
-// with c_v the fold's carry of groups 0 .. v under zero input (pref), all independent products.
+// cascade state) for tile cur's incoming 2K-word state Z, posted in row 0 of z_buf[slot], and its
+// resolved carry G when cur is an anchor.  The warp correcting group v then forms the group's own
+// incoming state Z_v = (A_C)^v Z + c_{v-1}, with c_v the fold's carry of groups 0 .. v under zero
+// input (pref): independent products, one per warp.
 // The composition is fixed, so that outputs are reproducible bit for bit:
 //   * every tile first sums the local carries L of the tiles after the anchor a below it (a multiple
 //     of 32): P = sum_{k=1}^{cur-1-a} (A_T)^(k-1) L(cur - k);
@@ -556,14 +557,8 @@ __device__ __forceinline__ void coordinate_tile(const LaneParams<K> &p, int lane
         }
     }
     if (tr) tr[2] = global_ns();
-    float *zb = z_buf + slot * W * S;
-    const float *pb = pref + slot * W * S;
-    if (lane < S) zb[lane] = zi_lane;
-#pragma unroll
-    for (int w = 1; w < W; ++w) {
-        const float zw = lane_mv<S>(mats.ACp + (w - 1) * S * S, zi_lane, lane) + pb[(w - 1) * S + li];
-        if (lane < S) zb[w * S + lane] = zw;
-    }
+    // the tile's incoming state; each group's is formed by the warp that corrects it
+    if (lane < S) z_buf[slot * W * S + lane] = zi_lane;
 }
 
 template <int K, int N, bool NORM, int W>

@@ -523,7 +523,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) sos_tc_kernel(const __grid_cons
                 float st[S];
 #pragma unroll
                 for (int j = 0; j < S; ++j) st[j] = Sp[j];
-                lane_state_mv<K>(sML + lane * MS, z_buf + (ps * kTcW + v) * S, st);
+                {
+                    // this warp's group state Z_v = (A_C)^v Z + c_{v-1} from the tile's Z and the fold's
+                    // prefix carries, into the group's row of z_buf (read back as a broadcast below)
+                    const int li = lane < S ? lane : 0;
+                    float *zv = z_buf + (ps * kTcW + v) * S;
+                    const float z0 = z_buf[ps * kTcW * S + li];
+                    const float w = v == 0 ? z0 : lane_mv<S>(sACp + (v - 1) * S * S, z0, lane) + pref[(ps * kTcW + v - 1) * S + li];
+                    __syncwarp();
+                    if (v > 0 && lane < S) zv[lane] = w;
+                    __syncwarp();
+                    lane_state_mv<K>(sML + lane * MS, zv, st);
+                }
                 const long long g = prev * kTcW + v;
                 if (want_zf && g == g_last && lane == lane_last) {
                     // final state: the lane's zero-state state after its last sample (G restricted to
