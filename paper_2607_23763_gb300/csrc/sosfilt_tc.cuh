@@ -23,11 +23,14 @@
 //               incoming states (on two different SM schedulers: 3 % faster at orders 8 and 16
 //               than both on the first)
 //   warp 12     producer: tickets, TMA loads of the units' rows (the ragged last row patched in)
-//   warp 2      tensor-memory owner; lane 0 issues every tcgen05.mma and commit
+//   warp 2      tensor-memory owner; lane 0 issues the units' products (particular solution and
+//               terminal states) and their commits
 //   warp 3      split of the staged input into its TF32 remainder
 //   warps 4-11  epilogue: warpgroup u (warps 4 + 4u .. 7 + 4u) takes unit u of every tile, warp
 //               q of it group 4u + q, reading accumulator lanes 32q..32q+31: terminal states,
-//               lane scan, fold, true row states, outputs staged for TMA stores
+//               lane scan, fold, true row states, the correction's products (issued by the
+//               warpgroup's first thread once its rows of the state operand are written: 3-5 %
+//               faster than handing them to warp 2), outputs staged for TMA stores
 // Pipelines: 2 input stages, 6 accumulator slots of 80 columns (tensor memory, 512 columns), one
 // state-and-output buffer per epilogue warpgroup.  Every wait is bounded by the spin budget.
 #pragma once
@@ -198,7 +201,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sos_tc_kernel(const __grid_cons
 
     __shared__ unsigned long long full[XS], mma_a[XS], conv[XS], xfree[XS];
     __shared__ unsigned long long dfull[kTcDS], dfree[kTcDS];
-    __shared__ unsigned long long st_ready[kTcUnits], corr_done[kTcUnits], patch_bar, mma_fin;
+    __shared__ unsigned long long corr_done[kTcUnits], patch_bar, mma_fin;
     __shared__ unsigned long long bar_local[2], bar_zready[2];
     __shared__ long long xs_tile[XS];  // tile of the unit in each input stage, -1: no more tiles
     __shared__ long long d_tile[kTcDS];   // tile of the unit in each accumulator slot, -1: no more
@@ -237,10 +240,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sos_tc_kernel(const __grid_cons
             mbar_init(&dfull[i], 2);  // the MMAs' commit and the issuing thread's arrival (slot's tile)
             mbar_init(&dfree[i], 4);
         }
-        for (int u = 0; u < kTcUnits; ++u) {
-            mbar_init(&st_ready[u], 4);
-            mbar_init(&corr_done[u], 1);
-        }
+        for (int u = 0; u < kTcUnits; ++u) mbar_init(&corr_done[u], 1);
         mbar_init(&patch_bar, 1);
         mbar_init(&mma_fin, 1);
         for (int i = 0; i < 2; ++i) {
@@ -353,12 +353,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) sos_tc_kernel(const __grid_cons
     } else if (warp == 2) {
         // ------------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            constexpr unsigned i80 = tc_idesc(kTcCols), i64 = tc_idesc(kTcN);
-            const unsigned b1h = smem_u32(sm), b1l = b1h + kTcB1, b2 = b1h + 2 * kTcB1;
-            const unsigned yb = smem_u32(sm + Td::OFF_Y), xb = smem_u32(sm + kTcOffX);
-            // units through the first products (ia), through the remainder (ib); corrections issued per
-            // epilogue warpgroup (ic[u]: units 2 ic[u] + u)
-            unsigned ia = 0, ib = 0, ic[kTcUnits] = {};
+            constexpr unsigned i80 = tc_idesc(kTcCols);
+            const unsigned b1h = smem_u32(sm), b1l = b1h + kTcB1;
+            const unsigned xb = smem_u32(sm + kTcOffX);
+            // units through the first products (ia), through the remainder (ib); the corrections are
+            // issued by the epilogue warpgroups
+            unsigned ia = 0, ib = 0;
             bool no_more = false, term_sent = false;
             long long t_idle = clock64();
             auto chain = [&](unsigned d, unsigned a, unsigned b, bool first) {
@@ -373,26 +373,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) sos_tc_kernel(const __grid_cons
             };
             for (;;) {
                 bool prog = false;
-#pragma unroll
-                for (int u = 0; u < kTcUnits; ++u) {
-                    const unsigned unit = ic[u] * kTcUnits + u;
-                    if (unit < ib && mbar_try_wait(&st_ready[u], ic[u] & 1)) {
-                        tc_fence_after();
-                        const unsigned d = tmem + (unit % kTcDS) * kTcCols, st = yb + u * kTcXBytes;
-                        // Y += St H_hi + St_lo H_hi + St H_lo: St | St_lo in the row's two 64-byte
-                        // halves, H_hi | H_lo likewise; 2K <= 8 state words take one K step of 8
-#pragma unroll
-                        for (int kk = 0; kk < (S > 8 ? 2 : 1); ++kk) {
-                            tc_mma(d, tc_sdesc(st + 32 * kk), tc_sdesc(b2 + 32 * kk), i64, 1u);
-                            tc_mma(d, tc_sdesc(st + 64 + 32 * kk), tc_sdesc(b2 + 32 * kk), i64, 1u);
-                            tc_mma(d, tc_sdesc(st + 32 * kk), tc_sdesc(b2 + 64 + 32 * kk), i64, 1u);
-                        }
-                        tc_commit(&corr_done[u]);
-                        if (u == 0) trace(d_tile[unit % kTcDS], 20);
-                        ++ic[u];
-                        prog = true;
-                    }
-                }
                 if (ib < ia && mbar_try_wait(&conv[ib % XS], (ib / XS) & 1)) {
                     tc_fence_after();
                     chain(tmem + (ib % kTcDS) * kTcCols, xb + (ib % XS) * kTcXBytes, b1h, false);  // X_lo B_hi
@@ -430,7 +410,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sos_tc_kernel(const __grid_cons
                     term_sent = true;
                     prog = true;
                 }
-                if (term_sent && ic[0] + ic[1] == ia) break;
+                if (term_sent) break;
                 if (prog) {
                     t_idle = clock64();
                 } else if (clock64() - t_idle > budget) {
@@ -567,9 +547,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) sos_tc_kernel(const __grid_cons
                     *reinterpret_cast<float4 *>(buf + tc_swz(r, 4 * ch)) = make_float4(e[0], e[1], e[2], e[3]);
                 }
                 fence_proxy_async_smem();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&st_ready[u]);
+                named_bar_sync(1 + u, 128);  // the warpgroup's rows of the operand are written
                 if (tw && u == 0) trace(prev, 11);
+                if (lead) {
+                    // Y += St H_hi + St_lo H_hi + St H_lo: St | St_lo in the row's two 64-byte halves,
+                    // H_hi | H_lo likewise; 2K <= 8 state words take one K step of 8
+                    tc_fence_after();
+                    const unsigned d = tmem + pds * kTcCols, sa = smem_u32(buf), b2 = smem_u32(sm) + 2 * kTcB1;
+                    constexpr unsigned i64 = tc_idesc(kTcN);
+#pragma unroll
+                    for (int kk = 0; kk < (S > 8 ? 2 : 1); ++kk) {
+                        tc_mma(d, tc_sdesc(sa + 32 * kk), tc_sdesc(b2 + 32 * kk), i64, 1u);
+                        tc_mma(d, tc_sdesc(sa + 64 + 32 * kk), tc_sdesc(b2 + 32 * kk), i64, 1u);
+                        tc_mma(d, tc_sdesc(sa + 32 * kk), tc_sdesc(b2 + 64 + 32 * kk), i64, 1u);
+                    }
+                    tc_commit(&corr_done[u]);
+                    if (u == 0) trace(prev, 20);
+                }
                 if (!mbar_wait(&corr_done[u], c & 1, budget, p.status)) break;
                 if (tw) trace(prev, u == 0 ? 12 : 24);
                 ++c;
