@@ -321,10 +321,9 @@ __device__ __forceinline__ void lane_state_mv(const float *__restrict__ A, const
     }
 }
 
-// Dense matrices the coordinator applies (column-major S x S): A_T, (A_T)^32, (A_T)^31, and
-// (A_C)^v for v = 1 .. W - 1 (consecutive).
+// Dense matrices the coordinator applies (column-major S x S): A_T, (A_T)^32 and (A_T)^31.
 struct CoordMats {
-    const float *AT, *AT32, *AT31, *ACp;
+    const float *AT, *AT32, *AT31;
 };
 
 constexpr long long kAnchor = 32;      // tiles between anchors
@@ -441,8 +440,7 @@ __device__ __forceinline__ float packed_row(const float *__restrict__ A, const f
 template <int K, int W, int MS, int P2, int SH>
 __device__ __forceinline__ void coordinate_tile(const LaneParams<K> &p, int lane, long long cur, unsigned slot,
                                                 long long budget, const float *sATl, const CoordMats &mats,
-                                                const float *pref, float *z_buf, const float *agg,
-                                                unsigned long long *tr) {
+                                                float *z_buf, const float *agg, unsigned long long *tr) {
     constexpr int S = 2 * K;
     const unsigned tagL = (p.epoch << 2) | 1u, tagG = (p.epoch << 2) | 2u, tagW = (p.epoch << 2) | 3u;
     auto zinit = [&](int i) -> float { return p.zi ? p.zi[i] * p.sec[i >> 1].zscale : 0.f; };

@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sos_tc_kernel(const __grid_cons
     float *sAT31d = tabs + Td::T_AT31;
     float *sACp = tabs + Td::T_ACP;
     float *pref = tabs + Td::T_PREF;
-    const CoordMats mats{sATd, sAT32d, sAT31d, sACp};
+    const CoordMats mats{sATd, sAT32d, sAT31d};
     float *a_buf = tabs + Td::T_A;
     float *z_buf = tabs + Td::T_Z;
     float *agg = tabs + Td::T_AGG;
@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sos_tc_kernel(const __grid_cons
                 tr[1] = global_ns();
                 tr[13] = smid;
             }
-            coordinate_tile<K, kTcW, MS, Dm::P2, Dm::SH>(p, lane, cur, slot, budget, sATl, mats, pref, z_buf, agg, tr);
+            coordinate_tile<K, kTcW, MS, Dm::P2, Dm::SH>(p, lane, cur, slot, budget, sATl, mats, z_buf, agg, tr);
             __syncwarp();
             if (lane == 0) mbar_arrive(&bar_zready[slot]);
             if (tr) tr[3] = global_ns();
