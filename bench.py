@@ -644,7 +644,7 @@ def plain_rates_by_sections(torch, dev, plain: dict, steps: int = 5, warmup: int
 
 
 def batched_leg(torch, dev, steps: int = 5, warmup: int = 3, no_cpu: bool = False, plain=None,
-                autotune: bool = True):
+                autotune: bool = True, n_sig: int = 4096):
     """Batched mix: 4096 signals (orders 2/4/8/16, lengths 2^10..2^22) in one sos_filter_run_batch call
     per step; GS/s of the whole batch, the same batch as a prepared plan replayed from a CUDA graph,
     and both as a fraction of the plain kernel's time for the same signals at each signal's order.
@@ -654,7 +654,6 @@ def batched_leg(torch, dev, steps: int = 5, warmup: int = 3, no_cpu: bool = Fals
     from paper_2607_23763_gb300 import (SosFilter, run_batch, batch_sync_status, BatchPlan, autotune_batch,
                                         autotune_batch_choice)
 
-    n_sig = 4096
     specs = [workloads.batched_signal(i) for i in range(n_sig)]
     tune_gss = autotune_batch() if autotune else None
     geom = [autotune_batch_choice(sos.shape[0], n) or 64 for sos, n, _ in specs]
@@ -710,7 +709,7 @@ def batched_leg(torch, dev, steps: int = 5, warmup: int = 3, no_cpu: bool = Fals
     del graph
     rate = plain_rates_by_sections(torch, dev, plain if plain is not None else {})
     plain_ms = sum(n / rate[sos.shape[0]] / 1e6 for sos, n, _ in specs)
-    out = {"workload": "batched mix: 4096 float32 signals, lengths round(2^U), U~U[10,22], orders uniform over "
+    out = {"workload": f"batched mix: {n_sig} float32 signals, lengths round(2^U), U~U[10,22], orders uniform over "
                        "{2,4,8,16}, random stable sections, N(0,1) input, seeds 1000+i",
            "samples": total, "l2": "inputs and outputs larger than L2",
            # the workload's configuration: one persistent launch, captured into a CUDA graph
@@ -753,7 +752,7 @@ def bench_batched(args):
     torch.cuda.set_device(0)
     _autotune_plain(args)
     leg = batched_leg(torch, torch.device("cuda", 0), args.steps, args.warmup, args.no_cpu,
-                      autotune=not args.no_autotune)
+                      autotune=not args.no_autotune, n_sig=args.batch_signals)
     line = {"metric": "GS/s", "value": leg["value"], "unit": "GS/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": leg["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -932,6 +931,8 @@ def main():
     ap.add_argument("--workload", default="plain", choices=["plain", "batched", "serving", "precision"],
                     help="plain = the order-16 single-signal workload (default); batched / serving mixes")
     ap.add_argument("--streams", type=int, default=10000, help="serving: streams")
+    ap.add_argument("--batch-signals", type=int, default=4096,
+                    help="batched: the first M signals of the mix (4096 = the workload; fewer for profiling captures)")
     ap.add_argument("--chunks-per-stream", type=int, default=10, help="serving: closed-loop chunks per stream")
     ap.add_argument("--open-requests", type=int, default=110000, help="serving: open-loop requests")
     ap.add_argument("--serving-open-requests", type=int, default=30000,
