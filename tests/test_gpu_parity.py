@@ -445,14 +445,16 @@ def _full_error_chunked(sos, x_host, y_dev, chunk=1 << 24):
     return num / den
 
 
-def test_precision_resonator_bank_full_size(dev):
+@pytest.mark.parametrize("tuning", [{"solver": SOLVER_PH}, {"solver": SOLVER_TC}], ids=["ph-64", "tc-64"])
+def test_precision_resonator_bank_full_size(dev, tuning):
     """Order-16 resonator bank (poles at radius 0.999, angles 0.30..0.34 pi), 2^30 samples of N(0,1)
     plus a unit sinusoid at 0.32 pi, seed 4; float32 path with float32 carries against the float64
-    oracle over every sample.  Bound 2e-3 (pole radius above 0.99)."""
+    oracle over every sample, on the FMA recurrence and on the tensor cores.  Bound 2e-3 (pole radius
+    above 0.99)."""
     sos = designs.resonator_bank()
     n = 1 << 30
     x = workloads.normal_f32(4, n, sin_amp=1.0, sin_omega=0.32 * np.pi)
-    f = _filt(sos)
+    f = _filt(sos, tuning=tuning)
     xd = torch.from_numpy(x).to(dev)
     y = f.run(xd)
     torch.cuda.synchronize()
