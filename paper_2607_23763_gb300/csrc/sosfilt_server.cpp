@@ -65,9 +65,13 @@ struct sos_server {
     sos_server_config cfg{};
     std::mutex mu;
     std::condition_variable cv;     // scheduler: new work or completions
-    std::condition_variable cv_done;  // pollers: new completions
+    std::condition_variable cv_done;  // drain and state readers: streams released
     std::deque<Stream> streams;     // a deque: adding a stream never moves the others
     std::deque<int> ready;          // idle streams with a queued chunk, in order of readiness
+    // completion records for the pollers, under their own lock, so that collecting them does not
+    // hold up admission
+    std::mutex mu_rec;
+    std::condition_variable cv_rec;
     std::vector<sos_completion> done;
     uint64_t next_id = 1;
     int64_t inflight_bytes = 0;
@@ -77,7 +81,7 @@ struct sos_server {
     std::vector<cudaStream_t> cstreams;
     int next_cs = 0;
     bool stop = false;
-    int sticky = SOS_OK;            // first error of a batch launch
+    std::atomic<int> sticky{SOS_OK};  // first error of a batch launch (written under mu)
     std::deque<Batch *> to_launch;  // admitted batches, in admission order, for the launcher threads
     std::condition_variable cv_launch;
     bool sched_done = false;        // the scheduler has exited; the launchers drain and exit
@@ -119,7 +123,6 @@ void complete_batch(Batch *b) {
     }
     {
         std::lock_guard<std::mutex> lk(s->mu);
-        s->done.insert(s->done.end(), recs.begin(), recs.end());
         for (const Req &r : b->reqs) {
             Stream &st = s->streams[r.sid];
             st.busy = false;
@@ -134,6 +137,11 @@ void complete_batch(Batch *b) {
     }
     s->cv.notify_all();
     s->cv_done.notify_all();
+    {
+        std::lock_guard<std::mutex> lk(s->mu_rec);
+        s->done.insert(s->done.end(), recs.begin(), recs.end());
+    }
+    s->cv_rec.notify_all();
     delete b;
 }
 
@@ -434,21 +442,21 @@ sos_status sos_server_submit(sos_server *s, int stream_id, const float *x_dev, f
 
 sos_status sos_server_poll(sos_server *s, sos_completion *out, int max, int *n_out, int wait_ms) {
     if (!s || !n_out || max < 0 || (max > 0 && !out)) return SOS_EINVAL;
-    std::unique_lock<std::mutex> lk(s->mu);
+    std::unique_lock<std::mutex> lk(s->mu_rec);
     if (s->done.empty() && wait_ms > 0)
-        s->cv_done.wait_for(lk, std::chrono::milliseconds(wait_ms), [&] { return !s->done.empty(); });
+        s->cv_rec.wait_for(lk, std::chrono::milliseconds(wait_ms), [&] { return !s->done.empty(); });
     const int k = std::min<int>(max, static_cast<int>(s->done.size()));
     for (int i = 0; i < k; ++i) out[i] = s->done[i];
     s->done.erase(s->done.begin(), s->done.begin() + k);
     *n_out = k;
-    return static_cast<sos_status>(s->sticky);
+    return static_cast<sos_status>(s->sticky.load());
 }
 
 sos_status sos_server_drain(sos_server *s) {
     if (!s) return SOS_EINVAL;
     std::unique_lock<std::mutex> lk(s->mu);
     s->cv_done.wait(lk, [&] { return s->queued == 0; });
-    return static_cast<sos_status>(s->sticky);
+    return static_cast<sos_status>(s->sticky.load());
 }
 
 sos_status sos_server_stream_state(sos_server *s, int stream_id, float *z_host) {
@@ -526,9 +534,9 @@ sos_status sos_server_replay(sos_server *s, int64_t n_req, const int32_t *stream
     // collect the completions of this replay
     int64_t got = 0;
     const uint64_t first = n_req ? ids[0] : 0;
-    std::unique_lock<std::mutex> lk(s->mu);
+    std::unique_lock<std::mutex> lk(s->mu_rec);
     while (got < n_req) {
-        s->cv_done.wait_for(lk, std::chrono::milliseconds(50), [&] { return !s->done.empty(); });
+        s->cv_rec.wait_for(lk, std::chrono::milliseconds(50), [&] { return !s->done.empty(); });
         for (const sos_completion &c : s->done) {
             const int64_t k = static_cast<int64_t>(c.request_id - first);
             if (k >= 0 && k < n_req && ids[k] == c.request_id) {
@@ -537,7 +545,7 @@ sos_status sos_server_replay(sos_server *s, int64_t n_req, const int32_t *stream
             }
         }
         s->done.clear();
-        if (s->sticky != SOS_OK) return static_cast<sos_status>(s->sticky);
+        if (s->sticky != SOS_OK) return static_cast<sos_status>(s->sticky.load());
     }
     return SOS_OK;
 }
