@@ -44,8 +44,8 @@ SOLVER_CR, SOLVER_PH, SOLVER_DTCR, SOLVER_TC = 1, 2, 3, 4
 TRAFFIC_BYTES_2P28 = {
     # sos_lane_kernel<8, 64, 7> at 2^26 samples: 268,859,904 B read + 211,708,672 B written
     (SOLVER_PH, 64): 4 * (268859904 + 211708672),
-    # sos_tc_kernel<8> at 2^26 samples: 269,069,824 B read + 213,070,848 B written
-    (SOLVER_TC, 64): 4 * (269069824 + 213070848),
+    # sos_tc_kernel<8> at 2^26 samples: 269,061,632 B read + 213,409,792 B written
+    (SOLVER_TC, 64): 4 * (269061632 + 213409792),
 }
 PH_GROUPS_PER_BLOCK = 7
 CR_GROUPS_PER_BLOCK = {32: 8, 64: 4}
