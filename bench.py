@@ -595,7 +595,7 @@ def bench_ours(args):
         _leg("batched", batched_leg, line, torch, dev, steps=5, warmup=3, no_cpu=args.no_cpu, plain=plain,
              autotune=not args.no_autotune)
         torch.cuda.empty_cache()
-        _leg("serving", serving_leg, line, torch, dev, n_streams=args.streams, per_stream=2,
+        _leg("serving", serving_leg, line, torch, dev, n_streams=args.streams, per_stream=args.chunks_per_stream,
              n_open=args.serving_open_requests, plain=plain, autotune=not args.no_autotune)
     line["wall_s"] = round(time.perf_counter() - t_start, 1)
     if rank == 0:
